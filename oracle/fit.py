@@ -1,0 +1,95 @@
+"""Plain FP64 oracle of the offline OpInf stage (POD bases + Tikhonov least squares).
+
+TEST INFRASTRUCTURE ONLY (tests/, smoke() and bench.py's CPU legs).  Library primitives serve as
+steps: numpy's thin SVD for POD and a dense solve of the normal equations for the regression.
+
+  * POD (Sec. 3.1, Eq. pod_cutoff): thin SVD U = Phi Sigma Psi^T of the uncentered snapshot matrix,
+    basis = first r left singular vectors (Euclidean inner product).
+  * energy criterion (Eq. pod_energy): E_r = sum_{i<=r} sigma_i^2 / sum_i sigma_i^2; the reduced
+    dimension is the smallest r with E_r >= delta_E.
+  * boundary POD (Sec. 4.2.1): a separate basis Phi_S of the Schwarz boundary snapshots, reduced
+    boundary data ghat = Phi_S^T s.
+  * regression (Eq. opinf_schwarz_inference), solved form qdd = K q + H kron_c(q) + B ghat + c:
+    minimise ||D O - Y||_F^2 + lambda ||O||_F^2 with D = [Ubar^T, kron_c(Ubar)^T, Ghat^T, 1],
+    Y = Abar^T (projected acceleration snapshots), one scalar lambda for every block.
+  * kron_c(q) = (q_i q_j)_{i <= j} in row-major upper-triangle order (compressed symmetric
+    Kronecker square, the footnote of Sec. 2).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def pod(U: np.ndarray, r: int):
+    """Thin SVD of the snapshot matrix U (n_dof x n_snap); returns (Phi_r, sigma)."""
+    Phi, sigma, _ = np.linalg.svd(U, full_matrices=False)
+    return Phi[:, :r].copy(), sigma
+
+
+def energy(sigma: np.ndarray) -> np.ndarray:
+    """E_r for r = 1..len(sigma)."""
+    s2 = sigma.astype(np.float64) ** 2
+    return np.cumsum(s2) / s2.sum()
+
+
+def energy_rank(sigma: np.ndarray, delta: float, r_max: int) -> int:
+    E = energy(sigma)
+    r = int(np.searchsorted(E, delta, side="left")) + 1
+    return max(1, min(r, r_max, len(sigma)))
+
+
+def kron_c(Q: np.ndarray) -> np.ndarray:
+    """Compressed Khatri-Rao square of the columns of Q (r x n) -> (r(r+1)/2 x n)."""
+    r = Q.shape[0]
+    rows = []
+    for i in range(r):
+        for j in range(i, r):
+            rows.append(Q[i] * Q[j])
+    return np.array(rows)
+
+
+def data_matrix(Ubar: np.ndarray, Ghat: np.ndarray, quadratic: bool = True) -> np.ndarray:
+    blocks = [Ubar.T]
+    if quadratic:
+        blocks.append(kron_c(Ubar).T)
+    blocks.append(Ghat.T)
+    blocks.append(np.ones((Ubar.shape[1], 1)))
+    return np.hstack(blocks)
+
+
+def tikhonov(D: np.ndarray, Y: np.ndarray, lam: float) -> np.ndarray:
+    """argmin_O ||D O - Y||_F^2 + lam ||O||_F^2 via the normal equations (D^T D + lam I) O = D^T Y."""
+    d = D.shape[1]
+    return np.linalg.solve(D.T @ D + lam * np.eye(d), D.T @ Y)
+
+
+def unpack(O: np.ndarray, r: int, r_s: int, quadratic: bool = True):
+    nq = r * (r + 1) // 2 if quadratic else 0
+    K = O[:r].T.copy()
+    H = O[r:r + nq].T.copy() if quadratic else np.zeros((r, r * (r + 1) // 2))
+    B = O[r + nq:r + nq + r_s].T.copy()
+    c = O[r + nq + r_s].copy()
+    return K, H, B, c
+
+
+def opinf_fit(U: np.ndarray, A: np.ndarray, S: np.ndarray, r: int, lam: float, r_s: int = None,
+              energy_s: float = 1.0 - 1e-6, r_s_max: int = 64, quadratic: bool = True):
+    """U, A: free-dof displacement / acceleration snapshots (n_dof x n_snap); S: Schwarz boundary
+    snapshots (n_sdof x n_snap).  Returns the ROM operators and bases."""
+    Phi, sigma = pod(U, r)
+    _, sigma_s, _ = np.linalg.svd(S, full_matrices=False)
+    if r_s is None:
+        r_s = energy_rank(sigma_s, energy_s, r_s_max)
+    Phi_S, _ = pod(S, r_s)
+    Ubar = Phi.T @ U
+    Abar = Phi.T @ A
+    Ghat = Phi_S.T @ S
+    D = data_matrix(Ubar, Ghat, quadratic)
+    O = tikhonov(D, Abar.T, lam)
+    K, H, B, c = unpack(O, r, r_s, quadratic)
+    return {"Phi": Phi, "Phi_S": Phi_S, "K": K, "H": H, "B": B, "c": c, "sigma": sigma, "sigma_s": sigma_s,
+            "r": r, "r_s": r_s}
+
+
+def rom_rhs(K, H, B, c, q, ghat):
+    return K @ q + H @ kron_c(q[:, None])[:, 0] + B @ ghat + c

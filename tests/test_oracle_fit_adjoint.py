@@ -1,0 +1,142 @@
+"""Pins of the oracle's offline OpInf fit and of its reverse-mode adjoint (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle import fit as OF
+from paper_2511_20687_gb300 import workloads as W
+
+
+def _orthonormal(n, r, rng):
+    q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return q
+
+
+def test_pod_eckart_young_and_orthonormality():
+    """Eq. pod_cutoff: ||U - Phi_r Phi_r^T U||_F^2 = sum_{i>r} sigma_i^2, Phi_r orthonormal, and the
+    energy rank is the smallest r with E_r >= delta (Eq. pod_energy, reading of its inequality)."""
+    rng = np.random.default_rng(0)
+    U = rng.standard_normal((300, 40)) @ np.diag(0.7 ** np.arange(40)) @ rng.standard_normal((40, 60))
+    for r in (3, 10, 25):
+        Phi, s = OF.pod(U, r)
+        resid = np.linalg.norm(U - Phi @ (Phi.T @ U)) ** 2
+        assert abs(resid - np.sum(s[r:] ** 2)) < 1e-10 * np.sum(s ** 2)
+        assert np.abs(Phi.T @ Phi - np.eye(r)).max() < 1e-13
+    E = OF.energy(s)
+    r = OF.energy_rank(s, 0.999, 100)
+    assert E[r - 1] >= 0.999 and E[r - 2] < 0.999
+
+
+def test_kron_c_order():
+    q = np.array([2.0, 3.0, 5.0])
+    assert np.allclose(OF.kron_c(q[:, None])[:, 0], [4, 6, 10, 9, 15, 25])
+
+
+def test_tikhonov_equals_augmented_least_squares():
+    """The regularised problem equals plain least squares on [D; sqrt(lam) I] O = [Y; 0]."""
+    rng = np.random.default_rng(1)
+    D = rng.standard_normal((50, 80))
+    Y = rng.standard_normal((50, 6))
+    lam = 1e-3
+    O = OF.tikhonov(D, Y, lam)
+    Da = np.vstack([D, np.sqrt(lam) * np.eye(80)])
+    Ya = np.vstack([Y, np.zeros((80, 6))])
+    O2 = np.linalg.lstsq(Da, Ya, rcond=None)[0]
+    assert np.abs(O - O2).max() < 1e-10 * np.abs(O2).max()
+    # dual form D^T (D D^T + lam I)^-1 Y gives the same minimiser
+    O3 = D.T @ np.linalg.solve(D @ D.T + lam * np.eye(50), Y)
+    assert np.abs(O - O3).max() < 1e-9 * np.abs(O3).max()
+
+
+def test_opinf_recovers_known_quadratic_operators():
+    """Consistency of OpInf (Sec. 3.2): data drawn from a known quadratic model
+    qdd = K q + H kron_c(q) + B ghat + c in known orthonormal bases is recovered with lambda -> 0.
+    Bases are unique only up to rotation, so the check is basis-invariant: full-space accelerations
+    Phi rhs(Phi^T u, Phi_S^T s) at fresh states."""
+    rng = np.random.default_rng(2)
+    n, ns, r, rs = 120, 30, 5, 3
+    nq = r * (r + 1) // 2
+    Phi_t, PhiS_t = _orthonormal(n, r, rng), _orthonormal(ns, rs, rng)
+    K = rng.standard_normal((r, r))
+    H = rng.standard_normal((r, nq))
+    B = rng.standard_normal((r, rs))
+    c = rng.standard_normal(r)
+    nsnap = 3 * (r + nq + rs + 1)
+    # well-spread singular values so the POD ordering is unambiguous
+    Q = np.diag([5.0, 4.0, 3.0, 2.0, 1.0]) @ rng.standard_normal((r, nsnap))
+    G = np.diag([3.0, 2.0, 1.0]) @ rng.standard_normal((rs, nsnap))
+    Qdd = K @ Q + H @ OF.kron_c(Q) + B @ G + c[:, None]
+    U, A, S = Phi_t @ Q, Phi_t @ Qdd, PhiS_t @ G
+    ops = OF.opinf_fit(U, A, S, r=r, lam=1e-14, r_s=rs)
+    q_new = rng.standard_normal((r, 10))
+    g_new = rng.standard_normal((rs, 10))
+    u_new, s_new = Phi_t @ q_new, PhiS_t @ g_new
+    for k in range(10):
+        want = Phi_t @ OF.rom_rhs(K, H, B, c, q_new[:, k], g_new[:, k])
+        q = ops["Phi"].T @ u_new[:, k]
+        g = ops["Phi_S"].T @ s_new[:, k]
+        got = ops["Phi"] @ OF.rom_rhs(ops["K"], ops["H"], ops["B"], ops["c"], q, g)
+        assert np.linalg.norm(got - want) < 1e-8 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small_adjoint_case():
+    p, w = W.adjoint_bar(n=2, nz=4, n_steps=30)
+    sd = p.subdomains[0]
+    # larger pulse so the nonlinearity matters
+    return sd, w, p.dt, 30
+
+
+@pytest.mark.parametrize("material", ["nh", "le"])
+def test_force_vjp_dot_product(oracle, small_adjoint_case, material):
+    """<ybar, (df/du) du> = <(df/du)^T ybar, du> with df/du du by central differences, and the
+    parameter gradients match central differences of ybar . f in lambda_e, mu_e."""
+    sd, _, _, _ = small_adjoint_case
+    rng = np.random.default_rng(3)
+    u = 2e-4 * rng.standard_normal((sd.n_nodes, 3))
+    y = rng.standard_normal(3 * sd.n_nodes)
+    du = rng.standard_normal(3 * sd.n_nodes)
+    ub, lb, mb = oracle.force_vjp(sd.dims, sd.h, sd.origin, material, sd.lam_e, sd.mu_e, u, y)
+    eps = 1e-7 * np.abs(u).max()
+    f = lambda uu, le=sd.lam_e, me=sd.mu_e: oracle.internal_force(sd.dims, sd.h, sd.origin, material, 0, 0, uu,  # noqa
+                                                                  lam_e=le, mu_e=me)
+    jvp = (f(u.reshape(-1) + eps * du) - f(u.reshape(-1) - eps * du)) / (2 * eps)
+    assert abs(y @ jvp - ub @ du) < 1e-7 * abs(ub @ du)
+    dl = rng.standard_normal(sd.n_elements)
+    el = 1e-6 * sd.lam
+    fl = (f(u, le=sd.lam_e + el * dl) - f(u, le=sd.lam_e - el * dl)) / (2 * el)
+    assert abs(y @ fl - lb @ dl) < 1e-7 * abs(lb @ dl)
+    em = 1e-6 * sd.mu
+    fm = (f(u, me=sd.mu_e + em * dl) - f(u, me=sd.mu_e - em * dl)) / (2 * em)
+    assert abs(y @ fm - mb @ dl) < 1e-7 * abs(mb @ dl)
+
+
+def test_rollout_adjoint_matches_central_differences(oracle, small_adjoint_case):
+    """Gradients of J = w . u_T through the explicit rollout vs central differences (relative 1e-6)."""
+    sd, w, dt, nsteps = small_adjoint_case
+    args = (sd.dims, sd.h, sd.origin, "nh")
+    u0 = sd.u0 * 3.0
+    J, gu, gv, gl, gm = oracle.adjoint(*args, sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, u0, None, dt, nsteps, w)
+    rng = np.random.default_rng(4)
+
+    def Jof(uu=u0, vv=None, le=sd.lam_e, me=sd.mu_e):
+        return w.reshape(-1) @ oracle.rollout(*args, le, me, sd.rho, sd.dirichlet, uu, vv, dt, nsteps)
+
+    assert abs(Jof() - J) < 1e-14 * abs(J)
+    d = rng.standard_normal(u0.shape)
+    d[np.repeat(sd.dirichlet, 3).reshape(-1, 3) > 0] = 0
+    h = 1e-6 * np.abs(u0).max()
+    fd = (Jof(uu=u0 + h * d) - Jof(uu=u0 - h * d)) / (2 * h)
+    assert abs(fd - gu @ d.reshape(-1)) < 1e-6 * abs(fd)
+    hv = 1e-6 * np.abs(u0).max() / dt
+    fdv = (Jof(vv=hv * d) - Jof(vv=-hv * d)) / (2 * hv)
+    assert abs(fdv - gv @ d.reshape(-1)) < 1e-6 * abs(fdv)
+    dl = rng.standard_normal(sd.n_elements)
+    hl = 1e-6 * sd.lam
+    fdl = (Jof(le=sd.lam_e + hl * dl) - Jof(le=sd.lam_e - hl * dl)) / (2 * hl)
+    assert abs(fdl - gl @ dl) < 1e-6 * abs(fdl)
+    hm = 1e-6 * sd.mu
+    fdm = (Jof(me=sd.mu_e + hm * dl) - Jof(me=sd.mu_e - hm * dl)) / (2 * hm)
+    assert abs(fdm - gm @ dl) < 1e-6 * abs(fdm)

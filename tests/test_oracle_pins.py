@@ -1,0 +1,336 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test checks the oracle against something other than itself: a closed form printed in the
+paper, an energy whose derivative the stress must be, an invariant of the discretisation or of
+the time integrator, or a special case that reduces to a known answer.  A plausible slip in the
+oracle (a dropped term, a wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2511_20687_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LAM, MU = W.lame(1e9, 0.25)
+
+
+def _rand_disp(dims, scale, seed):
+    nx, ny, nz = dims
+    return scale * np.random.default_rng(seed).standard_normal(((nx + 1) * (ny + 1) * (nz + 1), 3))
+
+
+def _coords(dims, h, origin):
+    sd = W.Subdomain(kind="fom", dims=dims, h=h, origin=origin)
+    return sd.node_coords(), sd.node_grid()
+
+
+# ---------------------------------------------------------------------------------------------
+# constitutive laws (Appendix A)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("material", ["le", "nh"])
+def test_stress_is_derivative_of_energy_density(oracle, material):
+    """P = dA/dF for the energies printed in Appendix A (A.1: 1/2 lam tr(eps)^2 + mu tr(eps^2);
+    A.3: 1/4 kappa (detC - log detC - 1) + 1/2 mu (detC^-1/3 trC - 3)).  This pins the
+    deviatoric coefficient 1/3 of S (the printed 1/2 would fail by O(mu))."""
+    rng = np.random.default_rng(1)
+    for trial in range(5):
+        H = 0.05 * rng.standard_normal((3, 3))
+        P = oracle.stress(material, H, LAM, MU)
+        fd = np.zeros((3, 3))
+        eps = 1e-6
+        for i in range(3):
+            for j in range(3):
+                Hp, Hm = H.copy(), H.copy()
+                Hp[i, j] += eps
+                Hm[i, j] -= eps
+                fd[i, j] = (oracle.energy_density(material, Hp, LAM, MU)
+                            - oracle.energy_density(material, Hm, LAM, MU)) / (2 * eps)
+        assert np.abs(P - fd).max() < 1e-6 * np.abs(P).max()
+
+
+def test_printed_half_coefficient_would_fail(oracle):
+    """The stress the oracle uses differs from the variant with the printed 1/2 coefficient, and the
+    energy derivative sides with the 1/3 one (reading c7)."""
+    H = np.diag([0.02, -0.01, 0.015]) + 0.01
+    F = np.eye(3) + H
+    C = F.T @ F
+    Ci = np.linalg.inv(C)
+    kappa = LAM + 2 * MU / 3
+    g = np.linalg.det(C) ** (-1 / 3)
+    S_half = 0.5 * kappa * (np.linalg.det(C) - 1) * Ci + MU * g * (np.eye(3) - 0.5 * np.trace(C) * Ci)
+    P = oracle.stress("nh", H, LAM, MU)
+    assert np.abs(P - F @ S_half).max() > 1e-3 * np.abs(P).max()
+
+
+@pytest.mark.parametrize("material", ["le", "nh"])
+def test_internal_force_is_gradient_of_discrete_energy(oracle, material):
+    """f_int = d/du of sum_e sum_gp w detJ A(F): checks quadrature, shape gradients and assembly
+    against the energy of Appendix A (central differences)."""
+    dims, h, org = (2, 2, 3), 0.01, (0.1, -0.2, 0.3)
+    u = _rand_disp(dims, 1e-3, 2)
+    f = oracle.internal_force(dims, h, org, material, LAM, MU, u)
+    eps = 1e-8
+    flat = u.reshape(-1)
+    fd = np.zeros_like(flat)
+    for d in range(flat.size):
+        up, um = flat.copy(), flat.copy()
+        up[d] += eps
+        um[d] -= eps
+        fd[d] = (oracle.strain_energy(dims, h, org, material, LAM, MU, up)
+                 - oracle.strain_energy(dims, h, org, material, LAM, MU, um)) / (2 * eps)
+    assert np.abs(f - fd).max() < 1e-6 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("material", ["le", "nh"])
+def test_patch_test_affine_field_has_zero_interior_force(oracle, material):
+    """A uniform deformation gradient gives a uniform stress, so the assembled force vanishes at
+    every interior node."""
+    dims, h, org = (3, 3, 4), 0.01, (0.0, 0.0, 0.0)
+    X, (i, j, k) = _coords(dims, h, org)
+    G = np.array([[0.01, 0.002, -0.003], [0.001, -0.004, 0.002], [0.003, 0.001, 0.006]])
+    u = X @ G.T + np.array([1e-3, -2e-3, 5e-4])
+    f = oracle.internal_force(dims, h, org, material, LAM, MU, u).reshape(-1, 3)
+    interior = (i > 0) & (i < 3) & (j > 0) & (j < 3) & (k > 0) & (k < 4)
+    scale = np.abs(f).max()
+    assert scale > 0
+    assert np.abs(f[interior]).max() < 1e-10 * scale
+
+
+def test_rigid_motion_gives_zero_force(oracle):
+    """Neo-Hookean is objective: a finite rotation plus translation gives zero force everywhere;
+    the linear elastic law gives zero force for a translation."""
+    dims, h, org = (2, 3, 2), 0.01, (0.05, 0.0, -0.02)
+    X, _ = _coords(dims, h, org)
+    th = 0.3
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    ax = np.array([1.0, 2.0, 2.0]) / 3.0
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    R = R @ (np.eye(3) + np.sin(0.4) * K + (1 - np.cos(0.4)) * K @ K)
+    u = X @ (R - np.eye(3)).T + np.array([0.1, -0.3, 0.2])
+    f = oracle.internal_force(dims, h, org, "nh", LAM, MU, u)
+    # stress scale of a 1% strain for comparison
+    u_ref = X @ (0.01 * np.eye(3)).T
+    f_ref = oracle.internal_force(dims, h, org, "nh", LAM, MU, u_ref)
+    assert np.abs(f).max() < 1e-8 * np.abs(f_ref).max()
+    ft = oracle.internal_force(dims, h, org, "le", LAM, MU, np.tile([1e-3, 2e-3, -3e-3], (X.shape[0], 1)))
+    assert np.abs(ft).max() < 1e-9 * np.abs(f_ref).max()
+
+
+def test_neo_hookean_linearises_to_linear_elastic(oracle):
+    """At small amplitude eps the NH force approaches the LE force with the same Lame pair
+    (kappa = lambda + 2/3 mu), with a relative gap of order eps."""
+    dims, h, org = (2, 2, 2), 0.01, (0.0, 0.0, 0.0)
+    base = _rand_disp(dims, 1.0, 3)
+    gaps = []
+    for eps in (1e-4, 1e-5):
+        u = eps * h * base
+        f_nh = oracle.internal_force(dims, h, org, "nh", LAM, MU, u)
+        f_le = oracle.internal_force(dims, h, org, "le", LAM, MU, u)
+        gaps.append(np.abs(f_nh - f_le).max() / np.abs(f_le).max())
+    assert gaps[0] < 1e-2
+    assert 5.0 < gaps[0] / gaps[1] < 20.0  # first order in eps
+
+
+def test_tangent_stiffness_is_symmetric(oracle):
+    """The FD Jacobian of f_int at a deformed NH state is symmetric (hyperelastic potential)."""
+    dims, h, org = (1, 2, 2), 0.01, (0.0, 0.0, 0.0)
+    u0 = _rand_disp(dims, 2e-4, 4).reshape(-1)
+    n = u0.size
+    Kt = np.zeros((n, n))
+    eps = 1e-9
+    for d in range(n):
+        up, um = u0.copy(), u0.copy()
+        up[d] += eps
+        um[d] -= eps
+        Kt[:, d] = (oracle.internal_force(dims, h, org, "nh", LAM, MU, up)
+                    - oracle.internal_force(dims, h, org, "nh", LAM, MU, um)) / (2 * eps)
+    assert np.abs(Kt - Kt.T).max() < 1e-5 * np.abs(Kt).max()
+
+
+def test_lumped_mass_totals_and_split(oracle):
+    dims, h, org = (3, 2, 4), 0.02, (0.0, 0.0, 0.0)
+    m = oracle.lumped_mass(dims, h, org, 1000.0)
+    assert abs(m.sum() - 1000.0 * 3 * 2 * 4 * h ** 3) < 1e-12 * m.sum()
+    # a corner node belongs to one element: rho V / 8
+    assert abs(m[0] - 1000.0 * h ** 3 / 8) < 1e-15
+
+
+# ---------------------------------------------------------------------------------------------
+# spatial projector Pi
+# ---------------------------------------------------------------------------------------------
+def test_projector_reproduces_trilinear_fields_and_injects_at_nodes(oracle):
+    dims, h, org = (3, 3, 5), 0.01, (0.0, 0.0, 0.0)
+    X, _ = _coords(dims, h, org)
+    rng = np.random.default_rng(5)
+    coef = rng.standard_normal(8)
+
+    def tri(p):
+        x, y, z = p[..., 0], p[..., 1], p[..., 2]
+        return (coef[0] + coef[1] * x + coef[2] * y + coef[3] * z + coef[4] * x * y + coef[5] * y * z
+                + coef[6] * x * z + coef[7] * x * y * z)
+
+    vals = tri(X)
+    for _ in range(20):
+        p = rng.uniform([0, 0, 0], [0.03, 0.03, 0.05])
+        nodes, w = oracle.donor(dims, h, org, p)
+        assert abs(w.sum() - 1.0) < 1e-14
+        assert abs(w @ vals[nodes] - tri(p)) < 1e-12
+    nodes, w = oracle.donor(dims, h, org, X[37])
+    assert np.count_nonzero(w) == 1 and nodes[np.argmax(w)] == 37 and w.max() == 1.0
+    with pytest.raises(ValueError):
+        oracle.donor(dims, h, org, np.array([0.5, 0.0, 0.0]))
+
+
+# ---------------------------------------------------------------------------------------------
+# explicit central difference + Schwarz controller
+# ---------------------------------------------------------------------------------------------
+def _wave_fixture():
+    with open(os.path.join(HERE, "golden", "wave1d_symmetric_gaussian.json")) as fh:
+        return json.load(fh)
+
+
+def _dalembert(g, z, t):
+    a, b, s = g["initial_condition"]["a"], g["initial_condition"]["b"], g["initial_condition"]["s"]
+    c = (g["E"] / g["rho"]) ** 0.5
+    T = g["T"]
+    f = lambda x: a * np.exp(-((x - b) ** 2) / (2 * s * s))  # noqa: E731
+    return 0.5 * f(z - c * t) + 0.5 * f(z + c * t) - 0.5 * f(z - c * (T - t)) - 0.5 * f(z + c * (T - t))
+
+
+def test_wave1d_matches_dalembert_at_courant_one(oracle):
+    """Sec. 5.1 bar with dt = dz/c: the lumped-mass central-difference scheme is exact at the nodes,
+    so the discrete solution equals Eq. disp_exact to rounding."""
+    g = _wave_fixture()
+    p = W.wave1d()
+    sd = p.subdomains[0]
+    assert p.dt == pytest.approx(g["dt_cfl"]) and sd.h == pytest.approx(g["dx"])
+    assert sd.origin[2] == g["domain"]["z"][0] and sd.origin[0] == g["domain"]["x"][0]
+    prob = oracle.Problem(p)
+    z = sd.node_coords()[:, 2]
+    t = 0.0
+    for _ in range(4):
+        for _ in range(10):
+            prob.step()
+            t += p.dt * p.n_substeps
+        u, _, _ = prob.state(0)
+        ex = _dalembert(g, z, t)
+        assert np.abs(u[:, 2] - ex).max() < 1e-11 * g["initial_condition"]["a"]
+        assert np.abs(u[:, :2]).max() == 0.0
+
+
+def test_wave1d_schwarz_fom_fom_matches_dalembert(oracle):
+    """FOM-FOM O-SAM on the paper's decomposition Omega_1 = (-0.5, 0.25), Omega_2 = (-0.25, 0.5)
+    reproduces the exact solution on both subdomains."""
+    g = _wave_fixture()
+    p = W.wave1d(subdomains=True, n_substeps=20)
+    assert p.subdomains[0].origin[2] + p.subdomains[0].dims[2] * p.subdomains[0].h == pytest.approx(
+        g["subdomains"]["Omega_1"][1])
+    assert p.subdomains[1].origin[2] == pytest.approx(g["subdomains"]["Omega_2"][0])
+    prob = oracle.Problem(p)
+    t = 0.0
+    for _ in range(12):  # the pulse crosses the overlap boundaries
+        r = prob.step()
+        assert r["status"] == oracle.OK
+        t += p.dt * p.n_substeps
+    for i in range(2):
+        u, _, _ = prob.state(i)
+        z = p.subdomains[i].node_coords()[:, 2]
+        assert np.abs(u[:, 2] - _dalembert(g, z, t)).max() < 1e-11 * g["initial_condition"]["a"]
+
+
+def test_leapfrog_modified_energy_is_conserved(oracle):
+    """Velocity-Verlet on M u'' = -K u conserves 1/2 v.Mv + 1/2 u.Ku - dt^2/8 a.Ma exactly; the
+    plain total energy only oscillates at O(dt^2)."""
+    p = W.single_bar("energy", 3, 8, "le", 1e9, 0.25, 1000.0, 1e-3, 2e-6, 5)
+    sd = p.subdomains[0]
+    prob = oracle.Problem(p)
+    m = oracle.lumped_mass(sd.dims, sd.h, sd.origin, sd.rho)
+    free = np.repeat(sd.dirichlet == 0, 3).reshape(-1, 3)
+
+    def energies():
+        u, v, a = prob.state(0)
+        f = oracle.internal_force(sd.dims, sd.h, sd.origin, "le", sd.lam, sd.mu, u).reshape(-1, 3)
+        kin = 0.5 * np.sum((m[:, None] * v * v)[free])
+        pot = 0.5 * np.sum((u * f)[free])
+        corr = p.dt ** 2 / 8 * np.sum((m[:, None] * a * a)[free])
+        return kin + pot - corr, kin + pot
+
+    e0, t0 = energies()
+    mods, tots = [], []
+    for _ in range(40):
+        prob.step()
+        e, t = energies()
+        mods.append(e)
+        tots.append(t)
+    assert np.abs(np.array(mods) - e0).max() < 1e-10 * e0
+    assert np.abs(np.array(tots) - t0).max() < 0.05 * t0
+
+
+def test_fom_fom_schwarz_equals_single_domain(oracle):
+    """Two conforming 6x6x12 subdomains (2-layer overlap) converge, within each controller step, to
+    the single-domain 6x6x22 explicit solution."""
+    p = W.fom_fom_plain()
+    ps = W.single_bar("single", 6, 22, "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 20)
+    A, S = oracle.Problem(p), oracle.Problem(ps)
+    for _ in range(3):
+        r = A.step()
+        S.step()
+        assert r["status"] == oracle.OK and 2 <= r["iterations"] < p.max_iters
+    us, vs, _ = S.state(0)
+    nn = 7 * 7
+    for i, k0 in ((0, 0), (1, 10)):
+        u, v, _ = A.state(i)
+        n = u.shape[0]
+        assert np.abs(u - us[k0 * nn:k0 * nn + n]).max() < 1e-12 * np.abs(us).max()
+        assert np.abs(v - vs[k0 * nn:k0 * nn + n]).max() < 1e-12 * np.abs(vs).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# OpInf ROM subdomain
+# ---------------------------------------------------------------------------------------------
+def _exact_linear_rom(oracle, p, i):
+    """Full-basis ROM of LE subdomain i: Phi = I on its free dofs, Phi_S = I on its Schwarz dofs,
+    K = -M^-1 K_ff, B = -M^-1 K_fS, H = 0, c = 0 (exact projection of the FOM)."""
+    probe = oracle.Problem(p)
+    free = probe.free_dofs(i)
+    sdof = probe.schwarz_dofs(i)
+    sd = p.subdomains[i]
+    m = oracle.lumped_mass(sd.dims, sd.h, sd.origin, sd.rho)
+    n3 = 3 * sd.n_nodes
+
+    def col(d):
+        e = np.zeros(n3)
+        e[d] = 1.0
+        f = oracle.internal_force(sd.dims, sd.h, sd.origin, "le", sd.lam, sd.mu, e)
+        return -f[free] / m[free // 3]
+
+    K = np.stack([col(d) for d in free], axis=1)
+    B = np.stack([col(d) for d in sdof], axis=1)
+    r = len(free)
+    ops = {"Phi": np.eye(r), "Phi_S": np.eye(len(sdof)), "K": K, "H": np.zeros((r, r * (r + 1) // 2)), "B": B,
+           "c": np.zeros(r)}
+    return ops, free
+
+
+def test_full_basis_rom_reproduces_fom_fom(oracle):
+    """FOM-ROM coupling with the exact full-basis linear ROM equals FOM-FOM to rounding: checks the
+    ROM step, the boundary projection ghat = Phi_S^T s and the reconstruction Pi Phi q."""
+    pf = W.bar_chain("ff", 2, [4, 4], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+    pr = W.bar_chain("fr", 2, [4, 4], ["fom", "rom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+    ops, free = _exact_linear_rom(oracle, pf, 1)
+    A = oracle.Problem(pf)
+    B = oracle.Problem(pr, rom_ops={1: ops})
+    for _ in range(4):
+        ra, rb = A.step(), B.step()
+        assert rb["status"] == oracle.OK
+    ua, va, _ = A.state(0)
+    ub, vb, _ = B.state(0)
+    assert np.abs(ua - ub).max() < 1e-12 * np.abs(ua).max()
+    u1, _, _ = A.state(1)
+    q, qd, _ = B.rom_state(1)
+    assert np.abs(q - u1.reshape(-1)[free]).max() < 1e-12 * np.abs(u1).max()
+    uB, _, _ = B.state(1)
+    assert np.abs(uB - u1).max() < 1e-12 * np.abs(u1).max()
