@@ -1,0 +1,267 @@
+/*
+ * osam.h -- C ABI of libosam, the GB300 (sm_103a) implementation of one controller step of the
+ * overlapping Schwarz alternating method (O-SAM) coupling hex8 full order models (FOMs) and
+ * quadratic operator-inference (OpInf) reduced order models (ROMs) for 3D solid dynamics
+ * (arXiv 2511.20687).
+ *
+ * Conventions used by every entry point
+ *   - Subdomains are structured boxes of nx*ny*nz cubic hex8 elements of edge h with origin at the
+ *     minimum corner.  Node (i,j,k) has index i + (nx+1)*(j + (ny+1)*k); element (i,j,k) has index
+ *     i + nx*(j + ny*k).
+ *   - Nodal fields passed across the ABI are interleaved [node][3] float64 arrays.
+ *   - Per-node Dirichlet masks (uint8) have bit c set when displacement component c is clamped to 0.
+ *   - Every pointer argument may be host memory (pageable or pinned) or device memory of the
+ *     context's GPU unless stated otherwise; the library copies what it needs.  The caller owns every
+ *     pointer it passes; the library never frees caller memory, never prints and never exits.
+ *   - Return values are osam_status codes; negative values are errors, with a message available
+ *     from osam_last_error().  OSAM_MAXITER is not an error: the controller step was committed after
+ *     max_iters Schwarz iterations, as the paper continues after hitting its iteration cap (Sec. 5.4).
+ *   - Calls are stream ordered on the context's stream and return after the work they describe has
+ *     completed unless stated otherwise.
+ *   - There is no CPU fallback: every step runs in the library's CUDA kernels and an error is
+ *     returned when no usable sm_103a device is present.
+ */
+#ifndef OSAM_H
+#define OSAM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OSAM_API __attribute__((visibility("default")))
+#else
+#define OSAM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OSAM_OK = 0,
+    OSAM_MAXITER = 1,      /* non-fatal: controller step committed at the iteration cap */
+    OSAM_EINVAL = -1,      /* invalid argument or inconsistent description */
+    OSAM_ECFL = -2,        /* explicit time step above the stability limit */
+    OSAM_ENONFINITE = -3,  /* NaN or Inf in the coupled state (cf. the non-finite ROM penalty, Alg. 3) */
+    OSAM_EDONOR = -4,      /* a Schwarz node has no donor element in its source subdomain */
+    OSAM_ECUDA = -5,       /* CUDA runtime error, or no usable device */
+    OSAM_ETIMEOUT = -6,    /* a bounded device-side wait gave up */
+    OSAM_ENOMEM = -7       /* device allocation failed */
+} osam_status;
+
+enum { OSAM_FOM = 0, OSAM_ROM = 1 };
+enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1 };
+enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1 };
+/* element-to-node scatter of the internal force: FP64 atomics, or a deterministic two-pass
+ * element-buffer / node-gather scheme; AUTO times both on the first step and keeps the faster */
+enum { OSAM_SCATTER_AUTO = 0, OSAM_SCATTER_ATOMIC = 1, OSAM_SCATTER_GATHER = 2 };
+
+typedef struct osam_ctx osam_ctx;
+
+/* One subdomain (Sec. 4, Eq. dynamic_elasticity_sam_bcs).
+ * FOM: hex8 isoparametric FE (Sec. 2, Eq. matrix_vector_form) with 2x2x2 Gauss quadrature,
+ *   row-sum lumped mass, explicit Newmark beta=0 gamma=1/2 (Sec. 5 setup), material of Appendix A.1
+ *   (linear elastic) or A.3 (Neo-Hookean, deviatoric coefficient 1/3 from its energy).
+ * ROM: quadratic OpInf model of Eq. opinf_model_schwarz in solved form
+ *   qdd = K q + H kron_c(q) + B ghat + c,  ghat = Phi_S^T s  (Sec. 4.2.1, boundary POD),
+ *   kron_c(q) = (q_i q_j)_{i<=j} in row-major upper-triangle order; the ROM's free dofs are all dofs
+ *   of its mesh that are neither clamped nor on a Schwarz node (increasing dof id 3*node+c), its
+ *   Schwarz dofs are the 3 components of every Schwarz node (increasing node order). */
+typedef struct {
+    int kind;                 /* OSAM_FOM or OSAM_ROM */
+    int nx, ny, nz;           /* elements per direction (>= 1) */
+    double h;                 /* element edge (> 0) */
+    double origin[3];
+    /* FOM material */
+    int material;             /* OSAM_LINEAR_ELASTIC or OSAM_NEO_HOOKEAN */
+    double lambda, mu, rho;   /* Lame parameters and density (kappa = lambda + 2/3 mu for NH) */
+    const double* lambda_e;   /* optional per-element Lame parameters [nx*ny*nz], NULL = uniform */
+    const double* mu_e;
+    const uint8_t* dirichlet; /* per-node clamp mask [nodes] or NULL */
+    const double* u0;         /* initial displacement [nodes][3] (required) */
+    const double* v0;         /* initial velocity [nodes][3] or NULL (zero) */
+    /* ROM operators (kind == OSAM_ROM), all row-major float64 */
+    int r, r_s;               /* reduced dimension and boundary reduced dimension */
+    const double* Phi;        /* [n_free][r] orthonormal POD basis */
+    const double* Phi_S;      /* [3*n_schwarz_nodes][r_s] boundary POD basis */
+    const double* K;          /* [r][r] */
+    const double* H;          /* [r][r(r+1)/2] */
+    const double* B;          /* [r][r_s] */
+    const double* c;          /* [r] */
+} osam_subdomain_desc;
+
+/* Dirichlet transfer from subdomain src to the Schwarz boundary nodes of dst (Sec. 4.1): the data
+ * on node n of dst is the trilinear interpolant (pointwise projector Pi) of src's solution at the
+ * position of n, in the lowest-index src element containing it (local coordinates within 1e-9 of
+ * +-1 are snapped to +-1).  nodes: uint8 [dst nodes], nonzero = Schwarz node fed by src. */
+typedef struct {
+    int dst, src;
+    const uint8_t* nodes;
+} osam_coupling_desc;
+
+typedef struct {
+    int n_subdomains;
+    const osam_subdomain_desc* subdomains;
+    int n_couplings;
+    const osam_coupling_desc* couplings;
+    double dt;                /* time step, equal on every subdomain (temporal interpolant = identity) */
+    int n_substeps;           /* substeps per controller step I_k */
+    double tol_abs, tol_rel;  /* delta_abs, delta_rel of Eq. conv_criterion (0 disables a test) */
+    int max_iters;            /* Schwarz iteration cap per controller step */
+    int precision;            /* OSAM_FP64 or OSAM_FP32_FORCE (internal force in FP32) */
+    int scatter;              /* OSAM_SCATTER_* */
+    void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream */
+    int device;               /* CUDA device ordinal */
+} osam_problem_desc;
+
+typedef struct {
+    int status;               /* OSAM_OK or OSAM_MAXITER (errors are returned, not reported here) */
+    int iterations;           /* Schwarz iterations performed */
+    double cnum, cden;        /* numerator / denominator sums of Eq. conv_criterion at the last iteration */
+    long long element_updates;/* FOM elements x substeps executed in this step */
+    double elapsed_ms;        /* device time of the step (CUDA events on the context stream) */
+} osam_step_report;
+
+/* Build the coupled problem on the device: meshes, lumped masses, node sets, donor elements and
+ * trilinear weights of every Schwarz node (Pi, Sec. 4.1), ROM operators, initial accelerations.
+ * Initial boundary data come from the sources' initial states.  Allocates all device memory the
+ * context will use.  *out receives the context (NULL on error; the error text is then available from
+ * osam_last_error(NULL) on the calling thread). */
+OSAM_API int schwarz_init(const osam_problem_desc* desc, osam_ctx** out);
+
+/* Advance subdomain `sub` over the current controller interval (n_substeps steps) from its current
+ * state, with Dirichlet data from its input boundary history (Eq. schwarz_discrete / Eq.
+ * schwarz_opinf_discrete), and record its trace at every Schwarz node it feeds. */
+OSAM_API int subdomain_advance(osam_ctx* ctx, int sub);
+
+/* Publish src's recorded trace of the current interval into dst's input boundary history:
+ * FOM->FOM copy; FOM->ROM the ROM's boundary snapshot rows; ROM->any Pi Phi q at every substep. */
+OSAM_API int transfer_overlap(osam_ctx* ctx, int src, int dst);
+
+/* Start a controller interval: save every state at t_{k-1} and fill every input boundary history with
+ * the zero-order hold of its source's state at t_{k-1} (initial guess of iteration 1). */
+OSAM_API int osam_begin_interval(osam_ctx* ctx);
+
+/* Return every subdomain to the state saved by osam_begin_interval (start of a new iteration). */
+OSAM_API int osam_restore_interval(osam_ctx* ctx);
+
+/* Sums of Eq. conv_criterion between the current end states and those of the previous call:
+ * cnum = sum_i ||du_i + dt dv_i||^2, cden = sum_i ||u_i + dt v_i||^2 over free dofs (ROM: over q, qd,
+ * equal to the full-space norms for an orthonormal Phi).  Remembers the current states. */
+OSAM_API int osam_criterion(osam_ctx* ctx, double* cnum, double* cden);
+
+/* One controller step (Algorithm 1): begin interval; for n = 1..max_iters: restore (n > 1),
+ * advance every subdomain in index order publishing its traces, criterion; converged when n >= 2 and
+ * cnum < tol_abs^2 or cnum < tol_rel^2 cden.  rep may be NULL. */
+OSAM_API int schwarz_step(osam_ctx* ctx, osam_step_report* rep);
+
+/* Copy a subdomain's nodal state out / in ([nodes][3] each, any pointer may be NULL).  For a ROM the
+ * output is the reconstructed field: Phi q on free dofs, boundary data on Schwarz dofs, 0 on clamped
+ * dofs; osam_set_state on a ROM projects u, v onto the basis (q = Phi^T u) and recomputes qdd. */
+OSAM_API int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a);
+OSAM_API int osam_set_state(osam_ctx* ctx, int sub, const double* u, const double* v, const double* a);
+/* Reduced state of a ROM subdomain ([r] each). */
+OSAM_API int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* qd, double* qdd);
+OSAM_API int osam_set_reduced_state(osam_ctx* ctx, int sub, const double* q, const double* qd, const double* qdd);
+/* Sizes of subdomain `sub` (any output may be NULL). */
+OSAM_API int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, int* n_free, int* n_schwarz_nodes);
+/* The scatter mode in use (OSAM_SCATTER_ATOMIC / GATHER) after any autotuning. */
+OSAM_API int osam_scatter_mode(osam_ctx* ctx);
+OSAM_API void osam_destroy(osam_ctx* ctx);
+/* Message of the last error on ctx, or of the calling thread's last failed schwarz_init if ctx is NULL. */
+OSAM_API const char* osam_last_error(const osam_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------------------
+ * Element-level operators on device arrays (device pointers only, [nodes][3] layout, stream ordered,
+ * asynchronous).  Internal force f = sum_e sum_gp w detJ P(F) grad N (Sec. 2, Eq. weak_form with
+ * the materials of Appendix A) and its vector-Jacobian product
+ *   ubar = (df/du)^T ybar,  lambda_bar[e] = ybar . df/dlambda_e,  mu_bar[e] = ybar . df/dmu_e.
+ * lambda_e / mu_e: per-element device arrays or NULL for the uniform lambda / mu.
+ * ------------------------------------------------------------------------------------------------ */
+OSAM_API int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambda, double mu,
+                    const double* lambda_e, const double* mu_e, const double* u, double* f, void* stream);
+OSAM_API int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double lambda, double mu,
+                        const double* lambda_e, const double* mu_e, const double* u, const double* ybar,
+                        double* ubar, double* lambda_bar, double* mu_bar, void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Offline OpInf (Sec. 3 and Sec. 4.2.1, Eq. opinf_schwarz_inference) on the GPU:
+ *   POD of the free-dof displacement snapshots U (thin SVD by the method of snapshots, Eq.
+ *   pod_cutoff), boundary POD of the Schwarz snapshots S with the smallest r_s whose energy
+ *   E_r (Eq. pod_energy) reaches energy_s (capped at r_s_max; r_s > 0 in the input fixes it),
+ *   projection Ubar = Phi^T U, Abar = Phi^T A, Ghat = Phi_S^T S, and the Tikhonov regression
+ *   min ||D O - Abar^T||^2 + lambda ||O||^2, D = [Ubar^T, kron_c(Ubar)^T, Ghat^T, 1]
+ *   (one scalar lambda for every block; the dual form D^T (D D^T + lambda I)^-1 Abar^T is used when
+ *   D has more columns than rows).  Snapshot matrices are [n_snap][n_dof] (one snapshot per row).
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct {
+    int n_dof, n_snap, n_sdof;
+    const double* U;          /* [n_snap][n_dof] displacement snapshots (free dofs) */
+    const double* A;          /* [n_snap][n_dof] acceleration snapshots */
+    const double* S;          /* [n_snap][n_sdof] Schwarz boundary displacement snapshots */
+    int r;                    /* POD rank of U */
+    int r_s;                  /* boundary rank, or 0 to select it by energy */
+    double energy_s;          /* energy threshold for r_s (e.g. 1 - 1e-6) */
+    int r_s_max;
+    double lambda;
+    int quadratic;            /* 1: quadratic OpInf, 0: linear (H = 0) */
+    void* stream;
+    int device;
+} osam_fit_input;
+
+typedef struct {
+    double* Phi;              /* [n_dof][r] */
+    double* Phi_S;            /* [n_sdof][r_s_max]; the first r_s columns are meaningful */
+    double* K;                /* [r][r] */
+    double* H;                /* [r][r(r+1)/2] */
+    double* B;                /* [r][r_s_max]; the first r_s columns are meaningful */
+    double* c;                /* [r] */
+    double* sigma;            /* [n_snap] singular values of U, or NULL */
+    double* sigma_s;          /* [n_snap] singular values of S, or NULL */
+    int r_s;                  /* selected boundary rank */
+} osam_fit_output;
+
+OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out);
+/* Message of the calling thread's last failed opinf_fit. */
+OSAM_API const char* osam_fit_last_error(void);
+
+/* ------------------------------------------------------------------------------------------------
+ * Adjoint of the explicit single-domain rollout (gradients through the central-difference scheme
+ * of Sec. 5 with the hex8 force and its VJP): J = w . u_T after n_steps steps from (u0, v0),
+ * gradients w.r.t. u0, v0 and the per-element Lame parameters.  The forward pass stores (u, v, a)
+ * every checkpoint_every steps; the reverse sweep recomputes each segment.  Outputs are host or
+ * device pointers ([nodes][3] or [elements]); any may be NULL.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz;
+    double h;
+    int material;
+    const double* lambda_e;   /* [elements] (required) */
+    const double* mu_e;       /* [elements] (required) */
+    double rho;
+    const uint8_t* dirichlet; /* per-node clamp mask or NULL */
+    const double* u0;         /* [nodes][3] */
+    const double* v0;         /* [nodes][3] or NULL */
+    double dt;
+    int n_steps;
+    int checkpoint_every;
+    const double* w;          /* [nodes][3] weights of J */
+    void* stream;
+    int device;
+} osam_adjoint_desc;
+
+typedef struct {
+    double J;
+    double* grad_u0;          /* [nodes][3] */
+    double* grad_v0;          /* [nodes][3] */
+    double* grad_lambda;      /* [elements] */
+    double* grad_mu;          /* [elements] */
+    double elapsed_ms;        /* device time of forward + reverse */
+} osam_adjoint_out;
+
+OSAM_API int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSAM_H */

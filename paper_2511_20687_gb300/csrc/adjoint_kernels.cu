@@ -1,0 +1,311 @@
+// Vector-Jacobian product of the hex8 internal force and the elementwise parts of the reverse
+// sweep through the explicit central-difference rollout.
+//
+// For a hyperelastic law the tangent dP/dF has major symmetry, so the VJP of f with cotangent ybar
+// at element level is the force-like contraction of the directional derivative dP[Gbar] with
+// Gbar = grad(ybar):  ubar_b = sum_gp w detJ dP[Gbar] grad N_b.  Parameter cotangents are
+// lambda_bar_e = sum_gp w detJ P_lambda : Gbar and mu_bar_e = sum_gp w detJ P_mu : Gbar.
+// Neo-Hookean (cofactor form P = beta cof(F) + alpha F, alpha = mu J^-2/3,
+// beta = [kappa/2 (J^2-1) - mu/3 J^-2/3 tr C] / J):
+//   dJ = cof(F) : G,  d trC = 2 F : G,  d alpha = -2/3 alpha dJ / J,
+//   d beta = [kappa J dJ - 1/3 (d alpha trC + alpha d trC)] / J - beta dJ / J,
+//   dP = d beta cof + beta dcof[G] + d alpha F + alpha G,  dcof linear in G (cof is quadratic in F).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "osam_internal.h"
+
+namespace osam {
+
+namespace {
+
+constexpr double kG0 = 0.21132486540518711775;
+constexpr double kG1 = 0.78867513459481288225;
+constexpr double kGd = 0.57735026918962576451;
+
+__device__ __forceinline__ void lerp2(const double D[2][2], double out[2][2]) {
+    double E[2][2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        double d = D[1][e] - D[0][e];
+        E[0][e] = fma(kG0, d, D[0][e]);
+        E[1][e] = fma(kG1, d, D[0][e]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        double d = E[q][1] - E[q][0];
+        out[q][0] = fma(kG0, d, E[q][0]);
+        out[q][1] = fma(kG1, d, E[q][0]);
+    }
+}
+
+__device__ __forceinline__ void lerp2T(const double S[2][2], double out[2][2]) {
+    double V[2][2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        double s = S[q][0] + S[q][1];
+        V[q][0] = fma(kGd, S[q][0], kG0 * s);
+        V[q][1] = s - V[q][0];
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        double s = V[0][e] + V[1][e];
+        out[0][e] = fma(kGd, V[0][e], kG0 * s);
+        out[1][e] = s - out[0][e];
+    }
+}
+
+// scaled edge differences of a nodal field (see the forward kernel)
+__device__ __forceinline__ void edge_diffs(const double* x, int sn, long long sc, const int node[8], double invh,
+                                           double Dx[3][2][2], double Dy[3][2][2], double Dz[3][2][2]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double U[8];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) U[c8] = x[(long long)c * sc + (long long)node[c8] * sn] * invh;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                Dx[c][p][q] = U[1 + 2 * p + 4 * q] - U[2 * p + 4 * q];
+                Dy[c][p][q] = U[p + 2 + 4 * q] - U[p + 4 * q];
+                Dz[c][p][q] = U[p + 2 * q + 4] - U[p + 2 * q];
+            }
+    }
+}
+
+// dP = tangent(H)[G] with pre-scaled (kap2, mu, mu3); pk, pm = P_kappa : G, P_mu : G (unscaled params)
+__device__ __forceinline__ void nh_tangent(const double H[3][3], const double G[3][3], double kap2, double mu,
+                                           double mu3, double dP[3][3], double& pk, double& pm) {
+    double F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? 1.0 : 0.0);
+    double cf[3][3], dc[3][3];
+    cf[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+    cf[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+    cf[0][2] = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+    cf[1][0] = F[0][2] * F[2][1] - F[0][1] * F[2][2];
+    cf[1][1] = F[0][0] * F[2][2] - F[0][2] * F[2][0];
+    cf[1][2] = F[0][1] * F[2][0] - F[0][0] * F[2][1];
+    cf[2][0] = F[0][1] * F[1][2] - F[0][2] * F[1][1];
+    cf[2][1] = F[0][2] * F[1][0] - F[0][0] * F[1][2];
+    cf[2][2] = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    dc[0][0] = G[1][1] * F[2][2] + F[1][1] * G[2][2] - G[1][2] * F[2][1] - F[1][2] * G[2][1];
+    dc[0][1] = G[1][2] * F[2][0] + F[1][2] * G[2][0] - G[1][0] * F[2][2] - F[1][0] * G[2][2];
+    dc[0][2] = G[1][0] * F[2][1] + F[1][0] * G[2][1] - G[1][1] * F[2][0] - F[1][1] * G[2][0];
+    dc[1][0] = G[0][2] * F[2][1] + F[0][2] * G[2][1] - G[0][1] * F[2][2] - F[0][1] * G[2][2];
+    dc[1][1] = G[0][0] * F[2][2] + F[0][0] * G[2][2] - G[0][2] * F[2][0] - F[0][2] * G[2][0];
+    dc[1][2] = G[0][1] * F[2][0] + F[0][1] * G[2][0] - G[0][0] * F[2][1] - F[0][0] * G[2][1];
+    dc[2][0] = G[0][1] * F[1][2] + F[0][1] * G[1][2] - G[0][2] * F[1][1] - F[0][2] * G[1][1];
+    dc[2][1] = G[0][2] * F[1][0] + F[0][2] * G[1][0] - G[0][0] * F[1][2] - F[0][0] * G[1][2];
+    dc[2][2] = G[0][0] * F[1][1] + F[0][0] * G[1][1] - G[0][1] * F[1][0] - F[0][1] * G[1][0];
+    const double J = F[0][0] * cf[0][0] + F[0][1] * cf[0][1] + F[0][2] * cf[0][2];
+    double trC = 0.0, dJ = 0.0, FG = 0.0, cG = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            trC += F[i][j] * F[i][j];
+            dJ += cf[i][j] * G[i][j];
+            FG += F[i][j] * G[i][j];
+        }
+    cG = dJ;
+    const double dtrC = 2.0 * FG;
+    const double J2 = J * J;
+    const double r3 = rcbrt(J2);
+    const double invJ = J * (r3 * r3 * r3);
+    const double alpha = mu * r3;
+    const double beta = (kap2 * (J2 - 1.0) - mu3 * r3 * trC) * invJ;
+    const double dalpha = -(2.0 / 3.0) * alpha * dJ * invJ;
+    const double dA = 2.0 * kap2 * J * dJ;
+    const double dB = (dalpha * trC + alpha * dtrC) / 3.0;
+    const double dbeta = (dA - dB) * invJ - beta * dJ * invJ;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dP[i][j] = dbeta * cf[i][j] + beta * dc[i][j] + dalpha * F[i][j] + alpha * G[i][j];
+    // P_kappa = 1/2 (J^2 - 1)/J cof ; P_mu = J^-2/3 F - 1/3 J^-2/3 trC / J cof
+    pk = 0.5 * (J2 - 1.0) * invJ * cG;
+    pm = r3 * FG - (r3 * trC * invJ / 3.0) * cG;
+}
+
+template <int MAT>
+__global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double* ybar, int ysn, long long ysc,
+                                                  double* lam_bar, double* mu_bar, int accumulate) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.ne) return;
+    const int i = e % a.nx;
+    const int t = e / a.nx;
+    const int j = t % a.ny;
+    const int k = t / a.ny;
+    const int sy = a.nx + 1, sz = (a.nx + 1) * (a.ny + 1);
+    const int n0 = i + sy * j + sz * k;
+    int node[8];
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
+    const double lam = a.lam_e ? a.lam_e[e] : a.lam;
+    const double mu = a.mu_e ? a.mu_e[e] : a.mu;
+    double Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
+    double Ex[3][2][2], Ey[3][2][2], Ez[3][2][2];
+    edge_diffs(a.u, a.usn, a.usc, node, a.invh, Dx, Dy, Dz);
+    edge_diffs(ybar, ysn, ysc, node, a.invh, Ex, Ey, Ez);
+    double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2], Bx[3][2][2], By[3][2][2], Bz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lerp2(Dx[c], Gx[c]); lerp2(Dy[c], Gy[c]); lerp2(Dz[c], Gz[c]);
+        lerp2(Ex[c], Bx[c]); lerp2(Ey[c], By[c]); lerp2(Ez[c], Bz[c]);
+    }
+    double m1, m2, m3;
+    if (MAT == OSAM_NEO_HOOKEAN) {
+        const double kappa = lam + (2.0 / 3.0) * mu;
+        m1 = 0.5 * kappa * a.w8; m2 = mu * a.w8; m3 = mu * a.w8 / 3.0;
+    } else {
+        m1 = lam * a.w8; m2 = mu * a.w8; m3 = 0.0;
+    }
+    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+    double lb = 0.0, mb = 0.0;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                double Hm[3][3], Gm[3][3], dP[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Hm[c][0] = Gx[c][q][r]; Hm[c][1] = Gy[c][p][r]; Hm[c][2] = Gz[c][p][q];
+                    Gm[c][0] = Bx[c][q][r]; Gm[c][1] = By[c][p][r]; Gm[c][2] = Bz[c][p][q];
+                }
+                if (MAT == OSAM_NEO_HOOKEAN) {
+                    double pk, pm;
+                    nh_tangent(Hm, Gm, m1, m2, m3, dP, pk, pm);
+                    lb += pk;
+                    mb += pm + (2.0 / 3.0) * pk;
+                } else {
+                    const double trG = Gm[0][0] + Gm[1][1] + Gm[2][2];
+                    const double trH = Hm[0][0] + Hm[1][1] + Hm[2][2];
+                    double symHG = 0.0;
+#pragma unroll
+                    for (int x = 0; x < 3; ++x)
+#pragma unroll
+                        for (int y = 0; y < 3; ++y) {
+                            dP[x][y] = m2 * (Gm[x][y] + Gm[y][x]) + (x == y ? m1 * trG : 0.0);
+                            symHG += (Hm[x][y] + Hm[y][x]) * Gm[x][y];
+                        }
+                    lb += trH * trG;
+                    mb += symHG;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (p == 0) Sx[c][q][r] = dP[c][0]; else Sx[c][q][r] += dP[c][0];
+                    if (q == 0) Sy[c][p][r] = dP[c][1]; else Sy[c][p][r] += dP[c][1];
+                    if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
+                }
+            }
+    double* ub = static_cast<double*>(a.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double Fc[8];
+        double Tm[2][2];
+        lerp2T(Sx[c], Tm);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
+        lerp2T(Sy[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
+        lerp2T(Sz[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) atomicAdd(ub + (long long)c * a.fsc + (long long)node[c8] * a.fsn, Fc[c8]);
+    }
+    // w detJ = h^3/8 per Gauss point; Gbar above is the physical gradient
+    const double vol8 = a.w8 / a.invh;
+    if (lam_bar) lam_bar[e] = (accumulate ? lam_bar[e] : 0.0) + vol8 * lb;
+    if (mu_bar) mu_bar[e] = (accumulate ? mu_bar[e] : 0.0) + vol8 * mb;
+}
+
+}  // namespace
+
+cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
+                            double* lam_bar, double* mu_bar, int acc, cudaStream_t s) {
+    if (a.ne <= 0) return cudaSuccess;
+    const int g = grid_for(a.ne, 128);
+    if (material == OSAM_NEO_HOOKEAN) k_hex8_vjp<OSAM_NEO_HOOKEAN><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+    else k_hex8_vjp<OSAM_LINEAR_ELASTIC><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace osam
+
+namespace osam {
+namespace {
+
+// reverse of the corrector v' = v + dt/2 (a + a'), a' = -M^-1 f(u'):  abar' += dt/2 vbar;
+// y = -M^-1 abar' (free dofs), cleared VJP accumulator
+__global__ void k_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb,
+                              double* ab, double* y, double* tmp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nn) return;
+    const int c = t / nn, n = t % nn;
+    tmp[t] = 0.0;
+    if (clamp[n] & (1 << c)) { y[t] = 0.0; ab[t] = 0.0; return; }
+    const double a = fma(0.5 * dt, vb[t], ab[t]);
+    ab[t] = a;
+    y[t] = -a * minv[n];
+}
+
+// ubar' += VJP; then the adjoints at the previous step:
+//   abar = dt/2 vbar' + dt^2/2 ubar',  vbar = vbar' + dt ubar',  ubar = ubar'
+__global__ void k_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
+                               double* ab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nn) return;
+    const int c = t / nn, n = t % nn;
+    if (clamp[n] & (1 << c)) { ub[t] = 0.0; vb[t] = 0.0; ab[t] = 0.0; return; }
+    const double u = ub[t] + tmp[t];
+    const double v = vb[t];
+    ub[t] = u;
+    ab[t] = fma(0.5 * dt * dt, u, 0.5 * dt * v);
+    vb[t] = fma(dt, u, v);
+}
+
+__global__ void k_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nn) return;
+    const int c = t / nn, n = t % nn;
+    if (clamp[n] & (1 << c)) {
+        u[t] = 0.0;
+        if (v) v[t] = 0.0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb, double* ab,
+                               double* y, double* tmp, cudaStream_t s) {
+    k_adjoint_pre<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, minv, vb, ab, y, tmp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
+                                double* ab, cudaStream_t s) {
+    k_adjoint_post<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, tmp, ub, vb, ab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, cudaStream_t s) {
+    k_zero_clamped<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, clamp, u, v);
+    return cudaGetLastError();
+}
+
+}  // namespace osam

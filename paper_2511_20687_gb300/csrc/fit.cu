@@ -1,0 +1,329 @@
+// opinf_fit: the offline OpInf stage of Sec. 3 and Sec. 4.2.1 (Eq. opinf_schwarz_inference).
+//   POD by the method of snapshots: G = U U^T (n_snap x n_snap Gram, device GEMM over the long dof
+//   dimension), G = V diag(sigma^2) V^T (symmetric eigensolver on the host), Phi = U^T V_r Sigma_r^-1,
+//   then one Cholesky re-orthonormalisation Phi <- Phi L^-T with L L^T = Phi^T Phi (same span).
+//   Boundary basis Phi_S likewise from the Schwarz snapshots, r_s chosen by the energy criterion
+//   (Eq. pod_energy: smallest r with E_r >= energy_s).
+//   Regression: D = [Ubar^T, kron_c(Ubar)^T, Ghat^T, 1], Y = Abar^T, Tikhonov with one lambda,
+//   dual form O = D^T (D D^T + lambda I)^-1 Y when D has more columns than rows, else the primal
+//   normal equations (D^T D + lambda I) O = D^T Y; the small SPD systems are factored by Cholesky
+//   on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "osam.h"
+#include "osam_internal.h"
+
+using namespace osam;
+
+namespace {
+
+thread_local std::string g_fit_error;
+
+// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major); on return A's diagonal
+// holds the eigenvalues and V (row-major) the eigenvectors as columns
+void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    double fro = 0.0;
+    for (double x : A) fro += x * x;
+    fro = std::sqrt(fro);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (std::sqrt(off) <= 1e-16 * fro) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) <= 1e-300) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// Cholesky L L^T = A (row-major, lower triangle written into A); false if not positive definite
+bool cholesky(std::vector<double>& A, int n) {
+    for (int j = 0; j < n; ++j) {
+        double s = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(s > 0.0)) return false;
+        const double d = std::sqrt(s);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = t / d;
+        }
+    }
+    return true;
+}
+
+// solve L L^T X = B in place (B row-major n x m)
+void chol_solve(const std::vector<double>& L, int n, std::vector<double>& B, int m) {
+    for (int c = 0; c < m; ++c) {
+        for (int i = 0; i < n; ++i) {
+            double t = B[(size_t)i * m + c];
+            for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * B[(size_t)k * m + c];
+            B[(size_t)i * m + c] = t / L[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double t = B[(size_t)i * m + c];
+            for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * B[(size_t)k * m + c];
+            B[(size_t)i * m + c] = t / L[(size_t)i * n + i];
+        }
+    }
+}
+
+struct Dev {
+    std::vector<void*> ptrs;
+    ~Dev() { for (void* p : ptrs) cudaFree(p); }
+    double* alloc(size_t n) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(double)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<double*>(p);
+    }
+};
+
+#define FK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            g_fit_error = std::string(#call) + ": " + cudaGetErrorString(e_);      \
+            return OSAM_ECUDA;                                                     \
+        }                                                                          \
+    } while (0)
+#define FA(p)                                                       \
+    do {                                                            \
+        if (!(p)) { g_fit_error = "device allocation failed"; return OSAM_ENOMEM; } \
+    } while (0)
+
+// POD of snapshots X [n_snap][n] on the device: returns Phi [n][r] (device), sigma (host, all)
+int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, double** Phi_out,
+        std::vector<double>& sigma) {
+    double* G = dev.alloc((size_t)nsnap * nsnap);
+    FA(G);
+    FK(launch_gemm_nt(nsnap, nsnap, n, X, n, X, n, G, nsnap, 1.0, 0.0, s));
+    std::vector<double> Gh((size_t)nsnap * nsnap), V;
+    FK(cudaMemcpyAsync(Gh.data(), G, sizeof(double) * Gh.size(), cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    for (int i = 0; i < nsnap; ++i)  // exact symmetry
+        for (int j = i + 1; j < nsnap; ++j) Gh[(size_t)j * nsnap + i] = Gh[(size_t)i * nsnap + j];
+    jacobi_eig(Gh, nsnap, V);
+    std::vector<int> order(nsnap);
+    for (int i = 0; i < nsnap; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return Gh[(size_t)a * nsnap + a] > Gh[(size_t)b * nsnap + b]; });
+    sigma.resize(nsnap);
+    for (int i = 0; i < nsnap; ++i) sigma[i] = std::sqrt(std::max(0.0, Gh[(size_t)order[i] * nsnap + order[i]]));
+    if (r > nsnap) { g_fit_error = "POD rank exceeds the snapshot count"; return OSAM_EINVAL; }
+    if (r > 0 && !(sigma[r - 1] > 0.0)) { g_fit_error = "snapshot matrix rank is below the requested POD rank"; return OSAM_EINVAL; }
+    // W = V_r Sigma_r^-1 [nsnap][r]
+    std::vector<double> W((size_t)nsnap * r);
+    for (int i = 0; i < nsnap; ++i)
+        for (int k = 0; k < r; ++k) W[(size_t)i * r + k] = V[(size_t)i * nsnap + order[k]] / sigma[k];
+    double* Wd = dev.alloc(W.size());
+    double* Phi = dev.alloc((size_t)n * r);
+    FA(Wd); FA(Phi);
+    FK(cudaMemcpyAsync(Wd, W.data(), sizeof(double) * W.size(), cudaMemcpyHostToDevice, s));
+    FK(launch_gemm_tn(n, r, nsnap, X, n, Wd, r, Phi, r, 1.0, 0.0, s));
+    // re-orthonormalise: M = Phi^T Phi = L L^T, Phi <- Phi L^-T
+    double* M = dev.alloc((size_t)r * r);
+    FA(M);
+    FK(launch_gemm_tn(r, r, n, Phi, r, Phi, r, M, r, 1.0, 0.0, s));
+    std::vector<double> Mh((size_t)r * r);
+    FK(cudaMemcpyAsync(Mh.data(), M, sizeof(double) * Mh.size(), cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    if (!cholesky(Mh, r)) { g_fit_error = "POD basis re-orthonormalisation failed"; return OSAM_EINVAL; }
+    // Linv^T (upper) as a dense r x r matrix: Phi_new = Phi * Linv^T
+    std::vector<double> Li((size_t)r * r, 0.0);
+    for (int c = 0; c < r; ++c) {  // solve L x = e_c
+        for (int i = 0; i < r; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) t -= Mh[(size_t)i * r + k] * Li[(size_t)k * r + c];
+            Li[(size_t)i * r + c] = t / Mh[(size_t)i * r + i];
+        }
+    }
+    std::vector<double> LiT((size_t)r * r);
+    for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) LiT[(size_t)i * r + j] = Li[(size_t)j * r + i];
+    double* T = dev.alloc((size_t)r * r);
+    double* Phi2 = dev.alloc((size_t)n * r);
+    FA(T); FA(Phi2);
+    FK(cudaMemcpyAsync(T, LiT.data(), sizeof(double) * LiT.size(), cudaMemcpyHostToDevice, s));
+    FK(launch_gemm_nn(n, r, r, Phi, r, T, r, Phi2, r, 1.0, 0.0, s));
+    *Phi_out = Phi2;
+    return OSAM_OK;
+}
+
+}  // namespace
+
+extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out) {
+    g_fit_error.clear();
+    if (!in || !out || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
+        in->lambda < 0.0 || (in->n_sdof > 0 && !in->S))
+        return OSAM_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { g_fit_error = "no CUDA device"; return OSAM_ECUDA; }
+    FK(cudaSetDevice(in->device));
+    cudaStream_t s = static_cast<cudaStream_t>(in->stream);
+    Dev dev;
+    const int ns = in->n_snap, n = in->n_dof, nsd = in->n_sdof, r = in->r;
+    double* U = dev.alloc((size_t)ns * n);
+    double* A = dev.alloc((size_t)ns * n);
+    FA(U); FA(A);
+    FK(cudaMemcpyAsync(U, in->U, sizeof(double) * ns * n, cudaMemcpyDefault, s));
+    FK(cudaMemcpyAsync(A, in->A, sizeof(double) * ns * n, cudaMemcpyDefault, s));
+    double* Phi = nullptr;
+    std::vector<double> sigma, sigma_s;
+    if (int rc = pod(s, dev, U, ns, n, r, &Phi, sigma)) return rc;
+    // boundary basis
+    int rs = 0;
+    double* PhiS = nullptr;
+    double* S = nullptr;
+    if (nsd > 0) {
+        S = dev.alloc((size_t)ns * nsd);
+        FA(S);
+        FK(cudaMemcpyAsync(S, in->S, sizeof(double) * ns * nsd, cudaMemcpyDefault, s));
+        std::vector<double> tmp_sigma;
+        double* tmpPhi = nullptr;
+        // energy selection needs the spectrum first: rank-1 pass gives sigma
+        if (int rc = pod(s, dev, S, ns, nsd, 1, &tmpPhi, sigma_s)) return rc;
+        if (in->r_s > 0) rs = in->r_s;
+        else {
+            double tot = 0.0, acc = 0.0;
+            for (double x : sigma_s) tot += x * x;
+            rs = (int)sigma_s.size();
+            for (int k = 0; k < (int)sigma_s.size(); ++k) {
+                acc += sigma_s[k] * sigma_s[k];
+                if (acc >= in->energy_s * tot) { rs = k + 1; break; }
+            }
+        }
+        rs = std::max(1, std::min({rs, in->r_s_max > 0 ? in->r_s_max : rs, ns}));
+        while (rs > 1 && !(sigma_s[rs - 1] > 0.0)) --rs;
+        if (int rc = pod(s, dev, S, ns, nsd, rs, &PhiS, sigma_s)) return rc;
+    }
+    const int nq = in->quadratic ? r * (r + 1) / 2 : 0;
+    const int d = r + nq + rs + 1;
+    // D [ns][d]
+    double* D = dev.alloc((size_t)ns * d);
+    double* Ubt = dev.alloc((size_t)ns * r);   // Ubar^T [ns][r]
+    double* Ub = dev.alloc((size_t)r * ns);    // Ubar [r][ns]
+    double* Y = dev.alloc((size_t)ns * r);     // Abar^T
+    FA(D); FA(Ubt); FA(Ub); FA(Y);
+    FK(launch_gemm_nn(ns, r, n, U, n, Phi, r, Ubt, r, 1.0, 0.0, s));
+    FK(launch_gemm_nn(ns, r, n, A, n, Phi, r, Y, r, 1.0, 0.0, s));
+    std::vector<double> Ubt_h((size_t)ns * r), Ub_h((size_t)r * ns);
+    FK(cudaMemcpyAsync(Ubt_h.data(), Ubt, sizeof(double) * Ubt_h.size(), cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    for (int i = 0; i < ns; ++i)
+        for (int k = 0; k < r; ++k) Ub_h[(size_t)k * ns + i] = Ubt_h[(size_t)i * r + k];
+    FK(cudaMemcpyAsync(Ub, Ub_h.data(), sizeof(double) * Ub_h.size(), cudaMemcpyHostToDevice, s));
+    std::vector<double> Dh((size_t)ns * d, 0.0);
+    // linear block and constant on the host (small); Kronecker block and boundary block on the device
+    FK(cudaMemsetAsync(D, 0, sizeof(double) * ns * d, s));
+    if (nq) FK(launch_kron_features(Ub, r, ns, D, d, r, s));
+    if (rs) FK(launch_gemm_nn(ns, rs, nsd, S, nsd, PhiS, rs, D + r + nq, d, 1.0, 0.0, s));
+    FK(cudaMemcpyAsync(Dh.data(), D, sizeof(double) * Dh.size(), cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    for (int i = 0; i < ns; ++i) {
+        for (int k = 0; k < r; ++k) Dh[(size_t)i * d + k] = Ubt_h[(size_t)i * r + k];
+        Dh[(size_t)i * d + d - 1] = 1.0;
+    }
+    FK(cudaMemcpyAsync(D, Dh.data(), sizeof(double) * Dh.size(), cudaMemcpyHostToDevice, s));
+    std::vector<double> Yh((size_t)ns * r);
+    FK(cudaMemcpyAsync(Yh.data(), Y, sizeof(double) * Yh.size(), cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    std::vector<double> Oh((size_t)d * r);  // O [d][r]
+    if (d > ns) {
+        // dual: (D D^T + lambda I) Z = Y, O = D^T Z
+        double* M = dev.alloc((size_t)ns * ns);
+        FA(M);
+        FK(launch_gemm_nt(ns, ns, d, D, d, D, d, M, ns, 1.0, 0.0, s));
+        std::vector<double> Mh((size_t)ns * ns);
+        FK(cudaMemcpyAsync(Mh.data(), M, sizeof(double) * Mh.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaStreamSynchronize(s));
+        for (int i = 0; i < ns; ++i) {
+            for (int j = i + 1; j < ns; ++j) Mh[(size_t)j * ns + i] = Mh[(size_t)i * ns + j];
+            Mh[(size_t)i * ns + i] += in->lambda;
+        }
+        if (!cholesky(Mh, ns)) { g_fit_error = "regularised dual system is not positive definite"; return OSAM_EINVAL; }
+        chol_solve(Mh, ns, Yh, r);
+        double* Z = dev.alloc((size_t)ns * r);
+        double* Od = dev.alloc((size_t)d * r);
+        FA(Z); FA(Od);
+        FK(cudaMemcpyAsync(Z, Yh.data(), sizeof(double) * Yh.size(), cudaMemcpyHostToDevice, s));
+        FK(launch_gemm_tn(d, r, ns, D, d, Z, r, Od, r, 1.0, 0.0, s));
+        FK(cudaMemcpyAsync(Oh.data(), Od, sizeof(double) * Oh.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaStreamSynchronize(s));
+    } else {
+        double* M = dev.alloc((size_t)d * d);
+        double* R = dev.alloc((size_t)d * r);
+        FA(M); FA(R);
+        FK(launch_gemm_tn(d, d, ns, D, d, D, d, M, d, 1.0, 0.0, s));
+        FK(launch_gemm_tn(d, r, ns, D, d, Y, r, R, r, 1.0, 0.0, s));
+        std::vector<double> Mh((size_t)d * d);
+        FK(cudaMemcpyAsync(Mh.data(), M, sizeof(double) * Mh.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaMemcpyAsync(Oh.data(), R, sizeof(double) * Oh.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaStreamSynchronize(s));
+        for (int i = 0; i < d; ++i) {
+            for (int j = i + 1; j < d; ++j) Mh[(size_t)j * d + i] = Mh[(size_t)i * d + j];
+            Mh[(size_t)i * d + i] += in->lambda;
+        }
+        if (!cholesky(Mh, d)) { g_fit_error = "regularised normal equations are not positive definite"; return OSAM_EINVAL; }
+        chol_solve(Mh, d, Oh, r);
+    }
+    // unpack O [d][r] -> K [r][r], H [r][nq_full], B [r][r_s_max], c [r]
+    const int nq_full = r * (r + 1) / 2;
+    const int rs_cols = std::max(in->r_s_max, rs);
+    std::vector<double> K((size_t)r * r), H((size_t)r * nq_full, 0.0), B((size_t)r * std::max(1, rs_cols), 0.0), c(r);
+    for (int i = 0; i < r; ++i) {
+        for (int k = 0; k < r; ++k) K[(size_t)i * r + k] = Oh[(size_t)k * r + i];
+        for (int k = 0; k < nq; ++k) H[(size_t)i * nq_full + k] = Oh[(size_t)(r + k) * r + i];
+        for (int k = 0; k < rs; ++k) B[(size_t)i * rs_cols + k] = Oh[(size_t)(r + nq + k) * r + i];
+        c[i] = Oh[(size_t)(d - 1) * r + i];
+    }
+    if (out->K) FK(cudaMemcpyAsync(out->K, K.data(), sizeof(double) * K.size(), cudaMemcpyDefault, s));
+    if (out->H) FK(cudaMemcpyAsync(out->H, H.data(), sizeof(double) * H.size(), cudaMemcpyDefault, s));
+    if (out->B && rs_cols > 0) FK(cudaMemcpyAsync(out->B, B.data(), sizeof(double) * (size_t)r * rs_cols, cudaMemcpyDefault, s));
+    if (out->c) FK(cudaMemcpyAsync(out->c, c.data(), sizeof(double) * r, cudaMemcpyDefault, s));
+    if (out->Phi) FK(cudaMemcpyAsync(out->Phi, Phi, sizeof(double) * (size_t)n * r, cudaMemcpyDefault, s));
+    if (out->Phi_S && rs > 0) {
+        // [nsd][rs] -> [nsd][rs_cols]
+        std::vector<double> P((size_t)nsd * rs), Pw((size_t)nsd * rs_cols, 0.0);
+        FK(cudaMemcpyAsync(P.data(), PhiS, sizeof(double) * P.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaStreamSynchronize(s));
+        for (int m = 0; m < nsd; ++m)
+            for (int k = 0; k < rs; ++k) Pw[(size_t)m * rs_cols + k] = P[(size_t)m * rs + k];
+        FK(cudaMemcpyAsync(out->Phi_S, Pw.data(), sizeof(double) * Pw.size(), cudaMemcpyDefault, s));
+    }
+    if (out->sigma) FK(cudaMemcpyAsync(out->sigma, sigma.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
+    if (out->sigma_s && !sigma_s.empty()) FK(cudaMemcpyAsync(out->sigma_s, sigma_s.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
+    FK(cudaStreamSynchronize(s));
+    out->r_s = rs;
+    return OSAM_OK;
+}
+
+extern "C" OSAM_API const char* osam_fit_last_error(void) { return g_fit_error.c_str(); }

@@ -1,0 +1,1004 @@
+// Host runtime of libosam: context construction (schwarz_init), the O-SAM controller (Algorithm 1
+// of the paper, with the criterion of Eq. conv_criterion), state I/O, the element-level operators
+// and the adjoint rollout.  Every numerical step runs in the kernels of fom_kernels.cu,
+// rom_kernels.cu and adjoint_kernels.cu; this file only allocates, sequences and checks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "osam.h"
+#include "osam_internal.h"
+
+using namespace osam;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct Sub {
+    int kind = OSAM_FOM;
+    Grid g;
+    std::vector<uint8_t> clamp_h;
+    std::vector<int> srow_h;
+    int ns = 0;
+    FomDev fom;
+    RomDev rom;
+};
+
+}  // namespace
+
+struct osam_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double dt = 0.0;
+    int nsub = 0;
+    double tol_abs = 0.0, tol_rel = 0.0;
+    int max_it = 1;
+    int precision = OSAM_FP64;
+    int scatter = kGather;
+    std::vector<Sub> subs;
+    std::vector<CplDev> cpls;
+    std::vector<void*> allocs;
+    double* partial = nullptr;
+    int nparts = 0;
+    double* result = nullptr;      // device [3]
+    double* result_h = nullptr;    // pinned host [3]
+    double* scratch = nullptr;     // device [3 * max nodes]
+    int* err_d = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+    long long fom_elements = 0;
+
+    ~osam_ctx() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void* p : allocs) cudaFree(p);
+        if (result_h) cudaFreeHost(result_h);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    template <typename T>
+    T* alloc(size_t n) {
+        if (n == 0) n = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        cudaMemsetAsync(p, 0, n * sizeof(T), stream);
+        return static_cast<T*>(p);
+    }
+
+    int fail(int code, const char* fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+};
+
+#define CK(call)                                                                                          \
+    do {                                                                                                  \
+        cudaError_t e_ = (call);                                                                          \
+        if (e_ != cudaSuccess) return ctx->fail(OSAM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                                __FILE__, __LINE__);                                      \
+    } while (0)
+
+#define CKA(ptr)                                                                                    \
+    do {                                                                                            \
+        if (!(ptr)) return ctx->fail(OSAM_ENOMEM, "device allocation failed (%s:%d)", __FILE__, __LINE__); \
+    } while (0)
+
+namespace {
+
+long long hist_stride_fom(const Sub& s) { return 9LL * s.ns; }
+
+double* fom_slot(osam_ctx* ctx, Sub& s, int slot) { return s.fom.hist + (long long)slot * hist_stride_fom(s); }
+
+ElemArgs elem_args(const FomDev& F, const double* u, int usn, long long usc) {
+    ElemArgs a{};
+    a.nx = F.g.nx; a.ny = F.g.ny; a.nz = F.g.nz; a.ne = F.g.ne();
+    a.invh = 1.0 / F.g.h;
+    a.w8 = F.g.h * F.g.h / 8.0;
+    a.lam = F.lam; a.mu = F.mu;
+    a.lam_e = F.lam_e; a.mu_e = F.mu_e;
+    a.u = u; a.usn = usn; a.usc = usc;
+    a.f = F.f; a.fsn = 1; a.fsc = F.g.nn();
+    a.fe = F.fe;
+    return a;
+}
+
+NodeArgs node_args(osam_ctx* ctx, Sub& s) {
+    FomDev& F = s.fom;
+    NodeArgs a{};
+    a.nx = F.g.nx; a.ny = F.g.ny; a.nz = F.g.nz; a.nn = F.g.nn(); a.ne = F.g.ne();
+    a.dt = ctx->dt;
+    a.minv = F.minv; a.clamp = F.clamp; a.srow = F.srow; a.ns = s.ns;
+    a.v = F.v; a.a = F.a;
+    a.force = F.fe; a.fclear = F.f;
+    return a;
+}
+
+// the FP32-force atomic path accumulates into a float buffer placed after the FP64 one
+void* f32_buffer(const FomDev& F) { return F.fe; }
+
+int advance_fom(osam_ctx* ctx, int i) {
+    Sub& s = ctx->subs[i];
+    FomDev& F = s.fom;
+    const int nn = F.g.nn();
+    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
+    const int scatter = ctx->scatter;
+    // predictor of substep 0: u^1 into buffer 1
+    NodeArgs p = node_args(ctx, s);
+    p.predict_only = 1;
+    p.ucur = F.u[0];
+    p.unext = F.u[1];
+    p.h2 = fom_slot(ctx, s, 1);
+    p.last = 0;
+    CK(launch_node_update(fp32, scatter, p, ctx->stream));
+    for (int j = 0; j < ctx->nsub; ++j) {
+        double* X = F.u[(j + 1) & 1];
+        double* Y = F.u[j & 1];
+        ElemArgs ea = elem_args(F, X, 1, nn);
+        if (fp32 && scatter == kAtomic) ea.f = f32_buffer(F);
+        CK(launch_hex8_force(F.material, fp32, scatter, ea, ctx->stream));
+        NodeArgs na = node_args(ctx, s);
+        if (fp32 && scatter == kAtomic) na.fclear = f32_buffer(F);
+        na.ucur = X;
+        na.unext = Y;
+        na.h1 = fom_slot(ctx, s, j + 1);
+        na.h2 = (j + 2 <= ctx->nsub) ? fom_slot(ctx, s, j + 2) : nullptr;
+        na.last = (j == ctx->nsub - 1);
+        CK(launch_node_update(fp32, scatter, na, ctx->stream));
+        for (CplDev& c : ctx->cpls)
+            if (c.src == i) CK(launch_trace(c, X, F.v, F.a, nn, j + 1, ctx->nsub, ctx->stream));
+    }
+    if (ctx->nsub & 1) CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+    return OSAM_OK;
+}
+
+int advance_rom(osam_ctx* ctx, int i) {
+    RomDev& R = ctx->subs[i].rom;
+    CK(cudaMemcpyAsync(R.qrec, R.q, sizeof(double) * 3 * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(launch_rom_project(R, 1, ctx->nsub, ctx->stream));
+    for (int j = 0; j < ctx->nsub; ++j) CK(launch_rom_step(R, j + 1, ctx->dt, 0, ctx->stream));
+    return OSAM_OK;
+}
+
+int dst_hist(osam_ctx* ctx, const CplDev& c, bool* dst_rom, double** hist, int* nd) {
+    Sub& d = ctx->subs[c.dst];
+    *dst_rom = d.kind == OSAM_ROM;
+    if (*dst_rom) { *hist = d.rom.hist; *nd = d.rom.nsdof; }
+    else { *hist = d.fom.hist; *nd = d.ns; }
+    return OSAM_OK;
+}
+
+int transfer(osam_ctx* ctx, const CplDev& c) {
+    bool dst_rom;
+    double* hist;
+    int nd;
+    dst_hist(ctx, c, &dst_rom, &hist, &nd);
+    Sub& src = ctx->subs[c.src];
+    if (src.kind == OSAM_FOM) CK(launch_publish_fom(c, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    else CK(launch_rom_reconstruct(c, src.rom, false, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    return OSAM_OK;
+}
+
+int zoh(osam_ctx* ctx, const CplDev& c) {
+    bool dst_rom;
+    double* hist;
+    int nd;
+    dst_hist(ctx, c, &dst_rom, &hist, &nd);
+    Sub& src = ctx->subs[c.src];
+    if (src.kind == OSAM_FOM)
+        CK(launch_zoh_from_fom(c, src.fom.u[0], src.fom.v, src.fom.a, src.g.nn(), dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    else CK(launch_rom_reconstruct(c, src.rom, true, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    return OSAM_OK;
+}
+
+int save_all(osam_ctx* ctx, bool restore) {
+    for (Sub& s : ctx->subs) {
+        if (s.kind == OSAM_FOM) {
+            const size_t b = sizeof(double) * 3 * s.g.nn();
+            FomDev& F = s.fom;
+            if (restore) {
+                CK(cudaMemcpyAsync(F.u[0], F.su, b, cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(F.v, F.sv, b, cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(F.a, F.sa, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            } else {
+                CK(cudaMemcpyAsync(F.su, F.u[0], b, cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(F.sv, F.v, b, cudaMemcpyDeviceToDevice, ctx->stream));
+                CK(cudaMemcpyAsync(F.sa, F.a, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            }
+        } else {
+            RomDev& R = s.rom;
+            const size_t b = sizeof(double) * 3 * R.r;
+            if (restore) CK(cudaMemcpyAsync(R.q, R.sq, b, cudaMemcpyDeviceToDevice, ctx->stream));
+            else CK(cudaMemcpyAsync(R.sq, R.q, b, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
+    return OSAM_OK;
+}
+
+int criterion_async(osam_ctx* ctx) {
+    int off = 0;
+    for (Sub& s : ctx->subs) {
+        if (s.kind == OSAM_FOM) {
+            CK(launch_norms_fom(s.fom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
+            off += s.fom.norm_blocks;
+        } else {
+            CK(launch_rom_norms(s.rom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
+            off += 1;
+        }
+    }
+    CK(launch_norms_final(ctx->partial, off, ctx->result, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->result_h, ctx->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return OSAM_OK;
+}
+
+// copy a user array (host or device) into a device buffer
+int upload(osam_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+    return OSAM_OK;
+}
+
+template <typename T>
+int to_host(osam_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
+    out.resize(n);
+    if (n == 0) return OSAM_OK;
+    CK(cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int check_device(osam_ctx* ctx, int device) {
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) return ctx->fail(OSAM_ECUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    if (device < 0 || device >= n) return ctx->fail(OSAM_EINVAL, "device %d out of range (%d devices)", device, n);
+    CK(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    if (prop.major < 10) return ctx->fail(OSAM_ECUDA, "device %d is sm_%d%d; libosam is built for sm_103a", device, prop.major, prop.minor);
+    return OSAM_OK;
+}
+
+int setup_fom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
+    FomDev& F = s.fom;
+    F.g = s.g;
+    F.material = d.material;
+    F.lam = d.lambda; F.mu = d.mu; F.rho = d.rho;
+    const int nn = s.g.nn(), ne = s.g.ne();
+    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
+    if (d.lambda_e) { CKA(F.lam_e = ctx->alloc<double>(ne)); if (int r = upload(ctx, F.lam_e, d.lambda_e, sizeof(double) * ne)) return r; }
+    if (d.mu_e) { CKA(F.mu_e = ctx->alloc<double>(ne)); if (int r = upload(ctx, F.mu_e, d.mu_e, sizeof(double) * ne)) return r; }
+    CKA(F.minv = ctx->alloc<double>(nn));
+    CK(launch_lumped_minv(s.g, d.rho, F.minv, ctx->stream));
+    CKA(F.clamp = ctx->alloc<uint8_t>(nn));
+    if (int r = upload(ctx, F.clamp, s.clamp_h.data(), nn)) return r;
+    CKA(F.srow = ctx->alloc<int>(nn));
+    if (int r = upload(ctx, F.srow, s.srow_h.data(), sizeof(int) * nn)) return r;
+    F.ns = s.ns;
+    for (int b = 0; b < 2; ++b) CKA(F.u[b] = ctx->alloc<double>(3LL * nn));
+    CKA(F.v = ctx->alloc<double>(3LL * nn));
+    CKA(F.a = ctx->alloc<double>(3LL * nn));
+    CKA(F.f = ctx->alloc<double>(3LL * nn));
+    // gather buffer (FP64 or FP32 element contributions); in FP32 atomic mode it holds the float accumulator
+    const size_t fe_bytes = std::max<size_t>(24ULL * ne * (fp32 ? 4 : 8), 3ULL * nn * 4);
+    CKA(F.fe = ctx->alloc<unsigned char>(fe_bytes));
+    CKA(F.su = ctx->alloc<double>(3LL * nn));
+    CKA(F.sv = ctx->alloc<double>(3LL * nn));
+    CKA(F.sa = ctx->alloc<double>(3LL * nn));
+    CKA(F.pu = ctx->alloc<double>(3LL * nn));
+    CKA(F.pv = ctx->alloc<double>(3LL * nn));
+    CKA(F.hist = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 9 * std::max(1, s.ns)));
+    F.norm_blocks = std::min(1024, grid_for(nn, 256));
+    // initial state (interleaved input -> SoA), clamped components zero
+    if (int r = upload(ctx, ctx->scratch, d.u0, sizeof(double) * 3 * nn)) return r;
+    CK(launch_aos_to_soa(ctx->scratch, F.u[0], nn, ctx->stream));
+    if (d.v0) {
+        if (int r = upload(ctx, ctx->scratch, d.v0, sizeof(double) * 3 * nn)) return r;
+        CK(launch_aos_to_soa(ctx->scratch, F.v, nn, ctx->stream));
+    }
+    CK(launch_zero_clamped(nn, F.clamp, F.u[0], F.v, ctx->stream));
+    return OSAM_OK;
+}
+
+int fom_initial_accel(osam_ctx* ctx, Sub& s) {
+    FomDev& F = s.fom;
+    const int nn = s.g.nn();
+    CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
+    ElemArgs ea = elem_args(F, F.u[0], 1, nn);
+    ea.f = F.f;
+    CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
+    CK(launch_accel_from_force(F, static_cast<const double*>(F.f), ctx->stream));
+    CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
+    return OSAM_OK;
+}
+
+int setup_rom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
+    RomDev& R = s.rom;
+    R.g = s.g;
+    const int nn = s.g.nn();
+    R.r = d.r;
+    R.rs = d.r_s;
+    R.ns = s.ns;
+    R.nsdof = 3 * s.ns;
+    R.nq = R.r * (R.r + 1) / 2;
+    R.d = R.r + R.nq + R.rs + 1;
+    if (R.r < 1 || R.r > 256) return ctx->fail(OSAM_EINVAL, "ROM rank r=%d outside [1, 256]", R.r);
+    if (R.rs < 0 || (R.rs > 0 && !d.Phi_S)) return ctx->fail(OSAM_EINVAL, "ROM boundary basis missing");
+    if (!d.Phi || !d.K || !d.H || !d.c || (R.rs > 0 && !d.B)) return ctx->fail(OSAM_EINVAL, "ROM operator missing");
+    // free dofs
+    std::vector<int> free_dof, dof_free(3 * nn, -1);
+    for (int n = 0; n < nn; ++n)
+        for (int c = 0; c < 3; ++c)
+            if (!(s.clamp_h[n] & (1 << c)) && s.srow_h[n] < 0) {
+                dof_free[3 * n + c] = (int)free_dof.size();
+                free_dof.push_back(3 * n + c);
+            }
+    R.nfree = (int)free_dof.size();
+    CKA(R.free_dof = ctx->alloc<int>(R.nfree));
+    CKA(R.dof_free = ctx->alloc<int>(3LL * nn));
+    if (int r = upload(ctx, R.free_dof, free_dof.data(), sizeof(int) * R.nfree)) return r;
+    if (int r = upload(ctx, R.dof_free, dof_free.data(), sizeof(int) * 3 * nn)) return r;
+    CKA(R.clamp = ctx->alloc<uint8_t>(nn));
+    if (int r = upload(ctx, R.clamp, s.clamp_h.data(), nn)) return r;
+    CKA(R.srow = ctx->alloc<int>(nn));
+    if (int r = upload(ctx, R.srow, s.srow_h.data(), sizeof(int) * nn)) return r;
+    CKA(R.Phi = ctx->alloc<double>((size_t)R.nfree * R.r));
+    if (int r = upload(ctx, R.Phi, d.Phi, sizeof(double) * R.nfree * R.r)) return r;
+    // packed operator rows [K | H | B | c]
+    std::vector<double> K, H, B, c, O((size_t)R.r * R.d);
+    if (int r = to_host(ctx, K, d.K, (size_t)R.r * R.r)) return r;
+    if (int r = to_host(ctx, H, d.H, (size_t)R.r * R.nq)) return r;
+    if (R.rs) { if (int r = to_host(ctx, B, d.B, (size_t)R.r * R.rs)) return r; }
+    if (int r = to_host(ctx, c, d.c, (size_t)R.r)) return r;
+    for (int i = 0; i < R.r; ++i) {
+        double* row = O.data() + (size_t)i * R.d;
+        std::copy(K.begin() + (size_t)i * R.r, K.begin() + (size_t)(i + 1) * R.r, row);
+        std::copy(H.begin() + (size_t)i * R.nq, H.begin() + (size_t)(i + 1) * R.nq, row + R.r);
+        if (R.rs) std::copy(B.begin() + (size_t)i * R.rs, B.begin() + (size_t)(i + 1) * R.rs, row + R.r + R.nq);
+        row[R.d - 1] = c[i];
+    }
+    CKA(R.O = ctx->alloc<double>(O.size()));
+    if (int r = upload(ctx, R.O, O.data(), sizeof(double) * O.size())) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // Phi_S^T
+    CKA(R.PhiSt = ctx->alloc<double>((size_t)std::max(1, R.rs) * std::max(1, R.nsdof)));
+    if (R.rs) {
+        std::vector<double> PS, PSt((size_t)R.rs * R.nsdof);
+        if (int r = to_host(ctx, PS, d.Phi_S, (size_t)R.nsdof * R.rs)) return r;
+        for (int m = 0; m < R.nsdof; ++m)
+            for (int k = 0; k < R.rs; ++k) PSt[(size_t)k * R.nsdof + m] = PS[(size_t)m * R.rs + k];
+        if (int r = upload(ctx, R.PhiSt, PSt.data(), sizeof(double) * PSt.size())) return r;
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    std::vector<short2> kij(std::max(1, R.nq));
+    int t = 0;
+    for (int i = 0; i < R.r; ++i)
+        for (int j = i; j < R.r; ++j) kij[t++] = make_short2((short)i, (short)j);
+    CKA(R.kron_ij = ctx->alloc<short2>(kij.size()));
+    if (int r = upload(ctx, R.kron_ij, kij.data(), sizeof(short2) * kij.size())) return r;
+    CKA(R.q = ctx->alloc<double>(3 * R.r));
+    CKA(R.sq = ctx->alloc<double>(3 * R.r));
+    CKA(R.pq = ctx->alloc<double>(3 * R.r));
+    CKA(R.qrec = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 3 * R.r));
+    CKA(R.ghat = ctx->alloc<double>((size_t)(ctx->nsub + 1) * std::max(1, R.rs)));
+    CKA(R.hist = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 3 * std::max(1, R.nsdof)));
+    R.step_gx = grid_for(R.d, 128);
+    R.step_gy = grid_for(R.r, 8);
+    CKA(R.partial = ctx->alloc<double>((size_t)R.step_gx * R.r));
+    CKA(R.counter = ctx->alloc<unsigned int>(1));
+    // q0 = Phi^T u0, qd0 = Phi^T v0 over the free dofs (u0, v0 interleaved, clamped parts ignored)
+    double* uv = ctx->alloc<double>(6LL * nn);
+    CKA(uv);
+    if (int r = upload(ctx, uv, d.u0, sizeof(double) * 3 * nn)) return r;
+    if (d.v0) { if (int r = upload(ctx, uv + 3LL * nn, d.v0, sizeof(double) * 3 * nn)) return r; }
+    CK(launch_rom_basis_project(R, uv, d.v0 ? uv + 3LL * nn : nullptr, ctx->stream));
+    return OSAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* osam_last_error(const osam_ctx* ctx) {
+    if (!ctx) return g_init_error.c_str();
+    return ctx->err.c_str();
+}
+
+int osam_scatter_mode(osam_ctx* ctx) { return ctx ? ctx->scatter : 0; }
+
+void osam_destroy(osam_ctx* ctx) { delete ctx; }
+
+static int init_impl(osam_ctx* ctx, const osam_problem_desc* desc);
+
+int schwarz_init(const osam_problem_desc* desc, osam_ctx** out) {
+    if (out) *out = nullptr;
+    g_init_error.clear();
+    if (!desc || !out) { g_init_error = "null argument"; return OSAM_EINVAL; }
+    auto* ctx = new osam_ctx();
+    int rc = init_impl(ctx, desc);
+    if (rc != OSAM_OK) {
+        g_init_error = ctx->err;
+        delete ctx;
+        return rc;
+    }
+    *out = ctx;
+    return OSAM_OK;
+}
+
+static int autotune_scatter(osam_ctx* ctx);
+
+static int init_impl(osam_ctx* ctx, const osam_problem_desc* desc) {
+    if (int r = check_device(ctx, desc->device)) return r;
+    ctx->device = desc->device;
+    if (desc->stream) ctx->stream = static_cast<cudaStream_t>(desc->stream);
+    else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    if (desc->n_subdomains < 1 || !desc->subdomains) return ctx->fail(OSAM_EINVAL, "no subdomains");
+    if (desc->n_couplings < 0 || (desc->n_couplings > 0 && !desc->couplings)) return ctx->fail(OSAM_EINVAL, "bad couplings");
+    if (!(desc->dt > 0.0) || desc->n_substeps < 1 || desc->max_iters < 1)
+        return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
+    if (desc->precision != OSAM_FP64 && desc->precision != OSAM_FP32_FORCE) return ctx->fail(OSAM_EINVAL, "bad precision");
+    ctx->dt = desc->dt;
+    ctx->nsub = desc->n_substeps;
+    ctx->tol_abs = desc->tol_abs;
+    ctx->tol_rel = desc->tol_rel;
+    ctx->max_it = desc->max_iters;
+    ctx->precision = desc->precision;
+    CK(cudaEventCreate(&ctx->ev0));
+    CK(cudaEventCreate(&ctx->ev1));
+    CK(cudaMallocHost(&ctx->result_h, 3 * sizeof(double)));
+    CKA(ctx->result = ctx->alloc<double>(3));
+    CKA(ctx->err_d = ctx->alloc<int>(1));
+    const int nsd = desc->n_subdomains;
+    ctx->subs.resize(nsd);
+    int max_nn = 0;
+    for (int i = 0; i < nsd; ++i) {
+        const osam_subdomain_desc& d = desc->subdomains[i];
+        Sub& s = ctx->subs[i];
+        if (d.kind != OSAM_FOM && d.kind != OSAM_ROM) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad kind", i);
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.h > 0.0)) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad mesh", i);
+        if ((long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1) > (1LL << 30)) return ctx->fail(OSAM_EINVAL, "subdomain %d too large", i);
+        if (!d.u0) return ctx->fail(OSAM_EINVAL, "subdomain %d: u0 required", i);
+        if (d.kind == OSAM_FOM) {
+            if (d.material != OSAM_LINEAR_ELASTIC && d.material != OSAM_NEO_HOOKEAN) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad material", i);
+            if (!(d.rho > 0.0)) return ctx->fail(OSAM_EINVAL, "subdomain %d: rho must be positive", i);
+        }
+        s.kind = d.kind;
+        s.g.nx = d.nx; s.g.ny = d.ny; s.g.nz = d.nz; s.g.h = d.h;
+        for (int a = 0; a < 3; ++a) s.g.org[a] = d.origin[a];
+        const int nn = s.g.nn();
+        max_nn = std::max(max_nn, nn);
+        s.clamp_h.assign(nn, 0);
+        if (d.dirichlet) {
+            std::vector<uint8_t> tmp;
+            CK(cudaMemcpy(s.clamp_h.data(), d.dirichlet, nn, cudaMemcpyDefault));
+        }
+        for (int n = 0; n < nn; ++n) s.clamp_h[n] &= 7;
+        s.srow_h.assign(nn, -1);
+        if (s.kind == OSAM_FOM) ctx->fom_elements += s.g.ne();
+    }
+    // couplings: masks -> Schwarz rows (union, increasing node order) -> donor search
+    std::vector<std::vector<uint8_t>> masks(desc->n_couplings);
+    for (int k = 0; k < desc->n_couplings; ++k) {
+        const osam_coupling_desc& c = desc->couplings[k];
+        if (c.dst < 0 || c.dst >= nsd || c.src < 0 || c.src >= nsd || c.dst == c.src || !c.nodes)
+            return ctx->fail(OSAM_EINVAL, "coupling %d: bad indices", k);
+        masks[k].resize(ctx->subs[c.dst].g.nn());
+        CK(cudaMemcpy(masks[k].data(), c.nodes, masks[k].size(), cudaMemcpyDefault));
+    }
+    for (int i = 0; i < nsd; ++i) {
+        Sub& s = ctx->subs[i];
+        int ns = 0;
+        for (int n = 0; n < s.g.nn(); ++n) {
+            bool any = false;
+            for (int k = 0; k < desc->n_couplings; ++k)
+                if (desc->couplings[k].dst == i && masks[k][n]) any = true;
+            if (any) s.srow_h[n] = ns++;
+        }
+        s.ns = ns;
+    }
+    CKA(ctx->scratch = ctx->alloc<double>(3LL * max_nn));
+    for (int i = 0; i < nsd; ++i) {
+        Sub& s = ctx->subs[i];
+        const osam_subdomain_desc& d = desc->subdomains[i];
+        int rc = s.kind == OSAM_FOM ? setup_fom(ctx, s, d) : setup_rom(ctx, s, d);
+        if (rc) return rc;
+    }
+    ctx->cpls.resize(desc->n_couplings);
+    for (int k = 0; k < desc->n_couplings; ++k) {
+        const osam_coupling_desc& cd = desc->couplings[k];
+        CplDev& c = ctx->cpls[k];
+        c.dst = cd.dst; c.src = cd.src;
+        Sub& dst = ctx->subs[cd.dst];
+        Sub& src = ctx->subs[cd.src];
+        std::vector<int> nodes, rows;
+        for (int n = 0; n < dst.g.nn(); ++n)
+            if (masks[k][n]) { nodes.push_back(n); rows.push_back(dst.srow_h[n]); }
+        c.nrow = (int)nodes.size();
+        CKA(c.row = ctx->alloc<int>(c.nrow));
+        CKA(c.dnode = ctx->alloc<int>(8LL * c.nrow));
+        CKA(c.dw = ctx->alloc<double>(8LL * c.nrow));
+        int* dn = ctx->alloc<int>(c.nrow);
+        CKA(dn);
+        if (int r = upload(ctx, c.row, rows.data(), sizeof(int) * c.nrow)) return r;
+        if (int r = upload(ctx, dn, nodes.data(), sizeof(int) * c.nrow)) return r;
+        CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
+        CK(launch_donor(src.g, dst.g, nullptr, dn, c.nrow, c.dnode, c.dw, ctx->err_d, ctx->stream));
+        int nerr = 0;
+        CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (nerr) return ctx->fail(OSAM_EDONOR, "coupling %d (%d <- %d): %d Schwarz nodes have no donor element", k, cd.dst, cd.src, nerr);
+        if (src.kind == OSAM_FOM) {
+            CKA(c.rec = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 9 * std::max(1, c.nrow)));
+        } else {
+            CKA(c.Rt = ctx->alloc<double>((size_t)src.rom.r * 3 * std::max(1, c.nrow)));
+            CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
+            CK(launch_build_Rt_checked(c, src.rom, ctx->err_d, ctx->stream));
+            CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (nerr) return ctx->fail(OSAM_EINVAL, "coupling %d: a donor node with nonzero weight is a Schwarz node of ROM %d", k, cd.src);
+        }
+    }
+    // criterion partial sums
+    int nparts = 0;
+    for (Sub& s : ctx->subs) nparts += s.kind == OSAM_FOM ? s.fom.norm_blocks : 1;
+    ctx->nparts = nparts;
+    CKA(ctx->partial = ctx->alloc<double>(2LL * nparts));
+    // initial boundary data: zero-order hold of every source's initial state (before accelerations)
+    for (CplDev& c : ctx->cpls)
+        if (int r = zoh(ctx, c)) return r;
+    for (Sub& s : ctx->subs) {
+        if (s.kind == OSAM_FOM) {
+            if (int r = fom_initial_accel(ctx, s)) return r;
+        } else {
+            CK(launch_rom_project(s.rom, 0, 0, ctx->stream));
+            CK(launch_rom_step(s.rom, 0, ctx->dt, 1, ctx->stream));
+        }
+    }
+    ctx->scatter = desc->scatter == OSAM_SCATTER_ATOMIC ? kAtomic : kGather;
+    if (desc->scatter == OSAM_SCATTER_AUTO && ctx->fom_elements > 0)
+        if (int r = autotune_scatter(ctx)) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+// time the force + node kernels of the largest FOM in both scatter modes on scratch copies
+static int autotune_scatter(osam_ctx* ctx) {
+    int best = -1;
+    long long ne = -1;
+    for (int i = 0; i < (int)ctx->subs.size(); ++i)
+        if (ctx->subs[i].kind == OSAM_FOM && ctx->subs[i].g.ne() > ne) { ne = ctx->subs[i].g.ne(); best = i; }
+    Sub& s = ctx->subs[best];
+    FomDev F = s.fom;  // shallow copy pointing at scratch state below
+    const int nn = s.g.nn();
+    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
+    double *u = nullptr, *v = nullptr, *a = nullptr, *un = nullptr;
+    CK(cudaMalloc(&u, sizeof(double) * 3 * nn));
+    CK(cudaMalloc(&v, sizeof(double) * 3 * nn));
+    CK(cudaMalloc(&a, sizeof(double) * 3 * nn));
+    CK(cudaMalloc(&un, sizeof(double) * 3 * nn));
+    CK(cudaMemcpyAsync(u, s.fom.u[0], sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(v, s.fom.v, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(a, s.fom.a, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
+    F.v = v; F.a = a;
+    float best_ms = 1e30f;
+    int best_mode = kGather;
+    for (int mode : {kGather, kAtomic}) {
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
+            ElemArgs ea = elem_args(F, u, 1, nn);
+            if (fp32 && mode == kAtomic) ea.f = F.fe;
+            CK(launch_hex8_force(F.material, fp32, mode, ea, ctx->stream));
+            NodeArgs na = node_args(ctx, s);
+            na.v = v; na.a = a;
+            if (fp32 && mode == kAtomic) na.fclear = F.fe;
+            na.ucur = u; na.unext = un;
+            na.h1 = fom_slot(ctx, s, 1);
+            na.h2 = fom_slot(ctx, s, std::min(2, ctx->nsub));
+            na.last = 0;
+            CK(launch_node_update(fp32, mode, na, ctx->stream));
+        }
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (ms < best_ms) { best_ms = ms; best_mode = mode; }
+    }
+    // the atomic buffers must be clean after the trial
+    CK(cudaMemsetAsync(s.fom.f, 0, sizeof(double) * 3 * nn, ctx->stream));
+    if (fp32) CK(cudaMemsetAsync(s.fom.fe, 0, sizeof(float) * 3 * nn, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(u); cudaFree(v); cudaFree(a); cudaFree(un);
+    ctx->scatter = best_mode;
+    return OSAM_OK;
+}
+
+int subdomain_advance(osam_ctx* ctx, int sub) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
+    int r = ctx->subs[sub].kind == OSAM_FOM ? advance_fom(ctx, sub) : advance_rom(ctx, sub);
+    if (r) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int transfer_overlap(osam_ctx* ctx, int src, int dst) {
+    if (!ctx) return OSAM_EINVAL;
+    bool any = false;
+    for (CplDev& c : ctx->cpls)
+        if (c.src == src && c.dst == dst) {
+            any = true;
+            if (int r = transfer(ctx, c)) return r;
+        }
+    if (!any) return ctx->fail(OSAM_EINVAL, "no coupling %d -> %d", src, dst);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_begin_interval(osam_ctx* ctx) {
+    if (!ctx) return OSAM_EINVAL;
+    if (int r = save_all(ctx, false)) return r;
+    for (CplDev& c : ctx->cpls)
+        if (int r = zoh(ctx, c)) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_restore_interval(osam_ctx* ctx) {
+    if (!ctx) return OSAM_EINVAL;
+    if (int r = save_all(ctx, true)) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_criterion(osam_ctx* ctx, double* cnum, double* cden) {
+    if (!ctx) return OSAM_EINVAL;
+    if (int r = criterion_async(ctx)) return r;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (cnum) *cnum = ctx->result_h[0];
+    if (cden) *cden = ctx->result_h[1];
+    if (ctx->result_h[2] != 0.0) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state");
+    return OSAM_OK;
+}
+
+int schwarz_step(osam_ctx* ctx, osam_step_report* rep) {
+    if (!ctx) return OSAM_EINVAL;
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (int r = save_all(ctx, false)) return r;
+    for (CplDev& c : ctx->cpls)
+        if (int r = zoh(ctx, c)) return r;
+    int status = OSAM_MAXITER, n = 1;
+    double cnum = 0.0, cden = 0.0;
+    for (n = 1; n <= ctx->max_it; ++n) {
+        if (n > 1)
+            if (int r = save_all(ctx, true)) return r;
+        for (int i = 0; i < (int)ctx->subs.size(); ++i) {
+            int r = ctx->subs[i].kind == OSAM_FOM ? advance_fom(ctx, i) : advance_rom(ctx, i);
+            if (r) return r;
+            for (CplDev& c : ctx->cpls)
+                if (c.src == i)
+                    if (int rr = transfer(ctx, c)) return rr;
+        }
+        if (int r = criterion_async(ctx)) return r;
+        CK(cudaStreamSynchronize(ctx->stream));
+        cnum = ctx->result_h[0];
+        cden = ctx->result_h[1];
+        if (ctx->result_h[2] != 0.0) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state at iteration %d", n);
+        if (ctx->cpls.empty()) { status = OSAM_OK; break; }
+        if (n >= 2 && (cnum < ctx->tol_abs * ctx->tol_abs || cnum < ctx->tol_rel * ctx->tol_rel * cden)) {
+            status = OSAM_OK;
+            break;
+        }
+    }
+    if (n > ctx->max_it) n = ctx->max_it;
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (rep) {
+        rep->status = status;
+        rep->iterations = n;
+        rep->cnum = cnum;
+        rep->cden = cden;
+        rep->element_updates = (long long)n * ctx->nsub * ctx->fom_elements;
+        rep->elapsed_ms = ms;
+    }
+    return status;
+}
+
+int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, int* n_free, int* n_schwarz) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
+    Sub& s = ctx->subs[sub];
+    if (n_nodes) *n_nodes = s.g.nn();
+    if (n_elements) *n_elements = s.g.ne();
+    if (n_schwarz) *n_schwarz = s.ns;
+    if (n_free) {
+        int nf = 0;
+        for (int n = 0; n < s.g.nn(); ++n)
+            for (int c = 0; c < 3; ++c) nf += !(s.clamp_h[n] & (1 << c)) && s.srow_h[n] < 0;
+        *n_free = nf;
+    }
+    return OSAM_OK;
+}
+
+int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
+    Sub& s = ctx->subs[sub];
+    const int nn = s.g.nn();
+    double* outs[3] = {u, v, a};
+    for (int f = 0; f < 3; ++f) {
+        if (!outs[f]) continue;
+        if (s.kind == OSAM_FOM) {
+            const double* src = f == 0 ? s.fom.u[0] : (f == 1 ? s.fom.v : s.fom.a);
+            CK(launch_soa_to_aos(src, ctx->scratch, nn, ctx->stream));
+        } else {
+            CK(launch_rom_full_field(s.rom, s.rom.q + (long long)f * s.rom.r, f, ctx->scratch, ctx->nsub, ctx->stream));
+        }
+        CK(cudaMemcpyAsync(outs[f], ctx->scratch, sizeof(double) * 3 * nn, cudaMemcpyDefault, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return OSAM_OK;
+}
+
+int osam_set_state(osam_ctx* ctx, int sub, const double* u, const double* v, const double* a) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || !u) return OSAM_EINVAL;
+    Sub& s = ctx->subs[sub];
+    const int nn = s.g.nn();
+    if (s.kind == OSAM_FOM) {
+        FomDev& F = s.fom;
+        if (int r = upload(ctx, ctx->scratch, u, sizeof(double) * 3 * nn)) return r;
+        CK(launch_aos_to_soa(ctx->scratch, F.u[0], nn, ctx->stream));
+        if (v) {
+            if (int r = upload(ctx, ctx->scratch, v, sizeof(double) * 3 * nn)) return r;
+            CK(launch_aos_to_soa(ctx->scratch, F.v, nn, ctx->stream));
+        } else CK(cudaMemsetAsync(F.v, 0, sizeof(double) * 3 * nn, ctx->stream));
+        CK(launch_zero_clamped(nn, F.clamp, F.u[0], F.v, ctx->stream));
+        if (a) {
+            if (int r = upload(ctx, ctx->scratch, a, sizeof(double) * 3 * nn)) return r;
+            CK(launch_aos_to_soa(ctx->scratch, F.a, nn, ctx->stream));
+        } else if (int r = fom_initial_accel(ctx, s)) return r;
+    } else {
+        RomDev& R = s.rom;
+        double* uv = ctx->scratch;  // needs 6 nn: use two passes
+        if (int r = upload(ctx, uv, u, sizeof(double) * 3 * nn)) return r;
+        CK(launch_rom_basis_project(R, uv, nullptr, ctx->stream));
+        if (v) {
+            if (int r = upload(ctx, uv, v, sizeof(double) * 3 * nn)) return r;
+            // project v into qd: reuse the kernel with u := v and copy q -> qd afterwards
+            CK(cudaMemcpyAsync(R.sq, R.q, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(launch_rom_basis_project(R, uv, nullptr, ctx->stream));
+            CK(cudaMemcpyAsync(R.q + R.r, R.q, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(R.q, R.sq, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
+        } else CK(cudaMemsetAsync(R.q + R.r, 0, sizeof(double) * R.r, ctx->stream));
+        CK(launch_rom_project(R, 0, 0, ctx->stream));
+        CK(launch_rom_step(R, 0, ctx->dt, 1, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* qd, double* qdd) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || ctx->subs[sub].kind != OSAM_ROM) return OSAM_EINVAL;
+    RomDev& R = ctx->subs[sub].rom;
+    double* outs[3] = {q, qd, qdd};
+    for (int f = 0; f < 3; ++f)
+        if (outs[f]) CK(cudaMemcpyAsync(outs[f], R.q + (long long)f * R.r, sizeof(double) * R.r, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_set_reduced_state(osam_ctx* ctx, int sub, const double* q, const double* qd, const double* qdd) {
+    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || ctx->subs[sub].kind != OSAM_ROM) return OSAM_EINVAL;
+    RomDev& R = ctx->subs[sub].rom;
+    const double* ins[3] = {q, qd, qdd};
+    for (int f = 0; f < 3; ++f)
+        if (ins[f]) CK(cudaMemcpyAsync(R.q + (long long)f * R.r, ins[f], sizeof(double) * R.r, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// element-level operators
+// ------------------------------------------------------------------------------------------------
+static ElemArgs standalone_args(int nx, int ny, int nz, double h, double lambda, double mu, const double* lam_e,
+                                const double* mu_e, const double* u) {
+    ElemArgs a{};
+    a.nx = nx; a.ny = ny; a.nz = nz; a.ne = nx * ny * nz;
+    a.invh = 1.0 / h;
+    a.w8 = h * h / 8.0;
+    a.lam = lambda; a.mu = mu;
+    a.lam_e = lam_e; a.mu_e = mu_e;
+    a.u = u; a.usn = 3; a.usc = 1;
+    a.fsn = 3; a.fsc = 1;
+    return a;
+}
+
+int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambda, double mu, const double* lambda_e,
+                    const double* mu_e, const double* u, double* f, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !f) return OSAM_EINVAL;
+    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN) return OSAM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    if (cudaMemsetAsync(f, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
+    ElemArgs a = standalone_args(nx, ny, nz, h, lambda, mu, lambda_e, mu_e, u);
+    a.f = f;
+    return launch_hex8_force(material, false, kAtomic, a, s) == cudaSuccess ? OSAM_OK : OSAM_ECUDA;
+}
+
+int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double lambda, double mu,
+                        const double* lambda_e, const double* mu_e, const double* u, const double* ybar, double* ubar,
+                        double* lambda_bar, double* mu_bar, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !ybar || !ubar) return OSAM_EINVAL;
+    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN) return OSAM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    if (cudaMemsetAsync(ubar, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
+    ElemArgs a = standalone_args(nx, ny, nz, h, lambda, mu, lambda_e, mu_e, u);
+    a.f = ubar;
+    return launch_hex8_vjp(material, a, ybar, 3, 1, lambda_bar, mu_bar, 0, s) == cudaSuccess ? OSAM_OK : OSAM_ECUDA;
+}
+
+// ------------------------------------------------------------------------------------------------
+// adjoint rollout
+// ------------------------------------------------------------------------------------------------
+int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
+    if (!d || !out) return OSAM_EINVAL;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || !(d->h > 0.0) || !d->u0 || !d->w || !d->lambda_e || !d->mu_e ||
+        d->n_steps < 0 || !(d->dt > 0.0) || !(d->rho > 0.0))
+        return OSAM_EINVAL;
+    auto holder = std::make_unique<osam_ctx>();
+    osam_ctx* ctx = holder.get();
+    if (int r = check_device(ctx, d->device)) { g_init_error = ctx->err; return r; }
+    if (d->stream) ctx->stream = static_cast<cudaStream_t>(d->stream);
+    else { CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)); ctx->own_stream = true; }
+    CK(cudaEventCreate(&ctx->ev0));
+    CK(cudaEventCreate(&ctx->ev1));
+    ctx->dt = d->dt;
+    ctx->nsub = 1;
+    Sub s;
+    s.kind = OSAM_FOM;
+    s.g.nx = d->nx; s.g.ny = d->ny; s.g.nz = d->nz; s.g.h = d->h;
+    const int nn = s.g.nn(), ne = s.g.ne();
+    s.clamp_h.assign(nn, 0);
+    if (d->dirichlet) CK(cudaMemcpy(s.clamp_h.data(), d->dirichlet, nn, cudaMemcpyDefault));
+    for (auto& c : s.clamp_h) c &= 7;
+    s.srow_h.assign(nn, -1);
+    s.ns = 0;
+    CKA(ctx->scratch = ctx->alloc<double>(3LL * nn));
+    osam_subdomain_desc sd{};
+    sd.kind = OSAM_FOM;
+    sd.nx = d->nx; sd.ny = d->ny; sd.nz = d->nz; sd.h = d->h;
+    sd.material = d->material;
+    sd.rho = d->rho;
+    sd.lambda_e = d->lambda_e; sd.mu_e = d->mu_e;
+    sd.u0 = d->u0; sd.v0 = d->v0;
+    ctx->subs.push_back(s);
+    Sub& S = ctx->subs[0];
+    if (int r = setup_fom(ctx, S, sd)) { g_init_error = ctx->err; return r; }
+    FomDev& F = S.fom;
+    const double dt = d->dt;
+    const int T = d->n_steps;
+    const int C = d->checkpoint_every > 0 ? d->checkpoint_every : 50;
+    const int nck = T / C + 1;
+    const long long n3 = 3LL * nn;
+    double* ck = ctx->alloc<double>((size_t)nck * 3 * n3);  // (u, v, a) at steps 0, C, 2C, ...
+    double* useg = ctx->alloc<double>((size_t)(C + 1) * n3); // displacements of one segment
+    double* ub = ctx->alloc<double>(n3);
+    double* vb = ctx->alloc<double>(n3);
+    double* ab = ctx->alloc<double>(n3);
+    double* y = ctx->alloc<double>(n3);
+    double* tmp = ctx->alloc<double>(n3);
+    double* glam = ctx->alloc<double>(ne);
+    double* gmu = ctx->alloc<double>(ne);
+    double* Jd = ctx->alloc<double>(1);
+    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(tmp); CKA(glam); CKA(gmu); CKA(Jd);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (int r = fom_initial_accel(ctx, S)) return r;
+    // one explicit step in place on (u[0], v, a), no Schwarz data
+    auto step = [&](double* u_store) -> int {
+        NodeArgs p = node_args(ctx, S);
+        p.predict_only = 1; p.ucur = F.u[0]; p.unext = F.u[1]; p.h2 = nullptr; p.last = 0;
+        CK(launch_node_update(false, kAtomic, p, ctx->stream));
+        ElemArgs ea = elem_args(F, F.u[1], 1, nn);
+        ea.f = F.f;
+        CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
+        NodeArgs na = node_args(ctx, S);
+        na.fclear = F.f; na.ucur = F.u[1]; na.unext = F.u[0]; na.last = 1;
+        CK(launch_node_update(false, kAtomic, na, ctx->stream));
+        CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        return OSAM_OK;
+    };
+    auto save_ck = [&](int idx) -> int {
+        double* base = ck + (size_t)idx * 3 * n3;
+        CK(cudaMemcpyAsync(base, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(base + n3, F.v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(base + 2 * n3, F.a, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        return OSAM_OK;
+    };
+    auto load_ck = [&](int idx) -> int {
+        double* base = ck + (size_t)idx * 3 * n3;
+        CK(cudaMemcpyAsync(F.u[0], base, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(F.v, base + n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(F.a, base + 2 * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        return OSAM_OK;
+    };
+    if (int r = save_ck(0)) return r;
+    for (int t = 1; t <= T; ++t) {
+        if (int r = step(nullptr)) return r;
+        if (t % C == 0)
+            if (int r = save_ck(t / C)) return r;
+    }
+    // J = w . u_T  (w interleaved -> SoA in y)
+    if (int r = upload(ctx, ctx->scratch, d->w, sizeof(double) * n3)) return r;
+    CK(launch_aos_to_soa(ctx->scratch, ub, nn, ctx->stream));
+    CK(launch_zero_clamped(nn, F.clamp, ub, nullptr, ctx->stream));
+    std::vector<double> wh(n3), uh(n3);
+    CK(cudaMemcpyAsync(wh.data(), ub, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(uh.data(), F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double J = 0.0;
+    for (long long q = 0; q < n3; ++q) J += wh[q] * uh[q];
+    // reverse sweep, one checkpoint segment at a time
+    ElemArgs va = elem_args(F, nullptr, 1, nn);
+    va.f = tmp;
+    for (int seg = (T - 1) / C; seg >= 0 && T > 0; --seg) {
+        const int t0 = seg * C, t1 = std::min(T, t0 + C);
+        if (int r = load_ck(seg)) return r;
+        CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int t = t0 + 1; t <= t1; ++t)
+            if (int r = step(useg + (size_t)(t - t0) * n3)) return r;
+        for (int t = t1 - 1; t >= t0; --t) {
+            CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
+            va.u = useg + (size_t)(t + 1 - t0) * n3;
+            va.usn = 1; va.usc = nn; va.fsn = 1; va.fsc = nn;
+            CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
+            CK(launch_adjoint_post(nn, dt, F.clamp, tmp, ub, vb, ab, ctx->stream));
+        }
+    }
+    // a_0 = -M^-1 f(u_0): y = -M^-1 abar_0 (the pre kernel with vbar = 0 contribution removed)
+    CK(cudaMemsetAsync(tmp, 0, sizeof(double) * n3, ctx->stream));
+    CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
+    if (int r = load_ck(0)) return r;
+    va.u = F.u[0];
+    CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
+    // gu0 = ubar + tmp (free dofs): the post kernel adds tmp into ubar
+    CK(launch_adjoint_post(nn, 0.0, F.clamp, tmp, ub, vb, ab, ctx->stream));
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    out->J = J;
+    out->elapsed_ms = ms;
+    if (out->grad_u0) {
+        CK(launch_soa_to_aos(ub, ctx->scratch, nn, ctx->stream));
+        CK(cudaMemcpyAsync(out->grad_u0, ctx->scratch, sizeof(double) * n3, cudaMemcpyDefault, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (out->grad_v0) {
+        CK(launch_soa_to_aos(vb, ctx->scratch, nn, ctx->stream));
+        CK(cudaMemcpyAsync(out->grad_v0, ctx->scratch, sizeof(double) * n3, cudaMemcpyDefault, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (out->grad_lambda) CK(cudaMemcpyAsync(out->grad_lambda, glam, sizeof(double) * ne, cudaMemcpyDefault, ctx->stream));
+    if (out->grad_mu) CK(cudaMemcpyAsync(out->grad_mu, gmu, sizeof(double) * ne, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+}  // extern "C"
