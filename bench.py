@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Schwarz-coupled element-updates/s of one O-SAM controller step on a GB300.
+
+Workload (N=1 line): the FOM / OpInf hybrid -- subdomain A a 40x40x80 Neo-Hookean hex8 FOM, subdomain
+B (mirror 40x40x80 mesh, 2-layer overlap) a quadratic OpInf ROM of rank 64 fitted (Tikhonov
+lambda = 1e-6) by the library's opinf_fit on 500 snapshots of a seeded FOM-FOM training run of the same
+geometry; explicit central difference dt = 1e-6 s, controller steps of 20 substeps, relative tolerance
+1e-12, at most 64 Schwarz iterations.  A bench "step" is one controller step (every Schwarz
+iteration: FOM substeps, ROM substeps, overlap transfers, convergence check).
+
+value   = FOM element-updates executed in the timed steps / device time of those steps (CUDA events
+          on the library's stream; L2 flushed between steps by a 256 MiB write outside the timing).
+e2e     = the same metric through the public API with host buffers: every step sets the FOM and ROM
+          states from pinned host memory, runs schwarz_step and reads the states back.
+roofline= the Neo-Hookean FP64 internal-force kernel (the dominant kernel): algorithmic FP64 flops of
+          its launches in the timed steps / their CUDA-event time, against the FP64 peak.
+--impl reference times the CPU oracle on a bounded sample of the same workload.
+Multi-GPU: replicas only (the coupled step does not shard); each rank runs the workload on its GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Schwarz-coupled element-updates/sec on 1 GB300"
+UNIT = "element-updates/s"
+# FP64 flops of one Neo-Hookean element evaluation in the sum-factorised kernel (FMA = 2 flops,
+# each of the 8 cube roots counted as one flop): edge scaling 24 + differences 36 + interpolation to
+# the Gauss points 180 + 8 x 90 constitutive + 36 accumulation + 180 transposed interpolation +
+# 48 nodal accumulation + 8.
+FLOPS_PER_NH_ELEMENT = 1232
+# FP64 peak: recipe figure for the GB300 (nominal FP64 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 1.25
+# DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
+# valid only for the kernel source it was captured on; None until captured.
+FORCE_TRAFFIC = {"source_sha256": None, "bytes_per_launch": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=90)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="osam", choices=["osam", "reference"])
+    ap.add_argument("--n", type=int, default=40)
+    ap.add_argument("--nz", type=int, default=80)
+    ap.add_argument("--rank", type=int, default=64)
+    ap.add_argument("--snapshots", type=int, default=500)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def source_sha():
+    import hashlib
+    p = os.path.join(ROOT, "paper_2511_20687_gb300", "csrc", "fom_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+# ---------------------------------------------------------------------------------------------
+# workload construction
+# ---------------------------------------------------------------------------------------------
+def train_rom(W, osam, args, device, log):
+    """Seeded FOM-FOM training run (snapshot every 4th step) and GPU OpInf fit of subdomain B."""
+    rng = np.random.default_rng(W.SEED_BASE + 1)
+    amp = float(rng.uniform(0.5e-3, 1.0e-3))
+    spec = W.bar_chain("train", args.n, [args.nz, args.nz], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, amp, 1e-6, 4)
+    prob = osam.Problem(spec, device=device)
+    sz = prob.sizes(1)
+    nn = sz["n_nodes"]
+    sd = spec.subdomains[1]
+    _, _, kk = sd.node_grid()
+    schwarz = np.zeros(nn, bool)
+    schwarz[kk == 0] = True
+    clamped = np.repeat(sd.dirichlet, 3).reshape(-1, 3) > 0
+    free = (~clamped & ~schwarz[:, None]).reshape(-1)
+    sdof = np.repeat(schwarz, 3)
+    U = np.empty((args.snapshots, int(free.sum())))
+    A = np.empty_like(U)
+    S = np.empty((args.snapshots, int(sdof.sum())))
+    t0 = time.time()
+    for k in range(args.snapshots):
+        prob.step()
+        u, _, a = prob.state(1, fields=(0, 2))
+        U[k] = u.reshape(-1)[free]
+        A[k] = a.reshape(-1)[free]
+        S[k] = u.reshape(-1)[sdof]
+    prob.close()
+    log(f"training run: {args.snapshots} controller steps of 4 substeps in {time.time() - t0:.1f}s (amplitude {amp:.3e})")
+    t0 = time.time()
+    ops = osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device)
+    log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {time.time() - t0:.1f}s")
+    return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}
+
+
+def hybrid_spec(W, args):
+    return W.fom_opinf_hybrid(args.n, args.nz, rom=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_problem(W, args, n_substeps):
+    """The hybrid workload for the oracle with seeded stand-in ROM operators of the same sizes and one
+    Schwarz iteration per controller step (a bounded sample of the same FOM work)."""
+    spec = hybrid_spec(W, args)
+    spec.n_substeps = n_substeps
+    spec.max_iters = 1
+    sd = spec.subdomains[1]
+    n_sdof = 3 * (args.n + 1) ** 2
+    n_free = 3 * sd.n_nodes - n_sdof
+    ops = W.synthetic_rom_operators(n_free, n_sdof, args.rank, 32, W.SEED_BASE + 11)
+    return spec, {1: ops}
+
+
+def cpu_oracle_rate(W, args, n_substeps, min_seconds, max_steps=None):
+    from oracle import oracle as O
+    spec, ops = oracle_sample_problem(W, args, n_substeps)
+    prob = O.Problem(spec, rom_ops=ops)
+    ne = spec.subdomains[0].n_elements
+    steps, elapsed = 0, 0.0
+    while elapsed < min_seconds and (max_steps is None or steps < max_steps):
+        t0 = time.process_time()
+        prob.step()
+        elapsed += time.process_time() - t0
+        steps += 1
+    return steps * n_substeps * ne / elapsed, steps, elapsed
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2511_20687_gb300 import workloads as W
+    n_sub = 5
+    spec, ops = oracle_sample_problem(W, args, n_sub)
+    from oracle import oracle as O
+    prob = O.Problem(spec, rom_ops=ops)
+    ne = spec.subdomains[0].n_elements
+    for _ in range(args.warmup):
+        prob.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        prob.step()
+    dt = time.perf_counter() - t0
+    value = args.steps * n_sub * ne / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} NH FOM + r={args.rank} OpInf ROM",
+                       "sample": f"{n_sub} substeps x 1 Schwarz iteration per step, seeded stand-in ROM operators",
+                       "l2": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} controller steps of {n_sub} substeps, 1 Schwarz iteration each"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+
+    def log(msg):
+        if rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2511_20687_gb300 import build_lib
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2511_20687_gb300 import osam
+    from paper_2511_20687_gb300 import workloads as W
+
+    ops = train_rom(W, osam, args, local, log)
+    spec = hybrid_spec(W, args)
+    prob = osam.Problem(spec, rom_ops={1: ops}, device=local)
+    log(f"scatter mode: {'atomic' if prob.scatter_mode() == osam.SCATTER_ATOMIC else 'gather'}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    for _ in range(args.warmup):
+        r = prob.step()
+        if r["status"] < 0:
+            raise RuntimeError(r)
+    prob.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    total_ms, updates, iters = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        r = prob.step()
+        total_ms += r["elapsed_ms"]
+        updates += r["element_updates"]
+        iters.append(r["iterations"])
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    prof = prob.profile_read()
+    # whole-job aggregate: all ranks' updates over the slowest rank's time
+    if world > 1:
+        t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device=f"cuda:{local}")
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms, updates = float(mx[0]), int(t[1])
+    value = updates / (total_ms * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    nA = prob.sizes(0)["n_nodes"]
+    hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
+    hq = [torch.empty(args.rank, dtype=torch.float64).pin_memory() for _ in range(3)]
+    prob.state(0, out=tuple(hu))
+    q = prob.reduced_state(1)
+    for k in range(3):
+        hq[k].copy_(torch.from_numpy(q[k]))
+    e2e_updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        prob.set_state(0, hu[0], hu[1], hu[2])
+        prob.set_reduced_state(1, hq[0], hq[1], hq[2])
+        r = prob.step()
+        e2e_updates += r["element_updates"]
+        prob.state(0, out=tuple(hu))
+        out_q = prob.reduced_state(1)
+        for k in range(3):
+            hq[k].copy_(torch.from_numpy(out_q[k]))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    io_bytes = 3 * nA * 3 * 8 + 3 * args.rank * 8
+    e2e = {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+
+    fp64_meas = osam.fp64_peak_gflops(local) / 1e3
+    achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
+    traffic = FORCE_TRAFFIC["bytes_per_launch"] if FORCE_TRAFFIC["source_sha256"] == source_sha() else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "k_hex8_force<NeoHookean, f64>", "peak_kind": "recipe nominal FP64",
+                "fp64_fma_measured_tflops": fp64_meas, "frac_of_measured_fp64": achieved / fp64_meas,
+                "force_ms_per_launch": prof["force_ms"] / max(1, prof["force_launches"]),
+                "force_time_share": prof["force_ms"] / total_ms if world == 1 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps} controller step(s) x 1 Schwarz iteration x 20 substeps of the 40x40x80 NH FOM "
+                         f"+ r={args.rank} ROM (seeded stand-in operators), {secs:.1f} s CPU"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} Neo-Hookean FOM + "
+                                       f"r={args.rank} quadratic OpInf ROM (fitted on {args.snapshots} snapshots)",
+                           "dt": 1e-6, "substeps_per_step": 20, "tol_rel": 1e-12, "max_iters": 64,
+                           "fom_elements": spec.subdomains[0].n_elements, "parallelism": "replicas",
+                           "l2": "flushed between steps (256 MiB write)",
+                           "mean_iterations": float(np.mean(iters)), "max_iterations": int(max(iters))},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": prof["kernel_launches"] if world == 1 else None,
+                "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

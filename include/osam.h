@@ -164,6 +164,16 @@ OSAM_API int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* q
 OSAM_API int osam_set_reduced_state(osam_ctx* ctx, int sub, const double* q, const double* qd, const double* qdd);
 /* Sizes of subdomain `sub` (any output may be NULL). */
 OSAM_API int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, int* n_free, int* n_schwarz_nodes);
+/* Kernel-level accounting for measurement: with enable = 1, every internal-force launch of
+ * schwarz_step / subdomain_advance is bracketed by CUDA events on the context stream; the counters
+ * (force time, force launches, elements processed by them, and all kernel launches issued by the
+ * controller) restart at zero on every osam_profile call. */
+OSAM_API int osam_profile(osam_ctx* ctx, int enable);
+OSAM_API int osam_profile_read(osam_ctx* ctx, double* force_ms, long long* force_launches, long long* force_elements,
+                      long long* kernel_launches);
+/* FP64 fused multiply-add throughput of device `device` in GFLOP/s (2 flops per FMA), measured by a
+ * register-resident FMA loop over 8 blocks per SM; the ALU roofline of the FP64 element kernels. */
+OSAM_API int osam_fp64_peak(int device, double* gflops);
 /* The scatter mode in use (OSAM_SCATTER_ATOMIC / GATHER) after any autotuning. */
 OSAM_API int osam_scatter_mode(osam_ctx* ctx);
 OSAM_API void osam_destroy(osam_ctx* ctx);

@@ -476,10 +476,23 @@ static int locate_in_element(const omesh* m, int e, const double x[3], double xi
     return 1;
 }
 
-/* donor = lowest-index element containing x; weights = N_b(xi) */
+/* donor = lowest-index element containing x; weights = N_b(xi).  Elements whose node bounding box
+ * (widened by the containment tolerance) misses x are skipped before the Newton inversion. */
 static int find_donor(const omesh* m, const double x[3], int nodes[8], double w[8]) {
     for (int e = 0; e < m->ne; ++e) {
-        double xi[3], N[8], dN[8][3];
+        double xi[3], N[8], dN[8][3], lo[3], hi[3], X[3];
+        int en[8], inside = 1;
+        elem_nodes(m, e, en);
+        for (int i = 0; i < 3; ++i) { lo[i] = 1e300; hi[i] = -1e300; }
+        for (int a = 0; a < 8; ++a) {
+            node_X(m, en[a], X);
+            for (int i = 0; i < 3; ++i) { lo[i] = fmin(lo[i], X[i]); hi[i] = fmax(hi[i], X[i]); }
+        }
+        for (int i = 0; i < 3; ++i) {
+            double tol = 1e-6 * (hi[i] - lo[i]);
+            if (x[i] < lo[i] - tol || x[i] > hi[i] + tol) inside = 0;
+        }
+        if (!inside) continue;
         if (locate_in_element(m, e, x, xi)) {
             elem_nodes(m, e, nodes);
             shape(xi, N, dN);
@@ -805,8 +818,9 @@ int orc_init(void* vp) {
             s->q[k] = a; s->qd[k] = b;
         }
     }
-    /* initial boundary data: slot 0 of every input history from the sources' initial states */
-    for (int k = 0; k < p->ncpl; ++k) transfer_slot(p, &p->cpl[k], 0, 1);
+    /* initial boundary data: zero-order hold of the sources' initial states in every slot */
+    for (int k = 0; k < p->ncpl; ++k)
+        for (int j = 0; j <= p->nsub; ++j) transfer_slot(p, &p->cpl[k], j, 1);
     /* initial accelerations */
     for (int i = 0; i < p->nsd; ++i) {
         osub* s = &p->sd[i];

@@ -121,9 +121,11 @@ struct Dev {
         if (!(p)) { g_fit_error = "device allocation failed"; return OSAM_ENOMEM; } \
     } while (0)
 
-// POD of snapshots X [n_snap][n] on the device: returns Phi [n][r] (device), sigma (host, all)
-int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, double** Phi_out,
-        std::vector<double>& sigma) {
+// POD of snapshots X [n_snap][n] on the device: returns Phi [n][r] (device), sigma (host, all).
+// r > 0 fixes the rank; r <= 0 selects the smallest rank whose energy E_r reaches `energy`, capped
+// at r_max; the rank used is returned in *r_used.
+int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, double energy, int r_max,
+        int* r_used, double** Phi_out, std::vector<double>& sigma) {
     double* G = dev.alloc((size_t)nsnap * nsnap);
     FA(G);
     FK(launch_gemm_nt(nsnap, nsnap, n, X, n, X, n, G, nsnap, 1.0, 0.0, s));
@@ -138,6 +140,18 @@ int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, doub
     std::sort(order.begin(), order.end(), [&](int a, int b) { return Gh[(size_t)a * nsnap + a] > Gh[(size_t)b * nsnap + b]; });
     sigma.resize(nsnap);
     for (int i = 0; i < nsnap; ++i) sigma[i] = std::sqrt(std::max(0.0, Gh[(size_t)order[i] * nsnap + order[i]]));
+    if (r <= 0) {
+        double tot = 0.0, acc = 0.0;
+        for (double x : sigma) tot += x * x;
+        r = nsnap;
+        for (int k = 0; k < nsnap; ++k) {
+            acc += sigma[k] * sigma[k];
+            if (acc >= energy * tot) { r = k + 1; break; }
+        }
+        if (r_max > 0) r = std::min(r, r_max);
+        while (r > 1 && !(sigma[r - 1] > 0.0)) --r;
+    }
+    *r_used = r;
     if (r > nsnap) { g_fit_error = "POD rank exceeds the snapshot count"; return OSAM_EINVAL; }
     if (r > 0 && !(sigma[r - 1] > 0.0)) { g_fit_error = "snapshot matrix rank is below the requested POD rank"; return OSAM_EINVAL; }
     // W = V_r Sigma_r^-1 [nsnap][r]
@@ -198,7 +212,8 @@ extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out
     FK(cudaMemcpyAsync(A, in->A, sizeof(double) * ns * n, cudaMemcpyDefault, s));
     double* Phi = nullptr;
     std::vector<double> sigma, sigma_s;
-    if (int rc = pod(s, dev, U, ns, n, r, &Phi, sigma)) return rc;
+    int r_used = 0;
+    if (int rc = pod(s, dev, U, ns, n, r, 0.0, 0, &r_used, &Phi, sigma)) return rc;
     // boundary basis
     int rs = 0;
     double* PhiS = nullptr;
@@ -207,23 +222,10 @@ extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out
         S = dev.alloc((size_t)ns * nsd);
         FA(S);
         FK(cudaMemcpyAsync(S, in->S, sizeof(double) * ns * nsd, cudaMemcpyDefault, s));
-        std::vector<double> tmp_sigma;
-        double* tmpPhi = nullptr;
-        // energy selection needs the spectrum first: rank-1 pass gives sigma
-        if (int rc = pod(s, dev, S, ns, nsd, 1, &tmpPhi, sigma_s)) return rc;
-        if (in->r_s > 0) rs = in->r_s;
-        else {
-            double tot = 0.0, acc = 0.0;
-            for (double x : sigma_s) tot += x * x;
-            rs = (int)sigma_s.size();
-            for (int k = 0; k < (int)sigma_s.size(); ++k) {
-                acc += sigma_s[k] * sigma_s[k];
-                if (acc >= in->energy_s * tot) { rs = k + 1; break; }
-            }
-        }
-        rs = std::max(1, std::min({rs, in->r_s_max > 0 ? in->r_s_max : rs, ns}));
-        while (rs > 1 && !(sigma_s[rs - 1] > 0.0)) --rs;
-        if (int rc = pod(s, dev, S, ns, nsd, rs, &PhiS, sigma_s)) return rc;
+        const int rs_cap = std::min(in->r_s_max > 0 ? in->r_s_max : ns, ns);
+        if (int rc = pod(s, dev, S, ns, nsd, in->r_s > 0 ? std::min(in->r_s, ns) : 0, in->energy_s, rs_cap, &rs,
+                         &PhiS, sigma_s))
+            return rc;
     }
     const int nq = in->quadratic ? r * (r + 1) / 2 : 0;
     const int d = r + nq + rs + 1;

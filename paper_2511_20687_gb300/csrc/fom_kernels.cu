@@ -516,6 +516,17 @@ __global__ void k_donor(Grid src, Grid dst, const int* dst_nodes, int nrow, int*
     }
 }
 
+// f[c][n] = sum of the element contributions of node n (fixed order), FP64 element buffer
+__global__ void k_gather_force(int nx, int ny, int nz, int ne, const double* fe, double* f) {
+    const int nn = (nx + 1) * (ny + 1) * (nz + 1);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nn) return;
+    const int c = t / nn, n = t % nn;
+    const int i = n % (nx + 1);
+    const int q = n / (nx + 1);
+    f[t] = gather_force<double>(fe, nx, ny, nz, ne, i, q % (ny + 1), q / (ny + 1), c);
+}
+
 __global__ void k_aos_to_soa(const double* aos, double* soa, int nn) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
@@ -613,6 +624,11 @@ cudaError_t launch_donor(const Grid& src, const Grid& dst, const uint8_t*, const
                          double* dw, int* err, cudaStream_t s) {
     if (nrow == 0) return cudaSuccess;
     k_donor<<<grid_for(nrow, 128), 128, 0, s>>>(src, dst, dst_nodes, nrow, dnode, dw, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_force(const Grid& g, const double* fe, double* f, cudaStream_t s) {
+    k_gather_force<<<grid_for(3LL * g.nn(), 256), 256, 0, s>>>(g.nx, g.ny, g.nz, g.ne(), fe, f);
     return cudaGetLastError();
 }
 

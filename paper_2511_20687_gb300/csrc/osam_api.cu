@@ -56,6 +56,38 @@ struct osam_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
     long long fom_elements = 0;
+    // kernel-level timing of the internal-force launches and a launch count
+    bool prof = false;
+    std::vector<cudaEvent_t> pev;
+    int pnext = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0, prof_elements = 0, launches = 0;
+
+    int prof_begin() {
+        if (!prof) return -1;
+        while (pnext + 2 > (int)pev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            pev.push_back(e);
+        }
+        cudaEventRecord(pev[pnext], stream);
+        return pnext;
+    }
+    void prof_end(int k, long long elements) {
+        if (k < 0) return;
+        cudaEventRecord(pev[k + 1], stream);
+        pnext = k + 2;
+        prof_launches += 1;
+        prof_elements += elements;
+    }
+    // after a stream synchronisation: fold the recorded pairs into prof_ms
+    void prof_collect() {
+        for (int k = 0; k + 1 < pnext; k += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) prof_ms += ms;
+        }
+        pnext = 0;
+    }
 
     ~osam_ctx() {
         if (stream) cudaStreamSynchronize(stream);
@@ -63,6 +95,7 @@ struct osam_ctx {
         if (result_h) cudaFreeHost(result_h);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : pev) cudaEventDestroy(e);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -92,6 +125,13 @@ struct osam_ctx {
         cudaError_t e_ = (call);                                                                          \
         if (e_ != cudaSuccess) return ctx->fail(OSAM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                                                 __FILE__, __LINE__);                                      \
+    } while (0)
+
+// checked kernel launch, counted
+#define LK(call)          \
+    do {                  \
+        CK(call);         \
+        ++ctx->launches;  \
     } while (0)
 
 #define CKA(ptr)                                                                                    \
@@ -145,13 +185,13 @@ int advance_fom(osam_ctx* ctx, int i) {
     p.unext = F.u[1];
     p.h2 = fom_slot(ctx, s, 1);
     p.last = 0;
-    CK(launch_node_update(fp32, scatter, p, ctx->stream));
+    LK(launch_node_update(fp32, scatter, p, ctx->stream));
     for (int j = 0; j < ctx->nsub; ++j) {
         double* X = F.u[(j + 1) & 1];
         double* Y = F.u[j & 1];
         ElemArgs ea = elem_args(F, X, 1, nn);
         if (fp32 && scatter == kAtomic) ea.f = f32_buffer(F);
-        CK(launch_hex8_force(F.material, fp32, scatter, ea, ctx->stream));
+        LK(launch_hex8_force(F.material, fp32, scatter, ea, ctx->stream));
         NodeArgs na = node_args(ctx, s);
         if (fp32 && scatter == kAtomic) na.fclear = f32_buffer(F);
         na.ucur = X;
@@ -159,9 +199,9 @@ int advance_fom(osam_ctx* ctx, int i) {
         na.h1 = fom_slot(ctx, s, j + 1);
         na.h2 = (j + 2 <= ctx->nsub) ? fom_slot(ctx, s, j + 2) : nullptr;
         na.last = (j == ctx->nsub - 1);
-        CK(launch_node_update(fp32, scatter, na, ctx->stream));
+        LK(launch_node_update(fp32, scatter, na, ctx->stream));
         for (CplDev& c : ctx->cpls)
-            if (c.src == i) CK(launch_trace(c, X, F.v, F.a, nn, j + 1, ctx->nsub, ctx->stream));
+            if (c.src == i) LK(launch_trace(c, X, F.v, F.a, nn, j + 1, ctx->nsub, ctx->stream));
     }
     if (ctx->nsub & 1) CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
     return OSAM_OK;
@@ -170,8 +210,8 @@ int advance_fom(osam_ctx* ctx, int i) {
 int advance_rom(osam_ctx* ctx, int i) {
     RomDev& R = ctx->subs[i].rom;
     CK(cudaMemcpyAsync(R.qrec, R.q, sizeof(double) * 3 * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(launch_rom_project(R, 1, ctx->nsub, ctx->stream));
-    for (int j = 0; j < ctx->nsub; ++j) CK(launch_rom_step(R, j + 1, ctx->dt, 0, ctx->stream));
+    LK(launch_rom_project(R, 1, ctx->nsub, ctx->stream));
+    for (int j = 0; j < ctx->nsub; ++j) LK(launch_rom_step(R, j + 1, ctx->dt, 0, ctx->stream));
     return OSAM_OK;
 }
 
@@ -189,8 +229,8 @@ int transfer(osam_ctx* ctx, const CplDev& c) {
     int nd;
     dst_hist(ctx, c, &dst_rom, &hist, &nd);
     Sub& src = ctx->subs[c.src];
-    if (src.kind == OSAM_FOM) CK(launch_publish_fom(c, dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    else CK(launch_rom_reconstruct(c, src.rom, false, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    if (src.kind == OSAM_FOM) LK(launch_publish_fom(c, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    else LK(launch_rom_reconstruct(c, src.rom, false, dst_rom, hist, nd, ctx->nsub, ctx->stream));
     return OSAM_OK;
 }
 
@@ -201,8 +241,8 @@ int zoh(osam_ctx* ctx, const CplDev& c) {
     dst_hist(ctx, c, &dst_rom, &hist, &nd);
     Sub& src = ctx->subs[c.src];
     if (src.kind == OSAM_FOM)
-        CK(launch_zoh_from_fom(c, src.fom.u[0], src.fom.v, src.fom.a, src.g.nn(), dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    else CK(launch_rom_reconstruct(c, src.rom, true, dst_rom, hist, nd, ctx->nsub, ctx->stream));
+        LK(launch_zoh_from_fom(c, src.fom.u[0], src.fom.v, src.fom.a, src.g.nn(), dst_rom, hist, nd, ctx->nsub, ctx->stream));
+    else LK(launch_rom_reconstruct(c, src.rom, true, dst_rom, hist, nd, ctx->nsub, ctx->stream));
     return OSAM_OK;
 }
 
@@ -234,14 +274,14 @@ int criterion_async(osam_ctx* ctx) {
     int off = 0;
     for (Sub& s : ctx->subs) {
         if (s.kind == OSAM_FOM) {
-            CK(launch_norms_fom(s.fom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
+            LK(launch_norms_fom(s.fom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
             off += s.fom.norm_blocks;
         } else {
-            CK(launch_rom_norms(s.rom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
+            LK(launch_rom_norms(s.rom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
             off += 1;
         }
     }
-    CK(launch_norms_final(ctx->partial, off, ctx->result, ctx->stream));
+    LK(launch_norms_final(ctx->partial, off, ctx->result, ctx->stream));
     CK(cudaMemcpyAsync(ctx->result_h, ctx->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     return OSAM_OK;
 }
@@ -314,13 +354,21 @@ int setup_fom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
     return OSAM_OK;
 }
 
+// a0 = -M^-1 f(u0) in FP64 through the deterministic element buffer (FP64 [24][ne] scratch = fe when
+// it is large enough, else the atomic buffer is used)
 int fom_initial_accel(osam_ctx* ctx, Sub& s) {
     FomDev& F = s.fom;
     const int nn = s.g.nn();
-    CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
     ElemArgs ea = elem_args(F, F.u[0], 1, nn);
-    ea.f = F.f;
-    CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
+    if (ctx->precision == OSAM_FP64) {
+        ea.fe = F.fe;
+        CK(launch_hex8_force(F.material, false, kGather, ea, ctx->stream));
+        CK(launch_gather_force(s.g, static_cast<const double*>(F.fe), static_cast<double*>(F.f), ctx->stream));
+    } else {
+        CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
+        ea.f = F.f;
+        CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
+    }
     CK(launch_accel_from_force(F, static_cast<const double*>(F.f), ctx->stream));
     CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
     return OSAM_OK;
@@ -634,6 +682,30 @@ int subdomain_advance(osam_ctx* ctx, int sub) {
     int r = ctx->subs[sub].kind == OSAM_FOM ? advance_fom(ctx, sub) : advance_rom(ctx, sub);
     if (r) return r;
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_collect();
+    return OSAM_OK;
+}
+
+int osam_profile(osam_ctx* ctx, int enable) {
+    if (!ctx) return OSAM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_collect();
+    ctx->prof = enable != 0;
+    ctx->prof_ms = 0.0;
+    ctx->prof_launches = ctx->prof_elements = 0;
+    ctx->launches = 0;
+    return OSAM_OK;
+}
+
+int osam_profile_read(osam_ctx* ctx, double* force_ms, long long* force_launches, long long* force_elements,
+                      long long* kernel_launches) {
+    if (!ctx) return OSAM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_collect();
+    if (force_ms) *force_ms = ctx->prof_ms;
+    if (force_launches) *force_launches = ctx->prof_launches;
+    if (force_elements) *force_elements = ctx->prof_elements;
+    if (kernel_launches) *kernel_launches = ctx->launches;
     return OSAM_OK;
 }
 
@@ -708,6 +780,7 @@ int schwarz_step(osam_ctx* ctx, osam_step_report* rep) {
     if (n > ctx->max_it) n = ctx->max_it;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
+    ctx->prof_collect();
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (rep) {

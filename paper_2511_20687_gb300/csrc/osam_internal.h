@@ -134,6 +134,7 @@ cudaError_t launch_norms_fom(const FomDev& f, double dt, double* partial, cudaSt
 cudaError_t launch_norms_final(const double* partial, int nparts, double* result, cudaStream_t s);
 cudaError_t launch_donor(const Grid& src, const Grid& dst, const uint8_t* mask_dummy, const int* dst_nodes, int nrow,
                          int* dnode, double* dw, int* err, cudaStream_t s);
+cudaError_t launch_gather_force(const Grid& g, const double* fe, double* f, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, cudaStream_t s);
 cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, cudaStream_t s);
 cudaError_t launch_accel_from_force(const FomDev& f, const double* force_soa, cudaStream_t s);

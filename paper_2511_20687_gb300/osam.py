@@ -24,7 +24,8 @@ SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER = 0, 1, 2
 EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin_interval", "osam_restore_interval",
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
-            "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint"]
+            "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
+            "osam_profile", "osam_profile_read", "osam_fp64_peak"]
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
@@ -116,6 +117,10 @@ def load():
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.opinf_fit.argtypes = [C.POINTER(FitInput), C.POINTER(FitOutput)]
     L.osam_adjoint.argtypes = [C.POINTER(AdjointDesc), C.POINTER(AdjointOut)]
+    L.osam_profile.argtypes = [_vp, C.c_int]
+    L.osam_profile_read.argtypes = [_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong)]
+    L.osam_fp64_peak.argtypes = [C.c_int, _dp]
     _lib = L
     return L
 
@@ -274,12 +279,25 @@ class Problem:
     def scatter_mode(self):
         return load().osam_scatter_mode(self.h)
 
-    def state(self, i, out=None):
-        """(u, v, a) of subdomain i as [nodes, 3] arrays (numpy unless `out` tensors are given)."""
+    def profile(self, enable=True):
+        """Start (and reset) kernel-level accounting of the internal-force launches."""
+        self._c(load().osam_profile(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        ms = C.c_double()
+        fl, fe, kl = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self._c(load().osam_profile_read(self.h, C.byref(ms), C.byref(fl), C.byref(fe), C.byref(kl)))
+        return {"force_ms": ms.value, "force_launches": fl.value, "force_elements": fe.value,
+                "kernel_launches": kl.value}
+
+    def state(self, i, out=None, fields=(0, 1, 2)):
+        """(u, v, a) of subdomain i as [nodes, 3] arrays (numpy unless `out` arrays / tensors are given;
+        fields not listed are returned as None)."""
         n = self.sizes(i)["n_nodes"]
-        outs = out if out is not None else tuple(np.zeros((n, 3)) for _ in range(3))
-        self._c(load().osam_get_state(self.h, i, *[_ptr(x) for x in outs]))
-        return outs
+        if out is None:
+            out = tuple(np.zeros((n, 3)) if f in fields else None for f in range(3))
+        self._c(load().osam_get_state(self.h, i, *[_ptr(x) for x in out]))
+        return out
 
     def set_state(self, i, u, v=None, a=None):
         u, v, a = _f64(u), _f64(v), _f64(a)
@@ -360,3 +378,10 @@ def adjoint(dims, h, material, lam_e, mu_e, rho, dirichlet, u0, v0, dt, n_steps,
         msg = load().osam_last_error(None)
         raise OsamError(rc, msg.decode() if msg else "")
     return {"J": o.J, "grad_u0": gu, "grad_v0": gv, "grad_lambda": gl, "grad_mu": gm, "elapsed_ms": o.elapsed_ms}
+
+
+def fp64_peak_gflops(device=0) -> float:
+    """Measured FP64 FMA throughput of the device (GFLOP/s)."""
+    g = C.c_double()
+    _check(load().osam_fp64_peak(device, C.byref(g)))
+    return g.value

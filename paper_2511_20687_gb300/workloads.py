@@ -253,3 +253,19 @@ def wave1d(n_elem: int = 1000, dt: Optional[float] = None, subdomains: bool = Fa
 
 def random_field(n_nodes: int, scale: float, seed: int) -> np.ndarray:
     return scale * np.random.default_rng(seed).standard_normal((n_nodes, 3))
+
+
+def synthetic_rom_operators(n_free: int, n_sdof: int, r: int, r_s: int, seed: int,
+                            omega_range=(1e4, 1e5)) -> dict:
+    """Seeded stand-in operators of a quadratic ROM of the given sizes (random orthonormal bases,
+    K = -diag(omega^2) with omega in omega_range rad/s, small random H and B, c = 0).  Used where a run
+    needs ROM-sized work but no trained model (CPU baselines, full-size parity at a fixed iteration
+    count)."""
+    rng = np.random.default_rng(seed)
+    Phi, _ = np.linalg.qr(rng.standard_normal((n_free, r)))
+    Phi_S, _ = np.linalg.qr(rng.standard_normal((n_sdof, r_s)))
+    omega = rng.uniform(omega_range[0], omega_range[1], r)
+    K = -np.diag(omega ** 2)
+    H = 1e6 * rng.standard_normal((r, r * (r + 1) // 2)) / r
+    B = 1e8 * rng.standard_normal((r, r_s)) / r_s
+    return {"Phi": Phi, "Phi_S": Phi_S, "K": K, "H": H, "B": B, "c": np.zeros(r)}
