@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--snapshots", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fom-only", action="store_true",
+                    help="FOM-FOM coupling of the same geometry (no ROM, no training): profiling runs")
     return ap.parse_args()
 
 
@@ -255,9 +257,13 @@ def main():
     from paper_2511_20687_gb300 import osam
     from paper_2511_20687_gb300 import workloads as W
 
-    ops = train_rom(W, osam, args, local, log)
-    spec = hybrid_spec(W, args)
-    prob = osam.Problem(spec, rom_ops={1: ops}, device=local)
+    if args.fom_only:
+        spec = W.fom_opinf_hybrid(args.n, args.nz, rom=False)
+        prob = osam.Problem(spec, device=local)
+    else:
+        ops = train_rom(W, osam, args, local, log)
+        spec = hybrid_spec(W, args)
+        prob = osam.Problem(spec, rom_ops={1: ops}, device=local)
     log(f"scatter mode: {'atomic' if prob.scatter_mode() == osam.SCATTER_ATOMIC else 'gather'}")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     for _ in range(args.warmup):
@@ -295,29 +301,32 @@ def main():
     value = updates / (total_ms * 1e-3)
 
     # end to end through the public API with pinned host buffers
-    nA = prob.sizes(0)["n_nodes"]
-    hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
-    hq = [torch.empty(args.rank, dtype=torch.float64).pin_memory() for _ in range(3)]
-    prob.state(0, out=tuple(hu))
-    q = prob.reduced_state(1)
-    for k in range(3):
-        hq[k].copy_(torch.from_numpy(q[k]))
-    e2e_updates = 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        prob.set_state(0, hu[0], hu[1], hu[2])
-        prob.set_reduced_state(1, hq[0], hq[1], hq[2])
-        r = prob.step()
-        e2e_updates += r["element_updates"]
+    e2e = None
+    if args.e2e_steps > 0 and not args.fom_only:
+        nA = prob.sizes(0)["n_nodes"]
+        hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
+        hq = [torch.empty(args.rank, dtype=torch.float64).pin_memory() for _ in range(3)]
         prob.state(0, out=tuple(hu))
-        out_q = prob.reduced_state(1)
+        q = prob.reduced_state(1)
         for k in range(3):
-            hq[k].copy_(torch.from_numpy(out_q[k]))
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    io_bytes = 3 * nA * 3 * 8 + 3 * args.rank * 8
-    e2e = {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+            hq[k].copy_(torch.from_numpy(q[k]))
+        e2e_updates = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            prob.set_state(0, hu[0], hu[1], hu[2])
+            prob.set_reduced_state(1, hq[0], hq[1], hq[2])
+            r = prob.step()
+            e2e_updates += r["element_updates"]
+            prob.state(0, out=tuple(hu))
+            out_q = prob.reduced_state(1)
+            for k in range(3):
+                hq[k].copy_(torch.from_numpy(out_q[k]))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        io_bytes = 3 * nA * 3 * 8 + 3 * args.rank * 8
+        e2e = {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
+               "d2h_bytes_per_step": io_bytes}
 
     fp64_meas = osam.fp64_peak_gflops(local) / 1e3
     achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
@@ -330,7 +339,7 @@ def main():
                 "force_time_share": prof["force_ms"] / total_ms if world == 1 else None}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
         rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{steps} controller step(s) x 1 Schwarz iteration x 20 substeps of the 40x40x80 NH FOM "
@@ -340,8 +349,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} Neo-Hookean FOM + "
-                                       f"r={args.rank} quadratic OpInf ROM (fitted on {args.snapshots} snapshots)",
+                "config": {"workload": (f"fom_fom {args.n}x{args.n}x{args.nz} x2 Neo-Hookean FOMs" if args.fom_only else
+                                        f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} Neo-Hookean FOM + "
+                                        f"r={args.rank} quadratic OpInf ROM (fitted on {args.snapshots} snapshots)"),
                            "dt": 1e-6, "substeps_per_step": 20, "tol_rel": 1e-12, "max_iters": 64,
                            "fom_elements": spec.subdomains[0].n_elements, "parallelism": "replicas",
                            "l2": "flushed between steps (256 MiB write)",

@@ -191,7 +191,9 @@ int advance_fom(osam_ctx* ctx, int i) {
         double* Y = F.u[j & 1];
         ElemArgs ea = elem_args(F, X, 1, nn);
         if (fp32 && scatter == kAtomic) ea.f = f32_buffer(F);
+        const int pk = ctx->prof_begin();
         LK(launch_hex8_force(F.material, fp32, scatter, ea, ctx->stream));
+        ctx->prof_end(pk, F.g.ne());
         NodeArgs na = node_args(ctx, s);
         if (fp32 && scatter == kAtomic) na.fclear = f32_buffer(F);
         na.ucur = X;

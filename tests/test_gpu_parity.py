@@ -344,3 +344,15 @@ def test_adjoint_matches_oracle_and_fd(torch_cuda):
 
     fd = (J_of(sd.lam_e + hl * dl) - J_of(sd.lam_e - hl * dl)) / (2 * hl)
     assert abs(fd - got["grad_lambda"] @ dl) < 1e-6 * abs(fd)
+
+
+def test_profile_counters(torch_cuda):
+    spec = W.fom_fom_plain()
+    g = osam.Problem(spec)
+    g.profile(True)
+    r = g.step()
+    p = g.profile_read()
+    assert p["force_launches"] == r["iterations"] * spec.n_substeps * 2
+    assert p["force_elements"] == r["element_updates"]
+    assert p["force_ms"] > 0.0 and p["kernel_launches"] > p["force_launches"]
+    assert osam.fp64_peak_gflops(0) > 0.0
