@@ -668,7 +668,9 @@ static int autotune_scatter(osam_ctx* ctx) {
         CK(cudaEventSynchronize(ctx->ev1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-        if (ms < best_ms) { best_ms = ms; best_mode = mode; }
+        // the deterministic gather scatter is kept unless atomics are clearly (> 5%) faster
+        if (mode == kGather) { best_ms = ms; best_mode = kGather; }
+        else if (ms < 0.95f * best_ms) { best_ms = ms; best_mode = kAtomic; }
     }
     // the atomic buffers must be clean after the trial
     CK(cudaMemsetAsync(s.fom.f, 0, sizeof(double) * 3 * nn, ctx->stream));
