@@ -193,6 +193,23 @@ OSAM_API int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material,
                         const double* lambda_e, const double* mu_e, const double* u, const double* ybar,
                         double* ubar, double* lambda_bar, double* mu_bar, void* stream);
 
+/* Internal force for callers that may not allocate device memory (the paper has no counterpart):
+ * an application that freezes its GPU memory budget after start-up and forbids cudaMalloc / cudaFree
+ * (they can synchronise the device and fragment a pool the application manages), code running inside
+ * another allocator's hooks, or a thread that must never block on cudaFree's implicit
+ * synchronisation.  Same inputs, layout and result as osam_hex8_force (device pointers, [nodes][3]),
+ * computed with the deterministic element-buffer scatter; the buffer is a static device array of
+ * 24 * OSAM_NOALLOC_MAX_ELEMENTS doubles (6 MiB) that every GPU loading the library holds until the
+ * process exits.  Calls no allocator.  More than OSAM_NOALLOC_MAX_ELEMENTS elements -> OSAM_EINVAL
+ * (message in osam_last_error(NULL)).  The first call on a device, with that device current, looks up
+ * the array's device address (once per device); make that first call before any stream capture.
+ * Every call shares the one buffer and overwrites it entirely (nothing in it needs to start at zero):
+ * calls whose kernels overlap on the GPU (different streams, or different host threads on one device)
+ * race and must be serialised by the caller.  Asynchronous on `stream`. */
+#define OSAM_NOALLOC_MAX_ELEMENTS 32768
+OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int material, double lambda, double mu,
+                            const double* lambda_e, const double* mu_e, const double* u, double* f, void* stream);
+
 /* ------------------------------------------------------------------------------------------------
  * Offline OpInf (Sec. 3 and Sec. 4.2.1, Eq. opinf_schwarz_inference) on the GPU:
  *   POD of the free-dof displacement snapshots U (thin SVD by the method of snapshots, Eq.

@@ -1,0 +1,118 @@
+// osam_hex8_force_noalloc: the internal force with the deterministic element-buffer scatter, for
+// callers that may not allocate device memory.  The element buffer lives in a fixed file-scope
+// device array instead of memory obtained from cudaMalloc.
+//
+// Who needs this: a host application that freezes its GPU memory budget after start-up and forbids
+// further cudaMalloc / cudaFree (those calls can synchronise the device and fragment a pool the
+// application manages itself), code that runs inside another allocator's hooks, and code on a thread
+// that must never block on the implicit synchronisation cudaFree performs.  Such callers still pass
+// their own input and output arrays; the only working memory used here is the static array below.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "osam.h"
+#include "osam_internal.h"
+
+namespace {
+
+// 24 element contributions per element, OSAM_NOALLOC_MAX_ELEMENTS elements: 6 MiB of FP64 held by
+// every GPU that loads the library, until the process exits.
+__device__ __align__(256) double g_noalloc_fe[24LL * OSAM_NOALLOC_MAX_ELEMENTS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_fe_addr[kMaxDevices] = {nullptr};
+
+// nodal force, interleaved output f[3 n + c], gathered from the element buffer in a fixed order
+__global__ void k_gather_aos(int nx, int ny, int nz, const double* __restrict__ fe, double* __restrict__ f) {
+    const int nn = (nx + 1) * (ny + 1) * (nz + 1);
+    const int ne = nx * ny * nz;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * nn) return;
+    const int n = t / 3, c = t % 3;
+    const int i = n % (nx + 1);
+    const int q = n / (nx + 1);
+    const int j = q % (ny + 1), k = q / (ny + 1);
+    double s = 0.0;
+    for (int az = 0; az < 2; ++az) {
+        const int ke = k - az;
+        if (ke < 0 || ke >= nz) continue;
+        for (int ay = 0; ay < 2; ++ay) {
+            const int je = j - ay;
+            if (je < 0 || je >= ny) continue;
+            for (int ax = 0; ax < 2; ++ax) {
+                const int ie = i - ax;
+                if (ie < 0 || ie >= nx) continue;
+                const int e = ie + nx * (je + ny * ke);
+                s += fe[(long long)((ax + 2 * ay + 4 * az) * 3 + c) * ne + e];
+            }
+        }
+    }
+    f[t] = s;
+}
+
+// device address of the static element buffer on the current device, looked up once per device
+int fe_address(double** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        osam::set_thread_error("osam_hex8_force_noalloc: no current CUDA device");
+        return OSAM_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_fe_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_fe);
+        if (e != cudaSuccess || !p) {
+            osam::set_thread_error(std::string("osam_hex8_force_noalloc: cudaGetSymbolAddress failed: ") +
+                                   cudaGetErrorString(e));
+            return OSAM_ECUDA;
+        }
+        g_fe_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_fe_addr[dev];
+    return OSAM_OK;
+}
+
+}  // namespace
+
+extern "C" OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int material, double lambda,
+                                                double mu, const double* lambda_e, const double* mu_e, const double* u,
+                                                double* f, void* stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !f ||
+        (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN)) {
+        osam::set_thread_error("osam_hex8_force_noalloc: invalid argument");
+        return OSAM_EINVAL;
+    }
+    const long long ne = (long long)nx * ny * nz;
+    if (ne > OSAM_NOALLOC_MAX_ELEMENTS) {
+        osam::set_thread_error("osam_hex8_force_noalloc: " + std::to_string(ne) +
+                               " elements exceed the static buffer limit of " +
+                               std::to_string(OSAM_NOALLOC_MAX_ELEMENTS));
+        return OSAM_EINVAL;
+    }
+    double* fe = nullptr;
+    if (int rc = fe_address(&fe)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    osam::ElemArgs a{};
+    a.nx = nx; a.ny = ny; a.nz = nz; a.ne = (int)ne;
+    a.invh = 1.0 / h;
+    a.w8 = h * h / 8.0;
+    a.lam = lambda; a.mu = mu;
+    a.lam_e = lambda_e; a.mu_e = mu_e;
+    a.u = u; a.usn = 3; a.usc = 1;
+    a.fe = fe;
+    // every element writes all 24 of its entries, so the buffer needs no clearing between calls
+    cudaError_t e = osam::launch_hex8_force(material, false, osam::kGather, a, s);
+    if (e == cudaSuccess) {
+        const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+        k_gather_aos<<<(int)((3 * nn + 255) / 256), 256, 0, s>>>(nx, ny, nz, fe, f);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        osam::set_thread_error(std::string("osam_hex8_force_noalloc: ") + cudaGetErrorString(e));
+        return OSAM_ECUDA;
+    }
+    return OSAM_OK;
+}

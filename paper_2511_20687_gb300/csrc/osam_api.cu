@@ -461,6 +461,10 @@ int setup_rom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
 
 }  // namespace
 
+namespace osam {
+void set_thread_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace osam
+
 extern "C" {
 
 const char* osam_last_error(const osam_ctx* ctx) {

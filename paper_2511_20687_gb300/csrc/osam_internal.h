@@ -171,4 +171,7 @@ cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double*
 
 int grid_for(long long n, int block);
 
+// message returned by osam_last_error(NULL) on the calling thread
+void set_thread_error(const std::string& msg);
+
 }  // namespace osam

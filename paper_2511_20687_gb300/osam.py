@@ -25,7 +25,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
             "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
-            "osam_profile", "osam_profile_read", "osam_fp64_peak"]
+            "osam_profile", "osam_profile_read", "osam_fp64_peak", "osam_hex8_force_noalloc"]
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
@@ -121,6 +121,8 @@ def load():
     L.osam_profile_read.argtypes = [_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                     C.POINTER(C.c_longlong)]
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
+    L.osam_hex8_force_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
+                                          _vp, _vp, _vp, _vp, _vp]
     _lib = L
     return L
 
