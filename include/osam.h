@@ -154,6 +154,36 @@ OSAM_API int osam_criterion(osam_ctx* ctx, double* cnum, double* cden);
  * cnum < tol_abs^2 or cnum < tol_rel^2 cden.  rep may be NULL. */
 OSAM_API int schwarz_step(osam_ctx* ctx, osam_step_report* rep);
 
+/* ------------------------------------------------------------------------------------------------
+ * Batches: one context advancing n_instances independent instances of the same coupled problem
+ * (same subdomain kinds and Neo-Hookean / linear-elastic choice per subdomain, same couplings, dt,
+ * n_substeps, tolerances, max_iters and precision; meshes, materials, initial data and ROM operators
+ * may differ per instance).  Every per-step kernel advances all instances in one launch; an instance
+ * that meets the criterion stops iterating (its state is frozen) while the others continue, so each
+ * instance follows exactly its own single-instance iteration sequence.  schwarz_init is a batch of
+ * one.  The instance index of the functions below is 0-based; functions without it act on instance 0.
+ * ------------------------------------------------------------------------------------------------ */
+OSAM_API int osam_batch_init(int n_instances, const osam_problem_desc* descs, osam_ctx** out);
+/* One controller step of every instance; per_instance[n_instances] (or NULL) receives each instance's
+ * report, total (or NULL) the aggregate (iterations = max, element_updates = sum, status = worst). */
+OSAM_API int osam_batch_step(osam_ctx* ctx, osam_step_report* per_instance, osam_step_report* total);
+OSAM_API int osam_num_instances(osam_ctx* ctx);
+OSAM_API int osam_instance_get_state(osam_ctx* ctx, int inst, int sub, double* u, double* v, double* a);
+OSAM_API int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, const double* v, const double* a);
+OSAM_API int osam_instance_get_reduced_state(osam_ctx* ctx, int inst, int sub, double* q, double* qd, double* qdd);
+OSAM_API int osam_instance_set_reduced_state(osam_ctx* ctx, int inst, int sub, const double* q, const double* qd,
+                                    const double* qdd);
+OSAM_API int osam_instance_sizes(osam_ctx* ctx, int inst, int sub, int* n_nodes, int* n_elements, int* n_free,
+                        int* n_schwarz_nodes);
+/* Controller-step execution: enable = 1 (default) records the whole step once as a CUDA graph -- save,
+ * zero-order hold, then a while node whose body is one Schwarz iteration of every instance and whose
+ * condition is set on the device by the convergence kernel -- and replays it with one host
+ * synchronisation per step; enable = 0 drives the iterations from the host (one synchronisation per
+ * iteration).  Kernel-level profiling (osam_profile) always uses the host-driven path. */
+OSAM_API int osam_set_graph(osam_ctx* ctx, int enable);
+/* Autotuned launch configuration: scatter mode and element block size of the force kernel. */
+OSAM_API int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block);
+
 /* Copy a subdomain's nodal state out / in ([nodes][3] each, any pointer may be NULL).  For a ROM the
  * output is the reconstructed field: Phi q on free dofs, boundary data on Schwarz dofs, 0 on clamped
  * dofs; osam_set_state on a ROM projects u, v onto the basis (q = Phi^T u) and recomputes qdd. */

@@ -279,16 +279,6 @@ __global__ void k_adjoint_post(int nn, double dt, const uint8_t* clamp, const do
     vb[t] = fma(dt, u, v);
 }
 
-__global__ void k_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * nn) return;
-    const int c = t / nn, n = t % nn;
-    if (clamp[n] & (1 << c)) {
-        u[t] = 0.0;
-        if (v) v[t] = 0.0;
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb, double* ab,
@@ -300,11 +290,6 @@ cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const do
 cudaError_t launch_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
                                 double* ab, cudaStream_t s) {
     k_adjoint_post<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, tmp, ub, vb, ab);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, cudaStream_t s) {
-    k_zero_clamped<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, clamp, u, v);
     return cudaGetLastError();
 }
 

@@ -1,191 +1,20 @@
-// FOM subdomain kernels: hex8 internal force (linear elastic / Neo-Hookean, 2x2x2 Gauss),
-// element-to-node scatter, explicit central-difference update with Dirichlet data, trace of the
-// solution at the Schwarz nodes of a neighbour (pointwise projector Pi), and the Schwarz
-// convergence sums.
-//
-// Internal-force formulation (uniform cubic elements of edge h).  With unit-cube coordinates s,
-// grad_X N = grad_s N / h, detJ * w = h^3/8 at each of the 8 Gauss points s = (1 -+ 1/sqrt3)/2, so
-//   H = grad u = sum_a (u_a / h) (x) grad_s N_a,     f_a = (h^2/8) sum_gp P(H) grad_s N_a.
-// Trilinear shape functions factor per axis, so both sums are evaluated by sum factorisation:
-// edge differences along one axis followed by linear interpolation along the other two (and the
-// transpose for the force), 16 FP64 operations per (component, direction) instead of 8 x 8.
-// The Neo-Hookean stress of Appendix A.3, P = F S with
-//   S = 1/2 kappa (det C - 1) C^-1 + mu (det C)^-1/3 (I - 1/3 tr C C^-1),
-// is evaluated through F C^-1 = F^-T = cof(F) / J, i.e.
-//   P = [1/2 kappa (J^2 - 1) - 1/3 mu J^-2/3 tr C] / J * cof(F) + mu J^-2/3 F,
-// with J^-2/3 = rcbrt(J^2) and 1/J = J * (J^-2/3)^3 (no division).
+// FOM set-up and I/O kernels, and the element-level internal-force kernel of the C ABI
+// (osam_hex8_force / osam_hex8_force_noalloc).  The per-step kernels of the controller, which work
+// on every instance of a batch at once, are in step_kernels.cu; both use hex8_math.cuh.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
+#include "hex8_math.cuh"
 #include "osam_internal.h"
 
 namespace osam {
 
 namespace {
 
-constexpr double kG0 = 0.21132486540518711775;   // (1 - 1/sqrt(3)) / 2
-constexpr double kG1 = 0.78867513459481288225;   // (1 + 1/sqrt(3)) / 2
-constexpr double kGd = 0.57735026918962576451;   // kG1 - kG0 = 1/sqrt(3)
+using namespace hex8;
 
-__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double rcbrtT(double x) { return rcbrt(x); }
-__device__ __forceinline__ float rcbrtT(float x) { return rcbrtf(x); }
-
-// nodal values D[b][e] on a unit square -> values at the 2x2 Gauss points out[q][r]
-template <typename T>
-__device__ __forceinline__ void lerp2(const T D[2][2], T out[2][2]) {
-    T E[2][2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        T d = D[1][e] - D[0][e];
-        E[0][e] = fmaT(T(kG0), d, D[0][e]);
-        E[1][e] = fmaT(T(kG1), d, D[0][e]);
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        T d = E[q][1] - E[q][0];
-        out[q][0] = fmaT(T(kG0), d, E[q][0]);
-        out[q][1] = fmaT(T(kG1), d, E[q][0]);
-    }
-}
-
-// transpose of lerp2: Gauss-point values S[q][r] -> nodal out[b][e] = sum l_b(g_q) l_e(g_r) S[q][r]
-template <typename T>
-__device__ __forceinline__ void lerp2T(const T S[2][2], T out[2][2]) {
-    T V[2][2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        T s = S[q][0] + S[q][1];
-        V[q][0] = fmaT(T(kGd), S[q][0], T(kG0) * s);  // g1 S0 + g0 S1
-        V[q][1] = s - V[q][0];                        // g0 S0 + g1 S1
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        T s = V[0][e] + V[1][e];
-        out[0][e] = fmaT(T(kGd), V[0][e], T(kG0) * s);
-        out[1][e] = s - out[0][e];
-    }
-}
-
-// Appendix A.1: P = lambda tr(eps) I + 2 mu eps (lam, mu pre-scaled by h^2/8)
-template <typename T>
-__device__ __forceinline__ void stress_le(const T H[3][3], T lam, T mu, T P[3][3]) {
-    T lt = lam * (H[0][0] + H[1][1] + H[2][2]);
-    T mu2 = mu + mu;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) P[c][c] = fmaT(mu2, H[c][c], lt);
-    P[0][1] = P[1][0] = mu * (H[0][1] + H[1][0]);
-    P[0][2] = P[2][0] = mu * (H[0][2] + H[2][0]);
-    P[1][2] = P[2][1] = mu * (H[1][2] + H[2][1]);
-}
-
-// Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8)
-template <typename T>
-__device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, T P[3][3]) {
-    const T F00 = T(1) + H[0][0], F11 = T(1) + H[1][1], F22 = T(1) + H[2][2];
-    const T F01 = H[0][1], F02 = H[0][2], F10 = H[1][0], F12 = H[1][2], F20 = H[2][0], F21 = H[2][1];
-    T c00 = fmaT(F11, F22, -F12 * F21);
-    T c01 = fmaT(F12, F20, -F10 * F22);
-    T c02 = fmaT(F10, F21, -F11 * F20);
-    T c10 = fmaT(F02, F21, -F01 * F22);
-    T c11 = fmaT(F00, F22, -F02 * F20);
-    T c12 = fmaT(F01, F20, -F00 * F21);
-    T c20 = fmaT(F01, F12, -F02 * F11);
-    T c21 = fmaT(F02, F10, -F00 * F12);
-    T c22 = fmaT(F00, F11, -F01 * F10);
-    T J = fmaT(F00, c00, fmaT(F01, c01, F02 * c02));
-    T trC = F00 * F00;
-    trC = fmaT(F01, F01, trC); trC = fmaT(F02, F02, trC);
-    trC = fmaT(F10, F10, trC); trC = fmaT(F11, F11, trC); trC = fmaT(F12, F12, trC);
-    trC = fmaT(F20, F20, trC); trC = fmaT(F21, F21, trC); trC = fmaT(F22, F22, trC);
-    T J2 = J * J;
-    T r3 = rcbrtT(J2);                 // J^-2/3
-    T invJ = J * (r3 * r3 * r3);       // J * J^-2 = 1/J
-    T alpha = mu * r3;
-    T beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
-    P[0][0] = fmaT(alpha, F00, beta * c00);
-    P[0][1] = fmaT(alpha, F01, beta * c01);
-    P[0][2] = fmaT(alpha, F02, beta * c02);
-    P[1][0] = fmaT(alpha, F10, beta * c10);
-    P[1][1] = fmaT(alpha, F11, beta * c11);
-    P[1][2] = fmaT(alpha, F12, beta * c12);
-    P[2][0] = fmaT(alpha, F20, beta * c20);
-    P[2][1] = fmaT(alpha, F21, beta * c21);
-    P[2][2] = fmaT(alpha, F22, beta * c22);
-}
-
-// Element force from scaled edge differences.
-//   Dx[c][ay][az] = (u_c(1,ay,az) - u_c(0,ay,az)) / h   (and Dy[c][ax][az], Dz[c][ax][ay])
-// Output F[c][corner], corner = ax + 2 ay + 4 az.
-template <int MAT, typename T>
-__device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3][2][2], const T Dz[3][2][2],
-                                              T m1, T m2, T m3, T F[3][8]) {
-    T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lerp2<T>(Dx[c], Gx[c]);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
-        lerp2<T>(Dy[c], Gy[c]);   // Gy[c][p][r]
-        lerp2<T>(Dz[c], Gz[c]);   // Gz[c][p][q]
-    }
-    T Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                T Hm[3][3], P[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Hm[c][0] = Gx[c][q][r];
-                    Hm[c][1] = Gy[c][p][r];
-                    Hm[c][2] = Gz[c][p][q];
-                }
-                if (MAT == OSAM_NEO_HOOKEAN) stress_nh<T>(Hm, m1, m2, m3, P);
-                else stress_le<T>(Hm, m1, m2, P);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (p == 0) Sx[c][q][r] = P[c][0]; else Sx[c][q][r] += P[c][0];
-                    if (q == 0) Sy[c][p][r] = P[c][1]; else Sy[c][p][r] += P[c][1];
-                    if (r == 0) Sz[c][p][q] = P[c][2]; else Sz[c][p][q] += P[c][2];
-                }
-            }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        T Tm[2][2];
-        lerp2T<T>(Sx[c], Tm);  // Tm[ay][az]
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[c][1 + 2 * ay + 4 * az] = Tm[ay][az];
-                F[c][2 * ay + 4 * az] = -Tm[ay][az];
-            }
-        lerp2T<T>(Sy[c], Tm);  // Tm[ax][az]
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[c][ax + 2 + 4 * az] += Tm[ax][az];
-                F[c][ax + 4 * az] -= Tm[ax][az];
-            }
-        lerp2T<T>(Sz[c], Tm);  // Tm[ax][ay]
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) {
-                F[c][ax + 2 * ay + 4] += Tm[ax][ay];
-                F[c][ax + 2 * ay] -= Tm[ax][ay];
-            }
-    }
-}
-
-__device__ __forceinline__ void atomic_add(double* p, double v) { atomicAdd(p, v); }
-__device__ __forceinline__ void atomic_add(float* p, float v) { atomicAdd(p, v); }
-
-// one thread per element
+// one thread per element of a single mesh, strided input / output (see ElemArgs)
 template <int MAT, typename T, int MODE>
 __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -199,21 +28,15 @@ __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
     int node[8];
 #pragma unroll
     for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
-
-    double lam = a.lam_e ? a.lam_e[e] : a.lam;
-    double mu = a.mu_e ? a.mu_e[e] : a.mu;
+    const double lam = a.lam_e ? a.lam_e[e] : a.lam;
+    const double mu = a.mu_e ? a.mu_e[e] : a.mu;
     T m1, m2, m3;
     if (MAT == OSAM_NEO_HOOKEAN) {
         const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = T(0.5 * kappa * a.w8);
-        m2 = T(mu * a.w8);
-        m3 = T(mu * a.w8 / 3.0);
+        m1 = T(0.5 * kappa * a.w8); m2 = T(mu * a.w8); m3 = T(mu * a.w8 / 3.0);
     } else {
-        m1 = T(lam * a.w8);
-        m2 = T(mu * a.w8);
-        m3 = T(0);
+        m1 = T(lam * a.w8); m2 = T(mu * a.w8); m3 = T(0);
     }
-
     T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -221,30 +44,7 @@ __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
         const double* uc = a.u + (long long)c * a.usc;
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) U[c8] = uc[(long long)node[c8] * a.usn];
-        if constexpr (sizeof(T) == 8) {
-            // FP64: scale the 8 nodal values, then difference
-#pragma unroll
-            for (int c8 = 0; c8 < 8; ++c8) U[c8] *= a.invh;
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    Dx[c][p][q] = T(U[1 + 2 * p + 4 * q] - U[2 * p + 4 * q]);
-                    Dy[c][p][q] = T(U[p + 2 + 4 * q] - U[p + 4 * q]);
-                    Dz[c][p][q] = T(U[p + 2 * q + 4] - U[p + 2 * q]);
-                }
-        } else {
-            // FP32 force: differences in FP64 (they cancel), the rest in FP32
-            const float ih = float(a.invh);
-#pragma unroll
-            for (int p = 0; p < 2; ++p)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    Dx[c][p][q] = T(U[1 + 2 * p + 4 * q] - U[2 * p + 4 * q]) * ih;
-                    Dy[c][p][q] = T(U[p + 2 + 4 * q] - U[p + 4 * q]) * ih;
-                    Dz[c][p][q] = T(U[p + 2 * q + 4] - U[p + 2 * q]) * ih;
-                }
-        }
+        edge_differences<T>(U, a.invh, Dx[c], Dy[c], Dz[c]);
     }
     T F[3][8];
     element_force<MAT, T>(Dx, Dy, Dz, m1, m2, m3, F);
@@ -263,87 +63,7 @@ __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
     }
 }
 
-// nodal force of node (i,j,k), component c, from the element buffer (fixed order: deterministic)
-template <typename TF>
-__device__ __forceinline__ double gather_force(const TF* fe, int nx, int ny, int nz, int ne, int i, int j, int k,
-                                               int c) {
-    double s = 0.0;
-#pragma unroll
-    for (int az = 0; az < 2; ++az) {
-        const int ke = k - az;
-        if (ke < 0 || ke >= nz) continue;
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay) {
-            const int je = j - ay;
-            if (je < 0 || je >= ny) continue;
-#pragma unroll
-            for (int ax = 0; ax < 2; ++ax) {
-                const int ie = i - ax;
-                if (ie < 0 || ie >= nx) continue;
-                const int e = ie + nx * (je + ny * ke);
-                const int corner = ax + 2 * ay + 4 * az;
-                s += double(fe[(long long)(corner * 3 + c) * ne + e]);
-            }
-        }
-    }
-    return s;
-}
-
-// Corrector of substep j and predictor of substep j+1 (explicit Newmark beta=0, gamma=1/2):
-//   free dofs:   a' = -f/m;  v += dt/2 (a + a');  a = a';  u^{j+2} = u^{j+1} + dt v + dt^2/2 a
-//   clamped:     u = v = a = 0
-//   Schwarz:     v, a from history slot j+1; u^{j+2} from history slot j+2
-template <typename TF, int MODE>
-__global__ void __launch_bounds__(256) k_node_update(const NodeArgs a) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= a.nn) return;
-    const int i = n % (a.nx + 1);
-    const int t = n / (a.nx + 1);
-    const int j = t % (a.ny + 1);
-    const int k = t / (a.ny + 1);
-    const uint8_t cm = a.clamp[n];
-    const int row = a.srow[n];
-    const double dt = a.dt, hdt = 0.5 * a.dt, hdt2 = 0.5 * a.dt * a.dt;
-    const double minv = a.minv[n];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long d = (long long)c * a.nn + n;
-        double un;
-        if (cm & (1 << c)) {
-            a.v[d] = 0.0;
-            a.a[d] = 0.0;
-            un = 0.0;
-        } else if (row >= 0) {
-            if (!a.predict_only) {
-                a.v[d] = a.h1[(long long)(3 + c) * a.ns + row];
-                a.a[d] = a.h1[(long long)(6 + c) * a.ns + row];
-            }
-            un = a.h2 ? a.h2[(long long)c * a.ns + row] : 0.0;
-        } else {
-            double vn = a.v[d], an = a.a[d];
-            if (!a.predict_only) {
-                double f;
-                if (MODE == kGather) {
-                    f = gather_force<TF>(static_cast<const TF*>(a.force), a.nx, a.ny, a.nz, a.ne, i, j, k, c);
-                } else {
-                    TF* fa = static_cast<TF*>(a.fclear);
-                    f = double(fa[d]);
-                    fa[d] = TF(0);
-                }
-                const double anew = -f * minv;
-                vn = fma(hdt, an + anew, vn);
-                an = anew;
-                a.v[d] = vn;
-                a.a[d] = an;
-            }
-            un = fma(hdt2, an, fma(dt, vn, a.ucur[d]));
-        }
-        if (!a.last) a.unext[d] = un;
-        // atomic mode: constrained dofs also received element contributions; reset them for the next substep
-        if (MODE == kAtomic && !a.predict_only && ((cm & (1 << c)) || row >= 0)) static_cast<TF*>(a.fclear)[d] = TF(0);
-    }
-}
-
+// inverse row-sum lumped mass of a uniform cubic mesh: m_n = rho h^3 / 8 x (adjacent elements)
 __global__ void k_lumped_minv(int nx, int ny, int nz, double m_e8, double* minv) {
     const int nn = (nx + 1) * (ny + 1) * (nz + 1);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,131 +76,9 @@ __global__ void k_lumped_minv(int nx, int ny, int nz, double m_e8, double* minv)
     minv[n] = 1.0 / (m_e8 * double(cx * cy * cz));
 }
 
-// trace of a FOM source at the coupling rows: rec[slot][f][c][i] = sum_b w_b field_f,c[dnode_b]
-__global__ void k_trace(const int nrow, const int* __restrict__ dnode, const double* __restrict__ dw,
-                        const double* u, const double* v, const double* acc, int nn, double* rec_slot) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * nrow) return;
-    const int i = t / 3, c = t % 3;
-    double su = 0.0, sv = 0.0, sa = 0.0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const double w = dw[8 * i + b];
-        const long long d = (long long)c * nn + dnode[8 * i + b];
-        su = fma(w, u[d], su);
-        sv = fma(w, v[d], sv);
-        sa = fma(w, acc[d], sa);
-    }
-    rec_slot[(long long)(0 * 3 + c) * nrow + i] = su;
-    rec_slot[(long long)(1 * 3 + c) * nrow + i] = sv;
-    rec_slot[(long long)(2 * 3 + c) * nrow + i] = sa;
-}
-
-__device__ __forceinline__ long long hist_index(bool dst_rom, int slot, int f, int c, int row, int nd) {
-    // FOM history [slot][f][c][ns]; ROM history [slot][f][3*row + c]
-    return dst_rom ? ((long long)(slot * 3 + f) * nd + 3 * row + c) : ((long long)((slot * 3 + f) * 3 + c) * nd + row);
-}
-
-__global__ void k_zoh_fom(const int nrow, const int* __restrict__ row, const int* __restrict__ dnode,
-                          const double* __restrict__ dw, const double* u, const double* v, const double* acc, int nn,
-                          bool dst_rom, double* hist, int nd, int nslots) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * nrow) return;
-    const int i = t / 3, c = t % 3;
-    double s[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const double w = dw[8 * i + b];
-        const long long d = (long long)c * nn + dnode[8 * i + b];
-        s[0] = fma(w, u[d], s[0]);
-        s[1] = fma(w, v[d], s[1]);
-        s[2] = fma(w, acc[d], s[2]);
-    }
-    for (int slot = 0; slot < nslots; ++slot)
-#pragma unroll
-        for (int f = 0; f < 3; ++f) hist[hist_index(dst_rom, slot, f, c, row[i], nd)] = s[f];
-}
-
-__global__ void k_publish_fom(const int nrow, const int* __restrict__ row, const double* __restrict__ rec,
-                              bool dst_rom, double* hist, int nd, int nsub) {
-    const long long total = (long long)nsub * 9 * nrow;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const int i = t % nrow;
-    const long long q = t / nrow;
-    const int fc = q % 9;
-    const int slot = 1 + int(q / 9);
-    const int f = fc / 3, c = fc % 3;
-    hist[hist_index(dst_rom, slot, f, c, row[i], nd)] = rec[((long long)slot * 9 + fc) * nrow + i];
-}
-
-template <int BLOCK>
-__device__ __forceinline__ void block_sum2(double& x, double& y) {
-    __shared__ double sx[BLOCK / 32], sy[BLOCK / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x += __shfl_down_sync(0xffffffffu, x, o);
-        y += __shfl_down_sync(0xffffffffu, y, o);
-    }
-    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-    if (l == 0) { sx[w] = x; sy[w] = y; }
-    __syncthreads();
-    if (w == 0) {
-        x = l < BLOCK / 32 ? sx[l] : 0.0;
-        y = l < BLOCK / 32 ? sy[l] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, o);
-            y += __shfl_down_sync(0xffffffffu, y, o);
-        }
-    }
-}
-
-// criterion sums over free dofs (fixed grid: deterministic) and remember the iterate
-__global__ void __launch_bounds__(256) k_norms_fom(int nn, double dt, const uint8_t* clamp, const int* srow,
-                                                   const double* u, const double* v, double* pu, double* pv,
-                                                   double* partial) {
-    double num = 0.0, den = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < nn; n += gridDim.x * blockDim.x) {
-        const uint8_t cm = clamp[n];
-        const bool sch = srow[n] >= 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long long d = (long long)c * nn + n;
-            const double un = u[d], vn = v[d];
-            if (!(cm & (1 << c)) && !sch) {
-                const double x = (un - pu[d]) + dt * (vn - pv[d]);
-                const double y = fma(dt, vn, un);
-                num = fma(x, x, num);
-                den = fma(y, y, den);
-            }
-            pu[d] = un;
-            pv[d] = vn;
-        }
-    }
-    block_sum2<256>(num, den);
-    if (threadIdx.x == 0) {
-        partial[2 * blockIdx.x] = num;
-        partial[2 * blockIdx.x + 1] = den;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_norms_final(const double* partial, int nparts, double* result) {
-    double num = 0.0, den = 0.0;
-    for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
-        num += partial[2 * p];
-        den += partial[2 * p + 1];
-    }
-    block_sum2<256>(num, den);
-    if (threadIdx.x == 0) {
-        result[0] = num;
-        result[1] = den;
-        result[2] = (isfinite(num) && isfinite(den)) ? 0.0 : 1.0;
-    }
-}
-
 // donor element and trilinear weights of each destination Schwarz node in a structured source box:
-// lowest-index element containing the point, local coordinates within 1e-9 of +-1 snapped to +-1
+// lowest-index element containing the point, local coordinates within 1e-9 of +-1 snapped to +-1.
+// dnode receives node indices local to the source mesh.
 __global__ void k_donor(Grid src, Grid dst, const int* dst_nodes, int nrow, int* dnode, double* dw, int* err) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nrow) return;
@@ -516,37 +114,29 @@ __global__ void k_donor(Grid src, Grid dst, const int* dst_nodes, int nrow, int*
     }
 }
 
-// f[c][n] = sum of the element contributions of node n (fixed order), FP64 element buffer
-__global__ void k_gather_force(int nx, int ny, int nz, int ne, const double* fe, double* f) {
-    const int nn = (nx + 1) * (ny + 1) * (nz + 1);
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * nn) return;
-    const int c = t / nn, n = t % nn;
-    const int i = n % (nx + 1);
-    const int q = n / (nx + 1);
-    f[t] = gather_force<double>(fe, nx, ny, nz, ne, i, q % (ny + 1), q / (ny + 1), c);
-}
-
-__global__ void k_aos_to_soa(const double* aos, double* soa, int nn) {
+// interleaved [nn][3] <-> component-strided soa[c * stride + n]
+__global__ void k_aos_to_soa(const double* aos, double* soa, int nn, long long stride) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
     const int n = t / 3, c = t % 3;
-    soa[(long long)c * nn + n] = aos[t];
+    soa[(long long)c * stride + n] = aos[t];
 }
 
-__global__ void k_soa_to_aos(const double* soa, double* aos, int nn) {
+__global__ void k_soa_to_aos(const double* soa, double* aos, int nn, long long stride) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
     const int n = t / 3, c = t % 3;
-    aos[t] = soa[(long long)c * nn + n];
+    aos[t] = soa[(long long)c * stride + n];
 }
 
-// a = -f / m on every non-clamped dof (initial acceleration), 0 on clamped dofs
-__global__ void k_accel_from_force(int nn, const uint8_t* clamp, const double* minv, const double* f, double* acc) {
+__global__ void k_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, long long stride) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
     const int c = t / nn, n = t % nn;
-    acc[t] = (clamp[n] & (1 << c)) ? 0.0 : -f[t] * minv[n];
+    if (clamp[n] & (1 << c)) {
+        u[(long long)c * stride + n] = 0.0;
+        if (v) v[(long long)c * stride + n] = 0.0;
+    }
 }
 
 }  // namespace
@@ -568,83 +158,31 @@ cudaError_t launch_hex8_force(int material, bool fp32, int scatter, const ElemAr
     return cudaGetLastError();
 }
 
-cudaError_t launch_node_update(bool fp32, int scatter, const NodeArgs& a, cudaStream_t s) {
-    const int g = grid_for(a.nn, 256);
-    if (fp32) {
-        if (scatter == kAtomic) k_node_update<float, kAtomic><<<g, 256, 0, s>>>(a);
-        else k_node_update<float, kGather><<<g, 256, 0, s>>>(a);
-    } else {
-        if (scatter == kAtomic) k_node_update<double, kAtomic><<<g, 256, 0, s>>>(a);
-        else k_node_update<double, kGather><<<g, 256, 0, s>>>(a);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s) {
     const double m_e8 = rho * g.h * g.h * g.h / 8.0;
     k_lumped_minv<<<grid_for(g.nn(), 256), 256, 0, s>>>(g.nx, g.ny, g.nz, m_e8, minv);
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace(const CplDev& c, const double* u, const double* v, const double* a, int nn, int slot,
-                         int nsub, cudaStream_t s) {
-    (void)nsub;
-    if (c.nrow == 0) return cudaSuccess;
-    k_trace<<<grid_for(3LL * c.nrow, 128), 128, 0, s>>>(c.nrow, c.dnode, c.dw, u, v, a, nn,
-                                                         c.rec + (long long)slot * 9 * c.nrow);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_zoh_from_fom(const CplDev& c, const double* u, const double* v, const double* a, int nn,
-                                bool dst_rom, double* dst_hist, int nd, int nsub, cudaStream_t s) {
-    if (c.nrow == 0) return cudaSuccess;
-    k_zoh_fom<<<grid_for(3LL * c.nrow, 128), 128, 0, s>>>(c.nrow, c.row, c.dnode, c.dw, u, v, a, nn, dst_rom,
-                                                           dst_hist, nd, nsub + 1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_publish_fom(const CplDev& c, bool dst_rom, double* dst_hist, int nd, int nsub, cudaStream_t s) {
-    if (c.nrow == 0 || nsub == 0) return cudaSuccess;
-    const long long total = (long long)nsub * 9 * c.nrow;
-    k_publish_fom<<<grid_for(total, 256), 256, 0, s>>>(c.nrow, c.row, c.rec, dst_rom, dst_hist, nd, nsub);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_norms_fom(const FomDev& f, double dt, double* partial, cudaStream_t s) {
-    k_norms_fom<<<f.norm_blocks, 256, 0, s>>>(f.g.nn(), dt, f.clamp, f.srow, f.u[0], f.v, f.pu, f.pv, partial);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_norms_final(const double* partial, int nparts, double* result, cudaStream_t s) {
-    k_norms_final<<<1, 256, 0, s>>>(partial, nparts, result);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_donor(const Grid& src, const Grid& dst, const uint8_t*, const int* dst_nodes, int nrow, int* dnode,
-                         double* dw, int* err, cudaStream_t s) {
+cudaError_t launch_donor(const Grid& src, const Grid& dst, const int* dst_nodes, int nrow, int* dnode, double* dw,
+                         int* err, cudaStream_t s) {
     if (nrow == 0) return cudaSuccess;
     k_donor<<<grid_for(nrow, 128), 128, 0, s>>>(src, dst, dst_nodes, nrow, dnode, dw, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_force(const Grid& g, const double* fe, double* f, cudaStream_t s) {
-    k_gather_force<<<grid_for(3LL * g.nn(), 256), 256, 0, s>>>(g.nx, g.ny, g.nz, g.ne(), fe, f);
+cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, long long stride, cudaStream_t s) {
+    k_aos_to_soa<<<grid_for(3LL * nn, 256), 256, 0, s>>>(aos, soa, nn, stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, cudaStream_t s) {
-    k_aos_to_soa<<<grid_for(3LL * nn, 256), 256, 0, s>>>(aos, soa, nn);
+cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, long long stride, cudaStream_t s) {
+    k_soa_to_aos<<<grid_for(3LL * nn, 256), 256, 0, s>>>(soa, aos, nn, stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, cudaStream_t s) {
-    k_soa_to_aos<<<grid_for(3LL * nn, 256), 256, 0, s>>>(soa, aos, nn);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_accel_from_force(const FomDev& f, const double* force_soa, cudaStream_t s) {
-    const int nn = f.g.nn();
-    k_accel_from_force<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, f.clamp, f.minv, force_soa, f.a);
+cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, long long stride, cudaStream_t s) {
+    k_zero_clamped<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, clamp, u, v, stride);
     return cudaGetLastError();
 }
 

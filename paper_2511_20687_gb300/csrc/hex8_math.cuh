@@ -1,0 +1,241 @@
+// Device-side arithmetic of the hex8 internal force, shared by the element-level kernels and the
+// batched per-step kernels.
+//
+// Internal-force formulation (uniform cubic elements of edge h).  With unit-cube coordinates s,
+// grad_X N = grad_s N / h, detJ * w = h^3/8 at each of the 8 Gauss points s = (1 -+ 1/sqrt3)/2, so
+//   H = grad u = sum_a (u_a / h) (x) grad_s N_a,     f_a = (h^2/8) sum_gp P(H) grad_s N_a.
+// Trilinear shape functions factor per axis, so both sums are evaluated by sum factorisation:
+// edge differences along one axis followed by linear interpolation along the other two (and the
+// transpose for the force), 16 FP64 operations per (component, direction) instead of 8 x 8.
+// The Neo-Hookean stress of Appendix A.3, P = F S with
+//   S = 1/2 kappa (det C - 1) C^-1 + mu (det C)^-1/3 (I - 1/3 tr C C^-1),
+// is evaluated through F C^-1 = F^-T = cof(F) / J, i.e.
+//   P = [1/2 kappa (J^2 - 1) - 1/3 mu J^-2/3 tr C] / J * cof(F) + mu J^-2/3 F,
+// with J^-2/3 = rcbrt(J^2) and 1/J = J * (J^-2/3)^3 (no division).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "osam.h"
+
+namespace osam {
+namespace hex8 {
+
+constexpr double kG0 = 0.21132486540518711775;   // (1 - 1/sqrt(3)) / 2
+constexpr double kG1 = 0.78867513459481288225;   // (1 + 1/sqrt(3)) / 2
+constexpr double kGd = 0.57735026918962576451;   // kG1 - kG0 = 1/sqrt(3)
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rcbrtT(double x) { return rcbrt(x); }
+__device__ __forceinline__ float rcbrtT(float x) { return rcbrtf(x); }
+
+// nodal values D[b][e] on a unit square -> values at the 2x2 Gauss points out[q][r]
+template <typename T>
+__device__ __forceinline__ void lerp2(const T D[2][2], T out[2][2]) {
+    T E[2][2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        T d = D[1][e] - D[0][e];
+        E[0][e] = fmaT(T(kG0), d, D[0][e]);
+        E[1][e] = fmaT(T(kG1), d, D[0][e]);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        T d = E[q][1] - E[q][0];
+        out[q][0] = fmaT(T(kG0), d, E[q][0]);
+        out[q][1] = fmaT(T(kG1), d, E[q][0]);
+    }
+}
+
+// transpose of lerp2: Gauss-point values S[q][r] -> nodal out[b][e] = sum l_b(g_q) l_e(g_r) S[q][r]
+template <typename T>
+__device__ __forceinline__ void lerp2T(const T S[2][2], T out[2][2]) {
+    T V[2][2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        T s = S[q][0] + S[q][1];
+        V[q][0] = fmaT(T(kGd), S[q][0], T(kG0) * s);  // g1 S0 + g0 S1
+        V[q][1] = s - V[q][0];                        // g0 S0 + g1 S1
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        T s = V[0][e] + V[1][e];
+        out[0][e] = fmaT(T(kGd), V[0][e], T(kG0) * s);
+        out[1][e] = s - out[0][e];
+    }
+}
+
+// Appendix A.1: P = lambda tr(eps) I + 2 mu eps (lam, mu pre-scaled by h^2/8)
+template <typename T>
+__device__ __forceinline__ void stress_le(const T H[3][3], T lam, T mu, T P[3][3]) {
+    T lt = lam * (H[0][0] + H[1][1] + H[2][2]);
+    T mu2 = mu + mu;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P[c][c] = fmaT(mu2, H[c][c], lt);
+    P[0][1] = P[1][0] = mu * (H[0][1] + H[1][0]);
+    P[0][2] = P[2][0] = mu * (H[0][2] + H[2][0]);
+    P[1][2] = P[2][1] = mu * (H[1][2] + H[2][1]);
+}
+
+// Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8)
+template <typename T>
+__device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, T P[3][3]) {
+    const T F00 = T(1) + H[0][0], F11 = T(1) + H[1][1], F22 = T(1) + H[2][2];
+    const T F01 = H[0][1], F02 = H[0][2], F10 = H[1][0], F12 = H[1][2], F20 = H[2][0], F21 = H[2][1];
+    T c00 = fmaT(F11, F22, -F12 * F21);
+    T c01 = fmaT(F12, F20, -F10 * F22);
+    T c02 = fmaT(F10, F21, -F11 * F20);
+    T c10 = fmaT(F02, F21, -F01 * F22);
+    T c11 = fmaT(F00, F22, -F02 * F20);
+    T c12 = fmaT(F01, F20, -F00 * F21);
+    T c20 = fmaT(F01, F12, -F02 * F11);
+    T c21 = fmaT(F02, F10, -F00 * F12);
+    T c22 = fmaT(F00, F11, -F01 * F10);
+    T J = fmaT(F00, c00, fmaT(F01, c01, F02 * c02));
+    T trC = F00 * F00;
+    trC = fmaT(F01, F01, trC); trC = fmaT(F02, F02, trC);
+    trC = fmaT(F10, F10, trC); trC = fmaT(F11, F11, trC); trC = fmaT(F12, F12, trC);
+    trC = fmaT(F20, F20, trC); trC = fmaT(F21, F21, trC); trC = fmaT(F22, F22, trC);
+    T J2 = J * J;
+    T r3 = rcbrtT(J2);                 // J^-2/3
+    T invJ = J * (r3 * r3 * r3);       // J * J^-2 = 1/J
+    T alpha = mu * r3;
+    T beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
+    P[0][0] = fmaT(alpha, F00, beta * c00);
+    P[0][1] = fmaT(alpha, F01, beta * c01);
+    P[0][2] = fmaT(alpha, F02, beta * c02);
+    P[1][0] = fmaT(alpha, F10, beta * c10);
+    P[1][1] = fmaT(alpha, F11, beta * c11);
+    P[1][2] = fmaT(alpha, F12, beta * c12);
+    P[2][0] = fmaT(alpha, F20, beta * c20);
+    P[2][1] = fmaT(alpha, F21, beta * c21);
+    P[2][2] = fmaT(alpha, F22, beta * c22);
+}
+
+// Element force from scaled edge differences.
+//   Dx[c][ay][az] = (u_c(1,ay,az) - u_c(0,ay,az)) / h   (and Dy[c][ax][az], Dz[c][ax][ay])
+// Output F[c][corner], corner = ax + 2 ay + 4 az.
+template <int MAT, typename T>
+__device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3][2][2], const T Dz[3][2][2],
+                                              T m1, T m2, T m3, T F[3][8]) {
+    T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lerp2<T>(Dx[c], Gx[c]);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
+        lerp2<T>(Dy[c], Gy[c]);   // Gy[c][p][r]
+        lerp2<T>(Dz[c], Gz[c]);   // Gz[c][p][q]
+    }
+    T Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                T Hm[3][3], P[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Hm[c][0] = Gx[c][q][r];
+                    Hm[c][1] = Gy[c][p][r];
+                    Hm[c][2] = Gz[c][p][q];
+                }
+                if (MAT == OSAM_NEO_HOOKEAN) stress_nh<T>(Hm, m1, m2, m3, P);
+                else stress_le<T>(Hm, m1, m2, P);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (p == 0) Sx[c][q][r] = P[c][0]; else Sx[c][q][r] += P[c][0];
+                    if (q == 0) Sy[c][p][r] = P[c][1]; else Sy[c][p][r] += P[c][1];
+                    if (r == 0) Sz[c][p][q] = P[c][2]; else Sz[c][p][q] += P[c][2];
+                }
+            }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T Tm[2][2];
+        lerp2T<T>(Sx[c], Tm);  // Tm[ay][az]
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) {
+                F[c][1 + 2 * ay + 4 * az] = Tm[ay][az];
+                F[c][2 * ay + 4 * az] = -Tm[ay][az];
+            }
+        lerp2T<T>(Sy[c], Tm);  // Tm[ax][az]
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) {
+                F[c][ax + 2 + 4 * az] += Tm[ax][az];
+                F[c][ax + 4 * az] -= Tm[ax][az];
+            }
+        lerp2T<T>(Sz[c], Tm);  // Tm[ax][ay]
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) {
+                F[c][ax + 2 * ay + 4] += Tm[ax][ay];
+                F[c][ax + 2 * ay] -= Tm[ax][ay];
+            }
+    }
+}
+
+__device__ __forceinline__ void atomic_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add(float* p, float v) { atomicAdd(p, v); }
+
+// scaled edge differences of the 8 nodal values of one component (FP64 arithmetic, T output)
+template <typename T>
+__device__ __forceinline__ void edge_differences(const double U[8], double invh, T Dx[2][2], T Dy[2][2], T Dz[2][2]) {
+    if constexpr (sizeof(T) == 8) {
+        double V[8];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) V[c8] = U[c8] * invh;
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                Dx[p][q] = T(V[1 + 2 * p + 4 * q] - V[2 * p + 4 * q]);
+                Dy[p][q] = T(V[p + 2 + 4 * q] - V[p + 4 * q]);
+                Dz[p][q] = T(V[p + 2 * q + 4] - V[p + 2 * q]);
+            }
+    } else {
+        // FP32 force: differences in FP64 (they cancel), the rest in FP32
+        const float ih = float(invh);
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                Dx[p][q] = T(U[1 + 2 * p + 4 * q] - U[2 * p + 4 * q]) * ih;
+                Dy[p][q] = T(U[p + 2 + 4 * q] - U[p + 4 * q]) * ih;
+                Dz[p][q] = T(U[p + 2 * q + 4] - U[p + 2 * q]) * ih;
+            }
+    }
+}
+
+// nodal force of node (i,j,k), component c, from the element buffer (fixed order: deterministic)
+template <typename TF>
+__device__ __forceinline__ double gather_force(const TF* fe, int nx, int ny, int nz, int ne, int i, int j, int k,
+                                               int c) {
+    double s = 0.0;
+#pragma unroll
+    for (int az = 0; az < 2; ++az) {
+        const int ke = k - az;
+        if (ke < 0 || ke >= nz) continue;
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+            const int je = j - ay;
+            if (je < 0 || je >= ny) continue;
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax) {
+                const int ie = i - ax;
+                if (ie < 0 || ie >= nx) continue;
+                const int e = ie + nx * (je + ny * ke);
+                const int corner = ax + 2 * ay + 4 * az;
+                s += double(fe[(long long)(corner * 3 + c) * ne + e]);
+            }
+        }
+    }
+    return s;
+}
+
+}  // namespace hex8
+}  // namespace osam

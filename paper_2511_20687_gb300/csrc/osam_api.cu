@@ -1,7 +1,9 @@
-// Host runtime of libosam: context construction (schwarz_init), the O-SAM controller (Algorithm 1
-// of the paper, with the criterion of Eq. conv_criterion), state I/O, the element-level operators
-// and the adjoint rollout.  Every numerical step runs in the kernels of fom_kernels.cu,
-// rom_kernels.cu and adjoint_kernels.cu; this file only allocates, sequences and checks.
+// Host runtime of libosam: context construction for one problem or a batch of instances
+// (schwarz_init / osam_batch_init), the O-SAM controller (Algorithm 1 of the paper with the
+// criterion of Eq. conv_criterion) as a CUDA graph whose Schwarz iterations run in a while node, or
+// as a host-driven loop, state I/O, the element-level operators and the adjoint rollout.  Every
+// numerical step runs in the kernels of step_kernels.cu, fom_kernels.cu, rom_kernels.cu and
+// adjoint_kernels.cu; this file only allocates, sequences and checks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,14 +24,42 @@ namespace {
 
 thread_local std::string g_init_error;
 
-struct Sub {
+struct FomGroupH {
+    std::vector<Grid> grid;
+    std::vector<std::vector<uint8_t>> clamp;
+    std::vector<std::vector<int>> srow;
+    std::vector<int> ns;
+    std::vector<InstFom> inst;
+    std::vector<int> nblk_off;
+    std::vector<int2> nblk;
+    FomB d{};
+    InstFom* inst_d = nullptr;
+};
+
+struct RomGroupH {
+    std::vector<Grid> grid;
+    std::vector<std::vector<uint8_t>> clamp;
+    std::vector<std::vector<int>> srow;
+    std::vector<int> ns, nfree;
+    std::vector<InstRom> inst;
+    // per-instance device pointers into flat arrays (set-up / I/O)
+    std::vector<double*> Phi;
+    std::vector<int*> free_dof, dof_free, srow_d;
+    std::vector<uint8_t*> clamp_d;
+    RomB d{};
+    InstRom* inst_d = nullptr;
+};
+
+struct Slot {
     int kind = OSAM_FOM;
-    Grid g;
-    std::vector<uint8_t> clamp_h;
-    std::vector<int> srow_h;
-    int ns = 0;
-    FomDev fom;
-    RomDev rom;
+    FomGroupH fom;
+    RomGroupH rom;
+};
+
+struct CplH {
+    int dst = 0, src = 0;
+    std::vector<int> nrow, row_first;
+    CplB d{};
 };
 
 }  // namespace
@@ -38,61 +68,50 @@ struct osam_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int n_inst = 1;
     double dt = 0.0;
     int nsub = 0;
     double tol_abs = 0.0, tol_rel = 0.0;
     int max_it = 1;
     int precision = OSAM_FP64;
     int scatter = kGather;
-    std::vector<Sub> subs;
-    std::vector<CplDev> cpls;
+    std::vector<Slot> slots;
+    std::vector<CplH> cpls;
     std::vector<void*> allocs;
-    double* partial = nullptr;
-    int nparts = 0;
-    double* result = nullptr;      // device [3]
-    double* result_h = nullptr;    // pinned host [3]
-    double* scratch = nullptr;     // device [3 * max nodes]
+    std::vector<long long> fom_elements;  // per instance
+    CtlB ctl{};
+    int* sel = nullptr;                   // one-hot instance mask for per-instance I/O
+    int* iters_h = nullptr;               // pinned mirrors
+    int* status_h = nullptr;
+    double* cnum_h = nullptr;
+    double* cden_h = nullptr;
+    int* any_h = nullptr;
+    double* scratch = nullptr;            // device [3 * max nodes of any instance]
     int* err_d = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
-    long long fom_elements = 0;
-    // kernel-level timing of the internal-force launches and a launch count
+    // CUDA graph of one controller step: begin nodes, then a while node over Schwarz iterations
+    bool use_graph = true;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond{};
+    // kernel-level timing of the internal-force launches (host-driven path) and a launch count
     bool prof = false;
     std::vector<cudaEvent_t> pev;
     int pnext = 0;
     double prof_ms = 0.0;
     long long prof_launches = 0, prof_elements = 0, launches = 0;
 
-    int prof_begin() {
-        if (!prof) return -1;
-        while (pnext + 2 > (int)pev.size()) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return -1;
-            pev.push_back(e);
-        }
-        cudaEventRecord(pev[pnext], stream);
-        return pnext;
-    }
-    void prof_end(int k, long long elements) {
-        if (k < 0) return;
-        cudaEventRecord(pev[k + 1], stream);
-        pnext = k + 2;
-        prof_launches += 1;
-        prof_elements += elements;
-    }
-    // after a stream synchronisation: fold the recorded pairs into prof_ms
-    void prof_collect() {
-        for (int k = 0; k + 1 < pnext; k += 2) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) prof_ms += ms;
-        }
-        pnext = 0;
-    }
-
     ~osam_ctx() {
         if (stream) cudaStreamSynchronize(stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
         for (void* p : allocs) cudaFree(p);
-        if (result_h) cudaFreeHost(result_h);
+        if (iters_h) cudaFreeHost(iters_h);
+        if (status_h) cudaFreeHost(status_h);
+        if (cnum_h) cudaFreeHost(cnum_h);
+        if (cden_h) cudaFreeHost(cden_h);
+        if (any_h) cudaFreeHost(any_h);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
@@ -118,13 +137,38 @@ struct osam_ctx {
         err = buf;
         return code;
     }
+
+    int prof_begin() {
+        if (!prof) return -1;
+        while (pnext + 2 > (int)pev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            pev.push_back(e);
+        }
+        cudaEventRecord(pev[pnext], stream);
+        return pnext;
+    }
+    void prof_end(int k, long long elements) {
+        if (k < 0) return;
+        cudaEventRecord(pev[k + 1], stream);
+        pnext = k + 2;
+        prof_launches += 1;
+        prof_elements += elements;
+    }
+    void prof_collect() {
+        for (int k = 0; k + 1 < pnext; k += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) prof_ms += ms;
+        }
+        pnext = 0;
+    }
 };
 
-#define CK(call)                                                                                          \
-    do {                                                                                                  \
-        cudaError_t e_ = (call);                                                                          \
-        if (e_ != cudaSuccess) return ctx->fail(OSAM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                                                __FILE__, __LINE__);                                      \
+#define CK(call)                                                                                              \
+    do {                                                                                                      \
+        cudaError_t e_ = (call);                                                                              \
+        if (e_ != cudaSuccess)                                                                                \
+            return ctx->fail(OSAM_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
 // checked kernel launch, counted
@@ -134,162 +178,24 @@ struct osam_ctx {
         ++ctx->launches;  \
     } while (0)
 
-#define CKA(ptr)                                                                                    \
-    do {                                                                                            \
+#define CKA(ptr)                                                                                         \
+    do {                                                                                                 \
         if (!(ptr)) return ctx->fail(OSAM_ENOMEM, "device allocation failed (%s:%d)", __FILE__, __LINE__); \
     } while (0)
 
+#define RET(expr)                       \
+    do {                                \
+        if (int r_ = (expr)) return r_; \
+    } while (0)
+
+namespace osam {
+void set_thread_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace osam
+
 namespace {
 
-long long hist_stride_fom(const Sub& s) { return 9LL * s.ns; }
-
-double* fom_slot(osam_ctx* ctx, Sub& s, int slot) { return s.fom.hist + (long long)slot * hist_stride_fom(s); }
-
-ElemArgs elem_args(const FomDev& F, const double* u, int usn, long long usc) {
-    ElemArgs a{};
-    a.nx = F.g.nx; a.ny = F.g.ny; a.nz = F.g.nz; a.ne = F.g.ne();
-    a.invh = 1.0 / F.g.h;
-    a.w8 = F.g.h * F.g.h / 8.0;
-    a.lam = F.lam; a.mu = F.mu;
-    a.lam_e = F.lam_e; a.mu_e = F.mu_e;
-    a.u = u; a.usn = usn; a.usc = usc;
-    a.f = F.f; a.fsn = 1; a.fsc = F.g.nn();
-    a.fe = F.fe;
-    return a;
-}
-
-NodeArgs node_args(osam_ctx* ctx, Sub& s) {
-    FomDev& F = s.fom;
-    NodeArgs a{};
-    a.nx = F.g.nx; a.ny = F.g.ny; a.nz = F.g.nz; a.nn = F.g.nn(); a.ne = F.g.ne();
-    a.dt = ctx->dt;
-    a.minv = F.minv; a.clamp = F.clamp; a.srow = F.srow; a.ns = s.ns;
-    a.v = F.v; a.a = F.a;
-    a.force = F.fe; a.fclear = F.f;
-    return a;
-}
-
-// the FP32-force atomic path accumulates into a float buffer placed after the FP64 one
-void* f32_buffer(const FomDev& F) { return F.fe; }
-
-int advance_fom(osam_ctx* ctx, int i) {
-    Sub& s = ctx->subs[i];
-    FomDev& F = s.fom;
-    const int nn = F.g.nn();
-    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
-    const int scatter = ctx->scatter;
-    // predictor of substep 0: u^1 into buffer 1
-    NodeArgs p = node_args(ctx, s);
-    p.predict_only = 1;
-    p.ucur = F.u[0];
-    p.unext = F.u[1];
-    p.h2 = fom_slot(ctx, s, 1);
-    p.last = 0;
-    LK(launch_node_update(fp32, scatter, p, ctx->stream));
-    for (int j = 0; j < ctx->nsub; ++j) {
-        double* X = F.u[(j + 1) & 1];
-        double* Y = F.u[j & 1];
-        ElemArgs ea = elem_args(F, X, 1, nn);
-        if (fp32 && scatter == kAtomic) ea.f = f32_buffer(F);
-        const int pk = ctx->prof_begin();
-        LK(launch_hex8_force(F.material, fp32, scatter, ea, ctx->stream));
-        ctx->prof_end(pk, F.g.ne());
-        NodeArgs na = node_args(ctx, s);
-        if (fp32 && scatter == kAtomic) na.fclear = f32_buffer(F);
-        na.ucur = X;
-        na.unext = Y;
-        na.h1 = fom_slot(ctx, s, j + 1);
-        na.h2 = (j + 2 <= ctx->nsub) ? fom_slot(ctx, s, j + 2) : nullptr;
-        na.last = (j == ctx->nsub - 1);
-        LK(launch_node_update(fp32, scatter, na, ctx->stream));
-        for (CplDev& c : ctx->cpls)
-            if (c.src == i) LK(launch_trace(c, X, F.v, F.a, nn, j + 1, ctx->nsub, ctx->stream));
-    }
-    if (ctx->nsub & 1) CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
-    return OSAM_OK;
-}
-
-int advance_rom(osam_ctx* ctx, int i) {
-    RomDev& R = ctx->subs[i].rom;
-    CK(cudaMemcpyAsync(R.qrec, R.q, sizeof(double) * 3 * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
-    LK(launch_rom_project(R, 1, ctx->nsub, ctx->stream));
-    for (int j = 0; j < ctx->nsub; ++j) LK(launch_rom_step(R, j + 1, ctx->dt, 0, ctx->stream));
-    return OSAM_OK;
-}
-
-int dst_hist(osam_ctx* ctx, const CplDev& c, bool* dst_rom, double** hist, int* nd) {
-    Sub& d = ctx->subs[c.dst];
-    *dst_rom = d.kind == OSAM_ROM;
-    if (*dst_rom) { *hist = d.rom.hist; *nd = d.rom.nsdof; }
-    else { *hist = d.fom.hist; *nd = d.ns; }
-    return OSAM_OK;
-}
-
-int transfer(osam_ctx* ctx, const CplDev& c) {
-    bool dst_rom;
-    double* hist;
-    int nd;
-    dst_hist(ctx, c, &dst_rom, &hist, &nd);
-    Sub& src = ctx->subs[c.src];
-    if (src.kind == OSAM_FOM) LK(launch_publish_fom(c, dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    else LK(launch_rom_reconstruct(c, src.rom, false, dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    return OSAM_OK;
-}
-
-int zoh(osam_ctx* ctx, const CplDev& c) {
-    bool dst_rom;
-    double* hist;
-    int nd;
-    dst_hist(ctx, c, &dst_rom, &hist, &nd);
-    Sub& src = ctx->subs[c.src];
-    if (src.kind == OSAM_FOM)
-        LK(launch_zoh_from_fom(c, src.fom.u[0], src.fom.v, src.fom.a, src.g.nn(), dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    else LK(launch_rom_reconstruct(c, src.rom, true, dst_rom, hist, nd, ctx->nsub, ctx->stream));
-    return OSAM_OK;
-}
-
-int save_all(osam_ctx* ctx, bool restore) {
-    for (Sub& s : ctx->subs) {
-        if (s.kind == OSAM_FOM) {
-            const size_t b = sizeof(double) * 3 * s.g.nn();
-            FomDev& F = s.fom;
-            if (restore) {
-                CK(cudaMemcpyAsync(F.u[0], F.su, b, cudaMemcpyDeviceToDevice, ctx->stream));
-                CK(cudaMemcpyAsync(F.v, F.sv, b, cudaMemcpyDeviceToDevice, ctx->stream));
-                CK(cudaMemcpyAsync(F.a, F.sa, b, cudaMemcpyDeviceToDevice, ctx->stream));
-            } else {
-                CK(cudaMemcpyAsync(F.su, F.u[0], b, cudaMemcpyDeviceToDevice, ctx->stream));
-                CK(cudaMemcpyAsync(F.sv, F.v, b, cudaMemcpyDeviceToDevice, ctx->stream));
-                CK(cudaMemcpyAsync(F.sa, F.a, b, cudaMemcpyDeviceToDevice, ctx->stream));
-            }
-        } else {
-            RomDev& R = s.rom;
-            const size_t b = sizeof(double) * 3 * R.r;
-            if (restore) CK(cudaMemcpyAsync(R.q, R.sq, b, cudaMemcpyDeviceToDevice, ctx->stream));
-            else CK(cudaMemcpyAsync(R.sq, R.q, b, cudaMemcpyDeviceToDevice, ctx->stream));
-        }
-    }
-    return OSAM_OK;
-}
-
-int criterion_async(osam_ctx* ctx) {
-    int off = 0;
-    for (Sub& s : ctx->subs) {
-        if (s.kind == OSAM_FOM) {
-            LK(launch_norms_fom(s.fom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
-            off += s.fom.norm_blocks;
-        } else {
-            LK(launch_rom_norms(s.rom, ctx->dt, ctx->partial + 2 * off, ctx->stream));
-            off += 1;
-        }
-    }
-    LK(launch_norms_final(ctx->partial, off, ctx->result, ctx->stream));
-    CK(cudaMemcpyAsync(ctx->result_h, ctx->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    return OSAM_OK;
-}
-
-// copy a user array (host or device) into a device buffer
 int upload(osam_ctx* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return OSAM_OK;
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
     return OSAM_OK;
 }
@@ -311,159 +217,788 @@ int check_device(osam_ctx* ctx, int device) {
     CK(cudaSetDevice(device));
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, device));
-    if (prop.major < 10) return ctx->fail(OSAM_ECUDA, "device %d is sm_%d%d; libosam is built for sm_103a", device, prop.major, prop.minor);
+    if (prop.major < 10)
+        return ctx->fail(OSAM_ECUDA, "device %d is sm_%d%d; libosam is built for sm_103a", device, prop.major, prop.minor);
     return OSAM_OK;
 }
 
-int setup_fom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
-    FomDev& F = s.fom;
-    F.g = s.g;
-    F.material = d.material;
-    F.lam = d.lambda; F.mu = d.mu; F.rho = d.rho;
-    const int nn = s.g.nn(), ne = s.g.ne();
-    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
-    if (d.lambda_e) { CKA(F.lam_e = ctx->alloc<double>(ne)); if (int r = upload(ctx, F.lam_e, d.lambda_e, sizeof(double) * ne)) return r; }
-    if (d.mu_e) { CKA(F.mu_e = ctx->alloc<double>(ne)); if (int r = upload(ctx, F.mu_e, d.mu_e, sizeof(double) * ne)) return r; }
-    CKA(F.minv = ctx->alloc<double>(nn));
-    CK(launch_lumped_minv(s.g, d.rho, F.minv, ctx->stream));
-    CKA(F.clamp = ctx->alloc<uint8_t>(nn));
-    if (int r = upload(ctx, F.clamp, s.clamp_h.data(), nn)) return r;
-    CKA(F.srow = ctx->alloc<int>(nn));
-    if (int r = upload(ctx, F.srow, s.srow_h.data(), sizeof(int) * nn)) return r;
-    F.ns = s.ns;
-    for (int b = 0; b < 2; ++b) CKA(F.u[b] = ctx->alloc<double>(3LL * nn));
-    CKA(F.v = ctx->alloc<double>(3LL * nn));
-    CKA(F.a = ctx->alloc<double>(3LL * nn));
-    CKA(F.f = ctx->alloc<double>(3LL * nn));
-    // gather buffer (FP64 or FP32 element contributions); in FP32 atomic mode it holds the float accumulator
-    const size_t fe_bytes = std::max<size_t>(24ULL * ne * (fp32 ? 4 : 8), 3ULL * nn * 4);
-    CKA(F.fe = ctx->alloc<unsigned char>(fe_bytes));
-    CKA(F.su = ctx->alloc<double>(3LL * nn));
-    CKA(F.sv = ctx->alloc<double>(3LL * nn));
-    CKA(F.sa = ctx->alloc<double>(3LL * nn));
-    CKA(F.pu = ctx->alloc<double>(3LL * nn));
-    CKA(F.pv = ctx->alloc<double>(3LL * nn));
-    CKA(F.hist = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 9 * std::max(1, s.ns)));
-    F.norm_blocks = std::min(1024, grid_for(nn, 256));
-    // initial state (interleaved input -> SoA), clamped components zero
-    if (int r = upload(ctx, ctx->scratch, d.u0, sizeof(double) * 3 * nn)) return r;
-    CK(launch_aos_to_soa(ctx->scratch, F.u[0], nn, ctx->stream));
-    if (d.v0) {
-        if (int r = upload(ctx, ctx->scratch, d.v0, sizeof(double) * 3 * nn)) return r;
-        CK(launch_aos_to_soa(ctx->scratch, F.v, nn, ctx->stream));
-    }
-    CK(launch_zero_clamped(nn, F.clamp, F.u[0], F.v, ctx->stream));
-    return OSAM_OK;
-}
-
-// a0 = -M^-1 f(u0) in FP64 through the deterministic element buffer (FP64 [24][ne] scratch = fe when
-// it is large enough, else the atomic buffer is used)
-int fom_initial_accel(osam_ctx* ctx, Sub& s) {
-    FomDev& F = s.fom;
-    const int nn = s.g.nn();
-    ElemArgs ea = elem_args(F, F.u[0], 1, nn);
-    if (ctx->precision == OSAM_FP64) {
-        ea.fe = F.fe;
-        CK(launch_hex8_force(F.material, false, kGather, ea, ctx->stream));
-        CK(launch_gather_force(s.g, static_cast<const double*>(F.fe), static_cast<double*>(F.f), ctx->stream));
+// ------------------------------------------------------------------------------------------------
+// per-step sequences (used by the graph capture and by the host-driven loop)
+// ------------------------------------------------------------------------------------------------
+int advance_slot(osam_ctx* ctx, int s, const int* active) {
+    Slot& S = ctx->slots[s];
+    if (S.kind == OSAM_FOM) {
+        FomB& g = S.fom.d;
+        long long ne = 0;
+        for (const InstFom& I : S.fom.inst) ne += I.ne;
+        LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
+        for (int j = 0; j < ctx->nsub; ++j) {
+            double* X = g.u[(j + 1) & 1];
+            double* Y = g.u[j & 1];
+            const int pk = ctx->prof_begin();
+            LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream));
+            ctx->prof_end(pk, ne);
+            LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
+                             ctx->stream));
+            for (CplH& c : ctx->cpls)
+                if (c.src == s) LK(launch_trace_b(c.d, active, g, X, j + 1, ctx->stream));
+        }
+        if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
     } else {
-        CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
-        ea.f = F.f;
-        CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
+        RomB& r = S.rom.d;
+        LK(launch_rom_record0_b(r, active, ctx->stream));
+        LK(launch_rom_project_b(r, active, 1, ctx->nsub, ctx->stream));
+        for (int j = 0; j < ctx->nsub; ++j) LK(launch_rom_step_b(r, active, j + 1, ctx->dt, 0, ctx->stream));
     }
-    CK(launch_accel_from_force(F, static_cast<const double*>(F.f), ctx->stream));
-    CK(cudaMemsetAsync(F.f, 0, sizeof(double) * 3 * nn, ctx->stream));
     return OSAM_OK;
 }
 
-int setup_rom(osam_ctx* ctx, Sub& s, const osam_subdomain_desc& d) {
-    RomDev& R = s.rom;
-    R.g = s.g;
-    const int nn = s.g.nn();
-    R.r = d.r;
-    R.rs = d.r_s;
-    R.ns = s.ns;
-    R.nsdof = 3 * s.ns;
-    R.nq = R.r * (R.r + 1) / 2;
-    R.d = R.r + R.nq + R.rs + 1;
-    if (R.r < 1 || R.r > 256) return ctx->fail(OSAM_EINVAL, "ROM rank r=%d outside [1, 256]", R.r);
-    if (R.rs < 0 || (R.rs > 0 && !d.Phi_S)) return ctx->fail(OSAM_EINVAL, "ROM boundary basis missing");
-    if (!d.Phi || !d.K || !d.H || !d.c || (R.rs > 0 && !d.B)) return ctx->fail(OSAM_EINVAL, "ROM operator missing");
-    // free dofs
-    std::vector<int> free_dof, dof_free(3 * nn, -1);
-    for (int n = 0; n < nn; ++n)
-        for (int c = 0; c < 3; ++c)
-            if (!(s.clamp_h[n] & (1 << c)) && s.srow_h[n] < 0) {
-                dof_free[3 * n + c] = (int)free_dof.size();
-                free_dof.push_back(3 * n + c);
-            }
-    R.nfree = (int)free_dof.size();
-    CKA(R.free_dof = ctx->alloc<int>(R.nfree));
-    CKA(R.dof_free = ctx->alloc<int>(3LL * nn));
-    if (int r = upload(ctx, R.free_dof, free_dof.data(), sizeof(int) * R.nfree)) return r;
-    if (int r = upload(ctx, R.dof_free, dof_free.data(), sizeof(int) * 3 * nn)) return r;
-    CKA(R.clamp = ctx->alloc<uint8_t>(nn));
-    if (int r = upload(ctx, R.clamp, s.clamp_h.data(), nn)) return r;
-    CKA(R.srow = ctx->alloc<int>(nn));
-    if (int r = upload(ctx, R.srow, s.srow_h.data(), sizeof(int) * nn)) return r;
-    CKA(R.Phi = ctx->alloc<double>((size_t)R.nfree * R.r));
-    if (int r = upload(ctx, R.Phi, d.Phi, sizeof(double) * R.nfree * R.r)) return r;
-    // packed operator rows [K | H | B | c]
-    std::vector<double> K, H, B, c, O((size_t)R.r * R.d);
-    if (int r = to_host(ctx, K, d.K, (size_t)R.r * R.r)) return r;
-    if (int r = to_host(ctx, H, d.H, (size_t)R.r * R.nq)) return r;
-    if (R.rs) { if (int r = to_host(ctx, B, d.B, (size_t)R.r * R.rs)) return r; }
-    if (int r = to_host(ctx, c, d.c, (size_t)R.r)) return r;
-    for (int i = 0; i < R.r; ++i) {
-        double* row = O.data() + (size_t)i * R.d;
-        std::copy(K.begin() + (size_t)i * R.r, K.begin() + (size_t)(i + 1) * R.r, row);
-        std::copy(H.begin() + (size_t)i * R.nq, H.begin() + (size_t)(i + 1) * R.nq, row + R.r);
-        if (R.rs) std::copy(B.begin() + (size_t)i * R.rs, B.begin() + (size_t)(i + 1) * R.rs, row + R.r + R.nq);
-        row[R.d - 1] = c[i];
+int transfer_cpl(osam_ctx* ctx, CplH& c, const int* active) {
+    Slot& src = ctx->slots[c.src];
+    if (src.kind == OSAM_FOM) LK(launch_publish_b(c.d, active, ctx->nsub, ctx->stream));
+    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 0, ctx->nsub, ctx->stream));
+    return OSAM_OK;
+}
+
+int zoh_cpl(osam_ctx* ctx, CplH& c, const int* active) {
+    Slot& src = ctx->slots[c.src];
+    if (src.kind == OSAM_FOM) LK(launch_zoh_fom_b(c.d, active, src.fom.d, ctx->nsub, ctx->stream));
+    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 1, ctx->nsub, ctx->stream));
+    return OSAM_OK;
+}
+
+int saverest_all(osam_ctx* ctx, const int* active, int restore) {
+    for (Slot& S : ctx->slots) {
+        if (S.kind == OSAM_FOM) LK(launch_saverest_fom_b(S.fom.d, active, restore, ctx->stream));
+        else LK(launch_saverest_rom_b(S.rom.d, active, restore, ctx->stream));
     }
-    CKA(R.O = ctx->alloc<double>(O.size()));
-    if (int r = upload(ctx, R.O, O.data(), sizeof(double) * O.size())) return r;
+    return OSAM_OK;
+}
+
+int norms_all(osam_ctx* ctx, const int* active) {
+    for (Slot& S : ctx->slots) {
+        if (S.kind == OSAM_FOM) LK(launch_norms_fom_b(S.fom.d, active, ctx->dt, ctx->stream));
+        else LK(launch_rom_norms_b(S.rom.d, active, ctx->dt, ctx->stream));
+    }
+    return OSAM_OK;
+}
+
+// start of a controller step: save the state at t_{k-1}, zero-order hold of every source, flags
+int enqueue_begin(osam_ctx* ctx) {
+    RET(saverest_all(ctx, nullptr, 0));
+    for (CplH& c : ctx->cpls) RET(zoh_cpl(ctx, c, nullptr));
+    LK(launch_reset_ctl(ctx->ctl, ctx->stream));
+    return OSAM_OK;
+}
+
+// one Schwarz iteration for every instance still iterating; instances that continue are restored
+// to the saved state for the next iteration
+int enqueue_iteration(osam_ctx* ctx, int use_cond) {
+    const int* act = ctx->ctl.active;
+    for (int s = 0; s < (int)ctx->slots.size(); ++s) {
+        RET(advance_slot(ctx, s, act));
+        for (CplH& c : ctx->cpls)
+            if (c.src == s) RET(transfer_cpl(ctx, c, act));
+    }
+    RET(norms_all(ctx, act));
+    LK(launch_controller(ctx->ctl, ctx->cond, use_cond, ctx->stream));
+    RET(saverest_all(ctx, act, 1));
+    return OSAM_OK;
+}
+
+int build_graph(osam_ctx* ctx) {
+    if (ctx->exec) return OSAM_OK;
+    const long long launches0 = ctx->launches;
+    CK(cudaGraphCreate(&ctx->graph, 0));
+    CK(cudaGraphConditionalHandleCreate(&ctx->cond, ctx->graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_begin(ctx);
+    cudaGraph_t g = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc) return rc;
+    CK(ec);
+    // the while node depends on every leaf of the begin nodes
+    size_t n = 0;
+    CK(cudaGraphGetNodes(ctx->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n), leaves;
+    CK(cudaGraphGetNodes(ctx->graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        size_t nd_out = 0;
+        CK(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out));
+        if (nd_out == 0) leaves.push_back(nd);
+    }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = ctx->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, ctx->graph, leaves.data(), nullptr, leaves.size(), &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_iteration(ctx, 1);
+    ec = cudaStreamEndCapture(ctx->stream, &body);
+    if (rc) return rc;
+    CK(ec);
+    CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+    ctx->launches = launches0;  // capture issued nothing
+    return OSAM_OK;
+}
+
+int read_ctl(osam_ctx* ctx) {
+    const int n = ctx->n_inst;
+    CK(cudaMemcpyAsync(ctx->iters_h, ctx->ctl.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->status_h, ctx->ctl.status, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->cnum_h, ctx->ctl.cnum, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->cden_h, ctx->ctl.cden, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    return OSAM_OK;
+}
+
+// kernels one Schwarz iteration launches (for the launch count of the graph path)
+long long launches_per_iteration(osam_ctx* ctx) {
+    long long n = 0;
+    for (int s = 0; s < (int)ctx->slots.size(); ++s) {
+        int traces = 0;
+        for (CplH& c : ctx->cpls) traces += c.src == s;
+        if (ctx->slots[s].kind == OSAM_FOM) n += 1 + (long long)ctx->nsub * (2 + traces) + (ctx->nsub & 1);
+        else n += 2 + ctx->nsub;
+        n += traces;  // transfers
+    }
+    n += (long long)ctx->slots.size() * 2 + 1;  // norms, restore, controller
+    return n;
+}
+
+// ------------------------------------------------------------------------------------------------
+// set-up
+// ------------------------------------------------------------------------------------------------
+int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
+    const osam_problem_desc& d0 = descs[0];
+    if (d0.n_subdomains < 1 || d0.n_subdomains > kMaxSlots || !d0.subdomains)
+        return ctx->fail(OSAM_EINVAL, "1..%d subdomains required", kMaxSlots);
+    if (d0.n_couplings < 0 || (d0.n_couplings > 0 && !d0.couplings)) return ctx->fail(OSAM_EINVAL, "bad couplings");
+    if (!(d0.dt > 0.0) || d0.n_substeps < 1 || d0.max_iters < 1)
+        return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
+    if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE) return ctx->fail(OSAM_EINVAL, "bad precision");
+    for (int k = 0; k < d0.n_couplings; ++k) {
+        const osam_coupling_desc& c = d0.couplings[k];
+        if (c.dst < 0 || c.dst >= d0.n_subdomains || c.src < 0 || c.src >= d0.n_subdomains || c.dst == c.src)
+            return ctx->fail(OSAM_EINVAL, "coupling %d: bad indices", k);
+    }
+    for (int i = 0; i < n; ++i) {
+        const osam_problem_desc& d = descs[i];
+        if (d.n_subdomains != d0.n_subdomains || d.n_couplings != d0.n_couplings || d.dt != d0.dt ||
+            d.n_substeps != d0.n_substeps || d.max_iters != d0.max_iters || d.tol_abs != d0.tol_abs ||
+            d.tol_rel != d0.tol_rel || d.precision != d0.precision || d.device != d0.device || !d.subdomains)
+            return ctx->fail(OSAM_EINVAL, "instance %d: controller settings differ from instance 0", i);
+        for (int s = 0; s < d0.n_subdomains; ++s) {
+            const osam_subdomain_desc& a = d.subdomains[s];
+            const osam_subdomain_desc& b = d0.subdomains[s];
+            if (a.kind != OSAM_FOM && a.kind != OSAM_ROM) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad kind", s);
+            if (a.kind != b.kind || (a.kind == OSAM_FOM && a.material != b.material))
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: kind / material differ from instance 0", i, s);
+            if (a.nx < 1 || a.ny < 1 || a.nz < 1 || !(a.h > 0.0))
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: bad mesh", i, s);
+            if ((long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1) > (1LL << 30))
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d too large", i, s);
+            if (!a.u0) return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: u0 required", i, s);
+            if (a.kind == OSAM_FOM && a.material != OSAM_LINEAR_ELASTIC && a.material != OSAM_NEO_HOOKEAN)
+                return ctx->fail(OSAM_EINVAL, "subdomain %d: bad material", s);
+            if (a.kind == OSAM_FOM && !(a.rho > 0.0))
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: rho must be positive", i, s);
+        }
+        for (int k = 0; k < d0.n_couplings; ++k) {
+            if (!d.couplings || d.couplings[k].dst != d0.couplings[k].dst || d.couplings[k].src != d0.couplings[k].src ||
+                !d.couplings[k].nodes)
+                return ctx->fail(OSAM_EINVAL, "instance %d coupling %d differs from instance 0", i, k);
+        }
+    }
+    return OSAM_OK;
+}
+
+std::vector<int2> make_blocks(const std::vector<int>& counts, int block, std::vector<int>* first_block) {
+    std::vector<int2> out;
+    if (first_block) first_block->assign(counts.size() + 1, 0);
+    for (size_t i = 0; i < counts.size(); ++i) {
+        if (first_block) (*first_block)[i] = (int)out.size();
+        for (int b = 0; b < counts[i]; b += block) out.push_back(make_int2((int)i, b));
+    }
+    if (first_block) (*first_block)[counts.size()] = (int)out.size();
+    return out;
+}
+
+int set_eblocks(osam_ctx* ctx, FomGroupH& G, int block) {
+    std::vector<int> ne;
+    for (const InstFom& I : G.inst) ne.push_back(I.ne);
+    std::vector<int2> eb = make_blocks(ne, block, nullptr);
+    int2* d = ctx->alloc<int2>(eb.size());
+    CKA(d);
+    RET(upload(ctx, d, eb.data(), sizeof(int2) * eb.size()));
+    G.d.eblk = d;
+    G.d.n_eblk = (int)eb.size();
+    G.d.eblock = block;
+    return OSAM_OK;
+}
+
+int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_problem_desc* descs) {
+    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
+    long long NN = 0, NE = 0, H = 0;
+    G.inst.resize(n);
+    for (int i = 0; i < n; ++i) {
+        const Grid& g = G.grid[i];
+        const osam_subdomain_desc& d = descs[i].subdomains[s];
+        InstFom& I = G.inst[i];
+        I = InstFom{};
+        I.nx = g.nx; I.ny = g.ny; I.nz = g.nz; I.nn = g.nn(); I.ne = g.ne(); I.ns = G.ns[i];
+        I.invh = 1.0 / g.h;
+        I.w8 = g.h * g.h / 8.0;
+        I.lam = d.lambda; I.mu = d.mu;
+        I.node_off = NN; I.elem_off = NE; I.hist_off = H;
+        NN += I.nn; NE += I.ne; H += (long long)(ctx->nsub + 1) * 9 * I.ns;
+    }
+    FomB& B = G.d;
+    B.n_inst = n; B.NN = NN; B.NE = NE;
+    B.material = descs[0].subdomains[s].material;
+    B.fp32 = fp32;
+    B.scatter = ctx->scatter;
+    double* minv = ctx->alloc<double>(NN);
+    uint8_t* clamp = ctx->alloc<uint8_t>(NN);
+    int* srow = ctx->alloc<int>(NN);
+    CKA(minv); CKA(clamp); CKA(srow);
+    B.minv = minv; B.clamp = clamp; B.srow = srow;
+    for (int b = 0; b < 2; ++b) CKA(B.u[b] = ctx->alloc<double>(3 * NN));
+    CKA(B.v = ctx->alloc<double>(3 * NN));
+    CKA(B.a = ctx->alloc<double>(3 * NN));
+    CKA(B.f = ctx->alloc<double>(3 * NN));
+    CKA(B.fe = ctx->alloc<double>(24 * NE));  // FP64-sized: the FP64 initial force also uses it
+    CKA(B.su = ctx->alloc<double>(3 * NN));
+    CKA(B.sv = ctx->alloc<double>(3 * NN));
+    CKA(B.sa = ctx->alloc<double>(3 * NN));
+    CKA(B.pu = ctx->alloc<double>(3 * NN));
+    CKA(B.pv = ctx->alloc<double>(3 * NN));
+    CKA(B.hist = ctx->alloc<double>(std::max<long long>(H, 1)));
+    bool any_le = false, any_me = false;
+    for (int i = 0; i < n; ++i) {
+        any_le |= descs[i].subdomains[s].lambda_e != nullptr;
+        any_me |= descs[i].subdomains[s].mu_e != nullptr;
+    }
+    double* lam_e = any_le ? ctx->alloc<double>(NE) : nullptr;
+    double* mu_e = any_me ? ctx->alloc<double>(NE) : nullptr;
+    if (any_le) CKA(lam_e);
+    if (any_me) CKA(mu_e);
+    for (int i = 0; i < n; ++i) {
+        const osam_subdomain_desc& d = descs[i].subdomains[s];
+        InstFom& I = G.inst[i];
+        if (d.lambda_e) {
+            RET(upload(ctx, lam_e + I.elem_off, d.lambda_e, sizeof(double) * I.ne));
+            I.lam_e = lam_e + I.elem_off;
+        }
+        if (d.mu_e) {
+            RET(upload(ctx, mu_e + I.elem_off, d.mu_e, sizeof(double) * I.ne));
+            I.mu_e = mu_e + I.elem_off;
+        }
+        CK(launch_lumped_minv(G.grid[i], d.rho, minv + I.node_off, ctx->stream));
+        RET(upload(ctx, clamp + I.node_off, G.clamp[i].data(), I.nn));
+        RET(upload(ctx, srow + I.node_off, G.srow[i].data(), sizeof(int) * I.nn));
+        RET(upload(ctx, ctx->scratch, d.u0, sizeof(double) * 3 * I.nn));
+        CK(launch_aos_to_soa(ctx->scratch, B.u[0] + I.node_off, I.nn, NN, ctx->stream));
+        if (d.v0) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            RET(upload(ctx, ctx->scratch, d.v0, sizeof(double) * 3 * I.nn));
+            CK(launch_aos_to_soa(ctx->scratch, B.v + I.node_off, I.nn, NN, ctx->stream));
+        }
+        CK(launch_zero_clamped(I.nn, clamp + I.node_off, B.u[0] + I.node_off, B.v + I.node_off, NN, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));  // the staging buffers are reused by the next instance
+    }
+    CKA(G.inst_d = ctx->alloc<InstFom>(n));
+    RET(upload(ctx, G.inst_d, G.inst.data(), sizeof(InstFom) * n));
+    B.inst = G.inst_d;
+    std::vector<int> nn;
+    for (const InstFom& I : G.inst) nn.push_back(I.nn);
+    G.nblk = make_blocks(nn, kNodeBlock, &G.nblk_off);
+    int2* nb = ctx->alloc<int2>(G.nblk.size());
+    int* nbo = ctx->alloc<int>(G.nblk_off.size());
+    CKA(nb); CKA(nbo);
+    RET(upload(ctx, nb, G.nblk.data(), sizeof(int2) * G.nblk.size()));
+    RET(upload(ctx, nbo, G.nblk_off.data(), sizeof(int) * G.nblk_off.size()));
+    B.nblk = nb;
+    B.n_nblk = (int)G.nblk.size();
+    B.nblk_off = nbo;
+    CKA(B.partial = ctx->alloc<double>(2LL * B.n_nblk));
+    RET(set_eblocks(ctx, G, 128));
     CK(cudaStreamSynchronize(ctx->stream));
-    // Phi_S^T
-    CKA(R.PhiSt = ctx->alloc<double>((size_t)std::max(1, R.rs) * std::max(1, R.nsdof)));
-    if (R.rs) {
-        std::vector<double> PS, PSt((size_t)R.rs * R.nsdof);
-        if (int r = to_host(ctx, PS, d.Phi_S, (size_t)R.nsdof * R.rs)) return r;
-        for (int m = 0; m < R.nsdof; ++m)
-            for (int k = 0; k < R.rs; ++k) PSt[(size_t)k * R.nsdof + m] = PS[(size_t)m * R.rs + k];
-        if (int r = upload(ctx, R.PhiSt, PSt.data(), sizeof(double) * PSt.size())) return r;
+    return OSAM_OK;
+}
+
+int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_problem_desc* descs) {
+    G.inst.resize(n);
+    G.nfree.resize(n);
+    long long nn_tot = 0, nfree_tot = 0, O_tot = 0, PS_tot = 0, kij_tot = 0, q_tot = 0, qrec_tot = 0, ghat_tot = 0,
+              hist_tot = 0, part_tot = 0, phi_tot = 0;
+    RomB& B = G.d;
+    B.n_inst = n;
+    B.gx_max = B.gy_max = B.rs_max = B.r_max = 0;
+    std::vector<std::vector<int>> free_dof(n), dof_free(n);
+    int max_nn = 1;
+    for (int i = 0; i < n; ++i) {
+        const osam_subdomain_desc& d = descs[i].subdomains[s];
+        InstRom& I = G.inst[i];
+        I = InstRom{};
+        const int nn = G.grid[i].nn();
+        max_nn = std::max(max_nn, nn);
+        if (d.r < 1 || d.r > 256) return ctx->fail(OSAM_EINVAL, "instance %d: ROM rank r=%d outside [1, 256]", i, d.r);
+        if (d.r_s < 0 || (d.r_s > 0 && !d.Phi_S)) return ctx->fail(OSAM_EINVAL, "instance %d: ROM boundary basis missing", i);
+        if (!d.Phi || !d.K || !d.H || !d.c || (d.r_s > 0 && !d.B))
+            return ctx->fail(OSAM_EINVAL, "instance %d: ROM operator missing", i);
+        dof_free[i].assign(3 * nn, -1);
+        for (int nd = 0; nd < nn; ++nd)
+            for (int c = 0; c < 3; ++c)
+                if (!(G.clamp[i][nd] & (1 << c)) && G.srow[i][nd] < 0) {
+                    dof_free[i][3 * nd + c] = (int)free_dof[i].size();
+                    free_dof[i].push_back(3 * nd + c);
+                }
+        G.nfree[i] = (int)free_dof[i].size();
+        I.r = d.r; I.rs = d.r_s; I.nsdof = 3 * G.ns[i];
+        I.nq = I.r * (I.r + 1) / 2;
+        I.d = I.r + I.nq + I.rs + 1;
+        I.gx = grid_for(I.d, 128);
+        I.gy = grid_for(I.r, 8);
+        I.O_off = O_tot; O_tot += (long long)I.r * I.d;
+        I.PhiSt_off = PS_tot; PS_tot += (long long)I.rs * I.nsdof;
+        I.kij_off = kij_tot; kij_tot += I.nq;
+        I.q_off = q_tot; q_tot += 3LL * I.r;
+        I.qrec_off = qrec_tot; qrec_tot += (long long)(ctx->nsub + 1) * 3 * I.r;
+        I.ghat_off = ghat_tot; ghat_tot += (long long)(ctx->nsub + 1) * std::max(1, I.rs);
+        I.hist_off = hist_tot; hist_tot += (long long)(ctx->nsub + 1) * 3 * std::max(1, I.nsdof);
+        I.partial_off = part_tot; part_tot += (long long)I.gx * I.r;
+        B.gx_max = std::max(B.gx_max, I.gx);
+        B.gy_max = std::max(B.gy_max, I.gy);
+        B.rs_max = std::max(B.rs_max, I.rs);
+        B.r_max = std::max(B.r_max, I.r);
+        nn_tot += nn;
+        nfree_tot += G.nfree[i];
+        phi_tot += (long long)G.nfree[i] * I.r;
+    }
+    double* O = ctx->alloc<double>(O_tot);
+    double* PhiSt = ctx->alloc<double>(std::max(1LL, PS_tot));
+    short2* kij = ctx->alloc<short2>(std::max(1LL, kij_tot));
+    CKA(O); CKA(PhiSt); CKA(kij);
+    CKA(B.q = ctx->alloc<double>(q_tot));
+    CKA(B.sq = ctx->alloc<double>(q_tot));
+    CKA(B.pq = ctx->alloc<double>(q_tot));
+    CKA(B.qrec = ctx->alloc<double>(qrec_tot));
+    CKA(B.ghat = ctx->alloc<double>(ghat_tot));
+    CKA(B.hist = ctx->alloc<double>(hist_tot));
+    CKA(B.partial = ctx->alloc<double>(part_tot));
+    CKA(B.counter = ctx->alloc<unsigned int>(n));
+    CKA(B.npart = ctx->alloc<double>(2LL * n));
+    double* PhiAll = ctx->alloc<double>(std::max(1LL, phi_tot));
+    int* fdAll = ctx->alloc<int>(std::max(1LL, nfree_tot));
+    int* dfAll = ctx->alloc<int>(3 * nn_tot);
+    uint8_t* clAll = ctx->alloc<uint8_t>(nn_tot);
+    int* srAll = ctx->alloc<int>(nn_tot);
+    double* uv = ctx->alloc<double>(6LL * max_nn);
+    CKA(PhiAll); CKA(fdAll); CKA(dfAll); CKA(clAll); CKA(srAll); CKA(uv);
+    G.Phi.resize(n); G.free_dof.resize(n); G.dof_free.resize(n); G.clamp_d.resize(n); G.srow_d.resize(n);
+    long long po = 0, fo = 0, no = 0;
+    for (int i = 0; i < n; ++i) {
+        const osam_subdomain_desc& d = descs[i].subdomains[s];
+        InstRom& I = G.inst[i];
+        const int nn = G.grid[i].nn();
+        G.Phi[i] = PhiAll + po;
+        G.free_dof[i] = fdAll + fo;
+        G.dof_free[i] = dfAll + 3 * no;
+        G.clamp_d[i] = clAll + no;
+        G.srow_d[i] = srAll + no;
+        RET(upload(ctx, G.Phi[i], d.Phi, sizeof(double) * G.nfree[i] * I.r));
+        RET(upload(ctx, G.free_dof[i], free_dof[i].data(), sizeof(int) * G.nfree[i]));
+        RET(upload(ctx, G.dof_free[i], dof_free[i].data(), sizeof(int) * 3 * nn));
+        RET(upload(ctx, G.clamp_d[i], G.clamp[i].data(), nn));
+        RET(upload(ctx, G.srow_d[i], G.srow[i].data(), sizeof(int) * nn));
+        po += (long long)G.nfree[i] * I.r;
+        fo += G.nfree[i];
+        no += nn;
+        std::vector<double> K, Hh, Bh, c, Op((size_t)I.r * I.d);
+        RET(to_host(ctx, K, d.K, (size_t)I.r * I.r));
+        RET(to_host(ctx, Hh, d.H, (size_t)I.r * I.nq));
+        if (I.rs) RET(to_host(ctx, Bh, d.B, (size_t)I.r * I.rs));
+        RET(to_host(ctx, c, d.c, (size_t)I.r));
+        for (int row = 0; row < I.r; ++row) {
+            double* o = Op.data() + (size_t)row * I.d;
+            std::copy(K.begin() + (size_t)row * I.r, K.begin() + (size_t)(row + 1) * I.r, o);
+            std::copy(Hh.begin() + (size_t)row * I.nq, Hh.begin() + (size_t)(row + 1) * I.nq, o + I.r);
+            if (I.rs) std::copy(Bh.begin() + (size_t)row * I.rs, Bh.begin() + (size_t)(row + 1) * I.rs, o + I.r + I.nq);
+            o[I.d - 1] = c[row];
+        }
+        RET(upload(ctx, O + I.O_off, Op.data(), sizeof(double) * Op.size()));
+        std::vector<double> PSt;
+        if (I.rs) {
+            std::vector<double> PS;
+            PSt.resize((size_t)I.rs * I.nsdof);
+            RET(to_host(ctx, PS, d.Phi_S, (size_t)I.nsdof * I.rs));
+            for (int m = 0; m < I.nsdof; ++m)
+                for (int k = 0; k < I.rs; ++k) PSt[(size_t)k * I.nsdof + m] = PS[(size_t)m * I.rs + k];
+            RET(upload(ctx, PhiSt + I.PhiSt_off, PSt.data(), sizeof(double) * PSt.size()));
+        }
+        std::vector<short2> kk(std::max(1, I.nq));
+        int t = 0;
+        for (int a = 0; a < I.r; ++a)
+            for (int b = a; b < I.r; ++b) kk[t++] = make_short2((short)a, (short)b);
+        RET(upload(ctx, kij + I.kij_off, kk.data(), sizeof(short2) * I.nq));
+        // q0 = Phi^T u0, qd0 = Phi^T v0 over the free dofs
+        RET(upload(ctx, uv, d.u0, sizeof(double) * 3 * nn));
+        if (d.v0) RET(upload(ctx, uv + 3LL * nn, d.v0, sizeof(double) * 3 * nn));
+        CK(launch_rom_basis_project(G.nfree[i], I.r, G.Phi[i], G.free_dof[i], uv, d.v0 ? uv + 3LL * nn : nullptr,
+                                    B.q + I.q_off, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));  // host staging buffers and uv are reused
+    }
+    B.O = O;
+    B.PhiSt = PhiSt;
+    B.kij = kij;
+    CKA(G.inst_d = ctx->alloc<InstRom>(n));
+    RET(upload(ctx, G.inst_d, G.inst.data(), sizeof(InstRom) * n));
+    B.inst = G.inst_d;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int setup_couplings(osam_ctx* ctx, int n, const osam_problem_desc* descs,
+                    const std::vector<std::vector<std::vector<uint8_t>>>& masks) {
+    const int ncpl = descs[0].n_couplings;
+    ctx->cpls.resize(ncpl);
+    for (int k = 0; k < ncpl; ++k) {
+        CplH& C = ctx->cpls[k];
+        C.dst = descs[0].couplings[k].dst;
+        C.src = descs[0].couplings[k].src;
+        Slot& dst = ctx->slots[C.dst];
+        Slot& src = ctx->slots[C.src];
+        const bool dst_rom = dst.kind == OSAM_ROM, src_rom = src.kind == OSAM_ROM;
+        std::vector<int> rinst, row, dnode_all, srcnode_local;
+        std::vector<double> dw_all;
+        std::vector<long long> rec_off(n), Rt_off(n), dst_hist_off(n);
+        std::vector<int> dst_nd(n);
+        C.nrow.assign(n, 0);
+        C.row_first.assign(n, 0);
+        long long rec_tot = 0, Rt_tot = 0;
+        int* dn = nullptr;
+        int* dnode_tmp = nullptr;
+        double* dw_tmp = nullptr;
+        size_t cap = 0;
+        for (int i = 0; i < n; ++i) {
+            const Grid& gd = dst_rom ? dst.rom.grid[i] : dst.fom.grid[i];
+            const Grid& gs = src_rom ? src.rom.grid[i] : src.fom.grid[i];
+            const std::vector<int>& srow_dst = dst_rom ? dst.rom.srow[i] : dst.fom.srow[i];
+            std::vector<int> nodes;
+            for (int nd = 0; nd < gd.nn(); ++nd)
+                if (masks[i][k][nd]) nodes.push_back(nd);
+            const int nr = (int)nodes.size();
+            C.nrow[i] = nr;
+            C.row_first[i] = (int)rinst.size();
+            if (nodes.size() > cap) {
+                cap = nodes.size();
+                CKA(dn = ctx->alloc<int>(cap));
+                CKA(dnode_tmp = ctx->alloc<int>(8 * cap));
+                CKA(dw_tmp = ctx->alloc<double>(8 * cap));
+            }
+            std::vector<int> dnl(8 * nr);
+            std::vector<double> dwl(8 * nr);
+            if (nr) {
+                RET(upload(ctx, dn, nodes.data(), sizeof(int) * nr));
+                CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
+                CK(launch_donor(gs, gd, dn, nr, dnode_tmp, dw_tmp, ctx->err_d, ctx->stream));
+                int nerr = 0;
+                CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaMemcpyAsync(dnl.data(), dnode_tmp, sizeof(int) * 8 * nr, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaMemcpyAsync(dwl.data(), dw_tmp, sizeof(double) * 8 * nr, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                if (nerr)
+                    return ctx->fail(OSAM_EDONOR, "instance %d coupling %d (%d <- %d): %d Schwarz nodes have no donor element",
+                                     i, k, C.dst, C.src, nerr);
+            }
+            const long long src_off = src_rom ? 0 : src.fom.inst[i].node_off;
+            for (int t = 0; t < nr; ++t) {
+                rinst.push_back(i);
+                row.push_back(srow_dst[nodes[t]]);
+                for (int b = 0; b < 8; ++b) {
+                    dnode_all.push_back((int)(src_off + dnl[8 * t + b]));
+                    srcnode_local.push_back(dnl[8 * t + b]);
+                    dw_all.push_back(dwl[8 * t + b]);
+                }
+            }
+            rec_off[i] = rec_tot;
+            rec_tot += (long long)(ctx->nsub + 1) * 9 * nr;
+            if (src_rom) {
+                Rt_off[i] = Rt_tot;
+                Rt_tot += (long long)src.rom.inst[i].r * 3 * nr;
+            }
+            dst_hist_off[i] = dst_rom ? dst.rom.inst[i].hist_off : dst.fom.inst[i].hist_off;
+            dst_nd[i] = dst_rom ? dst.rom.inst[i].nsdof : dst.fom.inst[i].ns;
+        }
+        const int R = (int)rinst.size();
+        CplB& B = C.d;
+        B.R = R;
+        B.dst_rom = dst_rom;
+        B.dst_hist = dst_rom ? dst.rom.d.hist : dst.fom.d.hist;
+        int* d_rinst = ctx->alloc<int>(R);
+        int* d_row = ctx->alloc<int>(R);
+        int* d_dnode = ctx->alloc<int>(8LL * R);
+        double* d_dw = ctx->alloc<double>(8LL * R);
+        int* d_first = ctx->alloc<int>(n);
+        int* d_nrow = ctx->alloc<int>(n);
+        long long* d_recoff = ctx->alloc<long long>(n);
+        long long* d_rtoff = ctx->alloc<long long>(n);
+        long long* d_dho = ctx->alloc<long long>(n);
+        int* d_dnd = ctx->alloc<int>(n);
+        CKA(d_rinst); CKA(d_row); CKA(d_dnode); CKA(d_dw); CKA(d_first); CKA(d_nrow); CKA(d_recoff); CKA(d_rtoff);
+        CKA(d_dho); CKA(d_dnd);
+        RET(upload(ctx, d_rinst, rinst.data(), sizeof(int) * R));
+        RET(upload(ctx, d_row, row.data(), sizeof(int) * R));
+        RET(upload(ctx, d_dnode, dnode_all.data(), sizeof(int) * 8 * R));
+        RET(upload(ctx, d_dw, dw_all.data(), sizeof(double) * 8 * R));
+        RET(upload(ctx, d_first, C.row_first.data(), sizeof(int) * n));
+        RET(upload(ctx, d_nrow, C.nrow.data(), sizeof(int) * n));
+        RET(upload(ctx, d_recoff, rec_off.data(), sizeof(long long) * n));
+        RET(upload(ctx, d_rtoff, Rt_off.data(), sizeof(long long) * n));
+        RET(upload(ctx, d_dho, dst_hist_off.data(), sizeof(long long) * n));
+        RET(upload(ctx, d_dnd, dst_nd.data(), sizeof(int) * n));
+        B.rinst = d_rinst; B.row = d_row; B.dnode = d_dnode; B.dw = d_dw; B.row_first = d_first; B.nrow = d_nrow;
+        B.rec_off = d_recoff; B.Rt_off = d_rtoff; B.dst_hist_off = d_dho; B.dst_nd = d_dnd;
+        if (!src_rom) {
+            CKA(B.rec = ctx->alloc<double>(std::max(1LL, rec_tot)));
+        } else {
+            double* Rt = ctx->alloc<double>(std::max(1LL, Rt_tot));
+            int* dloc = ctx->alloc<int>(8LL * std::max(1, R));
+            CKA(Rt); CKA(dloc);
+            RET(upload(ctx, dloc, srcnode_local.data(), sizeof(int) * 8 * R));
+            CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
+            for (int i = 0; i < n; ++i) {
+                const int f = C.row_first[i];
+                CK(launch_build_Rt(C.nrow[i], src.rom.inst[i].r, dloc + 8LL * f, d_dw + 8LL * f, src.rom.dof_free[i],
+                                   src.rom.srow_d[i], src.rom.Phi[i], Rt + Rt_off[i], ctx->err_d, ctx->stream));
+            }
+            int nerr = 0;
+            CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (nerr)
+                return ctx->fail(OSAM_EINVAL, "coupling %d: a donor node with nonzero weight is a Schwarz node of ROM %d", k,
+                                 C.src);
+            B.Rt = Rt;
+        }
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    std::vector<short2> kij(std::max(1, R.nq));
-    int t = 0;
-    for (int i = 0; i < R.r; ++i)
-        for (int j = i; j < R.r; ++j) kij[t++] = make_short2((short)i, (short)j);
-    CKA(R.kron_ij = ctx->alloc<short2>(kij.size()));
-    if (int r = upload(ctx, R.kron_ij, kij.data(), sizeof(short2) * kij.size())) return r;
-    CKA(R.q = ctx->alloc<double>(3 * R.r));
-    CKA(R.sq = ctx->alloc<double>(3 * R.r));
-    CKA(R.pq = ctx->alloc<double>(3 * R.r));
-    CKA(R.qrec = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 3 * R.r));
-    CKA(R.ghat = ctx->alloc<double>((size_t)(ctx->nsub + 1) * std::max(1, R.rs)));
-    CKA(R.hist = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 3 * std::max(1, R.nsdof)));
-    R.step_gx = grid_for(R.d, 128);
-    R.step_gy = grid_for(R.r, 8);
-    CKA(R.partial = ctx->alloc<double>((size_t)R.step_gx * R.r));
-    CKA(R.counter = ctx->alloc<unsigned int>(1));
-    // q0 = Phi^T u0, qd0 = Phi^T v0 over the free dofs (u0, v0 interleaved, clamped parts ignored)
-    double* uv = ctx->alloc<double>(6LL * nn);
-    CKA(uv);
-    if (int r = upload(ctx, uv, d.u0, sizeof(double) * 3 * nn)) return r;
-    if (d.v0) { if (int r = upload(ctx, uv + 3LL * nn, d.v0, sizeof(double) * 3 * nn)) return r; }
-    CK(launch_rom_basis_project(R, uv, d.v0 ? uv + 3LL * nn : nullptr, ctx->stream));
     return OSAM_OK;
+}
+
+int setup_controller(osam_ctx* ctx) {
+    const int n = ctx->n_inst;
+    CtlB& c = ctx->ctl;
+    c.n_inst = n;
+    c.ncpl = (int)ctx->cpls.size();
+    c.max_it = ctx->max_it;
+    c.tol_abs2 = ctx->tol_abs * ctx->tol_abs;
+    c.tol_rel2 = ctx->tol_rel * ctx->tol_rel;
+    c.n_fom = c.n_rom = 0;
+    for (Slot& S : ctx->slots) {
+        if (S.kind == OSAM_FOM) {
+            c.fom_partial[c.n_fom] = S.fom.d.partial;
+            c.fom_blk_off[c.n_fom] = S.fom.d.nblk_off;
+            ++c.n_fom;
+        } else {
+            c.rom_npart[c.n_rom] = S.rom.d.npart;
+            ++c.n_rom;
+        }
+    }
+    CKA(c.active = ctx->alloc<int>(n));
+    CKA(c.iters = ctx->alloc<int>(n));
+    CKA(c.status = ctx->alloc<int>(n));
+    CKA(c.cnum = ctx->alloc<double>(n));
+    CKA(c.cden = ctx->alloc<double>(n));
+    CKA(c.counter = ctx->alloc<unsigned int>(1));
+    CKA(c.any_active = ctx->alloc<int>(1));
+    CKA(ctx->sel = ctx->alloc<int>(n));
+    CK(cudaMallocHost(&ctx->iters_h, sizeof(int) * n));
+    CK(cudaMallocHost(&ctx->status_h, sizeof(int) * n));
+    CK(cudaMallocHost(&ctx->cnum_h, sizeof(double) * n));
+    CK(cudaMallocHost(&ctx->cden_h, sizeof(double) * n));
+    CK(cudaMallocHost(&ctx->any_h, sizeof(int)));
+    return OSAM_OK;
+}
+
+int select_instance(osam_ctx* ctx, int inst) {
+    std::vector<int> sel(ctx->n_inst, 0);
+    sel[inst] = 1;
+    RET(upload(ctx, ctx->sel, sel.data(), sizeof(int) * ctx->n_inst));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+// initial accelerations of the instances selected by `mask` (null = all)
+int initial_accel(osam_ctx* ctx, const int* mask) {
+    for (Slot& S : ctx->slots) {
+        if (S.kind == OSAM_FOM) {
+            CK(launch_force_init_b(S.fom.d, mask, ctx->stream));
+            CK(launch_init_accel_b(S.fom.d, mask, ctx->stream));
+        } else {
+            CK(launch_rom_project_b(S.rom.d, mask, 0, 0, ctx->stream));
+            CK(launch_rom_step_b(S.rom.d, mask, 0, ctx->dt, 1, ctx->stream));
+        }
+    }
+    return OSAM_OK;
+}
+
+// time force + node kernels of the largest FOM group for (element block, scatter) candidates on
+// scratch copies of its state; keep the fastest (the deterministic gather scatter unless atomics are
+// more than 5% faster)
+int autotune(osam_ctx* ctx) {
+    FomGroupH* best_g = nullptr;
+    long long ne = -1;
+    for (Slot& S : ctx->slots)
+        if (S.kind == OSAM_FOM && S.fom.d.NE > ne) { ne = S.fom.d.NE; best_g = &S.fom; }
+    if (!best_g) return OSAM_OK;
+    FomGroupH& G = *best_g;
+    FomB g = G.d;
+    const long long NN = g.NN;
+    double *u = nullptr, *v = nullptr, *a = nullptr, *un = nullptr;
+    CK(cudaMalloc(&u, sizeof(double) * 3 * NN));
+    CK(cudaMalloc(&v, sizeof(double) * 3 * NN));
+    CK(cudaMalloc(&a, sizeof(double) * 3 * NN));
+    CK(cudaMalloc(&un, sizeof(double) * 3 * NN));
+    CK(cudaMemcpyAsync(u, G.d.u[0], sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(v, G.d.v, sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(a, G.d.a, sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
+    g.v = v;
+    g.a = a;
+    const int slot2 = std::min(2, ctx->nsub);
+    float best_ms = 1e30f, gather_ms = 1e30f;
+    int best_block = 128, best_scatter = kGather;
+    const int cands[6][2] = {{kGather, 64}, {kGather, 128}, {kGather, 256}, {kAtomic, 64}, {kAtomic, 128}, {kAtomic, 256}};
+    for (const auto& cd : cands) {
+        const int mode = cd[0], block = cd[1];
+        RET(set_eblocks(ctx, G, block));
+        g.eblk = G.d.eblk;
+        g.n_eblk = G.d.n_eblk;
+        g.eblock = block;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
+            CK(launch_force_b(g, nullptr, u, mode, block, ctx->stream));
+            CK(launch_node_b(g, nullptr, mode, 1, slot2, 0, u, un, ctx->dt, ctx->stream));
+        }
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (mode == kGather) {
+            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; }
+        } else if (ms < 0.95f * gather_ms && ms < best_ms) {
+            best_ms = ms; best_block = block; best_scatter = kAtomic;
+        }
+    }
+    CK(cudaMemsetAsync(G.d.f, 0, sizeof(double) * 3 * NN, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(u); cudaFree(v); cudaFree(a); cudaFree(un);
+    ctx->scatter = best_scatter;
+    for (Slot& S : ctx->slots)
+        if (S.kind == OSAM_FOM) RET(set_eblocks(ctx, S.fom, best_block));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
+    if (n < 1 || !descs) return ctx->fail(OSAM_EINVAL, "no instances");
+    RET(validate_topology(ctx, n, descs));
+    const osam_problem_desc& d0 = descs[0];
+    RET(check_device(ctx, d0.device));
+    ctx->device = d0.device;
+    if (d0.stream) ctx->stream = static_cast<cudaStream_t>(d0.stream);
+    else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    ctx->n_inst = n;
+    ctx->dt = d0.dt;
+    ctx->nsub = d0.n_substeps;
+    ctx->tol_abs = d0.tol_abs;
+    ctx->tol_rel = d0.tol_rel;
+    ctx->max_it = d0.max_iters;
+    ctx->precision = d0.precision;
+    ctx->scatter = d0.scatter == OSAM_SCATTER_ATOMIC ? kAtomic : kGather;
+    CK(cudaEventCreate(&ctx->ev0));
+    CK(cudaEventCreate(&ctx->ev1));
+    CKA(ctx->err_d = ctx->alloc<int>(1));
+    const int nsd = d0.n_subdomains, ncpl = d0.n_couplings;
+    ctx->slots.resize(nsd);
+    ctx->fom_elements.assign(n, 0);
+    // masks, Schwarz rows (union over the couplings into a subdomain, increasing node order)
+    std::vector<std::vector<std::vector<uint8_t>>> masks(n, std::vector<std::vector<uint8_t>>(ncpl));
+    int max_nn = 1;
+    for (int s = 0; s < nsd; ++s) ctx->slots[s].kind = d0.subdomains[s].kind;
+    for (int i = 0; i < n; ++i) {
+        const osam_problem_desc& d = descs[i];
+        for (int s = 0; s < nsd; ++s) {
+            const osam_subdomain_desc& sd = d.subdomains[s];
+            Grid g;
+            g.nx = sd.nx; g.ny = sd.ny; g.nz = sd.nz; g.h = sd.h;
+            for (int a = 0; a < 3; ++a) g.org[a] = sd.origin[a];
+            const int nn = g.nn();
+            max_nn = std::max(max_nn, nn);
+            std::vector<uint8_t> clamp(nn, 0);
+            if (sd.dirichlet) CK(cudaMemcpy(clamp.data(), sd.dirichlet, nn, cudaMemcpyDefault));
+            for (auto& c : clamp) c &= 7;
+            Slot& S = ctx->slots[s];
+            if (S.kind == OSAM_FOM) {
+                S.fom.grid.push_back(g);
+                S.fom.clamp.push_back(clamp);
+                ctx->fom_elements[i] += g.ne();
+            } else {
+                S.rom.grid.push_back(g);
+                S.rom.clamp.push_back(clamp);
+            }
+        }
+        for (int k = 0; k < ncpl; ++k) {
+            const osam_coupling_desc& c = d.couplings[k];
+            const Slot& S = ctx->slots[c.dst];
+            const int nn = (S.kind == OSAM_FOM ? S.fom.grid[i] : S.rom.grid[i]).nn();
+            masks[i][k].resize(nn);
+            CK(cudaMemcpy(masks[i][k].data(), c.nodes, nn, cudaMemcpyDefault));
+        }
+        for (int s = 0; s < nsd; ++s) {
+            Slot& S = ctx->slots[s];
+            const int nn = (S.kind == OSAM_FOM ? S.fom.grid[i] : S.rom.grid[i]).nn();
+            std::vector<int> srow(nn, -1);
+            int ns = 0;
+            for (int nd = 0; nd < nn; ++nd) {
+                bool any = false;
+                for (int k = 0; k < ncpl; ++k)
+                    if (d.couplings[k].dst == s && masks[i][k][nd]) any = true;
+                if (any) srow[nd] = ns++;
+            }
+            if (S.kind == OSAM_FOM) { S.fom.srow.push_back(srow); S.fom.ns.push_back(ns); }
+            else { S.rom.srow.push_back(srow); S.rom.ns.push_back(ns); }
+        }
+    }
+    CKA(ctx->scratch = ctx->alloc<double>(3LL * max_nn));
+    for (int s = 0; s < nsd; ++s) {
+        Slot& S = ctx->slots[s];
+        if (S.kind == OSAM_FOM) RET(setup_fom_group(ctx, S.fom, s, n, descs));
+        else RET(setup_rom_group(ctx, S.rom, s, n, descs));
+    }
+    RET(setup_couplings(ctx, n, descs, masks));
+    RET(setup_controller(ctx));
+    // initial boundary data: zero-order hold of the initial states (before the accelerations)
+    for (CplH& c : ctx->cpls) RET(zoh_cpl(ctx, c, nullptr));
+    RET(initial_accel(ctx, nullptr));
+    if (d0.scatter == OSAM_SCATTER_AUTO) RET(autotune(ctx));
+    for (Slot& S : ctx->slots)
+        if (S.kind == OSAM_FOM) S.fom.d.scatter = ctx->scatter;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->launches = 0;
+    return OSAM_OK;
+}
+
+bool valid(osam_ctx* ctx, int inst, int sub) {
+    return ctx && inst >= 0 && inst < ctx->n_inst && sub >= 0 && sub < (int)ctx->slots.size();
 }
 
 }  // namespace
-
-namespace osam {
-void set_thread_error(const std::string& msg) { g_init_error = msg; }
-}  // namespace osam
 
 extern "C" {
 
@@ -474,16 +1009,33 @@ const char* osam_last_error(const osam_ctx* ctx) {
 
 int osam_scatter_mode(osam_ctx* ctx) { return ctx ? ctx->scatter : 0; }
 
+int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block) {
+    if (!ctx) return OSAM_EINVAL;
+    if (scatter) *scatter = ctx->scatter;
+    if (element_block) {
+        *element_block = 0;
+        for (Slot& S : ctx->slots)
+            if (S.kind == OSAM_FOM) *element_block = S.fom.d.eblock;
+    }
+    return OSAM_OK;
+}
+
+int osam_num_instances(osam_ctx* ctx) { return ctx ? ctx->n_inst : 0; }
+
+int osam_set_graph(osam_ctx* ctx, int enable) {
+    if (!ctx) return OSAM_EINVAL;
+    ctx->use_graph = enable != 0;
+    return OSAM_OK;
+}
+
 void osam_destroy(osam_ctx* ctx) { delete ctx; }
 
-static int init_impl(osam_ctx* ctx, const osam_problem_desc* desc);
-
-int schwarz_init(const osam_problem_desc* desc, osam_ctx** out) {
+int osam_batch_init(int n_instances, const osam_problem_desc* descs, osam_ctx** out) {
     if (out) *out = nullptr;
     g_init_error.clear();
-    if (!desc || !out) { g_init_error = "null argument"; return OSAM_EINVAL; }
+    if (!descs || !out || n_instances < 1) { g_init_error = "null argument"; return OSAM_EINVAL; }
     auto* ctx = new osam_ctx();
-    int rc = init_impl(ctx, desc);
+    int rc = init_impl(ctx, n_instances, descs);
     if (rc != OSAM_OK) {
         g_init_error = ctx->err;
         delete ctx;
@@ -493,205 +1045,119 @@ int schwarz_init(const osam_problem_desc* desc, osam_ctx** out) {
     return OSAM_OK;
 }
 
-static int autotune_scatter(osam_ctx* ctx);
-
-static int init_impl(osam_ctx* ctx, const osam_problem_desc* desc) {
-    if (int r = check_device(ctx, desc->device)) return r;
-    ctx->device = desc->device;
-    if (desc->stream) ctx->stream = static_cast<cudaStream_t>(desc->stream);
-    else {
-        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
-        ctx->own_stream = true;
-    }
-    if (desc->n_subdomains < 1 || !desc->subdomains) return ctx->fail(OSAM_EINVAL, "no subdomains");
-    if (desc->n_couplings < 0 || (desc->n_couplings > 0 && !desc->couplings)) return ctx->fail(OSAM_EINVAL, "bad couplings");
-    if (!(desc->dt > 0.0) || desc->n_substeps < 1 || desc->max_iters < 1)
-        return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
-    if (desc->precision != OSAM_FP64 && desc->precision != OSAM_FP32_FORCE) return ctx->fail(OSAM_EINVAL, "bad precision");
-    ctx->dt = desc->dt;
-    ctx->nsub = desc->n_substeps;
-    ctx->tol_abs = desc->tol_abs;
-    ctx->tol_rel = desc->tol_rel;
-    ctx->max_it = desc->max_iters;
-    ctx->precision = desc->precision;
-    CK(cudaEventCreate(&ctx->ev0));
-    CK(cudaEventCreate(&ctx->ev1));
-    CK(cudaMallocHost(&ctx->result_h, 3 * sizeof(double)));
-    CKA(ctx->result = ctx->alloc<double>(3));
-    CKA(ctx->err_d = ctx->alloc<int>(1));
-    const int nsd = desc->n_subdomains;
-    ctx->subs.resize(nsd);
-    int max_nn = 0;
-    for (int i = 0; i < nsd; ++i) {
-        const osam_subdomain_desc& d = desc->subdomains[i];
-        Sub& s = ctx->subs[i];
-        if (d.kind != OSAM_FOM && d.kind != OSAM_ROM) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad kind", i);
-        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !(d.h > 0.0)) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad mesh", i);
-        if ((long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1) > (1LL << 30)) return ctx->fail(OSAM_EINVAL, "subdomain %d too large", i);
-        if (!d.u0) return ctx->fail(OSAM_EINVAL, "subdomain %d: u0 required", i);
-        if (d.kind == OSAM_FOM) {
-            if (d.material != OSAM_LINEAR_ELASTIC && d.material != OSAM_NEO_HOOKEAN) return ctx->fail(OSAM_EINVAL, "subdomain %d: bad material", i);
-            if (!(d.rho > 0.0)) return ctx->fail(OSAM_EINVAL, "subdomain %d: rho must be positive", i);
-        }
-        s.kind = d.kind;
-        s.g.nx = d.nx; s.g.ny = d.ny; s.g.nz = d.nz; s.g.h = d.h;
-        for (int a = 0; a < 3; ++a) s.g.org[a] = d.origin[a];
-        const int nn = s.g.nn();
-        max_nn = std::max(max_nn, nn);
-        s.clamp_h.assign(nn, 0);
-        if (d.dirichlet) {
-            std::vector<uint8_t> tmp;
-            CK(cudaMemcpy(s.clamp_h.data(), d.dirichlet, nn, cudaMemcpyDefault));
-        }
-        for (int n = 0; n < nn; ++n) s.clamp_h[n] &= 7;
-        s.srow_h.assign(nn, -1);
-        if (s.kind == OSAM_FOM) ctx->fom_elements += s.g.ne();
-    }
-    // couplings: masks -> Schwarz rows (union, increasing node order) -> donor search
-    std::vector<std::vector<uint8_t>> masks(desc->n_couplings);
-    for (int k = 0; k < desc->n_couplings; ++k) {
-        const osam_coupling_desc& c = desc->couplings[k];
-        if (c.dst < 0 || c.dst >= nsd || c.src < 0 || c.src >= nsd || c.dst == c.src || !c.nodes)
-            return ctx->fail(OSAM_EINVAL, "coupling %d: bad indices", k);
-        masks[k].resize(ctx->subs[c.dst].g.nn());
-        CK(cudaMemcpy(masks[k].data(), c.nodes, masks[k].size(), cudaMemcpyDefault));
-    }
-    for (int i = 0; i < nsd; ++i) {
-        Sub& s = ctx->subs[i];
-        int ns = 0;
-        for (int n = 0; n < s.g.nn(); ++n) {
-            bool any = false;
-            for (int k = 0; k < desc->n_couplings; ++k)
-                if (desc->couplings[k].dst == i && masks[k][n]) any = true;
-            if (any) s.srow_h[n] = ns++;
-        }
-        s.ns = ns;
-    }
-    CKA(ctx->scratch = ctx->alloc<double>(3LL * max_nn));
-    for (int i = 0; i < nsd; ++i) {
-        Sub& s = ctx->subs[i];
-        const osam_subdomain_desc& d = desc->subdomains[i];
-        int rc = s.kind == OSAM_FOM ? setup_fom(ctx, s, d) : setup_rom(ctx, s, d);
-        if (rc) return rc;
-    }
-    ctx->cpls.resize(desc->n_couplings);
-    for (int k = 0; k < desc->n_couplings; ++k) {
-        const osam_coupling_desc& cd = desc->couplings[k];
-        CplDev& c = ctx->cpls[k];
-        c.dst = cd.dst; c.src = cd.src;
-        Sub& dst = ctx->subs[cd.dst];
-        Sub& src = ctx->subs[cd.src];
-        std::vector<int> nodes, rows;
-        for (int n = 0; n < dst.g.nn(); ++n)
-            if (masks[k][n]) { nodes.push_back(n); rows.push_back(dst.srow_h[n]); }
-        c.nrow = (int)nodes.size();
-        CKA(c.row = ctx->alloc<int>(c.nrow));
-        CKA(c.dnode = ctx->alloc<int>(8LL * c.nrow));
-        CKA(c.dw = ctx->alloc<double>(8LL * c.nrow));
-        int* dn = ctx->alloc<int>(c.nrow);
-        CKA(dn);
-        if (int r = upload(ctx, c.row, rows.data(), sizeof(int) * c.nrow)) return r;
-        if (int r = upload(ctx, dn, nodes.data(), sizeof(int) * c.nrow)) return r;
-        CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
-        CK(launch_donor(src.g, dst.g, nullptr, dn, c.nrow, c.dnode, c.dw, ctx->err_d, ctx->stream));
-        int nerr = 0;
-        CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
-        if (nerr) return ctx->fail(OSAM_EDONOR, "coupling %d (%d <- %d): %d Schwarz nodes have no donor element", k, cd.dst, cd.src, nerr);
-        if (src.kind == OSAM_FOM) {
-            CKA(c.rec = ctx->alloc<double>((size_t)(ctx->nsub + 1) * 9 * std::max(1, c.nrow)));
-        } else {
-            CKA(c.Rt = ctx->alloc<double>((size_t)src.rom.r * 3 * std::max(1, c.nrow)));
-            CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->stream));
-            CK(launch_build_Rt_checked(c, src.rom, ctx->err_d, ctx->stream));
-            CK(cudaMemcpyAsync(&nerr, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            if (nerr) return ctx->fail(OSAM_EINVAL, "coupling %d: a donor node with nonzero weight is a Schwarz node of ROM %d", k, cd.src);
-        }
-    }
-    // criterion partial sums
-    int nparts = 0;
-    for (Sub& s : ctx->subs) nparts += s.kind == OSAM_FOM ? s.fom.norm_blocks : 1;
-    ctx->nparts = nparts;
-    CKA(ctx->partial = ctx->alloc<double>(2LL * nparts));
-    // initial boundary data: zero-order hold of every source's initial state (before accelerations)
-    for (CplDev& c : ctx->cpls)
-        if (int r = zoh(ctx, c)) return r;
-    for (Sub& s : ctx->subs) {
-        if (s.kind == OSAM_FOM) {
-            if (int r = fom_initial_accel(ctx, s)) return r;
-        } else {
-            CK(launch_rom_project(s.rom, 0, 0, ctx->stream));
-            CK(launch_rom_step(s.rom, 0, ctx->dt, 1, ctx->stream));
-        }
-    }
-    ctx->scatter = desc->scatter == OSAM_SCATTER_ATOMIC ? kAtomic : kGather;
-    if (desc->scatter == OSAM_SCATTER_AUTO && ctx->fom_elements > 0)
-        if (int r = autotune_scatter(ctx)) return r;
-    CK(cudaStreamSynchronize(ctx->stream));
-    return OSAM_OK;
-}
-
-// time the force + node kernels of the largest FOM in both scatter modes on scratch copies
-static int autotune_scatter(osam_ctx* ctx) {
-    int best = -1;
-    long long ne = -1;
-    for (int i = 0; i < (int)ctx->subs.size(); ++i)
-        if (ctx->subs[i].kind == OSAM_FOM && ctx->subs[i].g.ne() > ne) { ne = ctx->subs[i].g.ne(); best = i; }
-    Sub& s = ctx->subs[best];
-    FomDev F = s.fom;  // shallow copy pointing at scratch state below
-    const int nn = s.g.nn();
-    const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
-    double *u = nullptr, *v = nullptr, *a = nullptr, *un = nullptr;
-    CK(cudaMalloc(&u, sizeof(double) * 3 * nn));
-    CK(cudaMalloc(&v, sizeof(double) * 3 * nn));
-    CK(cudaMalloc(&a, sizeof(double) * 3 * nn));
-    CK(cudaMalloc(&un, sizeof(double) * 3 * nn));
-    CK(cudaMemcpyAsync(u, s.fom.u[0], sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(v, s.fom.v, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(a, s.fom.a, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, ctx->stream));
-    F.v = v; F.a = a;
-    float best_ms = 1e30f;
-    int best_mode = kGather;
-    for (int mode : {kGather, kAtomic}) {
-        for (int rep = 0; rep < 4; ++rep) {
-            if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
-            ElemArgs ea = elem_args(F, u, 1, nn);
-            if (fp32 && mode == kAtomic) ea.f = F.fe;
-            CK(launch_hex8_force(F.material, fp32, mode, ea, ctx->stream));
-            NodeArgs na = node_args(ctx, s);
-            na.v = v; na.a = a;
-            if (fp32 && mode == kAtomic) na.fclear = F.fe;
-            na.ucur = u; na.unext = un;
-            na.h1 = fom_slot(ctx, s, 1);
-            na.h2 = fom_slot(ctx, s, std::min(2, ctx->nsub));
-            na.last = 0;
-            CK(launch_node_update(fp32, mode, na, ctx->stream));
-        }
-        CK(cudaEventRecord(ctx->ev1, ctx->stream));
-        CK(cudaEventSynchronize(ctx->ev1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-        // the deterministic gather scatter is kept unless atomics are clearly (> 5%) faster
-        if (mode == kGather) { best_ms = ms; best_mode = kGather; }
-        else if (ms < 0.95f * best_ms) { best_ms = ms; best_mode = kAtomic; }
-    }
-    // the atomic buffers must be clean after the trial
-    CK(cudaMemsetAsync(s.fom.f, 0, sizeof(double) * 3 * nn, ctx->stream));
-    if (fp32) CK(cudaMemsetAsync(s.fom.fe, 0, sizeof(float) * 3 * nn, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(u); cudaFree(v); cudaFree(a); cudaFree(un);
-    ctx->scatter = best_mode;
-    return OSAM_OK;
-}
+int schwarz_init(const osam_problem_desc* desc, osam_ctx** out) { return osam_batch_init(1, desc, out); }
 
 int subdomain_advance(osam_ctx* ctx, int sub) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
-    int r = ctx->subs[sub].kind == OSAM_FOM ? advance_fom(ctx, sub) : advance_rom(ctx, sub);
-    if (r) return r;
+    if (!valid(ctx, 0, sub)) return OSAM_EINVAL;
+    RET(advance_slot(ctx, sub, nullptr));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->prof_collect();
     return OSAM_OK;
+}
+
+int transfer_overlap(osam_ctx* ctx, int src, int dst) {
+    if (!ctx) return OSAM_EINVAL;
+    bool any = false;
+    for (CplH& c : ctx->cpls)
+        if (c.src == src && c.dst == dst) {
+            any = true;
+            RET(transfer_cpl(ctx, c, nullptr));
+        }
+    if (!any) return ctx->fail(OSAM_EINVAL, "no coupling %d -> %d", src, dst);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_begin_interval(osam_ctx* ctx) {
+    if (!ctx) return OSAM_EINVAL;
+    RET(enqueue_begin(ctx));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_restore_interval(osam_ctx* ctx) {
+    if (!ctx) return OSAM_EINVAL;
+    RET(saverest_all(ctx, nullptr, 1));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_criterion(osam_ctx* ctx, double* cnum, double* cden) {
+    if (!ctx) return OSAM_EINVAL;
+    LK(launch_reset_ctl(ctx->ctl, ctx->stream));
+    RET(norms_all(ctx, nullptr));
+    LK(launch_controller(ctx->ctl, ctx->cond, 0, ctx->stream));
+    RET(read_ctl(ctx));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (cnum) *cnum = ctx->cnum_h[0];
+    if (cden) *cden = ctx->cden_h[0];
+    if (ctx->status_h[0] == OSAM_ENONFINITE) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state");
+    return OSAM_OK;
+}
+
+int osam_batch_step(osam_ctx* ctx, osam_step_report* reps, osam_step_report* total) {
+    if (!ctx) return OSAM_EINVAL;
+    const bool graph = ctx->use_graph && !ctx->prof;
+    if (graph) RET(build_graph(ctx));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (graph) {
+        CK(cudaGraphLaunch(ctx->exec, ctx->stream));
+    } else {
+        RET(enqueue_begin(ctx));
+        for (int n = 1; n <= ctx->max_it; ++n) {
+            RET(enqueue_iteration(ctx, 0));
+            CK(cudaMemcpyAsync(ctx->any_h, ctx->ctl.any_active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (!*ctx->any_h) break;
+        }
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    RET(read_ctl(ctx));
+    CK(cudaEventSynchronize(ctx->ev1));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_collect();
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    int worst = OSAM_OK, max_its = 0;
+    long long updates = 0;
+    for (int i = 0; i < ctx->n_inst; ++i) {
+        const int st = ctx->status_h[i];
+        if (st < 0) worst = std::min(worst, st);
+        else if (worst >= 0) worst = std::max(worst, st);
+        max_its = std::max(max_its, ctx->iters_h[i]);
+        const long long u = (long long)ctx->iters_h[i] * ctx->nsub * ctx->fom_elements[i];
+        updates += u;
+        if (reps) {
+            reps[i].status = st;
+            reps[i].iterations = ctx->iters_h[i];
+            reps[i].cnum = ctx->cnum_h[i];
+            reps[i].cden = ctx->cden_h[i];
+            reps[i].element_updates = u;
+            reps[i].elapsed_ms = ms;
+        }
+    }
+    if (graph) {
+        long long begin = 0;
+        for (Slot& S : ctx->slots) { (void)S; begin += 1; }
+        begin += (long long)ctx->cpls.size() + 1;
+        ctx->launches += begin + (long long)max_its * launches_per_iteration(ctx);
+    }
+    if (total) {
+        total->status = worst;
+        total->iterations = max_its;
+        total->cnum = ctx->cnum_h[0];
+        total->cden = ctx->cden_h[0];
+        total->element_updates = updates;
+        total->elapsed_ms = ms;
+    }
+    if (worst == OSAM_ENONFINITE) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state");
+    return worst;
+}
+
+int schwarz_step(osam_ctx* ctx, osam_step_report* rep) {
+    if (!ctx) return OSAM_EINVAL;
+    if (ctx->n_inst == 1) return osam_batch_step(ctx, rep, nullptr);
+    return osam_batch_step(ctx, nullptr, rep);
 }
 
 int osam_profile(osam_ctx* ctx, int enable) {
@@ -717,118 +1183,48 @@ int osam_profile_read(osam_ctx* ctx, double* force_ms, long long* force_launches
     return OSAM_OK;
 }
 
-int transfer_overlap(osam_ctx* ctx, int src, int dst) {
-    if (!ctx) return OSAM_EINVAL;
-    bool any = false;
-    for (CplDev& c : ctx->cpls)
-        if (c.src == src && c.dst == dst) {
-            any = true;
-            if (int r = transfer(ctx, c)) return r;
-        }
-    if (!any) return ctx->fail(OSAM_EINVAL, "no coupling %d -> %d", src, dst);
-    CK(cudaStreamSynchronize(ctx->stream));
-    return OSAM_OK;
-}
-
-int osam_begin_interval(osam_ctx* ctx) {
-    if (!ctx) return OSAM_EINVAL;
-    if (int r = save_all(ctx, false)) return r;
-    for (CplDev& c : ctx->cpls)
-        if (int r = zoh(ctx, c)) return r;
-    CK(cudaStreamSynchronize(ctx->stream));
-    return OSAM_OK;
-}
-
-int osam_restore_interval(osam_ctx* ctx) {
-    if (!ctx) return OSAM_EINVAL;
-    if (int r = save_all(ctx, true)) return r;
-    CK(cudaStreamSynchronize(ctx->stream));
-    return OSAM_OK;
-}
-
-int osam_criterion(osam_ctx* ctx, double* cnum, double* cden) {
-    if (!ctx) return OSAM_EINVAL;
-    if (int r = criterion_async(ctx)) return r;
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (cnum) *cnum = ctx->result_h[0];
-    if (cden) *cden = ctx->result_h[1];
-    if (ctx->result_h[2] != 0.0) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state");
-    return OSAM_OK;
-}
-
-int schwarz_step(osam_ctx* ctx, osam_step_report* rep) {
-    if (!ctx) return OSAM_EINVAL;
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    if (int r = save_all(ctx, false)) return r;
-    for (CplDev& c : ctx->cpls)
-        if (int r = zoh(ctx, c)) return r;
-    int status = OSAM_MAXITER, n = 1;
-    double cnum = 0.0, cden = 0.0;
-    for (n = 1; n <= ctx->max_it; ++n) {
-        if (n > 1)
-            if (int r = save_all(ctx, true)) return r;
-        for (int i = 0; i < (int)ctx->subs.size(); ++i) {
-            int r = ctx->subs[i].kind == OSAM_FOM ? advance_fom(ctx, i) : advance_rom(ctx, i);
-            if (r) return r;
-            for (CplDev& c : ctx->cpls)
-                if (c.src == i)
-                    if (int rr = transfer(ctx, c)) return rr;
-        }
-        if (int r = criterion_async(ctx)) return r;
-        CK(cudaStreamSynchronize(ctx->stream));
-        cnum = ctx->result_h[0];
-        cden = ctx->result_h[1];
-        if (ctx->result_h[2] != 0.0) return ctx->fail(OSAM_ENONFINITE, "non-finite coupled state at iteration %d", n);
-        if (ctx->cpls.empty()) { status = OSAM_OK; break; }
-        if (n >= 2 && (cnum < ctx->tol_abs * ctx->tol_abs || cnum < ctx->tol_rel * ctx->tol_rel * cden)) {
-            status = OSAM_OK;
-            break;
-        }
-    }
-    if (n > ctx->max_it) n = ctx->max_it;
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    CK(cudaEventSynchronize(ctx->ev1));
-    ctx->prof_collect();
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-    if (rep) {
-        rep->status = status;
-        rep->iterations = n;
-        rep->cnum = cnum;
-        rep->cden = cden;
-        rep->element_updates = (long long)n * ctx->nsub * ctx->fom_elements;
-        rep->elapsed_ms = ms;
-    }
-    return status;
-}
-
-int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, int* n_free, int* n_schwarz) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
-    Sub& s = ctx->subs[sub];
-    if (n_nodes) *n_nodes = s.g.nn();
-    if (n_elements) *n_elements = s.g.ne();
-    if (n_schwarz) *n_schwarz = s.ns;
+int osam_instance_sizes(osam_ctx* ctx, int inst, int sub, int* n_nodes, int* n_elements, int* n_free,
+                        int* n_schwarz) {
+    if (!valid(ctx, inst, sub)) return OSAM_EINVAL;
+    Slot& S = ctx->slots[sub];
+    const Grid& g = S.kind == OSAM_FOM ? S.fom.grid[inst] : S.rom.grid[inst];
+    const std::vector<uint8_t>& cl = S.kind == OSAM_FOM ? S.fom.clamp[inst] : S.rom.clamp[inst];
+    const std::vector<int>& sr = S.kind == OSAM_FOM ? S.fom.srow[inst] : S.rom.srow[inst];
+    if (n_nodes) *n_nodes = g.nn();
+    if (n_elements) *n_elements = g.ne();
+    if (n_schwarz) *n_schwarz = S.kind == OSAM_FOM ? S.fom.ns[inst] : S.rom.ns[inst];
     if (n_free) {
         int nf = 0;
-        for (int n = 0; n < s.g.nn(); ++n)
-            for (int c = 0; c < 3; ++c) nf += !(s.clamp_h[n] & (1 << c)) && s.srow_h[n] < 0;
+        for (int nd = 0; nd < g.nn(); ++nd)
+            for (int c = 0; c < 3; ++c) nf += !(cl[nd] & (1 << c)) && sr[nd] < 0;
         *n_free = nf;
     }
     return OSAM_OK;
 }
 
-int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size()) return OSAM_EINVAL;
-    Sub& s = ctx->subs[sub];
-    const int nn = s.g.nn();
+int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, int* n_free, int* n_schwarz) {
+    return osam_instance_sizes(ctx, 0, sub, n_nodes, n_elements, n_free, n_schwarz);
+}
+
+int osam_instance_get_state(osam_ctx* ctx, int inst, int sub, double* u, double* v, double* a) {
+    if (!valid(ctx, inst, sub)) return OSAM_EINVAL;
+    Slot& S = ctx->slots[sub];
     double* outs[3] = {u, v, a};
     for (int f = 0; f < 3; ++f) {
         if (!outs[f]) continue;
-        if (s.kind == OSAM_FOM) {
-            const double* src = f == 0 ? s.fom.u[0] : (f == 1 ? s.fom.v : s.fom.a);
-            CK(launch_soa_to_aos(src, ctx->scratch, nn, ctx->stream));
+        int nn;
+        if (S.kind == OSAM_FOM) {
+            const InstFom& I = S.fom.inst[inst];
+            nn = I.nn;
+            const double* src = f == 0 ? S.fom.d.u[0] : (f == 1 ? S.fom.d.v : S.fom.d.a);
+            CK(launch_soa_to_aos(src + I.node_off, ctx->scratch, nn, S.fom.d.NN, ctx->stream));
         } else {
-            CK(launch_rom_full_field(s.rom, s.rom.q + (long long)f * s.rom.r, f, ctx->scratch, ctx->nsub, ctx->stream));
+            RomGroupH& G = S.rom;
+            const InstRom& I = G.inst[inst];
+            nn = G.grid[inst].nn();
+            const double* hs = G.d.hist + I.hist_off + ((long long)ctx->nsub * 3 + f) * I.nsdof;
+            CK(launch_rom_full_field(nn, I.r, G.Phi[inst], G.dof_free[inst], G.clamp_d[inst], G.srow_d[inst], hs,
+                                     G.d.q + I.q_off + (long long)f * I.r, ctx->scratch, ctx->stream));
         }
         CK(cudaMemcpyAsync(outs[f], ctx->scratch, sizeof(double) * 3 * nn, cudaMemcpyDefault, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -836,61 +1232,98 @@ int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a) {
     return OSAM_OK;
 }
 
-int osam_set_state(osam_ctx* ctx, int sub, const double* u, const double* v, const double* a) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || !u) return OSAM_EINVAL;
-    Sub& s = ctx->subs[sub];
-    const int nn = s.g.nn();
-    if (s.kind == OSAM_FOM) {
-        FomDev& F = s.fom;
-        if (int r = upload(ctx, ctx->scratch, u, sizeof(double) * 3 * nn)) return r;
-        CK(launch_aos_to_soa(ctx->scratch, F.u[0], nn, ctx->stream));
+int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a) {
+    return osam_instance_get_state(ctx, 0, sub, u, v, a);
+}
+
+int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, const double* v, const double* a) {
+    if (!valid(ctx, inst, sub) || !u) return OSAM_EINVAL;
+    Slot& S = ctx->slots[sub];
+    if (S.kind == OSAM_FOM) {
+        FomB& g = S.fom.d;
+        const InstFom& I = S.fom.inst[inst];
+        RET(upload(ctx, ctx->scratch, u, sizeof(double) * 3 * I.nn));
+        CK(launch_aos_to_soa(ctx->scratch, g.u[0] + I.node_off, I.nn, g.NN, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
         if (v) {
-            if (int r = upload(ctx, ctx->scratch, v, sizeof(double) * 3 * nn)) return r;
-            CK(launch_aos_to_soa(ctx->scratch, F.v, nn, ctx->stream));
-        } else CK(cudaMemsetAsync(F.v, 0, sizeof(double) * 3 * nn, ctx->stream));
-        CK(launch_zero_clamped(nn, F.clamp, F.u[0], F.v, ctx->stream));
+            RET(upload(ctx, ctx->scratch, v, sizeof(double) * 3 * I.nn));
+            CK(launch_aos_to_soa(ctx->scratch, g.v + I.node_off, I.nn, g.NN, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        } else {
+            for (int c = 0; c < 3; ++c)
+                CK(cudaMemsetAsync(g.v + c * g.NN + I.node_off, 0, sizeof(double) * I.nn, ctx->stream));
+        }
+        CK(launch_zero_clamped(I.nn, g.clamp + I.node_off, g.u[0] + I.node_off, g.v + I.node_off, g.NN, ctx->stream));
         if (a) {
-            if (int r = upload(ctx, ctx->scratch, a, sizeof(double) * 3 * nn)) return r;
-            CK(launch_aos_to_soa(ctx->scratch, F.a, nn, ctx->stream));
-        } else if (int r = fom_initial_accel(ctx, s)) return r;
+            RET(upload(ctx, ctx->scratch, a, sizeof(double) * 3 * I.nn));
+            CK(launch_aos_to_soa(ctx->scratch, g.a + I.node_off, I.nn, g.NN, ctx->stream));
+        } else {
+            RET(select_instance(ctx, inst));
+            CK(launch_force_init_b(g, ctx->sel, ctx->stream));
+            CK(launch_init_accel_b(g, ctx->sel, ctx->stream));
+        }
     } else {
-        RomDev& R = s.rom;
-        double* uv = ctx->scratch;  // needs 6 nn: use two passes
-        if (int r = upload(ctx, uv, u, sizeof(double) * 3 * nn)) return r;
-        CK(launch_rom_basis_project(R, uv, nullptr, ctx->stream));
+        RomGroupH& G = S.rom;
+        const InstRom& I = G.inst[inst];
+        const int nn = G.grid[inst].nn();
+        std::vector<double> qh(I.r), qdh(I.r, 0.0);
+        RET(upload(ctx, ctx->scratch, u, sizeof(double) * 3 * nn));
+        CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], ctx->scratch, nullptr,
+                                    G.d.q + I.q_off, ctx->stream));
+        RET(to_host(ctx, qh, G.d.q + I.q_off, I.r));
         if (v) {
-            if (int r = upload(ctx, uv, v, sizeof(double) * 3 * nn)) return r;
-            // project v into qd: reuse the kernel with u := v and copy q -> qd afterwards
-            CK(cudaMemcpyAsync(R.sq, R.q, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
-            CK(launch_rom_basis_project(R, uv, nullptr, ctx->stream));
-            CK(cudaMemcpyAsync(R.q + R.r, R.q, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
-            CK(cudaMemcpyAsync(R.q, R.sq, sizeof(double) * R.r, cudaMemcpyDeviceToDevice, ctx->stream));
-        } else CK(cudaMemsetAsync(R.q + R.r, 0, sizeof(double) * R.r, ctx->stream));
-        CK(launch_rom_project(R, 0, 0, ctx->stream));
-        CK(launch_rom_step(R, 0, ctx->dt, 1, ctx->stream));
+            RET(upload(ctx, ctx->scratch, v, sizeof(double) * 3 * nn));
+            CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], ctx->scratch, nullptr,
+                                        G.d.q + I.q_off, ctx->stream));
+            RET(to_host(ctx, qdh, G.d.q + I.q_off, I.r));
+        }
+        RET(upload(ctx, G.d.q + I.q_off, qh.data(), sizeof(double) * I.r));
+        RET(upload(ctx, G.d.q + I.q_off + I.r, qdh.data(), sizeof(double) * I.r));
+        RET(select_instance(ctx, inst));
+        CK(launch_rom_project_b(G.d, ctx->sel, 0, 0, ctx->stream));
+        CK(launch_rom_step_b(G.d, ctx->sel, 0, ctx->dt, 1, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }
 
-int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* qd, double* qdd) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || ctx->subs[sub].kind != OSAM_ROM) return OSAM_EINVAL;
-    RomDev& R = ctx->subs[sub].rom;
+int osam_set_state(osam_ctx* ctx, int sub, const double* u, const double* v, const double* a) {
+    return osam_instance_set_state(ctx, 0, sub, u, v, a);
+}
+
+int osam_instance_get_reduced_state(osam_ctx* ctx, int inst, int sub, double* q, double* qd, double* qdd) {
+    if (!valid(ctx, inst, sub) || ctx->slots[sub].kind != OSAM_ROM) return OSAM_EINVAL;
+    RomGroupH& G = ctx->slots[sub].rom;
+    const InstRom& I = G.inst[inst];
     double* outs[3] = {q, qd, qdd};
     for (int f = 0; f < 3; ++f)
-        if (outs[f]) CK(cudaMemcpyAsync(outs[f], R.q + (long long)f * R.r, sizeof(double) * R.r, cudaMemcpyDefault, ctx->stream));
+        if (outs[f])
+            CK(cudaMemcpyAsync(outs[f], G.d.q + I.q_off + (long long)f * I.r, sizeof(double) * I.r, cudaMemcpyDefault,
+                               ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* qd, double* qdd) {
+    return osam_instance_get_reduced_state(ctx, 0, sub, q, qd, qdd);
+}
+
+int osam_instance_set_reduced_state(osam_ctx* ctx, int inst, int sub, const double* q, const double* qd,
+                                    const double* qdd) {
+    if (!valid(ctx, inst, sub) || ctx->slots[sub].kind != OSAM_ROM) return OSAM_EINVAL;
+    RomGroupH& G = ctx->slots[sub].rom;
+    const InstRom& I = G.inst[inst];
+    const double* ins[3] = {q, qd, qdd};
+    for (int f = 0; f < 3; ++f)
+        if (ins[f])
+            CK(cudaMemcpyAsync(G.d.q + I.q_off + (long long)f * I.r, ins[f], sizeof(double) * I.r, cudaMemcpyDefault,
+                               ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }
 
 int osam_set_reduced_state(osam_ctx* ctx, int sub, const double* q, const double* qd, const double* qdd) {
-    if (!ctx || sub < 0 || sub >= (int)ctx->subs.size() || ctx->subs[sub].kind != OSAM_ROM) return OSAM_EINVAL;
-    RomDev& R = ctx->subs[sub].rom;
-    const double* ins[3] = {q, qd, qdd};
-    for (int f = 0; f < 3; ++f)
-        if (ins[f]) CK(cudaMemcpyAsync(R.q + (long long)f * R.r, ins[f], sizeof(double) * R.r, cudaMemcpyDefault, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    return OSAM_OK;
+    return osam_instance_set_reduced_state(ctx, 0, sub, q, qd, qdd);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -935,50 +1368,45 @@ int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double l
 }
 
 // ------------------------------------------------------------------------------------------------
-// adjoint rollout
+// adjoint rollout on a one-instance FOM group without couplings
 // ------------------------------------------------------------------------------------------------
 int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     if (!d || !out) return OSAM_EINVAL;
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || !(d->h > 0.0) || !d->u0 || !d->w || !d->lambda_e || !d->mu_e ||
         d->n_steps < 0 || !(d->dt > 0.0) || !(d->rho > 0.0))
         return OSAM_EINVAL;
-    auto holder = std::make_unique<osam_ctx>();
-    osam_ctx* ctx = holder.get();
-    if (int r = check_device(ctx, d->device)) { g_init_error = ctx->err; return r; }
-    if (d->stream) ctx->stream = static_cast<cudaStream_t>(d->stream);
-    else { CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)); ctx->own_stream = true; }
-    CK(cudaEventCreate(&ctx->ev0));
-    CK(cudaEventCreate(&ctx->ev1));
-    ctx->dt = d->dt;
-    ctx->nsub = 1;
-    Sub s;
-    s.kind = OSAM_FOM;
-    s.g.nx = d->nx; s.g.ny = d->ny; s.g.nz = d->nz; s.g.h = d->h;
-    const int nn = s.g.nn(), ne = s.g.ne();
-    s.clamp_h.assign(nn, 0);
-    if (d->dirichlet) CK(cudaMemcpy(s.clamp_h.data(), d->dirichlet, nn, cudaMemcpyDefault));
-    for (auto& c : s.clamp_h) c &= 7;
-    s.srow_h.assign(nn, -1);
-    s.ns = 0;
-    CKA(ctx->scratch = ctx->alloc<double>(3LL * nn));
     osam_subdomain_desc sd{};
     sd.kind = OSAM_FOM;
     sd.nx = d->nx; sd.ny = d->ny; sd.nz = d->nz; sd.h = d->h;
     sd.material = d->material;
     sd.rho = d->rho;
     sd.lambda_e = d->lambda_e; sd.mu_e = d->mu_e;
+    sd.dirichlet = d->dirichlet;
     sd.u0 = d->u0; sd.v0 = d->v0;
-    ctx->subs.push_back(s);
-    Sub& S = ctx->subs[0];
-    if (int r = setup_fom(ctx, S, sd)) { g_init_error = ctx->err; return r; }
-    FomDev& F = S.fom;
+    osam_problem_desc pd{};
+    pd.n_subdomains = 1;
+    pd.subdomains = &sd;
+    pd.dt = d->dt;
+    pd.n_substeps = 1;
+    pd.max_iters = 1;
+    pd.precision = OSAM_FP64;
+    pd.scatter = OSAM_SCATTER_ATOMIC;
+    pd.stream = d->stream;
+    pd.device = d->device;
+    osam_ctx* raw = nullptr;
+    if (int rc = osam_batch_init(1, &pd, &raw)) return rc;
+    std::unique_ptr<osam_ctx> holder(raw);
+    osam_ctx* ctx = raw;
+    FomB& F = ctx->slots[0].fom.d;
+    const InstFom& I = ctx->slots[0].fom.inst[0];
+    const int nn = I.nn, ne = I.ne;
     const double dt = d->dt;
     const int T = d->n_steps;
-    const int C = d->checkpoint_every > 0 ? d->checkpoint_every : 50;
-    const int nck = T / C + 1;
+    const int Cp = d->checkpoint_every > 0 ? d->checkpoint_every : 50;
+    const int nck = T / Cp + 1;
     const long long n3 = 3LL * nn;
     double* ck = ctx->alloc<double>((size_t)nck * 3 * n3);  // (u, v, a) at steps 0, C, 2C, ...
-    double* useg = ctx->alloc<double>((size_t)(C + 1) * n3); // displacements of one segment
+    double* useg = ctx->alloc<double>((size_t)(Cp + 1) * n3);
     double* ub = ctx->alloc<double>(n3);
     double* vb = ctx->alloc<double>(n3);
     double* ab = ctx->alloc<double>(n3);
@@ -986,21 +1414,13 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     double* tmp = ctx->alloc<double>(n3);
     double* glam = ctx->alloc<double>(ne);
     double* gmu = ctx->alloc<double>(ne);
-    double* Jd = ctx->alloc<double>(1);
-    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(tmp); CKA(glam); CKA(gmu); CKA(Jd);
+    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(tmp); CKA(glam); CKA(gmu);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    if (int r = fom_initial_accel(ctx, S)) return r;
-    // one explicit step in place on (u[0], v, a), no Schwarz data
+    // one explicit step in place on (u[0], v, a)
     auto step = [&](double* u_store) -> int {
-        NodeArgs p = node_args(ctx, S);
-        p.predict_only = 1; p.ucur = F.u[0]; p.unext = F.u[1]; p.h2 = nullptr; p.last = 0;
-        CK(launch_node_update(false, kAtomic, p, ctx->stream));
-        ElemArgs ea = elem_args(F, F.u[1], 1, nn);
-        ea.f = F.f;
-        CK(launch_hex8_force(F.material, false, kAtomic, ea, ctx->stream));
-        NodeArgs na = node_args(ctx, S);
-        na.fclear = F.f; na.ucur = F.u[1]; na.unext = F.u[0]; na.last = 1;
-        CK(launch_node_update(false, kAtomic, na, ctx->stream));
+        CK(launch_node_b(F, nullptr, kAtomic, -1, 1, 1, F.u[0], F.u[1], dt, ctx->stream));
+        CK(launch_force_b(F, nullptr, F.u[1], kAtomic, F.eblock, ctx->stream));
+        CK(launch_node_b(F, nullptr, kAtomic, 1, -1, 0, F.u[1], F.u[0], dt, ctx->stream));
         CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         return OSAM_OK;
@@ -1019,46 +1439,44 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
         CK(cudaMemcpyAsync(F.a, base + 2 * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         return OSAM_OK;
     };
-    if (int r = save_ck(0)) return r;
+    RET(save_ck(0));
     for (int t = 1; t <= T; ++t) {
-        if (int r = step(nullptr)) return r;
-        if (t % C == 0)
-            if (int r = save_ck(t / C)) return r;
+        RET(step(nullptr));
+        if (t % Cp == 0) RET(save_ck(t / Cp));
     }
-    // J = w . u_T  (w interleaved -> SoA in y)
-    if (int r = upload(ctx, ctx->scratch, d->w, sizeof(double) * n3)) return r;
-    CK(launch_aos_to_soa(ctx->scratch, ub, nn, ctx->stream));
-    CK(launch_zero_clamped(nn, F.clamp, ub, nullptr, ctx->stream));
+    // J = w . u_T
+    RET(upload(ctx, ctx->scratch, d->w, sizeof(double) * n3));
+    CK(launch_aos_to_soa(ctx->scratch, ub, nn, nn, ctx->stream));
+    CK(launch_zero_clamped(nn, F.clamp, ub, nullptr, nn, ctx->stream));
     std::vector<double> wh(n3), uh(n3);
     CK(cudaMemcpyAsync(wh.data(), ub, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(uh.data(), F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     double J = 0.0;
     for (long long q = 0; q < n3; ++q) J += wh[q] * uh[q];
-    // reverse sweep, one checkpoint segment at a time
-    ElemArgs va = elem_args(F, nullptr, 1, nn);
+    ElemArgs va{};
+    va.nx = I.nx; va.ny = I.ny; va.nz = I.nz; va.ne = ne;
+    va.invh = I.invh; va.w8 = I.w8;
+    va.lam_e = I.lam_e; va.mu_e = I.mu_e;
+    va.usn = 1; va.usc = nn; va.fsn = 1; va.fsc = nn;
     va.f = tmp;
-    for (int seg = (T - 1) / C; seg >= 0 && T > 0; --seg) {
-        const int t0 = seg * C, t1 = std::min(T, t0 + C);
-        if (int r = load_ck(seg)) return r;
+    for (int seg = (T - 1) / Cp; seg >= 0 && T > 0; --seg) {
+        const int t0 = seg * Cp, t1 = std::min(T, t0 + Cp);
+        RET(load_ck(seg));
         CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int t = t0 + 1; t <= t1; ++t)
-            if (int r = step(useg + (size_t)(t - t0) * n3)) return r;
+        for (int t = t0 + 1; t <= t1; ++t) RET(step(useg + (size_t)(t - t0) * n3));
         for (int t = t1 - 1; t >= t0; --t) {
             CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
             va.u = useg + (size_t)(t + 1 - t0) * n3;
-            va.usn = 1; va.usc = nn; va.fsn = 1; va.fsc = nn;
             CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
             CK(launch_adjoint_post(nn, dt, F.clamp, tmp, ub, vb, ab, ctx->stream));
         }
     }
-    // a_0 = -M^-1 f(u_0): y = -M^-1 abar_0 (the pre kernel with vbar = 0 contribution removed)
-    CK(cudaMemsetAsync(tmp, 0, sizeof(double) * n3, ctx->stream));
+    // a_0 = -M^-1 f(u_0)
     CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
-    if (int r = load_ck(0)) return r;
+    RET(load_ck(0));
     va.u = F.u[0];
     CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
-    // gu0 = ubar + tmp (free dofs): the post kernel adds tmp into ubar
     CK(launch_adjoint_post(nn, 0.0, F.clamp, tmp, ub, vb, ab, ctx->stream));
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
@@ -1067,12 +1485,12 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     out->J = J;
     out->elapsed_ms = ms;
     if (out->grad_u0) {
-        CK(launch_soa_to_aos(ub, ctx->scratch, nn, ctx->stream));
+        CK(launch_soa_to_aos(ub, ctx->scratch, nn, nn, ctx->stream));
         CK(cudaMemcpyAsync(out->grad_u0, ctx->scratch, sizeof(double) * n3, cudaMemcpyDefault, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     if (out->grad_v0) {
-        CK(launch_soa_to_aos(vb, ctx->scratch, nn, ctx->stream));
+        CK(launch_soa_to_aos(vb, ctx->scratch, nn, nn, ctx->stream));
         CK(cudaMemcpyAsync(out->grad_v0, ctx->scratch, sizeof(double) * n3, cudaMemcpyDefault, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }

@@ -1,12 +1,19 @@
-// Internal declarations of libosam: device data of the subdomains and couplings, and the kernel
-// launchers shared between translation units.  Not part of the public ABI (include/osam.h).
+// Internal declarations of libosam: device-side views of the batched subdomain groups and
+// couplings, and the kernel launchers shared between translation units.  Not part of the public ABI
+// (include/osam.h).
+//
+// A context holds n_inst instances of one coupled problem (same subdomain kinds, same coupling
+// topology, same time step and substep count; meshes, materials and ROM operators may differ).
+// Subdomain slot s of every instance forms one group whose arrays are concatenated across instances;
+// per-instance tables give each instance's sizes and offsets, and block tables map every CUDA block
+// of a per-step kernel to one instance, so a single launch advances every instance.  A single
+// problem is a batch of one.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <string>
-#include <vector>
 
 #include "osam.h"
 
@@ -14,6 +21,9 @@ namespace osam {
 
 // element-to-node scatter of the internal force
 enum Scatter { kAtomic = 1, kGather = 2 };
+
+constexpr int kMaxSlots = 8;    // subdomains per instance
+constexpr int kNodeBlock = 256; // nodes per block of the node kernels
 
 struct Grid {
     int nx = 0, ny = 0, nz = 0;
@@ -23,9 +33,9 @@ struct Grid {
     int ne() const { return nx * ny * nz; }
 };
 
-// Arguments of the hex8 internal-force kernel.  Displacements are read at u[n*usn + c*usc];
-// atomic mode adds into f[n*fsn + c*fsc]; gather mode writes the 24 element contributions to
-// fe[(corner*3 + c)*ne + e], corner = ax + 2*ay + 4*az.
+// Arguments of the element-level hex8 kernel (one mesh).  Displacements are read at
+// u[n*usn + c*usc]; atomic mode adds into f[n*fsn + c*fsc]; gather mode writes the 24 element
+// contributions to fe[(corner*3 + c)*ne + e], corner = ax + 2*ay + 4*az.
 struct ElemArgs {
     int nx, ny, nz, ne;
     double invh, w8;          // 1/h and h^2/8 (Gauss weight x detJ / h for unit cubes)
@@ -41,114 +51,149 @@ struct ElemArgs {
     void* fe;
 };
 
-// Arguments of the node kernel that finishes substep j (corrector) and predicts substep j+1.
-struct NodeArgs {
-    int nx, ny, nz, nn, ne;
-    double dt;
-    const double* minv;       // 1 / lumped mass
-    const uint8_t* clamp;     // per-node clamp bits
-    const int* srow;          // per-node Schwarz row or -1
-    int ns;                   // Schwarz rows
-    const double* h1;         // history slot j+1: [3 fields][3 comps][ns]
-    const double* h2;         // history slot j+2 (u field used) or null when j+1 is the last slot
-    const double* ucur;       // u^{j+1}
-    double* unext;            // out: u^{j+2} (unused when h2 == null and last)
+// one instance of a FOM slot
+struct InstFom {
+    int nx, ny, nz, nn, ne, ns;
+    double invh, w8, lam, mu;
+    const double* lam_e;      // absolute device pointers or null (uniform lam / mu)
+    const double* mu_e;
+    long long node_off, elem_off, hist_off;
+};
+
+// kernel view of a FOM slot across instances; nodal arrays are SoA over the concatenated nodes:
+// component c of global node g is at [c * NN + g]; element buffers [24][NE]
+struct FomB {
+    int n_inst;
+    const InstFom* inst;
+    long long NN, NE;
+    const int2* eblk;         // element blocks: (instance, first element), eblock elements each
+    int n_eblk, eblock;
+    const int2* nblk;         // node blocks: (instance, first node), kNodeBlock nodes each
+    int n_nblk;
+    const int* nblk_off;      // [n_inst + 1] first node block of each instance
+    const double* minv;
+    const uint8_t* clamp;
+    const int* srow;
+    double* u[2];
     double* v;
     double* a;
-    const void* force;        // f [3][nn] (atomic) or fe [24][ne] (gather)
-    void* fclear;             // atomic mode: f array to reset to zero after reading
-    int last;                 // 1 on the last substep of the interval (no predictor)
-    int predict_only;         // 1: write unext = predictor of ucur with (v, a); no force used
+    void* f;                  // atomic accumulator [3][NN] (double, or float for FP32 force)
+    void* fe;                 // element buffer [24][NE] (double, or float for FP32 force)
+    double* su;
+    double* sv;
+    double* sa;
+    double* pu;
+    double* pv;
+    double* hist;             // per instance [(nsub+1)][3 fields][3 comps][ns] at hist_off
+    double* partial;          // criterion partial sums, 2 per node block
+    int material, fp32, scatter;
 };
 
-struct FomDev {
-    Grid g;
-    int material = 0;
-    double lam = 0, mu = 0, rho = 0;
-    double* lam_e = nullptr;
-    double* mu_e = nullptr;
-    double* minv = nullptr;
-    uint8_t* clamp = nullptr;
-    int* srow = nullptr;
-    int ns = 0;
-    double* u[2] = {nullptr, nullptr};
-    double* v = nullptr;
-    double* a = nullptr;
-    void* f = nullptr;        // atomic accumulation buffer [3][nn] (double or float)
-    void* fe = nullptr;       // gather buffer [24][ne] (double or float)
-    double* su = nullptr;
-    double* sv = nullptr;
-    double* sa = nullptr;
-    double* pu = nullptr;
-    double* pv = nullptr;
-    double* hist = nullptr;   // input boundary history [(nsub+1)][3][3][ns]
-    int norm_blocks = 0;
+// one instance of a ROM slot
+struct InstRom {
+    int r, rs, nsdof, d, nq, gx, gy;
+    long long O_off, PhiSt_off, kij_off, q_off, qrec_off, ghat_off, hist_off, partial_off;
 };
 
-struct RomDev {
-    Grid g;
-    int r = 0, rs = 0, nfree = 0, nsdof = 0, d = 0, nq = 0;
-    double* O = nullptr;       // packed operator [r][d] = [K | H | B | c]
-    double* PhiSt = nullptr;   // Phi_S^T [rs][nsdof]
-    double* Phi = nullptr;     // [nfree][r]
-    int* free_dof = nullptr;   // [nfree] dof ids
-    int* dof_free = nullptr;   // [3 nn] free row of each dof or -1
-    uint8_t* clamp = nullptr;
-    int* srow = nullptr;
-    int ns = 0;
-    short2* kron_ij = nullptr; // [nq] (i, j) of each compressed Kronecker entry
-    double* q = nullptr;       // state [3][r] = q, qd, qdd
-    double* sq = nullptr;      // saved [3][r]
-    double* pq = nullptr;      // previous iterate [3][r]
-    double* qrec = nullptr;    // recorded [(nsub+1)][3][r]
-    double* ghat = nullptr;    // [(nsub+1)][rs]
-    double* hist = nullptr;    // input boundary history [(nsub+1)][3][nsdof]
-    double* partial = nullptr; // ROM step partial sums
-    unsigned int* counter = nullptr;
-    int step_gx = 0, step_gy = 0;
+struct RomB {
+    int n_inst;
+    const InstRom* inst;
+    int gx_max, gy_max, rs_max, r_max;
+    const double* O;          // packed operator rows [r][K | H | B | c] per instance
+    const double* PhiSt;      // Phi_S^T [rs][nsdof] per instance
+    const short2* kij;        // compressed Kronecker index pairs per instance
+    double* q;                // [3][r] per instance: q, qd, qdd
+    double* sq;
+    double* pq;
+    double* qrec;             // [(nsub+1)][3][r] per instance
+    double* ghat;             // [(nsub+1)][rs] per instance
+    double* hist;             // [(nsub+1)][3][nsdof] per instance
+    double* partial;          // reduced-step partial sums [gx][r] per instance
+    unsigned int* counter;    // [n_inst] last-block counters of the reduced step
+    double* npart;            // criterion partial sums, 2 per instance
 };
 
-struct CplDev {
-    int dst = 0, src = 0, nrow = 0;
-    int nfield = 3;            // fields recorded / transferred (3, or 1 for a ROM destination's u... kept 3)
-    int* row = nullptr;        // dst Schwarz row of each coupling row
-    int* dnode = nullptr;      // [nrow][8] donor nodes in src
-    double* dw = nullptr;      // [nrow][8] trilinear weights
-    double* rec = nullptr;     // FOM source: recorded trace [(nsub+1)][3][3][nrow]
-    double* Rt = nullptr;      // ROM source: (Pi Phi_rows)^T [r][3 nrow]
+// one coupling (dst slot <- src slot) across instances; rows are concatenated over instances
+struct CplB {
+    int R;                    // total rows
+    const int* rinst;         // instance of each row
+    const int* row_first;     // [n_inst] first row of each instance
+    const int* nrow;          // [n_inst] rows per instance
+    const int* row;           // dst Schwarz row (local to the instance) of each row
+    const int* dnode;         // [R][8] donor nodes, global index in the src group's node arrays
+    const double* dw;         // [R][8] trilinear weights
+    double* rec;              // FOM source: recorded trace, per instance [(nsub+1)][3][3][nrow]
+    const long long* rec_off; // [n_inst]
+    const double* Rt;         // ROM source: (Pi Phi_rows)^T, per instance [r][3 nrow]
+    const long long* Rt_off;  // [n_inst]
+    double* dst_hist;
+    const long long* dst_hist_off;  // [n_inst]
+    const int* dst_nd;        // [n_inst] dst Schwarz rows (FOM) or Schwarz dofs (ROM)
+    int dst_rom;
+};
+
+// per-instance controller state and criterion arguments
+struct CtlB {
+    int n_inst, n_fom, n_rom, ncpl, max_it;
+    double tol_abs2, tol_rel2;
+    const double* fom_partial[kMaxSlots];
+    const int* fom_blk_off[kMaxSlots];
+    const double* rom_npart[kMaxSlots];
+    int* active;
+    int* iters;
+    int* status;
+    double* cnum;
+    double* cden;
+    unsigned int* counter;
+    int* any_active;
 };
 
 // ------------------------------------------------------------------------------------------------
-// launchers (all asynchronous on `s`)
+// element level, set-up and I/O (fom_kernels.cu)
 // ------------------------------------------------------------------------------------------------
+int grid_for(long long n, int block);
 cudaError_t launch_hex8_force(int material, bool fp32, int scatter, const ElemArgs& a, cudaStream_t s);
-cudaError_t launch_node_update(bool fp32, int scatter, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s);
-cudaError_t launch_trace(const CplDev& c, const double* u, const double* v, const double* a, int nn, int slot,
-                         int nsub, cudaStream_t s);
-cudaError_t launch_zoh_from_fom(const CplDev& c, const double* u, const double* v, const double* a, int nn,
-                                bool dst_rom, double* dst_hist, int dst_ns_or_nsdof, int nsub, cudaStream_t s);
-cudaError_t launch_publish_fom(const CplDev& c, bool dst_rom, double* dst_hist, int dst_ns_or_nsdof, int nsub,
-                               cudaStream_t s);
-cudaError_t launch_norms_fom(const FomDev& f, double dt, double* partial, cudaStream_t s);
-cudaError_t launch_norms_final(const double* partial, int nparts, double* result, cudaStream_t s);
-cudaError_t launch_donor(const Grid& src, const Grid& dst, const uint8_t* mask_dummy, const int* dst_nodes, int nrow,
-                         int* dnode, double* dw, int* err, cudaStream_t s);
-cudaError_t launch_gather_force(const Grid& g, const double* fe, double* f, cudaStream_t s);
-cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, cudaStream_t s);
-cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, cudaStream_t s);
-cudaError_t launch_accel_from_force(const FomDev& f, const double* force_soa, cudaStream_t s);
+cudaError_t launch_donor(const Grid& src, const Grid& dst, const int* dst_nodes, int nrow, int* dnode, double* dw,
+                         int* err, cudaStream_t s);
+cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, long long stride, cudaStream_t s);
+cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, long long stride, cudaStream_t s);
+cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, long long stride, cudaStream_t s);
 
-// ROM
-cudaError_t launch_rom_project(const RomDev& r, int slot0, int slot1, cudaStream_t s);
-cudaError_t launch_rom_step(const RomDev& r, int slot, double dt, int rhs_only, cudaStream_t s);
-cudaError_t launch_rom_reconstruct(const CplDev& c, const RomDev& src, bool zoh, bool dst_rom, double* dst_hist,
-                                   int dst_ns_or_nsdof, int nsub, cudaStream_t s);
-cudaError_t launch_rom_norms(const RomDev& r, double dt, double* partial, cudaStream_t s);
-cudaError_t launch_rom_basis_project(const RomDev& r, const double* u_aos, const double* v_aos, cudaStream_t s);
-cudaError_t launch_rom_full_field(const RomDev& r, const double* qv, int field, double* out_aos, int slot,
+// ------------------------------------------------------------------------------------------------
+// batched per-step kernels (step_kernels.cu); `active` masks instances that have converged
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock_grid,
+                           cudaStream_t s);
+cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s);  // FP64 gather into fe
+cudaError_t launch_init_accel_b(const FomB& g, const int* active, cudaStream_t s);  // a = -M^-1 f from fe
+cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slot1, int slot2, int predict_only,
+                          const double* ucur, double* unext, double dt, cudaStream_t s);
+cudaError_t launch_saverest_fom_b(const FomB& g, const int* active, int restore, cudaStream_t s);
+cudaError_t launch_norms_fom_b(const FomB& g, const int* active, double dt, cudaStream_t s);
+cudaError_t launch_copy_u10_b(const FomB& g, const int* active, cudaStream_t s);
+cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
+                           cudaStream_t s);
+cudaError_t launch_publish_b(const CplB& c, const int* active, int nsub, cudaStream_t s);
+cudaError_t launch_zoh_fom_b(const CplB& c, const int* active, const FomB& src, int nsub, cudaStream_t s);
+cudaError_t launch_rom_record0_b(const RomB& r, const int* active, cudaStream_t s);
+cudaError_t launch_rom_project_b(const RomB& r, const int* active, int slot0, int slot1, cudaStream_t s);
+cudaError_t launch_rom_step_b(const RomB& r, const int* active, int slot, double dt, int rhs_only, cudaStream_t s);
+cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int nsub,
+                                     cudaStream_t s);
+cudaError_t launch_rom_norms_b(const RomB& r, const int* active, double dt, cudaStream_t s);
+cudaError_t launch_saverest_rom_b(const RomB& r, const int* active, int restore, cudaStream_t s);
+cudaError_t launch_reset_ctl(const CtlB& c, cudaStream_t s);
+cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+
+// ROM set-up and I/O (rom_kernels.cu)
+cudaError_t launch_rom_basis_project(int nfree, int r, const double* Phi, const int* free_dof, const double* u_aos,
+                                     const double* v_aos, double* q, cudaStream_t s);
+cudaError_t launch_rom_full_field(int nn, int r, const double* Phi, const int* dof_free, const uint8_t* clamp,
+                                  const int* srow, const double* hist_slot_field, const double* qv, double* out_aos,
                                   cudaStream_t s);
-cudaError_t launch_build_Rt_checked(const CplDev& c, const RomDev& src, int* err, cudaStream_t s);
+cudaError_t launch_build_Rt(int nrow, int r, const int* dnode_local, const double* dw, const int* dof_free,
+                            const int* srow, const double* Phi, double* Rt, int* err, cudaStream_t s);
 
 // dense helpers (fit)
 cudaError_t launch_gemm_tn(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C,
@@ -160,16 +205,13 @@ cudaError_t launch_gemm_nt(int m, int n, int k, const double* A, int lda, const 
 cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0,
                                  cudaStream_t s);
 
-// adjoint
+// adjoint (adjoint_kernels.cu)
 cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
                             double* lam_bar, double* mu_bar, int accumulate, cudaStream_t s);
 cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb, double* ab,
                                double* y, double* tmp, cudaStream_t s);
 cudaError_t launch_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
                                 double* ab, cudaStream_t s);
-cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, cudaStream_t s);
-
-int grid_for(long long n, int block);
 
 // message returned by osam_last_error(NULL) on the calling thread
 void set_thread_error(const std::string& msg);

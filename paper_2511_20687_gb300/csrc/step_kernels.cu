@@ -1,0 +1,699 @@
+// Per-step kernels of the O-SAM controller, batched over the instances of a context.
+//
+// Every kernel takes the group view of one subdomain slot (FomB / RomB) or coupling (CplB) and the
+// per-instance `active` mask: instances that have met the convergence criterion of the current
+// controller step (Eq. conv_criterion) are skipped, so each instance performs exactly the
+// iterations it would perform alone.  Blocks never span two instances.
+//   FOM: hex8 force (Sec. 2 / Appendix A, sum-factorised, hex8_math.cuh), corrector + predictor of
+//        the explicit Newmark scheme (beta = 0, gamma = 1/2) with Dirichlet and Schwarz data,
+//        state save / restore, criterion partial sums, trace Pi(u, v, a) at a neighbour's Schwarz
+//        nodes, publication into the neighbour's history, zero-order hold.
+//   ROM: boundary projection ghat = Phi_S^T s, reduced step qdd = K q + H kron_c(q) + B ghat + c,
+//        reconstruction (Pi Phi_rows) q, criterion partial sums, save / restore.
+//   Controller: per-instance criterion and convergence flags; the last block sets the condition of
+//        the CUDA graph's while node (any instance still iterating).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hex8_math.cuh"
+#include "osam_internal.h"
+
+namespace osam {
+
+namespace {
+
+using namespace hex8;
+
+constexpr int kRomBlock = 128;   // columns per block of the reduced step
+constexpr int kRomRows = 8;      // rows per block of the reduced step
+constexpr int kMaxR = 256;
+
+// ------------------------------------------------------------------------------------------------
+// FOM
+// ------------------------------------------------------------------------------------------------
+template <int MAT, typename T, int MODE>
+__global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
+                                                 const double* __restrict__ u) {
+    const int2 b = g.eblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int e = b.y + threadIdx.x;
+    if (e >= I.ne) return;
+    const int i = e % I.nx;
+    const int t = e / I.nx;
+    const int j = t % I.ny;
+    const int k = t / I.ny;
+    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
+    const int n0 = i + sy * j + sz * k;
+    int node[8];
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
+    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+    T m1, m2, m3;
+    if (MAT == OSAM_NEO_HOOKEAN) {
+        const double kappa = lam + (2.0 / 3.0) * mu;
+        m1 = T(0.5 * kappa * I.w8); m2 = T(mu * I.w8); m3 = T(mu * I.w8 / 3.0);
+    } else {
+        m1 = T(lam * I.w8); m2 = T(mu * I.w8); m3 = T(0);
+    }
+    T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
+    const double* ub = u + I.node_off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double U[8];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) U[c8] = ub[(long long)c * g.NN + node[c8]];
+        edge_differences<T>(U, I.invh, Dx[c], Dy[c], Dz[c]);
+    }
+    T F[3][8];
+    element_force<MAT, T>(Dx, Dy, Dz, m1, m2, m3, F);
+    if (MODE == kAtomic) {
+        T* f = static_cast<T*>(g.f) + I.node_off;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) atomic_add(f + (long long)c * g.NN + node[c8], F[c][c8]);
+    } else {
+        T* fe = static_cast<T*>(g.fe) + I.elem_off;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
+    }
+}
+
+// a = -M^-1 f on every non-clamped dof from the FP64 element buffer (initial acceleration)
+__global__ void __launch_bounds__(kNodeBlock) k_init_accel_b(const FomB g, const int* __restrict__ active) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    if (n >= I.nn) return;
+    const int i = n % (I.nx + 1);
+    const int t = n / (I.nx + 1);
+    const int j = t % (I.ny + 1);
+    const int k = t / (I.ny + 1);
+    const long long gn = I.node_off + n;
+    const uint8_t cm = g.clamp[gn];
+    const double* fe = static_cast<const double*>(g.fe) + I.elem_off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double f = gather_force<double>(fe, I.nx, I.ny, I.nz, (int)g.NE, i, j, k, c);
+        g.a[(long long)c * g.NN + gn] = (cm & (1 << c)) ? 0.0 : -f * g.minv[gn];
+    }
+}
+
+// Corrector of substep j and predictor of substep j+1 (explicit Newmark beta = 0, gamma = 1/2):
+//   free dofs:  a' = -f/m;  v += dt/2 (a + a');  a = a';  u^{j+2} = u^{j+1} + dt v + dt^2/2 a
+//   clamped:    u = v = a = 0
+//   Schwarz:    v, a from history slot j+1 (slot1); u^{j+2} from history slot j+2 (slot2)
+// predict_only: write the predictor of ucur with the current (v, a) (start of an interval).
+template <typename TF, int MODE>
+__global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* __restrict__ active, int slot1,
+                                                      int slot2, int predict_only, const double* ucur, double* unext,
+                                                      double dt) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    if (n >= I.nn) return;
+    const int i = n % (I.nx + 1);
+    const int t = n / (I.nx + 1);
+    const int j = t % (I.ny + 1);
+    const int k = t / (I.ny + 1);
+    const long long gn = I.node_off + n;
+    const uint8_t cm = g.clamp[gn];
+    const int row = g.srow[gn];
+    const double hdt = 0.5 * dt, hdt2 = 0.5 * dt * dt;
+    const double minv = g.minv[gn];
+    const double* h1 = slot1 >= 0 ? g.hist + I.hist_off + (long long)slot1 * 9 * I.ns : nullptr;
+    const double* h2 = slot2 >= 0 ? g.hist + I.hist_off + (long long)slot2 * 9 * I.ns : nullptr;
+    const TF* fe = static_cast<const TF*>(g.fe) + I.elem_off;
+    TF* fa = static_cast<TF*>(g.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + gn;
+        double un;
+        if (cm & (1 << c)) {
+            g.v[d] = 0.0;
+            g.a[d] = 0.0;
+            un = 0.0;
+            if (MODE == kAtomic && !predict_only) fa[d] = TF(0);
+        } else if (row >= 0) {
+            if (!predict_only) {
+                g.v[d] = h1[(long long)(3 + c) * I.ns + row];
+                g.a[d] = h1[(long long)(6 + c) * I.ns + row];
+                if (MODE == kAtomic) fa[d] = TF(0);
+            }
+            un = h2 ? h2[(long long)c * I.ns + row] : 0.0;
+        } else {
+            double vn = g.v[d], an = g.a[d];
+            if (!predict_only) {
+                double f;
+                if (MODE == kGather) {
+                    f = gather_force<TF>(fe, I.nx, I.ny, I.nz, (int)g.NE, i, j, k, c);
+                } else {
+                    f = double(fa[d]);
+                    fa[d] = TF(0);
+                }
+                const double anew = -f * minv;
+                vn = fma(hdt, an + anew, vn);
+                an = anew;
+                g.v[d] = vn;
+                g.a[d] = an;
+            }
+            un = fma(hdt2, an, fma(dt, vn, ucur[d]));
+        }
+        if (h2) unext[d] = un;
+    }
+}
+
+// save (restore = 0) or restore (restore = 1) the state at the start of the controller interval
+__global__ void __launch_bounds__(kNodeBlock) k_saverest_fom_b(const FomB g, const int* __restrict__ active,
+                                                              int restore) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    if (n >= I.nn) return;
+    const long long gn = I.node_off + n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + gn;
+        if (restore) { g.u[0][d] = g.su[d]; g.v[d] = g.sv[d]; g.a[d] = g.sa[d]; }
+        else { g.su[d] = g.u[0][d]; g.sv[d] = g.v[d]; g.sa[d] = g.a[d]; }
+    }
+}
+
+// u[0] <- u[1] (an interval with an odd substep count ends in the second displacement buffer)
+__global__ void __launch_bounds__(kNodeBlock) k_copy_u10_b(const FomB g, const int* __restrict__ active) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    if (n >= I.nn) return;
+    const long long gn = I.node_off + n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g.u[0][(long long)c * g.NN + gn] = g.u[1][(long long)c * g.NN + gn];
+}
+
+__device__ __forceinline__ void block_sum2(double& x, double& y) {
+    __shared__ double sx[32], sy[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    const int nw = (blockDim.x + 31) / 32;
+    __syncthreads();
+    if (l == 0) { sx[w] = x; sy[w] = y; }
+    __syncthreads();
+    if (w == 0) {
+        x = l < nw ? sx[l] : 0.0;
+        y = l < nw ? sy[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+    }
+}
+
+// criterion partial sums over free dofs of one node block; remembers the iterate
+__global__ void __launch_bounds__(kNodeBlock) k_norms_fom_b(const FomB g, const int* __restrict__ active, double dt) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    double num = 0.0, den = 0.0;
+    if (n < I.nn) {
+        const long long gn = I.node_off + n;
+        const uint8_t cm = g.clamp[gn];
+        const bool sch = g.srow[gn] >= 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = (long long)c * g.NN + gn;
+            const double un = g.u[0][d], vn = g.v[d];
+            if (!(cm & (1 << c)) && !sch) {
+                const double x = (un - g.pu[d]) + dt * (vn - g.pv[d]);
+                const double y = fma(dt, vn, un);
+                num = fma(x, x, num);
+                den = fma(y, y, den);
+            }
+            g.pu[d] = un;
+            g.pv[d] = vn;
+        }
+    }
+    block_sum2(num, den);
+    if (threadIdx.x == 0) {
+        g.partial[2 * blockIdx.x] = num;
+        g.partial[2 * blockIdx.x + 1] = den;
+    }
+}
+
+__device__ __forceinline__ long long dst_index(const CplB& c, int inst, int slot, int f, int cc, int row) {
+    const int nd = c.dst_nd[inst];
+    const long long base = c.dst_hist_off[inst];
+    return c.dst_rom ? base + (long long)(slot * 3 + f) * nd + 3 * row + cc
+                     : base + (long long)((slot * 3 + f) * 3 + cc) * nd + row;
+}
+
+// trace of a FOM source at slot `slot`: rec[inst][slot][f][c][row] = sum_b w_b field_f,c[donor_b]
+__global__ void k_trace_b(const CplB c, const int* __restrict__ active, const FomB src, const double* u, int slot) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * c.R) return;
+    const int gr = t / 3, cc = t % 3;
+    const int inst = c.rinst[gr];
+    if (active && !active[inst]) return;
+    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
+    double su = 0.0, sv = 0.0, sa = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const double w = c.dw[8 * gr + b];
+        const long long d = (long long)cc * src.NN + c.dnode[8 * gr + b];
+        su = fma(w, u[d], su);
+        sv = fma(w, src.v[d], sv);
+        sa = fma(w, src.a[d], sa);
+    }
+    double* r = c.rec + c.rec_off[inst] + (long long)slot * 9 * nr;
+    r[(long long)(0 + cc) * nr + li] = su;
+    r[(long long)(3 + cc) * nr + li] = sv;
+    r[(long long)(6 + cc) * nr + li] = sa;
+}
+
+// publish a FOM source's recorded slots 1..nsub into the destination history
+__global__ void k_publish_b(const CplB c, const int* __restrict__ active, int nsub) {
+    const long long total = (long long)c.R * 9 * nsub;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int gr = (int)(t % c.R);
+    const long long q = t / c.R;
+    const int fc = (int)(q % 9);
+    const int slot = 1 + (int)(q / 9);
+    const int inst = c.rinst[gr];
+    if (active && !active[inst]) return;
+    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
+    const double val = c.rec[c.rec_off[inst] + ((long long)slot * 9 + fc) * nr + li];
+    c.dst_hist[dst_index(c, inst, slot, fc / 3, fc % 3, c.row[gr])] = val;
+}
+
+// zero-order hold of a FOM source's current state into every slot of the destination history
+__global__ void k_zoh_fom_b(const CplB c, const int* __restrict__ active, const FomB src, int nslots) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * c.R) return;
+    const int gr = t / 3, cc = t % 3;
+    const int inst = c.rinst[gr];
+    if (active && !active[inst]) return;
+    double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const double w = c.dw[8 * gr + b];
+        const long long d = (long long)cc * src.NN + c.dnode[8 * gr + b];
+        s[0] = fma(w, src.u[0][d], s[0]);
+        s[1] = fma(w, src.v[d], s[1]);
+        s[2] = fma(w, src.a[d], s[2]);
+    }
+    for (int slot = 0; slot < nslots; ++slot)
+#pragma unroll
+        for (int f = 0; f < 3; ++f) c.dst_hist[dst_index(c, inst, slot, f, cc, c.row[gr])] = s[f];
+}
+
+// ------------------------------------------------------------------------------------------------
+// ROM
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double s[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    __syncthreads();
+    if (l == 0) s[w] = x;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) / 32;
+    if (w == 0) {
+        x = l < nw ? s[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    }
+    return x;  // valid in thread 0
+}
+
+__global__ void k_rom_record0_b(const RomB r, const int* __restrict__ active) {
+    const int inst = blockIdx.x;
+    if (active && !active[inst]) return;
+    const InstRom I = r.inst[inst];
+    for (int k = threadIdx.x; k < 3 * I.r; k += blockDim.x) r.qrec[I.qrec_off + k] = r.q[I.q_off + k];
+}
+
+// ghat[slot][k] = sum_m PhiSt[k][m] hist[slot][u][m]; one block per (k, slot, instance)
+__global__ void k_rom_project_b(const RomB r, const int* __restrict__ active, int slot0) {
+    const int inst = blockIdx.z;
+    if (active && !active[inst]) return;
+    const InstRom I = r.inst[inst];
+    const int k = blockIdx.x;
+    if (k >= I.rs) return;
+    const int slot = slot0 + blockIdx.y;
+    const double* s = r.hist + I.hist_off + (long long)slot * 3 * I.nsdof;
+    const double* p = r.PhiSt + I.PhiSt_off + (long long)k * I.nsdof;
+    double acc = 0.0;
+    for (int m = threadIdx.x; m < I.nsdof; m += blockDim.x) acc = fma(p[m], s[m], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) r.ghat[I.ghat_off + (long long)slot * I.rs + k] = acc;
+}
+
+// Column-split GEMV of the packed operator with phi = [q, kron_c(q), ghat, 1] at the predicted q;
+// the last block of each instance reduces the partial sums in a fixed order and applies the
+// corrector (rhs_only: qdd = rhs(q) without time stepping).
+__global__ void __launch_bounds__(kRomBlock) k_rom_step_b(const RomB r, const int* __restrict__ active, int slot,
+                                                          double dt, int rhs_only) {
+    __shared__ double qp[kMaxR];
+    __shared__ double red[kRomBlock / 32][kRomRows];
+    __shared__ bool last_block;
+    const int inst = blockIdx.z;
+    if (active && !active[inst]) return;
+    const InstRom I = r.inst[inst];
+    if ((int)blockIdx.x >= I.gx || (int)blockIdx.y >= I.gy) return;
+    const int tid = threadIdx.x;
+    double* q = r.q + I.q_off;
+    for (int t = tid; t < I.r; t += blockDim.x) {
+        const double qv = q[t];
+        qp[t] = rhs_only ? qv : fma(0.5 * dt * dt, q[2 * I.r + t], fma(dt, q[I.r + t], qv));
+    }
+    __syncthreads();
+    const int col = blockIdx.x * kRomBlock + tid;
+    double phi = 0.0;
+    if (col < I.r) phi = qp[col];
+    else if (col < I.r + I.nq) { const short2 ij = r.kij[I.kij_off + col - I.r]; phi = qp[ij.x] * qp[ij.y]; }
+    else if (col < I.r + I.nq + I.rs) phi = r.ghat[I.ghat_off + (long long)slot * I.rs + col - I.r - I.nq];
+    else if (col == I.d - 1) phi = 1.0;
+    const double* O = r.O + I.O_off;
+    double part[kRomRows];
+#pragma unroll
+    for (int rr = 0; rr < kRomRows; ++rr) {
+        const int row = blockIdx.y * kRomRows + rr;
+        part[rr] = (row < I.r && col < I.d) ? O[(long long)row * I.d + col] * phi : 0.0;
+    }
+#pragma unroll
+    for (int rr = 0; rr < kRomRows; ++rr)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part[rr] += __shfl_down_sync(0xffffffffu, part[rr], o);
+    if (tid % 32 == 0)
+#pragma unroll
+        for (int rr = 0; rr < kRomRows; ++rr) red[tid / 32][rr] = part[rr];
+    __syncthreads();
+    double* partial = r.partial + I.partial_off;
+    if (tid < kRomRows) {
+        const int row = blockIdx.y * kRomRows + tid;
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kRomBlock / 32; ++w) s += red[w][tid];
+        if (row < I.r) partial[(long long)blockIdx.x * I.r + row] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned int ticket = atomicAdd(r.counter + inst, 1u);
+        last_block = ticket == (unsigned int)(I.gx * I.gy - 1);
+    }
+    __syncthreads();
+    if (!last_block) return;
+    __threadfence();
+    double* rec = rhs_only ? nullptr : r.qrec + I.qrec_off + (long long)slot * 3 * I.r;
+    for (int row = tid; row < I.r; row += blockDim.x) {
+        double acc = 0.0;
+        for (int bx = 0; bx < I.gx; ++bx) acc += __ldcg(partial + (long long)bx * I.r + row);
+        if (rhs_only) {
+            q[2 * I.r + row] = acc;
+        } else {
+            const double qd = fma(0.5 * dt, q[2 * I.r + row] + acc, q[I.r + row]);
+            q[row] = qp[row];
+            q[I.r + row] = qd;
+            q[2 * I.r + row] = acc;
+            rec[row] = qp[row];
+            rec[I.r + row] = qd;
+            rec[2 * I.r + row] = acc;
+        }
+    }
+    if (tid == 0) r.counter[inst] = 0u;
+}
+
+// s_dst[slot][f][3 i + c] = sum_k Rt[k][3 i + c] q_src[slot][f][k]; grid (columns, slots, fields)
+__global__ void k_rom_reconstruct_b(const CplB c, const int* __restrict__ active, const RomB src, int zoh, int slot0) {
+    const int gc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gc >= 3 * c.R) return;
+    const int gr = gc / 3, cc = gc % 3;
+    const int inst = c.rinst[gr];
+    if (active && !active[inst]) return;
+    const InstRom I = src.inst[inst];
+    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
+    const int slot = slot0 + blockIdx.y;
+    const int f = blockIdx.z;
+    const double* q = zoh ? src.q + I.q_off + (long long)f * I.r
+                          : src.qrec + I.qrec_off + ((long long)slot * 3 + f) * I.r;
+    const double* Rt = c.Rt + c.Rt_off[inst];
+    const int col = 3 * li + cc;
+    double acc = 0.0;
+    for (int k = 0; k < I.r; ++k) acc = fma(Rt[(long long)k * 3 * nr + col], q[k], acc);
+    c.dst_hist[dst_index(c, inst, slot, f, cc, c.row[gr])] = acc;
+}
+
+__global__ void k_rom_norms_b(const RomB r, const int* __restrict__ active, double dt) {
+    const int inst = blockIdx.x;
+    if (active && !active[inst]) return;
+    const InstRom I = r.inst[inst];
+    const double* q = r.q + I.q_off;
+    double* pq = r.pq + I.q_off;
+    double num = 0.0, den = 0.0;
+    for (int k = threadIdx.x; k < I.r; k += blockDim.x) {
+        const double x = (q[k] - pq[k]) + dt * (q[I.r + k] - pq[I.r + k]);
+        const double y = fma(dt, q[I.r + k], q[k]);
+        num = fma(x, x, num);
+        den = fma(y, y, den);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < I.r; k += blockDim.x) {
+        pq[k] = q[k];
+        pq[I.r + k] = q[I.r + k];
+    }
+    block_sum2(num, den);
+    if (threadIdx.x == 0) {
+        r.npart[2 * inst] = num;
+        r.npart[2 * inst + 1] = den;
+    }
+}
+
+__global__ void k_saverest_rom_b(const RomB r, const int* __restrict__ active, int restore) {
+    const int inst = blockIdx.x;
+    if (active && !active[inst]) return;
+    const InstRom I = r.inst[inst];
+    for (int k = threadIdx.x; k < 3 * I.r; k += blockDim.x) {
+        if (restore) r.q[I.q_off + k] = r.sq[I.q_off + k];
+        else r.sq[I.q_off + k] = r.q[I.q_off + k];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// controller
+// ------------------------------------------------------------------------------------------------
+__global__ void k_reset_ctl(const CtlB c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n_inst) return;
+    c.active[i] = 1;
+    c.iters[i] = 0;
+    c.status[i] = OSAM_OK;
+    c.cnum[i] = 0.0;
+    c.cden[i] = 0.0;
+    if (i == 0) *c.any_active = 1;
+}
+
+// one block per instance: criterion sums (fixed order), convergence decision; the last block to
+// finish publishes "any instance still iterating" (and sets the while-node condition in a graph)
+__global__ void __launch_bounds__(256) k_controller(const CtlB c, cudaGraphConditionalHandle h, int use_cond) {
+    __shared__ bool last_block;
+    const int inst = blockIdx.x;
+    const bool act = c.active[inst] != 0;
+    double num = 0.0, den = 0.0;
+    if (act) {
+        for (int s = 0; s < c.n_fom; ++s) {
+            const int b0 = c.fom_blk_off[s][inst], b1 = c.fom_blk_off[s][inst + 1];
+            for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+                num += c.fom_partial[s][2 * b];
+                den += c.fom_partial[s][2 * b + 1];
+            }
+        }
+    }
+    block_sum2(num, den);
+    if (threadIdx.x == 0 && act) {
+        for (int s = 0; s < c.n_rom; ++s) {
+            num += c.rom_npart[s][2 * inst];
+            den += c.rom_npart[s][2 * inst + 1];
+        }
+        const int n = c.iters[inst] + 1;
+        c.iters[inst] = n;
+        c.cnum[inst] = num;
+        c.cden[inst] = den;
+        int done = 0, st = OSAM_OK;
+        if (!(isfinite(num) && isfinite(den))) { done = 1; st = OSAM_ENONFINITE; }
+        else if (c.ncpl == 0) done = 1;
+        else if (n >= 2 && (num < c.tol_abs2 || num < c.tol_rel2 * den)) done = 1;
+        else if (n >= c.max_it) { done = 1; st = OSAM_MAXITER; }
+        if (done) {
+            c.status[inst] = st;
+            c.active[inst] = 0;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int ticket = atomicAdd(c.counter, 1u);
+        last_block = ticket == (unsigned int)(c.n_inst - 1);
+    }
+    __syncthreads();
+    if (!last_block || threadIdx.x != 0) return;
+    __threadfence();
+    int any = 0;
+    for (int i = 0; i < c.n_inst; ++i) any |= __ldcg(c.active + i);
+    *c.any_active = any;
+    *c.counter = 0u;
+    if (use_cond) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock,
+                           cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    const int b = g.eblock;
+    (void)eblock;
+#define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<g.n_eblk, b, 0, s>>>(g, active, u)
+    const bool fp32 = g.fp32 != 0;
+    if (g.material == OSAM_NEO_HOOKEAN) {
+        if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kGather); }
+        else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kGather); }
+    } else {
+        if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kGather); }
+        else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kGather); }
+    }
+#undef OSAM_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    if (g.material == OSAM_NEO_HOOKEAN)
+        k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0]);
+    else
+        k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_accel_b(const FomB& g, const int* active, cudaStream_t s) {
+    k_init_accel_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slot1, int slot2, int predict_only,
+                          const double* ucur, double* unext, double dt, cudaStream_t s) {
+    const bool fp32 = g.fp32 != 0;
+    if (fp32) {
+        if (scatter == kAtomic) k_node_b<float, kAtomic><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
+        else k_node_b<float, kGather><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
+    } else {
+        if (scatter == kAtomic) k_node_b<double, kAtomic><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
+        else k_node_b<double, kGather><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_saverest_fom_b(const FomB& g, const int* active, int restore, cudaStream_t s) {
+    k_saverest_fom_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, restore);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_u10_b(const FomB& g, const int* active, cudaStream_t s) {
+    k_copy_u10_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norms_fom_b(const FomB& g, const int* active, double dt, cudaStream_t s) {
+    k_norms_fom_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
+                           cudaStream_t s) {
+    if (c.R == 0) return cudaSuccess;
+    k_trace_b<<<grid_for(3LL * c.R, 128), 128, 0, s>>>(c, active, src, u, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_publish_b(const CplB& c, const int* active, int nsub, cudaStream_t s) {
+    if (c.R == 0 || nsub == 0) return cudaSuccess;
+    k_publish_b<<<grid_for(9LL * c.R * nsub, 256), 256, 0, s>>>(c, active, nsub);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zoh_fom_b(const CplB& c, const int* active, const FomB& src, int nsub, cudaStream_t s) {
+    if (c.R == 0) return cudaSuccess;
+    k_zoh_fom_b<<<grid_for(3LL * c.R, 128), 128, 0, s>>>(c, active, src, nsub + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rom_record0_b(const RomB& r, const int* active, cudaStream_t s) {
+    k_rom_record0_b<<<r.n_inst, 128, 0, s>>>(r, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rom_project_b(const RomB& r, const int* active, int slot0, int slot1, cudaStream_t s) {
+    if (r.rs_max == 0 || slot1 < slot0) return cudaSuccess;
+    dim3 g(r.rs_max, slot1 - slot0 + 1, r.n_inst);
+    k_rom_project_b<<<g, 128, 0, s>>>(r, active, slot0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rom_step_b(const RomB& r, const int* active, int slot, double dt, int rhs_only, cudaStream_t s) {
+    if (r.r_max > kMaxR) return cudaErrorInvalidValue;
+    dim3 g(r.gx_max, r.gy_max, r.n_inst);
+    k_rom_step_b<<<g, kRomBlock, 0, s>>>(r, active, slot, dt, rhs_only);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int nsub,
+                                     cudaStream_t s) {
+    if (c.R == 0) return cudaSuccess;
+    if (zoh) {
+        dim3 g(grid_for(3LL * c.R, 128), nsub + 1, 3);
+        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 1, 0);
+    } else {
+        dim3 g(grid_for(3LL * c.R, 128), nsub, 3);
+        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 0, 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rom_norms_b(const RomB& r, const int* active, double dt, cudaStream_t s) {
+    k_rom_norms_b<<<r.n_inst, 128, 0, s>>>(r, active, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_saverest_rom_b(const RomB& r, const int* active, int restore, cudaStream_t s) {
+    k_saverest_rom_b<<<r.n_inst, 128, 0, s>>>(r, active, restore);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_ctl(const CtlB& c, cudaStream_t s) {
+    k_reset_ctl<<<grid_for(c.n_inst, 128), 128, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s) {
+    k_controller<<<c.n_inst, 256, 0, s>>>(c, h, use_cond);
+    return cudaGetLastError();
+}
+
+}  // namespace osam

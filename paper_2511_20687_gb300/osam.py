@@ -25,7 +25,10 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
             "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
-            "osam_profile", "osam_profile_read", "osam_fp64_peak", "osam_hex8_force_noalloc"]
+            "osam_profile", "osam_profile_read", "osam_fp64_peak", "osam_hex8_force_noalloc", "osam_batch_init",
+            "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
+            "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
+            "osam_set_graph", "osam_tuning"]
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
@@ -121,6 +124,15 @@ def load():
     L.osam_profile_read.argtypes = [_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                     C.POINTER(C.c_longlong)]
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
+    L.osam_batch_init.argtypes = [C.c_int, C.POINTER(ProblemDesc), C.POINTER(_vp)]
+    L.osam_batch_step.argtypes = [_vp, C.POINTER(StepReport), C.POINTER(StepReport)]
+    L.osam_num_instances.argtypes = [_vp]
+    for f in ("osam_instance_get_state", "osam_instance_set_state", "osam_instance_get_reduced_state",
+              "osam_instance_set_reduced_state"):
+        getattr(L, f).argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
+    L.osam_instance_sizes.argtypes = [_vp, C.c_int, C.c_int] + [C.POINTER(C.c_int)] * 4
+    L.osam_set_graph.argtypes = [_vp, C.c_int]
+    L.osam_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.osam_hex8_force_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                           _vp, _vp, _vp, _vp, _vp]
     _lib = L
@@ -178,63 +190,73 @@ def _stream_handle(stream):
 _MAT = {"le": LINEAR_ELASTIC, "nh": NEO_HOOKEAN, LINEAR_ELASTIC: LINEAR_ELASTIC, NEO_HOOKEAN: NEO_HOOKEAN}
 
 
-class Problem:
-    """A coupled O-SAM problem on the GPU, built from a workloads.Problem spec.
+class Batch:
+    """n instances of one coupled O-SAM problem advanced together on the GPU (osam_batch_init).
 
-    rom_ops: {subdomain index: {"Phi", "Phi_S", "K", "H", "B", "c"}} for the ROM subdomains.
+    specs: list of workloads.Problem with identical topology; rom_ops: list (one per instance) of
+    {subdomain index: {"Phi", "Phi_S", "K", "H", "B", "c"}} for the ROM subdomains (or None).
     """
 
-    def __init__(self, spec, rom_ops: Optional[Dict[int, dict]] = None, precision: int = FP64,
-                 scatter: int = SCATTER_AUTO, device: int = 0, stream=None):
+    def __init__(self, specs, rom_ops=None, precision: int = FP64, scatter: int = SCATTER_AUTO, device: int = 0,
+                 stream=None, graph: bool = True):
         L = load()
-        self.spec = spec
+        specs = list(specs)
+        rom_ops = rom_ops or [None] * len(specs)
+        self.specs = specs
         self._keep = []
-        rom_ops = rom_ops or {}
-        nsd = len(spec.subdomains)
-        subs = (SubdomainDesc * nsd)()
+        descs = (ProblemDesc * len(specs))()
         self.rank = {}
-        for i, sd in enumerate(spec.subdomains):
-            d = subs[i]
-            d.kind = FOM if sd.kind == "fom" else ROM
-            d.nx, d.ny, d.nz = sd.dims
-            d.h = sd.h
-            d.origin = (C.c_double * 3)(*sd.origin)
-            d.material = _MAT[sd.material]
-            d.lambda_, d.mu, d.rho = sd.lam, sd.mu, sd.rho
-            arrs = {"lambda_e": _f64(sd.lam_e), "mu_e": _f64(sd.mu_e), "dirichlet": _u8(sd.dirichlet),
-                    "u0": _f64(sd.u0), "v0": _f64(sd.v0)}
-            if sd.kind == "rom":
-                ops = rom_ops[i]
-                for k in ("Phi", "Phi_S", "K", "H", "B", "c"):
-                    arrs[k] = _f64(ops[k])
-                d.r = int(ops["Phi"].shape[1])
-                d.r_s = int(ops["Phi_S"].shape[1])
-                self.rank[i] = d.r
-            for k, a in arrs.items():
-                self._keep.append(a)
-                setattr(d, k, _ptr(a))
-        cpls = (CouplingDesc * max(1, len(spec.couplings)))()
-        for k, cp in enumerate(spec.couplings):
-            m = _u8(cp.nodes)
-            self._keep.append(m)
-            cpls[k].dst, cpls[k].src, cpls[k].nodes = cp.dst, cp.src, _ptr(m)
-        desc = ProblemDesc()
-        desc.n_subdomains = nsd
-        desc.subdomains = subs
-        desc.n_couplings = len(spec.couplings)
-        desc.couplings = cpls
-        desc.dt = spec.dt
-        desc.n_substeps = spec.n_substeps
-        desc.tol_abs, desc.tol_rel = spec.tol_abs, spec.tol_rel
-        desc.max_iters = spec.max_iters
-        desc.precision = precision
-        desc.scatter = scatter
-        desc.stream = _stream_handle(stream)
-        desc.device = device
+        for n, (spec, ops_n) in enumerate(zip(specs, rom_ops)):
+            ops_n = ops_n or {}
+            nsd = len(spec.subdomains)
+            subs = (SubdomainDesc * nsd)()
+            self._keep.append(subs)
+            for i, sd in enumerate(spec.subdomains):
+                d = subs[i]
+                d.kind = FOM if sd.kind == "fom" else ROM
+                d.nx, d.ny, d.nz = sd.dims
+                d.h = sd.h
+                d.origin = (C.c_double * 3)(*sd.origin)
+                d.material = _MAT[sd.material]
+                d.lambda_, d.mu, d.rho = sd.lam, sd.mu, sd.rho
+                arrs = {"lambda_e": _f64(sd.lam_e), "mu_e": _f64(sd.mu_e), "dirichlet": _u8(sd.dirichlet),
+                        "u0": _f64(sd.u0), "v0": _f64(sd.v0)}
+                if sd.kind == "rom":
+                    ops = ops_n[i]
+                    for k in ("Phi", "Phi_S", "K", "H", "B", "c"):
+                        arrs[k] = _f64(ops[k])
+                    d.r = int(ops["Phi"].shape[1])
+                    d.r_s = int(ops["Phi_S"].shape[1])
+                    self.rank[(n, i)] = d.r
+                for k, a in arrs.items():
+                    self._keep.append(a)
+                    setattr(d, k, _ptr(a))
+            cpls = (CouplingDesc * max(1, len(spec.couplings)))()
+            self._keep.append(cpls)
+            for k, cp in enumerate(spec.couplings):
+                m = _u8(cp.nodes)
+                self._keep.append(m)
+                cpls[k].dst, cpls[k].src, cpls[k].nodes = cp.dst, cp.src, _ptr(m)
+            desc = descs[n]
+            desc.n_subdomains = nsd
+            desc.subdomains = subs
+            desc.n_couplings = len(spec.couplings)
+            desc.couplings = cpls
+            desc.dt = spec.dt
+            desc.n_substeps = spec.n_substeps
+            desc.tol_abs, desc.tol_rel = spec.tol_abs, spec.tol_rel
+            desc.max_iters = spec.max_iters
+            desc.precision = precision
+            desc.scatter = scatter
+            desc.stream = _stream_handle(stream)
+            desc.device = device
         h = _vp()
-        _check(L.schwarz_init(C.byref(desc), C.byref(h)), None)
+        _check(L.osam_batch_init(len(specs), descs, C.byref(h)), None)
         self.h = h
+        self.n = len(specs)
         self._keep = None  # the library copied everything it needs
+        if not graph:
+            self._c(L.osam_set_graph(self.h, 0))
 
     def close(self):
         if getattr(self, "h", None):
@@ -250,11 +272,88 @@ class Problem:
     def _c(self, code):
         return _check(code, self.h)
 
+    def set_graph(self, enable: bool):
+        self._c(load().osam_set_graph(self.h, int(enable)))
+
+    def step(self):
+        """One controller step of every instance: (per-instance reports, aggregate report)."""
+        reps = (StepReport * self.n)()
+        tot = StepReport()
+        rc = self._c(load().osam_batch_step(self.h, reps, C.byref(tot)))
+        per = [{"status": r.status, "iterations": r.iterations, "cnum": r.cnum, "cden": r.cden,
+                "element_updates": r.element_updates, "elapsed_ms": r.elapsed_ms} for r in reps]
+        return per, {"status": rc, "iterations": tot.iterations, "cnum": tot.cnum, "cden": tot.cden,
+                     "element_updates": tot.element_updates, "elapsed_ms": tot.elapsed_ms}
+
+    def tuning(self):
+        sc, eb = C.c_int(), C.c_int()
+        self._c(load().osam_tuning(self.h, C.byref(sc), C.byref(eb)))
+        return {"scatter": "atomic" if sc.value == SCATTER_ATOMIC else "gather", "element_block": eb.value}
+
+    def profile(self, enable=True):
+        """Start (and reset) kernel-level accounting of the internal-force launches."""
+        self._c(load().osam_profile(self.h, int(enable)))
+
+    def profile_read(self) -> dict:
+        ms = C.c_double()
+        fl, fe, kl = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        self._c(load().osam_profile_read(self.h, C.byref(ms), C.byref(fl), C.byref(fe), C.byref(kl)))
+        return {"force_ms": ms.value, "force_launches": fl.value, "force_elements": fe.value,
+                "kernel_launches": kl.value}
+
+    def sizes(self, i, inst=0):
+        v = [C.c_int() for _ in range(4)]
+        self._c(load().osam_instance_sizes(self.h, inst, i, *[C.byref(x) for x in v]))
+        return {"n_nodes": v[0].value, "n_elements": v[1].value, "n_free": v[2].value, "n_schwarz": v[3].value}
+
+    def state(self, i, out=None, fields=(0, 1, 2), inst=0):
+        """(u, v, a) of subdomain i of instance inst as [nodes, 3] arrays (numpy unless `out` arrays /
+        tensors are given; fields not listed are returned as None)."""
+        n = self.sizes(i, inst)["n_nodes"]
+        if out is None:
+            out = tuple(np.zeros((n, 3)) if f in fields else None for f in range(3))
+        self._c(load().osam_instance_get_state(self.h, inst, i, *[_ptr(x) for x in out]))
+        return out
+
+    def set_state(self, i, u, v=None, a=None, inst=0):
+        u, v, a = _f64(u), _f64(v), _f64(a)
+        self._c(load().osam_instance_set_state(self.h, inst, i, _ptr(u), _ptr(v), _ptr(a)))
+
+    def reduced_state(self, i, inst=0):
+        r = self.rank[(inst, i)]
+        outs = tuple(np.zeros(r) for _ in range(3))
+        self._c(load().osam_instance_get_reduced_state(self.h, inst, i, *[_ptr(x) for x in outs]))
+        return outs
+
+    def set_reduced_state(self, i, q, qd=None, qdd=None, inst=0):
+        q, qd, qdd = _f64(q), _f64(qd), _f64(qdd)
+        self._c(load().osam_instance_set_reduced_state(self.h, inst, i, _ptr(q), _ptr(qd), _ptr(qdd)))
+
+
+class Problem(Batch):
+    """A single coupled O-SAM problem on the GPU (a batch of one), built from a workloads.Problem spec.
+
+    rom_ops: {subdomain index: {"Phi", "Phi_S", "K", "H", "B", "c"}} for the ROM subdomains.
+    """
+
+    def __init__(self, spec, rom_ops: Optional[Dict[int, dict]] = None, precision: int = FP64,
+                 scatter: int = SCATTER_AUTO, device: int = 0, stream=None, graph: bool = True):
+        super().__init__([spec], [rom_ops], precision=precision, scatter=scatter, device=device, stream=stream,
+                         graph=graph)
+        self.spec = spec
+        self.rank = {i: r for (_, i), r in self.rank.items()}
+
     def step(self) -> dict:
         rep = StepReport()
         rc = self._c(load().schwarz_step(self.h, C.byref(rep)))
         return {"status": rc, "iterations": rep.iterations, "cnum": rep.cnum, "cden": rep.cden,
                 "element_updates": rep.element_updates, "elapsed_ms": rep.elapsed_ms}
+
+    def reduced_state(self, i, inst=0):
+        r = self.rank[i]
+        outs = tuple(np.zeros(r) for _ in range(3))
+        self._c(load().osam_instance_get_reduced_state(self.h, inst, i, *[_ptr(x) for x in outs]))
+        return outs
 
     def advance(self, i):
         self._c(load().subdomain_advance(self.h, i))
@@ -273,47 +372,8 @@ class Problem:
         self._c(load().osam_criterion(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
-    def sizes(self, i):
-        v = [C.c_int() for _ in range(4)]
-        self._c(load().osam_sizes(self.h, i, *[C.byref(x) for x in v]))
-        return {"n_nodes": v[0].value, "n_elements": v[1].value, "n_free": v[2].value, "n_schwarz": v[3].value}
-
     def scatter_mode(self):
         return load().osam_scatter_mode(self.h)
-
-    def profile(self, enable=True):
-        """Start (and reset) kernel-level accounting of the internal-force launches."""
-        self._c(load().osam_profile(self.h, int(enable)))
-
-    def profile_read(self) -> dict:
-        ms = C.c_double()
-        fl, fe, kl = C.c_longlong(), C.c_longlong(), C.c_longlong()
-        self._c(load().osam_profile_read(self.h, C.byref(ms), C.byref(fl), C.byref(fe), C.byref(kl)))
-        return {"force_ms": ms.value, "force_launches": fl.value, "force_elements": fe.value,
-                "kernel_launches": kl.value}
-
-    def state(self, i, out=None, fields=(0, 1, 2)):
-        """(u, v, a) of subdomain i as [nodes, 3] arrays (numpy unless `out` arrays / tensors are given;
-        fields not listed are returned as None)."""
-        n = self.sizes(i)["n_nodes"]
-        if out is None:
-            out = tuple(np.zeros((n, 3)) if f in fields else None for f in range(3))
-        self._c(load().osam_get_state(self.h, i, *[_ptr(x) for x in out]))
-        return out
-
-    def set_state(self, i, u, v=None, a=None):
-        u, v, a = _f64(u), _f64(v), _f64(a)
-        self._c(load().osam_set_state(self.h, i, _ptr(u), _ptr(v), _ptr(a)))
-
-    def reduced_state(self, i):
-        r = self.rank[i]
-        outs = tuple(np.zeros(r) for _ in range(3))
-        self._c(load().osam_get_reduced_state(self.h, i, *[_ptr(x) for x in outs]))
-        return outs
-
-    def set_reduced_state(self, i, q, qd=None, qdd=None):
-        q, qd, qdd = _f64(q), _f64(qd), _f64(qdd)
-        self._c(load().osam_set_reduced_state(self.h, i, _ptr(q), _ptr(qd), _ptr(qdd)))
 
 
 # ---------------------------------------------------------------------------------------------
