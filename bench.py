@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--snapshots", type=int, default=500)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"],
+                    help="f64: native FP64 force; f32x2: double-float force on the FP32 pipes (FP64 state)")
     ap.add_argument("--fom-only", action="store_true",
                     help="FOM-FOM coupling of the same geometry (no ROM, no training): profiling runs")
     return ap.parse_args()
@@ -257,13 +259,14 @@ def main():
     from paper_2511_20687_gb300 import osam
     from paper_2511_20687_gb300 import workloads as W
 
+    prec = osam.F32X2_FORCE if args.precision == "f32x2" else osam.FP64
     if args.fom_only:
         spec = W.fom_opinf_hybrid(args.n, args.nz, rom=False)
-        prob = osam.Problem(spec, device=local)
+        prob = osam.Problem(spec, device=local, precision=prec)
     else:
         ops = train_rom(W, osam, args, local, log)
         spec = hybrid_spec(W, args)
-        prob = osam.Problem(spec, rom_ops={1: ops}, device=local)
+        prob = osam.Problem(spec, rom_ops={1: ops}, device=local, precision=prec)
     log(f"scatter mode: {'atomic' if prob.scatter_mode() == osam.SCATTER_ATOMIC else 'gather'}")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     for _ in range(args.warmup):

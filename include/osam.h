@@ -50,7 +50,11 @@ typedef enum {
 
 enum { OSAM_FOM = 0, OSAM_ROM = 1 };
 enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1 };
-enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1 };
+/* OSAM_FP64: native FP64 everywhere.  OSAM_FP32_FORCE: internal force in FP32 (checked to 1e-5).
+ * OSAM_F32X2_FORCE: internal force in double-float arithmetic (pairs of FP32 values, ~48-bit
+ * significands) on the FP32 pipes, state and time integration in FP64 (checked to 1e-9 like FP64);
+ * uses the deterministic gather scatter. */
+enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1, OSAM_F32X2_FORCE = 2 };
 /* element-to-node scatter of the internal force: FP64 atomics, or a deterministic two-pass
  * element-buffer / node-gather scheme; AUTO times both on the first step and keeps the faster */
 enum { OSAM_SCATTER_AUTO = 0, OSAM_SCATTER_ATOMIC = 1, OSAM_SCATTER_GATHER = 2 };

@@ -378,7 +378,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     if (d0.n_couplings < 0 || (d0.n_couplings > 0 && !d0.couplings)) return ctx->fail(OSAM_EINVAL, "bad couplings");
     if (!(d0.dt > 0.0) || d0.n_substeps < 1 || d0.max_iters < 1)
         return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
-    if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE) return ctx->fail(OSAM_EINVAL, "bad precision");
+    if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE)
+        return ctx->fail(OSAM_EINVAL, "bad precision");
     for (int k = 0; k < d0.n_couplings; ++k) {
         const osam_coupling_desc& c = d0.couplings[k];
         if (c.dst < 0 || c.dst >= d0.n_subdomains || c.src < 0 || c.src >= d0.n_subdomains || c.dst == c.src)
@@ -459,6 +460,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     B.n_inst = n; B.NN = NN; B.NE = NE;
     B.material = descs[0].subdomains[s].material;
     B.fp32 = fp32;
+    B.df32 = ctx->precision == OSAM_F32X2_FORCE;
     B.scatter = ctx->scatter;
     double* minv = ctx->alloc<double>(NN);
     uint8_t* clamp = ctx->alloc<uint8_t>(NN);
@@ -476,6 +478,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     CKA(B.pu = ctx->alloc<double>(3 * NN));
     CKA(B.pv = ctx->alloc<double>(3 * NN));
     CKA(B.hist = ctx->alloc<double>(std::max<long long>(H, 1)));
+    if (B.df32) CKA(B.u2 = ctx->alloc<float2>(3 * NN));
     bool any_le = false, any_me = false;
     for (int i = 0; i < n; ++i) {
         any_le |= descs[i].subdomains[s].lambda_e != nullptr;
@@ -525,6 +528,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     B.nblk_off = nbo;
     CKA(B.partial = ctx->alloc<double>(2LL * B.n_nblk));
     RET(set_eblocks(ctx, G, 128));
+    if (B.df32) CK(launch_split_u2_b(B, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }
@@ -873,6 +877,7 @@ int autotune(osam_ctx* ctx) {
     const int cands[6][2] = {{kGather, 64}, {kGather, 128}, {kGather, 256}, {kAtomic, 64}, {kAtomic, 128}, {kAtomic, 256}};
     for (const auto& cd : cands) {
         const int mode = cd[0], block = cd[1];
+        if (g.df32 && mode == kAtomic) continue;  // the double-float force has the gather scatter only
         RET(set_eblocks(ctx, G, block));
         g.eblk = G.d.eblk;
         g.n_eblk = G.d.n_eblk;
@@ -920,7 +925,7 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     ctx->tol_rel = d0.tol_rel;
     ctx->max_it = d0.max_iters;
     ctx->precision = d0.precision;
-    ctx->scatter = d0.scatter == OSAM_SCATTER_ATOMIC ? kAtomic : kGather;
+    ctx->scatter = (d0.scatter == OSAM_SCATTER_ATOMIC && d0.precision != OSAM_F32X2_FORCE) ? kAtomic : kGather;
     CK(cudaEventCreate(&ctx->ev0));
     CK(cudaEventCreate(&ctx->ev1));
     CKA(ctx->err_d = ctx->alloc<int>(1));

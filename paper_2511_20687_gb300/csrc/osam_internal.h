@@ -86,7 +86,9 @@ struct FomB {
     double* pv;
     double* hist;             // per instance [(nsub+1)][3 fields][3 comps][ns] at hist_off
     double* partial;          // criterion partial sums, 2 per node block
+    float2* u2;               // double-float copy of the predicted displacement [3][NN] (f32x2 force)
     int material, fp32, scatter;
+    int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 
 // one instance of a ROM slot
@@ -172,6 +174,7 @@ cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slo
 cudaError_t launch_saverest_fom_b(const FomB& g, const int* active, int restore, cudaStream_t s);
 cudaError_t launch_norms_fom_b(const FomB& g, const int* active, double dt, cudaStream_t s);
 cudaError_t launch_copy_u10_b(const FomB& g, const int* active, cudaStream_t s);
+cudaError_t launch_split_u2_b(const FomB& g, cudaStream_t s);
 cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
                            cudaStream_t s);
 cudaError_t launch_publish_b(const CplB& c, const int* active, int nsub, cudaStream_t s);

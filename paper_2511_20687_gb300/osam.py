@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libosam.so")
 OK, MAXITER, EINVAL, ECFL, ENONFINITE, EDONOR, ECUDA, ETIMEOUT, ENOMEM = 0, 1, -1, -2, -3, -4, -5, -6, -7
 FOM, ROM = 0, 1
 LINEAR_ELASTIC, NEO_HOOKEAN = 0, 1
-FP64, FP32_FORCE = 0, 1
+FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER = 0, 1, 2
 
 EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin_interval", "osam_restore_interval",

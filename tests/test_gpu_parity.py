@@ -356,3 +356,25 @@ def test_profile_counters(torch_cuda):
     assert p["force_elements"] == r["element_updates"]
     assert p["force_ms"] > 0.0 and p["kernel_launches"] > p["force_launches"]
     assert osam.fp64_peak_gflops(0) > 0.0
+
+
+# ---------------------------------------------------------------------------------------------
+# double-float force (f32x2): held to the FP64 tolerance
+# ---------------------------------------------------------------------------------------------
+def test_f32x2_force_fom_fom_plain_config(torch_cuda):
+    spec = W.fom_fom_plain()
+    hist, its, gf, rf = _run_pair(spec, spec.n_controller_steps, precision=osam.F32X2_FORCE)
+    for i in range(2):
+        assert rel_l2(*hist[i]) < 1e-9
+
+
+def test_f32x2_force_neo_hookean_and_hybrid(torch_cuda, fitted_hybrid):
+    spec = W.bar_chain("nh_df", 5, [9, 7], ["fom", "fom"], "nh", 1e9, 0.3, 1000.0, 2e-3, 1e-6, 7)
+    hist, _, _, _ = _run_pair(spec, 4, precision=osam.F32X2_FORCE)
+    for i in range(2):
+        assert rel_l2(*hist[i]) < 1e-9
+    pr, ops = fitted_hybrid
+    pr.max_iters = 16
+    hist, _, _, _ = _run_pair(pr, 5, rom_ops=ops, precision=osam.F32X2_FORCE)
+    for i in range(2):
+        assert rel_l2(*hist[i]) < 1e-9
