@@ -64,7 +64,16 @@ __device__ __forceinline__ f2 prod(float a, float b) {
     return f2{p, __fmaf_rn(a, b, -p)};
 }
 
-__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return add(mul(a, b), c); }
+// a * b + c with one renormalisation: the product's error terms are folded into the sum's
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    f2 s = two_sum(p, c.h);
+    s.l = __fadd_rn(s.l, __fadd_rn(e, c.l));
+    return fast_two_sum(s.h, s.l);
+}
 
 __device__ __forceinline__ f2 from_double(double x) {
     const float h = __double2float_rn(x);

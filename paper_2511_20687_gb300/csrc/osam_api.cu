@@ -877,7 +877,7 @@ int autotune(osam_ctx* ctx) {
     const int cands[6][2] = {{kGather, 64}, {kGather, 128}, {kGather, 256}, {kAtomic, 64}, {kAtomic, 128}, {kAtomic, 256}};
     for (const auto& cd : cands) {
         const int mode = cd[0], block = cd[1];
-        if (g.df32 && mode == kAtomic) continue;  // the double-float force has the gather scatter only
+        if (g.df32 && (mode == kAtomic || block > 128)) continue;  // double-float force: gather, <= 128 threads
         RET(set_eblocks(ctx, G, block));
         g.eblk = G.d.eblk;
         g.n_eblk = G.d.n_eblk;

@@ -278,6 +278,138 @@ __global__ void __launch_bounds__(256) k_force_df_b(const FomB g, const int* __r
     }
 }
 
+// Phased double-float force: (A) edge differences and interpolation to the Gauss points, unrolled,
+// the 36 gradient entries parked in shared memory; (B) a rolled loop over the 8 Gauss points with one
+// copy of the constitutive code, accumulating the Gauss-point sums of the transposed interpolation in
+// shared memory; (C) the transposed interpolation, unrolled.  Keeping the code small keeps it in the
+// instruction cache.  Shared memory is private per thread (column tid of a [72][blockDim] array of
+// float2), so no barrier is needed.
+constexpr int kDfSlots = 72;  // 36 gradient entries + 36 accumulated sums
+
+template <int MAT>
+__global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __restrict__ active) {
+    using df::f2;
+    extern __shared__ float2 sm[];
+    const int2 b = g.eblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int e = b.y + threadIdx.x;
+    if (e >= I.ne) return;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    auto slot = [&](int s) -> float2& { return sm[s * nt + tid]; };
+    auto ld = [&](int s) -> f2 { const float2 v = slot(s); return df::make(v.x, v.y); };
+    auto st = [&](int s, f2 v) { slot(s) = make_float2(v.h, v.l); };
+    const int i = e % I.nx;
+    const int t = e / I.nx;
+    const int j = t % I.ny;
+    const int k = t / I.ny;
+    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
+    const int n0 = i + sy * j + sz * k;
+    // (A) gradients: slot (dir * 12 + c * 4 + 2 * s0 + s1), dir 0: Gx[c][q][r], 1: Gy[c][p][r], 2: Gz[c][p][q]
+    {
+        const f2 invh = df::from_double(I.invh);
+        const float2* ub = g.u2 + I.node_off;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            f2 U[8];
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+                const float2 v = ub[(long long)c * g.NN + n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz];
+                U[c8] = df::make(v.x, v.y);
+            }
+            f2 D[2][2], G[2][2];
+#pragma unroll
+            for (int dir = 0; dir < 3; ++dir) {
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int hi = dir == 0 ? 1 + 2 * p + 4 * q : (dir == 1 ? p + 2 + 4 * q : p + 2 * q + 4);
+                        const int lo = dir == 0 ? 2 * p + 4 * q : (dir == 1 ? p + 4 * q : p + 2 * q);
+                        D[p][q] = df::mul(df::sub(U[hi], U[lo]), invh);
+                    }
+                dfk::lerp2(D, G);
+#pragma unroll
+                for (int p = 0; p < 2; ++p)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) st(dir * 12 + c * 4 + 2 * p + q, G[p][q]);
+            }
+        }
+    }
+    // (B) constitutive law at each Gauss point; sums into slots 36 + (dir * 12 + c * 4 + ...)
+    {
+        const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+        const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+        f2 m1, m2, m3;
+        if (MAT == OSAM_NEO_HOOKEAN) {
+            const double kappa = lam + (2.0 / 3.0) * mu;
+            m1 = df::from_double(0.5 * kappa * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::from_double(mu * I.w8 / 3.0);
+        } else {
+            m1 = df::from_double(lam * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::make(0.f, 0.f);
+        }
+#pragma unroll 1
+        for (int gp = 0; gp < 8; ++gp) {
+            const int p = gp >> 2, q = (gp >> 1) & 1, r = gp & 1;
+            f2 Hm[3][3], P[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Hm[c][0] = ld(0 * 12 + c * 4 + 2 * q + r);
+                Hm[c][1] = ld(1 * 12 + c * 4 + 2 * p + r);
+                Hm[c][2] = ld(2 * 12 + c * 4 + 2 * p + q);
+            }
+            if (MAT == OSAM_NEO_HOOKEAN) dfk::stress_nh(Hm, m1, m2, m3, P);
+            else dfk::stress_le(Hm, m1, m2, P);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int sx = 36 + 0 * 12 + c * 4 + 2 * q + r;
+                const int sy_ = 36 + 1 * 12 + c * 4 + 2 * p + r;
+                const int sz_ = 36 + 2 * 12 + c * 4 + 2 * p + q;
+                st(sx, p == 0 ? P[c][0] : df::add(ld(sx), P[c][0]));
+                st(sy_, q == 0 ? P[c][1] : df::add(ld(sy_), P[c][1]));
+                st(sz_, r == 0 ? P[c][2] : df::add(ld(sz_), P[c][2]));
+            }
+        }
+    }
+    // (C) transposed interpolation and edge-difference transpose, per component
+    float2* fe = static_cast<float2*>(g.fe) + I.elem_off;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        f2 F[8], S[2][2], Tm[2][2];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 0 * 12 + c * 4 + s);
+        dfk::lerp2T(S, Tm);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) {
+                F[1 + 2 * ay + 4 * az] = Tm[ay][az];
+                F[2 * ay + 4 * az] = df::neg(Tm[ay][az]);
+            }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 1 * 12 + c * 4 + s);
+        dfk::lerp2T(S, Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) {
+                F[ax + 2 + 4 * az] = df::add(F[ax + 2 + 4 * az], Tm[ax][az]);
+                F[ax + 4 * az] = df::sub(F[ax + 4 * az], Tm[ax][az]);
+            }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 2 * 12 + c * 4 + s);
+        dfk::lerp2T(S, Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) {
+                F[ax + 2 * ay + 4] = df::add(F[ax + 2 * ay + 4], Tm[ax][ay]);
+                F[ax + 2 * ay] = df::sub(F[ax + 2 * ay], Tm[ax][ay]);
+            }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = make_float2(F[c8].h, F[c8].l);
+    }
+}
+
 // node kernel of the double-float force: contributions summed in double-float in a fixed order,
 // the update in FP64, and the double-float copy of the predicted displacement for the next force
 __global__ void __launch_bounds__(kNodeBlock) k_node_df_b(const FomB g, const int* __restrict__ active, int slot1,
@@ -854,8 +986,21 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
     const int b = g.eblock;
     (void)eblock;
     if (g.df32) {
-        if (g.material == OSAM_NEO_HOOKEAN) k_force_df_b<OSAM_NEO_HOOKEAN><<<g.n_eblk, b, 0, s>>>(g, active);
-        else k_force_df_b<OSAM_LINEAR_ELASTIC><<<g.n_eblk, b, 0, s>>>(g, active);
+        if (b > 128) return cudaErrorInvalidConfiguration;
+        const size_t smem = sizeof(float2) * kDfSlots * b;
+        static bool attr_set = false;  // opt in to more than 48 KB of dynamic shared memory, once
+        if (!attr_set) {
+            const int max_bytes = (int)(sizeof(float2) * kDfSlots * 128);
+            cudaError_t e1 = cudaFuncSetAttribute(k_force_df2_b<OSAM_NEO_HOOKEAN>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+            cudaError_t e2 = cudaFuncSetAttribute(k_force_df2_b<OSAM_LINEAR_ELASTIC>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+            if (e1 != cudaSuccess) return e1;
+            if (e2 != cudaSuccess) return e2;
+            attr_set = true;
+        }
+        if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<g.n_eblk, b, smem, s>>>(g, active);
+        else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<g.n_eblk, b, smem, s>>>(g, active);
         return cudaGetLastError();
     }
 #define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<g.n_eblk, b, 0, s>>>(g, active, u)
