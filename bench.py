@@ -43,9 +43,13 @@ UNIT = "element-updates/s"
 FLOPS_PER_NH_ELEMENT = 1232
 # FP64 peak: recipe figure for the GB300 (nominal FP64 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
+# double-float force: FP32-pipe thread-instructions per Neo-Hookean element (ncu smsp__inst_executed
+# x 32 / elements of the phased kernel) and the FP32 issue peak (152 SMs x 128 lanes x 2.07 GHz)
+F32X2_INST_PER_NH_ELEMENT = 12012
+FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source it was captured on; None until captured.
-FORCE_TRAFFIC = {"source_sha256": "392b6d4c6cd81505f9c4eb523f304ec055fe8f45507835a54e802ac7bb07f9ca", "bytes_per_launch": 3.36e6}
+FORCE_TRAFFIC = {"source_sha256": "6f239e5091b53d0b29937186ac773b4688378b31af430e1f19314a2a82e316a3", "bytes_per_launch": 3.366e6}
 
 
 def parse():
@@ -129,8 +133,10 @@ class ClockSampler:
 
 def source_sha():
     import hashlib
-    p = os.path.join(ROOT, "paper_2511_20687_gb300", "csrc", "fom_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for f in ("step_kernels.cu", "hex8_math.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2511_20687_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -235,6 +241,53 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+def timed_pass(prob, torch, flush, steps, profile):
+    """`steps` controller steps with CUDA-event timing per step (L2 flushed in between, outside the
+    timing).  profile=True brackets every force launch with CUDA events (host-driven iterations)."""
+    prob.profile(profile)
+    prob.set_graph(not profile)
+    torch.cuda.synchronize()
+    total_ms, updates, iters = 0.0, 0, []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        r = prob.step()
+        total_ms += r["elapsed_ms"]
+        updates += r["element_updates"]
+        iters.append(r["iterations"])
+    torch.cuda.synchronize()
+    prof = prob.profile_read()
+    prob.profile(False)
+    return total_ms, updates, iters, prof
+
+
+def e2e_pass(prob, torch, steps, rank_r):
+    """Same metric through the public API with pinned host buffers: state in, step, state out."""
+    nA = prob.sizes(0)["n_nodes"]
+    hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
+    hq = [torch.empty(rank_r, dtype=torch.float64).pin_memory() for _ in range(3)]
+    prob.state(0, out=tuple(hu))
+    q = prob.reduced_state(1)
+    for k in range(3):
+        hq[k].copy_(torch.from_numpy(q[k]))
+    updates = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        prob.set_state(0, hu[0], hu[1], hu[2])
+        prob.set_reduced_state(1, hq[0], hq[1], hq[2])
+        r = prob.step()
+        updates += r["element_updates"]
+        prob.state(0, out=tuple(hu))
+        out_q = prob.reduced_state(1)
+        for k in range(3):
+            hq[k].copy_(torch.from_numpy(out_q[k]))
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    io_bytes = 3 * nA * 3 * 8 + 3 * rank_r * 8
+    return {"value": updates / secs, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -259,111 +312,103 @@ def main():
     from paper_2511_20687_gb300 import osam
     from paper_2511_20687_gb300 import workloads as W
 
-    prec = osam.F32X2_FORCE if args.precision == "f32x2" else osam.FP64
     if args.fom_only:
         spec = W.fom_opinf_hybrid(args.n, args.nz, rom=False)
-        prob = osam.Problem(spec, device=local, precision=prec)
+        rom_ops = None
     else:
-        ops = train_rom(W, osam, args, local, log)
+        rom_ops = {1: train_rom(W, osam, args, local, log)}
         spec = hybrid_spec(W, args)
-        prob = osam.Problem(spec, rom_ops={1: ops}, device=local, precision=prec)
-    log(f"scatter mode: {'atomic' if prob.scatter_mode() == osam.SCATTER_ATOMIC else 'gather'}")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
-    for _ in range(args.warmup):
-        r = prob.step()
-        if r["status"] < 0:
-            raise RuntimeError(r)
-    prob.profile(True)
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_push("timed")
-    total_ms, updates, iters = 0.0, 0, []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        r = prob.step()
-        total_ms += r["elapsed_ms"]
-        updates += r["element_updates"]
-        iters.append(r["iterations"])
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    prof = prob.profile_read()
-    # whole-job aggregate: all ranks' updates over the slowest rank's time
-    if world > 1:
-        t = torch.tensor([total_ms, float(updates)], dtype=torch.float64, device=f"cuda:{local}")
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms, updates = float(mx[0]), int(t[1])
-    value = updates / (total_ms * 1e-3)
-
-    # end to end through the public API with pinned host buffers
-    e2e = None
-    if args.e2e_steps > 0 and not args.fom_only:
-        nA = prob.sizes(0)["n_nodes"]
-        hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
-        hq = [torch.empty(args.rank, dtype=torch.float64).pin_memory() for _ in range(3)]
-        prob.state(0, out=tuple(hu))
-        q = prob.reduced_state(1)
-        for k in range(3):
-            hq[k].copy_(torch.from_numpy(q[k]))
-        e2e_updates = 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            prob.set_state(0, hu[0], hu[1], hu[2])
-            prob.set_reduced_state(1, hq[0], hq[1], hq[2])
+    head_prec = osam.F32X2_FORCE if args.precision == "f32x2" else osam.FP64
+    results = {}
+    for prec in ([head_prec] + [p for p in (osam.FP64, osam.F32X2_FORCE) if p != head_prec]):
+        name = "f32x2" if prec == osam.F32X2_FORCE else "f64"
+        prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=prec)
+        log(f"[{name}] tuning: {prob.tuning()}")
+        for _ in range(args.warmup):
             r = prob.step()
-            e2e_updates += r["element_updates"]
-            prob.state(0, out=tuple(hu))
-            out_q = prob.reduced_state(1)
-            for k in range(3):
-                hq[k].copy_(torch.from_numpy(out_q[k]))
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        io_bytes = 3 * nA * 3 * 8 + 3 * args.rank * 8
-        e2e = {"value": e2e_updates / e2e_s, "unit": UNIT, "h2d_bytes_per_step": io_bytes,
-               "d2h_bytes_per_step": io_bytes}
-
+        clocks = ClockSampler(local) if prec == head_prec else None
+        if clocks:
+            clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.nvtx.range_push("timed" if prec == head_prec else f"timed_{name}")
+        total_ms, updates, iters, prof = timed_pass(prob, torch, flush, args.steps, profile=True)
+        torch.cuda.nvtx.range_pop()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        g_ms, g_upd, _, _ = timed_pass(prob, torch, flush, args.steps, profile=False)
+        if world > 1:
+            t = torch.tensor([total_ms, float(updates), g_ms, float(g_upd)], dtype=torch.float64, device=f"cuda:{local}")
+            mx, sm = t.clone(), t.clone()
+            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+            total_ms, updates, g_ms, g_upd = float(mx[0]), int(sm[1]), float(mx[2]), int(sm[3])
+        e2e = e2e_pass(prob, torch, args.e2e_steps, args.rank) if (args.e2e_steps > 0 and rom_ops) else None
+        results[name] = {"total_ms": total_ms, "updates": updates, "iters": iters, "prof": prof, "clk": clk,
+                         "graph_value": g_upd / (g_ms * 1e-3), "graph_ms_per_step": g_ms / args.steps, "e2e": e2e,
+                         "tuning": prob.tuning()}
+        prob.close()
+    head = results["f32x2" if head_prec == osam.F32X2_FORCE else "f64"]
     fp64_meas = osam.fp64_peak_gflops(local) / 1e3
-    achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
-    traffic = FORCE_TRAFFIC["bytes_per_launch"] if FORCE_TRAFFIC["source_sha256"] == source_sha() else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_hex8_force<NeoHookean, f64>", "peak_kind": "recipe nominal FP64",
-                "fp64_fma_measured_tflops": fp64_meas, "frac_of_measured_fp64": achieved / fp64_meas,
-                "force_ms_per_launch": prof["force_ms"] / max(1, prof["force_launches"]),
-                "force_time_share": prof["force_ms"] / total_ms if world == 1 else None}
+
+    def roofline(res, prec_name):
+        prof = res["prof"]
+        per_launch = prof["force_ms"] / max(1, prof["force_launches"])
+        if prec_name == "f64":
+            achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
+            traffic = FORCE_TRAFFIC["bytes_per_launch"] if FORCE_TRAFFIC["source_sha256"] == source_sha() else None
+            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_force_b<NeoHookean, f64>",
+                    "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)", "fp64_fma_measured_tflops": fp64_meas,
+                    "frac_of_measured_fp64": achieved / fp64_meas, "force_ms_per_launch": per_launch,
+                    "force_time_share": prof["force_ms"] / res["total_ms"]}
+        # double-float force: FP32-pipe instruction issue is the binding unit
+        achieved = F32X2_INST_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP32_ISSUE_PEAK_TINST, "unit": "Tinst/s (FP32 pipe)",
+                "frac": achieved / FP32_ISSUE_PEAK_TINST, "traffic": None, "kernel": "k_force_df2_b<NeoHookean>",
+                "peak_kind": "152 SMs x 128 lanes x 2.07 GHz", "fp64_equivalent_tflops":
+                FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12,
+                "force_ms_per_launch": per_launch, "force_time_share": prof["force_ms"] / res["total_ms"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
         rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{steps} controller step(s) x 1 Schwarz iteration x 20 substeps of the 40x40x80 NH FOM "
-                         f"+ r={args.rank} ROM (seeded stand-in operators), {secs:.1f} s CPU"}
+               "sample": f"{steps} controller step(s) x 1 Schwarz iteration x 20 substeps of the {args.n}x{args.n}x"
+                         f"{args.nz} NH FOM + r={args.rank} ROM (seeded stand-in operators), {secs:.1f} s CPU"}
 
     if rank == 0:
+        head_name = "f32x2" if head_prec == osam.F32X2_FORCE else "f64"
+        value = head["updates"] / (head["total_ms"] * 1e-3)
+        variants = {}
+        for name, res in results.items():
+            variants[name] = {"value": res["updates"] / (res["total_ms"] * 1e-3),
+                              "ms_per_step": res["total_ms"] / args.steps,
+                              "value_graph": res["graph_value"], "ms_per_step_graph": res["graph_ms_per_step"],
+                              "e2e": res["e2e"]["value"] if res["e2e"] else None, "tuning": res["tuning"],
+                              "roofline": roofline(res, name),
+                              "parity": "1e-9 relative L2 vs the FP64 oracle (tests/test_gpu_parity.py)"}
+        clk = head["clk"] or {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head_name == "f64" else "f32x2",
+                "data": "synthetic",
                 "config": {"workload": (f"fom_fom {args.n}x{args.n}x{args.nz} x2 Neo-Hookean FOMs" if args.fom_only else
                                         f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} Neo-Hookean FOM + "
                                         f"r={args.rank} quadratic OpInf ROM (fitted on {args.snapshots} snapshots)"),
                            "dt": 1e-6, "substeps_per_step": 20, "tol_rel": 1e-12, "max_iters": 64,
                            "fom_elements": spec.subdomains[0].n_elements, "parallelism": "replicas",
                            "l2": "flushed between steps (256 MiB write)",
-                           "mean_iterations": float(np.mean(iters)), "max_iterations": int(max(iters))},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": prof["kernel_launches"] if world == 1 else None,
-                "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
+                           "mean_iterations": float(np.mean(head["iters"])), "max_iterations": int(max(head["iters"])),
+                           "timing": "host-driven Schwarz iterations with CUDA events around every force launch; "
+                                     "variants[*].value_graph times the graph-captured step"},
+                "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
+                "gpu_launches": head["prof"]["kernel_launches"] if world == 1 else None,
+                "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+                "variants": variants}
         print(json.dumps(line), flush=True)
-    prob.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

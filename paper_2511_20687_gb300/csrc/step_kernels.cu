@@ -172,112 +172,6 @@ __device__ __forceinline__ void stress_nh(const f2 H[3][3], f2 kap2, f2 mu, f2 m
 }
 }  // namespace dfk
 
-template <int MAT>
-__global__ void __launch_bounds__(256) k_force_df_b(const FomB g, const int* __restrict__ active) {
-    using df::f2;
-    const int2 b = g.eblk[blockIdx.x];
-    if (active && !active[b.x]) return;
-    const InstFom I = g.inst[b.x];
-    const int e = b.y + threadIdx.x;
-    if (e >= I.ne) return;
-    const int i = e % I.nx;
-    const int t = e / I.nx;
-    const int j = t % I.ny;
-    const int k = t / I.ny;
-    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
-    const int n0 = i + sy * j + sz * k;
-    int node[8];
-#pragma unroll
-    for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
-    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
-    f2 m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = df::from_double(0.5 * kappa * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::from_double(mu * I.w8 / 3.0);
-    } else {
-        m1 = df::from_double(lam * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::make(0.f, 0.f);
-    }
-    const f2 invh = df::from_double(I.invh);
-    f2 Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
-    const float2* ub = g.u2 + I.node_off;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        f2 U[8];
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            const float2 v = ub[(long long)c * g.NN + node[c8]];
-            U[c8] = df::make(v.x, v.y);
-        }
-        f2 Dx[2][2], Dy[2][2], Dz[2][2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                Dx[p][q] = df::mul(df::sub(U[1 + 2 * p + 4 * q], U[2 * p + 4 * q]), invh);
-                Dy[p][q] = df::mul(df::sub(U[p + 2 + 4 * q], U[p + 4 * q]), invh);
-                Dz[p][q] = df::mul(df::sub(U[p + 2 * q + 4], U[p + 2 * q]), invh);
-            }
-        dfk::lerp2(Dx, Gx[c]);
-        dfk::lerp2(Dy, Gy[c]);
-        dfk::lerp2(Dz, Gz[c]);
-    }
-    f2 Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                f2 Hm[3][3], P[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Hm[c][0] = Gx[c][q][r];
-                    Hm[c][1] = Gy[c][p][r];
-                    Hm[c][2] = Gz[c][p][q];
-                }
-                if (MAT == OSAM_NEO_HOOKEAN) dfk::stress_nh(Hm, m1, m2, m3, P);
-                else dfk::stress_le(Hm, m1, m2, P);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Sx[c][q][r] = (p == 0) ? P[c][0] : df::add(Sx[c][q][r], P[c][0]);
-                    Sy[c][p][r] = (q == 0) ? P[c][1] : df::add(Sy[c][p][r], P[c][1]);
-                    Sz[c][p][q] = (r == 0) ? P[c][2] : df::add(Sz[c][p][q], P[c][2]);
-                }
-            }
-    float2* fe = static_cast<float2*>(g.fe) + I.elem_off;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        f2 F[8], Tm[2][2];
-        dfk::lerp2T(Sx[c], Tm);
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[1 + 2 * ay + 4 * az] = Tm[ay][az];
-                F[2 * ay + 4 * az] = df::neg(Tm[ay][az]);
-            }
-        dfk::lerp2T(Sy[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[ax + 2 + 4 * az] = df::add(F[ax + 2 + 4 * az], Tm[ax][az]);
-                F[ax + 4 * az] = df::sub(F[ax + 4 * az], Tm[ax][az]);
-            }
-        dfk::lerp2T(Sz[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) {
-                F[ax + 2 * ay + 4] = df::add(F[ax + 2 * ay + 4], Tm[ax][ay]);
-                F[ax + 2 * ay] = df::sub(F[ax + 2 * ay], Tm[ax][ay]);
-            }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = make_float2(F[c8].h, F[c8].l);
-    }
-}
-
 // Phased double-float force: (A) edge differences and interpolation to the Gauss points, unrolled,
 // the 36 gradient entries parked in shared memory; (B) a rolled loop over the 8 Gauss points with one
 // copy of the constitutive code, accumulating the Gauss-point sums of the transposed interpolation in
