@@ -19,7 +19,13 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, MAXITER, EINVAL, ENONFINITE, EDONOR, ENOMEM = 0, 1, -1, -3, -4, -7
+OK, MAXITER, EINVAL, ECFL, ENONFINITE, EDONOR, ENOMEM = 0, 1, -1, -2, -3, -4, -7
+
+
+class OracleError(ValueError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg}: {code}")
+        self.code = code
 LE, NH = 0, 1
 
 _d = C.POINTER(C.c_double)
@@ -55,6 +61,9 @@ def lib():
             L.orc_force_vjp.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _d, C.c_int, _d, _d, _d, _d, _d,
                                         _d, _d]
             L.orc_donor.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _d, _d, _i, _d]
+            L.orc_stable_dt.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _d, C.c_double, C.c_double, _d, _d,
+                                        C.c_double]
+            L.orc_stable_dt.restype = C.c_double
             L.orc_problem_new.argtypes = [C.c_double, C.c_int, C.c_double, C.c_double, C.c_int]
             L.orc_problem_new.restype = C.c_void_p
             L.orc_problem_free.argtypes = [C.c_void_p]
@@ -142,6 +151,13 @@ def lumped_mass(dims, h, origin, rho):
     return m
 
 
+def stable_dt(dims, h, origin, lam, mu, rho, lam_e=None, mu_e=None):
+    """Largest stable explicit time step by the element eigenvalue bound (0: material not positive definite)."""
+    nx, ny, nz = dims
+    le, me = _f64(lam_e), _f64(mu_e)
+    return lib().orc_stable_dt(nx, ny, nz, h, _p(_f64(origin)), lam, mu, _p(le), _p(me), rho)
+
+
 def force_vjp(dims, h, origin, material, lam_e, mu_e, u, ybar):
     nx, ny, nz = dims
     u, ybar = _f64(u).reshape(-1), _f64(ybar).reshape(-1)
@@ -226,7 +242,7 @@ class Problem:
                 rc = L.orc_add_rom(self.h, nx, ny, nz, sd.h, _p(org), _p(dm), r, rs, arrs[0].shape[0],
                                    arrs[1].shape[0], *[_p(a) for a in arrs], _p(u0), _p(v0))
             if rc < 0:
-                raise ValueError(f"oracle add subdomain {i}: {rc}")
+                raise OracleError(rc, f"oracle add subdomain {i}")
         for cp in spec.couplings:
             m = np.ascontiguousarray(cp.nodes, np.uint8)
             self._keep.append(m)
@@ -234,7 +250,7 @@ class Problem:
                 raise ValueError("oracle couple")
         rc = L.orc_init(self.h)
         if rc != OK:
-            raise ValueError(f"oracle init failed: {rc}")
+            raise OracleError(rc, "oracle init failed")
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -246,7 +262,7 @@ class Problem:
         cn, cd = np.zeros(1), np.zeros(1)
         rc = lib().orc_step(self.h, _p(it), _p(cn), _p(cd))
         if rc < 0:
-            raise FloatingPointError(f"oracle step failed: {rc}")
+            raise OracleError(rc, "oracle step failed")
         return {"status": rc, "iterations": int(it[0]), "cnum": float(cn[0]), "cden": float(cd[0])}
 
     def state(self, i):

@@ -36,7 +36,7 @@
 #define ORC_MAX_SUB 8
 #define ORC_MAX_CPL 16
 
-enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_EINVAL = -1, ORC_ENONFINITE = -3, ORC_EDONOR = -4, ORC_ENOMEM = -7 };
+enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_EINVAL = -1, ORC_ECFL = -2, ORC_ENONFINITE = -3, ORC_EDONOR = -4, ORC_ENOMEM = -7 };
 enum { ORC_LE = 0, ORC_NH = 1 };
 enum { ORC_FOM = 0, ORC_ROM = 1 };
 
@@ -323,6 +323,117 @@ static void lumped_mass(const omesh* m, double rho, double* mass) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* stability limit of the explicit scheme                                                      */
+/* ------------------------------------------------------------------------------------------ */
+/* Central differences (Newmark beta = 0, gamma = 1/2) are stable for omega_max dt <= 2, where
+ * omega_max^2 is the largest eigenvalue of M^-1 K, K the stiffness at the reference configuration
+ * (linear elastic with (lambda, mu); the Neo-Hookean law of Appendix A linearises to the same).  With
+ * a lumped mass, omega_max^2 never exceeds the largest eigenvalue of any element's own M_e^-1 K_e
+ * (the element eigenvalue inequality of Irons and Treharne), so the oracle takes that bound: it forms
+ * K_e column by column from the linear elastic force of unit nodal displacements, M_e = rho V_e / 8
+ * per node, and finds the largest eigenvalue by the cyclic Jacobi method. */
+static void element_stiffness(const double X[8][3], double lam, double mu, double K[24][24]) {
+    for (int col = 0; col < 24; ++col) {
+        double U[8][3] = {{0}};
+        U[col / 3][col % 3] = 1.0;
+        double f[24] = {0};
+        for (int g = 0; g < 8; ++g) {
+            double dNdX[8][3], H[3][3], P[3][3];
+            double detJ = physical_gradients(X, g, dNdX);
+            grad_at(U, dNdX, H);
+            stress_le(H, lam, mu, P);
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) {
+                    double t = 0.0;
+                    for (int j = 0; j < 3; ++j) t += P[i][j] * dNdX[a][j];
+                    f[3 * a + i] += detJ * t;
+                }
+        }
+        for (int row = 0; row < 24; ++row) K[row][col] = f[row];
+    }
+}
+
+/* largest eigenvalue of a symmetric n x n matrix (row-major, overwritten) by cyclic Jacobi rotations */
+static double jacobi_max_eig(double* A, int n) {
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += A[i * n + i] * A[i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+        }
+        if (off <= 1e-30 * diag) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) { /* columns p, q */
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) { /* rows p, q */
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    double m = A[0];
+    for (int i = 1; i < n; ++i) m = fmax(m, A[i * n + i]);
+    return m;
+}
+
+/* max over elements of the largest eigenvalue of M_e^-1 K_e.  The eigenproblem is solved again only
+ * when an element's material differs from the previous element's or its volume differs by more than
+ * rounding (1e-12 relative): on a box of equal cubes the element matrices differ only in the last bits
+ * of their node coordinates. */
+static double max_element_omega2(const omesh* m, double lam, double mu, const double* lam_e, const double* mu_e,
+                                 double rho) {
+    double best = 0.0, last_l = NAN, last_m = NAN, last_v = NAN, last_w = 0.0;
+    for (int e = 0; e < m->ne; ++e) {
+        int nodes[8];
+        double X[8][3], dNdX[8][3], V = 0.0;
+        elem_nodes(m, e, nodes);
+        for (int a = 0; a < 8; ++a) node_X(m, nodes[a], X[a]);
+        for (int g = 0; g < 8; ++g) V += physical_gradients(X, g, dNdX);
+        double le = lam_e ? lam_e[e] : lam, me = mu_e ? mu_e[e] : mu;
+        double w;
+        if (le == last_l && me == last_m && fabs(V - last_v) <= 1e-12 * fabs(last_v)) {
+            w = last_w;
+        } else {
+            double K[24][24], A[24 * 24];
+            element_stiffness(X, le, me, K);
+            for (int i = 0; i < 24; ++i)
+                for (int j = 0; j < 24; ++j) A[i * 24 + j] = 0.5 * (K[i][j] + K[j][i]) * 8.0 / (rho * V);
+            w = jacobi_max_eig(A, 24);
+            last_l = le; last_m = me; last_v = V; last_w = w;
+        }
+        if (!(w == w)) return w; /* NaN propagates */
+        best = fmax(best, w);
+    }
+    return best;
+}
+
+/* largest stable explicit time step 2 / omega_max by the element bound; 0 for a material whose
+ * reference stiffness is not positive definite on the deformation modes (mu <= 0 or 3 lambda + 2 mu <= 0) */
+double orc_stable_dt(int nx, int ny, int nz, double h, const double* org, double lam, double mu,
+                     const double* lam_e, const double* mu_e, double rho) {
+    omesh m;
+    mesh_set(&m, nx, ny, nz, h, org);
+    for (int e = 0; e < m.ne; ++e) {
+        double le = lam_e ? lam_e[e] : lam, me = mu_e ? mu_e[e] : mu;
+        if (!(me > 0.0) || !(3.0 * le + 2.0 * me > 0.0)) return 0.0;
+    }
+    if (!(rho > 0.0)) return 0.0;
+    double w = max_element_omega2(&m, lam, mu, lam_e, mu_e, rho);
+    if (!(w > 0.0)) return 0.0;
+    return 2.0 / sqrt(w);
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* exported element-level entry points (used by the pin tests)                                 */
 /* ------------------------------------------------------------------------------------------ */
 int orc_internal_force(int nx, int ny, int nz, double h, const double* org, int model, double lam, double mu,
@@ -476,30 +587,40 @@ static int locate_in_element(const omesh* m, int e, const double x[3], double xi
     return 1;
 }
 
-/* donor = lowest-index element containing x; weights = N_b(xi).  Elements whose node bounding box
- * (widened by the containment tolerance) misses x are skipped before the Newton inversion. */
-static int find_donor(const omesh* m, const double x[3], int nodes[8], double w[8]) {
-    for (int e = 0; e < m->ne; ++e) {
-        double xi[3], N[8], dN[8][3], lo[3], hi[3], X[3];
-        int en[8], inside = 1;
-        elem_nodes(m, e, en);
-        for (int i = 0; i < 3; ++i) { lo[i] = 1e300; hi[i] = -1e300; }
-        for (int a = 0; a < 8; ++a) {
-            node_X(m, en[a], X);
-            for (int i = 0; i < 3; ++i) { lo[i] = fmin(lo[i], X[i]); hi[i] = fmax(hi[i], X[i]); }
-        }
-        for (int i = 0; i < 3; ++i) {
-            double tol = 1e-6 * (hi[i] - lo[i]);
-            if (x[i] < lo[i] - tol || x[i] > hi[i] + tol) inside = 0;
-        }
-        if (!inside) continue;
-        if (locate_in_element(m, e, x, xi)) {
-            elem_nodes(m, e, nodes);
-            shape(xi, N, dN);
-            for (int b = 0; b < 8; ++b) w[b] = N[b];
-            return 1;
-        }
+/* per-axis index range of the elements whose extent [org + i h, org + (i+1) h], widened by the
+ * containment tolerance, holds coordinate xc; returns 0 if there is none */
+static int axis_range(double xc, double org, double h, int n, int* first, int* last) {
+    *first = -1; *last = -2;
+    for (int i = 0; i < n; ++i) {
+        double lo = org + i * h, hi = org + (i + 1) * h, tol = 1e-6 * (hi - lo);
+        if (xc < lo - tol || xc > hi + tol) continue;
+        if (*first < 0) *first = i;
+        *last = i;
     }
+    return *first >= 0;
+}
+
+/* donor = lowest-index element containing x; weights = N_b(xi).  The mesh is an axis-aligned box of
+ * cubes, so an element's node bounding box is the product of its per-axis extents and the elements
+ * whose (widened) box holds x are the product of the per-axis index ranges; they are visited in
+ * increasing element index (k outer, then j, then i) and each is tested by the Newton inversion. */
+static int find_donor(const omesh* m, const double x[3], int nodes[8], double w[8]) {
+    int i0, i1, j0, j1, k0, k1;
+    if (!axis_range(x[0], m->org[0], m->h, m->nx, &i0, &i1) || !axis_range(x[1], m->org[1], m->h, m->ny, &j0, &j1) ||
+        !axis_range(x[2], m->org[2], m->h, m->nz, &k0, &k1))
+        return 0;
+    for (int k = k0; k <= k1; ++k)
+        for (int j = j0; j <= j1; ++j)
+            for (int i = i0; i <= i1; ++i) {
+                int e = i + m->nx * (j + m->ny * k);
+                double xi[3], N[8], dN[8][3];
+                if (locate_in_element(m, e, x, xi)) {
+                    elem_nodes(m, e, nodes);
+                    shape(xi, N, dN);
+                    for (int bb = 0; bb < 8; ++bb) w[bb] = N[bb];
+                    return 1;
+                }
+            }
     return 0;
 }
 
@@ -747,6 +868,16 @@ static void rom_ghat(const osub* s, int slot) {
 
 int orc_init(void* vp) {
     oprob* p = (oprob*)vp;
+    /* explicit stability: every FOM subdomain's time step within its element bound (a relative
+     * allowance of 1e-9 keeps a step exactly at the limit, such as the 1D bar at Courant number 1) */
+    for (int i = 0; i < p->nsd; ++i) {
+        osub* s = &p->sd[i];
+        if (s->kind != ORC_FOM) continue;
+        double lim = orc_stable_dt(s->m.nx, s->m.ny, s->m.nz, s->m.h, s->m.org, s->lam, s->mu, s->lam_e, s->mu_e,
+                                   s->rho);
+        if (!(lim > 0.0)) return ORC_EINVAL;
+        if (p->dt > lim * (1.0 + 1e-9)) return ORC_ECFL;
+    }
     /* Schwarz rows: union of the coupling masks, increasing node order */
     for (int i = 0; i < p->nsd; ++i) {
         osub* s = &p->sd[i];

@@ -334,3 +334,99 @@ def test_full_basis_rom_reproduces_fom_fom(oracle):
     assert np.abs(q - u1.reshape(-1)[free]).max() < 1e-12 * np.abs(u1).max()
     uB, _, _ = B.state(1)
     assert np.abs(uB - u1).max() < 1e-12 * np.abs(u1).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# stability limit of the explicit scheme (set-up check)
+# ---------------------------------------------------------------------------------------------
+def _assembled_stiffness(O, dims, h, lam, mu):
+    """K of the linear elastic mesh by columns of the force of unit displacements (dense, small meshes)."""
+    nx, ny, nz = dims
+    ndof = 3 * (nx + 1) * (ny + 1) * (nz + 1)
+    K = np.zeros((ndof, ndof))
+    for j in range(ndof):
+        u = np.zeros(ndof)
+        u[j] = 1.0
+        K[:, j] = O.internal_force(dims, h, (0.0, 0.0, 0.0), "le", lam, mu, u.reshape(-1, 3)).reshape(-1)
+    return 0.5 * (K + K.T)
+
+
+def _global_omega2(O, dims, h, lam, mu, rho):
+    K = _assembled_stiffness(O, dims, h, lam, mu)
+    m = np.repeat(O.lumped_mass(dims, h, (0.0, 0.0, 0.0), rho), 3)
+    s = 1.0 / np.sqrt(m)
+    return np.linalg.eigvalsh(s[:, None] * K * s[None, :])[-1]
+
+
+def test_stable_dt_of_one_element_is_its_dense_eigenvalue(oracle):
+    """For a single element the element bound is the exact limit 2 / sqrt(lambda_max(M^-1 K))."""
+    O = oracle
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        mu = float(rng.uniform(0.2, 3.0))
+        lam = float(rng.uniform(-0.6, 20.0)) * mu
+        h, rho = float(rng.uniform(0.5, 2.0)), float(rng.uniform(1.0, 10.0))
+        w2 = _global_omega2(O, (1, 1, 1), h, lam, mu, rho)
+        assert O.stable_dt((1, 1, 1), h, (0, 0, 0), lam, mu, rho) == pytest.approx(2.0 / np.sqrt(w2), rel=1e-12)
+
+
+def test_stable_dt_closed_form_for_cube_elements(oracle):
+    """The element eigenvalue of a cube with 2x2x2 Gauss points is h * max(3/2 lambda + mu, mu), so the
+    limit is h sqrt(rho / max(3 lambda + 2 mu, 2 mu)): the form the library evaluates per element."""
+    O = oracle
+    rng = np.random.default_rng(8)
+    for lam_over_mu in list(rng.uniform(-0.66, 200.0, 20)) + [0.0, -0.5, 1.0]:
+        mu, rho, h = 4e8, 1000.0, 0.01
+        lam = lam_over_mu * mu
+        ref = h * np.sqrt(rho / max(3 * lam + 2 * mu, 2 * mu))
+        assert O.stable_dt((2, 1, 1), h, (0, 0, 0), lam, mu, rho) == pytest.approx(ref, rel=1e-12)
+    # per-element materials: the limit is set by the stiffest element
+    lam_e = np.full(6, 4e8)
+    mu_e = np.full(6, 4e8)
+    lam_e[4] = 1.6e9
+    ref = 0.01 * np.sqrt(1000.0 / (3 * 1.6e9 + 2 * 4e8))
+    assert O.stable_dt((1, 2, 3), 0.01, (0, 0, 0), 4e8, 4e8, 1000.0, lam_e=lam_e, mu_e=mu_e) == pytest.approx(ref, rel=1e-12)
+    assert O.stable_dt((1, 1, 1), 0.01, (0, 0, 0), -3e8, 4e8, 1000.0) == 0.0  # 3 lambda + 2 mu < 0
+    assert O.stable_dt((1, 1, 1), 0.01, (0, 0, 0), 4e8, 0.0, 1000.0) == 0.0
+
+
+def test_element_bound_dominates_the_assembled_spectrum(oracle):
+    """Irons-Treharne: the assembled lumped-mass spectrum never exceeds the element bound, and on a
+    free 2x2x3 block the bound is within a factor 2 of it."""
+    O = oracle
+    dims, h, rho = (2, 2, 3), 0.01, 1000.0
+    w2 = _global_omega2(O, dims, h, LAM, MU, rho)
+    dt_elem = O.stable_dt(dims, h, (0, 0, 0), LAM, MU, rho)
+    dt_glob = 2.0 / np.sqrt(w2)
+    assert dt_elem <= dt_glob * (1 + 1e-12)
+    assert dt_elem > 0.5 * dt_glob
+
+
+def test_central_difference_blows_up_just_above_the_limit(oracle):
+    """The explicit integrator is stable just below omega_max dt = 2 and unstable just above it."""
+    O = oracle
+    dims, h, rho = (2, 2, 3), 0.01, 1000.0
+    dt_glob = 2.0 / np.sqrt(_global_omega2(O, dims, h, LAM, MU, rho))
+    ne = 12
+    le, me = np.full(ne, LAM), np.full(ne, MU)
+    u0 = _rand_disp(dims, 1e-6, 5)
+    dm = np.zeros(u0.shape[0], np.uint8)
+    below = O.rollout(dims, h, (0, 0, 0), "le", le, me, rho, dm, u0, None, 0.99 * dt_glob, 400)
+    above = O.rollout(dims, h, (0, 0, 0), "le", le, me, rho, dm, u0, None, 1.02 * dt_glob, 400)
+    assert np.abs(below).max() < 10 * np.abs(u0).max()
+    assert np.abs(above).max() > 1e6 * np.abs(u0).max()
+
+
+def test_problem_rejects_a_step_above_the_limit(oracle):
+    O = oracle
+    spec = W.fom_fom_plain()
+    lim = O.stable_dt(spec.subdomains[0].dims, spec.subdomains[0].h, spec.subdomains[0].origin,
+                      spec.subdomains[0].lam, spec.subdomains[0].mu, spec.subdomains[0].rho)
+    spec.dt = 1.01 * lim
+    with pytest.raises(O.OracleError) as ei:
+        O.Problem(spec)
+    assert ei.value.code == O.ECFL
+    spec.dt = 0.99 * lim
+    O.Problem(spec)
+    # the 1D bar at Courant number 1 sits exactly on the limit and is accepted
+    O.Problem(W.wave1d(n_elem=40))
