@@ -139,6 +139,30 @@ __global__ void k_zero_clamped(int nn, const uint8_t* clamp, double* u, double* 
     }
 }
 
+
+// Stiffest element modulus of each instance for the explicit stability check.  A cube element with
+// 2x2x2 Gauss points has the largest stiffness eigenvalue h max(3/2 lambda + mu, mu); with the lumped
+// element mass rho h^3 / 8 per node that bounds omega_max^2 by 8 max(3/2 lambda + mu, mu) / (rho h^2)
+// (the element eigenvalue inequality), so the stable step is h sqrt(rho / max(3 lambda + 2 mu, 2 mu)).
+// out[inst] receives the bits of the largest max(3 lambda_e + 2 mu_e, 2 mu_e) (non-negative doubles
+// order like their bit patterns); *bad is set for a material that is not positive definite.
+__global__ void k_cfl_modulus(const FomB g, unsigned long long* out, int* bad) {
+    const int2 b = g.eblk[blockIdx.x];
+    const InstFom I = g.inst[b.x];
+    const int e = b.y + (int)threadIdx.x;
+    double m = 0.0;
+    if ((int)threadIdx.x < g.eblock && e < I.ne) {
+        const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+        const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+        const double p = 3.0 * lam + 2.0 * mu;
+        if (!(mu > 0.0) || !(p > 0.0) || !isfinite(p)) *bad = 1;
+        else m = fmax(p, 2.0 * mu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out + b.x, (unsigned long long)__double_as_longlong(m));
+}
+
 }  // namespace
 
 int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
@@ -178,6 +202,13 @@ cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, long long 
 
 cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, long long stride, cudaStream_t s) {
     k_soa_to_aos<<<grid_for(3LL * nn, 256), 256, 0, s>>>(soa, aos, nn, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_modulus(const FomB& g, unsigned long long* out, int* bad, cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    const int threads = (g.eblock + 31) / 32 * 32;
+    k_cfl_modulus<<<g.n_eblk, threads, 0, s>>>(g, out, bad);
     return cudaGetLastError();
 }
 

@@ -440,6 +440,34 @@ int set_eblocks(osam_ctx* ctx, FomGroupH& G, int block) {
     return OSAM_OK;
 }
 
+// Explicit stability of every instance of FOM slot s: dt <= h sqrt(rho / max_e max(3 lambda_e + 2 mu_e,
+// 2 mu_e)) (element eigenvalue bound of the lumped-mass system at the reference configuration; the
+// Neo-Hookean law linearises to the same lambda, mu).  A relative allowance of 1e-9 keeps a step that
+// sits exactly on the limit.
+int check_stability(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_problem_desc* descs) {
+    unsigned long long* mod = ctx->alloc<unsigned long long>(n);
+    int* bad = ctx->alloc<int>(1);
+    CKA(mod); CKA(bad);
+    CK(cudaMemsetAsync(mod, 0, sizeof(unsigned long long) * n, ctx->stream));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+    CK(launch_cfl_modulus(G.d, mod, bad, ctx->stream));
+    std::vector<unsigned long long> mh;
+    std::vector<int> bh;
+    RET(to_host(ctx, mh, mod, n));
+    RET(to_host(ctx, bh, bad, 1));
+    if (bh[0]) return ctx->fail(OSAM_EINVAL, "subdomain %d: material not positive definite (mu > 0 and "
+                                             "3 lambda + 2 mu > 0 required)", s);
+    for (int i = 0; i < n; ++i) {
+        double m;
+        std::memcpy(&m, &mh[i], sizeof(double));
+        const double lim = G.grid[i].h * std::sqrt(descs[i].subdomains[s].rho / m);
+        if (ctx->dt > lim * (1.0 + 1e-9))
+            return ctx->fail(OSAM_ECFL, "instance %d subdomain %d: dt = %.6e above the explicit stability limit "
+                                        "%.6e", i, s, ctx->dt, lim);
+    }
+    return OSAM_OK;
+}
+
 int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_problem_desc* descs) {
     const bool fp32 = ctx->precision == OSAM_FP32_FORCE;
     long long NN = 0, NE = 0, H = 0;
@@ -528,6 +556,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     B.nblk_off = nbo;
     CKA(B.partial = ctx->alloc<double>(2LL * B.n_nblk));
     RET(set_eblocks(ctx, G, 128));
+    RET(check_stability(ctx, G, s, n, descs));
     if (B.df32) CK(launch_split_u2_b(B, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;

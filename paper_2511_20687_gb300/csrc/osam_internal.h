@@ -160,6 +160,7 @@ cudaError_t launch_donor(const Grid& src, const Grid& dst, const int* dst_nodes,
                          int* err, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, long long stride, cudaStream_t s);
 cudaError_t launch_soa_to_aos(const double* soa, double* aos, int nn, long long stride, cudaStream_t s);
+cudaError_t launch_cfl_modulus(const FomB& g, unsigned long long* out, int* bad, cudaStream_t s);
 cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double* v, long long stride, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------------

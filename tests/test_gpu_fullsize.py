@@ -1,0 +1,141 @@
+"""GPU parity at the full sizes of the paper-scale workloads.
+
+The oracle is too slow for these meshes over their whole horizons, so each comparison runs on a
+truncated horizon (a fixed number of substeps and Schwarz iterations, so that both sides take the
+same number of iterations) on the full mesh; what the oracle cannot reach in seconds is checked by
+properties that hold at any size (central differences of the GPU adjoint over the full horizon,
+agreement of the precision variants).
+
+  - FOM / OpInf hybrid, 40x40x80 Neo-Hookean FOM + r = 64 quadratic ROM (seeded stand-in operators of
+    the fitted model's sizes): 2 controller steps of 20 substeps, 2 Schwarz iterations each.
+  - adjoint bar, 20x20x40 Neo-Hookean, per-element Lame parameters: 200 steps against the oracle,
+    1000 steps against central differences.
+  - large chain, three 96x96x192 Neo-Hookean FOMs (1,769,472 elements each), dt = 5e-7: internal force
+    of the full mesh element by element, and one controller step of 2 substeps x 2 iterations.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2511_20687_gb300 import osam
+from paper_2511_20687_gb300 import workloads as W
+
+from .helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_20687_gb300 import build_lib
+    build_lib.build()
+    osam.load()
+    return torch
+
+
+def _compare(spec, rom_ops, n_ctrl, precisions, tols):
+    """Run the oracle once and every GPU precision mode on the same spec; relative L2 over the saved
+    controller steps of every FOM displacement and every ROM reduced state."""
+    ref = O.Problem(spec, rom_ops=rom_ops)
+    gpus = {p: osam.Problem(spec, rom_ops=rom_ops, precision=p) for p in precisions}
+    n_sd = len(spec.subdomains)
+    hist = {p: {i: [] for i in range(n_sd)} for p in precisions}
+    href = {i: [] for i in range(n_sd)}
+    for _ in range(n_ctrl):
+        rr = ref.step()
+        for p, g in gpus.items():
+            rg = g.step()
+            assert rg["iterations"] == rr["iterations"]
+            for i, sd in enumerate(spec.subdomains):
+                hist[p][i].append(g.state(i)[0].copy() if sd.kind == "fom" else g.reduced_state(i)[0].copy())
+        for i, sd in enumerate(spec.subdomains):
+            href[i].append(ref.state(i)[0].copy() if sd.kind == "fom" else ref.rom_state(i)[0].copy())
+    for p, g in gpus.items():
+        g.close()
+        for i in range(n_sd):
+            err = rel_l2(hist[p][i], href[i])
+            assert err < tols[p], (p, i, err)
+
+
+def test_hybrid_40x40x80_rom64_truncated_horizon(torch_cuda):
+    spec = W.fom_opinf_hybrid(40, 80, rom=True)
+    spec.max_iters = 2
+    sd = spec.subdomains[1]
+    n_sdof = 3 * (sd.dims[0] + 1) ** 2
+    ops = {1: W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, 64, 41, W.SEED_BASE + 12)}
+    _compare(spec, ops, 2, [osam.FP64, osam.F32X2_FORCE, osam.FP32_FORCE],
+             {osam.FP64: 1e-9, osam.F32X2_FORCE: 1e-9, osam.FP32_FORCE: 1e-5})
+
+
+def test_adjoint_20x20x40_against_oracle(torch_cuda):
+    p, w = W.adjoint_bar()
+    sd = p.subdomains[0]
+    n = 200
+    got = osam.adjoint(sd.dims, sd.h, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0, None, p.dt, n, w,
+                       checkpoint_every=50)
+    J, gu, gv, gl, gm = O.adjoint(sd.dims, sd.h, sd.origin, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0,
+                                  None, p.dt, n, w)
+    assert abs(got["J"] - J) < 1e-12 * abs(J)
+    for a, b in ((got["grad_u0"].reshape(-1), gu), (got["grad_v0"].reshape(-1), gv), (got["grad_lambda"], gl),
+                 (got["grad_mu"], gm)):
+        assert rel_l2([a], [b]) < 1e-9
+
+
+def test_adjoint_20x20x40_full_horizon_central_differences(torch_cuda):
+    """1000 steps with checkpoints every 50: the gradient's directional derivatives along random
+    directions of lambda_e, mu_e and u0 match central differences of the GPU's own J.  Steps of 1e-4
+    relative keep the truncation error (~1e-8) and the rounding noise of J (the adjoint's scatter uses
+    atomics; ~1e-15 relative per evaluation, ~1e-11 after the division) below the 1e-6 tolerance."""
+    p, w = W.adjoint_bar()
+    sd = p.subdomains[0]
+    n = p.info["n_steps"]
+    base = dict(dims=sd.dims, h=sd.h, material="nh", rho=sd.rho, dirichlet=sd.dirichlet, v0=None, dt=p.dt,
+                n_steps=n, w=w, checkpoint_every=p.info["checkpoint_every"])
+    got = osam.adjoint(lam_e=sd.lam_e, mu_e=sd.mu_e, u0=sd.u0, **base)
+    rng = np.random.default_rng(W.SEED_BASE + 13)
+    free = np.repeat(sd.dirichlet == 0, 3).reshape(-1, 3)
+
+    def J(le=sd.lam_e, me=sd.mu_e, u0=sd.u0):
+        return osam.adjoint(lam_e=le, mu_e=me, u0=u0, **base)["J"]
+
+    dl = rng.standard_normal(sd.n_elements)
+    hl = 1e-4 * sd.lam
+    fd = (J(le=sd.lam_e + hl * dl) - J(le=sd.lam_e - hl * dl)) / (2 * hl)
+    assert abs(fd - got["grad_lambda"] @ dl) < 1e-6 * abs(fd)
+    dm = rng.standard_normal(sd.n_elements)
+    hm = 1e-4 * sd.mu
+    fd = (J(me=sd.mu_e + hm * dm) - J(me=sd.mu_e - hm * dm)) / (2 * hm)
+    assert abs(fd - got["grad_mu"] @ dm) < 1e-6 * abs(fd)
+    du = rng.standard_normal(sd.u0.shape) * free
+    hu = 1e-4 * np.abs(sd.u0).max()
+    fd = (J(u0=sd.u0 + hu * du) - J(u0=sd.u0 - hu * du)) / (2 * hu)
+    assert abs(fd - np.sum(got["grad_u0"] * du)) < 1e-6 * abs(fd)
+
+
+def test_force_96x96x192_full_mesh(torch_cuda):
+    """Neo-Hookean internal force of a 96x96x192 mesh (1,769,472 elements) under a smooth large
+    deformation plus noise, element by element against the oracle."""
+    torch = torch_cuda
+    dims, h = (96, 96, 192), 0.01
+    sd = W.Subdomain(kind="fom", dims=dims, h=h, origin=(0.0, 0.0, 0.0))
+    X = sd.node_coords()
+    rng = np.random.default_rng(W.SEED_BASE + 14)
+    u = np.ascontiguousarray(0.02 * np.sin(3.0 * X[:, [1, 2, 0]]) + 1e-5 * rng.standard_normal(X.shape))
+    lam, mu = W.lame(1e9, 0.25)
+    ref = O.internal_force(dims, h, (0.0, 0.0, 0.0), "nh", lam, mu, u).reshape(-1, 3)
+    ut = torch.tensor(u, device="cuda")
+    ft = torch.zeros_like(ut)
+    osam.hex8_force(dims, h, "nh", lam, mu, ut, ft)
+    got = ft.cpu().numpy()
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_large_chain_96x96x192_one_truncated_step(torch_cuda):
+    spec = W.large_chain(rom_middle=False)
+    spec.n_substeps = 2
+    spec.max_iters = 2
+    _compare(spec, None, 1, [osam.FP64, osam.F32X2_FORCE, osam.FP32_FORCE],
+             {osam.FP64: 1e-9, osam.F32X2_FORCE: 1e-9, osam.FP32_FORCE: 1e-5})

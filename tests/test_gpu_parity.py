@@ -282,6 +282,70 @@ def test_invalid_description_is_rejected(torch_cuda):
     assert ei.value.code == osam.EINVAL
 
 
+@pytest.mark.parametrize("per_element", [False, True])
+def test_stability_check_agrees_with_oracle(torch_cuda, per_element):
+    """Both sides reject a time step 1% above the explicit stability limit (ECFL) and accept one 1%
+    below it; with per-element materials the stiffest element sets the limit."""
+    spec = W.fom_fom_plain()
+    sd = spec.subdomains[0]
+    le = me = None
+    if per_element:
+        rng = np.random.default_rng(12)
+        for k, s in enumerate(spec.subdomains):
+            s.lam_e = LAM * (1.0 + 0.5 * rng.uniform(-1, 1, s.n_elements))
+            s.mu_e = MU * (1.0 + 0.5 * rng.uniform(-1, 1, s.n_elements))
+        le, me = sd.lam_e, sd.mu_e
+    lim = min(O.stable_dt(s.dims, s.h, s.origin, s.lam, s.mu, s.rho, lam_e=s.lam_e, mu_e=s.mu_e)
+              for s in spec.subdomains)
+    assert lim > 0 and (le is None or lim < O.stable_dt(sd.dims, sd.h, sd.origin, LAM, MU, sd.rho))
+    spec.dt = 1.01 * lim
+    with pytest.raises(osam.OsamError) as ei:
+        osam.Problem(spec)
+    assert ei.value.code == osam.ECFL
+    with pytest.raises(O.OracleError) as eo:
+        O.Problem(spec)
+    assert eo.value.code == O.ECFL
+    spec.dt = 0.99 * lim
+    osam.Problem(spec).close()
+    O.Problem(spec)
+
+
+def test_stability_check_accepts_the_bar_at_courant_one(torch_cuda):
+    spec = W.wave1d(n_elem=40)
+    osam.Problem(spec).close()
+    O.Problem(spec)
+
+
+def test_non_positive_definite_material_is_rejected(torch_cuda):
+    spec = W.fom_fom_plain()
+    spec.subdomains[1].lam = -0.7 * spec.subdomains[1].mu  # 3 lambda + 2 mu < 0
+    with pytest.raises(osam.OsamError) as ei:
+        osam.Problem(spec)
+    assert ei.value.code == osam.EINVAL
+
+
+@pytest.mark.parametrize("rom", [False, True])
+def test_non_finite_state_is_reported(torch_cuda, rom):
+    """A NaN in the coupled state ends the controller step with ENONFINITE on both sides."""
+    if rom:
+        spec = W.bar_chain("nf", 3, [6, 6], ["fom", "rom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=6)
+        sd = spec.subdomains[1]
+        n_sdof = 3 * (sd.dims[0] + 1) ** 2
+        ops = {1: W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, 5, 4, 3)}
+    else:
+        spec, ops = W.fom_fom_plain(), None
+    spec.subdomains[0].u0 = spec.subdomains[0].u0.copy()
+    spec.subdomains[0].u0[spec.subdomains[0].n_nodes // 2, 2] = np.nan
+    gpu = osam.Problem(spec, rom_ops=ops)
+    with pytest.raises(osam.OsamError) as ei:
+        gpu.step()
+    assert ei.value.code == osam.ENONFINITE
+    with pytest.raises(O.OracleError) as eo:
+        O.Problem(spec, rom_ops=ops).step()
+    assert eo.value.code == O.ENONFINITE
+    gpu.close()
+
+
 # ---------------------------------------------------------------------------------------------
 # offline fit and adjoint
 # ---------------------------------------------------------------------------------------------
