@@ -14,6 +14,10 @@ e2e     = the same metric through the public API with host buffers: every step s
           states from pinned host memory, runs schwarz_step and reads the states back.
 roofline= the Neo-Hookean FP64 internal-force kernel (the dominant kernel): algorithmic FP64 flops of
           its launches in the timed steps / their CUDA-event time, against the FP64 peak.
+variants= both force precisions (native FP64; double-float on the FP32 pipes), each timed in the
+          host-driven loop and as the graph-captured step, with its own roofline.
+batched_vs_plain = 256 FOM / OpInf(r=32) samples advanced by one batched context vs one context per
+          sample (ROMs fitted per sample from batched training runs, untimed).
 --impl reference times the CPU oracle on a bounded sample of the same workload.
 Multi-GPU: replicas only (the coupled step does not shard); each rank runs the workload on its GPU.
 """
@@ -66,6 +70,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"],
                     help="f64: native FP64 force; f32x2: double-float force on the FP32 pipes (FP64 state)")
+    ap.add_argument("--batched-samples", type=int, default=256)
+    ap.add_argument("--batched-snapshots", type=int, default=100)
+    ap.add_argument("--batched-steps", type=int, default=5)
+    ap.add_argument("--batched-plain-steps", type=int, default=1)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain parameter sweep")
     ap.add_argument("--fom-only", action="store_true",
                     help="FOM-FOM coupling of the same geometry (no ROM, no training): profiling runs")
     return ap.parse_args()
@@ -142,21 +151,22 @@ def source_sha():
 # ---------------------------------------------------------------------------------------------
 # workload construction
 # ---------------------------------------------------------------------------------------------
+def rom_dof_masks(sd):
+    """Free and Schwarz dof masks of the top subdomain of a two-subdomain bar (Schwarz face z = 0)."""
+    _, _, kk = sd.node_grid()
+    schwarz = kk == 0
+    clamped = np.repeat(sd.dirichlet, 3).reshape(-1, 3) > 0
+    free = (~clamped & ~schwarz[:, None]).reshape(-1)
+    return free, np.repeat(schwarz, 3)
+
+
 def train_rom(W, osam, args, device, log):
     """Seeded FOM-FOM training run (snapshot every 4th step) and GPU OpInf fit of subdomain B."""
     rng = np.random.default_rng(W.SEED_BASE + 1)
     amp = float(rng.uniform(0.5e-3, 1.0e-3))
     spec = W.bar_chain("train", args.n, [args.nz, args.nz], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, amp, 1e-6, 4)
     prob = osam.Problem(spec, device=device)
-    sz = prob.sizes(1)
-    nn = sz["n_nodes"]
-    sd = spec.subdomains[1]
-    _, _, kk = sd.node_grid()
-    schwarz = np.zeros(nn, bool)
-    schwarz[kk == 0] = True
-    clamped = np.repeat(sd.dirichlet, 3).reshape(-1, 3) > 0
-    free = (~clamped & ~schwarz[:, None]).reshape(-1)
-    sdof = np.repeat(schwarz, 3)
+    free, sdof = rom_dof_masks(spec.subdomains[1])
     U = np.empty((args.snapshots, int(free.sum())))
     A = np.empty_like(U)
     S = np.empty((args.snapshots, int(sdof.sum())))
@@ -173,6 +183,96 @@ def train_rom(W, osam, args, device, log):
     ops = osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device)
     log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {time.time() - t0:.1f}s")
     return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}
+
+
+def train_batched_roms(W, osam, specs_ff, snapshots, r, device, log, chunk=32):
+    """Per-sample OpInf ROMs of subdomain B: FOM-FOM training runs of the samples advanced together
+    as batches (controller steps of 4 substeps, one snapshot per step, double-float force), then one
+    GPU opinf_fit per sample."""
+    ops, ranks = [], []
+    t0 = time.time()
+    for c0 in range(0, len(specs_ff), chunk):
+        group = specs_ff[c0:c0 + chunk]
+        for sp in group:
+            sp.n_substeps = 4
+        batch = osam.Batch(group, precision=osam.F32X2_FORCE, device=device)
+        masks = [rom_dof_masks(sp.subdomains[1]) for sp in group]
+        U = [np.empty((snapshots, int(f.sum()))) for f, _ in masks]
+        A = [np.empty_like(x) for x in U]
+        S = [np.empty((snapshots, int(sd.sum()))) for _, sd in masks]
+        for k in range(snapshots):
+            batch.step()
+            for i, (f, sd) in enumerate(masks):
+                u, _, a = batch.state(1, fields=(0, 2), inst=i)
+                U[i][k] = u.reshape(-1)[f]
+                A[i][k] = a.reshape(-1)[f]
+                S[i][k] = u.reshape(-1)[sd]
+        batch.close()
+        for i in range(len(group)):
+            # a short training run can have a numerical rank below r: take the largest of r, 3r/4, r/2, ...
+            for rr in (r, 3 * r // 4, r // 2, r // 4):
+                try:
+                    o = osam.opinf_fit(U[i], A[i], S[i], r=rr, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64,
+                                       device=device)
+                    break
+                except osam.OsamError:
+                    if rr == r // 4:
+                        raise
+            ranks.append(rr)
+            ops.append({1: {k: o[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}})
+    log(f"batched training: {len(specs_ff)} samples x {snapshots} snapshots, r={r} ({sum(x == r for x in ranks)} "
+        f"samples at full rank), in {time.time() - t0:.1f}s")
+    return ops, ranks
+
+
+def measure_batched(W, osam, torch, flush, args, device, log):
+    """Batched vs plain on the parameter-sweep workload: the same samples (FOM / OpInf pairs) advanced
+    by one batched context (graph-captured step) and by one context per sample, run one after another."""
+    specs = W.batched_samples(n_samples=args.batched_samples, rom=True)
+    ops, ranks = train_batched_roms(W, osam, W.batched_samples(n_samples=args.batched_samples, rom=False),
+                                    args.batched_snapshots, 32, device, log)
+    batch = osam.Batch(specs, rom_ops=ops, device=device)
+    for _ in range(3):
+        batch.step()
+    torch.cuda.synchronize()
+    dev_ms, upd, wall, its = 0.0, 0, 0.0, []
+    for _ in range(args.batched_steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        per, tot = batch.step()
+        wall += time.perf_counter() - t0
+        dev_ms += tot["elapsed_ms"]
+        upd += tot["element_updates"]
+        its += [p["iterations"] for p in per]
+    tuning = batch.tuning()
+    batch.close()
+    singles = [osam.Problem(sp, rom_ops=o, device=device) for sp, o in zip(specs, ops)]
+    for p in singles:
+        p.step()
+    torch.cuda.synchronize()
+    p_ms, p_upd, p_wall = 0.0, 0, 0.0
+    for _ in range(args.batched_plain_steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in singles:
+            r = p.step()
+            p_ms += r["elapsed_ms"]
+            p_upd += r["element_updates"]
+        p_wall += time.perf_counter() - t0
+    for p in singles:
+        p.close()
+    n_el = sum(sp.subdomains[0].n_elements for sp in specs)
+    return {"workload": f"{len(specs)} FOM / OpInf(r=32) pairs, n x n x 2n Neo-Hookean FOM, n ~ U{{8..32}}, "
+                        f"{n_el} FOM elements in total, ROMs fitted on {args.batched_snapshots} snapshots each",
+            "rom_ranks": {"32": sum(x == 32 for x in ranks), "below_32": sum(x < 32 for x in ranks)},
+            "steps": args.batched_steps, "value": upd / wall, "value_device": upd / (dev_ms * 1e-3),
+            "plain_steps": args.batched_plain_steps, "plain_value": p_upd / p_wall,
+            "plain_value_device": p_upd / (p_ms * 1e-3), "speedup": (upd / wall) / (p_upd / p_wall),
+            "mean_iterations": float(np.mean(its)), "max_iterations": int(max(its)), "unit": UNIT,
+            "tuning": tuning, "timing": "host wall clock around each synchronous step call (value) and the "
+                                        "library's CUDA events (value_device); L2 flushed between steps"}
 
 
 def hybrid_spec(W, args):
@@ -372,6 +472,11 @@ def main():
                 FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12,
                 "force_ms_per_launch": per_launch, "force_time_share": prof["force_ms"] / res["total_ms"]}
 
+    batched = None
+    if world == 1 and not args.no_batched and not args.fom_only:
+        batched = measure_batched(W, osam, torch, flush, args, local, log)
+        log(f"batched: {batched['value']:.3e} vs plain {batched['plain_value']:.3e} ({batched['speedup']:.1f}x)")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
         rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
@@ -407,7 +512,7 @@ def main():
                 "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
                 "gpu_launches": head["prof"]["kernel_launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-                "variants": variants}
+                "variants": variants, "batched_vs_plain": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
