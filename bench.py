@@ -56,6 +56,18 @@ FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 FORCE_TRAFFIC = {"source_sha256": "6f239e5091b53d0b29937186ac773b4688378b31af430e1f19314a2a82e316a3", "bytes_per_launch": 3.366e6}
 
 
+STATE_BYTES_PER_NODE_UPDATE = 152
+
+
+def measured_hbm_gbs():
+    """(HBM copy bandwidth in GB/s, where it comes from): the measured figure, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,6 +508,19 @@ def main():
                               "roofline": roofline(res, name),
                               "parity": "1e-9 relative L2 vs the FP64 oracle (tests/test_gpu_parity.py)"}
         clk = head["clk"] or {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        # HBM: the explicit state the method must move per node update (u, v read + write, a read +
+        # write, lumped mass read: 96 + 48 + 8 B), times nodes per element of the FOM mesh
+        sd0 = spec.subdomains[0]
+        bytes_per_update = STATE_BYTES_PER_NODE_UPDATE * sd0.n_nodes / sd0.n_elements
+        hbm_peak, hbm_kind = measured_hbm_gbs()
+        hbm = {}
+        for name, v in variants.items():
+            gbs = v["value"] * bytes_per_update / 1e9
+            hbm[name] = {"achieved_gbs": gbs, "frac": gbs / hbm_peak if hbm_peak else None}
+        hbm = {"algorithmic_bytes_per_element_update": bytes_per_update, "peak_gbs": hbm_peak,
+               "peak_kind": hbm_kind, **hbm,
+               "note": "the path is bound by the FP64 (or FP32-issue) pipes, not by HBM"}
+        mean_it = float(np.mean(head["iters"]))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if head_name == "f64" else "f32x2",
@@ -512,7 +537,9 @@ def main():
                 "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
                 "gpu_launches": head["prof"]["kernel_launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-                "variants": variants, "batched_vs_plain": batched}
+                "variants": variants, "batched_vs_plain": batched, "hbm": hbm,
+                "effective_rate": value / mean_it,
+                "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
