@@ -353,6 +353,20 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
+def combine_ranks(pairs, device):
+    """Whole-job figures of replicas: for every (milliseconds, element-updates) pair, the maximum time
+    and the summed updates over all ranks (identity on a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [(float(ms), int(u)) for ms, u in pairs]
+    ms = torch.tensor([float(p[0]) for p in pairs], dtype=torch.float64, device=device)
+    up = torch.tensor([float(p[1]) for p in pairs], dtype=torch.float64, device=device)
+    dist.all_reduce(ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(up, op=dist.ReduceOp.SUM)
+    return [(float(a), int(b)) for a, b in zip(ms.tolist(), up.tolist())]
+
+
 def timed_pass(prob, torch, flush, steps, profile):
     """`steps` controller steps with CUDA-event timing per step (L2 flushed in between, outside the
     timing).  profile=True brackets every force launch with CUDA events (host-driven iterations)."""
@@ -397,7 +411,8 @@ def e2e_pass(prob, torch, steps, rank_r):
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     io_bytes = 3 * nA * 3 * 8 + 3 * rank_r * 8
-    return {"value": updates / secs, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes}
+    return {"value": updates / secs, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+            "seconds": secs, "updates": updates}
 
 
 def main():
@@ -451,13 +466,13 @@ def main():
             torch.distributed.barrier()
         clk = clocks.stop() if clocks else None
         g_ms, g_upd, _, _ = timed_pass(prob, torch, flush, args.steps, profile=False)
-        if world > 1:
-            t = torch.tensor([total_ms, float(updates), g_ms, float(g_upd)], dtype=torch.float64, device=f"cuda:{local}")
-            mx, sm = t.clone(), t.clone()
-            torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-            torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-            total_ms, updates, g_ms, g_upd = float(mx[0]), int(sm[1]), float(mx[2]), int(sm[3])
         e2e = e2e_pass(prob, torch, args.e2e_steps, args.rank) if (args.e2e_steps > 0 and rom_ops) else None
+        (total_ms, updates), (g_ms, g_upd), e2e_pair = combine_ranks(
+            [(total_ms, updates), (g_ms, g_upd), (e2e["seconds"] * 1e3, e2e["updates"]) if e2e else (1.0, 0)],
+            f"cuda:{local}")
+        if e2e:
+            e2e["value"] = e2e_pair[1] / (e2e_pair[0] * 1e-3)
+            del e2e["seconds"], e2e["updates"]
         results[name] = {"total_ms": total_ms, "updates": updates, "iters": iters, "prof": prof, "clk": clk,
                          "graph_value": g_upd / (g_ms * 1e-3), "graph_ms_per_step": g_ms / args.steps, "e2e": e2e,
                          "tuning": prob.tuning()}
