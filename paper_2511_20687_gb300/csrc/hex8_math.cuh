@@ -27,7 +27,19 @@ constexpr double kGd = 0.57735026918962576451;   // kG1 - kG0 = 1/sqrt(3)
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double rcbrtT(double x) { return rcbrt(x); }
+// x^(-1/3) for x > 0 in FP64: a single-precision seed refined by two steps of Newton's method on
+// f(y) = y^-3 - x, i.e. y <- y + y (1 - x y^3) / 3.  Each step roughly squares the relative error
+// (e -> 2 e^2), so the seed's ~1e-7 falls to ~1e-14 and then below the FP64 rounding.  Twelve FP64
+// operations; x <= 0, Inf or NaN propagate to a non-finite result (caught by the step's criterion).
+__device__ __forceinline__ double rcbrtT(double x) {
+    double y = (double)rcbrtf(__double2float_rn(x));
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double y3 = y * y * y;
+        y = fma(y * (1.0 / 3.0), fma(-x, y3, 1.0), y);
+    }
+    return y;
+}
 __device__ __forceinline__ float rcbrtT(float x) { return rcbrtf(x); }
 
 // nodal values D[b][e] on a unit square -> values at the 2x2 Gauss points out[q][r]
@@ -78,39 +90,41 @@ __device__ __forceinline__ void stress_le(const T H[3][3], T lam, T mu, T P[3][3
     P[1][2] = P[2][1] = mu * (H[1][2] + H[2][1]);
 }
 
-// Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8)
+// Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8):
+// P = alpha F + beta cof(F); returns F, cof(F), alpha, beta
+template <typename T>
+__device__ __forceinline__ void nh_factors(const T H[3][3], T kap2, T mu, T mu3, T F[3][3], T C[3][3], T& alpha,
+                                           T& beta) {
+    F[0][0] = T(1) + H[0][0]; F[1][1] = T(1) + H[1][1]; F[2][2] = T(1) + H[2][2];
+    F[0][1] = H[0][1]; F[0][2] = H[0][2]; F[1][0] = H[1][0]; F[1][2] = H[1][2]; F[2][0] = H[2][0]; F[2][1] = H[2][1];
+    C[0][0] = fmaT(F[1][1], F[2][2], -F[1][2] * F[2][1]);
+    C[0][1] = fmaT(F[1][2], F[2][0], -F[1][0] * F[2][2]);
+    C[0][2] = fmaT(F[1][0], F[2][1], -F[1][1] * F[2][0]);
+    C[1][0] = fmaT(F[0][2], F[2][1], -F[0][1] * F[2][2]);
+    C[1][1] = fmaT(F[0][0], F[2][2], -F[0][2] * F[2][0]);
+    C[1][2] = fmaT(F[0][1], F[2][0], -F[0][0] * F[2][1]);
+    C[2][0] = fmaT(F[0][1], F[1][2], -F[0][2] * F[1][1]);
+    C[2][1] = fmaT(F[0][2], F[1][0], -F[0][0] * F[1][2]);
+    C[2][2] = fmaT(F[0][0], F[1][1], -F[0][1] * F[1][0]);
+    const T J = fmaT(F[0][0], C[0][0], fmaT(F[0][1], C[0][1], F[0][2] * C[0][2]));
+    T trC = F[0][0] * F[0][0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) trC = fmaT(F[k / 3][k % 3], F[k / 3][k % 3], trC);
+    const T J2 = J * J;
+    const T r3 = rcbrtT(J2);                 // J^-2/3
+    const T invJ = J * (r3 * r3 * r3);       // J * J^-2 = 1/J
+    alpha = mu * r3;
+    beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
+}
+
 template <typename T>
 __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, T P[3][3]) {
-    const T F00 = T(1) + H[0][0], F11 = T(1) + H[1][1], F22 = T(1) + H[2][2];
-    const T F01 = H[0][1], F02 = H[0][2], F10 = H[1][0], F12 = H[1][2], F20 = H[2][0], F21 = H[2][1];
-    T c00 = fmaT(F11, F22, -F12 * F21);
-    T c01 = fmaT(F12, F20, -F10 * F22);
-    T c02 = fmaT(F10, F21, -F11 * F20);
-    T c10 = fmaT(F02, F21, -F01 * F22);
-    T c11 = fmaT(F00, F22, -F02 * F20);
-    T c12 = fmaT(F01, F20, -F00 * F21);
-    T c20 = fmaT(F01, F12, -F02 * F11);
-    T c21 = fmaT(F02, F10, -F00 * F12);
-    T c22 = fmaT(F00, F11, -F01 * F10);
-    T J = fmaT(F00, c00, fmaT(F01, c01, F02 * c02));
-    T trC = F00 * F00;
-    trC = fmaT(F01, F01, trC); trC = fmaT(F02, F02, trC);
-    trC = fmaT(F10, F10, trC); trC = fmaT(F11, F11, trC); trC = fmaT(F12, F12, trC);
-    trC = fmaT(F20, F20, trC); trC = fmaT(F21, F21, trC); trC = fmaT(F22, F22, trC);
-    T J2 = J * J;
-    T r3 = rcbrtT(J2);                 // J^-2/3
-    T invJ = J * (r3 * r3 * r3);       // J * J^-2 = 1/J
-    T alpha = mu * r3;
-    T beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
-    P[0][0] = fmaT(alpha, F00, beta * c00);
-    P[0][1] = fmaT(alpha, F01, beta * c01);
-    P[0][2] = fmaT(alpha, F02, beta * c02);
-    P[1][0] = fmaT(alpha, F10, beta * c10);
-    P[1][1] = fmaT(alpha, F11, beta * c11);
-    P[1][2] = fmaT(alpha, F12, beta * c12);
-    P[2][0] = fmaT(alpha, F20, beta * c20);
-    P[2][1] = fmaT(alpha, F21, beta * c21);
-    P[2][2] = fmaT(alpha, F22, beta * c22);
+    T F[3][3], C[3][3], alpha, beta;
+    nh_factors<T>(H, kap2, mu, mu3, F, C, alpha, beta);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[i][j] = fmaT(alpha, F[i][j], beta * C[i][j]);
 }
 
 // Element force from scaled edge differences.
@@ -140,13 +154,28 @@ __device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3]
                     Hm[c][1] = Gy[c][p][r];
                     Hm[c][2] = Gz[c][p][q];
                 }
-                if (MAT == OSAM_NEO_HOOKEAN) stress_nh<T>(Hm, m1, m2, m3, P);
-                else stress_le<T>(Hm, m1, m2, P);
+                if (MAT == OSAM_NEO_HOOKEAN) {
+                    // P = alpha F + beta cof(F), folded into the Gauss-point sums: the second Gauss
+                    // point of a pair adds with two fused multiply-adds instead of mul + fma + add
+                    T Fm[3][3], Cm[3][3], alpha, beta;
+                    nh_factors<T>(Hm, m1, m2, m3, Fm, Cm, alpha, beta);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (p == 0) Sx[c][q][r] = P[c][0]; else Sx[c][q][r] += P[c][0];
-                    if (q == 0) Sy[c][p][r] = P[c][1]; else Sy[c][p][r] += P[c][1];
-                    if (r == 0) Sz[c][p][q] = P[c][2]; else Sz[c][p][q] += P[c][2];
+                    for (int c = 0; c < 3; ++c) {
+                        Sx[c][q][r] = p == 0 ? fmaT(alpha, Fm[c][0], beta * Cm[c][0])
+                                             : fmaT(alpha, Fm[c][0], fmaT(beta, Cm[c][0], Sx[c][q][r]));
+                        Sy[c][p][r] = q == 0 ? fmaT(alpha, Fm[c][1], beta * Cm[c][1])
+                                             : fmaT(alpha, Fm[c][1], fmaT(beta, Cm[c][1], Sy[c][p][r]));
+                        Sz[c][p][q] = r == 0 ? fmaT(alpha, Fm[c][2], beta * Cm[c][2])
+                                             : fmaT(alpha, Fm[c][2], fmaT(beta, Cm[c][2], Sz[c][p][q]));
+                    }
+                } else {
+                    stress_le<T>(Hm, m1, m2, P);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (p == 0) Sx[c][q][r] = P[c][0]; else Sx[c][q][r] += P[c][0];
+                        if (q == 0) Sy[c][p][r] = P[c][1]; else Sy[c][p][r] += P[c][1];
+                        if (r == 0) Sz[c][p][q] = P[c][2]; else Sz[c][p][q] += P[c][2];
+                    }
                 }
             }
 #pragma unroll

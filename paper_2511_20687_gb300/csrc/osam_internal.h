@@ -23,7 +23,7 @@ namespace osam {
 enum Scatter { kAtomic = 1, kGather = 2 };
 
 constexpr int kMaxSlots = 8;    // subdomains per instance
-constexpr int kNodeBlock = 256; // nodes per block of the node kernels
+constexpr int kNodeBlock = 128; // nodes per block of the node kernels
 
 struct Grid {
     int nx = 0, ny = 0, nz = 0;

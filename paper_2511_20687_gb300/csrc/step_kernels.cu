@@ -327,6 +327,41 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_df_b(const FomB g, const in
     const double* h1 = slot1 >= 0 ? g.hist + I.hist_off + (long long)slot1 * 9 * I.ns : nullptr;
     const double* h2 = slot2 >= 0 ? g.hist + I.hist_off + (long long)slot2 * 9 * I.ns : nullptr;
     const float2* fe = static_cast<const float2*>(g.fe) + I.elem_off;
+    // loads first (state, then the element contributions of the three components, summed per
+    // component in double-float in the fixed corner order)
+    double uc[3], vc[3], ac[3];
+    f2 f[3] = {df::make(0.f, 0.f), df::make(0.f, 0.f), df::make(0.f, 0.f)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + gn;
+        uc[c] = ucur[d];
+        vc[c] = g.v[d];
+        ac[c] = g.a[d];
+    }
+    if (!predict_only && row < 0 && cm != 7) {
+#pragma unroll
+        for (int az = 0; az < 2; ++az) {
+            const int ke = k - az;
+            if (ke < 0 || ke >= I.nz) continue;
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) {
+                const int je = j - ay;
+                if (je < 0 || je >= I.ny) continue;
+#pragma unroll
+                for (int ax = 0; ax < 2; ++ax) {
+                    const int ie = i - ax;
+                    if (ie < 0 || ie >= I.nx) continue;
+                    const long long e = ie + (long long)I.nx * (je + I.ny * ke);
+                    const int corner = ax + 2 * ay + 4 * az;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 v = __ldg(fe + (long long)(corner * 3 + c) * g.NE + e);
+                        f[c] = df::add(f[c], df::make(v.x, v.y));
+                    }
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long d = (long long)c * g.NN + gn;
@@ -342,34 +377,15 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_df_b(const FomB g, const in
             }
             un = h2 ? h2[(long long)c * I.ns + row] : 0.0;
         } else {
-            double vn = g.v[d], an = g.a[d];
+            double vn = vc[c], an = ac[c];
             if (!predict_only) {
-                f2 s = df::make(0.f, 0.f);
-#pragma unroll
-                for (int az = 0; az < 2; ++az) {
-                    const int ke = k - az;
-                    if (ke < 0 || ke >= I.nz) continue;
-#pragma unroll
-                    for (int ay = 0; ay < 2; ++ay) {
-                        const int je = j - ay;
-                        if (je < 0 || je >= I.ny) continue;
-#pragma unroll
-                        for (int ax = 0; ax < 2; ++ax) {
-                            const int ie = i - ax;
-                            if (ie < 0 || ie >= I.nx) continue;
-                            const int e = ie + I.nx * (je + I.ny * ke);
-                            const float2 v = fe[(long long)((ax + 2 * ay + 4 * az) * 3 + c) * g.NE + e];
-                            s = df::add(s, df::make(v.x, v.y));
-                        }
-                    }
-                }
-                const double anew = -df::to_double(s) * minv;
+                const double anew = -df::to_double(f[c]) * minv;
                 vn = fma(hdt, an + anew, vn);
                 an = anew;
                 g.v[d] = vn;
                 g.a[d] = an;
             }
-            un = fma(hdt2, an, fma(dt, vn, ucur[d]));
+            un = fma(hdt2, an, fma(dt, vn, uc[c]));
         }
         if (h2) {
             unext[d] = un;
@@ -427,6 +443,42 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
     const double* h2 = slot2 >= 0 ? g.hist + I.hist_off + (long long)slot2 * 9 * I.ns : nullptr;
     const TF* fe = static_cast<const TF*>(g.fe) + I.elem_off;
     TF* fa = static_cast<TF*>(g.f);
+    // all loads of a free node first (state and the element contributions of the three components,
+    // summed per component in the fixed corner order), so that they are in flight together
+    double uc[3], vc[3], ac[3], f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + gn;
+        uc[c] = ucur[d];
+        vc[c] = g.v[d];
+        ac[c] = g.a[d];
+    }
+    if (!predict_only && row < 0 && cm != 7) {
+        if (MODE == kGather) {
+#pragma unroll
+            for (int az = 0; az < 2; ++az) {
+                const int ke = k - az;
+                if (ke < 0 || ke >= I.nz) continue;
+#pragma unroll
+                for (int ay = 0; ay < 2; ++ay) {
+                    const int je = j - ay;
+                    if (je < 0 || je >= I.ny) continue;
+#pragma unroll
+                    for (int ax = 0; ax < 2; ++ax) {
+                        const int ie = i - ax;
+                        if (ie < 0 || ie >= I.nx) continue;
+                        const long long e = ie + (long long)I.nx * (je + I.ny * ke);
+                        const int corner = ax + 2 * ay + 4 * az;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) f[c] += double(__ldg(fe + (long long)(corner * 3 + c) * g.NE + e));
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = double(fa[(long long)c * g.NN + gn]);
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long d = (long long)c * g.NN + gn;
@@ -444,22 +496,16 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
             }
             un = h2 ? h2[(long long)c * I.ns + row] : 0.0;
         } else {
-            double vn = g.v[d], an = g.a[d];
+            double vn = vc[c], an = ac[c];
             if (!predict_only) {
-                double f;
-                if (MODE == kGather) {
-                    f = gather_force<TF>(fe, I.nx, I.ny, I.nz, (int)g.NE, i, j, k, c);
-                } else {
-                    f = double(fa[d]);
-                    fa[d] = TF(0);
-                }
-                const double anew = -f * minv;
+                if (MODE == kAtomic) fa[d] = TF(0);
+                const double anew = -f[c] * minv;
                 vn = fma(hdt, an + anew, vn);
                 an = anew;
                 g.v[d] = vn;
                 g.a[d] = an;
             }
-            un = fma(hdt2, an, fma(dt, vn, ucur[d]));
+            un = fma(hdt2, an, fma(dt, vn, uc[c]));
         }
         if (h2) unext[d] = un;
     }
