@@ -89,12 +89,18 @@ struct osam_ctx {
     double* scratch = nullptr;            // device [3 * max nodes of any instance]
     int* err_d = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // side stream that advances a ROM subdomain one substep behind the FOM that feeds it, joined back
+    // with events (also inside the graph capture).  It has the lowest priority, so its small kernels
+    // take the SM slots the internal-force kernel leaves free in its last wave instead of delaying it.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     // CUDA graph of one controller step: begin nodes, then a while node over Schwarz iterations
     bool use_graph = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle cond{};
+    long long graph_begin_launches = 0, graph_body_launches = 0;  // kernels per graph part (counted at capture)
     // kernel-level timing of the internal-force launches (host-driven path) and a launch count
     bool prof = false;
     std::vector<cudaEvent_t> pev;
@@ -104,6 +110,7 @@ struct osam_ctx {
 
     ~osam_ctx() {
         if (stream) cudaStreamSynchronize(stream);
+        if (side) cudaStreamSynchronize(side);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (void* p : allocs) cudaFree(p);
@@ -115,6 +122,9 @@ struct osam_ctx {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -253,9 +263,60 @@ int advance_slot(osam_ctx* ctx, int s, const int* active) {
     return OSAM_OK;
 }
 
+// FOM slot s followed by ROM slot s + 1 whose only source among the slots before it is s: the ROM's
+// substep j needs only the FOM's trace of substep j, so it can run one substep behind the FOM.
+bool pipelined_pair(const osam_ctx* ctx, int s) {
+    if (s + 1 >= (int)ctx->slots.size()) return false;
+    if (ctx->slots[s].kind != OSAM_FOM || ctx->slots[s + 1].kind != OSAM_ROM) return false;
+    bool fed = false;
+    for (const CplH& c : ctx->cpls) {
+        if (c.dst != s + 1 || c.src > s) continue;
+        if (c.src != s) return false;
+        fed = true;
+    }
+    return fed;
+}
+
+// FOM slot s on the main stream and ROM slot s + 1 on the side stream, one substep behind: after the
+// FOM's trace of substep j the side stream publishes that slot of every coupling s -> s + 1, projects
+// it onto the ROM's boundary basis and takes the ROM's substep j.  The same kernels in the same
+// per-subdomain order as advance_slot(s), transfer(s -> s + 1), advance_slot(s + 1), so the results
+// are identical; only the two subdomains' work overlaps.
+int advance_pair(osam_ctx* ctx, int s, const int* active) {
+    FomB& g = ctx->slots[s].fom.d;
+    RomB& r = ctx->slots[s + 1].rom.d;
+    long long ne = 0;
+    for (const InstFom& I : ctx->slots[s].fom.inst) ne += I.ne;
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    LK(launch_rom_record0_b(r, active, ctx->side));
+    LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
+    for (int j = 0; j < ctx->nsub; ++j) {
+        double* X = g.u[(j + 1) & 1];
+        double* Y = g.u[j & 1];
+        const int pk = ctx->prof_begin();
+        LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream));
+        ctx->prof_end(pk, ne);
+        LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
+                         ctx->stream));
+        for (CplH& c : ctx->cpls)
+            if (c.src == s) LK(launch_trace_b(c.d, active, g, X, j + 1, ctx->stream));
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+        for (CplH& c : ctx->cpls)
+            if (c.src == s && c.dst == s + 1) LK(launch_publish_b(c.d, active, j + 1, 1, ctx->side));
+        LK(launch_rom_project_b(r, active, j + 1, j + 1, ctx->side));
+        LK(launch_rom_step_b(r, active, j + 1, ctx->dt, 0, ctx->side));
+    }
+    if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_join, ctx->side));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    return OSAM_OK;
+}
+
 int transfer_cpl(osam_ctx* ctx, CplH& c, const int* active) {
     Slot& src = ctx->slots[c.src];
-    if (src.kind == OSAM_FOM) LK(launch_publish_b(c.d, active, ctx->nsub, ctx->stream));
+    if (src.kind == OSAM_FOM) LK(launch_publish_b(c.d, active, 1, ctx->nsub, ctx->stream));
     else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 0, ctx->nsub, ctx->stream));
     return OSAM_OK;
 }
@@ -296,7 +357,14 @@ int enqueue_begin(osam_ctx* ctx) {
 int enqueue_iteration(osam_ctx* ctx, int use_cond) {
     const int* act = ctx->ctl.active;
     for (int s = 0; s < (int)ctx->slots.size(); ++s) {
-        RET(advance_slot(ctx, s, act));
+        if (pipelined_pair(ctx, s)) {
+            RET(advance_pair(ctx, s, act));
+            for (CplH& c : ctx->cpls)
+                if (c.src == s && c.dst != s + 1) RET(transfer_cpl(ctx, c, act));
+            ++s;
+        } else {
+            RET(advance_slot(ctx, s, act));
+        }
         for (CplH& c : ctx->cpls)
             if (c.src == s) RET(transfer_cpl(ctx, c, act));
     }
@@ -313,6 +381,7 @@ int build_graph(osam_ctx* ctx) {
     CK(cudaGraphConditionalHandleCreate(&ctx->cond, ctx->graph, 1, cudaGraphCondAssignDefault));
     CK(cudaStreamBeginCaptureToGraph(ctx->stream, ctx->graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_begin(ctx);
+    ctx->graph_begin_launches = ctx->launches - launches0;
     cudaGraph_t g = nullptr;
     cudaError_t ec = cudaStreamEndCapture(ctx->stream, &g);
     if (rc) return rc;
@@ -336,11 +405,13 @@ int build_graph(osam_ctx* ctx) {
     CK(cudaGraphAddNode(&wnode, ctx->graph, leaves.data(), nullptr, leaves.size(), &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long body0 = ctx->launches;
     rc = enqueue_iteration(ctx, 1);
+    ctx->graph_body_launches = ctx->launches - body0;
     ec = cudaStreamEndCapture(ctx->stream, &body);
     if (rc) return rc;
     CK(ec);
-    CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, 0));
+    CK(cudaGraphInstantiate(&ctx->exec, ctx->graph, cudaGraphInstantiateFlagUseNodePriority));
     ctx->launches = launches0;  // capture issued nothing
     return OSAM_OK;
 }
@@ -355,19 +426,6 @@ int read_ctl(osam_ctx* ctx) {
 }
 
 // kernels one Schwarz iteration launches (for the launch count of the graph path)
-long long launches_per_iteration(osam_ctx* ctx) {
-    long long n = 0;
-    for (int s = 0; s < (int)ctx->slots.size(); ++s) {
-        int traces = 0;
-        for (CplH& c : ctx->cpls) traces += c.src == s;
-        if (ctx->slots[s].kind == OSAM_FOM) n += 1 + (long long)ctx->nsub * (2 + traces) + (ctx->nsub & 1);
-        else n += 2 + ctx->nsub;
-        n += traces;  // transfers
-    }
-    n += (long long)ctx->slots.size() * 2 + 1;  // norms, restore, controller
-    return n;
-}
-
 // ------------------------------------------------------------------------------------------------
 // set-up
 // ------------------------------------------------------------------------------------------------
@@ -944,7 +1002,9 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     ctx->device = d0.device;
     if (d0.stream) ctx->stream = static_cast<cudaStream_t>(d0.stream);
     else {
-        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CK(cudaStreamCreateWithPriority(&ctx->stream, cudaStreamNonBlocking, prio_hi));
         ctx->own_stream = true;
     }
     ctx->n_inst = n;
@@ -957,6 +1017,13 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     ctx->scatter = (d0.scatter == OSAM_SCATTER_ATOMIC && d0.precision != OSAM_F32X2_FORCE) ? kAtomic : kGather;
     CK(cudaEventCreate(&ctx->ev0));
     CK(cudaEventCreate(&ctx->ev1));
+    {
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_lo));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
     CKA(ctx->err_d = ctx->alloc<int>(1));
     const int nsd = d0.n_subdomains, ncpl = d0.n_couplings;
     ctx->slots.resize(nsd);
@@ -1170,12 +1237,7 @@ int osam_batch_step(osam_ctx* ctx, osam_step_report* reps, osam_step_report* tot
             reps[i].elapsed_ms = ms;
         }
     }
-    if (graph) {
-        long long begin = 0;
-        for (Slot& S : ctx->slots) { (void)S; begin += 1; }
-        begin += (long long)ctx->cpls.size() + 1;
-        ctx->launches += begin + (long long)max_its * launches_per_iteration(ctx);
-    }
+    if (graph) ctx->launches += ctx->graph_begin_launches + (long long)max_its * ctx->graph_body_launches;
     if (total) {
         total->status = worst;
         total->iterations = max_its;

@@ -178,7 +178,7 @@ cudaError_t launch_copy_u10_b(const FomB& g, const int* active, cudaStream_t s);
 cudaError_t launch_split_u2_b(const FomB& g, cudaStream_t s);
 cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
                            cudaStream_t s);
-cudaError_t launch_publish_b(const CplB& c, const int* active, int nsub, cudaStream_t s);
+cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, cudaStream_t s);  // slots [slot0, slot0 + nslots)
 cudaError_t launch_zoh_fom_b(const CplB& c, const int* active, const FomB& src, int nsub, cudaStream_t s);
 cudaError_t launch_rom_record0_b(const RomB& r, const int* active, cudaStream_t s);
 cudaError_t launch_rom_project_b(const RomB& r, const int* active, int slot0, int slot1, cudaStream_t s);

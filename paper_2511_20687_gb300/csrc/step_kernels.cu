@@ -640,14 +640,14 @@ __global__ void k_trace_b(const CplB c, const int* __restrict__ active, const Fo
 }
 
 // publish a FOM source's recorded slots 1..nsub into the destination history
-__global__ void k_publish_b(const CplB c, const int* __restrict__ active, int nsub) {
-    const long long total = (long long)c.R * 9 * nsub;
+__global__ void k_publish_b(const CplB c, const int* __restrict__ active, int slot0, int nslots) {
+    const long long total = (long long)c.R * 9 * nslots;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
     const int gr = (int)(t % c.R);
     const long long q = t / c.R;
     const int fc = (int)(q % 9);
-    const int slot = 1 + (int)(q / 9);
+    const int slot = slot0 + (int)(q / 9);
     const int inst = c.rinst[gr];
     if (active && !active[inst]) return;
     const int li = gr - c.row_first[inst], nr = c.nrow[inst];
@@ -1014,9 +1014,9 @@ cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_publish_b(const CplB& c, const int* active, int nsub, cudaStream_t s) {
-    if (c.R == 0 || nsub == 0) return cudaSuccess;
-    k_publish_b<<<grid_for(9LL * c.R * nsub, 256), 256, 0, s>>>(c, active, nsub);
+cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, cudaStream_t s) {
+    if (c.R == 0 || nslots <= 0) return cudaSuccess;
+    k_publish_b<<<grid_for(9LL * c.R * nslots, 256), 256, 0, s>>>(c, active, slot0, nslots);
     return cudaGetLastError();
 }
 
