@@ -235,6 +235,46 @@ int check_device(osam_ctx* ctx, int device) {
 // ------------------------------------------------------------------------------------------------
 // per-step sequences (used by the graph capture and by the host-driven loop)
 // ------------------------------------------------------------------------------------------------
+// traces of the couplings fed by FOM slot s at history slot `slot` (state u^slot in buffer u)
+bool trace_fuse(osam_ctx* ctx, int s, const double* u, int slot, TraceFuse& tr) {
+    tr = TraceFuse{};
+    for (CplH& c : ctx->cpls) {
+        if (c.src != s) continue;
+        if (tr.n == kMaxFusedTraces) return false;
+        tr.c[tr.n++] = c.d;
+    }
+    tr.u = u;
+    tr.slot = slot;
+    return true;
+}
+
+// substep j + 1 of FOM slot s: internal force at u^{j+1} (with the trace of substep j folded into the
+// same launch), corrector of j + 1 and predictor of j + 2
+int fom_substep(osam_ctx* ctx, int s, int j, const int* active, long long ne) {
+    FomB& g = ctx->slots[s].fom.d;
+    double* X = g.u[(j + 1) & 1];
+    double* Y = g.u[j & 1];
+    TraceFuse tr;
+    const bool fuse = j > 0 && trace_fuse(ctx, s, g.u[j & 1], j, tr);
+    if (j > 0 && !fuse)
+        for (CplH& c : ctx->cpls)
+            if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[j & 1], j, ctx->stream));
+    const int pk = ctx->prof_begin();
+    LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream, fuse ? &tr : nullptr));
+    ctx->prof_end(pk, ne);
+    LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
+                     ctx->stream));
+    return OSAM_OK;
+}
+
+// trace of the last substep of FOM slot s (no force launch follows it within the interval)
+int last_trace(osam_ctx* ctx, int s, const int* active) {
+    FomB& g = ctx->slots[s].fom.d;
+    for (CplH& c : ctx->cpls)
+        if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[ctx->nsub & 1], ctx->nsub, ctx->stream));
+    return OSAM_OK;
+}
+
 int advance_slot(osam_ctx* ctx, int s, const int* active) {
     Slot& S = ctx->slots[s];
     if (S.kind == OSAM_FOM) {
@@ -242,17 +282,8 @@ int advance_slot(osam_ctx* ctx, int s, const int* active) {
         long long ne = 0;
         for (const InstFom& I : S.fom.inst) ne += I.ne;
         LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
-        for (int j = 0; j < ctx->nsub; ++j) {
-            double* X = g.u[(j + 1) & 1];
-            double* Y = g.u[j & 1];
-            const int pk = ctx->prof_begin();
-            LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream));
-            ctx->prof_end(pk, ne);
-            LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
-                             ctx->stream));
-            for (CplH& c : ctx->cpls)
-                if (c.src == s) LK(launch_trace_b(c.d, active, g, X, j + 1, ctx->stream));
-        }
+        for (int j = 0; j < ctx->nsub; ++j) RET(fom_substep(ctx, s, j, active, ne));
+        RET(last_trace(ctx, s, active));
         if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
     } else {
         RomB& r = S.rom.d;
@@ -291,23 +322,22 @@ int advance_pair(osam_ctx* ctx, int s, const int* active) {
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     LK(launch_rom_record0_b(r, active, ctx->side));
     LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
-    for (int j = 0; j < ctx->nsub; ++j) {
-        double* X = g.u[(j + 1) & 1];
-        double* Y = g.u[j & 1];
-        const int pk = ctx->prof_begin();
-        LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream));
-        ctx->prof_end(pk, ne);
-        LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
-                         ctx->stream));
-        for (CplH& c : ctx->cpls)
-            if (c.src == s) LK(launch_trace_b(c.d, active, g, X, j + 1, ctx->stream));
+    // the trace of substep j is complete after the force launch of substep j + 1 (or the last trace)
+    auto rom_substep = [&](int j) -> int {
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
         CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
         for (CplH& c : ctx->cpls)
-            if (c.src == s && c.dst == s + 1) LK(launch_publish_b(c.d, active, j + 1, 1, ctx->side));
-        LK(launch_rom_project_b(r, active, j + 1, j + 1, ctx->side));
-        LK(launch_rom_step_b(r, active, j + 1, ctx->dt, 0, ctx->side));
+            if (c.src == s && c.dst == s + 1) LK(launch_publish_b(c.d, active, j, 1, ctx->side));
+        LK(launch_rom_project_b(r, active, j, j, ctx->side));
+        LK(launch_rom_step_b(r, active, j, ctx->dt, 0, ctx->side));
+        return OSAM_OK;
+    };
+    for (int j = 0; j < ctx->nsub; ++j) {
+        RET(fom_substep(ctx, s, j, active, ne));
+        if (j > 0) RET(rom_substep(j));
     }
+    RET(last_trace(ctx, s, active));
+    RET(rom_substep(ctx->nsub));
     if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
     CK(cudaEventRecord(ctx->ev_join, ctx->side));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));

@@ -134,6 +134,17 @@ struct CplB {
     int dst_rom;
 };
 
+// overlap traces folded into an internal-force launch as extra blocks at the end of its grid: the
+// trace of substep j (u^j, v^j, a^j at the neighbours' Schwarz nodes) is taken while the force of
+// substep j+1 runs, when u^j, v^j and a^j are still intact
+constexpr int kMaxFusedTraces = 2;
+struct TraceFuse {
+    int n = 0;                // couplings (0: none)
+    CplB c[kMaxFusedTraces];
+    const double* u = nullptr;
+    int slot = 0;
+};
+
 // per-instance controller state and criterion arguments
 struct CtlB {
     int n_inst, n_fom, n_rom, ncpl, max_it;
@@ -167,7 +178,7 @@ cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double*
 // batched per-step kernels (step_kernels.cu); `active` masks instances that have converged
 // ------------------------------------------------------------------------------------------------
 cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock_grid,
-                           cudaStream_t s);
+                           cudaStream_t s, const TraceFuse* tr = nullptr);
 cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s);  // FP64 gather into fe
 cudaError_t launch_init_accel_b(const FomB& g, const int* active, cudaStream_t s);  // a = -M^-1 f from fe
 cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slot1, int slot2, int predict_only,

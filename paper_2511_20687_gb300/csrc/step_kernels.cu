@@ -33,9 +33,51 @@ constexpr int kMaxR = 256;
 // ------------------------------------------------------------------------------------------------
 // FOM
 // ------------------------------------------------------------------------------------------------
+// one work item of the overlap trace: row gr = t / 3, component t % 3 of u, v and a interpolated at
+// the row's donor nodes with the trilinear weights, recorded at history slot `slot`
+__device__ __forceinline__ void trace_item(const CplB& c, const int* __restrict__ active, const FomB& src,
+                                           const double* u, int slot, int t) {
+    const int gr = t / 3, cc = t % 3;
+    const int inst = c.rinst[gr];
+    if (active && !active[inst]) return;
+    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
+    double su = 0.0, sv = 0.0, sa = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const double w = c.dw[8 * gr + b];
+        const long long d = (long long)cc * src.NN + c.dnode[8 * gr + b];
+        su = fma(w, u[d], su);
+        sv = fma(w, src.v[d], sv);
+        sa = fma(w, src.a[d], sa);
+    }
+    double* r = c.rec + c.rec_off[inst] + (long long)slot * 9 * nr;
+    r[(long long)(0 + cc) * nr + li] = su;
+    r[(long long)(3 + cc) * nr + li] = sv;
+    r[(long long)(6 + cc) * nr + li] = sa;
+}
+
+// the trace blocks appended to a force grid (block tb counted from the first trace block)
+__device__ __forceinline__ void fused_trace_block(const TraceFuse& tr, const int* __restrict__ active,
+                                                  const FomB& g, int tb) {
+    int t = tb * (int)blockDim.x + (int)threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kMaxFusedTraces; ++k) {
+        if (k >= tr.n) return;
+        if (t < 3 * tr.c[k].R) {
+            trace_item(tr.c[k], active, g, tr.u, tr.slot, t);
+            return;
+        }
+        t -= 3 * tr.c[k].R;
+    }
+}
+
 template <int MAT, typename T, int MODE>
 __global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
-                                                 const double* __restrict__ u) {
+                                                 const double* __restrict__ u, const TraceFuse tr) {
+    if ((int)blockIdx.x >= g.n_eblk) {
+        fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
+        return;
+    }
     const int2 b = g.eblk[blockIdx.x];
     if (active && !active[b.x]) return;
     const InstFom I = g.inst[b.x];
@@ -181,9 +223,14 @@ __device__ __forceinline__ void stress_nh(const f2 H[3][3], f2 kap2, f2 mu, f2 m
 constexpr int kDfSlots = 72;  // 36 gradient entries + 36 accumulated sums
 
 template <int MAT>
-__global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __restrict__ active) {
+__global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __restrict__ active,
+                                                     const TraceFuse tr) {
     using df::f2;
     extern __shared__ float2 sm[];
+    if ((int)blockIdx.x >= g.n_eblk) {
+        fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
+        return;
+    }
     const int2 b = g.eblk[blockIdx.x];
     if (active && !active[b.x]) return;
     const InstFom I = g.inst[b.x];
@@ -619,26 +666,8 @@ __device__ __forceinline__ long long dst_index(const CplB& c, int inst, int slot
 // trace of a FOM source at slot `slot`: rec[inst][slot][f][c][row] = sum_b w_b field_f,c[donor_b]
 __global__ void k_trace_b(const CplB c, const int* __restrict__ active, const FomB src, const double* u, int slot) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * c.R) return;
-    const int gr = t / 3, cc = t % 3;
-    const int inst = c.rinst[gr];
-    if (active && !active[inst]) return;
-    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
-    double su = 0.0, sv = 0.0, sa = 0.0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const double w = c.dw[8 * gr + b];
-        const long long d = (long long)cc * src.NN + c.dnode[8 * gr + b];
-        su = fma(w, u[d], su);
-        sv = fma(w, src.v[d], sv);
-        sa = fma(w, src.a[d], sa);
-    }
-    double* r = c.rec + c.rec_off[inst] + (long long)slot * 9 * nr;
-    r[(long long)(0 + cc) * nr + li] = su;
-    r[(long long)(3 + cc) * nr + li] = sv;
-    r[(long long)(6 + cc) * nr + li] = sa;
+    if (t < 3 * c.R) trace_item(c, active, src, u, slot, t);
 }
-
 // publish a FOM source's recorded slots 1..nsub into the destination history
 __global__ void k_publish_b(const CplB c, const int* __restrict__ active, int slot0, int nslots) {
     const long long total = (long long)c.R * 9 * nslots;
@@ -921,10 +950,15 @@ __global__ void __launch_bounds__(256) k_controller(const CtlB c, cudaGraphCondi
 // launchers
 // ------------------------------------------------------------------------------------------------
 cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock,
-                           cudaStream_t s) {
+                           cudaStream_t s, const TraceFuse* trp) {
     if (g.n_eblk == 0) return cudaSuccess;
     const int b = g.eblock;
     (void)eblock;
+    TraceFuse tr;
+    if (trp) tr = *trp;
+    long long items = 0;
+    for (int k = 0; k < tr.n; ++k) items += 3LL * tr.c[k].R;
+    const int grid = g.n_eblk + (int)((items + b - 1) / b);
     if (g.df32) {
         if (b > 128) return cudaErrorInvalidConfiguration;
         const size_t smem = sizeof(float2) * kDfSlots * b;
@@ -939,11 +973,11 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
             if (e2 != cudaSuccess) return e2;
             attr_set = true;
         }
-        if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<g.n_eblk, b, smem, s>>>(g, active);
-        else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<g.n_eblk, b, smem, s>>>(g, active);
+        if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<grid, b, smem, s>>>(g, active, tr);
+        else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<grid, b, smem, s>>>(g, active, tr);
         return cudaGetLastError();
     }
-#define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<g.n_eblk, b, 0, s>>>(g, active, u)
+#define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, u, tr)
     const bool fp32 = g.fp32 != 0;
     if (g.material == OSAM_NEO_HOOKEAN) {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kGather); }
@@ -959,9 +993,9 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
 cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s) {
     if (g.n_eblk == 0) return cudaSuccess;
     if (g.material == OSAM_NEO_HOOKEAN)
-        k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0]);
+        k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0], TraceFuse{});
     else
-        k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0]);
+        k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0], TraceFuse{});
     return cudaGetLastError();
 }
 
