@@ -11,7 +11,7 @@
 //   S = 1/2 kappa (det C - 1) C^-1 + mu (det C)^-1/3 (I - 1/3 tr C C^-1),
 // is evaluated through F C^-1 = F^-T = cof(F) / J, i.e.
 //   P = [1/2 kappa (J^2 - 1) - 1/3 mu J^-2/3 tr C] / J * cof(F) + mu J^-2/3 F,
-// with J^-2/3 = rcbrt(J^2) and 1/J = J * (J^-2/3)^3 (no division).
+// with J^-1/3 from a reciprocal cube root, J^-2/3 = (J^-1/3)^2 and 1/J = (J^-1/3)^3 (no division).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -27,18 +27,15 @@ constexpr double kGd = 0.57735026918962576451;   // kG1 - kG0 = 1/sqrt(3)
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
-// x^(-1/3) for x > 0 in FP64: a single-precision seed refined by two steps of Newton's method on
-// f(y) = y^-3 - x, i.e. y <- y + y (1 - x y^3) / 3.  Each step roughly squares the relative error
-// (e -> 2 e^2), so the seed's ~1e-7 falls to ~1e-14 and then below the FP64 rounding.  Twelve FP64
-// operations; x <= 0, Inf or NaN propagate to a non-finite result (caught by the step's criterion).
+// x^(-1/3) in FP64 (x != 0): a single-precision seed y, then one third-order correction from the
+// binomial series of the exact factor (1 - e)^(-1/3) = 1 + e/3 + 2e^2/9 + ..., e = 1 - x y^3 the seed's
+// residual (Householder's third-order iteration for y^-3 = x).  The remaining error is ~14 e^3 / 81:
+// with the seed's |e| < 1e-6 that is below the FP64 rounding.  Six FP64 operations and two
+// conversions; zero, Inf or NaN propagate to a non-finite result (caught by the step's criterion).
 __device__ __forceinline__ double rcbrtT(double x) {
-    double y = (double)rcbrtf(__double2float_rn(x));
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double y3 = y * y * y;
-        y = fma(y * (1.0 / 3.0), fma(-x, y3, 1.0), y);
-    }
-    return y;
+    const double y = (double)rcbrtf(__double2float_rn(x));
+    const double e = fma(-x, y * y * y, 1.0);
+    return fma(y, e * fma(e, 2.0 / 9.0, 1.0 / 3.0), y);
 }
 __device__ __forceinline__ float rcbrtT(float x) { return rcbrtf(x); }
 
@@ -111,8 +108,9 @@ __device__ __forceinline__ void nh_factors(const T H[3][3], T kap2, T mu, T mu3,
 #pragma unroll
     for (int k = 1; k < 9; ++k) trC = fmaT(F[k / 3][k % 3], F[k / 3][k % 3], trC);
     const T J2 = J * J;
-    const T r3 = rcbrtT(J2);                 // J^-2/3
-    const T invJ = J * (r3 * r3 * r3);       // J * J^-2 = 1/J
+    const T s1 = rcbrtT(J);                  // J^-1/3
+    const T r3 = s1 * s1;                    // J^-2/3
+    const T invJ = r3 * s1;                  // 1/J
     alpha = mu * r3;
     beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
 }
