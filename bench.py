@@ -53,7 +53,7 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source it was captured on; None until captured.
-FORCE_TRAFFIC = {"source_sha256": "6f239e5091b53d0b29937186ac773b4688378b31af430e1f19314a2a82e316a3", "bytes_per_launch": 3.366e6}
+FORCE_TRAFFIC = {"source_sha256": "15d6d06291cdefe63bce82ca63ee6cb23a6c7b6716345637321627f7b7acbd3e", "bytes_per_launch": 3.659e6}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -155,7 +155,7 @@ class ClockSampler:
 def source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("step_kernels.cu", "hex8_math.cuh"):
+    for f in ("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2511_20687_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -186,7 +186,11 @@ cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slo
 cudaError_t launch_saverest_fom_b(const FomB& g, const int* active, int restore, cudaStream_t s);
 cudaError_t launch_norms_fom_b(const FomB& g, const int* active, double dt, cudaStream_t s);
 cudaError_t launch_copy_u10_b(const FomB& g, const int* active, cudaStream_t s);
+// double-float mode (force_df.cu)
 cudaError_t launch_split_u2_b(const FomB& g, cudaStream_t s);
+cudaError_t launch_force_df_b(const FomB& g, const int* active, const TraceFuse& tr, cudaStream_t s);
+cudaError_t launch_node_df_b(const FomB& g, const int* active, int slot1, int slot2, int predict_only,
+                             const double* ucur, double* unext, double dt, cudaStream_t s);
 cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
                            cudaStream_t s);
 cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, cudaStream_t s);  // slots [slot0, slot0 + nslots)

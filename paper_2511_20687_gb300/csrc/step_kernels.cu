@@ -16,9 +16,9 @@
 
 #include <cstdint>
 
-#include "df32.cuh"
 #include "hex8_math.cuh"
 #include "osam_internal.h"
+#include "trace_item.cuh"
 
 namespace osam {
 
@@ -33,49 +33,11 @@ constexpr int kMaxR = 256;
 // ------------------------------------------------------------------------------------------------
 // FOM
 // ------------------------------------------------------------------------------------------------
-// one work item of the overlap trace: row gr = t / 3, component t % 3 of u, v and a interpolated at
-// the row's donor nodes with the trilinear weights, recorded at history slot `slot`
-__device__ __forceinline__ void trace_item(const CplB& c, const int* __restrict__ active, const FomB& src,
-                                           const double* u, int slot, int t) {
-    const int gr = t / 3, cc = t % 3;
-    const int inst = c.rinst[gr];
-    if (active && !active[inst]) return;
-    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
-    double su = 0.0, sv = 0.0, sa = 0.0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const double w = c.dw[8 * gr + b];
-        const long long d = (long long)cc * src.NN + c.dnode[8 * gr + b];
-        su = fma(w, u[d], su);
-        sv = fma(w, src.v[d], sv);
-        sa = fma(w, src.a[d], sa);
-    }
-    double* r = c.rec + c.rec_off[inst] + (long long)slot * 9 * nr;
-    r[(long long)(0 + cc) * nr + li] = su;
-    r[(long long)(3 + cc) * nr + li] = sv;
-    r[(long long)(6 + cc) * nr + li] = sa;
-}
-
-// the trace blocks appended to a force grid (block tb counted from the first trace block)
-__device__ __forceinline__ void fused_trace_block(const TraceFuse& tr, const int* __restrict__ active,
-                                                  const FomB& g, int tb) {
-    int t = tb * (int)blockDim.x + (int)threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < kMaxFusedTraces; ++k) {
-        if (k >= tr.n) return;
-        if (t < 3 * tr.c[k].R) {
-            trace_item(tr.c[k], active, g, tr.u, tr.slot, t);
-            return;
-        }
-        t -= 3 * tr.c[k].R;
-    }
-}
-
 template <int MAT, typename T, int MODE>
 __global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
                                                  const double* __restrict__ u, const TraceFuse tr) {
     if ((int)blockIdx.x >= g.n_eblk) {
-        fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
+        trace::fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
         return;
     }
     const int2 b = g.eblk[blockIdx.x];
@@ -124,321 +86,6 @@ __global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __rest
         for (int c8 = 0; c8 < 8; ++c8)
 #pragma unroll
             for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
-    }
-}
-
-// ------------------------------------------------------------------------------------------------
-// FOM internal force in double-float arithmetic (df32.cuh): the same sum-factorised formulation as
-// element_force, evaluated on the FP32 pipes (64x the FP64 issue rate of GB300) with ~48-bit
-// significands.  Reads the double-float copy of the displacement written by the node kernel and
-// writes float2 (hi, lo) element contributions.
-// ------------------------------------------------------------------------------------------------
-namespace dfk {
-using df::f2;
-__device__ __forceinline__ f2 G0() { return df::make(0.21132487058639526f, -5.181208351245914e-09f); }
-__device__ __forceinline__ f2 G1() { return df::make(0.7886751294136047f, 5.181208351245914e-09f); }
-__device__ __forceinline__ f2 GD() { return df::make(0.5773502588272095f, 1.0362416702491828e-08f); }
-
-__device__ __forceinline__ void lerp2(const f2 D[2][2], f2 out[2][2]) {
-    f2 E[2][2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const f2 d = df::sub(D[1][e], D[0][e]);
-        E[0][e] = df::fma(G0(), d, D[0][e]);
-        E[1][e] = df::fma(G1(), d, D[0][e]);
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const f2 d = df::sub(E[q][1], E[q][0]);
-        out[q][0] = df::fma(G0(), d, E[q][0]);
-        out[q][1] = df::fma(G1(), d, E[q][0]);
-    }
-}
-
-__device__ __forceinline__ void lerp2T(const f2 S[2][2], f2 out[2][2]) {
-    f2 V[2][2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const f2 s = df::add(S[q][0], S[q][1]);
-        V[q][0] = df::fma(GD(), S[q][0], df::mul(G0(), s));
-        V[q][1] = df::sub(s, V[q][0]);
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const f2 s = df::add(V[0][e], V[1][e]);
-        out[0][e] = df::fma(GD(), V[0][e], df::mul(G0(), s));
-        out[1][e] = df::sub(s, out[0][e]);
-    }
-}
-
-__device__ __forceinline__ void stress_le(const f2 H[3][3], f2 lam, f2 mu, f2 P[3][3]) {
-    const f2 lt = df::mul(lam, df::add(df::add(H[0][0], H[1][1]), H[2][2]));
-    const f2 mu2 = df::add(mu, mu);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) P[c][c] = df::fma(mu2, H[c][c], lt);
-    P[0][1] = P[1][0] = df::mul(mu, df::add(H[0][1], H[1][0]));
-    P[0][2] = P[2][0] = df::mul(mu, df::add(H[0][2], H[2][0]));
-    P[1][2] = P[2][1] = df::mul(mu, df::add(H[1][2], H[2][1]));
-}
-
-// cofactor form of the Neo-Hookean stress (see hex8_math.cuh)
-__device__ __forceinline__ void stress_nh(const f2 H[3][3], f2 kap2, f2 mu, f2 mu3, f2 P[3][3]) {
-    f2 F[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) F[i][j] = (i == j) ? df::add(df::one(), H[i][j]) : H[i][j];
-    f2 c[3][3];
-    c[0][0] = df::sub(df::mul(F[1][1], F[2][2]), df::mul(F[1][2], F[2][1]));
-    c[0][1] = df::sub(df::mul(F[1][2], F[2][0]), df::mul(F[1][0], F[2][2]));
-    c[0][2] = df::sub(df::mul(F[1][0], F[2][1]), df::mul(F[1][1], F[2][0]));
-    c[1][0] = df::sub(df::mul(F[0][2], F[2][1]), df::mul(F[0][1], F[2][2]));
-    c[1][1] = df::sub(df::mul(F[0][0], F[2][2]), df::mul(F[0][2], F[2][0]));
-    c[1][2] = df::sub(df::mul(F[0][1], F[2][0]), df::mul(F[0][0], F[2][1]));
-    c[2][0] = df::sub(df::mul(F[0][1], F[1][2]), df::mul(F[0][2], F[1][1]));
-    c[2][1] = df::sub(df::mul(F[0][2], F[1][0]), df::mul(F[0][0], F[1][2]));
-    c[2][2] = df::sub(df::mul(F[0][0], F[1][1]), df::mul(F[0][1], F[1][0]));
-    const f2 J = df::add(df::add(df::mul(F[0][0], c[0][0]), df::mul(F[0][1], c[0][1])), df::mul(F[0][2], c[0][2]));
-    f2 trC = df::mul(F[0][0], F[0][0]);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) trC = df::fma(F[k / 3][k % 3], F[k / 3][k % 3], trC);
-    const f2 J2 = df::mul(J, J);
-    const f2 r3 = df::rcbrt(J2);                          // J^-2/3
-    const f2 invJ = df::mul(J, df::mul(r3, df::mul(r3, r3)));
-    const f2 alpha = df::mul(mu, r3);
-    const f2 beta = df::mul(df::sub(df::mul(kap2, df::sub(J2, df::one())), df::mul(df::mul(mu3, r3), trC)), invJ);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) P[i][j] = df::fma(alpha, F[i][j], df::mul(beta, c[i][j]));
-}
-}  // namespace dfk
-
-// Phased double-float force: (A) edge differences and interpolation to the Gauss points, unrolled,
-// the 36 gradient entries parked in shared memory; (B) a rolled loop over the 8 Gauss points with one
-// copy of the constitutive code, accumulating the Gauss-point sums of the transposed interpolation in
-// shared memory; (C) the transposed interpolation, unrolled.  Keeping the code small keeps it in the
-// instruction cache.  Shared memory is private per thread (column tid of a [72][blockDim] array of
-// float2), so no barrier is needed.
-constexpr int kDfSlots = 72;  // 36 gradient entries + 36 accumulated sums
-
-template <int MAT>
-__global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __restrict__ active,
-                                                     const TraceFuse tr) {
-    using df::f2;
-    extern __shared__ float2 sm[];
-    if ((int)blockIdx.x >= g.n_eblk) {
-        fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
-        return;
-    }
-    const int2 b = g.eblk[blockIdx.x];
-    if (active && !active[b.x]) return;
-    const InstFom I = g.inst[b.x];
-    const int e = b.y + threadIdx.x;
-    if (e >= I.ne) return;
-    const int nt = blockDim.x, tid = threadIdx.x;
-    auto slot = [&](int s) -> float2& { return sm[s * nt + tid]; };
-    auto ld = [&](int s) -> f2 { const float2 v = slot(s); return df::make(v.x, v.y); };
-    auto st = [&](int s, f2 v) { slot(s) = make_float2(v.h, v.l); };
-    const int i = e % I.nx;
-    const int t = e / I.nx;
-    const int j = t % I.ny;
-    const int k = t / I.ny;
-    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
-    const int n0 = i + sy * j + sz * k;
-    // (A) gradients: slot (dir * 12 + c * 4 + 2 * s0 + s1), dir 0: Gx[c][q][r], 1: Gy[c][p][r], 2: Gz[c][p][q]
-    {
-        const f2 invh = df::from_double(I.invh);
-        const float2* ub = g.u2 + I.node_off;
-#pragma unroll 1
-        for (int c = 0; c < 3; ++c) {
-            f2 U[8];
-#pragma unroll
-            for (int c8 = 0; c8 < 8; ++c8) {
-                const float2 v = ub[(long long)c * g.NN + n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz];
-                U[c8] = df::make(v.x, v.y);
-            }
-            f2 D[2][2], G[2][2];
-#pragma unroll
-            for (int dir = 0; dir < 3; ++dir) {
-#pragma unroll
-                for (int p = 0; p < 2; ++p)
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int hi = dir == 0 ? 1 + 2 * p + 4 * q : (dir == 1 ? p + 2 + 4 * q : p + 2 * q + 4);
-                        const int lo = dir == 0 ? 2 * p + 4 * q : (dir == 1 ? p + 4 * q : p + 2 * q);
-                        D[p][q] = df::mul(df::sub(U[hi], U[lo]), invh);
-                    }
-                dfk::lerp2(D, G);
-#pragma unroll
-                for (int p = 0; p < 2; ++p)
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) st(dir * 12 + c * 4 + 2 * p + q, G[p][q]);
-            }
-        }
-    }
-    // (B) constitutive law at each Gauss point; sums into slots 36 + (dir * 12 + c * 4 + ...)
-    {
-        const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-        const double mu = I.mu_e ? I.mu_e[e] : I.mu;
-        f2 m1, m2, m3;
-        if (MAT == OSAM_NEO_HOOKEAN) {
-            const double kappa = lam + (2.0 / 3.0) * mu;
-            m1 = df::from_double(0.5 * kappa * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::from_double(mu * I.w8 / 3.0);
-        } else {
-            m1 = df::from_double(lam * I.w8); m2 = df::from_double(mu * I.w8); m3 = df::make(0.f, 0.f);
-        }
-#pragma unroll 1
-        for (int gp = 0; gp < 8; ++gp) {
-            const int p = gp >> 2, q = (gp >> 1) & 1, r = gp & 1;
-            f2 Hm[3][3], P[3][3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Hm[c][0] = ld(0 * 12 + c * 4 + 2 * q + r);
-                Hm[c][1] = ld(1 * 12 + c * 4 + 2 * p + r);
-                Hm[c][2] = ld(2 * 12 + c * 4 + 2 * p + q);
-            }
-            if (MAT == OSAM_NEO_HOOKEAN) dfk::stress_nh(Hm, m1, m2, m3, P);
-            else dfk::stress_le(Hm, m1, m2, P);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int sx = 36 + 0 * 12 + c * 4 + 2 * q + r;
-                const int sy_ = 36 + 1 * 12 + c * 4 + 2 * p + r;
-                const int sz_ = 36 + 2 * 12 + c * 4 + 2 * p + q;
-                st(sx, p == 0 ? P[c][0] : df::add(ld(sx), P[c][0]));
-                st(sy_, q == 0 ? P[c][1] : df::add(ld(sy_), P[c][1]));
-                st(sz_, r == 0 ? P[c][2] : df::add(ld(sz_), P[c][2]));
-            }
-        }
-    }
-    // (C) transposed interpolation and edge-difference transpose, per component
-    float2* fe = static_cast<float2*>(g.fe) + I.elem_off;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        f2 F[8], S[2][2], Tm[2][2];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 0 * 12 + c * 4 + s);
-        dfk::lerp2T(S, Tm);
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[1 + 2 * ay + 4 * az] = Tm[ay][az];
-                F[2 * ay + 4 * az] = df::neg(Tm[ay][az]);
-            }
-#pragma unroll
-        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 1 * 12 + c * 4 + s);
-        dfk::lerp2T(S, Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[ax + 2 + 4 * az] = df::add(F[ax + 2 + 4 * az], Tm[ax][az]);
-                F[ax + 4 * az] = df::sub(F[ax + 4 * az], Tm[ax][az]);
-            }
-#pragma unroll
-        for (int s = 0; s < 4; ++s) S[s >> 1][s & 1] = ld(36 + 2 * 12 + c * 4 + s);
-        dfk::lerp2T(S, Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) {
-                F[ax + 2 * ay + 4] = df::add(F[ax + 2 * ay + 4], Tm[ax][ay]);
-                F[ax + 2 * ay] = df::sub(F[ax + 2 * ay], Tm[ax][ay]);
-            }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = make_float2(F[c8].h, F[c8].l);
-    }
-}
-
-// node kernel of the double-float force: contributions summed in double-float in a fixed order,
-// the update in FP64, and the double-float copy of the predicted displacement for the next force
-__global__ void __launch_bounds__(kNodeBlock) k_node_df_b(const FomB g, const int* __restrict__ active, int slot1,
-                                                         int slot2, int predict_only, const double* ucur,
-                                                         double* unext, double dt) {
-    using df::f2;
-    const int2 b = g.nblk[blockIdx.x];
-    if (active && !active[b.x]) return;
-    const InstFom I = g.inst[b.x];
-    const int n = b.y + threadIdx.x;
-    if (n >= I.nn) return;
-    const int i = n % (I.nx + 1);
-    const int t = n / (I.nx + 1);
-    const int j = t % (I.ny + 1);
-    const int k = t / (I.ny + 1);
-    const long long gn = I.node_off + n;
-    const uint8_t cm = g.clamp[gn];
-    const int row = g.srow[gn];
-    const double hdt = 0.5 * dt, hdt2 = 0.5 * dt * dt;
-    const double minv = g.minv[gn];
-    const double* h1 = slot1 >= 0 ? g.hist + I.hist_off + (long long)slot1 * 9 * I.ns : nullptr;
-    const double* h2 = slot2 >= 0 ? g.hist + I.hist_off + (long long)slot2 * 9 * I.ns : nullptr;
-    const float2* fe = static_cast<const float2*>(g.fe) + I.elem_off;
-    // loads first (state, then the element contributions of the three components, summed per
-    // component in double-float in the fixed corner order)
-    double uc[3], vc[3], ac[3];
-    f2 f[3] = {df::make(0.f, 0.f), df::make(0.f, 0.f), df::make(0.f, 0.f)};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long d = (long long)c * g.NN + gn;
-        uc[c] = ucur[d];
-        vc[c] = g.v[d];
-        ac[c] = g.a[d];
-    }
-    if (!predict_only && row < 0 && cm != 7) {
-#pragma unroll
-        for (int az = 0; az < 2; ++az) {
-            const int ke = k - az;
-            if (ke < 0 || ke >= I.nz) continue;
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) {
-                const int je = j - ay;
-                if (je < 0 || je >= I.ny) continue;
-#pragma unroll
-                for (int ax = 0; ax < 2; ++ax) {
-                    const int ie = i - ax;
-                    if (ie < 0 || ie >= I.nx) continue;
-                    const long long e = ie + (long long)I.nx * (je + I.ny * ke);
-                    const int corner = ax + 2 * ay + 4 * az;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float2 v = __ldg(fe + (long long)(corner * 3 + c) * g.NE + e);
-                        f[c] = df::add(f[c], df::make(v.x, v.y));
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long d = (long long)c * g.NN + gn;
-        double un;
-        if (cm & (1 << c)) {
-            g.v[d] = 0.0;
-            g.a[d] = 0.0;
-            un = 0.0;
-        } else if (row >= 0) {
-            if (!predict_only) {
-                g.v[d] = h1[(long long)(3 + c) * I.ns + row];
-                g.a[d] = h1[(long long)(6 + c) * I.ns + row];
-            }
-            un = h2 ? h2[(long long)c * I.ns + row] : 0.0;
-        } else {
-            double vn = vc[c], an = ac[c];
-            if (!predict_only) {
-                const double anew = -df::to_double(f[c]) * minv;
-                vn = fma(hdt, an + anew, vn);
-                an = anew;
-                g.v[d] = vn;
-                g.a[d] = an;
-            }
-            un = fma(hdt2, an, fma(dt, vn, uc[c]));
-        }
-        if (h2) {
-            unext[d] = un;
-            const f2 s = df::from_double(un);
-            g.u2[d] = make_float2(s.h, s.l);
-        }
     }
 }
 
@@ -575,20 +222,6 @@ __global__ void __launch_bounds__(kNodeBlock) k_saverest_fom_b(const FomB g, con
     }
 }
 
-// double-float copy of u[0] (initialisation of the f32x2 force input)
-__global__ void __launch_bounds__(kNodeBlock) k_split_u2_b(const FomB g) {
-    const int2 b = g.nblk[blockIdx.x];
-    const InstFom I = g.inst[b.x];
-    const int n = b.y + threadIdx.x;
-    if (n >= I.nn) return;
-    const long long gn = I.node_off + n;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const df::f2 v = df::from_double(g.u[0][(long long)c * g.NN + gn]);
-        g.u2[(long long)c * g.NN + gn] = make_float2(v.h, v.l);
-    }
-}
-
 // u[0] <- u[1] (an interval with an odd substep count ends in the second displacement buffer)
 __global__ void __launch_bounds__(kNodeBlock) k_copy_u10_b(const FomB g, const int* __restrict__ active) {
     const int2 b = g.nblk[blockIdx.x];
@@ -666,7 +299,7 @@ __device__ __forceinline__ long long dst_index(const CplB& c, int inst, int slot
 // trace of a FOM source at slot `slot`: rec[inst][slot][f][c][row] = sum_b w_b field_f,c[donor_b]
 __global__ void k_trace_b(const CplB c, const int* __restrict__ active, const FomB src, const double* u, int slot) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 3 * c.R) trace_item(c, active, src, u, slot, t);
+    if (t < 3 * c.R) trace::trace_item(c, active, src, u, slot, t);
 }
 // publish a FOM source's recorded slots 1..nsub into the destination history
 __global__ void k_publish_b(const CplB c, const int* __restrict__ active, int slot0, int nslots) {
@@ -959,24 +592,7 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
     long long items = 0;
     for (int k = 0; k < tr.n; ++k) items += 3LL * tr.c[k].R;
     const int grid = g.n_eblk + (int)((items + b - 1) / b);
-    if (g.df32) {
-        if (b > 128) return cudaErrorInvalidConfiguration;
-        const size_t smem = sizeof(float2) * kDfSlots * b;
-        static bool attr_set = false;  // opt in to more than 48 KB of dynamic shared memory, once
-        if (!attr_set) {
-            const int max_bytes = (int)(sizeof(float2) * kDfSlots * 128);
-            cudaError_t e1 = cudaFuncSetAttribute(k_force_df2_b<OSAM_NEO_HOOKEAN>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-            cudaError_t e2 = cudaFuncSetAttribute(k_force_df2_b<OSAM_LINEAR_ELASTIC>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-            if (e1 != cudaSuccess) return e1;
-            if (e2 != cudaSuccess) return e2;
-            attr_set = true;
-        }
-        if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<grid, b, smem, s>>>(g, active, tr);
-        else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<grid, b, smem, s>>>(g, active, tr);
-        return cudaGetLastError();
-    }
+    if (g.df32) return launch_force_df_b(g, active, tr, s);
 #define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, u, tr)
     const bool fp32 = g.fp32 != 0;
     if (g.material == OSAM_NEO_HOOKEAN) {
@@ -1007,10 +623,7 @@ cudaError_t launch_init_accel_b(const FomB& g, const int* active, cudaStream_t s
 cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slot1, int slot2, int predict_only,
                           const double* ucur, double* unext, double dt, cudaStream_t s) {
     const bool fp32 = g.fp32 != 0;
-    if (g.df32) {
-        k_node_df_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
-        return cudaGetLastError();
-    }
+    if (g.df32) return launch_node_df_b(g, active, slot1, slot2, predict_only, ucur, unext, dt, s);
     if (fp32) {
         if (scatter == kAtomic) k_node_b<float, kAtomic><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
         else k_node_b<float, kGather><<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, slot2, predict_only, ucur, unext, dt);
@@ -1023,11 +636,6 @@ cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slo
 
 cudaError_t launch_saverest_fom_b(const FomB& g, const int* active, int restore, cudaStream_t s) {
     k_saverest_fom_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, restore);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_split_u2_b(const FomB& g, cudaStream_t s) {
-    k_split_u2_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g);
     return cudaGetLastError();
 }
 
