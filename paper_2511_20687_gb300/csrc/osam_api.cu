@@ -468,6 +468,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
     if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE)
         return ctx->fail(OSAM_EINVAL, "bad precision");
+    if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_LOWREG)
+        return ctx->fail(OSAM_EINVAL, "bad scatter mode");
     for (int k = 0; k < d0.n_couplings; ++k) {
         const osam_coupling_desc& c = d0.couplings[k];
         if (c.dst < 0 || c.dst >= d0.n_subdomains || c.src < 0 || c.src >= d0.n_subdomains || c.dst == c.src)
@@ -990,15 +992,19 @@ int autotune(osam_ctx* ctx) {
     g.a = a;
     const int slot2 = std::min(2, ctx->nsub);
     float best_ms = 1e30f, gather_ms = 1e30f;
-    int best_block = 128, best_scatter = kGather;
-    const int cands[6][2] = {{kGather, 64}, {kGather, 128}, {kGather, 256}, {kAtomic, 64}, {kAtomic, 128}, {kAtomic, 256}};
+    int best_block = 128, best_scatter = kGather, best_occ = 0;
+    // (scatter, element block, register cap); the capped FP64 kernel exists for gather and <= 128 threads
+    const int cands[8][3] = {{kGather, 64, 0}, {kGather, 128, 0}, {kGather, 256, 0}, {kGather, 64, 1},
+                             {kGather, 128, 1}, {kAtomic, 64, 0}, {kAtomic, 128, 0}, {kAtomic, 256, 0}};
     for (const auto& cd : cands) {
-        const int mode = cd[0], block = cd[1];
-        if (g.df32 && (mode == kAtomic || block > 128)) continue;  // double-float force: gather, <= 128 threads
+        const int mode = cd[0], block = cd[1], occ = cd[2];
+        if (g.df32 && (mode == kAtomic || block > 128 || occ)) continue;  // double-float force: gather, <= 128 threads
+        if (occ && g.fp32) continue;
         RET(set_eblocks(ctx, G, block));
         g.eblk = G.d.eblk;
         g.n_eblk = G.d.n_eblk;
         g.eblock = block;
+        g.occ = occ;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
             CK(launch_force_b(g, nullptr, u, mode, block, ctx->stream));
@@ -1009,9 +1015,9 @@ int autotune(osam_ctx* ctx) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
         if (mode == kGather) {
-            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; }
+            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; best_occ = occ; }
         } else if (ms < 0.95f * gather_ms && ms < best_ms) {
-            best_ms = ms; best_block = block; best_scatter = kAtomic;
+            best_ms = ms; best_block = block; best_scatter = kAtomic; best_occ = 0;
         }
     }
     CK(cudaMemsetAsync(G.d.f, 0, sizeof(double) * 3 * NN, ctx->stream));
@@ -1019,7 +1025,10 @@ int autotune(osam_ctx* ctx) {
     cudaFree(u); cudaFree(v); cudaFree(a); cudaFree(un);
     ctx->scatter = best_scatter;
     for (Slot& S : ctx->slots)
-        if (S.kind == OSAM_FOM) RET(set_eblocks(ctx, S.fom, best_block));
+        if (S.kind == OSAM_FOM) {
+            RET(set_eblocks(ctx, S.fom, best_block));
+            S.fom.d.occ = best_occ;
+        }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }
@@ -1118,6 +1127,9 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     for (CplH& c : ctx->cpls) RET(zoh_cpl(ctx, c, nullptr));
     RET(initial_accel(ctx, nullptr));
     if (d0.scatter == OSAM_SCATTER_AUTO) RET(autotune(ctx));
+    if (d0.scatter == OSAM_SCATTER_GATHER_LOWREG && d0.precision == OSAM_FP64)
+        for (Slot& S : ctx->slots)
+            if (S.kind == OSAM_FOM) S.fom.d.occ = 1;
     for (Slot& S : ctx->slots)
         if (S.kind == OSAM_FOM) S.fom.d.scatter = ctx->scatter;
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1140,9 +1152,14 @@ const char* osam_last_error(const osam_ctx* ctx) {
 
 int osam_scatter_mode(osam_ctx* ctx) { return ctx ? ctx->scatter : 0; }
 
-int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block) {
+int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap) {
     if (!ctx) return OSAM_EINVAL;
     if (scatter) *scatter = ctx->scatter;
+    if (register_cap) {
+        *register_cap = 0;
+        for (Slot& S : ctx->slots)
+            if (S.kind == OSAM_FOM && S.fom.d.occ) *register_cap = 128;
+    }
     if (element_block) {
         *element_block = 0;
         for (Slot& S : ctx->slots)

@@ -88,6 +88,7 @@ struct FomB {
     double* partial;          // criterion partial sums, 2 per node block
     float2* u2;               // double-float copy of the predicted displacement [3][NN] (f32x2 force)
     int material, fp32, scatter;
+    int occ;                  // 1: FP64 gather force capped at 128 registers (autotuned)
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 

@@ -34,8 +34,8 @@ constexpr int kMaxR = 256;
 // FOM
 // ------------------------------------------------------------------------------------------------
 template <int MAT, typename T, int MODE>
-__global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
-                                                 const double* __restrict__ u, const TraceFuse tr) {
+__device__ __forceinline__ void force_body(const FomB& g, const int* __restrict__ active,
+                                           const double* __restrict__ u, const TraceFuse& tr) {
     if ((int)blockIdx.x >= g.n_eblk) {
         trace::fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
         return;
@@ -87,6 +87,21 @@ __global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __rest
 #pragma unroll
             for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
     }
+}
+
+// the force kernel at its natural register count (168 for Neo-Hookean FP64: 12 warps per SM) ...
+template <int MAT, typename T, int MODE>
+__global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
+                                                 const double* __restrict__ u, const TraceFuse tr) {
+    force_body<MAT, T, MODE>(g, active, u, tr);
+}
+
+// ... and capped at 128 registers (16 warps per SM, a few spilled values): the autotuner keeps
+// whichever is faster on the problem at hand
+template <int MAT>
+__global__ void __launch_bounds__(128, 4) k_force_occ_b(const FomB g, const int* __restrict__ active,
+                                                        const double* __restrict__ u, const TraceFuse tr) {
+    force_body<MAT, double, kGather>(g, active, u, tr);
 }
 
 // a = -M^-1 f on every non-clamped dof from the FP64 element buffer (initial acceleration)
@@ -595,6 +610,11 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
     if (g.df32) return launch_force_df_b(g, active, tr, s);
 #define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, u, tr)
     const bool fp32 = g.fp32 != 0;
+    if (g.occ && !fp32 && scatter == kGather && b <= 128) {
+        if (g.material == OSAM_NEO_HOOKEAN) k_force_occ_b<OSAM_NEO_HOOKEAN><<<grid, b, 0, s>>>(g, active, u, tr);
+        else k_force_occ_b<OSAM_LINEAR_ELASTIC><<<grid, b, 0, s>>>(g, active, u, tr);
+        return cudaGetLastError();
+    }
     if (g.material == OSAM_NEO_HOOKEAN) {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kGather); }
         else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kGather); }
