@@ -193,14 +193,18 @@ def train_rom(W, osam, args, device, log):
     log(f"training run: {args.snapshots} controller steps of 4 substeps in {time.time() - t0:.1f}s (amplitude {amp:.3e})")
     t0 = time.time()
     ops = osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device)
-    log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {time.time() - t0:.1f}s")
-    return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}
+    fit_s = time.time() - t0
+    log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {fit_s:.1f}s")
+    fit = {"gpu_seconds": fit_s, "r": args.rank, "r_s": int(ops["r_s"]), "n_snap": args.snapshots,
+           "n_dof": int(U.shape[1]), "n_sdof": int(S.shape[1]), "training": (U, A, S)}
+    return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}, fit
 
 
-def train_batched_roms(W, osam, specs_ff, snapshots, r, device, log, chunk=32):
+def train_batched_roms(W, osam, torch, specs_ff, snapshots, r, device, log, chunk=32):
     """Per-sample OpInf ROMs of subdomain B: FOM-FOM training runs of the samples advanced together
-    as batches (controller steps of 4 substeps, one snapshot per step, double-float force), then one
-    GPU opinf_fit per sample."""
+    as batches (controller steps of 4 substeps, one snapshot per step, double-float force), snapshots
+    gathered on the device, then one GPU opinf_fit per sample."""
+    dev = f"cuda:{device}"
     ops, ranks = [], []
     t0 = time.time()
     for c0 in range(0, len(specs_ff), chunk):
@@ -208,18 +212,28 @@ def train_batched_roms(W, osam, specs_ff, snapshots, r, device, log, chunk=32):
         for sp in group:
             sp.n_substeps = 4
         batch = osam.Batch(group, precision=osam.F32X2_FORCE, device=device)
-        masks = [rom_dof_masks(sp.subdomains[1]) for sp in group]
-        U = [np.empty((snapshots, int(f.sum()))) for f, _ in masks]
-        A = [np.empty_like(x) for x in U]
-        S = [np.empty((snapshots, int(sd.sum()))) for _, sd in masks]
+        idx = []
+        for sp in group:
+            f, sd = rom_dof_masks(sp.subdomains[1])
+            idx.append((torch.from_numpy(np.flatnonzero(f)).to(dev), torch.from_numpy(np.flatnonzero(sd)).to(dev)))
+        max_nn = max(sp.subdomains[1].n_nodes for sp in group)
+        bu = torch.empty((max_nn, 3), dtype=torch.float64, device=dev)
+        ba = torch.empty((max_nn, 3), dtype=torch.float64, device=dev)
+        U = [torch.empty((snapshots, fi.numel()), dtype=torch.float64, device=dev) for fi, _ in idx]
+        A = [torch.empty_like(x) for x in U]
+        S = [torch.empty((snapshots, si.numel()), dtype=torch.float64, device=dev) for _, si in idx]
         for k in range(snapshots):
             batch.step()
-            for i, (f, sd) in enumerate(masks):
-                u, _, a = batch.state(1, fields=(0, 2), inst=i)
-                U[i][k] = u.reshape(-1)[f]
-                A[i][k] = a.reshape(-1)[f]
-                S[i][k] = u.reshape(-1)[sd]
+            for i, (fi, si) in enumerate(idx):
+                nn = group[i].subdomains[1].n_nodes
+                ub, ab = bu[:nn], ba[:nn]
+                batch.state(1, out=(ub, None, ab), inst=i)
+                uf, af = ub.reshape(-1), ab.reshape(-1)
+                U[i][k] = uf[fi]
+                A[i][k] = af[fi]
+                S[i][k] = uf[si]
         batch.close()
+        torch.cuda.synchronize()
         for i in range(len(group)):
             # a short training run can have a numerical rank below r: take the largest of r, 3r/4, r/2, ...
             for rr in (r, 3 * r // 4, r // 2, r // 4):
@@ -232,6 +246,7 @@ def train_batched_roms(W, osam, specs_ff, snapshots, r, device, log, chunk=32):
                         raise
             ranks.append(rr)
             ops.append({1: {k: o[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}})
+        del U, A, S
     log(f"batched training: {len(specs_ff)} samples x {snapshots} snapshots, r={r} ({sum(x == r for x in ranks)} "
         f"samples at full rank), in {time.time() - t0:.1f}s")
     return ops, ranks
@@ -241,7 +256,7 @@ def measure_batched(W, osam, torch, flush, args, device, log):
     """Batched vs plain on the parameter-sweep workload: the same samples (FOM / OpInf pairs) advanced
     by one batched context (graph-captured step) and by one context per sample, run one after another."""
     specs = W.batched_samples(n_samples=args.batched_samples, rom=True)
-    ops, ranks = train_batched_roms(W, osam, W.batched_samples(n_samples=args.batched_samples, rom=False),
+    ops, ranks = train_batched_roms(W, osam, torch, W.batched_samples(n_samples=args.batched_samples, rom=False),
                                     args.batched_snapshots, 32, device, log)
     batch = osam.Batch(specs, rom_ops=ops, device=device)
     for _ in range(3):
@@ -276,6 +291,18 @@ def measure_batched(W, osam, torch, flush, args, device, log):
     for p in singles:
         p.close()
     n_el = sum(sp.subdomains[0].n_elements for sp in specs)
+    # the oracle on a bounded sample of the same sweep: the first two samples, one controller step of
+    # one Schwarz iteration each, their fitted ROMs
+    from oracle import oracle as O
+    o_upd, o_s = 0, 0.0
+    for sp, o in list(zip(specs, ops))[:2]:
+        sp1 = sp
+        sp1.max_iters = 1
+        ref = O.Problem(sp1, rom_ops=o)
+        t0 = time.process_time()
+        ref.step()
+        o_s += time.process_time() - t0
+        o_upd += sp1.n_substeps * sp1.subdomains[0].n_elements
     return {"workload": f"{len(specs)} FOM / OpInf(r=32) pairs, n x n x 2n Neo-Hookean FOM, n ~ U{{8..32}}, "
                         f"{n_el} FOM elements in total, ROMs fitted on {args.batched_snapshots} snapshots each",
             "rom_ranks": {"32": sum(x == 32 for x in ranks), "below_32": sum(x < 32 for x in ranks)},
@@ -283,8 +310,52 @@ def measure_batched(W, osam, torch, flush, args, device, log):
             "plain_steps": args.batched_plain_steps, "plain_value": p_upd / p_wall,
             "plain_value_device": p_upd / (p_ms * 1e-3), "speedup": (upd / wall) / (p_upd / p_wall),
             "mean_iterations": float(np.mean(its)), "max_iterations": int(max(its)), "unit": UNIT,
+            "oracle_value": o_upd / o_s, "oracle_cores": 1,
+            "oracle_sample": f"samples 0-1, one controller step of one Schwarz iteration each, {o_s:.1f} s CPU",
             "tuning": tuning, "timing": "host wall clock around each synchronous step call (value) and the "
                                         "library's CUDA events (value_device); L2 flushed between steps"}
+
+
+def measure_fit(fit_info, log):
+    """opinf_fit on the GPU (timed during training, host snapshot matrices in, operators out) against
+    the oracle's numpy fit of the same snapshots with the same r and r_s."""
+    from oracle import fit as OF
+    U, A, S = fit_info.pop("training")
+    t0 = time.perf_counter()
+    OF.opinf_fit(U.T, A.T, S.T, r=fit_info["r"], lam=1e-6, r_s=fit_info["r_s"])
+    cpu = time.perf_counter() - t0
+    log(f"oracle fit: {cpu:.1f}s")
+    return {**fit_info, "unit": "s", "higher_is_better": False, "oracle_seconds": cpu,
+            "oracle_threads": os.cpu_count(), "oracle_kind": "oracle/fit.py (numpy SVD and solve, threaded BLAS)",
+            "speedup_vs_oracle": cpu / fit_info["gpu_seconds"]}
+
+
+def measure_adjoint(W, osam, local, log, oracle_steps=40):
+    """Checkpointed adjoint of the 20x20x40 Neo-Hookean bar (1000 steps, checkpoints every 50): J and its
+    gradients w.r.t. u0, v0, lambda_e, mu_e on the GPU, against the oracle's adjoint of the same bar on
+    a bounded number of steps."""
+    from oracle import oracle as O
+    p, w = W.adjoint_bar()
+    sd = p.subdomains[0]
+    n = p.info["n_steps"]
+    args = (sd.dims, sd.h, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0, None, p.dt, n, w)
+    osam.adjoint(*args, checkpoint_every=50, device=local)  # warm-up
+    reps = [osam.adjoint(*args, checkpoint_every=50, device=local)["elapsed_ms"] for _ in range(3)]
+    gpu_ms = min(reps)
+    t0 = time.process_time()
+    O.adjoint(sd.dims, sd.h, sd.origin, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0, None, p.dt,
+              oracle_steps, w)
+    cpu_s = time.process_time() - t0
+    ne = sd.n_elements
+    gpu_rate = ne * n / (gpu_ms * 1e-3)
+    cpu_rate = ne * oracle_steps / cpu_s
+    log(f"adjoint: GPU {gpu_ms:.1f} ms for {n} steps, oracle {cpu_s:.1f}s for {oracle_steps} steps")
+    return {"workload": f"adjoint_bar {sd.dims[0]}x{sd.dims[1]}x{sd.dims[2]} Neo-Hookean, per-element Lame "
+                        f"parameters, {n} steps, checkpoints every 50",
+            "unit": "element-steps/s (forward + reverse)", "value": gpu_rate, "ms": gpu_ms,
+            "oracle_value": cpu_rate, "oracle_cores": 1,
+            "oracle_sample": f"the same bar, {oracle_steps} steps, {cpu_s:.1f} s CPU", "speedup_vs_oracle": gpu_rate / cpu_rate,
+            "timing": "library CUDA events around the whole adjoint call (best of 3 after a warm-up)"}
 
 
 def hybrid_spec(W, args):
@@ -439,11 +510,13 @@ def main():
     from paper_2511_20687_gb300 import osam
     from paper_2511_20687_gb300 import workloads as W
 
+    fit_info = None
     if args.fom_only:
         spec = W.fom_opinf_hybrid(args.n, args.nz, rom=False)
         rom_ops = None
     else:
-        rom_ops = {1: train_rom(W, osam, args, local, log)}
+        hyb_ops, fit_info = train_rom(W, osam, args, local, log)
+        rom_ops = {1: hyb_ops}
         spec = hybrid_spec(W, args)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     head_prec = osam.F32X2_FORCE if args.precision == "f32x2" else osam.FP64
@@ -504,6 +577,11 @@ def main():
         batched = measure_batched(W, osam, torch, flush, args, local, log)
         log(f"batched: {batched['value']:.3e} vs plain {batched['plain_value']:.3e} ({batched['speedup']:.1f}x)")
 
+    fit_meas = adjoint_meas = None
+    if world == 1 and not args.no_cpu_baseline and fit_info is not None:
+        fit_meas = measure_fit(fit_info, log)
+        adjoint_meas = measure_adjoint(W, osam, local, log)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
         rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
@@ -552,7 +630,8 @@ def main():
                 "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
                 "gpu_launches": head["prof"]["kernel_launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-                "variants": variants, "batched_vs_plain": batched, "hbm": hbm,
+                "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "adjoint": adjoint_meas,
+                "hbm": hbm,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}
         print(json.dumps(line), flush=True)

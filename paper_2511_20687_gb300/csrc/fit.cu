@@ -1,6 +1,7 @@
 // opinf_fit: the offline OpInf stage of Sec. 3 and Sec. 4.2.1 (Eq. opinf_schwarz_inference).
 //   POD by the method of snapshots: G = U U^T (n_snap x n_snap Gram, device GEMM over the long dof
-//   dimension), G = V diag(sigma^2) V^T (symmetric eigensolver on the host), Phi = U^T V_r Sigma_r^-1,
+//   dimension), G = V diag(sigma^2) V^T (Householder tridiagonalisation + implicit QL on the host),
+//   Phi = U^T V_r Sigma_r^-1,
 //   then one Cholesky re-orthonormalisation Phi <- Phi L^-T with L L^T = Phi^T Phi (same span).
 //   Boundary basis Phi_S likewise from the Schwarz snapshots, r_s chosen by the energy criterion
 //   (Eq. pod_energy: smallest r with E_r >= energy_s).
@@ -24,44 +25,120 @@ namespace {
 
 thread_local std::string g_fit_error;
 
-// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major); on return A's diagonal
-// holds the eigenvalues and V (row-major) the eigenvectors as columns
-void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& V) {
-    V.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-    double fro = 0.0;
-    for (double x : A) fro += x * x;
-    fro = std::sqrt(fro);
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
-        if (std::sqrt(off) <= 1e-16 * fro) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[(size_t)p * n + q];
-                if (std::fabs(apq) <= 1e-300) continue;
-                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                const double theta = (aqq - app) / (2.0 * apq);
-                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+// Symmetric eigen-decomposition by Householder reduction to tridiagonal form followed by the
+// implicit QL iteration with Wilkinson-type shifts (Householder 1958; Bowdler, Martin, Reinsch and
+// Wilkinson 1968).  A is n x n, row-major, symmetric; on return A's diagonal holds the eigenvalues
+// and V (row-major) the eigenvectors as columns.  About 9 n^3 flops with contiguous row access.
+void sym_eig(std::vector<double>& A, int n, std::vector<double>& V) {
+    std::vector<double> d(n), e(n, 0.0), tau(n, 0.0), p(n), w(n);
+    // (1) A <- H_k A H_k, H_k = I - tau_k v_k v_k^T acting on rows / columns k+1..n-1; v_k is kept in
+    //     row k to the right of the diagonal (the part of A that the reduction no longer needs)
+    for (int k = 0; k + 2 < n; ++k) {
+        double* ak = &A[(size_t)k * n];
+        const int m0 = k + 1;
+        double scale = 0.0;
+        for (int i = m0; i < n; ++i) scale = std::max(scale, std::fabs(ak[i]));
+        if (scale == 0.0) { e[k] = 0.0; tau[k] = 0.0; continue; }
+        double ss = 0.0;
+        for (int i = m0; i < n; ++i) { ak[i] /= scale; ss += ak[i] * ak[i]; }
+        const double nrm = std::sqrt(ss);
+        const double alpha = ak[m0] > 0.0 ? -nrm : nrm;      // reflect x onto alpha e_1
+        e[k] = alpha * scale;
+        ak[m0] -= alpha;                                     // v = x - alpha e_1
+        const double vv = ss - 2.0 * alpha * (ak[m0] + alpha) + alpha * alpha;  // |v|^2
+        const double t = vv > 0.0 ? 2.0 / vv : 0.0;
+        tau[k] = t;
+        // p = t B v with B = A[m0.., m0..] (symmetric: use rows), then w = p - (t/2)(p.v) v
+        for (int i = m0; i < n; ++i) {
+            const double* ai = &A[(size_t)i * n];
+            double s = 0.0;
+            for (int j = m0; j < n; ++j) s += ai[j] * ak[j];
+            p[i] = t * s;
+        }
+        double pv = 0.0;
+        for (int i = m0; i < n; ++i) pv += p[i] * ak[i];
+        const double kk = 0.5 * t * pv;
+        for (int i = m0; i < n; ++i) w[i] = p[i] - kk * ak[i];
+        // B <- B - v w^T - w v^T
+        for (int i = m0; i < n; ++i) {
+            double* ai = &A[(size_t)i * n];
+            const double vi = ak[i], wi = w[i];
+            for (int j = m0; j < n; ++j) ai[j] -= vi * w[j] + wi * ak[j];
+        }
+    }
+    for (int k = 0; k < n; ++k) d[k] = A[(size_t)k * n + k];
+    if (n >= 2) e[n - 2] = A[(size_t)(n - 2) * n + (n - 1)];
+    // (2) Q = H_0 H_1 ... H_{n-3}, accumulated from the last reflector; Z = Q^T (rows = vectors)
+    std::vector<double> Q((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    for (int k = n - 3; k >= 0; --k) {
+        const double t = tau[k];
+        if (t == 0.0) continue;
+        const double* v = &A[(size_t)k * n];
+        const int m0 = k + 1;
+        // Q[m0.., m0..] <- (I - t v v^T) Q[m0.., m0..]: s_j = t sum_i v_i Q_ij, Q_ij -= v_i s_j
+        std::fill(p.begin(), p.end(), 0.0);
+        for (int i = m0; i < n; ++i) {
+            const double vi = v[i];
+            const double* qi = &Q[(size_t)i * n];
+            for (int j = m0; j < n; ++j) p[j] += vi * qi[j];
+        }
+        for (int i = m0; i < n; ++i) {
+            const double vi = t * v[i];
+            double* qi = &Q[(size_t)i * n];
+            for (int j = m0; j < n; ++j) qi[j] -= vi * p[j];
+        }
+    }
+    std::vector<double> Z((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Z[(size_t)j * n + i] = Q[(size_t)i * n + j];
+    // (3) implicit QL on (d, e), e[i] coupling d[i] and d[i+1]; each plane rotation of rows i, i+1 of
+    //     the tridiagonal matrix is applied to rows i, i+1 of Z
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter < 60; ++iter) {
+            int m = l;
+            for (; m + 1 < n; ++m) {
+                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-16 * dd) break;
+            }
+            if (m == l) break;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));   // shifted so that the shift is the
+            double s = 1.0, c = 1.0, pp = 0.0;                     // eigenvalue of the leading 2x2 closer to d[l]
+            int i = m - 1;
+            bool deflated = false;
+            for (; i >= l; --i) {
+                const double f = s * e[i], b = c * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) { d[i + 1] -= pp; e[m] = 0.0; deflated = true; break; }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - pp;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                pp = s * r;
+                d[i + 1] = g + pp;
+                g = c * r - b;
+                double* zi = &Z[(size_t)i * n];
+                double* zj = &Z[(size_t)(i + 1) * n];
                 for (int k = 0; k < n; ++k) {
-                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-                    A[(size_t)k * n + p] = c * akp - s * akq;
-                    A[(size_t)k * n + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-                    A[(size_t)p * n + k] = c * apk - s * aqk;
-                    A[(size_t)q * n + k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-                    V[(size_t)k * n + p] = c * vkp - s * vkq;
-                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                    const double a0 = zi[k], a1 = zj[k];
+                    zj[k] = s * a0 + c * a1;
+                    zi[k] = c * a0 - s * a1;
                 }
             }
+            if (deflated) continue;
+            d[l] -= pp;
+            e[l] = g;
+            e[m] = 0.0;
+        }
     }
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) V[(size_t)k * n + i] = Z[(size_t)i * n + k];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = i == j ? d[i] : 0.0;
 }
 
 // Cholesky L L^T = A (row-major, lower triangle written into A); false if not positive definite
@@ -134,7 +211,7 @@ int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, doub
     FK(cudaStreamSynchronize(s));
     for (int i = 0; i < nsnap; ++i)  // exact symmetry
         for (int j = i + 1; j < nsnap; ++j) Gh[(size_t)j * nsnap + i] = Gh[(size_t)i * nsnap + j];
-    jacobi_eig(Gh, nsnap, V);
+    sym_eig(Gh, nsnap, V);
     std::vector<int> order(nsnap);
     for (int i = 0; i < nsnap; ++i) order[i] = i;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return Gh[(size_t)a * nsnap + a] > Gh[(size_t)b * nsnap + b]; });
