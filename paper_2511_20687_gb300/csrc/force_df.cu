@@ -134,7 +134,6 @@ __global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __
     const int n0 = i + sy * j + sz * k;
     // (A) gradients: slot (dir * 12 + c * 4 + 2 * s0 + s1), dir 0: Gx[c][q][r], 1: Gy[c][p][r], 2: Gz[c][p][q]
     {
-        const f2 invh = df::from_double(I.invh);
         const float2* ub = g.u2 + I.node_off;
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __
                     for (int q = 0; q < 2; ++q) {
                         const int hi = dir == 0 ? 1 + 2 * p + 4 * q : (dir == 1 ? p + 2 + 4 * q : p + 2 * q + 4);
                         const int lo = dir == 0 ? 2 * p + 4 * q : (dir == 1 ? p + 4 * q : p + 2 * q);
-                        D[p][q] = df::mul(df::sub(U[hi], U[lo]), invh);
+                        D[p][q] = df::sub(U[hi], U[lo]);  // the copy holds u / h
                     }
                 dfk::lerp2(D, G);
 #pragma unroll
@@ -322,13 +321,13 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_df_b(const FomB g, const in
         }
         if (h2) {
             unext[d] = un;
-            const f2 s = df::from_double(un);
+            const f2 s = df::from_double(un * I.invh);
             g.u2[d] = make_float2(s.h, s.l);
         }
     }
 }
 
-// double-float copy of u[0] (initialisation of the f32x2 force input)
+// double-float copy of u[0] / h (initialisation of the f32x2 force input)
 __global__ void __launch_bounds__(kNodeBlock) k_split_u2_b(const FomB g) {
     const int2 b = g.nblk[blockIdx.x];
     const InstFom I = g.inst[b.x];
@@ -337,7 +336,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_split_u2_b(const FomB g) {
     const long long gn = I.node_off + n;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const df::f2 v = df::from_double(g.u[0][(long long)c * g.NN + gn]);
+        const df::f2 v = df::from_double(g.u[0][(long long)c * g.NN + gn] * I.invh);
         g.u2[(long long)c * g.NN + gn] = make_float2(v.h, v.l);
     }
 }

@@ -260,7 +260,7 @@ int fom_substep(osam_ctx* ctx, int s, int j, const int* active, long long ne) {
         for (CplH& c : ctx->cpls)
             if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[j & 1], j, ctx->stream));
     const int pk = ctx->prof_begin();
-    LK(launch_force_b(g, active, X, ctx->scatter, g.eblock, ctx->stream, fuse ? &tr : nullptr));
+    LK(launch_force_b(g, active, ctx->scatter, ctx->stream, fuse ? &tr : nullptr));
     ctx->prof_end(pk, ne);
     LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
                      ctx->stream));
@@ -596,6 +596,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     CKA(B.pu = ctx->alloc<double>(3 * NN));
     CKA(B.pv = ctx->alloc<double>(3 * NN));
     CKA(B.hist = ctx->alloc<double>(std::max<long long>(H, 1)));
+    CKA(B.us = ctx->alloc<double>(3 * NN));
     if (B.df32) CKA(B.u2 = ctx->alloc<float2>(3 * NN));
     bool any_le = false, any_me = false;
     for (int i = 0; i < n; ++i) {
@@ -1008,7 +1009,7 @@ int autotune(osam_ctx* ctx) {
         g.occ = occ;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
-            CK(launch_force_b(g, nullptr, u, mode, block, ctx->stream));
+            CK(launch_force_b(g, nullptr, mode, ctx->stream));
             CK(launch_node_b(g, nullptr, mode, 1, slot2, 0, u, un, ctx->dt, ctx->stream));
         }
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -1563,7 +1564,7 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     // one explicit step in place on (u[0], v, a)
     auto step = [&](double* u_store) -> int {
         CK(launch_node_b(F, nullptr, kAtomic, -1, 1, 1, F.u[0], F.u[1], dt, ctx->stream));
-        CK(launch_force_b(F, nullptr, F.u[1], kAtomic, F.eblock, ctx->stream));
+        CK(launch_force_b(F, nullptr, kAtomic, ctx->stream));
         CK(launch_node_b(F, nullptr, kAtomic, 1, -1, 0, F.u[1], F.u[0], dt, ctx->stream));
         CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));

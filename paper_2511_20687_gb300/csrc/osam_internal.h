@@ -86,7 +86,8 @@ struct FomB {
     double* pv;
     double* hist;             // per instance [(nsub+1)][3 fields][3 comps][ns] at hist_off
     double* partial;          // criterion partial sums, 2 per node block
-    float2* u2;               // double-float copy of the predicted displacement [3][NN] (f32x2 force)
+    double* us;               // predicted displacement divided by h [3][NN] (input of the FP64 / FP32 force)
+    float2* u2;               // double-float copy of the predicted displacement / h [3][NN] (f32x2 force)
     int material, fp32, scatter;
     int occ;                  // 1: FP64 gather force capped at 128 registers (autotuned)
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
@@ -178,9 +179,10 @@ cudaError_t launch_zero_clamped(int nn, const uint8_t* clamp, double* u, double*
 // ------------------------------------------------------------------------------------------------
 // batched per-step kernels (step_kernels.cu); `active` masks instances that have converged
 // ------------------------------------------------------------------------------------------------
-cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock_grid,
-                           cudaStream_t s, const TraceFuse* tr = nullptr);
-cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s);  // FP64 gather into fe
+// internal force of the predicted displacement held (divided by h) in g.us / g.u2
+cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaStream_t s,
+                           const TraceFuse* tr = nullptr);
+cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s);  // FP64 gather of f(u[0]) into fe
 cudaError_t launch_init_accel_b(const FomB& g, const int* active, cudaStream_t s);  // a = -M^-1 f from fe
 cudaError_t launch_node_b(const FomB& g, const int* active, int scatter, int slot1, int slot2, int predict_only,
                           const double* ucur, double* unext, double dt, cudaStream_t s);

@@ -34,8 +34,7 @@ constexpr int kMaxR = 256;
 // FOM
 // ------------------------------------------------------------------------------------------------
 template <int MAT, typename T, int MODE>
-__device__ __forceinline__ void force_body(const FomB& g, const int* __restrict__ active,
-                                           const double* __restrict__ u, const TraceFuse& tr) {
+__device__ __forceinline__ void force_body(const FomB& g, const int* __restrict__ active, const TraceFuse& tr) {
     if ((int)blockIdx.x >= g.n_eblk) {
         trace::fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_eblk);
         return;
@@ -64,13 +63,13 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
         m1 = T(lam * I.w8); m2 = T(mu * I.w8); m3 = T(0);
     }
     T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
-    const double* ub = u + I.node_off;
+    const double* ub = g.us + I.node_off;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         double U[8];
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) U[c8] = ub[(long long)c * g.NN + node[c8]];
-        edge_differences<T>(U, I.invh, Dx[c], Dy[c], Dz[c]);
+        edge_differences_prescaled<T>(U, Dx[c], Dy[c], Dz[c]);
     }
     T F[3][8];
     element_force<MAT, T>(Dx, Dy, Dz, m1, m2, m3, F);
@@ -91,17 +90,28 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
 
 // the force kernel at its natural register count (168 for Neo-Hookean FP64: 12 warps per SM) ...
 template <int MAT, typename T, int MODE>
-__global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active,
-                                                 const double* __restrict__ u, const TraceFuse tr) {
-    force_body<MAT, T, MODE>(g, active, u, tr);
+__global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active, const TraceFuse tr) {
+    force_body<MAT, T, MODE>(g, active, tr);
 }
 
 // ... and capped at 128 registers (16 warps per SM, a few spilled values): the autotuner keeps
 // whichever is faster on the problem at hand
 template <int MAT>
 __global__ void __launch_bounds__(128, 4) k_force_occ_b(const FomB g, const int* __restrict__ active,
-                                                        const double* __restrict__ u, const TraceFuse tr) {
-    force_body<MAT, double, kGather>(g, active, u, tr);
+                                                        const TraceFuse tr) {
+    force_body<MAT, double, kGather>(g, active, tr);
+}
+
+// us = u[0] / h (input of the FP64 force at the start of an interval / after a state change)
+__global__ void __launch_bounds__(kNodeBlock) k_scale_u0_b(const FomB g, const int* __restrict__ active) {
+    const int2 b = g.nblk[blockIdx.x];
+    if (active && !active[b.x]) return;
+    const InstFom I = g.inst[b.x];
+    const int n = b.y + threadIdx.x;
+    if (n >= I.nn) return;
+    const long long gn = I.node_off + n;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g.us[(long long)c * g.NN + gn] = g.u[0][(long long)c * g.NN + gn] * I.invh;
 }
 
 // a = -M^-1 f on every non-clamped dof from the FP64 element buffer (initial acceleration)
@@ -216,7 +226,10 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
             }
             un = fma(hdt2, an, fma(dt, vn, uc[c]));
         }
-        if (h2) unext[d] = un;
+        if (h2) {
+            unext[d] = un;
+            g.us[d] = un * I.invh;
+        }
     }
 }
 
@@ -597,22 +610,20 @@ __global__ void __launch_bounds__(256) k_controller(const CtlB c, cudaGraphCondi
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
-cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, int scatter, int eblock,
-                           cudaStream_t s, const TraceFuse* trp) {
+cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaStream_t s, const TraceFuse* trp) {
     if (g.n_eblk == 0) return cudaSuccess;
     const int b = g.eblock;
-    (void)eblock;
     TraceFuse tr;
     if (trp) tr = *trp;
     long long items = 0;
     for (int k = 0; k < tr.n; ++k) items += 3LL * tr.c[k].R;
     const int grid = g.n_eblk + (int)((items + b - 1) / b);
     if (g.df32) return launch_force_df_b(g, active, tr, s);
-#define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, u, tr)
+#define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, tr)
     const bool fp32 = g.fp32 != 0;
     if (g.occ && !fp32 && scatter == kGather && b <= 128) {
-        if (g.material == OSAM_NEO_HOOKEAN) k_force_occ_b<OSAM_NEO_HOOKEAN><<<grid, b, 0, s>>>(g, active, u, tr);
-        else k_force_occ_b<OSAM_LINEAR_ELASTIC><<<grid, b, 0, s>>>(g, active, u, tr);
+        if (g.material == OSAM_NEO_HOOKEAN) k_force_occ_b<OSAM_NEO_HOOKEAN><<<grid, b, 0, s>>>(g, active, tr);
+        else k_force_occ_b<OSAM_LINEAR_ELASTIC><<<grid, b, 0, s>>>(g, active, tr);
         return cudaGetLastError();
     }
     if (g.material == OSAM_NEO_HOOKEAN) {
@@ -628,10 +639,11 @@ cudaError_t launch_force_b(const FomB& g, const int* active, const double* u, in
 
 cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s) {
     if (g.n_eblk == 0) return cudaSuccess;
+    k_scale_u0_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active);
     if (g.material == OSAM_NEO_HOOKEAN)
-        k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0], TraceFuse{});
+        k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, TraceFuse{});
     else
-        k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, g.u[0], TraceFuse{});
+        k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, TraceFuse{});
     return cudaGetLastError();
 }
 

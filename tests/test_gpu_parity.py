@@ -197,6 +197,25 @@ def test_full_basis_rom_hybrid(torch_cuda):
         assert np.abs(ff.state(i)[0] - gf[i][0]).max() < 1e-11 * np.abs(gf[i][0]).max()
 
 
+@pytest.mark.parametrize("n_sub", [1, 2, 3])
+@pytest.mark.parametrize("kinds", [["fom", "fom"], ["fom", "rom"], ["fom", "rom", "fom"]])
+def test_short_controller_intervals(torch_cuda, n_sub, kinds):
+    """1-3 substeps per controller step: the trace of the last substep has no force launch to ride in,
+    and with one substep none is folded at all; the ROM side stream then runs only after it."""
+    spec = W.bar_chain("short", 3, [6] * len(kinds), kinds, "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, n_sub,
+                       max_iters=8)
+    ops = None
+    if "rom" in kinds:
+        sd = spec.subdomains[1]
+        faces = 2 if len(kinds) == 3 else 1
+        n_sdof = faces * 3 * (sd.dims[0] + 1) ** 2
+        ops = {1: W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, 5, 4, 21)}
+    hist, its, _, _ = _run_pair(spec, 5, rom_ops=ops)
+    for i in range(len(spec.subdomains)):
+        assert rel_l2(*hist[i]) < 1e-9, i
+    assert all(abs(a - b) <= 1 for a, b in its)
+
+
 @pytest.fixture(scope="module")
 def fitted_hybrid():
     """Small NH FOM-ROM hybrid with operators fitted by the oracle on a FOM-FOM training run."""
