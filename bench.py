@@ -560,7 +560,9 @@ def main():
             achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
             traffic = FORCE_TRAFFIC["bytes_per_launch"] if FORCE_TRAFFIC["source_sha256"] == source_sha() else None
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_force_b<NeoHookean, f64>",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                    "kernel": ("k_force_tile_b<NeoHookean, gather>" if res["tuning"].get("tiled")
+                               else "k_force_b<NeoHookean, f64, %s>" % res["tuning"]["scatter"]),
                     "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)", "fp64_fma_measured_tflops": fp64_meas,
                     "frac_of_measured_fp64": achieved / fp64_meas, "force_ms_per_launch": per_launch,
                     "force_time_share": prof["force_ms"] / res["total_ms"]}

@@ -57,9 +57,17 @@ enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1 };
 enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1, OSAM_F32X2_FORCE = 2 };
 /* element-to-node scatter of the internal force: FP64 atomics, or a deterministic two-pass
  * element-buffer / node-gather scheme; GATHER_LOWREG is the gather scheme with the FP64 force kernel
- * compiled for at most 128 registers per thread (more resident warps, a few spilled values; the FP32
- * variants ignore the cap); AUTO times the candidates at initialisation and keeps the fastest */
-enum { OSAM_SCATTER_AUTO = 0, OSAM_SCATTER_ATOMIC = 1, OSAM_SCATTER_GATHER = 2, OSAM_SCATTER_GATHER_LOWREG = 3 };
+ * compiled for at most 128 registers per thread (more resident warps, a few spilled values);
+ * GATHER_TILED the gather scheme with the FP64 force evaluated by 8x4x4 element tiles that share
+ * their edge interpolation (same results bit for bit); the FP32 variants ignore both.  AUTO times
+ * the candidates at initialisation and keeps the fastest */
+enum {
+    OSAM_SCATTER_AUTO = 0,
+    OSAM_SCATTER_ATOMIC = 1,
+    OSAM_SCATTER_GATHER = 2,
+    OSAM_SCATTER_GATHER_LOWREG = 3,
+    OSAM_SCATTER_GATHER_TILED = 4
+};
 
 typedef struct osam_ctx osam_ctx;
 
@@ -187,10 +195,10 @@ OSAM_API int osam_instance_sizes(osam_ctx* ctx, int inst, int sub, int* n_nodes,
  * synchronisation per step; enable = 0 drives the iterations from the host (one synchronisation per
  * iteration).  Kernel-level profiling (osam_profile) always uses the host-driven path. */
 OSAM_API int osam_set_graph(osam_ctx* ctx, int enable);
-/* Autotuned launch configuration of the force kernel: scatter mode, element block size and register
+/* Autotuned launch configuration of the force kernel: scatter mode, element block size, register
  * cap (0: natural register count; 128: the FP64 gather kernel compiled for at most 128 registers per
- * thread).  Any pointer may be NULL. */
-OSAM_API int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap);
+ * thread) and tiling (1: the FP64 force by 8x4x4 element tiles).  Any pointer may be NULL. */
+OSAM_API int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap, int* tiled);
 
 /* Copy a subdomain's nodal state out / in ([nodes][3] each, any pointer may be NULL).  For a ROM the
  * output is the reconstructed field: Phi q on free dofs, boundary data on Schwarz dofs, 0 on clamped

@@ -125,19 +125,12 @@ __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, 
         for (int j = 0; j < 3; ++j) P[i][j] = fmaT(alpha, F[i][j], beta * C[i][j]);
 }
 
-// Element force from scaled edge differences.
-//   Dx[c][ay][az] = (u_c(1,ay,az) - u_c(0,ay,az)) / h   (and Dy[c][ax][az], Dz[c][ax][ay])
+// Element force from the displacement gradients at the Gauss points:
+//   Gx[c][q][r] = d u_c / dx at (y GP q, z GP r), Gy[c][p][r], Gz[c][p][q].
 // Output F[c][corner], corner = ax + 2 ay + 4 az.
 template <int MAT, typename T>
-__device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3][2][2], const T Dz[3][2][2],
-                                              T m1, T m2, T m3, T F[3][8]) {
-    T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lerp2<T>(Dx[c], Gx[c]);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
-        lerp2<T>(Dy[c], Gy[c]);   // Gy[c][p][r]
-        lerp2<T>(Dz[c], Gz[c]);   // Gz[c][p][q]
-    }
+__device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
+                                                   T m1, T m2, T m3, T F[3][8]) {
     T Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
 #pragma unroll
     for (int p = 0; p < 2; ++p)
@@ -204,6 +197,21 @@ __device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3]
                 F[c][ax + 2 * ay] -= Tm[ax][ay];
             }
     }
+}
+
+// Element force from scaled edge differences.
+//   Dx[c][ay][az] = (u_c(1,ay,az) - u_c(0,ay,az)) / h   (and Dy[c][ax][az], Dz[c][ax][ay])
+template <int MAT, typename T>
+__device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3][2][2], const T Dz[3][2][2],
+                                              T m1, T m2, T m3, T F[3][8]) {
+    T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lerp2<T>(Dx[c], Gx[c]);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
+        lerp2<T>(Dy[c], Gy[c]);   // Gy[c][p][r]
+        lerp2<T>(Dz[c], Gz[c]);   // Gz[c][p][q]
+    }
+    element_force_grad<MAT, T>(Gx, Gy, Gz, m1, m2, m3, F);
 }
 
 __device__ __forceinline__ void atomic_add(double* p, double v) { atomicAdd(p, v); }

@@ -468,7 +468,7 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
     if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE)
         return ctx->fail(OSAM_EINVAL, "bad precision");
-    if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_LOWREG)
+    if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_TILED)
         return ctx->fail(OSAM_EINVAL, "bad scatter mode");
     for (int k = 0; k < d0.n_couplings; ++k) {
         const osam_coupling_desc& c = d0.couplings[k];
@@ -555,6 +555,23 @@ int check_stability(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
             return ctx->fail(OSAM_ECFL, "instance %d subdomain %d: dt = %.6e above the explicit stability limit "
                                         "%.6e", i, s, ctx->dt, lim);
     }
+    return OSAM_OK;
+}
+
+// 8x4x4 element tiles of every instance of a FOM group (the tiled force kernel's blocks)
+int set_tiles(osam_ctx* ctx, FomGroupH& G) {
+    std::vector<int4> tb;
+    for (int i = 0; i < (int)G.inst.size(); ++i) {
+        const InstFom& I = G.inst[i];
+        for (int k0 = 0; k0 < I.nz; k0 += 4)
+            for (int j0 = 0; j0 < I.ny; j0 += 4)
+                for (int i0 = 0; i0 < I.nx; i0 += 8) tb.push_back(make_int4(i, i0, j0, k0));
+    }
+    int4* d = ctx->alloc<int4>(tb.size());
+    CKA(d);
+    RET(upload(ctx, d, tb.data(), sizeof(int4) * tb.size()));
+    G.d.tblk = d;
+    G.d.n_tblk = (int)tb.size();
     return OSAM_OK;
 }
 
@@ -647,6 +664,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     B.nblk_off = nbo;
     CKA(B.partial = ctx->alloc<double>(2LL * B.n_nblk));
     RET(set_eblocks(ctx, G, 128));
+    RET(set_tiles(ctx, G));
     RET(check_stability(ctx, G, s, n, descs));
     if (B.df32) CK(launch_split_u2_b(B, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -993,20 +1011,21 @@ int autotune(osam_ctx* ctx) {
     g.a = a;
     const int slot2 = std::min(2, ctx->nsub);
     float best_ms = 1e30f, gather_ms = 1e30f;
-    int best_block = 128, best_scatter = kGather, best_occ = 0;
-    // (scatter, element block, register cap).  The 128-register FP64 kernel measured level with the
-    // natural one on the bench meshes, so AUTO does not try it (OSAM_SCATTER_GATHER_LOWREG selects it).
-    const int cands[6][3] = {{kGather, 64, 0}, {kGather, 128, 0}, {kGather, 256, 0},
-                             {kAtomic, 64, 0}, {kAtomic, 128, 0}, {kAtomic, 256, 0}};
+    int best_block = 128, best_scatter = kGather, best_tiled = 0;
+    // (scatter, element block, tiled).  The 128-register FP64 kernel measured level with the natural
+    // one on the bench meshes, so AUTO does not try it (OSAM_SCATTER_GATHER_LOWREG selects it).
+    const int cands[8][3] = {{kGather, 64, 0}, {kGather, 128, 0}, {kGather, 256, 0}, {kGather, 128, 1},
+                             {kAtomic, 64, 0}, {kAtomic, 128, 0}, {kAtomic, 256, 0}, {kAtomic, 128, 1}};
     for (const auto& cd : cands) {
-        const int mode = cd[0], block = cd[1], occ = cd[2];
-        if (g.df32 && (mode == kAtomic || block > 128 || occ)) continue;  // double-float force: gather, <= 128 threads
-        if (occ && g.fp32) continue;
+        const int mode = cd[0], block = cd[1], tiled = cd[2];
+        if (g.df32 && (mode == kAtomic || block > 128 || tiled)) continue;  // double-float force: gather, <= 128 threads
+        if (tiled && g.fp32) continue;                                    // the tiled kernel is FP64
         RET(set_eblocks(ctx, G, block));
         g.eblk = G.d.eblk;
         g.n_eblk = G.d.n_eblk;
         g.eblock = block;
-        g.occ = occ;
+        g.occ = 0;
+        g.tiled = tiled;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
             CK(launch_force_b(g, nullptr, mode, ctx->stream));
@@ -1017,9 +1036,9 @@ int autotune(osam_ctx* ctx) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
         if (mode == kGather) {
-            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; best_occ = occ; }
+            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; best_tiled = tiled; }
         } else if (ms < 0.95f * gather_ms && ms < best_ms) {
-            best_ms = ms; best_block = block; best_scatter = kAtomic; best_occ = 0;
+            best_ms = ms; best_block = block; best_scatter = kAtomic; best_tiled = tiled;
         }
     }
     CK(cudaMemsetAsync(G.d.f, 0, sizeof(double) * 3 * NN, ctx->stream));
@@ -1029,7 +1048,7 @@ int autotune(osam_ctx* ctx) {
     for (Slot& S : ctx->slots)
         if (S.kind == OSAM_FOM) {
             RET(set_eblocks(ctx, S.fom, best_block));
-            S.fom.d.occ = best_occ;
+            S.fom.d.tiled = best_tiled;
         }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
@@ -1132,6 +1151,9 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     if (d0.scatter == OSAM_SCATTER_GATHER_LOWREG && d0.precision == OSAM_FP64)
         for (Slot& S : ctx->slots)
             if (S.kind == OSAM_FOM) S.fom.d.occ = 1;
+    if (d0.scatter == OSAM_SCATTER_GATHER_TILED && d0.precision == OSAM_FP64)
+        for (Slot& S : ctx->slots)
+            if (S.kind == OSAM_FOM) S.fom.d.tiled = 1;
     for (Slot& S : ctx->slots)
         if (S.kind == OSAM_FOM) S.fom.d.scatter = ctx->scatter;
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1154,9 +1176,14 @@ const char* osam_last_error(const osam_ctx* ctx) {
 
 int osam_scatter_mode(osam_ctx* ctx) { return ctx ? ctx->scatter : 0; }
 
-int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap) {
+int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap, int* tiled) {
     if (!ctx) return OSAM_EINVAL;
     if (scatter) *scatter = ctx->scatter;
+    if (tiled) {
+        *tiled = 0;
+        for (Slot& S : ctx->slots)
+            if (S.kind == OSAM_FOM && S.fom.d.tiled) *tiled = 1;
+    }
     if (register_cap) {
         *register_cap = 0;
         for (Slot& S : ctx->slots)

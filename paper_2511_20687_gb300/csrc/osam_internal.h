@@ -89,7 +89,10 @@ struct FomB {
     double* us;               // predicted displacement divided by h [3][NN] (input of the FP64 / FP32 force)
     float2* u2;               // double-float copy of the predicted displacement / h [3][NN] (f32x2 force)
     int material, fp32, scatter;
-    int occ;                  // 1: FP64 gather force capped at 128 registers (autotuned)
+    int occ;                  // 1: FP64 gather force capped at 128 registers
+    const int4* tblk;         // 8x4x4 element tiles: (instance, i0, j0, k0)
+    int n_tblk;
+    int tiled;                // 1: FP64 force by tiles (shared edge interpolation)
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 

@@ -88,6 +88,122 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
     }
 }
 
+// Tiled FP64 force: one block of 128 threads per 8x4x4 tile of elements.  The edge differences and
+// the first interpolation stage of the gradients are shared by neighbouring elements (an x-edge pair
+// interpolated along y serves the elements below and above it), so the block computes them once per
+// tile in shared memory and each thread finishes its element with the second stage.  The arithmetic
+// per value is the one of edge_differences_prescaled + lerp2, so the result equals the untiled
+// kernel's bit for bit; the sharing saves ~34 of the ~850 FP64 operations per element.
+constexpr int kTX = 8, kTY = 4, kTZ = 4;
+
+template <int MAT, int MODE>
+__global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* __restrict__ active,
+                                                      const TraceFuse tr) {
+    if ((int)blockIdx.x >= g.n_tblk) {
+        trace::fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_tblk);
+        return;
+    }
+    __shared__ double su[3][kTZ + 1][kTY + 1][kTX + 1];  // u / h at the tile's nodes
+    __shared__ double sax[3][kTZ + 1][kTY][kTX][2];     // x-edges interpolated along y: [c][k][j][i][gy]
+    __shared__ double say[3][kTZ + 1][kTY][kTX][2];     // y-edges interpolated along x: [c][k][j][i][gx]
+    __shared__ double saz[3][kTZ][kTY + 1][kTX][2];     // z-edges interpolated along x: [c][k][j][i][gx]
+    const int4 tb = g.tblk[blockIdx.x];
+    if (active && !active[tb.x]) return;
+    const InstFom I = g.inst[tb.x];
+    const int i0 = tb.y, j0 = tb.z, k0 = tb.w;
+    const int tid = threadIdx.x;
+    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
+    // (1) nodal values of the tile (zero beyond the mesh; only elements inside read them)
+    for (int q = tid; q < 3 * (kTZ + 1) * (kTY + 1) * (kTX + 1); q += blockDim.x) {
+        const int c = q / ((kTZ + 1) * (kTY + 1) * (kTX + 1));
+        const int rem = q % ((kTZ + 1) * (kTY + 1) * (kTX + 1));
+        const int kk = rem / ((kTY + 1) * (kTX + 1)), jj = (rem / (kTX + 1)) % (kTY + 1), ii = rem % (kTX + 1);
+        const int gi = i0 + ii, gj = j0 + jj, gk = k0 + kk;
+        double v = 0.0;
+        if (gi <= I.nx && gj <= I.ny && gk <= I.nz)
+            v = g.us[(long long)c * g.NN + I.node_off + gi + (long long)sy * gj + (long long)sz * gk];
+        su[c][kk][jj][ii] = v;
+    }
+    __syncthreads();
+    // (2) edge differences and the first interpolation stage, 3 directions x 3 components x 160 pairs
+    const double G[2] = {hex8::kG0, hex8::kG1};
+    for (int q = tid; q < 3 * 3 * 160; q += blockDim.x) {
+        const int dir = q / 480, c = (q / 160) % 3, w = q % 160;
+        if (dir == 0) {          // x-edges (i; j, k) and (i; j + 1, k), interpolated along y
+            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
+            const double d0 = su[c][k][j][i + 1] - su[c][k][j][i];
+            const double d1 = su[c][k][j + 1][i + 1] - su[c][k][j + 1][i];
+            const double dd = d1 - d0;
+            sax[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
+            sax[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
+        } else if (dir == 1) {   // y-edges (i, j; k) and (i + 1, j; k), interpolated along x
+            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
+            const double d0 = su[c][k][j + 1][i] - su[c][k][j][i];
+            const double d1 = su[c][k][j + 1][i + 1] - su[c][k][j][i + 1];
+            const double dd = d1 - d0;
+            say[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
+            say[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
+        } else {                 // z-edges (i, j, k) and (i + 1, j, k), interpolated along x
+            const int k = w / 40, j = (w / 8) % 5, i = w % 8;
+            const double d0 = su[c][k + 1][j][i] - su[c][k][j][i];
+            const double d1 = su[c][k + 1][j][i + 1] - su[c][k][j][i + 1];
+            const double dd = d1 - d0;
+            saz[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
+            saz[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
+        }
+    }
+    __syncthreads();
+    // (3) one element per thread: second stage, constitutive law, transposed interpolation
+    const int ti = tid % kTX, tj = (tid / kTX) % kTY, tk = tid / (kTX * kTY);
+    const int ei = i0 + ti, ej = j0 + tj, ek = k0 + tk;
+    if (ei >= I.nx || ej >= I.ny || ek >= I.nz) return;
+    const int e = ei + I.nx * (ej + I.ny * ek);
+    double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            double e0 = sax[c][tk][tj][ti][a], d = sax[c][tk + 1][tj][ti][a] - e0;   // along z
+            Gx[c][a][0] = hex8::fmaT(G[0], d, e0);
+            Gx[c][a][1] = hex8::fmaT(G[1], d, e0);
+            e0 = say[c][tk][tj][ti][a];
+            d = say[c][tk + 1][tj][ti][a] - e0;                                       // along z
+            Gy[c][a][0] = hex8::fmaT(G[0], d, e0);
+            Gy[c][a][1] = hex8::fmaT(G[1], d, e0);
+            e0 = saz[c][tk][tj][ti][a];
+            d = saz[c][tk][tj + 1][ti][a] - e0;                                       // along y
+            Gz[c][a][0] = hex8::fmaT(G[0], d, e0);
+            Gz[c][a][1] = hex8::fmaT(G[1], d, e0);
+        }
+    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+    double m1, m2, m3;
+    if (MAT == OSAM_NEO_HOOKEAN) {
+        const double kappa = lam + (2.0 / 3.0) * mu;
+        m1 = 0.5 * kappa * I.w8; m2 = mu * I.w8; m3 = mu * I.w8 / 3.0;
+    } else {
+        m1 = lam * I.w8; m2 = mu * I.w8; m3 = 0.0;
+    }
+    double F[3][8];
+    element_force_grad<MAT, double>(Gx, Gy, Gz, m1, m2, m3, F);
+    if (MODE == kAtomic) {
+        double* f = static_cast<double*>(g.f) + I.node_off;
+        const int n0 = ei + sy * ej + sz * ek;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8)
+                atomic_add(f + (long long)c * g.NN + n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz,
+                           F[c][c8]);
+    } else {
+        double* fe = static_cast<double*>(g.fe) + I.elem_off;
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
+    }
+}
+
 // the force kernel at its natural register count (168 for Neo-Hookean FP64: 12 warps per SM) ...
 template <int MAT, typename T, int MODE>
 __global__ void __launch_bounds__(256) k_force_b(const FomB g, const int* __restrict__ active, const TraceFuse tr) {
@@ -621,6 +737,19 @@ cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaSt
     if (g.df32) return launch_force_df_b(g, active, tr, s);
 #define OSAM_LAUNCH(MAT, T, MODE) k_force_b<MAT, T, MODE><<<grid, b, 0, s>>>(g, active, tr)
     const bool fp32 = g.fp32 != 0;
+    if (g.tiled && !fp32) {
+        long long titems = 0;
+        for (int k = 0; k < tr.n; ++k) titems += 3LL * tr.c[k].R;
+        const int tgrid = g.n_tblk + (int)((titems + 127) / 128);
+        if (g.material == OSAM_NEO_HOOKEAN) {
+            if (scatter == kAtomic) k_force_tile_b<OSAM_NEO_HOOKEAN, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
+            else k_force_tile_b<OSAM_NEO_HOOKEAN, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);
+        } else {
+            if (scatter == kAtomic) k_force_tile_b<OSAM_LINEAR_ELASTIC, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
+            else k_force_tile_b<OSAM_LINEAR_ELASTIC, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);
+        }
+        return cudaGetLastError();
+    }
     if (g.occ && !fp32 && scatter == kGather && b <= 128) {
         if (g.material == OSAM_NEO_HOOKEAN) k_force_occ_b<OSAM_NEO_HOOKEAN><<<grid, b, 0, s>>>(g, active, tr);
         else k_force_occ_b<OSAM_LINEAR_ELASTIC><<<grid, b, 0, s>>>(g, active, tr);

@@ -19,7 +19,7 @@ OK, MAXITER, EINVAL, ECFL, ENONFINITE, EDONOR, ECUDA, ETIMEOUT, ENOMEM = 0, 1, -
 FOM, ROM = 0, 1
 LINEAR_ELASTIC, NEO_HOOKEAN = 0, 1
 FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
-SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG = 0, 1, 2, 3
+SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG, SCATTER_GATHER_TILED = 0, 1, 2, 3, 4
 
 EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin_interval", "osam_restore_interval",
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
@@ -132,7 +132,7 @@ def load():
         getattr(L, f).argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
     L.osam_instance_sizes.argtypes = [_vp, C.c_int, C.c_int] + [C.POINTER(C.c_int)] * 4
     L.osam_set_graph.argtypes = [_vp, C.c_int]
-    L.osam_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.osam_tuning.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.osam_hex8_force_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                           _vp, _vp, _vp, _vp, _vp]
     _lib = L
@@ -286,10 +286,10 @@ class Batch:
                      "element_updates": tot.element_updates, "elapsed_ms": tot.elapsed_ms}
 
     def tuning(self):
-        sc, eb, rc = C.c_int(), C.c_int(), C.c_int()
-        self._c(load().osam_tuning(self.h, C.byref(sc), C.byref(eb), C.byref(rc)))
+        sc, eb, rc, tl = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        self._c(load().osam_tuning(self.h, C.byref(sc), C.byref(eb), C.byref(rc), C.byref(tl)))
         return {"scatter": "atomic" if sc.value == SCATTER_ATOMIC else "gather", "element_block": eb.value,
-                "register_cap": rc.value}
+                "register_cap": rc.value, "tiled": bool(tl.value)}
 
     def profile(self, enable=True):
         """Start (and reset) kernel-level accounting of the internal-force launches."""

@@ -168,3 +168,32 @@ def _chain_rom(spec, r, rs, seed):
     sd = spec.subdomains[1]
     n_sdof = 2 * 3 * (sd.dims[0] + 1) ** 2
     return W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, r, rs, seed)
+
+
+@pytest.mark.parametrize("material", ["le", "nh"])
+def test_tiled_force_equals_untiled(gpu, material):
+    """The tiled FP64 force shares the edge interpolation between neighbouring elements with the same
+    per-value arithmetic: states equal the untiled gather path bit for bit (ragged tiles included)."""
+    spec = W.bar_chain("tile", 11, [13, 9], ["fom", "fom"], material, 1e9, 0.3, 1000.0, 2e-3, 1e-6, 5)
+    a = osam.Problem(spec, scatter=osam.SCATTER_GATHER_TILED)
+    b = osam.Problem(spec, scatter=osam.SCATTER_GATHER)
+    assert a.tuning()["tiled"] and not b.tuning()["tiled"]
+    for _ in range(3):
+        ra, rb = a.step(), b.step()
+        assert ra["iterations"] == rb["iterations"] and ra["cnum"] == rb["cnum"]
+    for i in range(2):
+        for f in range(3):
+            assert np.array_equal(a.state(i)[f], b.state(i)[f])
+
+
+def test_tiled_batch_equals_untiled_single_runs(gpu):
+    specs = W.batched_samples(n_samples=4, n_min=3, n_max=9, rom=False)
+    batch = osam.Batch(specs, scatter=osam.SCATTER_GATHER_TILED)
+    singles = [osam.Problem(s, scatter=osam.SCATTER_GATHER) for s in specs]
+    for _ in range(2):
+        per, _ = batch.step()
+        reps = [p.step() for p in singles]
+        assert [p["iterations"] for p in per] == [r["iterations"] for r in reps]
+    for n, p in enumerate(singles):
+        for i in range(2):
+            assert np.array_equal(batch.state(i, inst=n)[0], p.state(i)[0])

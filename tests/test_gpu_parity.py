@@ -128,7 +128,8 @@ def test_autograd_function_matches_oracle_vjp(torch_cuda):
 # ---------------------------------------------------------------------------------------------
 # coupled problems
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("scatter", [osam.SCATTER_GATHER, osam.SCATTER_ATOMIC, osam.SCATTER_GATHER_LOWREG])
+@pytest.mark.parametrize("scatter", [osam.SCATTER_GATHER, osam.SCATTER_ATOMIC, osam.SCATTER_GATHER_LOWREG,
+                                     osam.SCATTER_GATHER_TILED])
 def test_fom_fom_plain_config_matches_oracle(torch_cuda, scatter):
     """Two 6x6x12 linear-elastic FOMs, 10 controller steps of 20 (the whole 200-step run)."""
     spec = W.fom_fom_plain()
@@ -140,7 +141,7 @@ def test_fom_fom_plain_config_matches_oracle(torch_cuda, scatter):
     assert all(abs(a - b) <= 1 for a, b in its)
 
 
-@pytest.mark.parametrize("scatter", [osam.SCATTER_AUTO, osam.SCATTER_GATHER_LOWREG])
+@pytest.mark.parametrize("scatter", [osam.SCATTER_AUTO, osam.SCATTER_GATHER_LOWREG, osam.SCATTER_GATHER_TILED])
 def test_neo_hookean_fom_fom_odd_substeps(torch_cuda, scatter):
     """Neo-Hookean, unequal subdomain lengths, odd substep count (state ping-pong ends on buffer 1)."""
     spec = W.bar_chain("nh_odd", 5, [9, 7], ["fom", "fom"], "nh", 1e9, 0.3, 1000.0, 2e-3, 1e-6, 7)
