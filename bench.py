@@ -52,8 +52,9 @@ FP64_PEAK_TFLOPS = 1.25
 F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
-# valid only for the kernel source it was captured on; None until captured.
-FORCE_TRAFFIC = {"source_sha256": "15d6d06291cdefe63bce82ca63ee6cb23a6c7b6716345637321627f7b7acbd3e", "bytes_per_launch": 3.659e6}
+# valid only for the kernel source and variant (tiled or not) it was captured on.
+FORCE_TRAFFIC = {"source_sha256": "7b75524b888890d04e6831c55ebaea5cea934da54f34e6f946ab80b46e453866", "bytes_per_launch": 3.573e6,
+                 "tiled": True}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -82,6 +83,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"],
                     help="f64: native FP64 force; f32x2: double-float force on the FP32 pipes (FP64 state)")
+    ap.add_argument("--scatter", default="auto", choices=["auto", "gather", "atomic", "tiled", "lowreg"],
+                    help="force-kernel configuration (auto: the library's autotuner); fixed choices make ncu "
+                         "captures reproducible")
     ap.add_argument("--batched-samples", type=int, default=256)
     ap.add_argument("--batched-snapshots", type=int, default=100)
     ap.add_argument("--batched-steps", type=int, default=5)
@@ -523,7 +527,9 @@ def main():
     results = {}
     for prec in ([head_prec] + [p for p in (osam.FP64, osam.F32X2_FORCE) if p != head_prec]):
         name = "f32x2" if prec == osam.F32X2_FORCE else "f64"
-        prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=prec)
+        scatter = {"auto": osam.SCATTER_AUTO, "gather": osam.SCATTER_GATHER, "atomic": osam.SCATTER_ATOMIC,
+                   "tiled": osam.SCATTER_GATHER_TILED, "lowreg": osam.SCATTER_GATHER_LOWREG}[args.scatter]
+        prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=prec, scatter=scatter)
         log(f"[{name}] tuning: {prob.tuning()}")
         for _ in range(args.warmup):
             r = prob.step()
@@ -558,7 +564,9 @@ def main():
         per_launch = prof["force_ms"] / max(1, prof["force_launches"])
         if prec_name == "f64":
             achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
-            traffic = FORCE_TRAFFIC["bytes_per_launch"] if FORCE_TRAFFIC["source_sha256"] == source_sha() else None
+            same = (FORCE_TRAFFIC["source_sha256"] == source_sha()
+                    and FORCE_TRAFFIC["tiled"] == bool(res["tuning"].get("tiled")))
+            traffic = FORCE_TRAFFIC["bytes_per_launch"] if same else None
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                     "kernel": ("k_force_tile_b<NeoHookean, gather>" if res["tuning"].get("tiled")
