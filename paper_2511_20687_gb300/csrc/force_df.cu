@@ -3,6 +3,7 @@
 // sum-factorised formulation as the FP64 kernel (hex8_math.cuh).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "df32.cuh"
@@ -351,8 +352,13 @@ cudaError_t launch_force_df_b(const FomB& g, const int* active, const TraceFuse&
     for (int k = 0; k < tr.n; ++k) items += 3LL * tr.c[k].R;
     const int grid = g.n_eblk + (int)((items + b - 1) / b);
     const size_t smem = sizeof(float2) * kDfSlots * b;
-    static bool attr_set = false;  // opt in to more than 48 KB of dynamic shared memory, once
-    if (!attr_set) {
+    // opt in to more than 48 KB of dynamic shared memory, once per device (the attribute is per device)
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
         const int max_bytes = (int)(sizeof(float2) * kDfSlots * 128);
         cudaError_t e1 = cudaFuncSetAttribute(k_force_df2_b<OSAM_NEO_HOOKEAN>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
@@ -360,7 +366,7 @@ cudaError_t launch_force_df_b(const FomB& g, const int* active, const TraceFuse&
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         if (e1 != cudaSuccess) return e1;
         if (e2 != cudaSuccess) return e2;
-        attr_set = true;
+        attr_set.fetch_or(bit);
     }
     if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<grid, b, smem, s>>>(g, active, tr);
     else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<grid, b, smem, s>>>(g, active, tr);
