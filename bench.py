@@ -53,7 +53,6 @@ FP64_PEAK_TFLOPS = 1.25
 # x 32 / elements of the phased kernel) and the FP32 issue peak (152 SMs x 128 lanes x 2.07 GHz)
 F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 2 * FP32_ISSUE_PEAK_TINST
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
 FORCE_TRAFFIC = {"source_sha256": "7b75524b888890d04e6831c55ebaea5cea934da54f34e6f946ab80b46e453866", "bytes_per_launch": 3.573e6,
@@ -527,10 +526,9 @@ def main():
         spec = hybrid_spec(W, args)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     head_prec = osam.F32X2_FORCE if args.precision == "f32x2" else osam.FP64
-    names = {osam.FP64: "f64", osam.F32X2_FORCE: "f32x2", osam.FP32_FORCE: "fp32_force"}
     results = {}
-    for prec in ([head_prec] + [p for p in (osam.FP64, osam.F32X2_FORCE, osam.FP32_FORCE) if p != head_prec]):
-        name = names[prec]
+    for prec in ([head_prec] + [p for p in (osam.FP64, osam.F32X2_FORCE) if p != head_prec]):
+        name = "f32x2" if prec == osam.F32X2_FORCE else "f64"
         scatter = {"auto": osam.SCATTER_AUTO, "gather": osam.SCATTER_GATHER, "atomic": osam.SCATTER_ATOMIC,
                    "tiled": osam.SCATTER_GATHER_TILED, "lowreg": osam.SCATTER_GATHER_LOWREG}[args.scatter]
         prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=prec, scatter=scatter)
@@ -585,14 +583,6 @@ def main():
                     "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)", "fp64_fma_measured_tflops": fp64_meas,
                     "frac_of_measured_fp64": achieved / fp64_meas, "force_ms_per_launch": per_launch,
                     "force_time_share": prof["force_ms"] / res["prof_total_ms"]}
-        if prec_name == "fp32_force":
-            # FP32 force (checked to 1e-5): the same 1232 algorithmic flops per element in FP32
-            achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
-            return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                    "kernel": "k_force_b<NeoHookean, f32, %s>" % res["tuning"]["scatter"],
-                    "peak_kind": "152 SMs x 128 FFMA x 2 flops x 2.07 GHz", "force_ms_per_launch": per_launch,
-                    "force_time_share": prof["force_ms"] / res["prof_total_ms"]}
         # double-float force: FP32-pipe instruction issue is the binding unit
         achieved = F32X2_INST_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": FP32_ISSUE_PEAK_TINST, "unit": "Tinst/s (FP32 pipe)",
@@ -628,8 +618,7 @@ def main():
                               "value_host_loop": res["host_value"], "ms_per_step_host_loop": res["host_ms_per_step"],
                               "e2e": res["e2e"]["value"] if res["e2e"] else None, "tuning": res["tuning"],
                               "roofline": roofline(res, name),
-                              "parity": ("1e-5" if name == "fp32_force" else "1e-9")
-                                        + " relative L2 vs the FP64 oracle (tests/test_gpu_parity.py)"}
+                              "parity": "1e-9 relative L2 vs the FP64 oracle (tests/test_gpu_parity.py)"}
         clk = head["clk"] or {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
         # HBM: the explicit state the method must move per node update (u, v read + write, a read +
         # write, lumped mass read: 96 + 48 + 8 B), times nodes per element of the FOM mesh
