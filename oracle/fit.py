@@ -93,3 +93,58 @@ def opinf_fit(U: np.ndarray, A: np.ndarray, S: np.ndarray, r: int, lam: float, r
 
 def rom_rhs(K, H, B, c, q, ghat):
     return K @ q + H @ kron_c(q[:, None])[:, 0] + B @ ghat + c
+
+
+# ---------------------------------------------------------------------------------------------
+# Schwarz-aware regularisation selection (Sec. 4.2.4, Algorithm 3, Eq. schwarz_regularization_error)
+# ---------------------------------------------------------------------------------------------
+def lambda_grid(n: int = 11, lo: float = 1e-10, hi: float = 1.0) -> np.ndarray:
+    """Logarithmically spaced candidates lo .. hi (the paper's grid: 11 values from 1e-10 to 1)."""
+    return np.logspace(np.log10(lo), np.log10(hi), n)
+
+
+def rollout_frozen(K, H, B, c, q0, qd0, qdd0, Ghat, dt, k):
+    """Advance the ROM alone with its Schwarz boundary data frozen to the training columns.
+
+    Explicit central differences (Newmark beta = 0, gamma = 1/2) with step dt; the snapshot columns
+    are k steps apart, and within an interval the boundary vector is the linear interpolant in time of
+    the two columns (k = 1: the stored column of the new time level, as the paper prescribes).
+    Returns the reduced displacements at the snapshot times (r x n_snap)."""
+    q, qd, qdd = q0.astype(np.float64).copy(), qd0.astype(np.float64).copy(), qdd0.astype(np.float64).copy()
+    n = Ghat.shape[1]
+    Q = np.empty((q.shape[0], n))
+    Q[:, 0] = q
+    with np.errstate(all="ignore"):
+        for j in range(n - 1):
+            for s in range(1, k + 1):
+                g = Ghat[:, j] + (s / k) * (Ghat[:, j + 1] - Ghat[:, j])
+                q = q + dt * qd + 0.5 * dt * dt * qdd
+                qdd_new = rom_rhs(K, H, B, c, q, g)
+                qd = qd + 0.5 * dt * (qdd + qdd_new)
+                qdd = qdd_new
+            Q[:, j + 1] = q
+    return Q
+
+
+def select_lambda(U, A, S, v0, r, lambdas, dt, k, r_s=None, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True):
+    """Algorithm 3: for every candidate lambda fit the operators (Eq. opinf_schwarz_inference), roll
+    the ROM out from the training initial state (q0 = Phi^T u_0, qd0 = Phi^T v_0, qdd0 = Phi^T a_0)
+    under the frozen training boundary data, score E(lambda) = ||Q - Ubar||_F / ||Ubar||_F (a
+    non-finite rollout scores +inf), and return (errors, index of the minimum, operators refitted at
+    the selected lambda)."""
+    errors = []
+    for lam in lambdas:
+        ops = opinf_fit(U, A, S, r, lam, r_s, energy_s, r_s_max, quadratic)
+        Phi, PhiS = ops["Phi"], ops["Phi_S"]
+        Ubar = Phi.T @ U
+        Q = rollout_frozen(ops["K"], ops["H"], ops["B"], ops["c"], Ubar[:, 0], Phi.T @ v0, Phi.T @ A[:, 0],
+                           PhiS.T @ S, dt, k)
+        if np.all(np.isfinite(Q)):
+            errors.append(float(np.linalg.norm(Q - Ubar) / np.linalg.norm(Ubar)))
+        else:
+            errors.append(np.inf)
+        if r_s is None:
+            r_s = ops["r_s"]   # the boundary basis does not depend on lambda
+    errors = np.array(errors)
+    best = int(np.argmin(errors))
+    return errors, best, opinf_fit(U, A, S, r, float(lambdas[best]), r_s, energy_s, r_s_max, quadratic)

@@ -140,3 +140,82 @@ def test_rollout_adjoint_matches_central_differences(oracle, small_adjoint_case)
     hm = 1e-6 * sd.mu
     fdm = (Jof(me=sd.mu_e + hm * dl) - Jof(me=sd.mu_e - hm * dl)) / (2 * hm)
     assert abs(fdm - gm @ dl) < 1e-6 * abs(fdm)
+
+
+# ---------------------------------------------------------------------------------------------
+# regularisation selection (Algorithm 3)
+# ---------------------------------------------------------------------------------------------
+def _known_quadratic_trajectory(n=5, n_g=2, steps=400, dt=0.02, seed=3, k=1):
+    """Trajectory of q'' = K q + H kron_c(q) + B g(t) + c by explicit central differences with step dt,
+    recorded every k steps; g(t) smooth.  Returns snapshots (U, A, S, v0) and the step."""
+    rng = np.random.default_rng(seed)
+    K = -np.diag(rng.uniform(1.0, 4.0, n) ** 2)
+    H = 0.05 * rng.standard_normal((n, n * (n + 1) // 2))
+    B = rng.standard_normal((n, n_g))
+    c = 0.1 * rng.standard_normal(n)
+    g = lambda t: np.array([np.sin(1.3 * t), np.cos(0.7 * t)])[:n_g]
+    q = 0.1 * rng.standard_normal(n)
+    qd = 0.1 * rng.standard_normal(n)
+    qdd = OF.rom_rhs(K, H, B, c, q, g(0.0))
+    U, A, S, V = [q.copy()], [qdd.copy()], [g(0.0)], [qd.copy()]
+    t = 0.0
+    for j in range(steps):
+        for _ in range(k):
+            t += dt
+            q = q + dt * qd + 0.5 * dt * dt * qdd
+            qn = OF.rom_rhs(K, H, B, c, q, g(t))
+            qd = qd + 0.5 * dt * (qdd + qn)
+            qdd = qn
+        U.append(q.copy()); A.append(qdd.copy()); S.append(g(t)); V.append(qd.copy())
+    return np.array(U).T, np.array(A).T, np.array(S).T, np.array(V)[0]
+
+
+def test_selection_recovers_the_generating_model():
+    """Noise-free data of a known quadratic model: small lambdas reproduce the trajectory, the largest
+    ones do not, and the selected lambda is one of the small ones."""
+    U, A, S, v0 = _known_quadratic_trajectory()
+    lams = OF.lambda_grid()
+    assert lams[0] == pytest.approx(1e-10) and lams[-1] == pytest.approx(1.0) and len(lams) == 11
+    errs, best, ops = OF.select_lambda(U, A, S, v0, r=5, lambdas=lams, dt=0.02, k=1, r_s=2)
+    assert errs[0] < 1e-6 and errs[best] < 1e-6
+    assert errs[-1] > 1e-3
+    assert lams[best] <= 1e-4
+
+
+def test_selection_rollout_interpolates_the_boundary_between_snapshots():
+    """Snapshots every 3 steps with a boundary input that is linear in time: the interpolated frozen
+    boundary is exact, so the rollout of the generating operators reproduces the recorded states."""
+    n, dt, k = 4, 0.01, 3
+    rng = np.random.default_rng(5)
+    K = -np.diag(rng.uniform(1.0, 3.0, n) ** 2)
+    H = 0.02 * rng.standard_normal((n, n * (n + 1) // 2))
+    B = rng.standard_normal((n, 1))
+    c = np.zeros(n)
+    q0, qd0 = 0.1 * rng.standard_normal(n), 0.1 * rng.standard_normal(n)
+    g = lambda t: np.array([0.5 - 2.0 * t])
+    # reference: every step with the exact boundary, recorded every k steps
+    q, qd = q0.copy(), qd0.copy()
+    qdd = OF.rom_rhs(K, H, B, c, q, g(0.0))
+    Qref, G = [q.copy()], [g(0.0)]
+    t = 0.0
+    for j in range(60):
+        for _ in range(k):
+            t += dt
+            q = q + dt * qd + 0.5 * dt * dt * qdd
+            qn = OF.rom_rhs(K, H, B, c, q, g(t))
+            qd = qd + 0.5 * dt * (qdd + qn)
+            qdd = qn
+        Qref.append(q.copy()); G.append(g(t))
+    Qref, G = np.array(Qref).T, np.array(G).T
+    Q = OF.rollout_frozen(K, H, B, c, q0, qd0, OF.rom_rhs(K, H, B, c, q0, g(0.0)), G, dt, k)
+    assert np.abs(Q - Qref).max() < 1e-12 * np.abs(Qref).max()
+
+
+def test_selection_penalises_a_non_finite_rollout():
+    """A candidate whose rollout overflows scores +inf and is never selected."""
+    n = 3
+    K = np.diag([50.0, 1.0, -1.0]) ** 2  # one exponentially growing mode
+    H = np.zeros((n, n * (n + 1) // 2)); B = np.zeros((n, 1)); c = np.zeros(n)
+    G = np.zeros((1, 2000))
+    Q = OF.rollout_frozen(K, H, B, c, np.ones(n), np.zeros(n), np.zeros(n), G, 1.0, 1)
+    assert not np.all(np.isfinite(Q))
