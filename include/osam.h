@@ -294,7 +294,26 @@ typedef struct {
 } osam_fit_output;
 
 OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out);
-/* Message of the calling thread's last failed opinf_fit. */
+
+/* Schwarz-aware regularisation selection (Sec. 4.2.4, Algorithm 3): for every candidate lambda the
+ * operators are fitted as by opinf_fit (in->lambda is ignored) and the ROM is advanced alone from
+ * the training initial state (q0 = Phi^T u_0, qd0 = Phi^T v_0, qdd0 = Phi^T a_0, u_0 and a_0 the first
+ * rows of U and A) by explicit central differences with step dt, its Schwarz boundary data frozen to
+ * the training columns Ghat = Phi_S^T S; consecutive snapshot rows are `substeps` steps apart and the
+ * boundary vector is interpolated linearly in time between them (substeps = 1: the stored column of
+ * the new time level).  errors[l] = ||Q_l - Ubar||_F / ||Ubar||_F over the snapshot times
+ * (Eq. schwarz_regularization_error), HUGE_VAL for a non-finite rollout; *best = the minimiser, whose
+ * operators are written to out.  OSAM_ENONFINITE if every rollout is non-finite.  r <= 128. */
+typedef struct {
+    const double* lambdas;    /* [n_lambda] candidates (>= 0), e.g. 11 log-spaced values 1e-10 .. 1 */
+    int n_lambda;             /* 1 .. 64 */
+    const double* v0;         /* [n_dof] velocity of the first snapshot on the free dofs, or NULL (zero) */
+    double dt;                /* rollout step (the ROM's online step) */
+    int substeps;             /* steps between consecutive snapshot rows (>= 1) */
+} osam_select_input;
+OSAM_API int opinf_select(const osam_fit_input* in, const osam_select_input* sel, double* errors, int* best,
+                          osam_fit_output* out);
+/* Message of the calling thread's last failed opinf_fit / opinf_select. */
 OSAM_API const char* osam_fit_last_error(void);
 
 /* ------------------------------------------------------------------------------------------------

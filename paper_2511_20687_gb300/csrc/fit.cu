@@ -9,6 +9,10 @@
 //   dual form O = D^T (D D^T + lambda I)^-1 Y when D has more columns than rows, else the primal
 //   normal equations (D^T D + lambda I) O = D^T Y; the small SPD systems are factored by Cholesky
 //   on the host.
+// opinf_select: Schwarz-aware regularisation selection (Sec. 4.2.4, Algorithm 3): the lambda-
+//   independent part once, one Tikhonov solve per candidate, every candidate ROM rolled out on the
+//   device under the frozen training boundary data (k_select_rollout, rom_kernels.cu), the minimiser
+//   of Eq. schwarz_regularization_error returned with its operators.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -269,51 +273,54 @@ int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, doub
     return OSAM_OK;
 }
 
-}  // namespace
+// The lambda-independent part of the fit: bases, projections, the data matrix and the Gram matrix of
+// the regression (dual D D^T or primal D^T D, without lambda).
+struct FitData {
+    int ns = 0, n = 0, nsd = 0, r = 0, rs = 0, nq = 0, d = 0;
+    bool dual = false;
+    double* Phi = nullptr;    // device [n][r]
+    double* PhiS = nullptr;   // device [nsd][rs]
+    double* D = nullptr;      // device [ns][d] = [Ubar^T | kron_c(Ubar)^T | Ghat^T | 1]
+    double* Y = nullptr;      // device [ns][r] = Abar^T
+    std::vector<double> Yh;   // host Abar^T
+    std::vector<double> M0;   // host Gram without lambda: [ns][ns] (dual) or [d][d] (primal)
+    std::vector<double> R0;   // host D^T Y [d][r] (primal)
+    std::vector<double> sigma, sigma_s;
+};
 
-extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out) {
-    g_fit_error.clear();
-    if (!in || !out || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
-        in->lambda < 0.0 || (in->n_sdof > 0 && !in->S))
-        return OSAM_EINVAL;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { g_fit_error = "no CUDA device"; return OSAM_ECUDA; }
-    FK(cudaSetDevice(in->device));
-    cudaStream_t s = static_cast<cudaStream_t>(in->stream);
-    Dev dev;
+int fit_prepare(const osam_fit_input* in, cudaStream_t s, Dev& dev, FitData& F) {
     const int ns = in->n_snap, n = in->n_dof, nsd = in->n_sdof, r = in->r;
+    F.ns = ns; F.n = n; F.nsd = nsd; F.r = r;
     double* U = dev.alloc((size_t)ns * n);
     double* A = dev.alloc((size_t)ns * n);
     FA(U); FA(A);
     FK(cudaMemcpyAsync(U, in->U, sizeof(double) * ns * n, cudaMemcpyDefault, s));
     FK(cudaMemcpyAsync(A, in->A, sizeof(double) * ns * n, cudaMemcpyDefault, s));
-    double* Phi = nullptr;
-    std::vector<double> sigma, sigma_s;
     int r_used = 0;
-    if (int rc = pod(s, dev, U, ns, n, r, 0.0, 0, &r_used, &Phi, sigma)) return rc;
+    if (int rc = pod(s, dev, U, ns, n, r, 0.0, 0, &r_used, &F.Phi, F.sigma)) return rc;
     // boundary basis
-    int rs = 0;
-    double* PhiS = nullptr;
     double* S = nullptr;
     if (nsd > 0) {
         S = dev.alloc((size_t)ns * nsd);
         FA(S);
         FK(cudaMemcpyAsync(S, in->S, sizeof(double) * ns * nsd, cudaMemcpyDefault, s));
         const int rs_cap = std::min(in->r_s_max > 0 ? in->r_s_max : ns, ns);
-        if (int rc = pod(s, dev, S, ns, nsd, in->r_s > 0 ? std::min(in->r_s, ns) : 0, in->energy_s, rs_cap, &rs,
-                         &PhiS, sigma_s))
+        if (int rc = pod(s, dev, S, ns, nsd, in->r_s > 0 ? std::min(in->r_s, ns) : 0, in->energy_s, rs_cap, &F.rs,
+                         &F.PhiS, F.sigma_s))
             return rc;
     }
+    const int rs = F.rs;
     const int nq = in->quadratic ? r * (r + 1) / 2 : 0;
     const int d = r + nq + rs + 1;
+    F.nq = nq; F.d = d;
     // D [ns][d]
     double* D = dev.alloc((size_t)ns * d);
     double* Ubt = dev.alloc((size_t)ns * r);   // Ubar^T [ns][r]
     double* Ub = dev.alloc((size_t)r * ns);    // Ubar [r][ns]
     double* Y = dev.alloc((size_t)ns * r);     // Abar^T
     FA(D); FA(Ubt); FA(Ub); FA(Y);
-    FK(launch_gemm_nn(ns, r, n, U, n, Phi, r, Ubt, r, 1.0, 0.0, s));
-    FK(launch_gemm_nn(ns, r, n, A, n, Phi, r, Y, r, 1.0, 0.0, s));
+    FK(launch_gemm_nn(ns, r, n, U, n, F.Phi, r, Ubt, r, 1.0, 0.0, s));
+    FK(launch_gemm_nn(ns, r, n, A, n, F.Phi, r, Y, r, 1.0, 0.0, s));
     std::vector<double> Ubt_h((size_t)ns * r), Ub_h((size_t)r * ns);
     FK(cudaMemcpyAsync(Ubt_h.data(), Ubt, sizeof(double) * Ubt_h.size(), cudaMemcpyDeviceToHost, s));
     FK(cudaStreamSynchronize(s));
@@ -324,7 +331,7 @@ extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out
     // linear block and constant on the host (small); Kronecker block and boundary block on the device
     FK(cudaMemsetAsync(D, 0, sizeof(double) * ns * d, s));
     if (nq) FK(launch_kron_features(Ub, r, ns, D, d, r, s));
-    if (rs) FK(launch_gemm_nn(ns, rs, nsd, S, nsd, PhiS, rs, D + r + nq, d, 1.0, 0.0, s));
+    if (rs) FK(launch_gemm_nn(ns, rs, nsd, S, nsd, F.PhiS, rs, D + r + nq, d, 1.0, 0.0, s));
     FK(cudaMemcpyAsync(Dh.data(), D, sizeof(double) * Dh.size(), cudaMemcpyDeviceToHost, s));
     FK(cudaStreamSynchronize(s));
     for (int i = 0; i < ns; ++i) {
@@ -332,49 +339,69 @@ extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out
         Dh[(size_t)i * d + d - 1] = 1.0;
     }
     FK(cudaMemcpyAsync(D, Dh.data(), sizeof(double) * Dh.size(), cudaMemcpyHostToDevice, s));
-    std::vector<double> Yh((size_t)ns * r);
-    FK(cudaMemcpyAsync(Yh.data(), Y, sizeof(double) * Yh.size(), cudaMemcpyDeviceToHost, s));
+    F.Yh.resize((size_t)ns * r);
+    FK(cudaMemcpyAsync(F.Yh.data(), Y, sizeof(double) * F.Yh.size(), cudaMemcpyDeviceToHost, s));
     FK(cudaStreamSynchronize(s));
-    std::vector<double> Oh((size_t)d * r);  // O [d][r]
-    if (d > ns) {
-        // dual: (D D^T + lambda I) Z = Y, O = D^T Z
+    F.D = D;
+    F.Y = Y;
+    F.dual = d > ns;
+    if (F.dual) {
         double* M = dev.alloc((size_t)ns * ns);
         FA(M);
         FK(launch_gemm_nt(ns, ns, d, D, d, D, d, M, ns, 1.0, 0.0, s));
-        std::vector<double> Mh((size_t)ns * ns);
-        FK(cudaMemcpyAsync(Mh.data(), M, sizeof(double) * Mh.size(), cudaMemcpyDeviceToHost, s));
+        F.M0.resize((size_t)ns * ns);
+        FK(cudaMemcpyAsync(F.M0.data(), M, sizeof(double) * F.M0.size(), cudaMemcpyDeviceToHost, s));
         FK(cudaStreamSynchronize(s));
-        for (int i = 0; i < ns; ++i) {
-            for (int j = i + 1; j < ns; ++j) Mh[(size_t)j * ns + i] = Mh[(size_t)i * ns + j];
-            Mh[(size_t)i * ns + i] += in->lambda;
-        }
-        if (!cholesky(Mh, ns)) { g_fit_error = "regularised dual system is not positive definite"; return OSAM_EINVAL; }
-        chol_solve(Mh, ns, Yh, r);
-        double* Z = dev.alloc((size_t)ns * r);
-        double* Od = dev.alloc((size_t)d * r);
-        FA(Z); FA(Od);
-        FK(cudaMemcpyAsync(Z, Yh.data(), sizeof(double) * Yh.size(), cudaMemcpyHostToDevice, s));
-        FK(launch_gemm_tn(d, r, ns, D, d, Z, r, Od, r, 1.0, 0.0, s));
-        FK(cudaMemcpyAsync(Oh.data(), Od, sizeof(double) * Oh.size(), cudaMemcpyDeviceToHost, s));
-        FK(cudaStreamSynchronize(s));
+        for (int i = 0; i < ns; ++i)
+            for (int j = i + 1; j < ns; ++j) F.M0[(size_t)j * ns + i] = F.M0[(size_t)i * ns + j];
     } else {
         double* M = dev.alloc((size_t)d * d);
         double* R = dev.alloc((size_t)d * r);
         FA(M); FA(R);
         FK(launch_gemm_tn(d, d, ns, D, d, D, d, M, d, 1.0, 0.0, s));
         FK(launch_gemm_tn(d, r, ns, D, d, Y, r, R, r, 1.0, 0.0, s));
-        std::vector<double> Mh((size_t)d * d);
-        FK(cudaMemcpyAsync(Mh.data(), M, sizeof(double) * Mh.size(), cudaMemcpyDeviceToHost, s));
-        FK(cudaMemcpyAsync(Oh.data(), R, sizeof(double) * Oh.size(), cudaMemcpyDeviceToHost, s));
+        F.M0.resize((size_t)d * d);
+        F.R0.resize((size_t)d * r);
+        FK(cudaMemcpyAsync(F.M0.data(), M, sizeof(double) * F.M0.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaMemcpyAsync(F.R0.data(), R, sizeof(double) * F.R0.size(), cudaMemcpyDeviceToHost, s));
         FK(cudaStreamSynchronize(s));
-        for (int i = 0; i < d; ++i) {
-            for (int j = i + 1; j < d; ++j) Mh[(size_t)j * d + i] = Mh[(size_t)i * d + j];
-            Mh[(size_t)i * d + i] += in->lambda;
-        }
+        for (int i = 0; i < d; ++i)
+            for (int j = i + 1; j < d; ++j) F.M0[(size_t)j * d + i] = F.M0[(size_t)i * d + j];
+    }
+    return OSAM_OK;
+}
+
+// Tikhonov solution for one lambda: O [d][r] (host)
+int fit_solve(const FitData& F, double lambda, cudaStream_t s, Dev& dev, std::vector<double>& Oh) {
+    const int ns = F.ns, d = F.d, r = F.r;
+    Oh.assign((size_t)d * r, 0.0);
+    if (F.dual) {
+        // (D D^T + lambda I) Z = Y, O = D^T Z
+        std::vector<double> Mh = F.M0, Zh = F.Yh;
+        for (int i = 0; i < ns; ++i) Mh[(size_t)i * ns + i] += lambda;
+        if (!cholesky(Mh, ns)) { g_fit_error = "regularised dual system is not positive definite"; return OSAM_EINVAL; }
+        chol_solve(Mh, ns, Zh, r);
+        double* Z = dev.alloc((size_t)ns * r);
+        double* Od = dev.alloc((size_t)d * r);
+        FA(Z); FA(Od);
+        FK(cudaMemcpyAsync(Z, Zh.data(), sizeof(double) * Zh.size(), cudaMemcpyHostToDevice, s));
+        FK(launch_gemm_tn(d, r, ns, F.D, d, Z, r, Od, r, 1.0, 0.0, s));
+        FK(cudaMemcpyAsync(Oh.data(), Od, sizeof(double) * Oh.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaStreamSynchronize(s));
+    } else {
+        std::vector<double> Mh = F.M0;
+        Oh = F.R0;
+        for (int i = 0; i < d; ++i) Mh[(size_t)i * d + i] += lambda;
         if (!cholesky(Mh, d)) { g_fit_error = "regularised normal equations are not positive definite"; return OSAM_EINVAL; }
         chol_solve(Mh, d, Oh, r);
     }
-    // unpack O [d][r] -> K [r][r], H [r][nq_full], B [r][r_s_max], c [r]
+    return OSAM_OK;
+}
+
+// write the operators of O [d][r] and the bases to the caller's output
+int fit_output(const osam_fit_input* in, const FitData& F, const std::vector<double>& Oh, cudaStream_t s,
+               osam_fit_output* out) {
+    const int r = F.r, nq = F.nq, rs = F.rs, d = F.d, nsd = F.nsd, ns = F.ns;
     const int nq_full = r * (r + 1) / 2;
     const int rs_cols = std::max(in->r_s_max, rs);
     std::vector<double> K((size_t)r * r), H((size_t)r * nq_full, 0.0), B((size_t)r * std::max(1, rs_cols), 0.0), c(r);
@@ -388,21 +415,111 @@ extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out
     if (out->H) FK(cudaMemcpyAsync(out->H, H.data(), sizeof(double) * H.size(), cudaMemcpyDefault, s));
     if (out->B && rs_cols > 0) FK(cudaMemcpyAsync(out->B, B.data(), sizeof(double) * (size_t)r * rs_cols, cudaMemcpyDefault, s));
     if (out->c) FK(cudaMemcpyAsync(out->c, c.data(), sizeof(double) * r, cudaMemcpyDefault, s));
-    if (out->Phi) FK(cudaMemcpyAsync(out->Phi, Phi, sizeof(double) * (size_t)n * r, cudaMemcpyDefault, s));
+    if (out->Phi) FK(cudaMemcpyAsync(out->Phi, F.Phi, sizeof(double) * (size_t)F.n * r, cudaMemcpyDefault, s));
     if (out->Phi_S && rs > 0) {
         // [nsd][rs] -> [nsd][rs_cols]
         std::vector<double> P((size_t)nsd * rs), Pw((size_t)nsd * rs_cols, 0.0);
-        FK(cudaMemcpyAsync(P.data(), PhiS, sizeof(double) * P.size(), cudaMemcpyDeviceToHost, s));
+        FK(cudaMemcpyAsync(P.data(), F.PhiS, sizeof(double) * P.size(), cudaMemcpyDeviceToHost, s));
         FK(cudaStreamSynchronize(s));
         for (int m = 0; m < nsd; ++m)
             for (int k = 0; k < rs; ++k) Pw[(size_t)m * rs_cols + k] = P[(size_t)m * rs + k];
         FK(cudaMemcpyAsync(out->Phi_S, Pw.data(), sizeof(double) * Pw.size(), cudaMemcpyDefault, s));
     }
-    if (out->sigma) FK(cudaMemcpyAsync(out->sigma, sigma.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
-    if (out->sigma_s && !sigma_s.empty()) FK(cudaMemcpyAsync(out->sigma_s, sigma_s.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
+    if (out->sigma) FK(cudaMemcpyAsync(out->sigma, F.sigma.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
+    if (out->sigma_s && !F.sigma_s.empty())
+        FK(cudaMemcpyAsync(out->sigma_s, F.sigma_s.data(), sizeof(double) * ns, cudaMemcpyDefault, s));
     FK(cudaStreamSynchronize(s));
     out->r_s = rs;
     return OSAM_OK;
+}
+
+int fit_check(const osam_fit_input* in) {
+    if (!in || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
+        (in->n_sdof > 0 && !in->S))
+        return OSAM_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { g_fit_error = "no CUDA device"; return OSAM_ECUDA; }
+    FK(cudaSetDevice(in->device));
+    return OSAM_OK;
+}
+
+}  // namespace
+
+extern "C" OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out) {
+    g_fit_error.clear();
+    if (!out || !in || in->lambda < 0.0) return OSAM_EINVAL;
+    if (int rc = fit_check(in)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(in->stream);
+    Dev dev;
+    FitData F;
+    if (int rc = fit_prepare(in, s, dev, F)) return rc;
+    std::vector<double> Oh;
+    if (int rc = fit_solve(F, in->lambda, s, dev, Oh)) return rc;
+    return fit_output(in, F, Oh, s, out);
+}
+
+extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select_input* sel, double* errors,
+                                     int* best, osam_fit_output* out) {
+    g_fit_error.clear();
+    if (!out || !in || !sel || !sel->lambdas || sel->n_lambda < 1 || sel->n_lambda > 64 || !(sel->dt > 0.0) ||
+        sel->substeps < 1 || !errors || !best)
+        return OSAM_EINVAL;
+    for (int l = 0; l < sel->n_lambda; ++l)
+        if (!(sel->lambdas[l] >= 0.0)) return OSAM_EINVAL;
+    if (in->r > 128) { g_fit_error = "regularisation selection supports r <= 128"; return OSAM_EINVAL; }
+    if (int rc = fit_check(in)) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(in->stream);
+    Dev dev;
+    FitData F;
+    if (int rc = fit_prepare(in, s, dev, F)) return rc;
+    const int nl = sel->n_lambda, r = F.r, d = F.d;
+    // packed operator rows [nl][r][d] (K | H | B | c), one fit per candidate
+    std::vector<double> Op((size_t)nl * r * d);
+    std::vector<std::vector<double>> Os(nl);
+    for (int l = 0; l < nl; ++l) {
+        if (int rc = fit_solve(F, sel->lambdas[l], s, dev, Os[l])) return rc;
+        for (int i = 0; i < r; ++i)
+            for (int k = 0; k < d; ++k) Op[((size_t)l * r + i) * d + k] = Os[l][(size_t)k * r + i];
+    }
+    std::vector<short2> kij;
+    for (int i = 0; i < r; ++i)
+        for (int j = i; j < r; ++j) kij.push_back(make_short2((short)i, (short)j));
+    double* Od = dev.alloc(Op.size());
+    double* qd0 = dev.alloc(r);
+    double* v0 = dev.alloc(F.n);
+    double* phi = dev.alloc((size_t)nl * d);
+    double* num = dev.alloc(nl);
+    double* den = dev.alloc(nl);
+    FA(Od); FA(qd0); FA(v0); FA(phi); FA(num); FA(den);
+    short2* kd = nullptr;
+    if (!kij.empty()) {
+        if (cudaMalloc(&kd, sizeof(short2) * kij.size()) != cudaSuccess) { g_fit_error = "device allocation failed"; return OSAM_ENOMEM; }
+        dev.ptrs.push_back(kd);
+        FK(cudaMemcpyAsync(kd, kij.data(), sizeof(short2) * kij.size(), cudaMemcpyHostToDevice, s));
+    }
+    FK(cudaMemcpyAsync(Od, Op.data(), sizeof(double) * Op.size(), cudaMemcpyHostToDevice, s));
+    // qd0 = Phi^T v0
+    if (sel->v0) {
+        FK(cudaMemcpyAsync(v0, sel->v0, sizeof(double) * F.n, cudaMemcpyDefault, s));
+        FK(launch_gemm_tn(r, 1, F.n, F.Phi, r, v0, 1, qd0, 1, 1.0, 0.0, s));
+    } else {
+        FK(cudaMemsetAsync(qd0, 0, sizeof(double) * r, s));
+    }
+    FK(launch_select_rollout(nl, r, d, F.nq, F.rs, Od, kd, F.D, F.Y, qd0, F.ns, sel->substeps, sel->dt, phi, num,
+                             den, s));
+    std::vector<double> nh(nl), dh(nl);
+    FK(cudaMemcpyAsync(nh.data(), num, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+    FK(cudaMemcpyAsync(dh.data(), den, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));
+    FK(cudaStreamSynchronize(s));
+    int b = -1;
+    for (int l = 0; l < nl; ++l) {
+        const double e = std::sqrt(nh[l] / dh[l]);
+        errors[l] = std::isfinite(e) ? e : HUGE_VAL;
+        if (std::isfinite(e) && (b < 0 || e < errors[b])) b = l;
+    }
+    if (b < 0) { g_fit_error = "every candidate rollout is non-finite"; return OSAM_ENONFINITE; }
+    *best = b;
+    return fit_output(in, F, Os[b], s, out);
 }
 
 extern "C" OSAM_API const char* osam_fit_last_error(void) { return g_fit_error.c_str(); }

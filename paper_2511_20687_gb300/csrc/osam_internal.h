@@ -229,6 +229,11 @@ cudaError_t launch_gemm_nt(int m, int n, int k, const double* A, int lda, const 
                            int ldc, double alpha, double beta, cudaStream_t s);
 cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0,
                                  cudaStream_t s);
+// regularisation selection: nl candidate ROMs (packed rows [nl][r][d]) rolled out under frozen
+// boundary data (D's boundary columns), error sums per candidate
+cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int rs, const double* O, const short2* kij,
+                                  const double* D, const double* Y, const double* qd0, int ns, int k, double dt,
+                                  double* phi, double* num, double* den, cudaStream_t s);
 
 // adjoint (adjoint_kernels.cu)
 cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,

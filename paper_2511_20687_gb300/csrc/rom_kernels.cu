@@ -134,6 +134,98 @@ __global__ void k_kron_features(const double* Ubar, int r, int nsnap, double* D,
     }
 }
 
+
+// Regularisation selection (Sec. 4.2.4, Algorithm 3): one block per candidate lambda rolls its ROM
+// out alone, explicit central differences with step dt, Schwarz boundary data frozen to the training
+// columns (linear in time between columns that are k steps apart), from the training initial state;
+// accumulates ||q(t_j) - Ubar_j||^2 and ||Ubar_j||^2 over the snapshot times in a fixed order.
+constexpr int kSelBlock = 256;
+constexpr int kSelMaxR = 128;
+
+__device__ __forceinline__ double2 block_sum_pair(double x, double y) {
+    __shared__ double sx[kSelBlock / 32], sy[kSelBlock / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+    }
+    const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+    __syncthreads();
+    if (ln == 0) { sx[w] = x; sy[w] = y; }
+    __syncthreads();
+    double a = 0.0, b = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x / 32); ++i) { a += sx[i]; b += sy[i]; }
+    return make_double2(a, b);
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_select_rollout(int r, int d, int nq, int rs, const double* __restrict__ O,
+                                                              const short2* __restrict__ kij, const double* __restrict__ D,
+                                                              const double* __restrict__ Y, const double* __restrict__ qd0,
+                                                              int ns, int k, double dt, double* phi_all, double* num,
+                                                              double* den) {
+    __shared__ double q[kSelMaxR], qd[kSelMaxR], qdd[kSelMaxR], qp[kSelMaxR], qn[kSelMaxR];
+    const int l = blockIdx.x, tid = threadIdx.x;
+    const double* Ol = O + (size_t)l * r * d;
+    double* phi = phi_all + (size_t)l * d;
+    const int nwarp = blockDim.x / 32, warp = tid / 32, lane = tid % 32;
+    for (int t = tid; t < r; t += blockDim.x) {
+        q[t] = D[t];
+        qd[t] = qd0[t];
+        qdd[t] = Y[t];
+    }
+    double2 acc = block_sum_pair(0.0, tid < r ? D[tid] * D[tid] : 0.0);
+    double sn = 0.0, sd = acc.y;   // meaningful in thread 0
+    const double hdt = 0.5 * dt, hdt2 = 0.5 * dt * dt;
+    for (int j = 0; j + 1 < ns; ++j) {
+        const double* g0 = D + (size_t)j * d + r + nq;
+        const double* g1 = D + (size_t)(j + 1) * d + r + nq;
+        for (int s = 1; s <= k; ++s) {
+            __syncthreads();
+            for (int t = tid; t < r; t += blockDim.x) qp[t] = q[t] + dt * qd[t] + hdt2 * qdd[t];
+            __syncthreads();
+            const double w = (double)s / (double)k;
+            for (int col = tid; col < d; col += blockDim.x) {
+                double v;
+                if (col < r) v = qp[col];
+                else if (col < r + nq) { const short2 ij = kij[col - r]; v = qp[ij.x] * qp[ij.y]; }
+                else if (col < r + nq + rs) { const int b = col - r - nq; v = g0[b] + w * (g1[b] - g0[b]); }
+                else v = 1.0;
+                phi[col] = v;
+            }
+            __syncthreads();
+            for (int row = warp; row < r; row += nwarp) {
+                const double* orow = Ol + (size_t)row * d;
+                double a = 0.0;
+                for (int col = lane; col < d; col += 32) a = fma(orow[col], phi[col], a);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+                if (lane == 0) qn[row] = a;
+            }
+            __syncthreads();
+            for (int t = tid; t < r; t += blockDim.x) {
+                qd[t] = qd[t] + hdt * (qdd[t] + qn[t]);
+                qdd[t] = qn[t];
+                q[t] = qp[t];
+            }
+        }
+        __syncthreads();
+        double e = 0.0, u = 0.0;
+        if (tid < r) {
+            const double ub = D[(size_t)(j + 1) * d + tid];
+            e = (q[tid] - ub) * (q[tid] - ub);
+            u = ub * ub;
+        }
+        acc = block_sum_pair(e, u);
+        sn += acc.x;
+        sd += acc.y;
+    }
+    if (tid == 0) {
+        num[l] = sn;
+        den[l] = sd;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_rom_basis_project(int nfree, int r, const double* Phi, const int* free_dof, const double* u_aos,
@@ -185,6 +277,14 @@ cudaError_t launch_gemm_nt(int m, int n, int k, const double* A, int lda, const 
 
 cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0, cudaStream_t s) {
     k_kron_features<<<nsnap, 64, 0, s>>>(Ubar, r, nsnap, D, ldd, col0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int rs, const double* O, const short2* kij,
+                                  const double* D, const double* Y, const double* qd0, int ns, int k, double dt,
+                                  double* phi, double* num, double* den, cudaStream_t s) {
+    if (r > kSelMaxR || r < 1 || nl < 1) return cudaErrorInvalidValue;
+    k_select_rollout<<<nl, kSelBlock, 0, s>>>(r, d, nq, rs, O, kij, D, Y, qd0, ns, k, dt, phi, num, den);
     return cudaGetLastError();
 }
 

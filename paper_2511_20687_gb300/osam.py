@@ -28,7 +28,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_profile", "osam_profile_read", "osam_fp64_peak", "osam_hex8_force_noalloc", "osam_batch_init",
             "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
             "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
-            "osam_set_graph", "osam_tuning"]
+            "osam_set_graph", "osam_tuning", "opinf_select"]
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
@@ -75,6 +75,10 @@ class FitOutput(C.Structure):
                 ("sigma_s", _vp), ("r_s", C.c_int)]
 
 
+class SelectInput(C.Structure):
+    _fields_ = [("lambdas", _vp), ("n_lambda", C.c_int), ("v0", _vp), ("dt", C.c_double), ("substeps", C.c_int)]
+
+
 class AdjointDesc(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double), ("material", C.c_int),
                 ("lambda_e", _vp), ("mu_e", _vp), ("rho", C.c_double), ("dirichlet", _vp), ("u0", _vp), ("v0", _vp),
@@ -119,6 +123,8 @@ def load():
     L.osam_hex8_force_vjp.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, _vp,
                                       _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.opinf_fit.argtypes = [C.POINTER(FitInput), C.POINTER(FitOutput)]
+    L.opinf_select.argtypes = [C.POINTER(FitInput), C.POINTER(SelectInput), _dp, C.POINTER(C.c_int),
+                               C.POINTER(FitOutput)]
     L.osam_adjoint.argtypes = [C.POINTER(AdjointDesc), C.POINTER(AdjointOut)]
     L.osam_profile.argtypes = [_vp, C.c_int]
     L.osam_profile_read.argtypes = [_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
@@ -417,6 +423,35 @@ def opinf_fit(U, A, S, r, lam, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic
     out_arrs["Phi_S"] = out_arrs["Phi_S"][:, :rs].copy()
     out_arrs["B"] = out_arrs["B"][:, :rs].copy()
     out_arrs["r_s"] = rs
+    return out_arrs
+
+
+def opinf_select(U, A, S, v0, r, lambdas, dt, substeps, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True,
+                 device=0, stream=None):
+    """Schwarz-aware regularisation selection (Algorithm 3) on the GPU.  U, A: [n_snap, n_dof];
+    S: [n_snap, n_sdof]; v0: [n_dof] velocity of the first snapshot (or None); lambdas: candidates.
+    Returns the operators at the selected lambda (as opinf_fit) plus "errors", "best" and "lambda"."""
+    U, A, S, v0 = _f64(U), _f64(A), _f64(S), _f64(v0)
+    lams = np.ascontiguousarray(lambdas, dtype=np.float64)
+    ns, n = U.shape
+    nsd = S.shape[1] if S is not None else 0
+    rs_cols = max(r_s_max, r_s)
+    out_arrs = {"Phi": np.zeros((n, r)), "Phi_S": np.zeros((max(nsd, 1), rs_cols)), "K": np.zeros((r, r)),
+                "H": np.zeros((r, r * (r + 1) // 2)), "B": np.zeros((r, rs_cols)), "c": np.zeros(r),
+                "sigma": np.zeros(ns), "sigma_s": np.zeros(ns)}
+    fi = FitInput(n_dof=n, n_snap=ns, n_sdof=nsd, U=_ptr(U), A=_ptr(A), S=_ptr(S), r=r, r_s=r_s, energy_s=energy_s,
+                  r_s_max=r_s_max, lambda_=0.0, quadratic=int(quadratic), stream=_stream_handle(stream), device=device)
+    si = SelectInput(lambdas=lams.ctypes.data, n_lambda=len(lams), v0=_ptr(v0), dt=dt, substeps=substeps)
+    fo = FitOutput(**{k: _ptr(v) for k, v in out_arrs.items()}, r_s=0)
+    errors = np.zeros(len(lams))
+    best = C.c_int(-1)
+    rc = load().opinf_select(C.byref(fi), C.byref(si), errors.ctypes.data_as(_dp), C.byref(best), C.byref(fo))
+    if rc < 0:
+        raise OsamError(rc, load().osam_fit_last_error().decode())
+    rs = fo.r_s
+    out_arrs["Phi_S"] = out_arrs["Phi_S"][:, :rs].copy()
+    out_arrs["B"] = out_arrs["B"][:, :rs].copy()
+    out_arrs.update(r_s=rs, errors=errors, best=best.value, **{"lambda": float(lams[best.value])})
     return out_arrs
 
 
