@@ -189,12 +189,15 @@ def train_rom(W, osam, args, device, log):
     A = np.empty_like(U)
     S = np.empty((args.snapshots, int(sdof.sum())))
     t0 = time.time()
+    v0 = None
     for k in range(args.snapshots):
         prob.step()
-        u, _, a = prob.state(1, fields=(0, 2))
+        u, v, a = prob.state(1, fields=(0, 1, 2) if k == 0 else (0, 2))
         U[k] = u.reshape(-1)[free]
         A[k] = a.reshape(-1)[free]
         S[k] = u.reshape(-1)[sdof]
+        if k == 0:
+            v0 = v.reshape(-1)[free].copy()
     prob.close()
     log(f"training run: {args.snapshots} controller steps of 4 substeps in {time.time() - t0:.1f}s (amplitude {amp:.3e})")
     t0 = time.time()
@@ -202,7 +205,7 @@ def train_rom(W, osam, args, device, log):
     fit_s = time.time() - t0
     log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {fit_s:.1f}s")
     fit = {"gpu_seconds": fit_s, "r": args.rank, "r_s": int(ops["r_s"]), "n_snap": args.snapshots,
-           "n_dof": int(U.shape[1]), "n_sdof": int(S.shape[1]), "training": (U, A, S)}
+           "n_dof": int(U.shape[1]), "n_sdof": int(S.shape[1]), "training": (U, A, S, v0)}
     return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}, fit
 
 
@@ -326,14 +329,45 @@ def measure_fit(fit_info, log):
     """opinf_fit on the GPU (timed during training, host snapshot matrices in, operators out) against
     the oracle's numpy fit of the same snapshots with the same r and r_s."""
     from oracle import fit as OF
-    U, A, S = fit_info.pop("training")
+    U, A, S, _ = fit_info["training"]
     t0 = time.perf_counter()
     OF.opinf_fit(U.T, A.T, S.T, r=fit_info["r"], lam=1e-6, r_s=fit_info["r_s"])
     cpu = time.perf_counter() - t0
     log(f"oracle fit: {cpu:.1f}s")
-    return {**fit_info, "unit": "s", "higher_is_better": False, "oracle_seconds": cpu,
+    return {**{k: v for k, v in fit_info.items() if k != "training"}, "unit": "s", "higher_is_better": False,
+            "oracle_seconds": cpu,
             "oracle_threads": os.cpu_count(), "oracle_kind": "oracle/fit.py (numpy SVD and solve, threaded BLAS)",
             "speedup_vs_oracle": cpu / fit_info["gpu_seconds"]}
+
+
+def measure_select(osam, fit_info, local, log, sample_snaps=100, sample_r=32):
+    """Schwarz-aware regularisation selection (Algorithm 3, 11 candidates 1e-10 .. 1, rollouts with the
+    online step 1e-6 s and 4 steps between snapshots): the GPU on the whole headline training set, and
+    GPU and oracle on a bounded sample of it (first snapshots, smaller rank)."""
+    from oracle import fit as OF
+    U, A, S, v0 = fit_info["training"]
+    lams = OF.lambda_grid()
+    t0 = time.perf_counter()
+    full = osam.opinf_select(U, A, S, v0, r=fit_info["r"], lambdas=lams, dt=1e-6, substeps=4, r_s=fit_info["r_s"],
+                             device=local)
+    gpu_full = time.perf_counter() - t0
+    Us, As, Ss = U[:sample_snaps], A[:sample_snaps], S[:sample_snaps]
+    t0 = time.perf_counter()
+    gs = osam.opinf_select(Us, As, Ss, v0, r=sample_r, lambdas=lams, dt=1e-6, substeps=4, device=local)
+    gpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oe, ob, _ = OF.select_lambda(Us.T, As.T, Ss.T, v0, r=sample_r, lambdas=lams, dt=1e-6, k=4, r_s=gs["r_s"])
+    cpu_s = time.perf_counter() - t0
+    fin = np.isfinite(oe)
+    agree = bool(gs["best"] == ob) and bool(np.all(np.abs(gs["errors"][fin] - oe[fin]) <= 1e-6 * oe[fin] + 1e-9))
+    log(f"opinf_select: GPU {gpu_full:.1f}s (full), sample GPU {gpu_s:.1f}s vs oracle {cpu_s:.1f}s")
+    return {"candidates": [float(x) for x in lams], "unit": "s", "higher_is_better": False,
+            "gpu_seconds": gpu_full, "errors": [float(x) for x in full["errors"]], "selected_lambda": full["lambda"],
+            "workload": f"{fit_info['n_snap']} snapshots x {fit_info['n_dof']} free dofs, r={fit_info['r']}, "
+                        f"r_s={fit_info['r_s']}, 11 rollouts of {4 * (fit_info['n_snap'] - 1)} steps",
+            "sample": f"first {sample_snaps} snapshots, r={sample_r}, r_s={gs['r_s']}, 11 candidates",
+            "sample_gpu_seconds": gpu_s, "sample_oracle_seconds": cpu_s, "oracle_threads": os.cpu_count(),
+            "sample_speedup_vs_oracle": cpu_s / gpu_s, "sample_agrees_with_oracle": agree}
 
 
 def measure_adjoint(W, osam, local, log, oracle_steps=40):
@@ -596,9 +630,10 @@ def main():
         batched = measure_batched(W, osam, torch, flush, args, local, log)
         log(f"batched: {batched['value']:.3e} vs plain {batched['plain_value']:.3e} ({batched['speedup']:.1f}x)")
 
-    fit_meas = adjoint_meas = None
+    fit_meas = select_meas = adjoint_meas = None
     if world == 1 and not args.no_cpu_baseline and fit_info is not None:
         fit_meas = measure_fit(fit_info, log)
+        select_meas = measure_select(osam, fit_info, local, log)
         adjoint_meas = measure_adjoint(W, osam, local, log)
 
     cpu = None
@@ -651,7 +686,8 @@ def main():
                 "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
                 "gpu_launches": head["launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-                "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "adjoint": adjoint_meas,
+                "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
+                "adjoint": adjoint_meas,
                 "hbm": hbm,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}
