@@ -74,6 +74,7 @@ def lib():
                                       C.c_int, C.c_int, _d, _d, _d, _d, _d, _d, _d, _d]
             L.orc_couple.argtypes = [C.c_void_p, C.c_int, C.c_int, _u8]
             L.orc_init.argtypes = [C.c_void_p]
+            L.orc_set_implicit.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_step.argtypes = [C.c_void_p, _i, _d, _d]
             L.orc_num_nodes.argtypes = [C.c_void_p, C.c_int]
             L.orc_num_free.argtypes = [C.c_void_p, C.c_int]
@@ -232,6 +233,8 @@ class Problem:
                 self._keep += [le, me]
                 rc = L.orc_add_fom(self.h, nx, ny, nz, sd.h, _p(org), _mat(sd.material), sd.lam, sd.mu, sd.rho,
                                    _p(le), _p(me), _p(dm), _p(u0), _p(v0))
+                if rc >= 0 and getattr(sd, "integrator", "explicit") == "implicit":
+                    rc = L.orc_set_implicit(self.h, i, 1)
             else:
                 ops = rom_ops[i]
                 arrs = [_f64(ops[k]) for k in ("Phi", "Phi_S", "K", "H", "B", "c")]

@@ -657,6 +657,8 @@ typedef struct {
     double* qrec;         /* recorded reduced history [(nsub+1)][3][r] */
     double* ghat;
     int rs_rows;          /* declared row count of PhiS */
+    /* time integrator of a FOM: 0 explicit central differences, 1 implicit average acceleration */
+    int implicit;
 } osub;
 
 typedef struct {
@@ -866,13 +868,21 @@ static void rom_ghat(const osub* s, int slot) {
     }
 }
 
+/* time integrator of FOM subdomain i: 0 explicit central differences, 1 implicit average acceleration */
+int orc_set_implicit(void* vp, int i, int implicit) {
+    oprob* p = (oprob*)vp;
+    if (i < 0 || i >= p->nsd || p->sd[i].kind != ORC_FOM) return ORC_EINVAL;
+    p->sd[i].implicit = implicit != 0;
+    return ORC_OK;
+}
+
 int orc_init(void* vp) {
     oprob* p = (oprob*)vp;
     /* explicit stability: every FOM subdomain's time step within its element bound (a relative
      * allowance of 1e-9 keeps a step exactly at the limit, such as the 1D bar at Courant number 1) */
     for (int i = 0; i < p->nsd; ++i) {
         osub* s = &p->sd[i];
-        if (s->kind != ORC_FOM) continue;
+        if (s->kind != ORC_FOM || s->implicit) continue; /* the average-acceleration rule is unconditionally stable */
         double lim = orc_stable_dt(s->m.nx, s->m.ny, s->m.nz, s->m.h, s->m.org, s->lam, s->mu, s->lam_e, s->mu_e,
                                    s->rho);
         if (!(lim > 0.0)) return ORC_EINVAL;
@@ -979,11 +989,167 @@ static void rom_record(osub* s, int j) {
 }
 
 /* advance subdomain i over the controller interval (nsub substeps) with its input history */
+/* ------------------------------------------------------------------------------------------ */
+/* implicit Newmark (beta = 1/4, gamma = 1/2: average acceleration), Sec. 4.1 with reading c1     */
+/* ------------------------------------------------------------------------------------------ */
+/* element tangent K_e(u) (24 x 24, element dof order 3*a + i): column q is the directional
+ * derivative of the element force along the unit vector of element dof q (Appendix A tangents) */
+static void element_tangent(const omesh* m, int model, double lam, double mu, int e, const double* u,
+                            double Ke[24][24], int nodes[8]) {
+    double X[8][3], U[8][3], dNdX[8][3], H[3][3], G[3][3], dP[3][3];
+    gather_elem(m, e, u, nodes, X, U);
+    for (int q = 0; q < 24; ++q)
+        for (int r = 0; r < 24; ++r) Ke[r][q] = 0.0;
+    for (int g = 0; g < 8; ++g) {
+        double detJ = physical_gradients(X, g, dNdX);
+        grad_at(U, dNdX, H);
+        for (int q = 0; q < 24; ++q) {
+            double Y[8][3] = {{0}};
+            Y[q / 3][q % 3] = 1.0;
+            grad_at(Y, dNdX, G);
+            if (model == ORC_NH) {
+                double dPk[3][3], dPm[3][3], kappa = lam + 2.0 * mu / 3.0;
+                nh_tangent(H, G, dPk, dPm);
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) dP[i][j] = kappa * dPk[i][j] + mu * dPm[i][j];
+            } else {
+                stress_le(G, lam, mu, dP);
+            }
+            for (int a = 0; a < 8; ++a)
+                for (int i = 0; i < 3; ++i) {
+                    double t = 0.0;
+                    for (int j = 0; j < 3; ++j) t += dP[i][j] * dNdX[a][j];
+                    Ke[3 * a + i][q] += detJ * t;
+                }
+        }
+    }
+}
+
+/* Cholesky solve of the dense SPD system A x = b (n x n, row-major, overwritten); 0 if not SPD */
+static int dense_spd_solve(double* A, int n, double* b) {
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+        if (!(d > 0.0)) return 0;
+        d = sqrt(d);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) t -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+            A[(size_t)i * n + j] = t / d;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double t = b[i];
+        for (int k = 0; k < i; ++k) t -= A[(size_t)i * n + k] * b[k];
+        b[i] = t / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double t = b[i];
+        for (int k = i + 1; k < n; ++k) t -= A[(size_t)k * n + i] * b[k];
+        b[i] = t / A[(size_t)i * n + i];
+    }
+    return 1;
+}
+
+/* One implicit substep of FOM subdomain s with boundary data h1 (history slot of the new level).
+ * Predictor ut = u + dt v + (1/2 - beta) dt^2 a on free dofs; solve R(u) = M (u - ut) / (beta dt^2)
+ * + f_int(u) = 0 by Newton's method with the exact tangent M / (beta dt^2) + K(u) (assembled densely,
+ * Cholesky), until |R| <= 1e-12 |R(ut)| (at most 25 iterations); then a = (u - ut) / (beta dt^2) and
+ * v += dt ((1 - gamma) a_old + gamma a).  Returns 0, or -3 for a non-finite or failed solve. */
+static int implicit_substep(osub* s, double dt, const double* h1, size_t ns) {
+    const double beta = 0.25, gamma = 0.5, c0 = 1.0 / (beta * dt * dt);
+    size_t nn = (size_t)s->m.nn;
+    int* fid = (int*)xcalloc(3 * nn, sizeof(int)); /* dof -> free index or -1 */
+    int nf = 0;
+    for (size_t n = 0; n < nn; ++n)
+        for (int c = 0; c < 3; ++c) {
+            size_t d = 3 * n + c;
+            fid[d] = (!(s->dmask[n] & (1 << c)) && s->srow[n] < 0) ? nf++ : -1;
+        }
+    double* ut = (double*)xcalloc(3 * nn, sizeof(double));
+    double* f = (double*)xcalloc(3 * nn, sizeof(double));
+    double* R = (double*)xcalloc((size_t)(nf ? nf : 1), sizeof(double));
+    double* J = (double*)xcalloc((size_t)(nf ? nf : 1) * (nf ? nf : 1), sizeof(double));
+    for (size_t n = 0; n < nn; ++n)
+        for (int c = 0; c < 3; ++c) {
+            size_t d = 3 * n + c;
+            if (s->dmask[n] & (1 << c)) s->u[d] = 0.0;
+            else if (s->srow[n] >= 0) s->u[d] = h1[(size_t)s->srow[n] * 3 + c];
+            else s->u[d] += dt * s->v[d] + (0.5 - beta) * dt * dt * s->a[d];
+            ut[d] = s->u[d];
+        }
+    int status = -3;
+    double r0 = -1.0;
+    for (int it = 0; it < 25; ++it) {
+        internal_force(&s->m, s->model, s->lam, s->mu, s->lam_e, s->mu_e, s->u, f);
+        double rn = 0.0;
+        for (size_t d = 0; d < 3 * nn; ++d)
+            if (fid[d] >= 0) {
+                R[fid[d]] = c0 * s->mass[d / 3] * (s->u[d] - ut[d]) + f[d];
+                rn += R[fid[d]] * R[fid[d]];
+            }
+        rn = sqrt(rn);
+        if (!(rn == rn) || isinf(rn)) break;
+        if (r0 < 0.0) r0 = rn;
+        if (rn <= 1e-12 * r0 || rn == 0.0) { status = 0; break; }
+        /* J = M c0 + sum_e K_e on the free dofs */
+        memset(J, 0, sizeof(double) * (size_t)nf * nf);
+        for (size_t d = 0; d < 3 * nn; ++d)
+            if (fid[d] >= 0) J[(size_t)fid[d] * nf + fid[d]] += c0 * s->mass[d / 3];
+        for (int e = 0; e < s->m.ne; ++e) {
+            double Ke[24][24];
+            int nodes[8];
+            double le = s->lam_e ? s->lam_e[e] : s->lam, me = s->mu_e ? s->mu_e[e] : s->mu;
+            element_tangent(&s->m, s->model, le, me, e, s->u, Ke, nodes);
+            for (int r = 0; r < 24; ++r) {
+                int fr = fid[3 * nodes[r / 3] + r % 3];
+                if (fr < 0) continue;
+                for (int q = 0; q < 24; ++q) {
+                    int fq = fid[3 * nodes[q / 3] + q % 3];
+                    if (fq >= 0) J[(size_t)fr * nf + fq] += Ke[r][q];
+                }
+            }
+        }
+        for (int k = 0; k < nf; ++k) R[k] = -R[k];
+        if (!dense_spd_solve(J, nf, R)) break;
+        for (size_t d = 0; d < 3 * nn; ++d)
+            if (fid[d] >= 0) s->u[d] += R[fid[d]];
+    }
+    if (status == 0) {
+        for (size_t n = 0; n < nn; ++n)
+            for (int c = 0; c < 3; ++c) {
+                size_t d = 3 * n + c;
+                if (s->dmask[n] & (1 << c)) { s->v[d] = 0.0; s->a[d] = 0.0; }
+                else if (s->srow[n] >= 0) {
+                    s->v[d] = h1[ns * 3 + (size_t)s->srow[n] * 3 + c];
+                    s->a[d] = h1[2 * ns * 3 + (size_t)s->srow[n] * 3 + c];
+                } else {
+                    double an = c0 * (s->u[d] - ut[d]);
+                    s->v[d] += dt * ((1.0 - gamma) * s->a[d] + gamma * an);
+                    s->a[d] = an;
+                }
+            }
+    }
+    free(fid); free(ut); free(f); free(R); free(J);
+    return status;
+}
+
 static void advance(oprob* p, int i) {
     osub* s = &p->sd[i];
     double dt = p->dt;
     size_t ns = (size_t)s->ns;
-    if (s->kind == ORC_FOM) {
+    if (s->kind == ORC_FOM && s->implicit) {
+        for (int j = 0; j < p->nsub; ++j) {
+            const double* h1 = s->hist + (size_t)(j + 1) * 3 * ns * 3;
+            if (implicit_substep(s, dt, h1, ns) != 0) {
+                /* a failed Newton solve leaves a non-finite state for the criterion to report */
+                for (size_t d = 0; d < 3 * (size_t)s->m.nn; ++d) s->u[d] = NAN;
+            }
+            for (int k = 0; k < p->ncpl; ++k)
+                if (p->cpl[k].src == i) transfer_slot(p, &p->cpl[k], j + 1, 0);
+        }
+    } else if (s->kind == ORC_FOM) {
         size_t nn = (size_t)s->m.nn;
         double* f = (double*)xcalloc(3 * nn, sizeof(double));
         for (int j = 0; j < p->nsub; ++j) {

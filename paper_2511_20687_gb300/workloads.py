@@ -44,6 +44,7 @@ class Subdomain:
     dirichlet: Optional[np.ndarray] = None   # uint8 [N]
     u0: Optional[np.ndarray] = None          # [N, 3]
     v0: Optional[np.ndarray] = None          # [N, 3]
+    integrator: str = "explicit"             # FOM time integrator: "explicit" (central differences) or "implicit"
 
     @property
     def n_nodes(self) -> int:

@@ -430,3 +430,72 @@ def test_problem_rejects_a_step_above_the_limit(oracle):
     O.Problem(spec)
     # the 1D bar at Courant number 1 sits exactly on the limit and is accepted
     O.Problem(W.wave1d(n_elem=40))
+
+
+# ---------------------------------------------------------------------------------------------
+# implicit Newmark (average acceleration) subdomains
+# ---------------------------------------------------------------------------------------------
+def _implicit(spec, which=None):
+    for i, sd in enumerate(spec.subdomains):
+        if which is None or i in which:
+            sd.integrator = "implicit"
+    return spec
+
+
+def test_implicit_linear_elastic_conserves_energy(oracle):
+    """The average-acceleration rule conserves 1/2 v.Mv + 1/2 u.Ku exactly on a linear system, also at
+    a time step five times the explicit stability limit (unconditional stability)."""
+    p = W.single_bar("energy_imp", 3, 8, "le", 1e9, 0.25, 1000.0, 1e-3, 2e-6, 5)
+    sd = p.subdomains[0]
+    lim = oracle.stable_dt(sd.dims, sd.h, sd.origin, sd.lam, sd.mu, sd.rho)
+    for dt in (2e-6, 5.0 * lim):
+        p.dt = dt
+        prob = oracle.Problem(_implicit(p))
+        m = oracle.lumped_mass(sd.dims, sd.h, sd.origin, sd.rho)
+        free = np.repeat(sd.dirichlet == 0, 3).reshape(-1, 3)
+
+        def energy():
+            u, v, _ = prob.state(0)
+            f = oracle.internal_force(sd.dims, sd.h, sd.origin, "le", sd.lam, sd.mu, u).reshape(-1, 3)
+            return 0.5 * np.sum((m[:, None] * v * v)[free]) + 0.5 * np.sum((u * f)[free])
+
+        e0 = energy()
+        es = []
+        for _ in range(30):
+            prob.step()
+            es.append(energy())
+        assert np.abs(np.array(es) - e0).max() < 1e-9 * e0
+
+
+def test_implicit_and_explicit_agree_to_second_order(oracle):
+    """Both integrators are second order: their difference after a fixed time falls ~4x per halving
+    of the step (Neo-Hookean bar)."""
+    diffs = []
+    for n_sub, dt in ((10, 2e-6), (20, 1e-6), (40, 5e-7)):
+        pe = W.single_bar("cmp", 3, 8, "nh", 1e9, 0.25, 1000.0, 2e-3, dt, n_sub)
+        pi = _implicit(W.single_bar("cmp", 3, 8, "nh", 1e9, 0.25, 1000.0, 2e-3, dt, n_sub))
+        A, B = oracle.Problem(pe), oracle.Problem(pi)
+        for _ in range(3):
+            A.step()
+            B.step()
+        diffs.append(np.abs(A.state(0)[0] - B.state(0)[0]).max())
+    r1, r2 = diffs[0] / diffs[1], diffs[1] / diffs[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0
+
+
+def test_implicit_fom_fom_schwarz_converges_to_single_domain(oracle):
+    """Two implicit subdomains coupled by O-SAM reach the single-domain implicit solution to the
+    Schwarz tolerance (implicit information crosses the overlap in every iteration, so the iteration
+    converges geometrically rather than terminating)."""
+    p = _implicit(W.bar_chain("imp2", 3, [8, 8], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10))
+    ps = _implicit(W.single_bar("imp1", 3, 14, "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10))
+    A, S = oracle.Problem(p), oracle.Problem(ps)
+    for _ in range(3):
+        r = A.step()
+        S.step()
+        assert r["status"] == oracle.OK
+    us = S.state(0)[0]
+    nn = 4 * 4
+    for i, k0 in ((0, 0), (1, 6)):
+        u = A.state(i)[0]
+        assert np.abs(u - us[k0 * nn:k0 * nn + u.shape[0]]).max() < 1e-7 * np.abs(us).max()
