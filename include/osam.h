@@ -50,6 +50,9 @@ typedef enum {
 
 enum { OSAM_FOM = 0, OSAM_ROM = 1 };
 enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1 };
+/* FOM time integrator: explicit Newmark (beta = 0, gamma = 1/2, central difference) or implicit
+ * Newmark (beta = 1/4, gamma = 1/2, average acceleration) */
+enum { OSAM_EXPLICIT = 0, OSAM_IMPLICIT = 1 };
 /* OSAM_FP64: native FP64 everywhere.  OSAM_FP32_FORCE: internal force in FP32 (checked to 1e-5).
  * OSAM_F32X2_FORCE: internal force in double-float arithmetic (pairs of FP32 values, ~48-bit
  * significands) on the FP32 pipes, state and time integration in FP64 (checked to 1e-9 like FP64);
@@ -73,7 +76,8 @@ typedef struct osam_ctx osam_ctx;
 
 /* One subdomain (Sec. 4, Eq. dynamic_elasticity_sam_bcs).
  * FOM: hex8 isoparametric FE (Sec. 2, Eq. matrix_vector_form) with 2x2x2 Gauss quadrature,
- *   row-sum lumped mass, explicit Newmark beta=0 gamma=1/2 (Sec. 5 setup), material of Appendix A.1
+ *   row-sum lumped mass, explicit Newmark beta=0 gamma=1/2 (Sec. 5 setup) or implicit Newmark
+ *   beta=1/4 gamma=1/2 (Sec. 4.1, `integrator`), material of Appendix A.1
  *   (linear elastic) or A.3 (Neo-Hookean, deviatoric coefficient 1/3 from its energy).
  * ROM: quadratic OpInf model of Eq. opinf_model_schwarz in solved form
  *   qdd = K q + H kron_c(q) + B ghat + c,  ghat = Phi_S^T s  (Sec. 4.2.1, boundary POD),
@@ -101,6 +105,13 @@ typedef struct {
     const double* H;          /* [r][r(r+1)/2] */
     const double* B;          /* [r][r_s] */
     const double* c;          /* [r] */
+    /* FOM integrator (OSAM_EXPLICIT or OSAM_IMPLICIT; ignored for ROMs).  An implicit FOM solves
+     * M (u - u~) / (beta dt^2) + f_int(u) = 0 on its free dofs each substep (u~ the Newmark predictor)
+     * by Newton's method, |R| <= 1e-12 |R(u~)| within 25 iterations, each Newton system by conjugate
+     * gradients with the exact tangent applied matrix-free (Appendix A tangents).  No stability
+     * limit applies to it.  Implicit FOMs need OSAM_FP64 and run host-driven (no CUDA graph); a Newton
+     * solve that fails leaves a non-finite state, reported as OSAM_ENONFINITE. */
+    int integrator;
 } osam_subdomain_desc;
 
 /* Dirichlet transfer from subdomain src to the Schwarz boundary nodes of dst (Sec. 4.1): the data

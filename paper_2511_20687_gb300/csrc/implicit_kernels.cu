@@ -1,0 +1,418 @@
+// Implicit Newmark subdomains (average acceleration, beta = 1/4, gamma = 1/2, the implicit member of
+// the Newmark family of Sec. 4.1), batched over the instances of a FOM group like the explicit
+// kernels.  Per substep:
+//   predictor  u~ = u + dt v + (1/2 - beta) dt^2 a on free dofs, Dirichlet / Schwarz data elsewhere;
+//   Newton     R(u) = M (u - u~) / (beta dt^2) + f_int(u) = 0 on the free dofs; each Newton system
+//              J du = -R, J = M / (beta dt^2) + K(u), solved by conjugate gradients preconditioned
+//              with the mass term, J applied matrix-free: K(u) p is the directional derivative of the
+//              element forces (Appendix A tangents) in the force kernels' sum factorisation;
+//   corrector  a = (u - u~) / (beta dt^2), v += dt ((1 - gamma) a_old + gamma a).
+// Every inner product is reduced per node block, then per instance in a fixed order (deterministic).
+// Newton and CG activity is tracked per instance on the device; the host reads it to stop.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hex8_math.cuh"
+#include "nh_tangent.cuh"
+#include "osam_internal.h"
+
+namespace osam {
+
+namespace {
+
+using namespace hex8;
+
+__device__ __forceinline__ bool run(const int* mask, int inst) { return !mask || mask[inst]; }
+
+__device__ __forceinline__ double block_sum1(double x) {
+    __shared__ double sx[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    __syncthreads();
+    if (l == 0) sx[w] = x;
+    __syncthreads();
+    double a = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)((blockDim.x + 31) / 32); ++i) a += sx[i];
+    return a;
+}
+
+struct NodeCtx {
+    int inst, n;
+    long long gn;
+    InstFom I;
+    bool ok;
+};
+
+__device__ __forceinline__ NodeCtx node_ctx(const FomB& g, const int* mask) {
+    NodeCtx c;
+    const int2 b = g.nblk[blockIdx.x];
+    c.inst = b.x;
+    c.I = g.inst[b.x];
+    c.n = b.y + threadIdx.x;
+    c.gn = c.I.node_off + c.n;
+    c.ok = run(mask, b.x) && c.n < c.I.nn;
+    return c;
+}
+
+__device__ __forceinline__ bool is_free(const FomB& g, long long gn, int c) {
+    return !(g.clamp[gn] & (1 << c)) && g.srow[gn] < 0;
+}
+
+// predictor and boundary data of the new level; u lives in u[0] for implicit groups
+__global__ void __launch_bounds__(kNodeBlock) k_imp_predict_b(const FomB g, const int* __restrict__ active, int slot1,
+                                                              double dt) {
+    const NodeCtx x = node_ctx(g, active);
+    if (!x.ok) return;
+    const uint8_t cm = g.clamp[x.gn];
+    const int row = g.srow[x.gn];
+    const double* h1 = g.hist + x.I.hist_off + (long long)slot1 * 9 * x.I.ns;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + x.gn;
+        double u;
+        if (cm & (1 << c)) u = 0.0;
+        else if (row >= 0) u = h1[(long long)c * x.I.ns + row];
+        else u = g.u[0][d] + dt * g.v[d] + (0.25 * dt * dt) * g.a[d];
+        g.u[0][d] = u;
+        g.ut[d] = u;
+        g.us[d] = u * x.I.invh;
+    }
+}
+
+// R = M (u - ut) c0 + f (free dofs; the element forces of u are in the element buffer).  CG start
+// x = 0, r = -R, z = p = M^-1 r / c0 (the mass part of the tangent as preconditioner); partials
+// |R|^2 and r . z
+__global__ void __launch_bounds__(kNodeBlock) k_imp_residual_b(const FomB g, const int* __restrict__ mask, double c0) {
+    const NodeCtx x = node_ctx(g, mask);
+    double s = 0.0, sz = 0.0;
+    if (x.ok) {
+        const int i = x.n % (x.I.nx + 1);
+        const int t = x.n / (x.I.nx + 1);
+        const int j = t % (x.I.ny + 1);
+        const int k = t / (x.I.ny + 1);
+        const double* fe = static_cast<const double*>(g.fe) + x.I.elem_off;
+        const double mi = g.minv[x.gn];
+        const double m = 1.0 / mi;
+        const double pz = mi / c0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = (long long)c * g.NN + x.gn;
+            double R = 0.0;
+            if (is_free(g, x.gn, c)) {
+                const double f = gather_force<double>(fe, x.I.nx, x.I.ny, x.I.nz, (int)g.NE, i, j, k, c);
+                R = c0 * m * (g.u[0][d] - g.ut[d]) + f;
+            }
+            g.cg_x[d] = 0.0;
+            g.cg_r[d] = -R;
+            g.cg_p[d] = -R * pz;
+            s = fma(R, R, s);
+            sz = fma(R * pz, R, sz);
+        }
+    }
+    s = block_sum1(s);
+    sz = block_sum1(sz);
+    if (threadIdx.x == 0) {
+        g.ipart[blockIdx.x] = s;
+        g.ipart[g.n_nblk + blockIdx.x] = sz;
+    }
+}
+
+// per-instance fixed-order sums of the node-block partials, and the decisions that depend on them
+__global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int mode, int first, double tol2) {
+    const int inst = blockIdx.x;
+    if (!run(mask, inst)) return;
+    const int b0 = g.nblk_off[inst], b1 = g.nblk_off[inst + 1];
+    double s = 0.0, sz = 0.0;
+    for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
+        s += g.ipart[b];
+        if (mode == 0) sz += g.ipart[g.n_nblk + b];
+    }
+    s = block_sum1(s);
+    if (mode == 0) sz = block_sum1(sz);
+    if (threadIdx.x != 0) return;
+    if (mode == 0) {
+        if (first) g.r0[inst] = s;
+        g.rn2[inst] = s;
+        g.rr[inst] = sz;
+        g.rr0[inst] = sz;
+        const bool fin = isfinite(s) && isfinite(sz);
+        const int st = !fin ? 2 : ((s == 0.0 || s <= tol2 * g.r0[inst]) ? 0 : 1);
+        g.nact[inst] = st;
+        g.cgact[inst] = st == 1 ? 1 : 0;
+    } else if (mode == 1) {
+        g.pap[inst] = s;
+    } else {
+        g.rrn[inst] = s;
+        if (!(s > tol2 * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
+    }
+}
+
+// element tangent action: the directional derivative of the element forces at u along p, written
+// to the element buffer (same layout and sum factorisation as the force kernels)
+template <int MAT>
+__global__ void __launch_bounds__(256) k_tangent_b(const FomB g, const int* __restrict__ mask) {
+    const int2 b = g.eblk[blockIdx.x];
+    if (!run(mask, b.x)) return;
+    const InstFom I = g.inst[b.x];
+    const int e = b.y + threadIdx.x;
+    if (e >= I.ne) return;
+    const int i = e % I.nx;
+    const int t = e / I.nx;
+    const int j = t % I.ny;
+    const int k = t / I.ny;
+    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
+    const int n0 = i + sy * j + sz * k;
+    int node[8];
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
+    double Dx[3][2][2], Dy[3][2][2], Dz[3][2][2], Ex[3][2][2], Ey[3][2][2], Ez[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double U[8], P[8];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            const long long d = (long long)c * g.NN + I.node_off + node[c8];
+            U[c8] = g.us[d];
+            P[c8] = g.cg_p[d] * I.invh;
+        }
+        edge_differences_prescaled<double>(U, Dx[c], Dy[c], Dz[c]);
+        edge_differences_prescaled<double>(P, Ex[c], Ey[c], Ez[c]);
+    }
+    double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2], Bx[3][2][2], By[3][2][2], Bz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lerp2<double>(Dx[c], Gx[c]); lerp2<double>(Dy[c], Gy[c]); lerp2<double>(Dz[c], Gz[c]);
+        lerp2<double>(Ex[c], Bx[c]); lerp2<double>(Ey[c], By[c]); lerp2<double>(Ez[c], Bz[c]);
+    }
+    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+    double m1, m2, m3;
+    if (MAT == OSAM_NEO_HOOKEAN) {
+        const double kappa = lam + (2.0 / 3.0) * mu;
+        m1 = 0.5 * kappa * I.w8; m2 = mu * I.w8; m3 = mu * I.w8 / 3.0;
+    } else {
+        m1 = lam * I.w8; m2 = mu * I.w8; m3 = 0.0;
+    }
+    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                double Hm[3][3], Gm[3][3], dP[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Hm[c][0] = Gx[c][q][r]; Hm[c][1] = Gy[c][p][r]; Hm[c][2] = Gz[c][p][q];
+                    Gm[c][0] = Bx[c][q][r]; Gm[c][1] = By[c][p][r]; Gm[c][2] = Bz[c][p][q];
+                }
+                if (MAT == OSAM_NEO_HOOKEAN) {
+                    double pk, pm;
+                    tangent::nh_tangent(Hm, Gm, m1, m2, m3, dP, pk, pm);
+                } else {
+                    stress_le<double>(Gm, m1, m2, dP);  // linear: the tangent applied to G is sigma(G)
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (p == 0) Sx[c][q][r] = dP[c][0]; else Sx[c][q][r] += dP[c][0];
+                    if (q == 0) Sy[c][p][r] = dP[c][1]; else Sy[c][p][r] += dP[c][1];
+                    if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
+                }
+            }
+    double* fe = static_cast<double*>(g.fe) + I.elem_off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double Fc[8], Tm[2][2];
+        lerp2T<double>(Sx[c], Tm);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
+        lerp2T<double>(Sy[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
+        lerp2T<double>(Sz[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
+    }
+}
+
+// Ap = M p c0 + K p (free dofs); partial p . Ap
+__global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int* __restrict__ mask, double c0) {
+    const NodeCtx x = node_ctx(g, mask);
+    double s = 0.0;
+    if (x.ok) {
+        const int i = x.n % (x.I.nx + 1);
+        const int t = x.n / (x.I.nx + 1);
+        const int j = t % (x.I.ny + 1);
+        const int k = t / (x.I.ny + 1);
+        const double* fe = static_cast<const double*>(g.fe) + x.I.elem_off;
+        const double m = 1.0 / g.minv[x.gn];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = (long long)c * g.NN + x.gn;
+            double ap = 0.0;
+            if (is_free(g, x.gn, c)) {
+                const double kp = gather_force<double>(fe, x.I.nx, x.I.ny, x.I.nz, (int)g.NE, i, j, k, c);
+                ap = c0 * m * g.cg_p[d] + kp;
+            }
+            g.cg_ap[d] = ap;
+            s = fma(g.cg_p[d], ap, s);
+        }
+    }
+    s = block_sum1(s);
+    if (threadIdx.x == 0) g.ipart[blockIdx.x] = s;
+}
+
+// x += alpha p, r -= alpha Ap with alpha = (r . z) / (p . Ap); partial r . z of the new residual
+__global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const int* __restrict__ mask, double c0) {
+    const NodeCtx x = node_ctx(g, mask);
+    double s = 0.0;
+    if (x.ok) {
+        const double pap = g.pap[x.inst];
+        const double alpha = pap > 0.0 ? g.rr[x.inst] / pap : 0.0;
+        const double pz = g.minv[x.gn] / c0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long d = (long long)c * g.NN + x.gn;
+            g.cg_x[d] = fma(alpha, g.cg_p[d], g.cg_x[d]);
+            const double r = fma(-alpha, g.cg_ap[d], g.cg_r[d]);
+            g.cg_r[d] = r;
+            s = fma(r * pz, r, s);
+        }
+    }
+    s = block_sum1(s);
+    if (threadIdx.x == 0) g.ipart[blockIdx.x] = s;
+}
+
+// p = z + ((r . z)_new / (r . z)) p; the per-instance r . z is advanced by the kernel after it
+__global__ void __launch_bounds__(kNodeBlock) k_cg_dir_b(const FomB g, const int* __restrict__ mask, double c0) {
+    const NodeCtx x = node_ctx(g, mask);
+    if (!x.ok) return;
+    const double rr = g.rr[x.inst];
+    const double beta = rr > 0.0 ? g.rrn[x.inst] / rr : 0.0;
+    const double pz = g.minv[x.gn] / c0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + x.gn;
+        g.cg_p[d] = fma(beta, g.cg_p[d], g.cg_r[d] * pz);
+    }
+}
+
+__global__ void k_cg_rr_b(const FomB g, const int* __restrict__ mask) {
+    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= g.n_inst || !run(mask, inst)) return;
+    g.rr[inst] = g.rrn[inst];
+}
+
+// u += x on free dofs, refreshed u / h for the force kernel
+__global__ void __launch_bounds__(kNodeBlock) k_imp_update_b(const FomB g, const int* __restrict__ mask) {
+    const NodeCtx x = node_ctx(g, mask);
+    if (!x.ok) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + x.gn;
+        if (is_free(g, x.gn, c)) {
+            const double u = g.u[0][d] + g.cg_x[d];
+            g.u[0][d] = u;
+            g.us[d] = u * x.I.invh;
+        }
+    }
+}
+
+// a = (u - ut) c0, v += dt ((1 - gamma) a_old + gamma a) with gamma = 1/2; Dirichlet / Schwarz data.
+// An instance whose Newton solve failed (non-finite residual, or no convergence within the iteration
+// cap) gets a non-finite displacement, which the convergence criterion reports.
+__global__ void __launch_bounds__(kNodeBlock) k_imp_finish_b(const FomB g, const int* __restrict__ active, int slot1,
+                                                             double dt, double c0) {
+    const NodeCtx x = node_ctx(g, active);
+    if (!x.ok) return;
+    if (g.nact[x.inst] != 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g.u[0][(long long)c * g.NN + x.gn] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    const uint8_t cm = g.clamp[x.gn];
+    const int row = g.srow[x.gn];
+    const double* h1 = g.hist + x.I.hist_off + (long long)slot1 * 9 * x.I.ns;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long d = (long long)c * g.NN + x.gn;
+        if (cm & (1 << c)) {
+            g.v[d] = 0.0;
+            g.a[d] = 0.0;
+        } else if (row >= 0) {
+            g.v[d] = h1[(long long)(3 + c) * x.I.ns + row];
+            g.a[d] = h1[(long long)(6 + c) * x.I.ns + row];
+        } else {
+            const double an = c0 * (g.u[0][d] - g.ut[d]);
+            g.v[d] = g.v[d] + dt * (0.5 * g.a[d] + 0.5 * an);
+            g.a[d] = an;
+        }
+    }
+}
+
+__global__ void k_mask_copy(int n, const int* __restrict__ src, int* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src ? src[i] : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, double dt, cudaStream_t s) {
+    k_imp_predict_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, dt);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
+    k_imp_residual_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s) {
+    k_imp_reduce_b<<<g.n_inst, 128, 0, s>>>(g, mask, mode, first, tol2);
+    return cudaGetLastError();
+}
+cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    if (g.eblock > 256) return cudaErrorInvalidConfiguration;
+    if (g.material == OSAM_NEO_HOOKEAN) k_tangent_b<OSAM_NEO_HOOKEAN><<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    else k_tangent_b<OSAM_LINEAR_ELASTIC><<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
+    k_cg_ap_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
+    k_cg_step_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
+    k_cg_dir_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cg_rr_b<<<(g.n_inst + 127) / 128, 128, 0, s>>>(g, mask);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s) {
+    k_imp_update_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_finish_b(const FomB& g, const int* active, int slot1, double dt, double c0, cudaStream_t s) {
+    k_imp_finish_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, dt, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_mask_copy(int n, const int* src, int* dst, cudaStream_t s) {
+    k_mask_copy<<<(n + 127) / 128, 128, 0, s>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace osam

@@ -86,6 +86,8 @@ struct osam_ctx {
     double* cnum_h = nullptr;
     double* cden_h = nullptr;
     int* any_h = nullptr;
+    int* imp_h = nullptr;                 // pinned mirror of a per-instance Newton / CG activity mask
+    bool any_implicit = false;            // some FOM group integrates implicitly (host-driven steps)
     double* scratch = nullptr;            // device [3 * max nodes of any instance]
     int* err_d = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -119,6 +121,7 @@ struct osam_ctx {
         if (cnum_h) cudaFreeHost(cnum_h);
         if (cden_h) cudaFreeHost(cden_h);
         if (any_h) cudaFreeHost(any_h);
+        if (imp_h) cudaFreeHost(imp_h);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
@@ -275,8 +278,66 @@ int last_trace(osam_ctx* ctx, int s, const int* active) {
     return OSAM_OK;
 }
 
+// any instance of a per-instance mask still set (synchronises the stream)
+int any_set(osam_ctx* ctx, const int* mask, int n, bool& any) {
+    CK(cudaMemcpyAsync(ctx->imp_h, mask, sizeof(int) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    any = false;
+    for (int i = 0; i < n; ++i) any |= ctx->imp_h[i] == 1;
+    return OSAM_OK;
+}
+
+constexpr int kNewtonMax = 25;         // Newton iterations per substep
+constexpr double kNewtonTol2 = 1e-24;  // |R|^2 <= kNewtonTol2 |R(u~)|^2
+constexpr int kCgMax = 1000;           // CG iterations per Newton step
+constexpr int kCgCheck = 8;            // CG iterations between host checks of the activity mask
+constexpr double kCgTol2 = 1e-26;      // r.z <= kCgTol2 (r.z)_0 (mass-preconditioned residual)
+
+// Implicit Newmark interval of FOM slot s (beta = 1/4, gamma = 1/2): per substep the predictor, a
+// Newton solve of M (u - u~) c0 + f_int(u) = 0 (c0 = 1 / (beta dt^2)) with mass-preconditioned
+// conjugate gradients on the exact tangent, the corrector and the traces of the new level.
+// Activity is tracked per instance on the device: Newton (nact: 1 iterating, 0 converged, 2 failed)
+// and CG (cgact); the host reads the masks to end the loops.
+int advance_implicit(osam_ctx* ctx, int s, const int* active) {
+    FomB& g = ctx->slots[s].fom.d;
+    const int n = g.n_inst;
+    const double dt = ctx->dt, c0 = 4.0 / (dt * dt);
+    for (int j = 0; j < ctx->nsub; ++j) {
+        LK(launch_imp_predict_b(g, active, j + 1, dt, ctx->stream));
+        LK(launch_mask_copy(n, active, g.nact, ctx->stream));
+        LK(launch_mask_copy(n, active, g.cgact, ctx->stream));
+        for (int it = 0; it < kNewtonMax; ++it) {
+            LK(launch_force_b(g, g.nact, kGather, ctx->stream, nullptr));
+            LK(launch_imp_residual_b(g, g.nact, c0, ctx->stream));
+            LK(launch_imp_reduce_b(g, g.nact, 0, it == 0, kNewtonTol2, ctx->stream));
+            bool any = false;
+            RET(any_set(ctx, g.nact, n, any));
+            if (!any) break;
+            for (int k = 0; k < kCgMax;) {
+                for (int q = 0; q < kCgCheck; ++q, ++k) {
+                    LK(launch_tangent_b(g, g.cgact, ctx->stream));
+                    LK(launch_cg_ap_b(g, g.cgact, c0, ctx->stream));
+                    LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, ctx->stream));
+                    LK(launch_cg_step_b(g, g.cgact, c0, ctx->stream));
+                    LK(launch_imp_reduce_b(g, g.cgact, 2, 0, kCgTol2, ctx->stream));
+                    LK(launch_cg_dir_b(g, g.cgact, c0, ctx->stream));
+                }
+                bool cg = false;
+                RET(any_set(ctx, g.cgact, n, cg));
+                if (!cg) break;
+            }
+            LK(launch_imp_update_b(g, g.nact, ctx->stream));
+        }
+        LK(launch_imp_finish_b(g, active, j + 1, dt, c0, ctx->stream));
+        for (CplH& c : ctx->cpls)
+            if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[0], j + 1, ctx->stream));
+    }
+    return OSAM_OK;
+}
+
 int advance_slot(osam_ctx* ctx, int s, const int* active) {
     Slot& S = ctx->slots[s];
+    if (S.kind == OSAM_FOM && S.fom.d.implicit) return advance_implicit(ctx, s, active);
     if (S.kind == OSAM_FOM) {
         FomB& g = S.fom.d;
         long long ne = 0;
@@ -299,6 +360,7 @@ int advance_slot(osam_ctx* ctx, int s, const int* active) {
 bool pipelined_pair(const osam_ctx* ctx, int s) {
     if (s + 1 >= (int)ctx->slots.size()) return false;
     if (ctx->slots[s].kind != OSAM_FOM || ctx->slots[s + 1].kind != OSAM_ROM) return false;
+    if (ctx->slots[s].fom.d.implicit) return false;
     bool fed = false;
     for (const CplH& c : ctx->cpls) {
         if (c.dst != s + 1 || c.src > s) continue;
@@ -496,6 +558,12 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
                 return ctx->fail(OSAM_EINVAL, "subdomain %d: bad material", s);
             if (a.kind == OSAM_FOM && !(a.rho > 0.0))
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: rho must be positive", i, s);
+            if (a.kind == OSAM_FOM && a.integrator != OSAM_EXPLICIT && a.integrator != OSAM_IMPLICIT)
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: bad integrator", i, s);
+            if (a.kind == OSAM_FOM && a.integrator != b.integrator)
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: integrator differs from instance 0", i, s);
+            if (a.kind == OSAM_FOM && a.integrator == OSAM_IMPLICIT && d0.precision != OSAM_FP64)
+                return ctx->fail(OSAM_EINVAL, "subdomain %d: implicit integration needs OSAM_FP64", s);
         }
         for (int k = 0; k < d0.n_couplings; ++k) {
             if (!d.couplings || d.couplings[k].dst != d0.couplings[k].dst || d.couplings[k].src != d0.couplings[k].src ||
@@ -551,7 +619,7 @@ int check_stability(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         double m;
         std::memcpy(&m, &mh[i], sizeof(double));
         const double lim = G.grid[i].h * std::sqrt(descs[i].subdomains[s].rho / m);
-        if (ctx->dt > lim * (1.0 + 1e-9))
+        if (!G.d.implicit && ctx->dt > lim * (1.0 + 1e-9))
             return ctx->fail(OSAM_ECFL, "instance %d subdomain %d: dt = %.6e above the explicit stability limit "
                                         "%.6e", i, s, ctx->dt, lim);
     }
@@ -615,6 +683,20 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     CKA(B.hist = ctx->alloc<double>(std::max<long long>(H, 1)));
     CKA(B.us = ctx->alloc<double>(3 * NN));
     if (B.df32) CKA(B.u2 = ctx->alloc<float2>(3 * NN));
+    B.implicit = descs[0].subdomains[s].integrator == OSAM_IMPLICIT;
+    if (B.implicit) {
+        ctx->any_implicit = true;
+        CKA(B.ut = ctx->alloc<double>(3 * NN));
+        CKA(B.cg_x = ctx->alloc<double>(3 * NN));
+        CKA(B.cg_r = ctx->alloc<double>(3 * NN));
+        CKA(B.cg_p = ctx->alloc<double>(3 * NN));
+        CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
+        for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap}) CKA(*p = ctx->alloc<double>(n));
+        CKA(B.nact = ctx->alloc<int>(n));
+        CKA(B.cgact = ctx->alloc<int>(n));
+        CK(cudaMemsetAsync(B.nact, 0, sizeof(int) * n, ctx->stream));
+        CK(cudaMemsetAsync(B.cgact, 0, sizeof(int) * n, ctx->stream));
+    }
     bool any_le = false, any_me = false;
     for (int i = 0; i < n; ++i) {
         any_le |= descs[i].subdomains[s].lambda_e != nullptr;
@@ -663,6 +745,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     B.n_nblk = (int)G.nblk.size();
     B.nblk_off = nbo;
     CKA(B.partial = ctx->alloc<double>(2LL * B.n_nblk));
+    if (B.implicit) CKA(B.ipart = ctx->alloc<double>(2LL * B.n_nblk));
     RET(set_eblocks(ctx, G, 128));
     RET(set_tiles(ctx, G));
     RET(check_stability(ctx, G, s, n, descs));
@@ -962,6 +1045,7 @@ int setup_controller(osam_ctx* ctx) {
     CK(cudaMallocHost(&ctx->cnum_h, sizeof(double) * n));
     CK(cudaMallocHost(&ctx->cden_h, sizeof(double) * n));
     CK(cudaMallocHost(&ctx->any_h, sizeof(int)));
+    CK(cudaMallocHost(&ctx->imp_h, sizeof(int) * n));
     return OSAM_OK;
 }
 
@@ -1274,7 +1358,7 @@ int osam_criterion(osam_ctx* ctx, double* cnum, double* cden) {
 
 int osam_batch_step(osam_ctx* ctx, osam_step_report* reps, osam_step_report* total) {
     if (!ctx) return OSAM_EINVAL;
-    const bool graph = ctx->use_graph && !ctx->prof;
+    const bool graph = ctx->use_graph && !ctx->prof && !ctx->any_implicit;
     if (graph) RET(build_graph(ctx));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (graph) {

@@ -93,6 +93,22 @@ struct FomB {
     const int4* tblk;         // 8x4x4 element tiles: (instance, i0, j0, k0)
     int n_tblk;
     int tiled;                // 1: FP64 force by tiles (shared edge interpolation)
+    // implicit Newmark (average acceleration) groups: Newton with a matrix-free CG per substep
+    int implicit;
+    double* ut;               // predictor [3][NN]
+    double* cg_x;             // Newton increment [3][NN]
+    double* cg_r;             // CG residual [3][NN]
+    double* cg_p;             // CG direction [3][NN]
+    double* cg_ap;            // tangent times direction [3][NN]
+    double* ipart;            // partial sums, two per node block
+    double* rn2;              // per instance: squared Newton residual
+    double* r0;               // per instance: squared residual of the predictor
+    double* rr;               // per instance: r . z of the current CG iterate (z = M^-1 r / c0)
+    double* rrn;              // per instance: r . z after the update
+    double* rr0;              // per instance: r . z at the start of the CG solve
+    double* pap;              // per instance: p . A p
+    int* nact;                // per instance Newton state: 1 iterating, 0 converged, 2 failed
+    int* cgact;               // per instance: CG still iterating
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 
@@ -210,6 +226,20 @@ cudaError_t launch_rom_norms_b(const RomB& r, const int* active, double dt, cuda
 cudaError_t launch_saverest_rom_b(const RomB& r, const int* active, int restore, cudaStream_t s);
 cudaError_t launch_reset_ctl(const CtlB& c, cudaStream_t s);
 cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int use_cond, cudaStream_t s);
+
+// implicit Newmark, beta = 1/4, gamma = 1/2 (implicit_kernels.cu); `mask` = per-instance activity
+cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, double dt, cudaStream_t s);
+cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
+// reduce the node-block partials per instance; mode 0: Newton residual (sets rn2, r0 on the first
+// iteration, rr, rr0, nact, cgact), 1: p . Ap, 2: r . z after a CG update (sets rrn, cgact)
+cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s);
+cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
+cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
+cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
+cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
+cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s);
+cudaError_t launch_imp_finish_b(const FomB& g, const int* active, int slot1, double dt, double c0, cudaStream_t s);
+cudaError_t launch_mask_copy(int n, const int* src, int* dst, cudaStream_t s);
 
 // ROM set-up and I/O (rom_kernels.cu)
 cudaError_t launch_rom_basis_project(int nfree, int r, const double* Phi, const int* free_dof, const double* u_aos,

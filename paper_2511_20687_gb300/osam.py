@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libosam.so")
 OK, MAXITER, EINVAL, ECFL, ENONFINITE, EDONOR, ECUDA, ETIMEOUT, ENOMEM = 0, 1, -1, -2, -3, -4, -5, -6, -7
 FOM, ROM = 0, 1
 LINEAR_ELASTIC, NEO_HOOKEAN = 0, 1
+EXPLICIT, IMPLICIT = 0, 1
 FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG, SCATTER_GATHER_TILED = 0, 1, 2, 3, 4
 
@@ -45,7 +46,7 @@ class SubdomainDesc(C.Structure):
                 ("origin", C.c_double * 3), ("material", C.c_int), ("lambda_", C.c_double), ("mu", C.c_double),
                 ("rho", C.c_double), ("lambda_e", _vp), ("mu_e", _vp), ("dirichlet", _vp), ("u0", _vp), ("v0", _vp),
                 ("r", C.c_int), ("r_s", C.c_int), ("Phi", _vp), ("Phi_S", _vp), ("K", _vp), ("H", _vp), ("B", _vp),
-                ("c", _vp)]
+                ("c", _vp), ("integrator", C.c_int)]
 
 
 class CouplingDesc(C.Structure):
@@ -224,6 +225,7 @@ class Batch:
                 d.h = sd.h
                 d.origin = (C.c_double * 3)(*sd.origin)
                 d.material = _MAT[sd.material]
+                d.integrator = {"explicit": EXPLICIT, "implicit": IMPLICIT}[getattr(sd, "integrator", "explicit")]
                 d.lambda_, d.mu, d.rho = sd.lam, sd.mu, sd.rho
                 arrs = {"lambda_e": _f64(sd.lam_e), "mu_e": _f64(sd.mu_e), "dirichlet": _u8(sd.dirichlet),
                         "u0": _f64(sd.u0), "v0": _f64(sd.v0)}
