@@ -75,6 +75,7 @@ def lib():
             L.orc_couple.argtypes = [C.c_void_p, C.c_int, C.c_int, _u8]
             L.orc_init.argtypes = [C.c_void_p]
             L.orc_set_implicit.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_set_substeps.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_step.argtypes = [C.c_void_p, _i, _d, _d]
             L.orc_num_nodes.argtypes = [C.c_void_p, C.c_int]
             L.orc_num_free.argtypes = [C.c_void_p, C.c_int]
@@ -244,6 +245,8 @@ class Problem:
                 self.rank[i] = r
                 rc = L.orc_add_rom(self.h, nx, ny, nz, sd.h, _p(org), _p(dm), r, rs, arrs[0].shape[0],
                                    arrs[1].shape[0], *[_p(a) for a in arrs], _p(u0), _p(v0))
+            if rc >= 0 and getattr(sd, "n_substeps", 0):
+                rc = L.orc_set_substeps(self.h, i, int(sd.n_substeps))
             if rc < 0:
                 raise OracleError(rc, f"oracle add subdomain {i}")
         for cp in spec.couplings:

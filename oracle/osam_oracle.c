@@ -14,11 +14,13 @@
  *     coefficient of S is 1/3, obtained by differentiating the printed energy A_dev (the printed 1/2
  *     disagrees with that energy; tests pin P against finite differences of A).
  *   - row-sum lumped mass (each element gives rho*V_e/8 to each of its nodes; Sec. 5 setup)
- *   - explicit Newmark (beta = 0, gamma = 1/2) in predictor / corrector form (Sec. 4.1)
+ *   - explicit Newmark (beta = 0, gamma = 1/2) in predictor / corrector form (Sec. 4.1), and implicit
+ *     Newmark (beta = 1/4, gamma = 1/2) solved by Newton's method with the exact tangent
  *   - O-SAM controller of Algorithm 1 / Eq. schwarz_discrete with the criterion conv_criterion:
  *     multiplicative sweep over the subdomains in index order, pointwise spatial projector Pi
  *     (trilinear interpolation in a donor element found by brute-force search and Newton inversion
- *     of the trilinear map), identity temporal interpolant (equal time steps).
+ *     of the trilinear map), temporal interpolant Xi linear between the source's time levels
+ *     (identity when the time steps agree); each subdomain has its own number of substeps.
  *   - quadratic OpInf ROM subdomain of Eq. schwarz_opinf_discrete, written in the solved form
  *     qdd = K q + H kron_c(q) + B ghat + c, with ghat = Phi_S^T s (boundary POD, Sec. 4.2.1) and the
  *     ROM -> FOM trace Pi (Phi q) built from the reconstructed full field.
@@ -659,6 +661,9 @@ typedef struct {
     int rs_rows;          /* declared row count of PhiS */
     /* time integrator of a FOM: 0 explicit central differences, 1 implicit average acceleration */
     int implicit;
+    /* substeps per controller interval and their length (Sec. 4.1: Delta t_i = (t_k - t_{k-1}) / n_i) */
+    int nsub;
+    double dt;
 } osub;
 
 typedef struct {
@@ -667,6 +672,7 @@ typedef struct {
     int* row;    /* Schwarz row of dst */
     int* dnode;  /* [nrow][8] donor nodes in src */
     double* dw;  /* [nrow][8] weights */
+    double* rec; /* src trace Pi(u, v, a) at the src's time levels [(nsub_src+1)][3 fields][nrow][3] */
 } ocpl;
 
 typedef struct {
@@ -698,7 +704,9 @@ void orc_problem_free(void* vp) {
     oprob* p = (oprob*)vp;
     if (!p) return;
     for (int i = 0; i < p->nsd; ++i) sub_free(&p->sd[i]);
-    for (int i = 0; i < p->ncpl; ++i) { free(p->cpl[i].row); free(p->cpl[i].dnode); free(p->cpl[i].dw); }
+    for (int i = 0; i < p->ncpl; ++i) {
+        free(p->cpl[i].row); free(p->cpl[i].dnode); free(p->cpl[i].dw); free(p->cpl[i].rec);
+    }
     free(p);
 }
 
@@ -714,6 +722,8 @@ static osub* add_common(oprob* p, int kind, int nx, int ny, int nz, double h, co
     osub* s = &p->sd[p->nsd++];
     memset(s, 0, sizeof(*s));
     s->kind = kind;
+    s->nsub = p->nsub;
+    s->dt = p->dt;
     mesh_set(&s->m, nx, ny, nz, h, org);
     size_t nn = (size_t)s->m.nn;
     s->dmask = (unsigned char*)xcalloc(nn, 1);
@@ -811,12 +821,12 @@ static double rom_field(const oprob* p, const osub* s, int field, int n, int c, 
     return val;
 }
 
-/* write Pi(src fields) into dst history slot `slot` for coupling cp.
- * FOM src: from its current (u, v, a).  ROM src: from its recorded reduced history at `slot`. */
-static void transfer_slot(oprob* p, const ocpl* cp, int slot, int zoh) {
-    osub* d = &p->sd[cp->dst];
+/* record Pi(src fields) at the src's time level `level` into the coupling's trace (Sec. 4.1, the
+ * pointwise spatial projector).  FOM src: from its current (u, v, a).  ROM src: from its recorded
+ * reduced history at `level`, or from its current (q, qd, qdd) when zoh is set. */
+static void trace_level(oprob* p, const ocpl* cp, int level, int zoh) {
     const osub* s = &p->sd[cp->src];
-    size_t ns = (size_t)d->ns;
+    size_t nr = (size_t)cp->nrow;
     for (int i = 0; i < cp->nrow; ++i) {
         for (int f = 0; f < 3; ++f)
             for (int c = 0; c < 3; ++c) {
@@ -832,14 +842,53 @@ static void transfer_slot(oprob* p, const ocpl* cp, int slot, int zoh) {
                     } else {
                         const double* qv;
                         if (zoh) qv = f == 0 ? s->q : (f == 1 ? s->qd : s->qdd);
-                        else qv = s->qrec + ((size_t)slot * 3 + f) * s->r;
-                        x = rom_field(p, s, f, n, c, qv, slot);
+                        else qv = s->qrec + ((size_t)level * 3 + f) * s->r;
+                        x = rom_field(p, s, f, n, c, qv, zoh ? 0 : level);
                     }
                     val += w * x;
                 }
-                d->hist[((size_t)slot * 3 + f) * ns * 3 + (size_t)cp->row[i] * 3 + c] = val;
+                cp->rec[((size_t)level * 3 + f) * nr * 3 + (size_t)i * 3 + c] = val;
             }
     }
+}
+
+/* Temporal interpolant Xi (Sec. 4.1, Fig. schwarz_time_discretization): the data of dst level m
+ * (time t_{k-1} + m T / n_dst) from the src trace at levels l = 0..n_src (times t_{k-1} + l T / n_src),
+ * linear between the two levels that bracket it; an exact level is copied. */
+static void publish(oprob* p, const ocpl* cp) {
+    osub* d = &p->sd[cp->dst];
+    int ns_ = p->sd[cp->src].nsub, nd = d->nsub;
+    size_t nr = (size_t)cp->nrow, dns = (size_t)d->ns;
+    for (int m = 1; m <= nd; ++m) {
+        long long num = (long long)m * ns_;
+        int l = (int)(num / nd);
+        long long rem = num - (long long)l * nd;
+        double w = (double)rem / (double)nd;
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < cp->nrow; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    double x0 = cp->rec[((size_t)l * 3 + f) * nr * 3 + (size_t)i * 3 + c];
+                    double val = x0;
+                    if (rem != 0) {
+                        double x1 = cp->rec[((size_t)(l + 1) * 3 + f) * nr * 3 + (size_t)i * 3 + c];
+                        val = (1.0 - w) * x0 + w * x1;
+                    }
+                    d->hist[((size_t)m * 3 + f) * dns * 3 + (size_t)cp->row[i] * 3 + c] = val;
+                }
+    }
+}
+
+/* zero-order hold of the src's current state: trace level 0 and every dst level */
+static void zoh(oprob* p, const ocpl* cp) {
+    osub* d = &p->sd[cp->dst];
+    size_t nr = (size_t)cp->nrow, dns = (size_t)d->ns;
+    trace_level(p, cp, 0, 1);
+    for (int m = 0; m <= d->nsub; ++m)
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < cp->nrow; ++i)
+                for (int c = 0; c < 3; ++c)
+                    d->hist[((size_t)m * 3 + f) * dns * 3 + (size_t)cp->row[i] * 3 + c] =
+                        cp->rec[((size_t)f) * nr * 3 + (size_t)i * 3 + c];
 }
 
 /* ROM right-hand side: K q + H kron_c(q) + B ghat + c, kron_c(q) = (q_i q_j)_{i<=j} row-major */
@@ -876,6 +925,15 @@ int orc_set_implicit(void* vp, int i, int implicit) {
     return ORC_OK;
 }
 
+/* substeps of subdomain i per controller interval (its time step is the interval length over n) */
+int orc_set_substeps(void* vp, int i, int n) {
+    oprob* p = (oprob*)vp;
+    if (i < 0 || i >= p->nsd || n < 1 || p->initialised) return ORC_EINVAL;
+    p->sd[i].nsub = n;
+    p->sd[i].dt = n == p->nsub ? p->dt : (p->dt * (double)p->nsub) / (double)n;
+    return ORC_OK;
+}
+
 int orc_init(void* vp) {
     oprob* p = (oprob*)vp;
     /* explicit stability: every FOM subdomain's time step within its element bound (a relative
@@ -886,7 +944,7 @@ int orc_init(void* vp) {
         double lim = orc_stable_dt(s->m.nx, s->m.ny, s->m.nz, s->m.h, s->m.org, s->lam, s->mu, s->lam_e, s->mu_e,
                                    s->rho);
         if (!(lim > 0.0)) return ORC_EINVAL;
-        if (p->dt > lim * (1.0 + 1e-9)) return ORC_ECFL;
+        if (s->dt > lim * (1.0 + 1e-9)) return ORC_ECFL;
     }
     /* Schwarz rows: union of the coupling masks, increasing node order */
     for (int i = 0; i < p->nsd; ++i) {
@@ -902,7 +960,7 @@ int orc_init(void* vp) {
         s->snode = (int*)xcalloc((size_t)ns, sizeof(int));
         for (int n = 0; n < s->m.nn; ++n)
             if (s->srow[n] >= 0) s->snode[s->srow[n]] = n;
-        s->hist = dup_or_zero(NULL, (size_t)(p->nsub + 1) * 3 * ns * 3);
+        s->hist = dup_or_zero(NULL, (size_t)(s->nsub + 1) * 3 * ns * 3);
     }
     /* couplings: donor search */
     for (int k = 0; k < p->ncpl; ++k) {
@@ -927,6 +985,7 @@ int orc_init(void* vp) {
         }
         free(mask);
         cp->row = row;
+        cp->rec = dup_or_zero(NULL, (size_t)(s->nsub + 1) * 3 * (size_t)cnt * 3);
     }
     for (int k = 0; k < p->ncpl; ++k) {
         ocpl* cp = &p->cpl[k];
@@ -948,7 +1007,7 @@ int orc_init(void* vp) {
         for (int n = 0; n < s->m.nn; ++n)
             for (int c = 0; c < 3; ++c)
                 if (is_free(s, n, c)) s->free_dof[t++] = 3 * n + c;
-        s->qrec = dup_or_zero(NULL, (size_t)(p->nsub + 1) * 3 * s->r);
+        s->qrec = dup_or_zero(NULL, (size_t)(s->nsub + 1) * 3 * s->r);
         /* q0 = Phi^T u0, qd0 = Phi^T v0 over the free dofs */
         for (int k = 0; k < s->r; ++k) {
             double a = 0.0, b = 0.0;
@@ -960,8 +1019,7 @@ int orc_init(void* vp) {
         }
     }
     /* initial boundary data: zero-order hold of the sources' initial states in every slot */
-    for (int k = 0; k < p->ncpl; ++k)
-        for (int j = 0; j <= p->nsub; ++j) transfer_slot(p, &p->cpl[k], j, 1);
+    for (int k = 0; k < p->ncpl; ++k) zoh(p, &p->cpl[k]);
     /* initial accelerations */
     for (int i = 0; i < p->nsd; ++i) {
         osub* s = &p->sd[i];
@@ -1055,8 +1113,9 @@ static int dense_spd_solve(double* A, int n, double* b) {
 /* One implicit substep of FOM subdomain s with boundary data h1 (history slot of the new level).
  * Predictor ut = u + dt v + (1/2 - beta) dt^2 a on free dofs; solve R(u) = M (u - ut) / (beta dt^2)
  * + f_int(u) = 0 by Newton's method with the exact tangent M / (beta dt^2) + K(u) (assembled densely,
- * Cholesky), until |R| <= 1e-12 |R(ut)| (at most 25 iterations); then a = (u - ut) / (beta dt^2) and
- * v += dt ((1 - gamma) a_old + gamma a).  Returns 0, or -3 for a non-finite or failed solve. */
+ * Cholesky), until |R| <= 1e-12 |R(ut)| or an increment |du|^2 <= 1e-28 |u|^2 (at most 25 iterations);
+ * then a = (u - ut) / (beta dt^2) and v += dt ((1 - gamma) a_old + gamma a).  Returns 0, or -3 for a
+ * non-finite or failed solve. */
 static int implicit_substep(osub* s, double dt, const double* h1, size_t ns) {
     const double beta = 0.25, gamma = 0.5, c0 = 1.0 / (beta * dt * dt);
     size_t nn = (size_t)s->m.nn;
@@ -1113,8 +1172,16 @@ static int implicit_substep(osub* s, double dt, const double* h1, size_t ns) {
         }
         for (int k = 0; k < nf; ++k) R[k] = -R[k];
         if (!dense_spd_solve(J, nf, R)) break;
+        double du2 = 0.0, u2 = 0.0;
         for (size_t d = 0; d < 3 * nn; ++d)
-            if (fid[d] >= 0) s->u[d] += R[fid[d]];
+            if (fid[d] >= 0) {
+                s->u[d] += R[fid[d]];
+                du2 += R[fid[d]] * R[fid[d]];
+                u2 += s->u[d] * s->u[d];
+            }
+        /* an increment at the rounding level of u ends the iteration as well (reading: the predictor
+         * may already solve the system to rounding, where the relative residual test cannot be met) */
+        if (du2 <= 1e-28 * u2) { status = 0; break; }
     }
     if (status == 0) {
         for (size_t n = 0; n < nn; ++n)
@@ -1137,22 +1204,22 @@ static int implicit_substep(osub* s, double dt, const double* h1, size_t ns) {
 
 static void advance(oprob* p, int i) {
     osub* s = &p->sd[i];
-    double dt = p->dt;
+    double dt = s->dt;
     size_t ns = (size_t)s->ns;
     if (s->kind == ORC_FOM && s->implicit) {
-        for (int j = 0; j < p->nsub; ++j) {
+        for (int j = 0; j < s->nsub; ++j) {
             const double* h1 = s->hist + (size_t)(j + 1) * 3 * ns * 3;
             if (implicit_substep(s, dt, h1, ns) != 0) {
                 /* a failed Newton solve leaves a non-finite state for the criterion to report */
                 for (size_t d = 0; d < 3 * (size_t)s->m.nn; ++d) s->u[d] = NAN;
             }
             for (int k = 0; k < p->ncpl; ++k)
-                if (p->cpl[k].src == i) transfer_slot(p, &p->cpl[k], j + 1, 0);
+                if (p->cpl[k].src == i) trace_level(p, &p->cpl[k], j + 1, 0);
         }
     } else if (s->kind == ORC_FOM) {
         size_t nn = (size_t)s->m.nn;
         double* f = (double*)xcalloc(3 * nn, sizeof(double));
-        for (int j = 0; j < p->nsub; ++j) {
+        for (int j = 0; j < s->nsub; ++j) {
             const double* h1 = s->hist + (size_t)(j + 1) * 3 * ns * 3;
             /* predictor on free dofs, Dirichlet data on constrained dofs */
             for (size_t n = 0; n < nn; ++n)
@@ -1177,15 +1244,15 @@ static void advance(oprob* p, int i) {
                         s->a[d] = an;
                     }
                 }
-            /* publish this substep's trace to every subdomain that takes data from this one */
+            /* record this substep's trace for every subdomain that takes data from this one */
             for (int k = 0; k < p->ncpl; ++k)
-                if (p->cpl[k].src == i) transfer_slot(p, &p->cpl[k], j + 1, 0);
+                if (p->cpl[k].src == i) trace_level(p, &p->cpl[k], j + 1, 0);
         }
         free(f);
     } else {
         double* qn = (double*)xcalloc((size_t)s->r, sizeof(double));
         rom_record(s, 0);
-        for (int j = 0; j < p->nsub; ++j) {
+        for (int j = 0; j < s->nsub; ++j) {
             for (int k = 0; k < s->r; ++k) s->q[k] += dt * s->qd[k] + 0.5 * dt * dt * s->qdd[k];
             rom_ghat(s, j + 1);
             rom_rhs(s, s->q, s->ghat, qn);
@@ -1196,11 +1263,14 @@ static void advance(oprob* p, int i) {
             rom_record(s, j + 1);
         }
         free(qn);
-        /* ROM -> neighbours: Pi (Phi q) at every recorded slot */
+        /* ROM -> neighbours: Pi (Phi q) at every recorded level */
         for (int k = 0; k < p->ncpl; ++k)
             if (p->cpl[k].src == i)
-                for (int j = 1; j <= p->nsub; ++j) transfer_slot(p, &p->cpl[k], j, 0);
+                for (int j = 1; j <= s->nsub; ++j) trace_level(p, &p->cpl[k], j, 0);
     }
+    /* the interval's trace, mapped onto each destination's time levels */
+    for (int k = 0; k < p->ncpl; ++k)
+        if (p->cpl[k].src == i) publish(p, &p->cpl[k]);
 }
 
 static void save_state(oprob* p) {
@@ -1236,9 +1306,10 @@ static void restore_state(oprob* p) {
 /* criterion conv_criterion at t_k: numerator sum_i ||du_i + dt dv_i||^2, denominator
  * sum_i ||u_i + dt v_i||^2 over free dofs (ROM: over q, qd); then remember this iterate */
 static void criterion(oprob* p, double* cnum, double* cden, int* nonfinite) {
-    double num = 0.0, den = 0.0, dt = p->dt;
+    double num = 0.0, den = 0.0;
     for (int i = 0; i < p->nsd; ++i) {
         osub* s = &p->sd[i];
+        double dt = s->dt;
         if (s->kind == ORC_FOM) {
             for (int n = 0; n < s->m.nn; ++n)
                 for (int c = 0; c < 3; ++c) {
@@ -1273,8 +1344,7 @@ int orc_step(void* vp, int* iters, double* cnum_out, double* cden_out) {
     if (!p->initialised) return ORC_EINVAL;
     save_state(p);
     /* zero-order hold of every source's state at t_{k-1} over all slots */
-    for (int k = 0; k < p->ncpl; ++k)
-        for (int j = 0; j <= p->nsub; ++j) transfer_slot(p, &p->cpl[k], j, 1);
+    for (int k = 0; k < p->ncpl; ++k) zoh(p, &p->cpl[k]);
     int n, status = ORC_MAXITER;
     double cnum = 0.0, cden = 0.0;
     for (n = 1; n <= p->max_it; ++n) {
@@ -1317,7 +1387,7 @@ int orc_get_state(void* vp, int i, double* u, double* v, double* a) {
     for (int f = 0; f < 3; ++f) {
         if (!outs[f]) continue;
         for (int n = 0; n < s->m.nn; ++n)
-            for (int c = 0; c < 3; ++c) outs[f][3 * n + c] = rom_field(p, s, f, n, c, qs[f], p->nsub);
+            for (int c = 0; c < 3; ++c) outs[f][3 * n + c] = rom_field(p, s, f, n, c, qs[f], s->nsub);
     }
     return ORC_OK;
 }

@@ -45,6 +45,7 @@ class Subdomain:
     u0: Optional[np.ndarray] = None          # [N, 3]
     v0: Optional[np.ndarray] = None          # [N, 3]
     integrator: str = "explicit"             # FOM time integrator: "explicit" (central differences) or "implicit"
+    n_substeps: int = 0                      # substeps per controller step (0: the problem's n_substeps)
 
     @property
     def n_nodes(self) -> int:

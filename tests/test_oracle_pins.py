@@ -499,3 +499,84 @@ def test_implicit_fom_fom_schwarz_converges_to_single_domain(oracle):
     for i, k0 in ((0, 0), (1, 6)):
         u = A.state(i)[0]
         assert np.abs(u - us[k0 * nn:k0 * nn + u.shape[0]]).max() < 1e-7 * np.abs(us).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# different time steps per subdomain (temporal interpolant Xi of Sec. 4.1)
+# ---------------------------------------------------------------------------------------------
+def _translating_pair(material, n_sub, integrators):
+    """Two overlapping unclamped 3x3x6 FOMs moving as a rigid body at constant velocity V: the exact
+    solution u = V t, v = V, a = 0 is reproduced by both integrators, so the coupled run stays exact
+    to rounding whatever the time levels of each subdomain, provided every Schwarz datum is taken at
+    the right time (a misplaced level or weight shears the overlap at O(|V| dt))."""
+    p = W.bar_chain("trans", 3, [6, 6], ["fom", "fom"], material, 1e9, 0.25, 1000.0, 0.0, 1e-6, 6, max_iters=10)
+    V = np.array([0.3, -0.2, 0.5])
+    for sd, n, integ in zip(p.subdomains, n_sub, integrators):
+        sd.dirichlet = np.zeros(sd.n_nodes, np.uint8)
+        sd.u0 = np.zeros((sd.n_nodes, 3))
+        sd.v0 = np.tile(V, (sd.n_nodes, 1))
+        sd.n_substeps = n
+        sd.integrator = integ
+    return p, V
+
+
+@pytest.mark.parametrize("n_sub", [(6, 6), (6, 4), (5, 3), (3, 7)])
+@pytest.mark.parametrize("integrators", [("explicit", "explicit"), ("explicit", "implicit")])
+def test_mixed_time_steps_keep_rigid_translation_exact(oracle, n_sub, integrators):
+    p, V = _translating_pair("nh", n_sub, integrators)
+    prob = oracle.Problem(p)
+    t = 0.0
+    for _ in range(3):
+        r = prob.step()
+        assert r["status"] == oracle.OK
+        t += p.dt * p.n_substeps
+    for i in range(2):
+        u, v, a = prob.state(i)
+        assert np.abs(u - V * t).max() < 1e-13 * np.abs(V).max() * t
+        assert np.abs(v - V).max() < 1e-12 * np.abs(V).max()
+        assert np.abs(a).max() < 1e-6 * np.abs(V).max() / p.dt
+
+
+def test_mixed_time_steps_equal_counts_reduce_to_the_common_step(oracle):
+    """Setting every subdomain's substep count to the problem's is the plain common-step run."""
+    p = W.bar_chain("eq", 3, [6, 6], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+    A = oracle.Problem(p)
+    for sd in p.subdomains:
+        sd.n_substeps = 5
+    B = oracle.Problem(p)
+    for _ in range(2):
+        A.step()
+        B.step()
+    for i in range(2):
+        for f in range(3):
+            assert np.array_equal(A.state(i)[f], B.state(i)[f])
+
+
+def test_mixed_time_steps_converge_at_second_order(oracle):
+    """Omega_1 explicit with n substeps, Omega_2 implicit with n/2 (the paper's explicit / implicit
+    pairing with Delta t_2 = 2 Delta t_1): against a single-domain run with a step 8x finer than the
+    finest coupled one, the error falls ~4x per halving of both steps (the linear interpolant and both
+    integrators are second order; conforming overlap meshes add no spatial coupling error)."""
+    T = 2e-5
+    ref_p = W.single_bar("ref", 3, 14, "le", 1e9, 0.25, 1000.0, 1e-3, T / 256, 256)
+    ref = oracle.Problem(ref_p)
+    for _ in range(2):
+        ref.step()
+    uref = ref.state(0)[0]
+    nn = 4 * 4
+    errs = []
+    for n in (8, 16, 32):
+        p = W.bar_chain("mix", 3, [8, 8], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, T / n, n, tol_rel=1e-13,
+                        max_iters=60)
+        p.subdomains[1].integrator = "implicit"
+        p.subdomains[1].n_substeps = n // 2
+        prob = oracle.Problem(p)
+        for _ in range(2):
+            assert prob.step()["status"] == oracle.OK
+        e = 0.0
+        for i, k0 in ((0, 0), (1, 6)):
+            u = prob.state(i)[0]
+            e = max(e, np.abs(u - uref[k0 * nn:k0 * nn + u.shape[0]]).max())
+        errs.append(e)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, errs
