@@ -60,6 +60,12 @@ FORCE_TRAFFIC = {"source_sha256": "7b75524b888890d04e6831c55ebaea5cea934da54f34e
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
+# FP64 flops of one Neo-Hookean element tangent action K(u) p (implicit Newton-CG; FMA = 2 flops, the
+# cube root counted as one flop): scaling of p 24 + differences of u and p 72 + their interpolation
+# to the Gauss points 360 + 8 x 243 directional derivative of P (F, cof F and its derivative, J,
+# traces, scalar chain, dP) + 36 accumulation + 180 transposed interpolation + 48 nodal accumulation
+# + 6 material constants.
+TANGENT_FLOPS_PER_NH_ELEMENT = 2670
 
 
 def measured_hbm_gbs():
@@ -93,6 +99,9 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--batched-plain-steps", type=int, default=1)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain parameter sweep")
+    ap.add_argument("--no-implicit", action="store_true", help="skip the implicit-FOM measurement")
+    ap.add_argument("--implicit-only", action="store_true",
+                    help="run only the implicit-FOM block (stand-in ROM operators): profiling runs")
     ap.add_argument("--fom-only", action="store_true",
                     help="FOM-FOM coupling of the same geometry (no ROM, no training): profiling runs")
     return ap.parse_args()
@@ -398,6 +407,74 @@ def measure_adjoint(W, osam, local, log, oracle_steps=40):
             "timing": "library CUDA events around the whole adjoint call (best of 3 after a warm-up)"}
 
 
+def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, oracle_dims=(4, 4, 8),
+                     max_iters=None, warmup=1):
+    """Implicit Newmark FOM (beta = 1/4, gamma = 1/2; Newton with mass-preconditioned matrix-free CG)
+    in the headline hybrid: the same 40x40x80 Neo-Hookean FOM and fitted ROM, the FOM integrated
+    implicitly at the same dt (host-driven steps, no graph).  Metric as the headline (FOM
+    element-updates/s) plus Newton / CG counts and the tangent-action kernel's FP64 roofline; the
+    oracle (dense assembled tangent, Cholesky) and the GPU on a bounded sample: a small implicit
+    Neo-Hookean bar."""
+    from oracle import oracle as O
+    spec = hybrid_spec(W, args)
+    spec.subdomains[0].integrator = "implicit"
+    if max_iters:
+        spec.max_iters = max_iters
+    prob = osam.Problem(spec, rom_ops=rom_ops, device=local)
+    for _ in range(warmup):
+        prob.step()
+    prob.profile(True)
+    total_ms, upd, its = 0.0, 0, []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        r = prob.step()
+        total_ms += r["elapsed_ms"]
+        upd += r["element_updates"]
+        its.append(r["iterations"])
+    ip = prob.implicit_profile()
+    prof = prob.profile_read()
+    prob.profile(False)
+    prob.close()
+    ne = spec.subdomains[0].n_elements
+    substeps = 20 * sum(its)
+    achieved = TANGENT_FLOPS_PER_NH_ELEMENT * ip["tangent_elements"] / (ip["tangent_ms"] * 1e-3) / 1e12
+    # bounded sample: a small implicit Neo-Hookean bar, 1 controller step of 4 substeps, both sides
+    sample = W.single_bar("imp_sample", oracle_dims[0], oracle_dims[2], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 4)
+    sample.subdomains[0].integrator = "implicit"
+    g = osam.Problem(sample, device=local)
+    g.step()
+    rg = g.step()
+    g.close()
+    ref = O.Problem(sample)
+    t0 = time.process_time()
+    ref.step()
+    cpu_s = time.process_time() - t0
+    ns = sample.subdomains[0].n_elements * 4
+    log(f"implicit: {total_ms / steps:.1f} ms/step, {ip['newton_steps'] / max(1, substeps):.2f} Newton/substep, "
+        f"{ip['cg_iterations'] / max(1, ip['newton_steps']):.1f} CG/Newton, tangent {achieved:.3f} TFLOP/s")
+    return {"workload": f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} Neo-Hookean FOM integrated implicitly "
+                        f"(Newmark beta=1/4, gamma=1/2) + r={args.rank} OpInf ROM, dt=1e-6, 20 substeps",
+            "unit": UNIT, "value": upd / (total_ms * 1e-3), "ms_per_step": total_ms / steps, "steps": steps,
+            "mean_iterations": float(np.mean(its)),
+            "newton_per_substep": ip["newton_steps"] / max(1, substeps),
+            "cg_per_newton": ip["cg_iterations"] / max(1, ip["newton_steps"]),
+            "tangent_time_share": ip["tangent_ms"] / total_ms if total_ms else None,
+            "roofline": {"bound": "alu", "kernel": "k_tangent_b<NeoHookean>", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
+                         "ms_per_launch": ip["tangent_ms"] / max(1, ip["tangent_launches"]),
+                         "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)"},
+            "timing": "library CUDA events around each controller step (host-driven, L2 flushed between steps); "
+                      "tangent launches bracketed by CUDA events",
+            "kernel_launches": prof["kernel_launches"],
+            "sample": f"implicit Neo-Hookean bar {oracle_dims[0]}x{oracle_dims[1]}x{oracle_dims[2]}, 1 controller "
+                      f"step of 4 substeps",
+            "sample_gpu_value": ns * rg["iterations"] / (rg["elapsed_ms"] * 1e-3),
+            "sample_oracle_value": ns / cpu_s, "oracle_cores": 1,
+            "parity": "1e-9 relative L2 vs the oracle (tests/test_gpu_implicit.py)"}
+
+
 def hybrid_spec(W, args):
     return W.fom_opinf_hybrid(args.n, args.nz, rom=True)
 
@@ -551,6 +628,15 @@ def main():
     from paper_2511_20687_gb300 import workloads as W
 
     fit_info = None
+    if args.implicit_only:
+        # profiling entry: the implicit-FOM block alone, with seeded stand-in ROM operators of the
+        # fitted model's sizes and at most 3 Schwarz iterations per controller step
+        spec, ops = oracle_sample_problem(W, args, 20)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+        res = measure_implicit(W, osam, torch, flush, ops, args, local, log, steps=args.steps, max_iters=3,
+                               warmup=args.warmup)
+        print(json.dumps({"implicit": res}), flush=True)
+        return
     if args.fom_only:
         spec = W.fom_opinf_hybrid(args.n, args.nz, rom=False)
         rom_ops = None
@@ -630,11 +716,13 @@ def main():
         batched = measure_batched(W, osam, torch, flush, args, local, log)
         log(f"batched: {batched['value']:.3e} vs plain {batched['plain_value']:.3e} ({batched['speedup']:.1f}x)")
 
-    fit_meas = select_meas = adjoint_meas = None
+    fit_meas = select_meas = adjoint_meas = implicit_meas = None
     if world == 1 and not args.no_cpu_baseline and fit_info is not None:
         fit_meas = measure_fit(fit_info, log)
         select_meas = measure_select(osam, fit_info, local, log)
         adjoint_meas = measure_adjoint(W, osam, local, log)
+    if world == 1 and not args.no_implicit and rom_ops:
+        implicit_meas = measure_implicit(W, osam, torch, flush, rom_ops, args, local, log)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
@@ -687,7 +775,7 @@ def main():
                 "gpu_launches": head["launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
                 "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
-                "adjoint": adjoint_meas,
+                "adjoint": adjoint_meas, "implicit": implicit_meas,
                 "hbm": hbm,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}

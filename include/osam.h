@@ -112,6 +112,11 @@ typedef struct {
      * limit applies to it.  Implicit FOMs need OSAM_FP64 and run host-driven (no CUDA graph); a Newton
      * solve that fails leaves a non-finite state, reported as OSAM_ENONFINITE. */
     int integrator;
+    /* substeps of this subdomain per controller step (Sec. 4.1: n_i, Delta t_i = dt n_substeps / n_i of
+     * the problem; 0 = the problem's n_substeps).  Schwarz data between subdomains with different
+     * counts go through the temporal interpolant Xi: linear in time between the two source levels
+     * that bracket each destination level (identity for equal counts). */
+    int n_substeps;
 } osam_subdomain_desc;
 
 /* Dirichlet transfer from subdomain src to the Schwarz boundary nodes of dst (Sec. 4.1): the data
@@ -128,8 +133,8 @@ typedef struct {
     const osam_subdomain_desc* subdomains;
     int n_couplings;
     const osam_coupling_desc* couplings;
-    double dt;                /* time step, equal on every subdomain (temporal interpolant = identity) */
-    int n_substeps;           /* substeps per controller step I_k */
+    double dt;                /* time step of every subdomain with the default substep count */
+    int n_substeps;           /* substeps per controller step I_k (its length is dt n_substeps) */
     double tol_abs, tol_rel;  /* delta_abs, delta_rel of Eq. conv_criterion (0 disables a test) */
     int max_iters;            /* Schwarz iteration cap per controller step */
     int precision;            /* OSAM_FP64 or OSAM_FP32_FORCE (internal force in FP32) */
@@ -228,6 +233,12 @@ OSAM_API int osam_sizes(osam_ctx* ctx, int sub, int* n_nodes, int* n_elements, i
 OSAM_API int osam_profile(osam_ctx* ctx, int enable);
 OSAM_API int osam_profile_read(osam_ctx* ctx, double* force_ms, long long* force_launches, long long* force_elements,
                       long long* kernel_launches);
+/* Accounting of the implicit subdomains since the last osam_profile call: time of the tangent-action
+ * launches (CUDA events around each, recorded only while profiling is enabled) and their count,
+ * elements whose tangent action was applied (CG iterations x elements, per instance), Newton linear
+ * solves and CG iterations summed over instances and implicit subdomains.  Any output may be NULL. */
+OSAM_API int osam_implicit_profile(osam_ctx* ctx, double* tangent_ms, long long* tangent_launches,
+                                   long long* tangent_elements, long long* newton_steps, long long* cg_iterations);
 /* FP64 fused multiply-add throughput of device `device` in GFLOP/s (2 flops per FMA), measured by a
  * register-resident FMA loop over 8 blocks per SM; the ALU roofline of the FP64 element kernels. */
 OSAM_API int osam_fp64_peak(int device, double* gflops);

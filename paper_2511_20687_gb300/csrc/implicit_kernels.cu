@@ -125,13 +125,14 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
     const int inst = blockIdx.x;
     if (!run(mask, inst)) return;
     const int b0 = g.nblk_off[inst], b1 = g.nblk_off[inst + 1];
+    const bool two = mode == 0 || mode == 3;
     double s = 0.0, sz = 0.0;
     for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
         s += g.ipart[b];
-        if (mode == 0) sz += g.ipart[g.n_nblk + b];
+        if (two) sz += g.ipart[g.n_nblk + b];
     }
     s = block_sum1(s);
-    if (mode == 0) sz = block_sum1(sz);
+    if (two) sz = block_sum1(sz);
     if (threadIdx.x != 0) return;
     if (mode == 0) {
         if (first) g.r0[inst] = s;
@@ -142,10 +143,15 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
         const int st = !fin ? 2 : ((s == 0.0 || s <= tol2 * g.r0[inst]) ? 0 : 1);
         g.nact[inst] = st;
         g.cgact[inst] = st == 1 ? 1 : 0;
+        if (st == 1) g.istat[2 * inst] += 1;
     } else if (mode == 1) {
         g.pap[inst] = s;
+    } else if (mode == 3) {
+        // |du|^2 against |u|^2 after the update: an increment at the rounding level of u converges
+        if (isfinite(s) && s <= tol2 * sz) g.nact[inst] = 0;
     } else {
         g.rrn[inst] = s;
+        g.istat[2 * inst + 1] += 1;
         if (!(s > tol2 * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
     }
 }
@@ -314,18 +320,29 @@ __global__ void k_cg_rr_b(const FomB g, const int* __restrict__ mask) {
     g.rr[inst] = g.rrn[inst];
 }
 
-// u += x on free dofs, refreshed u / h for the force kernel
+// u += x on free dofs, refreshed u / h for the force kernel; partials |x|^2 and |u|^2 (free dofs)
 __global__ void __launch_bounds__(kNodeBlock) k_imp_update_b(const FomB g, const int* __restrict__ mask) {
     const NodeCtx x = node_ctx(g, mask);
-    if (!x.ok) return;
+    double sx = 0.0, su = 0.0;
+    if (x.ok) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const long long d = (long long)c * g.NN + x.gn;
-        if (is_free(g, x.gn, c)) {
-            const double u = g.u[0][d] + g.cg_x[d];
-            g.u[0][d] = u;
-            g.us[d] = u * x.I.invh;
+        for (int c = 0; c < 3; ++c) {
+            const long long d = (long long)c * g.NN + x.gn;
+            if (is_free(g, x.gn, c)) {
+                const double dx = g.cg_x[d];
+                const double u = g.u[0][d] + dx;
+                g.u[0][d] = u;
+                g.us[d] = u * x.I.invh;
+                sx = fma(dx, dx, sx);
+                su = fma(u, u, su);
+            }
         }
+    }
+    sx = block_sum1(sx);
+    su = block_sum1(su);
+    if (threadIdx.x == 0) {
+        g.ipart[blockIdx.x] = sx;
+        g.ipart[g.n_nblk + blockIdx.x] = su;
     }
 }
 

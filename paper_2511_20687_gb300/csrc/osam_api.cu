@@ -52,6 +52,8 @@ struct RomGroupH {
 
 struct Slot {
     int kind = OSAM_FOM;
+    int nsub = 0;        // substeps per controller interval (Sec. 4.1: n_i)
+    double dt = 0.0;     // Delta t_i = interval length / n_i
     FomGroupH fom;
     RomGroupH rom;
 };
@@ -106,9 +108,11 @@ struct osam_ctx {
     // kernel-level timing of the internal-force launches (host-driven path) and a launch count
     bool prof = false;
     std::vector<cudaEvent_t> pev;
+    std::vector<int> pkind;               // per event pair: 0 internal force, 1 implicit tangent action
     int pnext = 0;
-    double prof_ms = 0.0;
+    double prof_ms = 0.0, tprof_ms = 0.0;
     long long prof_launches = 0, prof_elements = 0, launches = 0;
+    long long tprof_launches = 0;
 
     ~osam_ctx() {
         if (stream) cudaStreamSynchronize(stream);
@@ -151,27 +155,33 @@ struct osam_ctx {
         return code;
     }
 
-    int prof_begin() {
+    int prof_begin(int kind = 0) {
         if (!prof) return -1;
         while (pnext + 2 > (int)pev.size()) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             pev.push_back(e);
+            pkind.push_back(0);
         }
         cudaEventRecord(pev[pnext], stream);
+        pkind[pnext] = kind;
         return pnext;
     }
     void prof_end(int k, long long elements) {
         if (k < 0) return;
         cudaEventRecord(pev[k + 1], stream);
         pnext = k + 2;
-        prof_launches += 1;
-        prof_elements += elements;
+        if (pkind[k] == 0) {
+            prof_launches += 1;
+            prof_elements += elements;
+        } else {
+            tprof_launches += 1;
+        }
     }
     void prof_collect() {
         for (int k = 0; k + 1 < pnext; k += 2) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) prof_ms += ms;
+            if (cudaEventElapsedTime(&ms, pev[k], pev[k + 1]) == cudaSuccess) (pkind[k] == 0 ? prof_ms : tprof_ms) += ms;
         }
         pnext = 0;
     }
@@ -254,6 +264,7 @@ bool trace_fuse(osam_ctx* ctx, int s, const double* u, int slot, TraceFuse& tr) 
 // substep j + 1 of FOM slot s: internal force at u^{j+1} (with the trace of substep j folded into the
 // same launch), corrector of j + 1 and predictor of j + 2
 int fom_substep(osam_ctx* ctx, int s, int j, const int* active, long long ne) {
+    const Slot& S = ctx->slots[s];
     FomB& g = ctx->slots[s].fom.d;
     double* X = g.u[(j + 1) & 1];
     double* Y = g.u[j & 1];
@@ -265,16 +276,16 @@ int fom_substep(osam_ctx* ctx, int s, int j, const int* active, long long ne) {
     const int pk = ctx->prof_begin();
     LK(launch_force_b(g, active, ctx->scatter, ctx->stream, fuse ? &tr : nullptr));
     ctx->prof_end(pk, ne);
-    LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= ctx->nsub) ? j + 2 : -1, 0, X, Y, ctx->dt,
-                     ctx->stream));
+    LK(launch_node_b(g, active, ctx->scatter, j + 1, (j + 2 <= S.nsub) ? j + 2 : -1, 0, X, Y, S.dt, ctx->stream));
     return OSAM_OK;
 }
 
 // trace of the last substep of FOM slot s (no force launch follows it within the interval)
 int last_trace(osam_ctx* ctx, int s, const int* active) {
     FomB& g = ctx->slots[s].fom.d;
+    const int n = ctx->slots[s].nsub;
     for (CplH& c : ctx->cpls)
-        if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[ctx->nsub & 1], ctx->nsub, ctx->stream));
+        if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[n & 1], n, ctx->stream));
     return OSAM_OK;
 }
 
@@ -289,20 +300,22 @@ int any_set(osam_ctx* ctx, const int* mask, int n, bool& any) {
 
 constexpr int kNewtonMax = 25;         // Newton iterations per substep
 constexpr double kNewtonTol2 = 1e-24;  // |R|^2 <= kNewtonTol2 |R(u~)|^2
+constexpr double kNewtonInc2 = 1e-28;  // or an increment |du|^2 <= kNewtonInc2 |u|^2 (rounding level of u)
 constexpr int kCgMax = 1000;           // CG iterations per Newton step
 constexpr int kCgCheck = 8;            // CG iterations between host checks of the activity mask
 constexpr double kCgTol2 = 1e-26;      // r.z <= kCgTol2 (r.z)_0 (mass-preconditioned residual)
 
 // Implicit Newmark interval of FOM slot s (beta = 1/4, gamma = 1/2): per substep the predictor, a
 // Newton solve of M (u - u~) c0 + f_int(u) = 0 (c0 = 1 / (beta dt^2)) with mass-preconditioned
-// conjugate gradients on the exact tangent, the corrector and the traces of the new level.
+// conjugate gradients on the exact tangent, until |R| <= 1e-12 |R(u~)| or an increment at the rounding
+// level of u (at most 25 Newton steps), the corrector and the traces of the new level.
 // Activity is tracked per instance on the device: Newton (nact: 1 iterating, 0 converged, 2 failed)
 // and CG (cgact); the host reads the masks to end the loops.
 int advance_implicit(osam_ctx* ctx, int s, const int* active) {
     FomB& g = ctx->slots[s].fom.d;
     const int n = g.n_inst;
-    const double dt = ctx->dt, c0 = 4.0 / (dt * dt);
-    for (int j = 0; j < ctx->nsub; ++j) {
+    const double dt = ctx->slots[s].dt, c0 = 4.0 / (dt * dt);
+    for (int j = 0; j < ctx->slots[s].nsub; ++j) {
         LK(launch_imp_predict_b(g, active, j + 1, dt, ctx->stream));
         LK(launch_mask_copy(n, active, g.nact, ctx->stream));
         LK(launch_mask_copy(n, active, g.cgact, ctx->stream));
@@ -315,7 +328,9 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
             if (!any) break;
             for (int k = 0; k < kCgMax;) {
                 for (int q = 0; q < kCgCheck; ++q, ++k) {
+                    const int pk = ctx->prof_begin(1);
                     LK(launch_tangent_b(g, g.cgact, ctx->stream));
+                    ctx->prof_end(pk, 0);
                     LK(launch_cg_ap_b(g, g.cgact, c0, ctx->stream));
                     LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, ctx->stream));
                     LK(launch_cg_step_b(g, g.cgact, c0, ctx->stream));
@@ -327,6 +342,7 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
                 if (!cg) break;
             }
             LK(launch_imp_update_b(g, g.nact, ctx->stream));
+            LK(launch_imp_reduce_b(g, g.nact, 3, 0, kNewtonInc2, ctx->stream));
         }
         LK(launch_imp_finish_b(g, active, j + 1, dt, c0, ctx->stream));
         for (CplH& c : ctx->cpls)
@@ -342,15 +358,15 @@ int advance_slot(osam_ctx* ctx, int s, const int* active) {
         FomB& g = S.fom.d;
         long long ne = 0;
         for (const InstFom& I : S.fom.inst) ne += I.ne;
-        LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
-        for (int j = 0; j < ctx->nsub; ++j) RET(fom_substep(ctx, s, j, active, ne));
+        LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], S.dt, ctx->stream));
+        for (int j = 0; j < S.nsub; ++j) RET(fom_substep(ctx, s, j, active, ne));
         RET(last_trace(ctx, s, active));
-        if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
+        if (S.nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
     } else {
         RomB& r = S.rom.d;
         LK(launch_rom_record0_b(r, active, ctx->stream));
-        LK(launch_rom_project_b(r, active, 1, ctx->nsub, ctx->stream));
-        for (int j = 0; j < ctx->nsub; ++j) LK(launch_rom_step_b(r, active, j + 1, ctx->dt, 0, ctx->stream));
+        LK(launch_rom_project_b(r, active, 1, S.nsub, ctx->stream));
+        for (int j = 0; j < S.nsub; ++j) LK(launch_rom_step_b(r, active, j + 1, S.dt, 0, ctx->stream));
     }
     return OSAM_OK;
 }
@@ -361,6 +377,7 @@ bool pipelined_pair(const osam_ctx* ctx, int s) {
     if (s + 1 >= (int)ctx->slots.size()) return false;
     if (ctx->slots[s].kind != OSAM_FOM || ctx->slots[s + 1].kind != OSAM_ROM) return false;
     if (ctx->slots[s].fom.d.implicit) return false;
+    if (ctx->slots[s].nsub != ctx->slots[s + 1].nsub) return false;  // substep j <-> j needs equal levels
     bool fed = false;
     for (const CplH& c : ctx->cpls) {
         if (c.dst != s + 1 || c.src > s) continue;
@@ -376,6 +393,8 @@ bool pipelined_pair(const osam_ctx* ctx, int s) {
 // per-subdomain order as advance_slot(s), transfer(s -> s + 1), advance_slot(s + 1), so the results
 // are identical; only the two subdomains' work overlaps.
 int advance_pair(osam_ctx* ctx, int s, const int* active) {
+    const int nsub = ctx->slots[s].nsub;
+    const double dt = ctx->slots[s].dt;
     FomB& g = ctx->slots[s].fom.d;
     RomB& r = ctx->slots[s + 1].rom.d;
     long long ne = 0;
@@ -383,40 +402,45 @@ int advance_pair(osam_ctx* ctx, int s, const int* active) {
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
     LK(launch_rom_record0_b(r, active, ctx->side));
-    LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], ctx->dt, ctx->stream));
+    LK(launch_node_b(g, active, ctx->scatter, -1, 1, 1, g.u[0], g.u[1], dt, ctx->stream));
     // the trace of substep j is complete after the force launch of substep j + 1 (or the last trace)
     auto rom_substep = [&](int j) -> int {
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
         CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
         for (CplH& c : ctx->cpls)
-            if (c.src == s && c.dst == s + 1) LK(launch_publish_b(c.d, active, j, 1, ctx->side));
+            if (c.src == s && c.dst == s + 1) LK(launch_publish_b(c.d, active, j, 1, nsub, nsub, ctx->side));
         LK(launch_rom_project_b(r, active, j, j, ctx->side));
-        LK(launch_rom_step_b(r, active, j, ctx->dt, 0, ctx->side));
+        LK(launch_rom_step_b(r, active, j, dt, 0, ctx->side));
         return OSAM_OK;
     };
-    for (int j = 0; j < ctx->nsub; ++j) {
+    for (int j = 0; j < nsub; ++j) {
         RET(fom_substep(ctx, s, j, active, ne));
         if (j > 0) RET(rom_substep(j));
     }
     RET(last_trace(ctx, s, active));
-    RET(rom_substep(ctx->nsub));
-    if (ctx->nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
+    RET(rom_substep(nsub));
+    if (nsub & 1) LK(launch_copy_u10_b(g, active, ctx->stream));
     CK(cudaEventRecord(ctx->ev_join, ctx->side));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     return OSAM_OK;
 }
 
+// src's interval trace onto dst's time levels 1..n_dst (temporal interpolant Xi, Sec. 4.1: linear
+// between the src levels that bracket each dst level; identity for equal substep counts)
 int transfer_cpl(osam_ctx* ctx, CplH& c, const int* active) {
     Slot& src = ctx->slots[c.src];
-    if (src.kind == OSAM_FOM) LK(launch_publish_b(c.d, active, 1, ctx->nsub, ctx->stream));
-    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 0, ctx->nsub, ctx->stream));
+    const int ns = src.nsub, nd = ctx->slots[c.dst].nsub;
+    if (src.kind == OSAM_FOM) LK(launch_publish_b(c.d, active, 1, nd, ns, nd, ctx->stream));
+    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 0, ns, nd, ctx->stream));
     return OSAM_OK;
 }
 
+// zero-order hold of src's current state into every dst level (and the FOM trace's level 0)
 int zoh_cpl(osam_ctx* ctx, CplH& c, const int* active) {
     Slot& src = ctx->slots[c.src];
-    if (src.kind == OSAM_FOM) LK(launch_zoh_fom_b(c.d, active, src.fom.d, ctx->nsub, ctx->stream));
-    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 1, ctx->nsub, ctx->stream));
+    const int ns = src.nsub, nd = ctx->slots[c.dst].nsub;
+    if (src.kind == OSAM_FOM) LK(launch_zoh_fom_b(c.d, active, src.fom.d, nd, ctx->stream));
+    else LK(launch_rom_reconstruct_b(c.d, active, src.rom.d, 1, ns, nd, ctx->stream));
     return OSAM_OK;
 }
 
@@ -430,8 +454,8 @@ int saverest_all(osam_ctx* ctx, const int* active, int restore) {
 
 int norms_all(osam_ctx* ctx, const int* active) {
     for (Slot& S : ctx->slots) {
-        if (S.kind == OSAM_FOM) LK(launch_norms_fom_b(S.fom.d, active, ctx->dt, ctx->stream));
-        else LK(launch_rom_norms_b(S.rom.d, active, ctx->dt, ctx->stream));
+        if (S.kind == OSAM_FOM) LK(launch_norms_fom_b(S.fom.d, active, S.dt, ctx->stream));
+        else LK(launch_rom_norms_b(S.rom.d, active, S.dt, ctx->stream));
     }
     return OSAM_OK;
 }
@@ -560,6 +584,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: rho must be positive", i, s);
             if (a.kind == OSAM_FOM && a.integrator != OSAM_EXPLICIT && a.integrator != OSAM_IMPLICIT)
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: bad integrator", i, s);
+            if (a.n_substeps < 0 || a.n_substeps > (1 << 20) || a.n_substeps != b.n_substeps)
+                return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: bad or differing n_substeps", i, s);
             if (a.kind == OSAM_FOM && a.integrator != b.integrator)
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: integrator differs from instance 0", i, s);
             if (a.kind == OSAM_FOM && a.integrator == OSAM_IMPLICIT && d0.precision != OSAM_FP64)
@@ -619,9 +645,10 @@ int check_stability(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         double m;
         std::memcpy(&m, &mh[i], sizeof(double));
         const double lim = G.grid[i].h * std::sqrt(descs[i].subdomains[s].rho / m);
-        if (!G.d.implicit && ctx->dt > lim * (1.0 + 1e-9))
+        const double dt = ctx->slots[s].dt;
+        if (!G.d.implicit && dt > lim * (1.0 + 1e-9))
             return ctx->fail(OSAM_ECFL, "instance %d subdomain %d: dt = %.6e above the explicit stability limit "
-                                        "%.6e", i, s, ctx->dt, lim);
+                                        "%.6e", i, s, dt, lim);
     }
     return OSAM_OK;
 }
@@ -657,7 +684,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         I.w8 = g.h * g.h / 8.0;
         I.lam = d.lambda; I.mu = d.mu;
         I.node_off = NN; I.elem_off = NE; I.hist_off = H;
-        NN += I.nn; NE += I.ne; H += (long long)(ctx->nsub + 1) * 9 * I.ns;
+        NN += I.nn; NE += I.ne; H += (long long)(ctx->slots[s].nsub + 1) * 9 * I.ns;
     }
     FomB& B = G.d;
     B.n_inst = n; B.NN = NN; B.NE = NE;
@@ -692,6 +719,8 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CKA(B.cg_p = ctx->alloc<double>(3 * NN));
         CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
         for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap}) CKA(*p = ctx->alloc<double>(n));
+        CKA(B.istat = ctx->alloc<long long>(2 * n));
+        CK(cudaMemsetAsync(B.istat, 0, sizeof(long long) * 2 * n, ctx->stream));
         CKA(B.nact = ctx->alloc<int>(n));
         CKA(B.cgact = ctx->alloc<int>(n));
         CK(cudaMemsetAsync(B.nact, 0, sizeof(int) * n, ctx->stream));
@@ -791,9 +820,10 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
         I.PhiSt_off = PS_tot; PS_tot += (long long)I.rs * I.nsdof;
         I.kij_off = kij_tot; kij_tot += I.nq;
         I.q_off = q_tot; q_tot += 3LL * I.r;
-        I.qrec_off = qrec_tot; qrec_tot += (long long)(ctx->nsub + 1) * 3 * I.r;
-        I.ghat_off = ghat_tot; ghat_tot += (long long)(ctx->nsub + 1) * std::max(1, I.rs);
-        I.hist_off = hist_tot; hist_tot += (long long)(ctx->nsub + 1) * 3 * std::max(1, I.nsdof);
+        const long long nl = ctx->slots[s].nsub + 1;
+        I.qrec_off = qrec_tot; qrec_tot += nl * 3 * I.r;
+        I.ghat_off = ghat_tot; ghat_tot += nl * std::max(1, I.rs);
+        I.hist_off = hist_tot; hist_tot += nl * 3 * std::max(1, I.nsdof);
         I.partial_off = part_tot; part_tot += (long long)I.gx * I.r;
         B.gx_max = std::max(B.gx_max, I.gx);
         B.gy_max = std::max(B.gy_max, I.gy);
@@ -950,7 +980,7 @@ int setup_couplings(osam_ctx* ctx, int n, const osam_problem_desc* descs,
                 }
             }
             rec_off[i] = rec_tot;
-            rec_tot += (long long)(ctx->nsub + 1) * 9 * nr;
+            rec_tot += (long long)(ctx->slots[C.src].nsub + 1) * 9 * nr;
             if (src_rom) {
                 Rt_off[i] = Rt_tot;
                 Rt_tot += (long long)src.rom.inst[i].r * 3 * nr;
@@ -1065,7 +1095,7 @@ int initial_accel(osam_ctx* ctx, const int* mask) {
             CK(launch_init_accel_b(S.fom.d, mask, ctx->stream));
         } else {
             CK(launch_rom_project_b(S.rom.d, mask, 0, 0, ctx->stream));
-            CK(launch_rom_step_b(S.rom.d, mask, 0, ctx->dt, 1, ctx->stream));
+            CK(launch_rom_step_b(S.rom.d, mask, 0, S.dt, 1, ctx->stream));
         }
     }
     return OSAM_OK;
@@ -1076,9 +1106,10 @@ int initial_accel(osam_ctx* ctx, const int* mask) {
 // more than 5% faster)
 int autotune(osam_ctx* ctx) {
     FomGroupH* best_g = nullptr;
+    const Slot* best_s = nullptr;
     long long ne = -1;
     for (Slot& S : ctx->slots)
-        if (S.kind == OSAM_FOM && S.fom.d.NE > ne) { ne = S.fom.d.NE; best_g = &S.fom; }
+        if (S.kind == OSAM_FOM && S.fom.d.NE > ne) { ne = S.fom.d.NE; best_g = &S.fom; best_s = &S; }
     if (!best_g) return OSAM_OK;
     FomGroupH& G = *best_g;
     FomB g = G.d;
@@ -1093,7 +1124,7 @@ int autotune(osam_ctx* ctx) {
     CK(cudaMemcpyAsync(a, G.d.a, sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
     g.v = v;
     g.a = a;
-    const int slot2 = std::min(2, ctx->nsub);
+    const int slot2 = std::min(2, best_s->nsub);
     float best_ms = 1e30f, gather_ms = 1e30f;
     int best_block = 128, best_scatter = kGather, best_tiled = 0;
     // (scatter, element block, tiled).  The 128-register FP64 kernel measured level with the natural
@@ -1113,7 +1144,7 @@ int autotune(osam_ctx* ctx) {
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
             CK(launch_force_b(g, nullptr, mode, ctx->stream));
-            CK(launch_node_b(g, nullptr, mode, 1, slot2, 0, u, un, ctx->dt, ctx->stream));
+            CK(launch_node_b(g, nullptr, mode, 1, slot2, 0, u, un, best_s->dt, ctx->stream));
         }
         CK(cudaEventRecord(ctx->ev1, ctx->stream));
         CK(cudaEventSynchronize(ctx->ev1));
@@ -1175,7 +1206,14 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     // masks, Schwarz rows (union over the couplings into a subdomain, increasing node order)
     std::vector<std::vector<std::vector<uint8_t>>> masks(n, std::vector<std::vector<uint8_t>>(ncpl));
     int max_nn = 1;
-    for (int s = 0; s < nsd; ++s) ctx->slots[s].kind = d0.subdomains[s].kind;
+    for (int s = 0; s < nsd; ++s) {
+        Slot& S = ctx->slots[s];
+        S.kind = d0.subdomains[s].kind;
+        // Delta t_i = (dt n_substeps) / n_i; exactly dt for the common count
+        const int ni = d0.subdomains[s].n_substeps;
+        S.nsub = ni > 0 ? ni : ctx->nsub;
+        S.dt = S.nsub == ctx->nsub ? ctx->dt : (ctx->dt * (double)ctx->nsub) / (double)S.nsub;
+    }
     for (int i = 0; i < n; ++i) {
         const osam_problem_desc& d = descs[i];
         for (int s = 0; s < nsd; ++s) {
@@ -1192,7 +1230,7 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
             if (S.kind == OSAM_FOM) {
                 S.fom.grid.push_back(g);
                 S.fom.clamp.push_back(clamp);
-                ctx->fom_elements[i] += g.ne();
+                ctx->fom_elements[i] += (long long)g.ne() * S.nsub;
             } else {
                 S.rom.grid.push_back(g);
                 S.rom.clamp.push_back(clamp);
@@ -1386,7 +1424,7 @@ int osam_batch_step(osam_ctx* ctx, osam_step_report* reps, osam_step_report* tot
         if (st < 0) worst = std::min(worst, st);
         else if (worst >= 0) worst = std::max(worst, st);
         max_its = std::max(max_its, ctx->iters_h[i]);
-        const long long u = (long long)ctx->iters_h[i] * ctx->nsub * ctx->fom_elements[i];
+        const long long u = (long long)ctx->iters_h[i] * ctx->fom_elements[i];
         updates += u;
         if (reps) {
             reps[i].status = st;
@@ -1421,9 +1459,37 @@ int osam_profile(osam_ctx* ctx, int enable) {
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->prof_collect();
     ctx->prof = enable != 0;
-    ctx->prof_ms = 0.0;
-    ctx->prof_launches = ctx->prof_elements = 0;
+    ctx->prof_ms = ctx->tprof_ms = 0.0;
+    ctx->prof_launches = ctx->prof_elements = ctx->tprof_launches = 0;
     ctx->launches = 0;
+    for (Slot& S : ctx->slots)
+        if (S.kind == OSAM_FOM && S.fom.d.implicit)
+            CK(cudaMemsetAsync(S.fom.d.istat, 0, sizeof(long long) * 2 * S.fom.d.n_inst, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OSAM_OK;
+}
+
+int osam_implicit_profile(osam_ctx* ctx, double* tangent_ms, long long* tangent_launches,
+                          long long* tangent_elements, long long* newton_steps, long long* cg_iterations) {
+    if (!ctx) return OSAM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof_collect();
+    long long el = 0, nw = 0, cg = 0;
+    for (Slot& S : ctx->slots) {
+        if (S.kind != OSAM_FOM || !S.fom.d.implicit) continue;
+        std::vector<long long> st;
+        RET(to_host(ctx, st, S.fom.d.istat, 2 * (size_t)S.fom.d.n_inst));
+        for (int i = 0; i < S.fom.d.n_inst; ++i) {
+            nw += st[2 * i];
+            cg += st[2 * i + 1];
+            el += st[2 * i + 1] * S.fom.inst[i].ne;
+        }
+    }
+    if (tangent_ms) *tangent_ms = ctx->tprof_ms;
+    if (tangent_launches) *tangent_launches = ctx->tprof_launches;
+    if (tangent_elements) *tangent_elements = el;
+    if (newton_steps) *newton_steps = nw;
+    if (cg_iterations) *cg_iterations = cg;
     return OSAM_OK;
 }
 
@@ -1478,7 +1544,7 @@ int osam_instance_get_state(osam_ctx* ctx, int inst, int sub, double* u, double*
             RomGroupH& G = S.rom;
             const InstRom& I = G.inst[inst];
             nn = G.grid[inst].nn();
-            const double* hs = G.d.hist + I.hist_off + ((long long)ctx->nsub * 3 + f) * I.nsdof;
+            const double* hs = G.d.hist + I.hist_off + ((long long)S.nsub * 3 + f) * I.nsdof;
             CK(launch_rom_full_field(nn, I.r, G.Phi[inst], G.dof_free[inst], G.clamp_d[inst], G.srow_d[inst], hs,
                                      G.d.q + I.q_off + (long long)f * I.r, ctx->scratch, ctx->stream));
         }
@@ -1537,7 +1603,7 @@ int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, c
         RET(upload(ctx, G.d.q + I.q_off + I.r, qdh.data(), sizeof(double) * I.r));
         RET(select_instance(ctx, inst));
         CK(launch_rom_project_b(G.d, ctx->sel, 0, 0, ctx->stream));
-        CK(launch_rom_step_b(G.d, ctx->sel, 0, ctx->dt, 1, ctx->stream));
+        CK(launch_rom_step_b(G.d, ctx->sel, 0, S.dt, 1, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;

@@ -109,6 +109,7 @@ struct FomB {
     double* pap;              // per instance: p . A p
     int* nact;                // per instance Newton state: 1 iterating, 0 converged, 2 failed
     int* cgact;               // per instance: CG still iterating
+    long long* istat;         // per instance: Newton linear solves, CG iterations (since the last reset)
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 
@@ -145,7 +146,7 @@ struct CplB {
     const int* row;           // dst Schwarz row (local to the instance) of each row
     const int* dnode;         // [R][8] donor nodes, global index in the src group's node arrays
     const double* dw;         // [R][8] trilinear weights
-    double* rec;              // FOM source: recorded trace, per instance [(nsub+1)][3][3][nrow]
+    double* rec;              // FOM source: recorded trace, per instance [(nsub_src+1)][3][3][nrow]
     const long long* rec_off; // [n_inst]
     const double* Rt;         // ROM source: (Pi Phi_rows)^T, per instance [r][3 nrow]
     const long long* Rt_off;  // [n_inst]
@@ -215,12 +216,16 @@ cudaError_t launch_node_df_b(const FomB& g, const int* active, int slot1, int sl
                              const double* ucur, double* unext, double dt, cudaStream_t s);
 cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, const double* u, int slot,
                            cudaStream_t s);
-cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, cudaStream_t s);  // slots [slot0, slot0 + nslots)
-cudaError_t launch_zoh_fom_b(const CplB& c, const int* active, const FomB& src, int nsub, cudaStream_t s);
+// destination levels [slot0, slot0 + nslots) of nd from the source trace's levels 0..ns (temporal
+// interpolant: linear between bracketing source levels, identity for ns == nd)
+cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, int ns, int nd, cudaStream_t s);
+// zero-order hold into destination levels 0..nd and trace level 0
+cudaError_t launch_zoh_fom_b(const CplB& c, const int* active, const FomB& src, int nd, cudaStream_t s);
 cudaError_t launch_rom_record0_b(const RomB& r, const int* active, cudaStream_t s);
 cudaError_t launch_rom_project_b(const RomB& r, const int* active, int slot0, int slot1, cudaStream_t s);
 cudaError_t launch_rom_step_b(const RomB& r, const int* active, int slot, double dt, int rhs_only, cudaStream_t s);
-cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int nsub,
+// ROM source -> destination levels 1..nd (zoh: 0..nd from the current state) from ns source levels
+cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int ns, int nd,
                                      cudaStream_t s);
 cudaError_t launch_rom_norms_b(const RomB& r, const int* active, double dt, cudaStream_t s);
 cudaError_t launch_saverest_rom_b(const RomB& r, const int* active, int restore, cudaStream_t s);
@@ -231,7 +236,8 @@ cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int u
 cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, double dt, cudaStream_t s);
 cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 // reduce the node-block partials per instance; mode 0: Newton residual (sets rn2, r0 on the first
-// iteration, rr, rr0, nact, cgact), 1: p . Ap, 2: r . z after a CG update (sets rrn, cgact)
+// iteration, rr, rr0, nact, cgact), 1: p . Ap, 2: r . z after a CG update (sets rrn, cgact),
+// 3: |du|^2 <= tol2 |u|^2 after a Newton update (clears nact)
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s);
 cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s);

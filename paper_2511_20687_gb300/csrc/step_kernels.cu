@@ -445,8 +445,19 @@ __global__ void k_trace_b(const CplB c, const int* __restrict__ active, const Fo
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 3 * c.R) trace::trace_item(c, active, src, u, slot, t);
 }
-// publish a FOM source's recorded slots 1..nsub into the destination history
-__global__ void k_publish_b(const CplB c, const int* __restrict__ active, int slot0, int nslots) {
+// temporal interpolant Xi (Sec. 4.1): destination level m of nd (time m T / nd) lies at source level
+// l + w of ns (time (l + w) T / ns); w = 0 exactly when the levels coincide
+__device__ __forceinline__ int xi_level(int m, int ns, int nd, double& w) {
+    const long long num = (long long)m * ns;
+    const int l = (int)(num / nd);
+    const long long rem = num - (long long)l * nd;
+    w = rem ? (double)rem / (double)nd : 0.0;
+    return l;
+}
+
+// publish a FOM source's recorded trace (levels 0..ns) into destination levels [slot0, slot0 + nslots)
+// of nd, linear in time between the bracketing source levels
+__global__ void k_publish_b(const CplB c, const int* __restrict__ active, int slot0, int nslots, int ns, int nd) {
     const long long total = (long long)c.R * 9 * nslots;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
@@ -457,11 +468,16 @@ __global__ void k_publish_b(const CplB c, const int* __restrict__ active, int sl
     const int inst = c.rinst[gr];
     if (active && !active[inst]) return;
     const int li = gr - c.row_first[inst], nr = c.nrow[inst];
-    const double val = c.rec[c.rec_off[inst] + ((long long)slot * 9 + fc) * nr + li];
+    double w;
+    const int l = xi_level(slot, ns, nd, w);
+    const double* rec = c.rec + c.rec_off[inst];
+    double val = rec[((long long)l * 9 + fc) * nr + li];
+    if (w != 0.0) val = (1.0 - w) * val + w * rec[((long long)(l + 1) * 9 + fc) * nr + li];
     c.dst_hist[dst_index(c, inst, slot, fc / 3, fc % 3, c.row[gr])] = val;
 }
 
-// zero-order hold of a FOM source's current state into every slot of the destination history
+// zero-order hold of a FOM source's current state into every slot of the destination history and
+// into level 0 of the recorded trace (the state at the start of the interval)
 __global__ void k_zoh_fom_b(const CplB c, const int* __restrict__ active, const FomB src, int nslots) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * c.R) return;
@@ -480,6 +496,9 @@ __global__ void k_zoh_fom_b(const CplB c, const int* __restrict__ active, const 
     for (int slot = 0; slot < nslots; ++slot)
 #pragma unroll
         for (int f = 0; f < 3; ++f) c.dst_hist[dst_index(c, inst, slot, f, cc, c.row[gr])] = s[f];
+    const int li = gr - c.row_first[inst], nr = c.nrow[inst];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) c.rec[c.rec_off[inst] + (long long)(3 * f + cc) * nr + li] = s[f];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -601,8 +620,11 @@ __global__ void __launch_bounds__(kRomBlock) k_rom_step_b(const RomB r, const in
     if (tid == 0) r.counter[inst] = 0u;
 }
 
-// s_dst[slot][f][3 i + c] = sum_k Rt[k][3 i + c] q_src[slot][f][k]; grid (columns, slots, fields)
-__global__ void k_rom_reconstruct_b(const CplB c, const int* __restrict__ active, const RomB src, int zoh, int slot0) {
+// s_dst[slot][f][3 i + c] = sum_k Rt[k][3 i + c] q_src(t_slot)[f][k]; grid (columns, slots, fields).
+// q_src(t_slot) is the recorded source level, or linear in time between the two bracketing source
+// levels (temporal interpolant Xi) when the substep counts differ; zoh: the current state.
+__global__ void k_rom_reconstruct_b(const CplB c, const int* __restrict__ active, const RomB src, int zoh, int slot0,
+                                    int ns, int nd) {
     const int gc = blockIdx.x * blockDim.x + threadIdx.x;
     if (gc >= 3 * c.R) return;
     const int gr = gc / 3, cc = gc % 3;
@@ -612,12 +634,19 @@ __global__ void k_rom_reconstruct_b(const CplB c, const int* __restrict__ active
     const int li = gr - c.row_first[inst], nr = c.nrow[inst];
     const int slot = slot0 + blockIdx.y;
     const int f = blockIdx.z;
+    double w = 0.0;
+    const int l = zoh ? 0 : xi_level(slot, ns, nd, w);
     const double* q = zoh ? src.q + I.q_off + (long long)f * I.r
-                          : src.qrec + I.qrec_off + ((long long)slot * 3 + f) * I.r;
+                          : src.qrec + I.qrec_off + ((long long)l * 3 + f) * I.r;
     const double* Rt = c.Rt + c.Rt_off[inst];
     const int col = 3 * li + cc;
     double acc = 0.0;
-    for (int k = 0; k < I.r; ++k) acc = fma(Rt[(long long)k * 3 * nr + col], q[k], acc);
+    if (w == 0.0) {
+        for (int k = 0; k < I.r; ++k) acc = fma(Rt[(long long)k * 3 * nr + col], q[k], acc);
+    } else {
+        const double* q1 = q + 3LL * I.r;
+        for (int k = 0; k < I.r; ++k) acc = fma(Rt[(long long)k * 3 * nr + col], (1.0 - w) * q[k] + w * q1[k], acc);
+    }
     c.dst_hist[dst_index(c, inst, slot, f, cc, c.row[gr])] = acc;
 }
 
@@ -817,9 +846,10 @@ cudaError_t launch_trace_b(const CplB& c, const int* active, const FomB& src, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, cudaStream_t s) {
+cudaError_t launch_publish_b(const CplB& c, const int* active, int slot0, int nslots, int ns, int nd, cudaStream_t s) {
     if (c.R == 0 || nslots <= 0) return cudaSuccess;
-    k_publish_b<<<grid_for(9LL * c.R * nslots, 256), 256, 0, s>>>(c, active, slot0, nslots);
+    if (ns < 1 || nd < 1 || slot0 < 0 || slot0 + nslots > nd + 1) return cudaErrorInvalidValue;
+    k_publish_b<<<grid_for(9LL * c.R * nslots, 256), 256, 0, s>>>(c, active, slot0, nslots, ns, nd);
     return cudaGetLastError();
 }
 
@@ -848,15 +878,16 @@ cudaError_t launch_rom_step_b(const RomB& r, const int* active, int slot, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int nsub,
+cudaError_t launch_rom_reconstruct_b(const CplB& c, const int* active, const RomB& src, int zoh, int ns, int nd,
                                      cudaStream_t s) {
     if (c.R == 0) return cudaSuccess;
+    if (ns < 1 || nd < 1) return cudaErrorInvalidValue;
     if (zoh) {
-        dim3 g(grid_for(3LL * c.R, 128), nsub + 1, 3);
-        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 1, 0);
+        dim3 g(grid_for(3LL * c.R, 128), nd + 1, 3);
+        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 1, 0, ns, nd);
     } else {
-        dim3 g(grid_for(3LL * c.R, 128), nsub, 3);
-        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 0, 1);
+        dim3 g(grid_for(3LL * c.R, 128), nd, 3);
+        k_rom_reconstruct_b<<<g, 128, 0, s>>>(c, active, src, 0, 1, ns, nd);
     }
     return cudaGetLastError();
 }

@@ -26,7 +26,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
             "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
-            "osam_profile", "osam_profile_read", "osam_fp64_peak", "osam_hex8_force_noalloc", "osam_batch_init",
+            "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_hex8_force_noalloc", "osam_batch_init",
             "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
             "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
             "osam_set_graph", "osam_tuning", "opinf_select"]
@@ -46,7 +46,7 @@ class SubdomainDesc(C.Structure):
                 ("origin", C.c_double * 3), ("material", C.c_int), ("lambda_", C.c_double), ("mu", C.c_double),
                 ("rho", C.c_double), ("lambda_e", _vp), ("mu_e", _vp), ("dirichlet", _vp), ("u0", _vp), ("v0", _vp),
                 ("r", C.c_int), ("r_s", C.c_int), ("Phi", _vp), ("Phi_S", _vp), ("K", _vp), ("H", _vp), ("B", _vp),
-                ("c", _vp), ("integrator", C.c_int)]
+                ("c", _vp), ("integrator", C.c_int), ("n_substeps", C.c_int)]
 
 
 class CouplingDesc(C.Structure):
@@ -130,6 +130,7 @@ def load():
     L.osam_profile.argtypes = [_vp, C.c_int]
     L.osam_profile_read.argtypes = [_vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                     C.POINTER(C.c_longlong)]
+    L.osam_implicit_profile.argtypes = [_vp, _dp] + [C.POINTER(C.c_longlong)] * 4
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
     L.osam_batch_init.argtypes = [C.c_int, C.POINTER(ProblemDesc), C.POINTER(_vp)]
     L.osam_batch_step.argtypes = [_vp, C.POINTER(StepReport), C.POINTER(StepReport)]
@@ -226,6 +227,7 @@ class Batch:
                 d.origin = (C.c_double * 3)(*sd.origin)
                 d.material = _MAT[sd.material]
                 d.integrator = {"explicit": EXPLICIT, "implicit": IMPLICIT}[getattr(sd, "integrator", "explicit")]
+                d.n_substeps = int(getattr(sd, "n_substeps", 0) or 0)
                 d.lambda_, d.mu, d.rho = sd.lam, sd.mu, sd.rho
                 arrs = {"lambda_e": _f64(sd.lam_e), "mu_e": _f64(sd.mu_e), "dirichlet": _u8(sd.dirichlet),
                         "u0": _f64(sd.u0), "v0": _f64(sd.v0)}
@@ -309,6 +311,15 @@ class Batch:
         self._c(load().osam_profile_read(self.h, C.byref(ms), C.byref(fl), C.byref(fe), C.byref(kl)))
         return {"force_ms": ms.value, "force_launches": fl.value, "force_elements": fe.value,
                 "kernel_launches": kl.value}
+
+    def implicit_profile(self) -> dict:
+        """Tangent-action time / launches / elements and Newton / CG counts of the implicit subdomains
+        since the last profile() call (time only while profiling is enabled)."""
+        ms = C.c_double()
+        v = [C.c_longlong() for _ in range(4)]
+        self._c(load().osam_implicit_profile(self.h, C.byref(ms), *[C.byref(x) for x in v]))
+        return {"tangent_ms": ms.value, "tangent_launches": v[0].value, "tangent_elements": v[1].value,
+                "newton_steps": v[2].value, "cg_iterations": v[3].value}
 
     def sizes(self, i, inst=0):
         v = [C.c_int() for _ in range(4)]
