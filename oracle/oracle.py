@@ -76,6 +76,7 @@ def lib():
             L.orc_init.argtypes = [C.c_void_p]
             L.orc_set_implicit.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_set_substeps.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_set_additive.argtypes = [C.c_void_p, C.c_int]
             L.orc_step.argtypes = [C.c_void_p, _i, _d, _d]
             L.orc_num_nodes.argtypes = [C.c_void_p, C.c_int]
             L.orc_num_free.argtypes = [C.c_void_p, C.c_int]
@@ -254,6 +255,8 @@ class Problem:
             self._keep.append(m)
             if L.orc_couple(self.h, cp.dst, cp.src, _p(m)) < 0:
                 raise ValueError("oracle couple")
+        if getattr(spec, "schwarz", "multiplicative") == "additive":
+            L.orc_set_additive(self.h, 1)
         rc = L.orc_init(self.h)
         if rc != OK:
             raise OracleError(rc, "oracle init failed")

@@ -17,7 +17,8 @@
  *   - explicit Newmark (beta = 0, gamma = 1/2) in predictor / corrector form (Sec. 4.1), and implicit
  *     Newmark (beta = 1/4, gamma = 1/2) solved by Newton's method with the exact tangent
  *   - O-SAM controller of Algorithm 1 / Eq. schwarz_discrete with the criterion conv_criterion:
- *     multiplicative sweep over the subdomains in index order, pointwise spatial projector Pi
+ *     multiplicative sweep over the subdomains in index order (or the additive variant of Remark
+ *     additive_sam: every subdomain from the previous iteration's data), pointwise spatial projector Pi
  *     (trilinear interpolation in a donor element found by brute-force search and Newton inversion
  *     of the trilinear map), temporal interpolant Xi linear between the source's time levels
  *     (identity when the time steps agree); each subdomain has its own number of substeps.
@@ -683,6 +684,10 @@ typedef struct {
     osub sd[ORC_MAX_SUB];
     ocpl cpl[ORC_MAX_CPL];
     int initialised;
+    /* Schwarz variant: 0 multiplicative (each subdomain uses the data its predecessors published in
+     * the same iteration), 1 additive (every subdomain uses the previous iteration's data; Remark
+     * additive_sam) */
+    int additive;
 } oprob;
 
 static void* xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
@@ -922,6 +927,14 @@ int orc_set_implicit(void* vp, int i, int implicit) {
     oprob* p = (oprob*)vp;
     if (i < 0 || i >= p->nsd || p->sd[i].kind != ORC_FOM) return ORC_EINVAL;
     p->sd[i].implicit = implicit != 0;
+    return ORC_OK;
+}
+
+/* Schwarz variant of the controller: 0 multiplicative, 1 additive */
+int orc_set_additive(void* vp, int additive) {
+    oprob* p = (oprob*)vp;
+    if (p->initialised) return ORC_EINVAL;
+    p->additive = additive != 0;
     return ORC_OK;
 }
 
@@ -1268,7 +1281,10 @@ static void advance(oprob* p, int i) {
             if (p->cpl[k].src == i)
                 for (int j = 1; j <= s->nsub; ++j) trace_level(p, &p->cpl[k], j, 0);
     }
-    /* the interval's trace, mapped onto each destination's time levels */
+}
+
+/* the interval's trace of subdomain i, mapped onto each destination's time levels */
+static void publish_from(oprob* p, int i) {
     for (int k = 0; k < p->ncpl; ++k)
         if (p->cpl[k].src == i) publish(p, &p->cpl[k]);
 }
@@ -1338,7 +1354,8 @@ static void criterion(oprob* p, double* cnum, double* cden, int* nonfinite) {
 }
 
 /* One controller step I_k (Algorithm 1): save, zero-order-hold initial boundary data, then
- * multiplicative sweeps until the criterion holds at iteration n >= 2 or max_it is reached. */
+ * multiplicative (or additive) sweeps until the criterion holds at iteration n >= 2 or max_it is
+ * reached. */
 int orc_step(void* vp, int* iters, double* cnum_out, double* cden_out) {
     oprob* p = (oprob*)vp;
     if (!p->initialised) return ORC_EINVAL;
@@ -1349,7 +1366,12 @@ int orc_step(void* vp, int* iters, double* cnum_out, double* cden_out) {
     double cnum = 0.0, cden = 0.0;
     for (n = 1; n <= p->max_it; ++n) {
         if (n > 1) restore_state(p);
-        for (int i = 0; i < p->nsd; ++i) advance(p, i);
+        for (int i = 0; i < p->nsd; ++i) {
+            advance(p, i);
+            if (!p->additive) publish_from(p, i);
+        }
+        if (p->additive)
+            for (int i = 0; i < p->nsd; ++i) publish_from(p, i);
         int nonfinite = 0;
         criterion(p, &cnum, &cden, &nonfinite);
         if (nonfinite) { status = ORC_ENONFINITE; break; }

@@ -87,6 +87,7 @@ class Problem:
     max_iters: int = 64
     n_controller_steps: int = 1
     info: dict = field(default_factory=dict)
+    schwarz: str = "multiplicative"          # "multiplicative" (sequential sweep) or "additive"
 
     @property
     def fom_elements(self) -> int:

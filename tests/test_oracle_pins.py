@@ -580,3 +580,72 @@ def test_mixed_time_steps_converge_at_second_order(oracle):
         errs.append(e)
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, errs
+
+
+# ---------------------------------------------------------------------------------------------
+# additive Schwarz and ROM-ROM coupling
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("integrator", ["explicit", "implicit"])
+def test_additive_schwarz_reaches_the_single_domain_solution(oracle, integrator):
+    """Additive (Jacobi) sweeps converge to the same coupled solution as multiplicative ones: the
+    single-domain solution for conforming overlapping FOMs (to the Schwarz tolerance), using more
+    iterations (information crosses one overlap per iteration instead of a whole sweep)."""
+    p = W.bar_chain("add", 3, [8, 8], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10, tol_rel=1e-13,
+                    max_iters=80)
+    ps = W.single_bar("one", 3, 14, "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10)
+    for sd in p.subdomains + ps.subdomains:
+        sd.integrator = integrator
+    pm = W.bar_chain("mul", 3, [8, 8], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10, tol_rel=1e-13,
+                     max_iters=80)
+    for sd in pm.subdomains:
+        sd.integrator = integrator
+    p.schwarz = "additive"
+    A, S, M = oracle.Problem(p), oracle.Problem(ps), oracle.Problem(pm)
+    its_a, its_m = [], []
+    for _ in range(3):
+        ra, rm = A.step(), M.step()
+        S.step()
+        assert ra["status"] == oracle.OK and rm["status"] == oracle.OK
+        its_a.append(ra["iterations"])
+        its_m.append(rm["iterations"])
+    us = S.state(0)[0]
+    nn = 4 * 4
+    for i, k0 in ((0, 0), (1, 6)):
+        u = A.state(i)[0]
+        assert np.abs(u - us[k0 * nn:k0 * nn + u.shape[0]]).max() < 1e-7 * np.abs(us).max()
+    assert sum(its_a) > sum(its_m)
+
+
+def test_additive_first_iteration_uses_only_the_zero_order_hold(oracle):
+    """One iteration: the first subdomain of the sweep runs on the held data in both variants (equal
+    states); the second sees its neighbour's new trace only in the multiplicative variant."""
+    p = W.bar_chain("add1", 3, [6, 6], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=1)
+    p.schwarz = "additive"
+    A = oracle.Problem(p)
+    A.step()
+    q = W.bar_chain("add1", 3, [6, 6], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=1)
+    B = oracle.Problem(q)
+    B.step()
+    assert np.array_equal(A.state(0)[0], B.state(0)[0])
+    assert not np.array_equal(A.state(1)[0], B.state(1)[0])
+
+
+def test_rom_rom_full_basis_reproduces_fom_fom(oracle):
+    """OpInf-OpInf coupling: two exact full-basis linear ROMs reproduce the FOM-FOM run to rounding
+    (ROM -> ROM reconstruction into the other ROM's boundary snapshots), multiplicative and additive."""
+    for variant in ("multiplicative", "additive"):
+        pf = W.bar_chain("ff", 2, [4, 4], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=200)
+        pr = W.bar_chain("rr", 2, [4, 4], ["rom", "rom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=200)
+        pf.schwarz = pr.schwarz = variant
+        ops0, free0 = _exact_linear_rom(oracle, pf, 0)
+        ops1, free1 = _exact_linear_rom(oracle, pf, 1)
+        A = oracle.Problem(pf)
+        B = oracle.Problem(pr, rom_ops={0: ops0, 1: ops1})
+        for _ in range(4):
+            ra, rb = A.step(), B.step()
+            assert rb["status"] == oracle.OK and ra["iterations"] == rb["iterations"]
+        for i, free in ((0, free0), (1, free1)):
+            u = A.state(i)[0]
+            q = B.rom_state(i)[0]
+            assert np.abs(q - u.reshape(-1)[free]).max() < 1e-12 * np.abs(u).max()
+            assert np.abs(B.state(i)[0] - u).max() < 1e-12 * np.abs(u).max()
