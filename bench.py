@@ -57,6 +57,8 @@ FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # valid only for the kernel source and variant (tiled or not) it was captured on.
 FORCE_TRAFFIC = {"source_sha256": "7b75524b888890d04e6831c55ebaea5cea934da54f34e6f946ab80b46e453866", "bytes_per_launch": 3.573e6,
                  "tiled": True}
+# the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
+TANGENT_TRAFFIC = {"source_sha256": None, "bytes_per_launch": 6.708e6}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -66,6 +68,9 @@ STATE_BYTES_PER_NODE_UPDATE = 152
 # traces, scalar chain, dP) + 36 accumulation + 180 transposed interpolation + 48 nodal accumulation
 # + 6 material constants.
 TANGENT_FLOPS_PER_NH_ELEMENT = 2670
+# FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
+# around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
+FLOPS_PER_SVK_ELEMENT = 1424
 
 
 def measured_hbm_gbs():
@@ -167,12 +172,15 @@ class ClockSampler:
         return out
 
 
-def source_sha():
+def source_sha(files=("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh")):
     import hashlib
     h = hashlib.sha256()
-    for f in ("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2511_20687_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+TANGENT_SOURCES = ("tangent_kernels.cu", "hex8_math.cuh", "nh_tangent.cuh")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -187,19 +195,22 @@ def rom_dof_masks(sd):
     return free, np.repeat(schwarz, 3)
 
 
-def train_rom(W, osam, args, device, log):
+def train_rom(W, osam, args, device, log, material="nh", rank=None, cubic=False, snapshots=None):
     """Seeded FOM-FOM training run (snapshot every 4th step) and GPU OpInf fit of subdomain B."""
+    rank = rank or args.rank
+    n_snap = snapshots or args.snapshots
     rng = np.random.default_rng(W.SEED_BASE + 1)
     amp = float(rng.uniform(0.5e-3, 1.0e-3))
-    spec = W.bar_chain("train", args.n, [args.nz, args.nz], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, amp, 1e-6, 4)
+    nu = 0.3 if material == "svk" else 0.25
+    spec = W.bar_chain("train", args.n, [args.nz, args.nz], ["fom", "fom"], material, 1e9, nu, 1000.0, amp, 1e-6, 4)
     prob = osam.Problem(spec, device=device)
     free, sdof = rom_dof_masks(spec.subdomains[1])
-    U = np.empty((args.snapshots, int(free.sum())))
+    U = np.empty((n_snap, int(free.sum())))
     A = np.empty_like(U)
-    S = np.empty((args.snapshots, int(sdof.sum())))
+    S = np.empty((n_snap, int(sdof.sum())))
     t0 = time.time()
     v0 = None
-    for k in range(args.snapshots):
+    for k in range(n_snap):
         prob.step()
         u, v, a = prob.state(1, fields=(0, 1, 2) if k == 0 else (0, 2))
         U[k] = u.reshape(-1)[free]
@@ -208,14 +219,17 @@ def train_rom(W, osam, args, device, log):
         if k == 0:
             v0 = v.reshape(-1)[free].copy()
     prob.close()
-    log(f"training run: {args.snapshots} controller steps of 4 substeps in {time.time() - t0:.1f}s (amplitude {amp:.3e})")
+    log(f"training run ({material}): {n_snap} controller steps of 4 substeps in {time.time() - t0:.1f}s "
+        f"(amplitude {amp:.3e})")
     t0 = time.time()
-    ops = osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device)
+    ops = osam.opinf_fit(U, A, S, r=rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device,
+                         cubic=cubic)
     fit_s = time.time() - t0
-    log(f"opinf_fit: r={args.rank} r_s={ops['r_s']} in {fit_s:.1f}s")
-    fit = {"gpu_seconds": fit_s, "r": args.rank, "r_s": int(ops["r_s"]), "n_snap": args.snapshots,
+    log(f"opinf_fit: r={rank} r_s={ops['r_s']}{' cubic' if cubic else ''} in {fit_s:.1f}s")
+    fit = {"gpu_seconds": fit_s, "r": rank, "r_s": int(ops["r_s"]), "n_snap": n_snap,
            "n_dof": int(U.shape[1]), "n_sdof": int(S.shape[1]), "training": (U, A, S, v0)}
-    return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}, fit
+    keys = ("Phi", "Phi_S", "K", "H", "B", "c") + (("C",) if cubic else ())
+    return {k: ops[k] for k in keys}, fit
 
 
 def train_batched_roms(W, osam, torch, specs_ff, snapshots, r, device, log, chunk=32):
@@ -462,7 +476,9 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
             "tangent_time_share": ip["tangent_ms"] / total_ms if total_ms else None,
             "roofline": {"bound": "alu", "kernel": "k_tangent_b<NeoHookean>", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None, "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
+                         "traffic": (TANGENT_TRAFFIC["bytes_per_launch"]
+                                     if TANGENT_TRAFFIC["source_sha256"] == source_sha(TANGENT_SOURCES) else None),
+                         "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
                          "ms_per_launch": ip["tangent_ms"] / max(1, ip["tangent_launches"]),
                          "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)"},
             "timing": "library CUDA events around each controller step (host-driven, L2 flushed between steps); "
@@ -473,6 +489,74 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
             "sample_gpu_value": ns * rg["iterations"] / (rg["elapsed_ms"] * 1e-3),
             "sample_oracle_value": ns / cpu_s, "oracle_cores": 1,
             "parity": "1e-9 relative L2 vs the oracle (tests/test_gpu_implicit.py)"}
+
+
+def _timed_steps(prob, torch, flush, steps, warmup):
+    for _ in range(warmup):
+        prob.step()
+    ms, upd, its = 0.0, 0, []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        r = prob.step()
+        ms += r["elapsed_ms"]
+        upd += r["element_updates"]
+        its.append(r["iterations"])
+    return ms, upd, its
+
+
+def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5, warmup=2):
+    """The headline hybrid under the method's other variants (each a parity-tested path):
+    additive sweeps (FOM and ROM concurrently on their own streams), mixed time integrators and steps
+    (the FOM implicit with 2 substeps of 10 us per controller step, the ROM explicit with 20 of 1 us,
+    coupled through the temporal interpolant), and the Saint Venant-Kirchhoff FOM with a cubic OpInf
+    ROM (r = 20, fitted on the GPU from a Saint Venant-Kirchhoff FOM-FOM run).  Metric as the headline,
+    plus the controller intervals advanced per second (T = 20 us each)."""
+    out = {}
+    T = 20e-6
+    spec = hybrid_spec(W, args)
+    spec.schwarz = "additive"
+    prob = osam.Problem(spec, rom_ops=rom_ops, device=local)
+    ms, upd, its = _timed_steps(prob, torch, flush, steps, warmup)
+    prob.close()
+    out["additive"] = {"value": upd / (ms * 1e-3), "ms_per_step": ms / steps, "mean_iterations": float(np.mean(its)),
+                       "intervals_per_s": steps / (ms * 1e-3),
+                       "workload": "headline hybrid, additive sweeps (FOM and ROM on their own streams)"}
+    spec = hybrid_spec(W, args)
+    spec.subdomains[0].integrator = "implicit"
+    spec.subdomains[0].n_substeps = 2
+    prob = osam.Problem(spec, rom_ops=rom_ops, device=local)
+    ms, upd, its = _timed_steps(prob, torch, flush, max(2, steps // 2), 1)
+    prob.close()
+    n = max(2, steps // 2)
+    out["mixed_implicit_explicit"] = {
+        "value": upd / (ms * 1e-3), "ms_per_step": ms / n, "mean_iterations": float(np.mean(its)),
+        "intervals_per_s": n / (ms * 1e-3),
+        "workload": "headline hybrid, FOM implicit (Newmark 1/4, 1/2) with 2 substeps of 10 us, ROM explicit with "
+                    "20 substeps of 1 us, temporal interpolant between them (host-driven steps)"}
+    svk_ops, svk_fit = train_rom(W, osam, args, local, log, material="svk", rank=20, cubic=True, snapshots=300)
+    spec = W.bar_chain("svk_copinf", args.n, [args.nz, args.nz], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 1e-3,
+                       1e-6, 20, max_iters=64)
+    prob = osam.Problem(spec, rom_ops={1: svk_ops}, device=local)
+    ms, upd, its = _timed_steps(prob, torch, flush, steps, warmup)
+    p_ms, p_upd, _, prof = timed_pass(prob, torch, flush, 2, profile=True)
+    prob.close()
+    achieved = FLOPS_PER_SVK_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
+    out["svk_copinf"] = {
+        "value": upd / (ms * 1e-3), "ms_per_step": ms / steps, "mean_iterations": float(np.mean(its)),
+        "intervals_per_s": steps / (ms * 1e-3),
+        "workload": f"{args.n}x{args.n}x{args.nz} Saint Venant-Kirchhoff FOM + cubic OpInf ROM r=20 "
+                    f"(r_s={svk_fit['r_s']}, fitted on {svk_fit['n_snap']} snapshots of an SVK FOM-FOM run)",
+        "fit_seconds": svk_fit["gpu_seconds"],
+        "roofline": {"bound": "alu", "kernel": "k_force_*<SaintVenantKirchhoff>", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "flops_per_element": FLOPS_PER_SVK_ELEMENT,
+                     "force_ms_per_launch": prof["force_ms"] / max(1, prof["force_launches"])}}
+    for k, v in out.items():
+        log(f"{k}: {v['value']:.3e} element-updates/s, {v['ms_per_step']:.2f} ms/step, {v['mean_iterations']:.1f} its")
+    out["note"] = (f"intervals_per_s: controller intervals of {T * 1e6:.0f} us advanced per second; "
+                   "parity: tests/test_gpu_additive.py, test_gpu_mixed_dt.py, test_gpu_svk.py, test_gpu_cubic.py")
+    return out
 
 
 def hybrid_spec(W, args):
@@ -721,8 +805,10 @@ def main():
         fit_meas = measure_fit(fit_info, log)
         select_meas = measure_select(osam, fit_info, local, log)
         adjoint_meas = measure_adjoint(W, osam, local, log)
+    next_meas = None
     if world == 1 and not args.no_implicit and rom_ops:
         implicit_meas = measure_implicit(W, osam, torch, flush, rom_ops, args, local, log)
+        next_meas = measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
@@ -775,7 +861,7 @@ def main():
                 "gpu_launches": head["launches"] if world == 1 else None,
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
                 "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
-                "adjoint": adjoint_meas, "implicit": implicit_meas,
+                "adjoint": adjoint_meas, "implicit": implicit_meas, "next_rows": next_meas,
                 "hbm": hbm,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}

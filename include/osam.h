@@ -49,10 +49,11 @@ typedef enum {
 } osam_status;
 
 enum { OSAM_FOM = 0, OSAM_ROM = 1 };
-enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1 };
+enum { OSAM_LINEAR_ELASTIC = 0, OSAM_NEO_HOOKEAN = 1, OSAM_SAINT_VENANT_KIRCHHOFF = 2 };
 /* FOM time integrator: explicit Newmark (beta = 0, gamma = 1/2, central difference) or implicit
  * Newmark (beta = 1/4, gamma = 1/2, average acceleration) */
 enum { OSAM_EXPLICIT = 0, OSAM_IMPLICIT = 1 };
+enum { OSAM_MULTIPLICATIVE = 0, OSAM_ADDITIVE = 1 };
 /* OSAM_FP64: native FP64 everywhere.  OSAM_FP32_FORCE: internal force in FP32 (checked to 1e-5).
  * OSAM_F32X2_FORCE: internal force in double-float arithmetic (pairs of FP32 values, ~48-bit
  * significands) on the FP32 pipes, state and time integration in FP64 (checked to 1e-9 like FP64);
@@ -90,7 +91,8 @@ typedef struct {
     double h;                 /* element edge (> 0) */
     double origin[3];
     /* FOM material */
-    int material;             /* OSAM_LINEAR_ELASTIC or OSAM_NEO_HOOKEAN */
+    int material;             /* OSAM_LINEAR_ELASTIC, OSAM_NEO_HOOKEAN or OSAM_SAINT_VENANT_KIRCHHOFF (A.2:
+                               * E = 1/2 (F^T F - I), S = lambda tr(E) I + 2 mu E, P = F S) */
     double lambda, mu, rho;   /* Lame parameters and density (kappa = lambda + 2/3 mu for NH) */
     const double* lambda_e;   /* optional per-element Lame parameters [nx*ny*nz], NULL = uniform */
     const double* mu_e;
@@ -117,6 +119,10 @@ typedef struct {
      * counts go through the temporal interpolant Xi: linear in time between the two source levels
      * that bracket each destination level (identity for equal counts). */
     int n_substeps;
+    /* cubic OpInf (COpInf, Eq. opinf_rom with all terms): qdd += C kron3_c(q), kron3_c(q) =
+     * (q_i q_j q_k)_{i<=j<=k} in lexicographic order; [r][r(r+1)(r+2)/6] row-major, or NULL for the
+     * quadratic model; r <= 128 with it */
+    const double* C;
 } osam_subdomain_desc;
 
 /* Dirichlet transfer from subdomain src to the Schwarz boundary nodes of dst (Sec. 4.1): the data
@@ -141,6 +147,11 @@ typedef struct {
     int scatter;              /* OSAM_SCATTER_* */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream */
     int device;               /* CUDA device ordinal */
+    /* OSAM_MULTIPLICATIVE (Algorithm 1: subdomains in index order, each from the data its
+     * predecessors published in the same iteration) or OSAM_ADDITIVE (Remark additive_sam: every
+     * subdomain from the previous iteration's data, all subdomains advanced concurrently on their own
+     * streams, then every transfer) */
+    int schwarz;
 } osam_problem_desc;
 
 typedef struct {
@@ -284,7 +295,7 @@ OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int mater
  *   pod_cutoff), boundary POD of the Schwarz snapshots S with the smallest r_s whose energy
  *   E_r (Eq. pod_energy) reaches energy_s (capped at r_s_max; r_s > 0 in the input fixes it),
  *   projection Ubar = Phi^T U, Abar = Phi^T A, Ghat = Phi_S^T S, and the Tikhonov regression
- *   min ||D O - Abar^T||^2 + lambda ||O||^2, D = [Ubar^T, kron_c(Ubar)^T, Ghat^T, 1]
+ *   min ||D O - Abar^T||^2 + lambda ||O||^2, D = [Ubar^T, kron_c(Ubar)^T, (kron3_c(Ubar)^T,) Ghat^T, 1]
  *   (one scalar lambda for every block; the dual form D^T (D D^T + lambda I)^-1 Abar^T is used when
  *   D has more columns than rows).  Snapshot matrices are [n_snap][n_dof] (one snapshot per row).
  * ------------------------------------------------------------------------------------------------ */
@@ -301,6 +312,8 @@ typedef struct {
     int quadratic;            /* 1: quadratic OpInf, 0: linear (H = 0) */
     void* stream;
     int device;
+    int cubic;                /* 1: cubic OpInf (COpInf): the block kron3_c(Ubar)^T after the quadratic one,
+                               * operator C [r][r(r+1)(r+2)/6] (implies the quadratic block); r <= 128 */
 } osam_fit_input;
 
 typedef struct {
@@ -313,6 +326,7 @@ typedef struct {
     double* sigma;            /* [n_snap] singular values of U, or NULL */
     double* sigma_s;          /* [n_snap] singular values of S, or NULL */
     int r_s;                  /* selected boundary rank */
+    double* C;                /* [r][r(r+1)(r+2)/6] cubic operator (cubic fits), or NULL */
 } osam_fit_output;
 
 OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out);

@@ -11,9 +11,12 @@ steps: numpy's thin SVD for POD and a dense solve of the normal equations for th
     boundary data ghat = Phi_S^T s.
   * regression (Eq. opinf_schwarz_inference), solved form qdd = K q + H kron_c(q) + B ghat + c:
     minimise ||D O - Y||_F^2 + lambda ||O||_F^2 with D = [Ubar^T, kron_c(Ubar)^T, Ghat^T, 1],
-    Y = Abar^T (projected acceleration snapshots), one scalar lambda for every block.
+    Y = Abar^T (projected acceleration snapshots), one scalar lambda for every block.  The cubic
+    model (COpInf, Eq. quadratic_opinf with all terms) adds C kron3_c(q) and the block
+    kron3_c(Ubar)^T after the quadratic one.
   * kron_c(q) = (q_i q_j)_{i <= j} in row-major upper-triangle order (compressed symmetric
-    Kronecker square, the footnote of Sec. 2).
+    Kronecker square, the footnote of Sec. 2); kron3_c(q) = (q_i q_j q_k)_{i <= j <= k} in the same
+    lexicographic order (compressed Kronecker cube, r(r+1)(r+2)/6 entries).
 """
 from __future__ import annotations
 
@@ -48,10 +51,23 @@ def kron_c(Q: np.ndarray) -> np.ndarray:
     return np.array(rows)
 
 
-def data_matrix(Ubar: np.ndarray, Ghat: np.ndarray, quadratic: bool = True) -> np.ndarray:
+def kron3_c(Q: np.ndarray) -> np.ndarray:
+    """Compressed Khatri-Rao cube of the columns of Q (r x n) -> (r(r+1)(r+2)/6 x n)."""
+    r = Q.shape[0]
+    rows = []
+    for i in range(r):
+        for j in range(i, r):
+            for k in range(j, r):
+                rows.append(Q[i] * Q[j] * Q[k])
+    return np.array(rows).reshape(-1, Q.shape[1])
+
+
+def data_matrix(Ubar: np.ndarray, Ghat: np.ndarray, quadratic: bool = True, cubic: bool = False) -> np.ndarray:
     blocks = [Ubar.T]
-    if quadratic:
+    if quadratic or cubic:
         blocks.append(kron_c(Ubar).T)
+    if cubic:
+        blocks.append(kron3_c(Ubar).T)
     blocks.append(Ghat.T)
     blocks.append(np.ones((Ubar.shape[1], 1)))
     return np.hstack(blocks)
@@ -63,17 +79,23 @@ def tikhonov(D: np.ndarray, Y: np.ndarray, lam: float) -> np.ndarray:
     return np.linalg.solve(D.T @ D + lam * np.eye(d), D.T @ Y)
 
 
-def unpack(O: np.ndarray, r: int, r_s: int, quadratic: bool = True):
+def unpack(O: np.ndarray, r: int, r_s: int, quadratic: bool = True, cubic: bool = False):
+    """Operator blocks of the stacked solution O; with cubic=True returns (K, H, C, B, c)."""
+    quadratic = quadratic or cubic
     nq = r * (r + 1) // 2 if quadratic else 0
+    nc = r * (r + 1) * (r + 2) // 6 if cubic else 0
     K = O[:r].T.copy()
     H = O[r:r + nq].T.copy() if quadratic else np.zeros((r, r * (r + 1) // 2))
-    B = O[r + nq:r + nq + r_s].T.copy()
-    c = O[r + nq + r_s].copy()
+    C = O[r + nq:r + nq + nc].T.copy()
+    B = O[r + nq + nc:r + nq + nc + r_s].T.copy()
+    c = O[r + nq + nc + r_s].copy()
+    if cubic:
+        return K, H, C, B, c
     return K, H, B, c
 
 
 def opinf_fit(U: np.ndarray, A: np.ndarray, S: np.ndarray, r: int, lam: float, r_s: int = None,
-              energy_s: float = 1.0 - 1e-6, r_s_max: int = 64, quadratic: bool = True):
+              energy_s: float = 1.0 - 1e-6, r_s_max: int = 64, quadratic: bool = True, cubic: bool = False):
     """U, A: free-dof displacement / acceleration snapshots (n_dof x n_snap); S: Schwarz boundary
     snapshots (n_sdof x n_snap).  Returns the ROM operators and bases."""
     Phi, sigma = pod(U, r)
@@ -84,15 +106,21 @@ def opinf_fit(U: np.ndarray, A: np.ndarray, S: np.ndarray, r: int, lam: float, r
     Ubar = Phi.T @ U
     Abar = Phi.T @ A
     Ghat = Phi_S.T @ S
-    D = data_matrix(Ubar, Ghat, quadratic)
+    D = data_matrix(Ubar, Ghat, quadratic, cubic)
     O = tikhonov(D, Abar.T, lam)
-    K, H, B, c = unpack(O, r, r_s, quadratic)
-    return {"Phi": Phi, "Phi_S": Phi_S, "K": K, "H": H, "B": B, "c": c, "sigma": sigma, "sigma_s": sigma_s,
-            "r": r, "r_s": r_s}
+    ops = {"Phi": Phi, "Phi_S": Phi_S, "sigma": sigma, "sigma_s": sigma_s, "r": r, "r_s": r_s}
+    if cubic:
+        ops["K"], ops["H"], ops["C"], ops["B"], ops["c"] = unpack(O, r, r_s, quadratic, cubic)
+    else:
+        ops["K"], ops["H"], ops["B"], ops["c"] = unpack(O, r, r_s, quadratic)
+    return ops
 
 
-def rom_rhs(K, H, B, c, q, ghat):
-    return K @ q + H @ kron_c(q[:, None])[:, 0] + B @ ghat + c
+def rom_rhs(K, H, B, c, q, ghat, C=None):
+    out = K @ q + H @ kron_c(q[:, None])[:, 0] + B @ ghat + c
+    if C is not None:
+        out = out + C @ kron3_c(q[:, None])[:, 0]
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -103,7 +131,7 @@ def lambda_grid(n: int = 11, lo: float = 1e-10, hi: float = 1.0) -> np.ndarray:
     return np.logspace(np.log10(lo), np.log10(hi), n)
 
 
-def rollout_frozen(K, H, B, c, q0, qd0, qdd0, Ghat, dt, k):
+def rollout_frozen(K, H, B, c, q0, qd0, qdd0, Ghat, dt, k, C=None):
     """Advance the ROM alone with its Schwarz boundary data frozen to the training columns.
 
     Explicit central differences (Newmark beta = 0, gamma = 1/2) with step dt; the snapshot columns
@@ -119,14 +147,15 @@ def rollout_frozen(K, H, B, c, q0, qd0, qdd0, Ghat, dt, k):
             for s in range(1, k + 1):
                 g = Ghat[:, j] + (s / k) * (Ghat[:, j + 1] - Ghat[:, j])
                 q = q + dt * qd + 0.5 * dt * dt * qdd
-                qdd_new = rom_rhs(K, H, B, c, q, g)
+                qdd_new = rom_rhs(K, H, B, c, q, g, C)
                 qd = qd + 0.5 * dt * (qdd + qdd_new)
                 qdd = qdd_new
             Q[:, j + 1] = q
     return Q
 
 
-def select_lambda(U, A, S, v0, r, lambdas, dt, k, r_s=None, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True):
+def select_lambda(U, A, S, v0, r, lambdas, dt, k, r_s=None, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True,
+                  cubic=False):
     """Algorithm 3: for every candidate lambda fit the operators (Eq. opinf_schwarz_inference), roll
     the ROM out from the training initial state (q0 = Phi^T u_0, qd0 = Phi^T v_0, qdd0 = Phi^T a_0)
     under the frozen training boundary data, score E(lambda) = ||Q - Ubar||_F / ||Ubar||_F (a
@@ -134,11 +163,11 @@ def select_lambda(U, A, S, v0, r, lambdas, dt, k, r_s=None, energy_s=1.0 - 1e-6,
     the selected lambda)."""
     errors = []
     for lam in lambdas:
-        ops = opinf_fit(U, A, S, r, lam, r_s, energy_s, r_s_max, quadratic)
+        ops = opinf_fit(U, A, S, r, lam, r_s, energy_s, r_s_max, quadratic, cubic)
         Phi, PhiS = ops["Phi"], ops["Phi_S"]
         Ubar = Phi.T @ U
         Q = rollout_frozen(ops["K"], ops["H"], ops["B"], ops["c"], Ubar[:, 0], Phi.T @ v0, Phi.T @ A[:, 0],
-                           PhiS.T @ S, dt, k)
+                           PhiS.T @ S, dt, k, ops.get("C"))
         if np.all(np.isfinite(Q)):
             errors.append(float(np.linalg.norm(Q - Ubar) / np.linalg.norm(Ubar)))
         else:
@@ -147,4 +176,4 @@ def select_lambda(U, A, S, v0, r, lambdas, dt, k, r_s=None, energy_s=1.0 - 1e-6,
             r_s = ops["r_s"]   # the boundary basis does not depend on lambda
     errors = np.array(errors)
     best = int(np.argmin(errors))
-    return errors, best, opinf_fit(U, A, S, r, float(lambdas[best]), r_s, energy_s, r_s_max, quadratic)
+    return errors, best, opinf_fit(U, A, S, r, float(lambdas[best]), r_s, energy_s, r_s_max, quadratic, cubic)

@@ -26,7 +26,7 @@ class OracleError(ValueError):
     def __init__(self, code, msg):
         super().__init__(f"{msg}: {code}")
         self.code = code
-LE, NH = 0, 1
+LE, NH, SVK = 0, 1, 2
 
 _d = C.POINTER(C.c_double)
 _i = C.POINTER(C.c_int)
@@ -76,7 +76,10 @@ def lib():
             L.orc_init.argtypes = [C.c_void_p]
             L.orc_set_implicit.argtypes = [C.c_void_p, C.c_int, C.c_int]
             L.orc_set_substeps.argtypes = [C.c_void_p, C.c_int, C.c_int]
+            L.orc_tangent_action.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, _d, C.c_int, C.c_double,
+                                             C.c_double, _d, _d, _d]
             L.orc_set_additive.argtypes = [C.c_void_p, C.c_int]
+            L.orc_set_rom_cubic.argtypes = [C.c_void_p, C.c_int, _d]
             L.orc_step.argtypes = [C.c_void_p, _i, _d, _d]
             L.orc_num_nodes.argtypes = [C.c_void_p, C.c_int]
             L.orc_num_free.argtypes = [C.c_void_p, C.c_int]
@@ -111,6 +114,8 @@ def _f64(a):
 
 
 def _mat(name):
+    if name in ("svk", "saint_venant_kirchhoff", SVK):
+        return SVK
     return NH if name in ("nh", "neo_hookean", NH) else LE
 
 
@@ -145,6 +150,15 @@ def stress(material, H, lam, mu):
 def energy_density(material, H, lam, mu):
     H = _f64(H).reshape(9)
     return lib().orc_energy_density(_mat(material), _p(H), lam, mu)
+
+
+def tangent_action(dims, h, origin, material, lam, mu, u, p):
+    """K(u) p with the oracle's assembled element tangents (Appendix A tangents)."""
+    nx, ny, nz = dims
+    u, p = _f64(u), _f64(p)
+    y = np.zeros(u.size)
+    lib().orc_tangent_action(nx, ny, nz, h, _p(_f64(origin)), _mat(material), lam, mu, _p(u), _p(p), _p(y))
+    return y
 
 
 def lumped_mass(dims, h, origin, rho):
@@ -246,6 +260,10 @@ class Problem:
                 self.rank[i] = r
                 rc = L.orc_add_rom(self.h, nx, ny, nz, sd.h, _p(org), _p(dm), r, rs, arrs[0].shape[0],
                                    arrs[1].shape[0], *[_p(a) for a in arrs], _p(u0), _p(v0))
+                if rc >= 0 and ops.get("C") is not None:
+                    Cc = _f64(ops["C"])
+                    self._keep.append(Cc)
+                    rc = L.orc_set_rom_cubic(self.h, i, _p(Cc))
             if rc >= 0 and getattr(sd, "n_substeps", 0):
                 rc = L.orc_set_substeps(self.h, i, int(sd.n_substeps))
             if rc < 0:

@@ -40,7 +40,7 @@
 #define ORC_MAX_CPL 16
 
 enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_EINVAL = -1, ORC_ECFL = -2, ORC_ENONFINITE = -3, ORC_EDONOR = -4, ORC_ENOMEM = -7 };
-enum { ORC_LE = 0, ORC_NH = 1 };
+enum { ORC_LE = 0, ORC_NH = 1, ORC_SVK = 2 };
 enum { ORC_FOM = 0, ORC_ROM = 1 };
 
 /* ------------------------------------------------------------------------------------------ */
@@ -266,9 +266,75 @@ static void nh_tangent(const double H[3][3], const double G[3][3], double dPk[3]
         }
 }
 
+/* A.2 Saint Venant-Kirchhoff: F = I + H, E = 1/2 (F^T F - I) (the printed "1/2 F^T F - I" read as the
+ * Green-Lagrange strain), S = lambda tr(E) I + 2 mu E, P = F S. */
+static void svk_strain(const double H[3][3], double F[3][3], double E[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) F[i][j] = H[i][j] + (i == j ? 1.0 : 0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double c = 0.0;
+            for (int k = 0; k < 3; ++k) c += F[k][i] * F[k][j];
+            E[i][j] = 0.5 * (c - (i == j ? 1.0 : 0.0));
+        }
+}
+
+static void stress_svk(const double H[3][3], double lam, double mu, double P[3][3]) {
+    double F[3][3], E[3][3], S[3][3];
+    svk_strain(H, F, E);
+    double tr = E[0][0] + E[1][1] + E[2][2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[i][j] = 2.0 * mu * E[i][j] + (i == j ? lam * tr : 0.0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            P[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) P[i][j] += F[i][k] * S[k][j];
+        }
+}
+
+/* A.2 energy: lambda/2 (tr E)^2 + mu tr(E^2) */
+static double energy_svk(const double H[3][3], double lam, double mu) {
+    double F[3][3], E[3][3];
+    svk_strain(H, F, E);
+    double tr = E[0][0] + E[1][1] + E[2][2], tr2 = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) tr2 += E[i][j] * E[j][i];
+    return 0.5 * lam * tr * tr + mu * tr2;
+}
+
+/* dP = G S + F dS, dS = lambda tr(dE) I + 2 mu dE, dE = 1/2 (G^T F + F^T G) */
+static void svk_tangent(const double H[3][3], const double G[3][3], double lam, double mu, double dP[3][3]) {
+    double F[3][3], E[3][3], S[3][3], dE[3][3], dS[3][3];
+    svk_strain(H, F, E);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double c = 0.0;
+            for (int k = 0; k < 3; ++k) c += G[k][i] * F[k][j] + F[k][i] * G[k][j];
+            dE[i][j] = 0.5 * c;
+        }
+    double tr = E[0][0] + E[1][1] + E[2][2], dtr = dE[0][0] + dE[1][1] + dE[2][2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            S[i][j] = 2.0 * mu * E[i][j] + (i == j ? lam * tr : 0.0);
+            dS[i][j] = 2.0 * mu * dE[i][j] + (i == j ? lam * dtr : 0.0);
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            dP[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k) dP[i][j] += G[i][k] * S[k][j] + F[i][k] * dS[k][j];
+        }
+}
+
 static void stress(int model, const double H[3][3], double lam, double mu, double P[3][3]) {
     if (model == ORC_NH) stress_nh(H, lam, mu, P);
+    else if (model == ORC_SVK) stress_svk(H, lam, mu, P);
     else stress_le(H, lam, mu, P);
+}
+
+static double energy(int model, const double H[3][3], double lam, double mu) {
+    if (model == ORC_NH) return energy_nh(H, lam, mu);
+    if (model == ORC_SVK) return energy_svk(H, lam, mu);
+    return energy_le(H, lam, mu);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -460,7 +526,7 @@ double orc_strain_energy(int nx, int ny, int nz, double h, const double* org, in
         for (int g = 0; g < 8; ++g) {
             double detJ = physical_gradients(X, g, dNdX);
             grad_at(U, dNdX, H);
-            E += detJ * (model == ORC_NH ? energy_nh(H, le, me) : energy_le(H, le, me));
+            E += detJ * energy(model, H, le, me);
         }
     }
     return E;
@@ -477,7 +543,7 @@ int orc_stress(int model, const double* H, double lam, double mu, double* P) {
 double orc_energy_density(int model, const double* H, double lam, double mu) {
     double Hm[3][3];
     for (int i = 0; i < 9; ++i) Hm[i / 3][i % 3] = H[i];
-    return model == ORC_NH ? energy_nh(Hm, lam, mu) : energy_le(Hm, lam, mu);
+    return energy(model, Hm, lam, mu);
 }
 
 void orc_lumped_mass(int nx, int ny, int nz, double h, const double* org, double rho, double* mass) {
@@ -544,6 +610,7 @@ static void force_vjp(const omesh* m, int model, const double* lam_e, const doub
 int orc_force_vjp(int nx, int ny, int nz, double h, const double* org, int model, const double* lam_e,
                   const double* mu_e, const double* u, const double* ybar, double* ubar, double* lam_bar,
                   double* mu_bar) {
+    if (model == ORC_SVK) return ORC_EINVAL; /* the adjoint covers LE and NH */
     omesh m;
     mesh_set(&m, nx, ny, nz, h, org);
     force_vjp(&m, model, lam_e, mu_e, u, ybar, ubar, lam_bar, mu_bar);
@@ -658,6 +725,7 @@ typedef struct {
     double *Phi, *PhiS, *K, *Hq, *B, *c;
     double *q, *qd, *qdd, *sq, *sqd, *sqdd, *pq, *pqd;
     double* qrec;         /* recorded reduced history [(nsub+1)][3][r] */
+    double* Cq;           /* cubic operator [r][r(r+1)(r+2)/6] (COpInf) or NULL */
     double* ghat;
     int rs_rows;          /* declared row count of PhiS */
     /* time integrator of a FOM: 0 explicit central differences, 1 implicit average acceleration */
@@ -701,7 +769,7 @@ void* orc_problem_new(double dt, int nsub, double tol_abs, double tol_rel, int m
 static void sub_free(osub* s) {
     void* ptrs[] = {s->lam_e, s->mu_e, s->dmask, s->srow, s->snode, s->mass, s->u, s->v, s->a, s->su, s->sv,
                     s->sa, s->pu, s->pv, s->hist, s->free_dof, s->sdof, s->Phi, s->PhiS, s->K, s->Hq, s->B,
-                    s->c, s->q, s->qd, s->qdd, s->sq, s->sqd, s->sqdd, s->pq, s->pqd, s->qrec, s->ghat};
+                    s->c, s->q, s->qd, s->qdd, s->sq, s->sqd, s->sqdd, s->pq, s->pqd, s->qrec, s->ghat, s->Cq};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
 }
 
@@ -750,6 +818,7 @@ static osub* add_common(oprob* p, int kind, int nx, int ny, int nz, double h, co
 int orc_add_fom(void* vp, int nx, int ny, int nz, double h, const double* org, int model, double lam, double mu,
                 double rho, const double* lam_e, const double* mu_e, const unsigned char* dmask, const double* u0,
                 const double* v0) {
+    if (model != ORC_LE && model != ORC_NH && model != ORC_SVK) return ORC_EINVAL;
     oprob* p = (oprob*)vp;
     osub* s = add_common(p, ORC_FOM, nx, ny, nz, h, org, dmask, u0, v0);
     if (!s) return ORC_EINVAL;
@@ -896,16 +965,23 @@ static void zoh(oprob* p, const ocpl* cp) {
                         cp->rec[((size_t)f) * nr * 3 + (size_t)i * 3 + c];
 }
 
-/* ROM right-hand side: K q + H kron_c(q) + B ghat + c, kron_c(q) = (q_i q_j)_{i<=j} row-major */
+/* ROM right-hand side: K q + H kron_c(q) [+ C kron3_c(q)] + B ghat + c, kron_c(q) = (q_i q_j)_{i<=j}
+ * and kron3_c(q) = (q_i q_j q_k)_{i<=j<=k}, both in lexicographic (row-major) order */
 static void rom_rhs(const osub* s, const double* q, const double* ghat, double* out) {
     int r = s->r;
-    size_t nq = (size_t)r * (r + 1) / 2;
+    size_t nq = (size_t)r * (r + 1) / 2, nc = (size_t)r * (r + 1) * (r + 2) / 6;
     for (int i = 0; i < r; ++i) {
         double acc = s->c[i];
         for (int j = 0; j < r; ++j) acc += s->K[(size_t)i * r + j] * q[j];
         size_t col = 0;
         for (int j = 0; j < r; ++j)
             for (int k = j; k < r; ++k) acc += s->Hq[(size_t)i * nq + col++] * q[j] * q[k];
+        if (s->Cq) {
+            col = 0;
+            for (int j = 0; j < r; ++j)
+                for (int k = j; k < r; ++k)
+                    for (int l = k; l < r; ++l) acc += s->Cq[(size_t)i * nc + col++] * q[j] * q[k] * q[l];
+        }
         for (int j = 0; j < s->rs; ++j) acc += s->B[(size_t)i * s->rs + j] * ghat[j];
         out[i] = acc;
     }
@@ -927,6 +1003,16 @@ int orc_set_implicit(void* vp, int i, int implicit) {
     oprob* p = (oprob*)vp;
     if (i < 0 || i >= p->nsd || p->sd[i].kind != ORC_FOM) return ORC_EINVAL;
     p->sd[i].implicit = implicit != 0;
+    return ORC_OK;
+}
+
+/* cubic operator C [r][r(r+1)(r+2)/6] of ROM subdomain i (cubic OpInf; NULL keeps it quadratic) */
+int orc_set_rom_cubic(void* vp, int i, const double* C) {
+    oprob* p = (oprob*)vp;
+    if (i < 0 || i >= p->nsd || p->sd[i].kind != ORC_ROM || p->initialised) return ORC_EINVAL;
+    osub* s = &p->sd[i];
+    free(s->Cq);
+    s->Cq = C ? dup_or_zero(C, (size_t)s->r * ((size_t)s->r * (s->r + 1) * (s->r + 2) / 6)) : NULL;
     return ORC_OK;
 }
 
@@ -1083,6 +1169,8 @@ static void element_tangent(const omesh* m, int model, double lam, double mu, in
                 nh_tangent(H, G, dPk, dPm);
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j) dP[i][j] = kappa * dPk[i][j] + mu * dPm[i][j];
+            } else if (model == ORC_SVK) {
+                svk_tangent(H, G, lam, mu, dP);
             } else {
                 stress_le(G, lam, mu, dP);
             }
@@ -1094,6 +1182,25 @@ static void element_tangent(const omesh* m, int model, double lam, double mu, in
                 }
         }
     }
+}
+
+/* tangent action y = K(u) p of the assembled element tangents (test entry point) */
+int orc_tangent_action(int nx, int ny, int nz, double h, const double* org, int model, double lam, double mu,
+                       const double* u, const double* p, double* y) {
+    omesh m;
+    mesh_set(&m, nx, ny, nz, h, org);
+    memset(y, 0, sizeof(double) * 3 * (size_t)m.nn);
+    for (int e = 0; e < m.ne; ++e) {
+        double Ke[24][24];
+        int nodes[8];
+        element_tangent(&m, model, lam, mu, e, u, Ke, nodes);
+        for (int r = 0; r < 24; ++r) {
+            double acc = 0.0;
+            for (int q = 0; q < 24; ++q) acc += Ke[r][q] * p[3 * nodes[q / 3] + q % 3];
+            y[3 * nodes[r / 3] + r % 3] += acc;
+        }
+    }
+    return ORC_OK;
 }
 
 /* Cholesky solve of the dense SPD system A x = b (n x n, row-major, overwritten); 0 if not SPD */
@@ -1493,6 +1600,7 @@ int orc_adjoint(int nx, int ny, int nz, double h, const double* org, int model, 
                 const double* mu_e, double rho, const unsigned char* dmask, const double* u0, const double* v0,
                 double dt, int nsteps, const double* w, double* J, double* gu0, double* gv0, double* glam,
                 double* gmu) {
+    if (model == ORC_SVK) return ORC_EINVAL;
     omesh m;
     mesh_set(&m, nx, ny, nz, h, org);
     size_t n3 = 3 * (size_t)m.nn, ne = (size_t)m.ne;

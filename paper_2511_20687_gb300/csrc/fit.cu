@@ -276,11 +276,11 @@ int pod(cudaStream_t s, Dev& dev, const double* X, int nsnap, int n, int r, doub
 // The lambda-independent part of the fit: bases, projections, the data matrix and the Gram matrix of
 // the regression (dual D D^T or primal D^T D, without lambda).
 struct FitData {
-    int ns = 0, n = 0, nsd = 0, r = 0, rs = 0, nq = 0, d = 0;
+    int ns = 0, n = 0, nsd = 0, r = 0, rs = 0, nq = 0, nc = 0, d = 0;
     bool dual = false;
     double* Phi = nullptr;    // device [n][r]
     double* PhiS = nullptr;   // device [nsd][rs]
-    double* D = nullptr;      // device [ns][d] = [Ubar^T | kron_c(Ubar)^T | Ghat^T | 1]
+    double* D = nullptr;      // device [ns][d] = [Ubar^T | kron_c(Ubar)^T | kron3_c(Ubar)^T | Ghat^T | 1]
     double* Y = nullptr;      // device [ns][r] = Abar^T
     std::vector<double> Yh;   // host Abar^T
     std::vector<double> M0;   // host Gram without lambda: [ns][ns] (dual) or [d][d] (primal)
@@ -310,9 +310,10 @@ int fit_prepare(const osam_fit_input* in, cudaStream_t s, Dev& dev, FitData& F) 
             return rc;
     }
     const int rs = F.rs;
-    const int nq = in->quadratic ? r * (r + 1) / 2 : 0;
-    const int d = r + nq + rs + 1;
-    F.nq = nq; F.d = d;
+    const int nq = (in->quadratic || in->cubic) ? r * (r + 1) / 2 : 0;
+    const int nc = in->cubic ? r * (r + 1) * (r + 2) / 6 : 0;
+    const int d = r + nq + nc + rs + 1;
+    F.nq = nq; F.nc = nc; F.d = d;
     // D [ns][d]
     double* D = dev.alloc((size_t)ns * d);
     double* Ubt = dev.alloc((size_t)ns * r);   // Ubar^T [ns][r]
@@ -331,7 +332,8 @@ int fit_prepare(const osam_fit_input* in, cudaStream_t s, Dev& dev, FitData& F) 
     // linear block and constant on the host (small); Kronecker block and boundary block on the device
     FK(cudaMemsetAsync(D, 0, sizeof(double) * ns * d, s));
     if (nq) FK(launch_kron_features(Ub, r, ns, D, d, r, s));
-    if (rs) FK(launch_gemm_nn(ns, rs, nsd, S, nsd, F.PhiS, rs, D + r + nq, d, 1.0, 0.0, s));
+    if (nc) FK(launch_kron3_features(Ub, r, ns, D, d, r + nq, s));
+    if (rs) FK(launch_gemm_nn(ns, rs, nsd, S, nsd, F.PhiS, rs, D + r + nq + nc, d, 1.0, 0.0, s));
     FK(cudaMemcpyAsync(Dh.data(), D, sizeof(double) * Dh.size(), cudaMemcpyDeviceToHost, s));
     FK(cudaStreamSynchronize(s));
     for (int i = 0; i < ns; ++i) {
@@ -401,16 +403,19 @@ int fit_solve(const FitData& F, double lambda, cudaStream_t s, Dev& dev, std::ve
 // write the operators of O [d][r] and the bases to the caller's output
 int fit_output(const osam_fit_input* in, const FitData& F, const std::vector<double>& Oh, cudaStream_t s,
                osam_fit_output* out) {
-    const int r = F.r, nq = F.nq, rs = F.rs, d = F.d, nsd = F.nsd, ns = F.ns;
+    const int r = F.r, nq = F.nq, nc = F.nc, rs = F.rs, d = F.d, nsd = F.nsd, ns = F.ns;
     const int nq_full = r * (r + 1) / 2;
     const int rs_cols = std::max(in->r_s_max, rs);
     std::vector<double> K((size_t)r * r), H((size_t)r * nq_full, 0.0), B((size_t)r * std::max(1, rs_cols), 0.0), c(r);
+    std::vector<double> Cc((size_t)r * nc);
     for (int i = 0; i < r; ++i) {
         for (int k = 0; k < r; ++k) K[(size_t)i * r + k] = Oh[(size_t)k * r + i];
         for (int k = 0; k < nq; ++k) H[(size_t)i * nq_full + k] = Oh[(size_t)(r + k) * r + i];
-        for (int k = 0; k < rs; ++k) B[(size_t)i * rs_cols + k] = Oh[(size_t)(r + nq + k) * r + i];
+        for (int k = 0; k < nc; ++k) Cc[(size_t)i * nc + k] = Oh[(size_t)(r + nq + k) * r + i];
+        for (int k = 0; k < rs; ++k) B[(size_t)i * rs_cols + k] = Oh[(size_t)(r + nq + nc + k) * r + i];
         c[i] = Oh[(size_t)(d - 1) * r + i];
     }
+    if (out->C && nc) FK(cudaMemcpyAsync(out->C, Cc.data(), sizeof(double) * Cc.size(), cudaMemcpyDefault, s));
     if (out->K) FK(cudaMemcpyAsync(out->K, K.data(), sizeof(double) * K.size(), cudaMemcpyDefault, s));
     if (out->H) FK(cudaMemcpyAsync(out->H, H.data(), sizeof(double) * H.size(), cudaMemcpyDefault, s));
     if (out->B && rs_cols > 0) FK(cudaMemcpyAsync(out->B, B.data(), sizeof(double) * (size_t)r * rs_cols, cudaMemcpyDefault, s));
@@ -435,7 +440,7 @@ int fit_output(const osam_fit_input* in, const FitData& F, const std::vector<dou
 
 int fit_check(const osam_fit_input* in) {
     if (!in || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
-        (in->n_sdof > 0 && !in->S))
+        (in->n_sdof > 0 && !in->S) || (in->cubic && in->r > 128))
         return OSAM_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { g_fit_error = "no CUDA device"; return OSAM_ECUDA; }
@@ -473,7 +478,7 @@ extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select
     FitData F;
     if (int rc = fit_prepare(in, s, dev, F)) return rc;
     const int nl = sel->n_lambda, r = F.r, d = F.d;
-    // packed operator rows [nl][r][d] (K | H | B | c), one fit per candidate
+    // packed operator rows [nl][r][d] (K | H | C | B | c), one fit per candidate
     std::vector<double> Op((size_t)nl * r * d);
     std::vector<std::vector<double>> Os(nl);
     for (int l = 0; l < nl; ++l) {
@@ -484,6 +489,11 @@ extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select
     std::vector<short2> kij;
     for (int i = 0; i < r; ++i)
         for (int j = i; j < r; ++j) kij.push_back(make_short2((short)i, (short)j));
+    std::vector<short4> kijk;
+    if (F.nc)
+        for (int i = 0; i < r; ++i)
+            for (int j = i; j < r; ++j)
+                for (int k = j; k < r; ++k) kijk.push_back(make_short4((short)i, (short)j, (short)k, 0));
     double* Od = dev.alloc(Op.size());
     double* qd0 = dev.alloc(r);
     double* v0 = dev.alloc(F.n);
@@ -497,6 +507,12 @@ extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select
         dev.ptrs.push_back(kd);
         FK(cudaMemcpyAsync(kd, kij.data(), sizeof(short2) * kij.size(), cudaMemcpyHostToDevice, s));
     }
+    short4* kkd = nullptr;
+    if (!kijk.empty()) {
+        if (cudaMalloc(&kkd, sizeof(short4) * kijk.size()) != cudaSuccess) { g_fit_error = "device allocation failed"; return OSAM_ENOMEM; }
+        dev.ptrs.push_back(kkd);
+        FK(cudaMemcpyAsync(kkd, kijk.data(), sizeof(short4) * kijk.size(), cudaMemcpyHostToDevice, s));
+    }
     FK(cudaMemcpyAsync(Od, Op.data(), sizeof(double) * Op.size(), cudaMemcpyHostToDevice, s));
     // qd0 = Phi^T v0
     if (sel->v0) {
@@ -505,7 +521,7 @@ extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select
     } else {
         FK(cudaMemsetAsync(qd0, 0, sizeof(double) * r, s));
     }
-    FK(launch_select_rollout(nl, r, d, F.nq, F.rs, Od, kd, F.D, F.Y, qd0, F.ns, sel->substeps, sel->dt, phi, num,
+    FK(launch_select_rollout(nl, r, d, F.nq, F.nc, F.rs, Od, kd, kkd, F.D, F.Y, qd0, F.ns, sel->substeps, sel->dt, phi, num,
                              den, s));
     std::vector<double> nh(nl), dh(nl);
     FK(cudaMemcpyAsync(nh.data(), num, sizeof(double) * nl, cudaMemcpyDeviceToHost, s));

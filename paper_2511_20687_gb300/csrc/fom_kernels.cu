@@ -174,6 +174,9 @@ cudaError_t launch_hex8_force(int material, bool fp32, int scatter, const ElemAr
     if (material == OSAM_NEO_HOOKEAN) {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kGather); }
         else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kGather); }
+    } else if (material == OSAM_SAINT_VENANT_KIRCHHOFF) {
+        if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, float, kAtomic); else OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, float, kGather); }
+        else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, double, kAtomic); else OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, double, kGather); }
     } else {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kGather); }
         else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kGather); }

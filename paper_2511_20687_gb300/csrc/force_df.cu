@@ -68,6 +68,38 @@ __device__ __forceinline__ void stress_le(const f2 H[3][3], f2 lam, f2 mu, f2 P[
     P[1][2] = P[2][1] = df::mul(mu, df::add(H[1][2], H[2][1]));
 }
 
+// Saint Venant-Kirchhoff stress (see hex8_math.cuh): E = 1/2 (H + H^T + H^T H), P = (I + H) S
+__device__ __forceinline__ void stress_svk(const f2 H[3][3], f2 lam, f2 mu, f2 P[3][3]) {
+    f2 S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            f2 c = df::add(H[i][j], H[j][i]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c = df::fma(H[k][i], H[k][j], c);
+            S[i][j] = df::make(0.5f * c.h, 0.5f * c.l);  // E (exact halving)
+        }
+    const f2 lt = df::mul(lam, df::add(df::add(S[0][0], S[1][1]), S[2][2]));
+    const f2 mu2 = df::add(mu, mu);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            S[i][j] = i == j ? df::fma(mu2, S[i][j], lt) : df::mul(mu2, S[i][j]);
+            if (j != i) S[j][i] = S[i][j];
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            f2 p = S[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p = df::fma(H[i][k], S[k][j], p);
+            P[i][j] = p;
+        }
+}
+
 // cofactor form of the Neo-Hookean stress (see hex8_math.cuh)
 __device__ __forceinline__ void stress_nh(const f2 H[3][3], f2 kap2, f2 mu, f2 mu3, f2 P[3][3]) {
     f2 F[3][3];
@@ -185,6 +217,7 @@ __global__ void __launch_bounds__(128) k_force_df2_b(const FomB g, const int* __
                 Hm[c][2] = ld(2 * 12 + c * 4 + 2 * p + q);
             }
             if (MAT == OSAM_NEO_HOOKEAN) dfk::stress_nh(Hm, m1, m2, m3, P);
+            else if (MAT == OSAM_SAINT_VENANT_KIRCHHOFF) dfk::stress_svk(Hm, m1, m2, P);
             else dfk::stress_le(Hm, m1, m2, P);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -364,11 +397,15 @@ cudaError_t launch_force_df_b(const FomB& g, const int* active, const TraceFuse&
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaError_t e2 = cudaFuncSetAttribute(k_force_df2_b<OSAM_LINEAR_ELASTIC>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaError_t e3 = cudaFuncSetAttribute(k_force_df2_b<OSAM_SAINT_VENANT_KIRCHHOFF>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         if (e1 != cudaSuccess) return e1;
         if (e2 != cudaSuccess) return e2;
+        if (e3 != cudaSuccess) return e3;
         attr_set.fetch_or(bit);
     }
     if (g.material == OSAM_NEO_HOOKEAN) k_force_df2_b<OSAM_NEO_HOOKEAN><<<grid, b, smem, s>>>(g, active, tr);
+    else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF) k_force_df2_b<OSAM_SAINT_VENANT_KIRCHHOFF><<<grid, b, smem, s>>>(g, active, tr);
     else k_force_df2_b<OSAM_LINEAR_ELASTIC><<<grid, b, smem, s>>>(g, active, tr);
     return cudaGetLastError();
 }

@@ -87,6 +87,40 @@ __device__ __forceinline__ void stress_le(const T H[3][3], T lam, T mu, T P[3][3
     P[1][2] = P[2][1] = mu * (H[1][2] + H[2][1]);
 }
 
+// Appendix A.2 Saint Venant-Kirchhoff (lam, mu pre-scaled by h^2/8): E = 1/2 (H + H^T + H^T H),
+// S = lam tr(E) I + 2 mu E, P = (I + H) S
+template <typename T>
+__device__ __forceinline__ void stress_svk(const T H[3][3], T lam, T mu, T P[3][3]) {
+    T S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            T c = H[i][j] + H[j][i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c = fmaT(H[k][i], H[k][j], c);
+            S[i][j] = T(0.5) * c;  // E
+        }
+    const T lt = lam * (S[0][0] + S[1][1] + S[2][2]);
+    const T mu2 = mu + mu;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            S[i][j] = i == j ? fmaT(mu2, S[i][j], lt) : mu2 * S[i][j];
+            if (j != i) S[j][i] = S[i][j];
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T p = S[i][j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) p = fmaT(H[i][k], S[k][j], p);
+            P[i][j] = p;
+        }
+}
+
 // Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8):
 // P = alpha F + beta cof(F); returns F, cof(F), alpha, beta
 template <typename T>
@@ -160,7 +194,8 @@ __device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T 
                                              : fmaT(alpha, Fm[c][2], fmaT(beta, Cm[c][2], Sz[c][p][q]));
                     }
                 } else {
-                    stress_le<T>(Hm, m1, m2, P);
+                    if (MAT == OSAM_SAINT_VENANT_KIRCHHOFF) stress_svk<T>(Hm, m1, m2, P);
+                    else stress_le<T>(Hm, m1, m2, P);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         if (p == 0) Sx[c][q][r] = P[c][0]; else Sx[c][q][r] += P[c][0];

@@ -14,7 +14,6 @@
 #include <cstdint>
 
 #include "hex8_math.cuh"
-#include "nh_tangent.cuh"
 #include "osam_internal.h"
 
 namespace osam {
@@ -153,102 +152,6 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
         g.rrn[inst] = s;
         g.istat[2 * inst + 1] += 1;
         if (!(s > tol2 * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
-    }
-}
-
-// element tangent action: the directional derivative of the element forces at u along p, written
-// to the element buffer (same layout and sum factorisation as the force kernels)
-template <int MAT>
-__global__ void __launch_bounds__(256) k_tangent_b(const FomB g, const int* __restrict__ mask) {
-    const int2 b = g.eblk[blockIdx.x];
-    if (!run(mask, b.x)) return;
-    const InstFom I = g.inst[b.x];
-    const int e = b.y + threadIdx.x;
-    if (e >= I.ne) return;
-    const int i = e % I.nx;
-    const int t = e / I.nx;
-    const int j = t % I.ny;
-    const int k = t / I.ny;
-    const int sy = I.nx + 1, sz = (I.nx + 1) * (I.ny + 1);
-    const int n0 = i + sy * j + sz * k;
-    int node[8];
-#pragma unroll
-    for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
-    double Dx[3][2][2], Dy[3][2][2], Dz[3][2][2], Ex[3][2][2], Ey[3][2][2], Ez[3][2][2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double U[8], P[8];
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) {
-            const long long d = (long long)c * g.NN + I.node_off + node[c8];
-            U[c8] = g.us[d];
-            P[c8] = g.cg_p[d] * I.invh;
-        }
-        edge_differences_prescaled<double>(U, Dx[c], Dy[c], Dz[c]);
-        edge_differences_prescaled<double>(P, Ex[c], Ey[c], Ez[c]);
-    }
-    double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2], Bx[3][2][2], By[3][2][2], Bz[3][2][2];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lerp2<double>(Dx[c], Gx[c]); lerp2<double>(Dy[c], Gy[c]); lerp2<double>(Dz[c], Gz[c]);
-        lerp2<double>(Ex[c], Bx[c]); lerp2<double>(Ey[c], By[c]); lerp2<double>(Ez[c], Bz[c]);
-    }
-    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
-    double m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = 0.5 * kappa * I.w8; m2 = mu * I.w8; m3 = mu * I.w8 / 3.0;
-    } else {
-        m1 = lam * I.w8; m2 = mu * I.w8; m3 = 0.0;
-    }
-    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                double Hm[3][3], Gm[3][3], dP[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Hm[c][0] = Gx[c][q][r]; Hm[c][1] = Gy[c][p][r]; Hm[c][2] = Gz[c][p][q];
-                    Gm[c][0] = Bx[c][q][r]; Gm[c][1] = By[c][p][r]; Gm[c][2] = Bz[c][p][q];
-                }
-                if (MAT == OSAM_NEO_HOOKEAN) {
-                    double pk, pm;
-                    tangent::nh_tangent(Hm, Gm, m1, m2, m3, dP, pk, pm);
-                } else {
-                    stress_le<double>(Gm, m1, m2, dP);  // linear: the tangent applied to G is sigma(G)
-                }
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (p == 0) Sx[c][q][r] = dP[c][0]; else Sx[c][q][r] += dP[c][0];
-                    if (q == 0) Sy[c][p][r] = dP[c][1]; else Sy[c][p][r] += dP[c][1];
-                    if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
-                }
-            }
-    double* fe = static_cast<double*>(g.fe) + I.elem_off;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double Fc[8], Tm[2][2];
-        lerp2T<double>(Sx[c], Tm);
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
-        lerp2T<double>(Sy[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
-        lerp2T<double>(Sz[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
     }
 }
 
@@ -395,13 +298,6 @@ cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cud
 }
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s) {
     k_imp_reduce_b<<<g.n_inst, 128, 0, s>>>(g, mask, mode, first, tol2);
-    return cudaGetLastError();
-}
-cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s) {
-    if (g.n_eblk == 0) return cudaSuccess;
-    if (g.eblock > 256) return cudaErrorInvalidConfiguration;
-    if (g.material == OSAM_NEO_HOOKEAN) k_tangent_b<OSAM_NEO_HOOKEAN><<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
-    else k_tangent_b<OSAM_LINEAR_ELASTIC><<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
     return cudaGetLastError();
 }
 cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {

@@ -81,7 +81,7 @@ extern "C" OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h
                                                 double mu, const double* lambda_e, const double* mu_e, const double* u,
                                                 double* f, void* stream) {
     if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !f ||
-        (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN)) {
+        (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN && material != OSAM_SAINT_VENANT_KIRCHHOFF)) {
         osam::set_thread_error("osam_hex8_force_noalloc: invalid argument");
         return OSAM_EINVAL;
     }

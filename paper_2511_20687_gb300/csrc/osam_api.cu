@@ -98,6 +98,11 @@ struct osam_ctx {
     // take the SM slots the internal-force kernel leaves free in its last wave instead of delaying it.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // additive Schwarz: every subdomain but the first advances on a stream of its own, forked from and
+    // joined back to the context stream in every iteration (also inside the graph capture)
+    bool additive = false;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_join;
     std::string err;
     // CUDA graph of one controller step: begin nodes, then a while node over Schwarz iterations
     bool use_graph = true;
@@ -131,6 +136,11 @@ struct osam_ctx {
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (cudaEvent_t e : lane_join) cudaEventDestroy(e);
+        for (cudaStream_t l : lanes) {
+            cudaStreamSynchronize(l);
+            cudaStreamDestroy(l);
+        }
         if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -468,10 +478,46 @@ int enqueue_begin(osam_ctx* ctx) {
     return OSAM_OK;
 }
 
+// additive sweep (Remark additive_sam): every subdomain advances from the boundary data of the previous
+// iteration, concurrently on its own stream (subdomain 0 on the context stream); the transfers follow
+// the join.  Implicit subdomains synchronise with the host inside their Newton loops, so they are
+// enqueued after the explicit ones, whose work is then already in flight.
+int additive_sweep(osam_ctx* ctx, const int* act) {
+    const int n = (int)ctx->slots.size();
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    cudaStream_t main = ctx->stream;
+    int rc = OSAM_OK;
+    for (int pass = 0; pass < 2 && rc == OSAM_OK; ++pass)
+        for (int s = 0; s < n && rc == OSAM_OK; ++s) {
+            const Slot& S = ctx->slots[s];
+            const bool imp = S.kind == OSAM_FOM && S.fom.d.implicit;
+            if (imp != (pass == 1)) continue;
+            if (s > 0) {
+                cudaStream_t lane = ctx->lanes[s - 1];
+                CK(cudaStreamWaitEvent(lane, ctx->ev_fork, 0));
+                ctx->stream = lane;
+            }
+            rc = advance_slot(ctx, s, act);
+            ctx->stream = main;
+            if (rc == OSAM_OK && s > 0) CK(cudaEventRecord(ctx->lane_join[s - 1], ctx->lanes[s - 1]));
+        }
+    if (rc) return rc;
+    for (int s = 1; s < n; ++s) CK(cudaStreamWaitEvent(ctx->stream, ctx->lane_join[s - 1], 0));
+    for (CplH& c : ctx->cpls) RET(transfer_cpl(ctx, c, act));
+    return OSAM_OK;
+}
+
 // one Schwarz iteration for every instance still iterating; instances that continue are restored
 // to the saved state for the next iteration
 int enqueue_iteration(osam_ctx* ctx, int use_cond) {
     const int* act = ctx->ctl.active;
+    if (ctx->additive) {
+        RET(additive_sweep(ctx, act));
+        RET(norms_all(ctx, act));
+        LK(launch_controller(ctx->ctl, ctx->cond, use_cond, ctx->stream));
+        RET(saverest_all(ctx, act, 1));
+        return OSAM_OK;
+    }
     for (int s = 0; s < (int)ctx->slots.size(); ++s) {
         if (pipelined_pair(ctx, s)) {
             RET(advance_pair(ctx, s, act));
@@ -556,6 +602,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         return ctx->fail(OSAM_EINVAL, "bad precision");
     if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_TILED)
         return ctx->fail(OSAM_EINVAL, "bad scatter mode");
+    if (d0.schwarz != OSAM_MULTIPLICATIVE && d0.schwarz != OSAM_ADDITIVE)
+        return ctx->fail(OSAM_EINVAL, "bad Schwarz variant");
     for (int k = 0; k < d0.n_couplings; ++k) {
         const osam_coupling_desc& c = d0.couplings[k];
         if (c.dst < 0 || c.dst >= d0.n_subdomains || c.src < 0 || c.src >= d0.n_subdomains || c.dst == c.src)
@@ -565,7 +613,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         const osam_problem_desc& d = descs[i];
         if (d.n_subdomains != d0.n_subdomains || d.n_couplings != d0.n_couplings || d.dt != d0.dt ||
             d.n_substeps != d0.n_substeps || d.max_iters != d0.max_iters || d.tol_abs != d0.tol_abs ||
-            d.tol_rel != d0.tol_rel || d.precision != d0.precision || d.device != d0.device || !d.subdomains)
+            d.tol_rel != d0.tol_rel || d.precision != d0.precision || d.device != d0.device || !d.subdomains ||
+            d.schwarz != d0.schwarz)
             return ctx->fail(OSAM_EINVAL, "instance %d: controller settings differ from instance 0", i);
         for (int s = 0; s < d0.n_subdomains; ++s) {
             const osam_subdomain_desc& a = d.subdomains[s];
@@ -578,7 +627,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
             if ((long long)(a.nx + 1) * (a.ny + 1) * (a.nz + 1) > (1LL << 30))
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d too large", i, s);
             if (!a.u0) return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: u0 required", i, s);
-            if (a.kind == OSAM_FOM && a.material != OSAM_LINEAR_ELASTIC && a.material != OSAM_NEO_HOOKEAN)
+            if (a.kind == OSAM_FOM && a.material != OSAM_LINEAR_ELASTIC && a.material != OSAM_NEO_HOOKEAN &&
+                a.material != OSAM_SAINT_VENANT_KIRCHHOFF)
                 return ctx->fail(OSAM_EINVAL, "subdomain %d: bad material", s);
             if (a.kind == OSAM_FOM && !(a.rho > 0.0))
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: rho must be positive", i, s);
@@ -786,8 +836,8 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
 int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_problem_desc* descs) {
     G.inst.resize(n);
     G.nfree.resize(n);
-    long long nn_tot = 0, nfree_tot = 0, O_tot = 0, PS_tot = 0, kij_tot = 0, q_tot = 0, qrec_tot = 0, ghat_tot = 0,
-              hist_tot = 0, part_tot = 0, phi_tot = 0;
+    long long nn_tot = 0, nfree_tot = 0, O_tot = 0, PS_tot = 0, kij_tot = 0, kijk_tot = 0, q_tot = 0, qrec_tot = 0,
+              ghat_tot = 0, hist_tot = 0, part_tot = 0, phi_tot = 0;
     RomB& B = G.d;
     B.n_inst = n;
     B.gx_max = B.gy_max = B.rs_max = B.r_max = 0;
@@ -813,12 +863,15 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
         G.nfree[i] = (int)free_dof[i].size();
         I.r = d.r; I.rs = d.r_s; I.nsdof = 3 * G.ns[i];
         I.nq = I.r * (I.r + 1) / 2;
-        I.d = I.r + I.nq + I.rs + 1;
+        if (d.C && d.r > 128) return ctx->fail(OSAM_EINVAL, "instance %d: cubic ROM rank r=%d above 128", i, d.r);
+        I.nc = d.C ? I.r * (I.r + 1) * (I.r + 2) / 6 : 0;
+        I.d = I.r + I.nq + I.nc + I.rs + 1;
         I.gx = grid_for(I.d, 128);
         I.gy = grid_for(I.r, 8);
         I.O_off = O_tot; O_tot += (long long)I.r * I.d;
         I.PhiSt_off = PS_tot; PS_tot += (long long)I.rs * I.nsdof;
         I.kij_off = kij_tot; kij_tot += I.nq;
+        I.kijk_off = kijk_tot; kijk_tot += I.nc;
         I.q_off = q_tot; q_tot += 3LL * I.r;
         const long long nl = ctx->slots[s].nsub + 1;
         I.qrec_off = qrec_tot; qrec_tot += nl * 3 * I.r;
@@ -836,7 +889,8 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
     double* O = ctx->alloc<double>(O_tot);
     double* PhiSt = ctx->alloc<double>(std::max(1LL, PS_tot));
     short2* kij = ctx->alloc<short2>(std::max(1LL, kij_tot));
-    CKA(O); CKA(PhiSt); CKA(kij);
+    short4* kijk = ctx->alloc<short4>(std::max(1LL, kijk_tot));
+    CKA(O); CKA(PhiSt); CKA(kij); CKA(kijk);
     CKA(B.q = ctx->alloc<double>(q_tot));
     CKA(B.sq = ctx->alloc<double>(q_tot));
     CKA(B.pq = ctx->alloc<double>(q_tot));
@@ -872,16 +926,20 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
         po += (long long)G.nfree[i] * I.r;
         fo += G.nfree[i];
         no += nn;
-        std::vector<double> K, Hh, Bh, c, Op((size_t)I.r * I.d);
+        std::vector<double> K, Hh, Ch, Bh, c, Op((size_t)I.r * I.d);
         RET(to_host(ctx, K, d.K, (size_t)I.r * I.r));
         RET(to_host(ctx, Hh, d.H, (size_t)I.r * I.nq));
+        if (I.nc) RET(to_host(ctx, Ch, d.C, (size_t)I.r * I.nc));
         if (I.rs) RET(to_host(ctx, Bh, d.B, (size_t)I.r * I.rs));
         RET(to_host(ctx, c, d.c, (size_t)I.r));
         for (int row = 0; row < I.r; ++row) {
             double* o = Op.data() + (size_t)row * I.d;
             std::copy(K.begin() + (size_t)row * I.r, K.begin() + (size_t)(row + 1) * I.r, o);
             std::copy(Hh.begin() + (size_t)row * I.nq, Hh.begin() + (size_t)(row + 1) * I.nq, o + I.r);
-            if (I.rs) std::copy(Bh.begin() + (size_t)row * I.rs, Bh.begin() + (size_t)(row + 1) * I.rs, o + I.r + I.nq);
+            if (I.nc)
+                std::copy(Ch.begin() + (size_t)row * I.nc, Ch.begin() + (size_t)(row + 1) * I.nc, o + I.r + I.nq);
+            if (I.rs)
+                std::copy(Bh.begin() + (size_t)row * I.rs, Bh.begin() + (size_t)(row + 1) * I.rs, o + I.r + I.nq + I.nc);
             o[I.d - 1] = c[row];
         }
         RET(upload(ctx, O + I.O_off, Op.data(), sizeof(double) * Op.size()));
@@ -899,6 +957,15 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
         for (int a = 0; a < I.r; ++a)
             for (int b = a; b < I.r; ++b) kk[t++] = make_short2((short)a, (short)b);
         RET(upload(ctx, kij + I.kij_off, kk.data(), sizeof(short2) * I.nq));
+        if (I.nc) {
+            std::vector<short4> k3;
+            k3.reserve(I.nc);
+            for (int a = 0; a < I.r; ++a)
+                for (int b = a; b < I.r; ++b)
+                    for (int e = b; e < I.r; ++e) k3.push_back(make_short4((short)a, (short)b, (short)e, 0));
+            RET(upload(ctx, kijk + I.kijk_off, k3.data(), sizeof(short4) * I.nc));
+            CK(cudaStreamSynchronize(ctx->stream));  // k3 is a host staging buffer
+        }
         // q0 = Phi^T u0, qd0 = Phi^T v0 over the free dofs
         RET(upload(ctx, uv, d.u0, sizeof(double) * 3 * nn));
         if (d.v0) RET(upload(ctx, uv + 3LL * nn, d.v0, sizeof(double) * 3 * nn));
@@ -909,6 +976,7 @@ int setup_rom_group(osam_ctx* ctx, RomGroupH& G, int s, int n, const osam_proble
     B.O = O;
     B.PhiSt = PhiSt;
     B.kij = kij;
+    B.kijk = kijk;
     CKA(G.inst_d = ctx->alloc<InstRom>(n));
     RET(upload(ctx, G.inst_d, G.inst.data(), sizeof(InstRom) * n));
     B.inst = G.inst_d;
@@ -1198,6 +1266,16 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_lo));
         CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+        ctx->additive = d0.schwarz == OSAM_ADDITIVE;
+        if (ctx->additive)
+            for (int s = 1; s < d0.n_subdomains; ++s) {
+                cudaStream_t l;
+                cudaEvent_t e;
+                CK(cudaStreamCreateWithPriority(&l, cudaStreamNonBlocking, prio_hi));
+                ctx->lanes.push_back(l);
+                CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                ctx->lane_join.push_back(e);
+            }
     }
     CKA(ctx->err_d = ctx->alloc<int>(1));
     const int nsd = d0.n_subdomains, ncpl = d0.n_couplings;
@@ -1667,7 +1745,8 @@ static ElemArgs standalone_args(int nx, int ny, int nz, double h, double lambda,
 int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambda, double mu, const double* lambda_e,
                     const double* mu_e, const double* u, double* f, void* stream) {
     if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !f) return OSAM_EINVAL;
-    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN) return OSAM_EINVAL;
+    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN && material != OSAM_SAINT_VENANT_KIRCHHOFF)
+        return OSAM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
     if (cudaMemsetAsync(f, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
@@ -1695,7 +1774,8 @@ int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double l
 int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     if (!d || !out) return OSAM_EINVAL;
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || !(d->h > 0.0) || !d->u0 || !d->w || !d->lambda_e || !d->mu_e ||
-        d->n_steps < 0 || !(d->dt > 0.0) || !(d->rho > 0.0))
+        d->n_steps < 0 || !(d->dt > 0.0) || !(d->rho > 0.0) ||
+        (d->material != OSAM_LINEAR_ELASTIC && d->material != OSAM_NEO_HOOKEAN))
         return OSAM_EINVAL;
     osam_subdomain_desc sd{};
     sd.kind = OSAM_FOM;

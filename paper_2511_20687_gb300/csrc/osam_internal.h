@@ -115,17 +115,18 @@ struct FomB {
 
 // one instance of a ROM slot
 struct InstRom {
-    int r, rs, nsdof, d, nq, gx, gy;
-    long long O_off, PhiSt_off, kij_off, q_off, qrec_off, ghat_off, hist_off, partial_off;
+    int r, rs, nsdof, d, nq, nc, gx, gy;   // nc: cubic columns r(r+1)(r+2)/6 (0: quadratic ROM)
+    long long O_off, PhiSt_off, kij_off, kijk_off, q_off, qrec_off, ghat_off, hist_off, partial_off;
 };
 
 struct RomB {
     int n_inst;
     const InstRom* inst;
     int gx_max, gy_max, rs_max, r_max;
-    const double* O;          // packed operator rows [r][K | H | B | c] per instance
+    const double* O;          // packed operator rows [r][K | H | C | B | c] per instance (C: cubic ROMs)
     const double* PhiSt;      // Phi_S^T [rs][nsdof] per instance
     const short2* kij;        // compressed Kronecker index pairs per instance
+    const short4* kijk;       // compressed Kronecker index triples per instance (cubic ROMs)
     double* q;                // [3][r] per instance: q, qd, qdd
     double* sq;
     double* pq;
@@ -265,11 +266,14 @@ cudaError_t launch_gemm_nt(int m, int n, int k, const double* A, int lda, const 
                            int ldc, double alpha, double beta, cudaStream_t s);
 cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0,
                                  cudaStream_t s);
+// compressed Kronecker cube (q_i q_j q_k)_{i<=j<=k} of every snapshot into columns col0.. of D
+cudaError_t launch_kron3_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0,
+                                  cudaStream_t s);
 // regularisation selection: nl candidate ROMs (packed rows [nl][r][d]) rolled out under frozen
 // boundary data (D's boundary columns), error sums per candidate
-cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int rs, const double* O, const short2* kij,
-                                  const double* D, const double* Y, const double* qd0, int ns, int k, double dt,
-                                  double* phi, double* num, double* den, cudaStream_t s);
+cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int nc, int rs, const double* O, const short2* kij,
+                                  const short4* kijk, const double* D, const double* Y, const double* qd0, int ns,
+                                  int k, double dt, double* phi, double* num, double* den, cudaStream_t s);
 
 // adjoint (adjoint_kernels.cu)
 cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,

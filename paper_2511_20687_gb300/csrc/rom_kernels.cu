@@ -135,6 +135,21 @@ __global__ void k_kron_features(const double* Ubar, int r, int nsnap, double* D,
 }
 
 
+// compressed Kronecker cube: one block per snapshot, index triples (i <= j <= k) in lexicographic order
+__global__ void k_kron3_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0) {
+    const int s = blockIdx.x;
+    long long idx = 0;
+    for (int i = 0; i < r; ++i) {
+        const double qi = Ubar[(long long)i * nsnap + s];
+        for (int j = i; j < r; ++j) {
+            const double qij = qi * Ubar[(long long)j * nsnap + s];
+            for (int k = j + threadIdx.x; k < r; k += blockDim.x)
+                D[(long long)s * ldd + col0 + idx + (k - j)] = qij * Ubar[(long long)k * nsnap + s];
+            idx += r - j;
+        }
+    }
+}
+
 // Regularisation selection (Sec. 4.2.4, Algorithm 3): one block per candidate lambda rolls its ROM
 // out alone, explicit central differences with step dt, Schwarz boundary data frozen to the training
 // columns (linear in time between columns that are k steps apart), from the training initial state;
@@ -159,8 +174,11 @@ __device__ __forceinline__ double2 block_sum_pair(double x, double y) {
     return make_double2(a, b);
 }
 
-__global__ void __launch_bounds__(kSelBlock) k_select_rollout(int r, int d, int nq, int rs, const double* __restrict__ O,
-                                                              const short2* __restrict__ kij, const double* __restrict__ D,
+__global__ void __launch_bounds__(kSelBlock) k_select_rollout(int r, int d, int nq, int nc, int rs,
+                                                              const double* __restrict__ O,
+                                                              const short2* __restrict__ kij,
+                                                              const short4* __restrict__ kijk,
+                                                              const double* __restrict__ D,
                                                               const double* __restrict__ Y, const double* __restrict__ qd0,
                                                               int ns, int k, double dt, double* phi_all, double* num,
                                                               double* den) {
@@ -178,8 +196,8 @@ __global__ void __launch_bounds__(kSelBlock) k_select_rollout(int r, int d, int 
     double sn = 0.0, sd = acc.y;   // meaningful in thread 0
     const double hdt = 0.5 * dt, hdt2 = 0.5 * dt * dt;
     for (int j = 0; j + 1 < ns; ++j) {
-        const double* g0 = D + (size_t)j * d + r + nq;
-        const double* g1 = D + (size_t)(j + 1) * d + r + nq;
+        const double* g0 = D + (size_t)j * d + r + nq + nc;
+        const double* g1 = D + (size_t)(j + 1) * d + r + nq + nc;
         for (int s = 1; s <= k; ++s) {
             __syncthreads();
             for (int t = tid; t < r; t += blockDim.x) qp[t] = q[t] + dt * qd[t] + hdt2 * qdd[t];
@@ -189,7 +207,11 @@ __global__ void __launch_bounds__(kSelBlock) k_select_rollout(int r, int d, int 
                 double v;
                 if (col < r) v = qp[col];
                 else if (col < r + nq) { const short2 ij = kij[col - r]; v = qp[ij.x] * qp[ij.y]; }
-                else if (col < r + nq + rs) { const int b = col - r - nq; v = g0[b] + w * (g1[b] - g0[b]); }
+                else if (col < r + nq + nc) {
+                    const short4 t3 = kijk[col - r - nq];
+                    v = qp[t3.x] * qp[t3.y] * qp[t3.z];
+                }
+                else if (col < r + nq + nc + rs) { const int b = col - r - nq - nc; v = g0[b] + w * (g1[b] - g0[b]); }
                 else v = 1.0;
                 phi[col] = v;
             }
@@ -280,11 +302,16 @@ cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int rs, const double* O, const short2* kij,
-                                  const double* D, const double* Y, const double* qd0, int ns, int k, double dt,
-                                  double* phi, double* num, double* den, cudaStream_t s) {
-    if (r > kSelMaxR || r < 1 || nl < 1) return cudaErrorInvalidValue;
-    k_select_rollout<<<nl, kSelBlock, 0, s>>>(r, d, nq, rs, O, kij, D, Y, qd0, ns, k, dt, phi, num, den);
+cudaError_t launch_kron3_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0, cudaStream_t s) {
+    k_kron3_features<<<nsnap, 64, 0, s>>>(Ubar, r, nsnap, D, ldd, col0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int nc, int rs, const double* O, const short2* kij,
+                                  const short4* kijk, const double* D, const double* Y, const double* qd0, int ns,
+                                  int k, double dt, double* phi, double* num, double* den, cudaStream_t s) {
+    if (r > kSelMaxR || r < 1 || nl < 1 || (nc > 0 && !kijk)) return cudaErrorInvalidValue;
+    k_select_rollout<<<nl, kSelBlock, 0, s>>>(r, d, nq, nc, rs, O, kij, kijk, D, Y, qd0, ns, k, dt, phi, num, den);
     return cudaGetLastError();
 }
 

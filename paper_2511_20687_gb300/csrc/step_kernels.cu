@@ -567,7 +567,11 @@ __global__ void __launch_bounds__(kRomBlock) k_rom_step_b(const RomB r, const in
     double phi = 0.0;
     if (col < I.r) phi = qp[col];
     else if (col < I.r + I.nq) { const short2 ij = r.kij[I.kij_off + col - I.r]; phi = qp[ij.x] * qp[ij.y]; }
-    else if (col < I.r + I.nq + I.rs) phi = r.ghat[I.ghat_off + (long long)slot * I.rs + col - I.r - I.nq];
+    else if (col < I.r + I.nq + I.nc) {
+        const short4 t3 = r.kijk[I.kijk_off + col - I.r - I.nq];
+        phi = qp[t3.x] * qp[t3.y] * qp[t3.z];
+    }
+    else if (col < I.r + I.nq + I.nc + I.rs) phi = r.ghat[I.ghat_off + (long long)slot * I.rs + col - I.r - I.nq - I.nc];
     else if (col == I.d - 1) phi = 1.0;
     const double* O = r.O + I.O_off;
     double part[kRomRows];
@@ -773,6 +777,9 @@ cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaSt
         if (g.material == OSAM_NEO_HOOKEAN) {
             if (scatter == kAtomic) k_force_tile_b<OSAM_NEO_HOOKEAN, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
             else k_force_tile_b<OSAM_NEO_HOOKEAN, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);
+        } else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF) {
+            if (scatter == kAtomic) k_force_tile_b<OSAM_SAINT_VENANT_KIRCHHOFF, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
+            else k_force_tile_b<OSAM_SAINT_VENANT_KIRCHHOFF, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);
         } else {
             if (scatter == kAtomic) k_force_tile_b<OSAM_LINEAR_ELASTIC, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
             else k_force_tile_b<OSAM_LINEAR_ELASTIC, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);
@@ -781,12 +788,16 @@ cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaSt
     }
     if (g.occ && !fp32 && scatter == kGather && b <= 128) {
         if (g.material == OSAM_NEO_HOOKEAN) k_force_occ_b<OSAM_NEO_HOOKEAN><<<grid, b, 0, s>>>(g, active, tr);
+        else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF) k_force_occ_b<OSAM_SAINT_VENANT_KIRCHHOFF><<<grid, b, 0, s>>>(g, active, tr);
         else k_force_occ_b<OSAM_LINEAR_ELASTIC><<<grid, b, 0, s>>>(g, active, tr);
         return cudaGetLastError();
     }
     if (g.material == OSAM_NEO_HOOKEAN) {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, float, kGather); }
         else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kAtomic); else OSAM_LAUNCH(OSAM_NEO_HOOKEAN, double, kGather); }
+    } else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF) {
+        if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, float, kAtomic); else OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, float, kGather); }
+        else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, double, kAtomic); else OSAM_LAUNCH(OSAM_SAINT_VENANT_KIRCHHOFF, double, kGather); }
     } else {
         if (fp32) { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, float, kGather); }
         else { if (scatter == kAtomic) OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kAtomic); else OSAM_LAUNCH(OSAM_LINEAR_ELASTIC, double, kGather); }
@@ -800,6 +811,8 @@ cudaError_t launch_force_init_b(const FomB& g, const int* active, cudaStream_t s
     k_scale_u0_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active);
     if (g.material == OSAM_NEO_HOOKEAN)
         k_force_b<OSAM_NEO_HOOKEAN, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, TraceFuse{});
+    else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF)
+        k_force_b<OSAM_SAINT_VENANT_KIRCHHOFF, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, TraceFuse{});
     else
         k_force_b<OSAM_LINEAR_ELASTIC, double, kGather><<<g.n_eblk, g.eblock, 0, s>>>(g, active, TraceFuse{});
     return cudaGetLastError();

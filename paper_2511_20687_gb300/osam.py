@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libosam.so")
 
 OK, MAXITER, EINVAL, ECFL, ENONFINITE, EDONOR, ECUDA, ETIMEOUT, ENOMEM = 0, 1, -1, -2, -3, -4, -5, -6, -7
 FOM, ROM = 0, 1
-LINEAR_ELASTIC, NEO_HOOKEAN = 0, 1
+LINEAR_ELASTIC, NEO_HOOKEAN, SAINT_VENANT_KIRCHHOFF = 0, 1, 2
 EXPLICIT, IMPLICIT = 0, 1
+MULTIPLICATIVE, ADDITIVE = 0, 1
 FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG, SCATTER_GATHER_TILED = 0, 1, 2, 3, 4
 
@@ -46,7 +47,7 @@ class SubdomainDesc(C.Structure):
                 ("origin", C.c_double * 3), ("material", C.c_int), ("lambda_", C.c_double), ("mu", C.c_double),
                 ("rho", C.c_double), ("lambda_e", _vp), ("mu_e", _vp), ("dirichlet", _vp), ("u0", _vp), ("v0", _vp),
                 ("r", C.c_int), ("r_s", C.c_int), ("Phi", _vp), ("Phi_S", _vp), ("K", _vp), ("H", _vp), ("B", _vp),
-                ("c", _vp), ("integrator", C.c_int), ("n_substeps", C.c_int)]
+                ("c", _vp), ("integrator", C.c_int), ("n_substeps", C.c_int), ("C", _vp)]
 
 
 class CouplingDesc(C.Structure):
@@ -57,7 +58,7 @@ class ProblemDesc(C.Structure):
     _fields_ = [("n_subdomains", C.c_int), ("subdomains", C.POINTER(SubdomainDesc)), ("n_couplings", C.c_int),
                 ("couplings", C.POINTER(CouplingDesc)), ("dt", C.c_double), ("n_substeps", C.c_int),
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("max_iters", C.c_int), ("precision", C.c_int),
-                ("scatter", C.c_int), ("stream", _vp), ("device", C.c_int)]
+                ("scatter", C.c_int), ("stream", _vp), ("device", C.c_int), ("schwarz", C.c_int)]
 
 
 class StepReport(C.Structure):
@@ -68,12 +69,13 @@ class StepReport(C.Structure):
 class FitInput(C.Structure):
     _fields_ = [("n_dof", C.c_int), ("n_snap", C.c_int), ("n_sdof", C.c_int), ("U", _vp), ("A", _vp), ("S", _vp),
                 ("r", C.c_int), ("r_s", C.c_int), ("energy_s", C.c_double), ("r_s_max", C.c_int),
-                ("lambda_", C.c_double), ("quadratic", C.c_int), ("stream", _vp), ("device", C.c_int)]
+                ("lambda_", C.c_double), ("quadratic", C.c_int), ("stream", _vp), ("device", C.c_int),
+                ("cubic", C.c_int)]
 
 
 class FitOutput(C.Structure):
     _fields_ = [("Phi", _vp), ("Phi_S", _vp), ("K", _vp), ("H", _vp), ("B", _vp), ("c", _vp), ("sigma", _vp),
-                ("sigma_s", _vp), ("r_s", C.c_int)]
+                ("sigma_s", _vp), ("r_s", C.c_int), ("C", _vp)]
 
 
 class SelectInput(C.Structure):
@@ -195,14 +197,16 @@ def _stream_handle(stream):
     return int(stream)
 
 
-_MAT = {"le": LINEAR_ELASTIC, "nh": NEO_HOOKEAN, LINEAR_ELASTIC: LINEAR_ELASTIC, NEO_HOOKEAN: NEO_HOOKEAN}
+_MAT = {"le": LINEAR_ELASTIC, "nh": NEO_HOOKEAN, "svk": SAINT_VENANT_KIRCHHOFF, LINEAR_ELASTIC: LINEAR_ELASTIC,
+        NEO_HOOKEAN: NEO_HOOKEAN, SAINT_VENANT_KIRCHHOFF: SAINT_VENANT_KIRCHHOFF}
 
 
 class Batch:
     """n instances of one coupled O-SAM problem advanced together on the GPU (osam_batch_init).
 
     specs: list of workloads.Problem with identical topology; rom_ops: list (one per instance) of
-    {subdomain index: {"Phi", "Phi_S", "K", "H", "B", "c"}} for the ROM subdomains (or None).
+    {subdomain index: {"Phi", "Phi_S", "K", "H", "B", "c"[, "C"]}} for the ROM subdomains (or None; "C"
+    makes the ROM cubic).
     """
 
     def __init__(self, specs, rom_ops=None, precision: int = FP64, scatter: int = SCATTER_AUTO, device: int = 0,
@@ -235,6 +239,8 @@ class Batch:
                     ops = ops_n[i]
                     for k in ("Phi", "Phi_S", "K", "H", "B", "c"):
                         arrs[k] = _f64(ops[k])
+                    if ops.get("C") is not None:
+                        arrs["C"] = _f64(ops["C"])
                     d.r = int(ops["Phi"].shape[1])
                     d.r_s = int(ops["Phi_S"].shape[1])
                     self.rank[(n, i)] = d.r
@@ -260,6 +266,7 @@ class Batch:
             desc.scatter = scatter
             desc.stream = _stream_handle(stream)
             desc.device = device
+            desc.schwarz = ADDITIVE if getattr(spec, "schwarz", "multiplicative") == "additive" else MULTIPLICATIVE
         h = _vp()
         _check(L.osam_batch_init(len(specs), descs, C.byref(h)), None)
         self.h = h
@@ -416,18 +423,27 @@ def hex8_force_vjp(dims, h, material, lam, mu, u, ybar, ubar, lam_bar=None, mu_b
 # ---------------------------------------------------------------------------------------------
 # offline OpInf fit
 # ---------------------------------------------------------------------------------------------
-def opinf_fit(U, A, S, r, lam, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True, device=0, stream=None):
+def _fit_outputs(n, nsd, ns, r, rs_cols, cubic):
+    out = {"Phi": np.zeros((n, r)), "Phi_S": np.zeros((max(nsd, 1), rs_cols)), "K": np.zeros((r, r)),
+           "H": np.zeros((r, r * (r + 1) // 2)), "B": np.zeros((r, rs_cols)), "c": np.zeros(r),
+           "sigma": np.zeros(ns), "sigma_s": np.zeros(ns)}
+    if cubic:
+        out["C"] = np.zeros((r, r * (r + 1) * (r + 2) // 6))
+    return out
+
+
+def opinf_fit(U, A, S, r, lam, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True, device=0, stream=None,
+              cubic=False):
     """U, A: [n_snap, n_dof]; S: [n_snap, n_sdof] snapshots (host or device float64).  Returns numpy
-    operators {Phi [n_dof, r], Phi_S [n_sdof, r_s], K, H, B [r, r_s], c, sigma, sigma_s, r_s}."""
+    operators {Phi [n_dof, r], Phi_S [n_sdof, r_s], K, H, (C,) B [r, r_s], c, sigma, sigma_s, r_s}."""
     U, A, S = _f64(U), _f64(A), _f64(S)
     ns, n = U.shape
     nsd = S.shape[1] if S is not None else 0
     rs_cols = max(r_s_max, r_s)
-    out_arrs = {"Phi": np.zeros((n, r)), "Phi_S": np.zeros((max(nsd, 1), rs_cols)), "K": np.zeros((r, r)),
-                "H": np.zeros((r, r * (r + 1) // 2)), "B": np.zeros((r, rs_cols)), "c": np.zeros(r),
-                "sigma": np.zeros(ns), "sigma_s": np.zeros(ns)}
+    out_arrs = _fit_outputs(n, nsd, ns, r, rs_cols, cubic)
     fi = FitInput(n_dof=n, n_snap=ns, n_sdof=nsd, U=_ptr(U), A=_ptr(A), S=_ptr(S), r=r, r_s=r_s, energy_s=energy_s,
-                  r_s_max=r_s_max, lambda_=lam, quadratic=int(quadratic), stream=_stream_handle(stream), device=device)
+                  r_s_max=r_s_max, lambda_=lam, quadratic=int(quadratic), stream=_stream_handle(stream), device=device,
+                  cubic=int(cubic))
     fo = FitOutput(**{k: _ptr(v) for k, v in out_arrs.items()}, r_s=0)
     rc = load().opinf_fit(C.byref(fi), C.byref(fo))
     if rc < 0:
@@ -440,7 +456,7 @@ def opinf_fit(U, A, S, r, lam, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic
 
 
 def opinf_select(U, A, S, v0, r, lambdas, dt, substeps, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, quadratic=True,
-                 device=0, stream=None):
+                 device=0, stream=None, cubic=False):
     """Schwarz-aware regularisation selection (Algorithm 3) on the GPU.  U, A: [n_snap, n_dof];
     S: [n_snap, n_sdof]; v0: [n_dof] velocity of the first snapshot (or None); lambdas: candidates.
     Returns the operators at the selected lambda (as opinf_fit) plus "errors", "best" and "lambda"."""
@@ -449,11 +465,10 @@ def opinf_select(U, A, S, v0, r, lambdas, dt, substeps, r_s=0, energy_s=1.0 - 1e
     ns, n = U.shape
     nsd = S.shape[1] if S is not None else 0
     rs_cols = max(r_s_max, r_s)
-    out_arrs = {"Phi": np.zeros((n, r)), "Phi_S": np.zeros((max(nsd, 1), rs_cols)), "K": np.zeros((r, r)),
-                "H": np.zeros((r, r * (r + 1) // 2)), "B": np.zeros((r, rs_cols)), "c": np.zeros(r),
-                "sigma": np.zeros(ns), "sigma_s": np.zeros(ns)}
+    out_arrs = _fit_outputs(n, nsd, ns, r, rs_cols, cubic)
     fi = FitInput(n_dof=n, n_snap=ns, n_sdof=nsd, U=_ptr(U), A=_ptr(A), S=_ptr(S), r=r, r_s=r_s, energy_s=energy_s,
-                  r_s_max=r_s_max, lambda_=0.0, quadratic=int(quadratic), stream=_stream_handle(stream), device=device)
+                  r_s_max=r_s_max, lambda_=0.0, quadratic=int(quadratic), stream=_stream_handle(stream), device=device,
+                  cubic=int(cubic))
     si = SelectInput(lambdas=lams.ctypes.data, n_lambda=len(lams), v0=_ptr(v0), dt=dt, substeps=substeps)
     fo = FitOutput(**{k: _ptr(v) for k, v in out_arrs.items()}, r_s=0)
     errors = np.zeros(len(lams))

@@ -219,3 +219,78 @@ def test_selection_penalises_a_non_finite_rollout():
     G = np.zeros((1, 2000))
     Q = OF.rollout_frozen(K, H, B, c, np.ones(n), np.zeros(n), np.zeros(n), G, 1.0, 1)
     assert not np.all(np.isfinite(Q))
+
+
+# ---------------------------------------------------------------------------------------------
+# cubic OpInf (COpInf)
+# ---------------------------------------------------------------------------------------------
+def test_kron3_c_order():
+    """Compressed Kronecker cube = products over index triples i <= j <= k in lexicographic order
+    (itertools' combinations with replacement)."""
+    import itertools
+    q = np.array([2.0, 3.0, 5.0, 7.0])
+    want = [np.prod(c) for c in itertools.combinations_with_replacement(q, 3)]
+    assert np.array_equal(OF.kron3_c(q[:, None])[:, 0], want)
+    assert OF.kron3_c(np.ones((6, 1))).shape[0] == 6 * 7 * 8 // 6
+
+
+def test_opinf_recovers_known_cubic_operators():
+    """Data of a known cubic model qdd = K q + H kron_c(q) + C kron3_c(q) + B ghat + c is recovered
+    (basis-invariant check on fresh states), and dropping the cubic block leaves a visible residual."""
+    rng = np.random.default_rng(5)
+    n, ns, r, rs = 90, 20, 4, 2
+    nq, nc = r * (r + 1) // 2, r * (r + 1) * (r + 2) // 6
+    Phi_t, PhiS_t = _orthonormal(n, r, rng), _orthonormal(ns, rs, rng)
+    K = rng.standard_normal((r, r))
+    H = rng.standard_normal((r, nq))
+    Cc = rng.standard_normal((r, nc))
+    B = rng.standard_normal((r, rs))
+    c = rng.standard_normal(r)
+    nsnap = 3 * (r + nq + nc + rs + 1)
+    Q = np.diag([4.0, 3.0, 2.0, 1.0]) @ rng.standard_normal((r, nsnap))
+    G = np.diag([2.0, 1.0]) @ rng.standard_normal((rs, nsnap))
+    Qdd = K @ Q + H @ OF.kron_c(Q) + Cc @ OF.kron3_c(Q) + B @ G + c[:, None]
+    U, A, S = Phi_t @ Q, Phi_t @ Qdd, PhiS_t @ G
+    ops = OF.opinf_fit(U, A, S, r=r, lam=1e-14, r_s=rs, cubic=True)
+    quad = OF.opinf_fit(U, A, S, r=r, lam=1e-14, r_s=rs)
+    q_new = rng.standard_normal((r, 10))
+    g_new = rng.standard_normal((rs, 10))
+    for k in range(10):
+        want = Phi_t @ OF.rom_rhs(K, H, B, c, q_new[:, k], g_new[:, k], Cc)
+        q = ops["Phi"].T @ (Phi_t @ q_new[:, k])
+        g = ops["Phi_S"].T @ (PhiS_t @ g_new[:, k])
+        got = ops["Phi"] @ OF.rom_rhs(ops["K"], ops["H"], ops["B"], ops["c"], q, g, ops["C"])
+        assert np.linalg.norm(got - want) < 1e-8 * np.linalg.norm(want)
+        got_q = quad["Phi"] @ OF.rom_rhs(quad["K"], quad["H"], quad["B"], quad["c"], q, g)
+        assert np.linalg.norm(got_q - want) > 1e-2 * np.linalg.norm(want)
+
+
+def test_cubic_rom_subdomain_integrates_a_duffing_oscillator(oracle):
+    """A one-mode cubic ROM subdomain q'' = -w^2 q - g q^3 (K = -w^2, C = -g) advanced by the
+    controller: its trajectory converges at second order to the ODE's solution (scipy, tight
+    tolerances), and the cubic term changes it at leading order (sign and placement of C)."""
+    from scipy.integrate import solve_ivp
+    w, g, a0, T = 2.0e4, 4.0e14, 1e-3, 4e-4
+    ref = solve_ivp(lambda t, y: [y[1], -w * w * y[0] - g * y[0] ** 3], (0.0, T), [a0, 0.0], rtol=1e-12,
+                    atol=1e-16, method="DOP853").y[0, -1]
+    lin = a0 * np.cos(w * T)
+    assert abs(ref - lin) > 0.1 * a0  # the cubic term matters
+
+    def run(n_steps):
+        sd = W.Subdomain(kind="rom", dims=(1, 1, 1), h=0.01, origin=(0.0, 0.0, 0.0))
+        sd.dirichlet = np.zeros(sd.n_nodes, np.uint8)
+        sd.u0 = np.zeros((sd.n_nodes, 3))
+        sd.u0[0, 0] = a0
+        sd.v0 = np.zeros((sd.n_nodes, 3))
+        p = W.Problem(name="duffing", subdomains=[sd], couplings=[], dt=T / n_steps, n_substeps=n_steps)
+        Phi = np.zeros((3 * sd.n_nodes, 1))
+        Phi[0, 0] = 1.0
+        ops = {"Phi": Phi, "Phi_S": np.zeros((0, 0)), "K": np.array([[-w * w]]), "H": np.zeros((1, 1)),
+               "C": np.array([[-g]]), "B": np.zeros((1, 0)), "c": np.zeros(1)}
+        prob = oracle.Problem(p, rom_ops={0: ops})
+        prob.step()
+        return prob.rom_state(0)[0][0]
+
+    errs = [abs(run(n) - ref) for n in (400, 800, 1600)]
+    assert errs[2] < 1e-3 * a0
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5

@@ -30,11 +30,12 @@ def _coords(dims, h, origin):
 # ---------------------------------------------------------------------------------------------
 # constitutive laws (Appendix A)
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("material", ["le", "nh"])
+@pytest.mark.parametrize("material", ["le", "nh", "svk"])
 def test_stress_is_derivative_of_energy_density(oracle, material):
     """P = dA/dF for the energies printed in Appendix A (A.1: 1/2 lam tr(eps)^2 + mu tr(eps^2);
-    A.3: 1/4 kappa (detC - log detC - 1) + 1/2 mu (detC^-1/3 trC - 3)).  This pins the
-    deviatoric coefficient 1/3 of S (the printed 1/2 would fail by O(mu))."""
+    A.2: lam/2 (tr E)^2 + mu tr(E^2); A.3: 1/4 kappa (detC - log detC - 1) + 1/2 mu (detC^-1/3 trC -
+    3)).  This pins the deviatoric coefficient 1/3 of S (the printed 1/2 would fail by O(mu)) and
+    P = F S with S = lam tr(E) I + 2 mu E for Saint Venant-Kirchhoff."""
     rng = np.random.default_rng(1)
     for trial in range(5):
         H = 0.05 * rng.standard_normal((3, 3))
@@ -65,7 +66,7 @@ def test_printed_half_coefficient_would_fail(oracle):
     assert np.abs(P - F @ S_half).max() > 1e-3 * np.abs(P).max()
 
 
-@pytest.mark.parametrize("material", ["le", "nh"])
+@pytest.mark.parametrize("material", ["le", "nh", "svk"])
 def test_internal_force_is_gradient_of_discrete_energy(oracle, material):
     """f_int = d/du of sum_e sum_gp w detJ A(F): checks quadrature, shape gradients and assembly
     against the energy of Appendix A (central differences)."""
@@ -84,7 +85,7 @@ def test_internal_force_is_gradient_of_discrete_energy(oracle, material):
     assert np.abs(f - fd).max() < 1e-6 * np.abs(f).max()
 
 
-@pytest.mark.parametrize("material", ["le", "nh"])
+@pytest.mark.parametrize("material", ["le", "nh", "svk"])
 def test_patch_test_affine_field_has_zero_interior_force(oracle, material):
     """A uniform deformation gradient gives a uniform stress, so the assembled force vanishes at
     every interior node."""
@@ -649,3 +650,67 @@ def test_rom_rom_full_basis_reproduces_fom_fom(oracle):
             q = B.rom_state(i)[0]
             assert np.abs(q - u.reshape(-1)[free]).max() < 1e-12 * np.abs(u).max()
             assert np.abs(B.state(i)[0] - u).max() < 1e-12 * np.abs(u).max()
+
+
+
+# ---------------------------------------------------------------------------------------------
+# Saint Venant-Kirchhoff (Appendix A.2) and the tangents of the implicit solver
+# ---------------------------------------------------------------------------------------------
+def test_svk_energy_uses_the_green_lagrange_strain(oracle):
+    """A.2 with E = 1/2 (F^T F - I): a pure stretch F = diag(1 + a) has E = diag(a + a^2/2); the
+    printed "1/2 F^T F - I" would give a nonzero energy at F = I."""
+    a = np.array([0.02, -0.01, 0.03])
+    E = a + 0.5 * a * a
+    ref = 0.5 * LAM * E.sum() ** 2 + MU * (E * E).sum()
+    assert abs(oracle.energy_density("svk", np.diag(a), LAM, MU) - ref) < 1e-12 * ref
+    assert oracle.energy_density("svk", np.zeros((3, 3)), LAM, MU) == 0.0
+
+
+def test_svk_force_is_cubic_in_the_displacement(oracle):
+    """f(t u) is a polynomial of degree exactly three in t for Saint Venant-Kirchhoff (Appendix A.2:
+    the PDE has cubic nonlinearities); the Neo-Hookean force is not a cubic."""
+    dims, h, org = (2, 1, 2), 0.01, (0.0, 0.0, 0.0)
+    u = _rand_disp(dims, 0.02 * h, 11)
+    ts = np.array([-2.0, -1.0, 1.0, 2.0, 3.0, 0.5])
+    for material, cubic in (("svk", True), ("nh", False)):
+        f = np.array([oracle.internal_force(dims, h, org, material, LAM, MU, t * u) for t in ts])
+        V = np.vander(ts[:4], 4)
+        coef = np.linalg.solve(V, f[:4])
+        pred = np.vander(ts[4:], 4) @ coef
+        err = np.abs(pred - f[4:]).max() / np.abs(f).max()
+        if cubic:
+            assert err < 1e-10 and np.abs(coef[0]).max() > 1e-6 * np.abs(coef[2]).max()
+        else:
+            assert err > 1e-8
+
+
+def test_svk_is_objective_and_linearises_to_linear_elastic(oracle):
+    dims, h, org = (2, 3, 2), 0.01, (0.05, 0.0, -0.02)
+    X, _ = _coords(dims, h, org)
+    th = 0.4
+    R = np.array([[1, 0, 0], [0, np.cos(th), -np.sin(th)], [0, np.sin(th), np.cos(th)]])
+    u = X @ (R - np.eye(3)).T + np.array([0.1, -0.3, 0.2])
+    f_ref = oracle.internal_force(dims, h, org, "svk", LAM, MU, X @ (0.01 * np.eye(3)).T)
+    assert np.abs(oracle.internal_force(dims, h, org, "svk", LAM, MU, u)).max() < 1e-9 * np.abs(f_ref).max()
+    base = _rand_disp(dims, 1.0, 3)
+    gaps = []
+    for eps in (1e-4, 1e-5):
+        w = eps * h * base
+        f_s = oracle.internal_force(dims, h, org, "svk", LAM, MU, w)
+        f_l = oracle.internal_force(dims, h, org, "le", LAM, MU, w)
+        gaps.append(np.abs(f_s - f_l).max() / np.abs(f_l).max())
+    assert gaps[0] < 1e-2 and 5.0 < gaps[0] / gaps[1] < 20.0
+
+
+@pytest.mark.parametrize("material", ["le", "nh", "svk"])
+def test_tangent_action_is_the_derivative_of_the_force(oracle, material):
+    """K(u) p of the assembled element tangents equals the central difference of f_int along p (the
+    Newton matrix of the implicit integrator)."""
+    dims, h, org = (2, 2, 3), 0.01, (0.0, 0.1, 0.0)
+    u = _rand_disp(dims, 0.03 * h, 12)
+    p = _rand_disp(dims, 1.0, 13)
+    y = oracle.tangent_action(dims, h, org, material, LAM, MU, u, p)
+    eps = 1e-7 * h
+    fd = (oracle.internal_force(dims, h, org, material, LAM, MU, u + eps * p)
+          - oracle.internal_force(dims, h, org, material, LAM, MU, u - eps * p)) / (2 * eps)
+    assert np.abs(y - fd).max() < 1e-6 * np.abs(fd).max()
