@@ -55,19 +55,23 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "7b75524b888890d04e6831c55ebaea5cea934da54f34e6f946ab80b46e453866", "bytes_per_launch": 3.573e6,
+FORCE_TRAFFIC = {"source_sha256": "527d0af58909dbf621ae4e71b9915f9b2e4dd69db3ed81e4d8366e9d0639aba0", "bytes_per_launch": 3.573e6,
                  "tiled": True}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
-TANGENT_TRAFFIC = {"source_sha256": None, "bytes_per_launch": 6.708e6}
+# bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
+# points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
+TANGENT_BYTES_PER_ELEMENT = 22 * 8 * 8 + 24
+TANGENT_TRAFFIC = {"source_sha256": "c880ed687a427bdd598d39c0ac1e3688caa02ed0ebdb8fd6d89e623ed8606ed4",
+                   "bytes_per_launch": 1.96896e8}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
-# FP64 flops of one Neo-Hookean element tangent action K(u) p (implicit Newton-CG; FMA = 2 flops, the
-# cube root counted as one flop): scaling of p 24 + differences of u and p 72 + their interpolation
-# to the Gauss points 360 + 8 x 243 directional derivative of P (F, cof F and its derivative, J,
-# traces, scalar chain, dP) + 36 accumulation + 180 transposed interpolation + 48 nodal accumulation
-# + 6 material constants.
-TANGENT_FLOPS_PER_NH_ELEMENT = 2670
+# FP64 flops of one Neo-Hookean element tangent action K(u) p of the implicit Newton-CG (FMA = 2
+# flops), from the Gauss-point linearisation stored with the Newton residual's force: scaling of p
+# 24 + differences of p 36 + their interpolation to the Gauss points 180 + 8 x 166 (cof : G and F : G
+# 36, derivative of the cofactor 63, scalar chain 4, dP 63) + 36 accumulation + 180 transposed
+# interpolation + 48 nodal accumulation.
+TANGENT_FLOPS_PER_NH_ELEMENT = 1832
 # FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
 # around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
 FLOPS_PER_SVK_ELEMENT = 1424
@@ -474,10 +478,11 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
             "newton_per_substep": ip["newton_steps"] / max(1, substeps),
             "cg_per_newton": ip["cg_iterations"] / max(1, ip["newton_steps"]),
             "tangent_time_share": ip["tangent_ms"] / total_ms if total_ms else None,
-            "roofline": {"bound": "alu", "kernel": "k_tangent_b<NeoHookean>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "k_tangent_lin_b (Neo-Hookean)", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                          "traffic": (TANGENT_TRAFFIC["bytes_per_launch"]
                                      if TANGENT_TRAFFIC["source_sha256"] == source_sha(TANGENT_SOURCES) else None),
+                         "algorithmic_bytes_per_launch": ne * TANGENT_BYTES_PER_ELEMENT,
                          "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
                          "ms_per_launch": ip["tangent_ms"] / max(1, ip["tangent_launches"]),
                          "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)"},

@@ -135,6 +135,15 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
     if (threadIdx.x != 0) return;
     if (mode == 0) {
         if (first) g.r0[inst] = s;
+        // forcing term of the inexact Newton step (Eisenstat and Walker's second choice, gamma = 1,
+        // alpha = 2): relative CG tolerance eta = min(1e-6, (|R_k| / |R_k-1|)^2), never below the
+        // floor tol of mode 2; stored squared, as r . z is compared squared-norm to squared-norm
+        double eta2 = 1e-12;
+        if (!first && g.rn2[inst] > 0.0) {
+            const double ratio2 = s / g.rn2[inst];
+            eta2 = fmin(1e-12, ratio2 * ratio2);
+        }
+        g.cgtol2[inst] = eta2;
         g.rn2[inst] = s;
         g.rr[inst] = sz;
         g.rr0[inst] = sz;
@@ -151,7 +160,7 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
     } else {
         g.rrn[inst] = s;
         g.istat[2 * inst + 1] += 1;
-        if (!(s > tol2 * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
+        if (!(s > fmax(tol2, g.cgtol2[inst]) * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
     }
 }
 

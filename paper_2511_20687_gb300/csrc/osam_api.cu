@@ -313,12 +313,14 @@ constexpr double kNewtonTol2 = 1e-24;  // |R|^2 <= kNewtonTol2 |R(u~)|^2
 constexpr double kNewtonInc2 = 1e-28;  // or an increment |du|^2 <= kNewtonInc2 |u|^2 (rounding level of u)
 constexpr int kCgMax = 1000;           // CG iterations per Newton step
 constexpr int kCgCheck = 8;            // CG iterations between host checks of the activity mask
-constexpr double kCgTol2 = 1e-26;      // r.z <= kCgTol2 (r.z)_0 (mass-preconditioned residual)
+constexpr double kCgTol2 = 1e-26;      // floor of the CG test r.z <= eta^2 (r.z)_0 (eta: the Newton forcing term)
 
 // Implicit Newmark interval of FOM slot s (beta = 1/4, gamma = 1/2): per substep the predictor, a
 // Newton solve of M (u - u~) c0 + f_int(u) = 0 (c0 = 1 / (beta dt^2)) with mass-preconditioned
 // conjugate gradients on the exact tangent, until |R| <= 1e-12 |R(u~)| or an increment at the rounding
-// level of u (at most 25 Newton steps), the corrector and the traces of the new level.
+// level of u (at most 25 Newton steps), the corrector and the traces of the new level.  Each CG solve
+// is inexact (Eisenstat-Walker forcing term: relative tolerance min(1e-6, (|R_k| / |R_k-1|)^2), floor
+// 1e-13), so early Newton steps do not over-solve; the Newton test itself is unchanged.
 // Activity is tracked per instance on the device: Newton (nact: 1 iterating, 0 converged, 2 failed)
 // and CG (cgact); the host reads the masks to end the loops.
 int advance_implicit(osam_ctx* ctx, int s, const int* active) {
@@ -330,7 +332,8 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
         LK(launch_mask_copy(n, active, g.nact, ctx->stream));
         LK(launch_mask_copy(n, active, g.cgact, ctx->stream));
         for (int it = 0; it < kNewtonMax; ++it) {
-            LK(launch_force_b(g, g.nact, kGather, ctx->stream, nullptr));
+            if (g.lin) LK(launch_force_lin_b(g, g.nact, ctx->stream));
+            else LK(launch_force_b(g, g.nact, kGather, ctx->stream, nullptr));
             LK(launch_imp_residual_b(g, g.nact, c0, ctx->stream));
             LK(launch_imp_reduce_b(g, g.nact, 0, it == 0, kNewtonTol2, ctx->stream));
             bool any = false;
@@ -339,7 +342,8 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
             for (int k = 0; k < kCgMax;) {
                 for (int q = 0; q < kCgCheck; ++q, ++k) {
                     const int pk = ctx->prof_begin(1);
-                    LK(launch_tangent_b(g, g.cgact, ctx->stream));
+                    if (g.lin) LK(launch_tangent_lin_b(g, g.cgact, ctx->stream));
+                    else LK(launch_tangent_b(g, g.cgact, ctx->stream));
                     ctx->prof_end(pk, 0);
                     LK(launch_cg_ap_b(g, g.cgact, c0, ctx->stream));
                     LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, ctx->stream));
@@ -768,8 +772,9 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CKA(B.cg_r = ctx->alloc<double>(3 * NN));
         CKA(B.cg_p = ctx->alloc<double>(3 * NN));
         CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
-        for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap}) CKA(*p = ctx->alloc<double>(n));
+        for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap, &B.cgtol2}) CKA(*p = ctx->alloc<double>(n));
         CKA(B.istat = ctx->alloc<long long>(2 * n));
+        if (B.material == OSAM_NEO_HOOKEAN) CKA(B.lin = ctx->alloc<double>((long long)kLinPerGp * 8 * NE));
         CK(cudaMemsetAsync(B.istat, 0, sizeof(long long) * 2 * n, ctx->stream));
         CKA(B.nact = ctx->alloc<int>(n));
         CKA(B.cgact = ctx->alloc<int>(n));

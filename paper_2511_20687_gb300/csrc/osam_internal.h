@@ -23,6 +23,7 @@ namespace osam {
 enum Scatter { kAtomic = 1, kGather = 2 };
 
 constexpr int kMaxSlots = 8;    // subdomains per instance
+constexpr int kLinPerGp = 22;   // doubles per Gauss point of the stored Neo-Hookean Newton linearisation
 constexpr int kNodeBlock = 128; // nodes per block of the node kernels
 
 struct Grid {
@@ -107,9 +108,11 @@ struct FomB {
     double* rrn;              // per instance: r . z after the update
     double* rr0;              // per instance: r . z at the start of the CG solve
     double* pap;              // per instance: p . A p
+    double* cgtol2;           // per instance: squared relative CG tolerance of the current Newton step
     int* nact;                // per instance Newton state: 1 iterating, 0 converged, 2 failed
     int* cgact;               // per instance: CG still iterating
     long long* istat;         // per instance: Newton linear solves, CG iterations (since the last reset)
+    double* lin;              // Neo-Hookean implicit groups: stored Newton linearisation [kLinPerGp][8][NE]
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 
@@ -241,6 +244,10 @@ cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cud
 // 3: |du|^2 <= tol2 |u|^2 after a Newton update (clears nact)
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s);
 cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
+// Neo-Hookean implicit groups: Newton force that also stores the Gauss-point linearisation, and the
+// tangent action that reads it
+cudaError_t launch_force_lin_b(const FomB& g, const int* mask, cudaStream_t s);
+cudaError_t launch_tangent_lin_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s);

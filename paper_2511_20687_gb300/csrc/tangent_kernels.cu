@@ -155,7 +155,214 @@ __global__ void __launch_bounds__(256) k_tangent_b(const FomB g, const int* __re
     }
 }
 
+// ---- Neo-Hookean Newton linearisation stored once per Newton step --------------------------------
+// The tangent at u is applied ~6 times per Newton step (CG iterations) while u stays fixed, so the
+// u-dependent part of dP = dbeta cof + beta dcof[G] + dalpha F + alpha G is computed once, with the
+// force of the Newton residual, and stored per Gauss point: F, cof F, alpha, beta and the two
+// coefficients of the scalar derivatives, dalpha = a1 dJ and dbeta = b1 dJ + a1 (F : G), dJ = cof : G,
+//   a1 = -2/3 alpha / J,  b1 = 2 kappa/2 - (a1 trC / 3 + beta) / J   (from P = alpha F + beta cof,
+//   alpha = mu J^-2/3, beta = (kappa/2 (J^2 - 1) - mu/3 J^-2/3 trC) / J).
+// Layout [kLinPerGp][8 Gauss points][NE], element index fastest (coalesced): F (9), cof F (9), alpha,
+// beta, a1, b1.
+static_assert(kLinPerGp == 22, "stored linearisation: F, cof F, alpha, beta, a1, b1");
+
+__device__ __forceinline__ void nodal_grads(const FomB& g, const InstFom& I, const double* x, double scale,
+                                            const int node[8], double Gx[3][2][2], double Gy[3][2][2],
+                                            double Gz[3][2][2]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double V[8], Dx[2][2], Dy[2][2], Dz[2][2];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) V[c8] = x[(long long)c * g.NN + I.node_off + node[c8]] * scale;
+        edge_differences_prescaled<double>(V, Dx, Dy, Dz);
+        lerp2<double>(Dx, Gx[c]); lerp2<double>(Dy, Gy[c]); lerp2<double>(Dz, Gz[c]);
+    }
+}
+
+// transposed interpolation of the Gauss-point sums and the element-buffer write
+__device__ __forceinline__ void write_element(const FomB& g, const InstFom& I, int e, const double Sx[3][2][2],
+                                              const double Sy[3][2][2], const double Sz[3][2][2]) {
+    double* fe = static_cast<double*>(g.fe) + I.elem_off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double Fc[8], Tm[2][2];
+        lerp2T<double>(Sx[c], Tm);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
+        lerp2T<double>(Sy[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
+        lerp2T<double>(Sz[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
+    }
+}
+
+struct ElemIdx {
+    InstFom I;
+    int e;
+    int node[8];
+    bool ok;
+};
+
+__device__ __forceinline__ ElemIdx elem_idx(const FomB& g, const int* mask) {
+    ElemIdx x;
+    const int2 b = g.eblk[blockIdx.x];
+    x.ok = run_inst(mask, b.x);
+    x.I = g.inst[b.x];
+    x.e = b.y + threadIdx.x;
+    x.ok = x.ok && x.e < x.I.ne;
+    if (!x.ok) return x;
+    const int i = x.e % x.I.nx;
+    const int t = x.e / x.I.nx;
+    const int j = t % x.I.ny;
+    const int k = t / x.I.ny;
+    const int sy = x.I.nx + 1, sz = (x.I.nx + 1) * (x.I.ny + 1);
+    const int n0 = i + sy * j + sz * k;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) x.node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
+    return x;
+}
+
+// Newton residual force of a Neo-Hookean group at u (from u / h) plus the stored linearisation
+__global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, const int* __restrict__ mask) {
+    const ElemIdx x = elem_idx(g, mask);
+    if (!x.ok) return;
+    const InstFom& I = x.I;
+    const int e = x.e;
+    double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
+    nodal_grads(g, I, g.us, 1.0, x.node, Gx, Gy, Gz);
+    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
+    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
+    const double kappa = lam + (2.0 / 3.0) * mu;
+    const double m1 = 0.5 * kappa * I.w8, m2 = mu * I.w8, m3 = mu * I.w8 / 3.0;
+    double* lin = g.lin + I.elem_off + e;
+    const long long st = 8LL * g.NE;  // stride between quantities
+    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int gp = 4 * p + 2 * q + r;
+                double Hm[3][3], Fm[3][3], Cm[3][3], alpha, beta;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { Hm[c][0] = Gx[c][q][r]; Hm[c][1] = Gy[c][p][r]; Hm[c][2] = Gz[c][p][q]; }
+                nh_factors<double>(Hm, m1, m2, m3, Fm, Cm, alpha, beta);
+                const double J = fma(Fm[0][0], Cm[0][0], fma(Fm[0][1], Cm[0][1], Fm[0][2] * Cm[0][2]));
+                double trC = 0.0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) trC = fma(Fm[a / 3][a % 3], Fm[a / 3][a % 3], trC);
+                const double invJ = 1.0 / J;
+                const double a1 = -(2.0 / 3.0) * alpha * invJ;
+                const double b1 = 2.0 * m1 - invJ * fma(a1, trC * (1.0 / 3.0), beta);
+                double* lg = lin + (long long)gp * g.NE;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    lg[a * st] = Fm[a / 3][a % 3];
+                    lg[(9 + a) * st] = Cm[a / 3][a % 3];
+                }
+                lg[18 * st] = alpha; lg[19 * st] = beta; lg[20 * st] = a1; lg[21 * st] = b1;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double P0 = fma(alpha, Fm[c][0], beta * Cm[c][0]);
+                    const double P1 = fma(alpha, Fm[c][1], beta * Cm[c][1]);
+                    const double P2 = fma(alpha, Fm[c][2], beta * Cm[c][2]);
+                    if (p == 0) Sx[c][q][r] = P0; else Sx[c][q][r] += P0;
+                    if (q == 0) Sy[c][p][r] = P1; else Sy[c][p][r] += P1;
+                    if (r == 0) Sz[c][p][q] = P2; else Sz[c][p][q] += P2;
+                }
+            }
+    write_element(g, I, e, Sx, Sy, Sz);
+}
+
+// tangent action from the stored linearisation: per Gauss point 166 FP64 flops instead of 243, and
+// no interpolation of u
+__global__ void __launch_bounds__(256) k_tangent_lin_b(const FomB g, const int* __restrict__ mask) {
+    const ElemIdx x = elem_idx(g, mask);
+    if (!x.ok) return;
+    const InstFom& I = x.I;
+    const int e = x.e;
+    double Bx[3][2][2], By[3][2][2], Bz[3][2][2];
+    nodal_grads(g, I, g.cg_p, I.invh, x.node, Bx, By, Bz);
+    const double* lin = g.lin + I.elem_off + e;
+    const long long st = 8LL * g.NE;
+    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int gp = 4 * p + 2 * q + r;
+                const double* lg = lin + (long long)gp * g.NE;
+                double F[3][3], cf[3][3], G[3][3], dc[3][3];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    F[a / 3][a % 3] = __ldg(lg + a * st);
+                    cf[a / 3][a % 3] = __ldg(lg + (9 + a) * st);
+                }
+                const double alpha = __ldg(lg + 18 * st), beta = __ldg(lg + 19 * st);
+                const double a1 = __ldg(lg + 20 * st), b1 = __ldg(lg + 21 * st);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { G[c][0] = Bx[c][q][r]; G[c][1] = By[c][p][r]; G[c][2] = Bz[c][p][q]; }
+                double dJ = 0.0, FG = 0.0;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    dJ = fma(cf[a / 3][a % 3], G[a / 3][a % 3], dJ);
+                    FG = fma(F[a / 3][a % 3], G[a / 3][a % 3], FG);
+                }
+                dc[0][0] = G[1][1] * F[2][2] + F[1][1] * G[2][2] - G[1][2] * F[2][1] - F[1][2] * G[2][1];
+                dc[0][1] = G[1][2] * F[2][0] + F[1][2] * G[2][0] - G[1][0] * F[2][2] - F[1][0] * G[2][2];
+                dc[0][2] = G[1][0] * F[2][1] + F[1][0] * G[2][1] - G[1][1] * F[2][0] - F[1][1] * G[2][0];
+                dc[1][0] = G[0][2] * F[2][1] + F[0][2] * G[2][1] - G[0][1] * F[2][2] - F[0][1] * G[2][2];
+                dc[1][1] = G[0][0] * F[2][2] + F[0][0] * G[2][2] - G[0][2] * F[2][0] - F[0][2] * G[2][0];
+                dc[1][2] = G[0][1] * F[2][0] + F[0][1] * G[2][0] - G[0][0] * F[2][1] - F[0][0] * G[2][1];
+                dc[2][0] = G[0][1] * F[1][2] + F[0][1] * G[1][2] - G[0][2] * F[1][1] - F[0][2] * G[1][1];
+                dc[2][1] = G[0][2] * F[1][0] + F[0][2] * G[1][0] - G[0][0] * F[1][2] - F[0][0] * G[1][2];
+                dc[2][2] = G[0][0] * F[1][1] + F[0][0] * G[1][1] - G[0][1] * F[1][0] - F[0][1] * G[1][0];
+                const double dalpha = a1 * dJ;
+                const double dbeta = fma(b1, dJ, a1 * FG);
+                double dP[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b2 = 0; b2 < 3; ++b2)
+                        dP[a][b2] = fma(dbeta, cf[a][b2], fma(beta, dc[a][b2], fma(dalpha, F[a][b2], alpha * G[a][b2])));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (p == 0) Sx[c][q][r] = dP[c][0]; else Sx[c][q][r] += dP[c][0];
+                    if (q == 0) Sy[c][p][r] = dP[c][1]; else Sy[c][p][r] += dP[c][1];
+                    if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
+                }
+            }
+    write_element(g, I, e, Sx, Sy, Sz);
+}
+
 }  // namespace
+
+cudaError_t launch_force_lin_b(const FomB& g, const int* mask, cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    if (g.eblock > 256 || !g.lin || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
+    k_force_lin_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tangent_lin_b(const FomB& g, const int* mask, cudaStream_t s) {
+    if (g.n_eblk == 0) return cudaSuccess;
+    if (g.eblock > 256 || !g.lin || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
+    k_tangent_lin_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s) {
     if (g.n_eblk == 0) return cudaSuccess;
