@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_imp_residual_b(const FomB g, con
 __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int mode, int first, double tol2) {
     const int inst = blockIdx.x;
     if (!run(mask, inst)) return;
+    if (first < 0) first = g.iloop[0] == 0;  // device-side Newton loop: its counter says which step this is
     const int b0 = g.nblk_off[inst], b1 = g.nblk_off[inst + 1];
     const bool two = mode == 0 || mode == 3;
     double s = 0.0, sz = 0.0;
@@ -290,6 +291,30 @@ __global__ void __launch_bounds__(kNodeBlock) k_imp_finish_b(const FomB g, const
     }
 }
 
+// Device-side loop control (conditional WHILE nodes of a CUDA graph): which = 0 the Newton loop,
+// 1 the CG loop.  Entry: reset the loop's counter, enter (Newton) or enter if an instance still has
+// a CG solve to do.  Condition at the end of a pass: count the pass, continue while some instance is
+// still iterating and the cap is not reached (the loops end after at most max_it passes).
+__global__ void k_imp_loop_entry(const FomB g, cudaGraphConditionalHandle h, int which) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    g.iloop[which] = 0;
+    unsigned int go = 1;
+    if (which == 1) {
+        go = 0;
+        for (int i = 0; i < g.n_inst; ++i) go |= g.cgact[i] == 1 ? 1u : 0u;
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+__global__ void k_imp_loop_cond(const FomB g, cudaGraphConditionalHandle h, int which, int max_it) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = ++g.iloop[which];
+    const int* m = which == 0 ? g.nact : g.cgact;
+    unsigned int go = 0;
+    for (int i = 0; i < g.n_inst; ++i) go |= m[i] == 1 ? 1u : 0u;
+    cudaGraphSetConditional(h, (go && it < max_it) ? 1u : 0u);
+}
+
 __global__ void k_mask_copy(int n, const int* __restrict__ src, int* dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = src ? src[i] : 1;
@@ -330,6 +355,14 @@ cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s) 
 }
 cudaError_t launch_imp_finish_b(const FomB& g, const int* active, int slot1, double dt, double c0, cudaStream_t s) {
     k_imp_finish_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, active, slot1, dt, c0);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_loop_entry(const FomB& g, cudaGraphConditionalHandle h, int which, cudaStream_t s) {
+    k_imp_loop_entry<<<1, 32, 0, s>>>(g, h, which);
+    return cudaGetLastError();
+}
+cudaError_t launch_imp_loop_cond(const FomB& g, cudaGraphConditionalHandle h, int which, int max_it, cudaStream_t s) {
+    k_imp_loop_cond<<<1, 32, 0, s>>>(g, h, which, max_it);
     return cudaGetLastError();
 }
 cudaError_t launch_mask_copy(int n, const int* src, int* dst, cudaStream_t s) {

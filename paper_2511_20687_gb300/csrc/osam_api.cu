@@ -89,7 +89,19 @@ struct osam_ctx {
     double* cden_h = nullptr;
     int* any_h = nullptr;
     int* imp_h = nullptr;                 // pinned mirror of a per-instance Newton / CG activity mask
-    bool any_implicit = false;            // some FOM group integrates implicitly (host-driven steps)
+    bool any_implicit = false;            // some FOM group integrates implicitly
+    // implicit intervals as CUDA graphs with device-side Newton / CG loops: two streams on which the
+    // bodies of the nested conditional nodes are captured, and one instantiated interval per
+    // (subdomain, activity mask) for launches outside a controller-step capture
+    cudaStream_t cap[2] = {nullptr, nullptr};
+    struct ImpExec {
+        int slot;
+        const int* active;
+        cudaGraph_t graph;
+        cudaGraphExec_t exec;
+        long long kernels;
+    };
+    std::vector<ImpExec> imp_exec;
     double* scratch = nullptr;            // device [3 * max nodes of any instance]
     int* err_d = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -136,6 +148,12 @@ struct osam_ctx {
         for (cudaEvent_t e : pev) cudaEventDestroy(e);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        for (ImpExec& x : imp_exec) {
+            cudaGraphExecDestroy(x.exec);
+            cudaGraphDestroy(x.graph);
+        }
+        for (cudaStream_t c : cap)
+            if (c) cudaStreamDestroy(c);
         for (cudaEvent_t e : lane_join) cudaEventDestroy(e);
         for (cudaStream_t l : lanes) {
             cudaStreamSynchronize(l);
@@ -365,9 +383,146 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
     return OSAM_OK;
 }
 
+// ---- implicit interval as a graph with device-side loops ------------------------------------------
+// A conditional WHILE node added to the graph being captured on stream st (the handle must exist
+// before the kernel that sets its entry value is captured, so it is created first).
+int while_handle(osam_ctx* ctx, cudaStream_t st, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive) return ctx->fail(OSAM_ECUDA, "implicit loop outside a capture");
+    CK(cudaGraphConditionalHandleCreate(h, g, 0, 0));
+    return OSAM_OK;
+}
+
+int while_node(osam_ctx* ctx, cudaStream_t st, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, ed, nd, &cp));
+    CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *body = cp.conditional.phGraph_out[0];
+    return OSAM_OK;
+}
+
+// One implicit interval of FOM slot s into the graph being captured on ctx->stream: per substep the
+// predictor, a WHILE node over Newton steps whose body holds the residual, a nested WHILE node over
+// CG iterations and the update, then the corrector and the traces.  Same kernels and per-instance
+// masks as advance_implicit, without host round trips and without masked trailing CG passes.
+int enqueue_implicit_captured(osam_ctx* ctx, int s, const int* active) {
+    FomB& g = ctx->slots[s].fom.d;
+    const int n = g.n_inst;
+    const double dt = ctx->slots[s].dt, c0 = 4.0 / (dt * dt);
+    cudaStream_t main = ctx->stream;
+    for (int j = 0; j < ctx->slots[s].nsub; ++j) {
+        LK(launch_imp_predict_b(g, active, j + 1, dt, main));
+        LK(launch_mask_copy(n, active, g.nact, main));
+        LK(launch_mask_copy(n, active, g.cgact, main));
+        cudaGraphConditionalHandle hn, hc;
+        cudaGraph_t nbody, cbody;
+        RET(while_handle(ctx, main, &hn));
+        LK(launch_imp_loop_entry(g, hn, 0, main));
+        RET(while_node(ctx, main, hn, &nbody));
+        // Newton body on cap[0]
+        CK(cudaStreamBeginCaptureToGraph(ctx->cap[0], nbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = OSAM_OK;
+        {
+            cudaStream_t a = ctx->cap[0];
+            auto body = [&]() -> int {
+                if (g.lin) LK(launch_force_lin_b(g, g.nact, a));
+                else LK(launch_force_b(g, g.nact, kGather, a, nullptr));
+                LK(launch_imp_residual_b(g, g.nact, c0, a));
+                LK(launch_imp_reduce_b(g, g.nact, 0, -1, kNewtonTol2, a));
+                RET(while_handle(ctx, a, &hc));
+                LK(launch_imp_loop_entry(g, hc, 1, a));
+                RET(while_node(ctx, a, hc, &cbody));
+                // CG body on cap[1]
+                CK(cudaStreamBeginCaptureToGraph(ctx->cap[1], cbody, nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeThreadLocal));
+                cudaStream_t b = ctx->cap[1];
+                int rc2 = OSAM_OK;
+                auto cg = [&]() -> int {
+                    if (g.lin) LK(launch_tangent_lin_b(g, g.cgact, b));
+                    else LK(launch_tangent_b(g, g.cgact, b));
+                    LK(launch_cg_ap_b(g, g.cgact, c0, b));
+                    LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, b));
+                    LK(launch_cg_step_b(g, g.cgact, c0, b));
+                    LK(launch_imp_reduce_b(g, g.cgact, 2, 0, kCgTol2, b));
+                    LK(launch_cg_dir_b(g, g.cgact, c0, b));
+                    LK(launch_imp_loop_cond(g, hc, 1, kCgMax, b));
+                    return OSAM_OK;
+                };
+                rc2 = cg();
+                cudaGraph_t cb = nullptr;
+                cudaError_t ec = cudaStreamEndCapture(b, &cb);
+                if (rc2) return rc2;
+                CK(ec);
+                LK(launch_imp_update_b(g, g.nact, a));
+                LK(launch_imp_reduce_b(g, g.nact, 3, 0, kNewtonInc2, a));
+                LK(launch_imp_loop_cond(g, hn, 0, kNewtonMax, a));
+                return OSAM_OK;
+            };
+            rc = body();
+        }
+        cudaGraph_t nb = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(ctx->cap[0], &nb);
+        if (rc) return rc;
+        CK(ec);
+        LK(launch_imp_finish_b(g, active, j + 1, dt, c0, main));
+        for (CplH& c : ctx->cpls)
+            if (c.src == s) LK(launch_trace_b(c.d, active, g, g.u[0], j + 1, main));
+    }
+    return OSAM_OK;
+}
+
+// implicit interval of FOM slot s: inside a controller-step capture its nodes join that graph;
+// otherwise an instantiated graph of the interval (built once per activity mask) is launched; with
+// kernel-level profiling on, the host-driven loop (CUDA events around every tangent launch)
+int enqueue_implicit(osam_ctx* ctx, int s, const int* active) {
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusActive) return enqueue_implicit_captured(ctx, s, active);
+    if (ctx->prof) return advance_implicit(ctx, s, active);
+    for (osam_ctx::ImpExec& x : ctx->imp_exec)
+        if (x.slot == s && x.active == active) {
+            CK(cudaGraphLaunch(x.exec, ctx->stream));
+            ctx->launches += x.kernels;
+            return OSAM_OK;
+        }
+    if (!ctx->cap[0])
+        for (cudaStream_t& c : ctx->cap) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    const long long l0 = ctx->launches;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_implicit_captured(ctx, s, active);
+    cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+    const long long nk = ctx->launches - l0;
+    ctx->launches = l0;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CK(ec);
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    ctx->imp_exec.push_back({s, active, graph, exec, nk});
+    CK(cudaGraphLaunch(exec, ctx->stream));
+    ctx->launches += nk;
+    return OSAM_OK;
+}
+
 int advance_slot(osam_ctx* ctx, int s, const int* active) {
     Slot& S = ctx->slots[s];
-    if (S.kind == OSAM_FOM && S.fom.d.implicit) return advance_implicit(ctx, s, active);
+    if (S.kind == OSAM_FOM && S.fom.d.implicit) return enqueue_implicit(ctx, s, active);
     if (S.kind == OSAM_FOM) {
         FomB& g = S.fom.d;
         long long ne = 0;
@@ -774,6 +929,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
         for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap, &B.cgtol2}) CKA(*p = ctx->alloc<double>(n));
         CKA(B.istat = ctx->alloc<long long>(2 * n));
+        CKA(B.iloop = ctx->alloc<int>(2));
         if (B.material == OSAM_NEO_HOOKEAN) CKA(B.lin = ctx->alloc<double>((long long)kLinPerGp * 8 * NE));
         CK(cudaMemsetAsync(B.istat, 0, sizeof(long long) * 2 * n, ctx->stream));
         CKA(B.nact = ctx->alloc<int>(n));
@@ -1348,6 +1504,8 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         else RET(setup_rom_group(ctx, S.rom, s, n, descs));
     }
     RET(setup_couplings(ctx, n, descs, masks));
+    if (ctx->any_implicit)
+        for (cudaStream_t& c : ctx->cap) CK(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
     RET(setup_controller(ctx));
     // initial boundary data: zero-order hold of the initial states (before the accelerations)
     for (CplH& c : ctx->cpls) RET(zoh_cpl(ctx, c, nullptr));
@@ -1479,7 +1637,7 @@ int osam_criterion(osam_ctx* ctx, double* cnum, double* cden) {
 
 int osam_batch_step(osam_ctx* ctx, osam_step_report* reps, osam_step_report* total) {
     if (!ctx) return OSAM_EINVAL;
-    const bool graph = ctx->use_graph && !ctx->prof && !ctx->any_implicit;
+    const bool graph = ctx->use_graph && !ctx->prof;
     if (graph) RET(build_graph(ctx));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (graph) {

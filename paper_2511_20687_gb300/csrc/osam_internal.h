@@ -109,6 +109,7 @@ struct FomB {
     double* rr0;              // per instance: r . z at the start of the CG solve
     double* pap;              // per instance: p . A p
     double* cgtol2;           // per instance: squared relative CG tolerance of the current Newton step
+    int* iloop;               // device-side loop counters: [0] Newton steps, [1] CG iterations
     int* nact;                // per instance Newton state: 1 iterating, 0 converged, 2 failed
     int* cgact;               // per instance: CG still iterating
     long long* istat;         // per instance: Newton linear solves, CG iterations (since the last reset)
@@ -240,7 +241,8 @@ cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int u
 cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, double dt, cudaStream_t s);
 cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 // reduce the node-block partials per instance; mode 0: Newton residual (sets rn2, r0 on the first
-// iteration, rr, rr0, nact, cgact), 1: p . Ap, 2: r . z after a CG update (sets rrn, cgact),
+// iteration (first < 0: the device-side Newton counter decides), rr, rr0, nact, cgact), 1: p . Ap,
+// 2: r . z after a CG update (sets rrn, cgact),
 // 3: |du|^2 <= tol2 |u|^2 after a Newton update (clears nact)
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s);
 cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
@@ -254,6 +256,9 @@ cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStrea
 cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_imp_finish_b(const FomB& g, const int* active, int slot1, double dt, double c0, cudaStream_t s);
 cudaError_t launch_mask_copy(int n, const int* src, int* dst, cudaStream_t s);
+// device-side loop control of the implicit solve (conditional WHILE nodes): which 0 Newton, 1 CG
+cudaError_t launch_imp_loop_entry(const FomB& g, cudaGraphConditionalHandle h, int which, cudaStream_t s);
+cudaError_t launch_imp_loop_cond(const FomB& g, cudaGraphConditionalHandle h, int which, int max_it, cudaStream_t s);
 
 // ROM set-up and I/O (rom_kernels.cu)
 cudaError_t launch_rom_basis_project(int nfree, int r, const double* Phi, const int* free_dof, const double* u_aos,

@@ -155,3 +155,23 @@ def test_implicit_nonfinite_state_reported(gpu):
     with pytest.raises(O.OracleError) as e:
         ref.step()
     assert e.value.code == O.ENONFINITE
+
+
+def test_device_loops_equal_host_loop(gpu):
+    """The implicit interval as a graph (Newton and CG as device-side WHILE nodes, inside the captured
+    controller step or as a per-interval graph) follows the host-driven Newton / CG loop bit for bit:
+    same kernels, same per-instance masks, only the trailing masked CG passes and the host round trips
+    are gone."""
+    spec = _implicit(W.bar_chain("dl", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 2e-6, 5,
+                                 max_iters=40), {1})
+    a = osam.Problem(spec, graph=True)
+    b = osam.Problem(spec, graph=False)
+    c = osam.Problem(spec, graph=False)
+    c.profile(True)   # kernel-level profiling drives the Newton / CG loops from the host
+    for _ in range(3):
+        ra, rb, rc = a.step(), b.step(), c.step()
+        assert ra["iterations"] == rb["iterations"] == rc["iterations"]
+    for i in range(2):
+        for f in range(3):
+            assert np.array_equal(a.state(i)[f], b.state(i)[f])
+            assert np.array_equal(a.state(i)[f], c.state(i)[f])

@@ -167,3 +167,40 @@ def test_substep_counts_must_agree_across_instances(gpu):
     with pytest.raises(osam.OsamError) as e:
         osam.Batch(specs)
     assert e.value.code == osam.EINVAL
+
+
+@pytest.mark.parametrize("steppers,counts", [(("implicit", "implicit"), (10, 10)), (("explicit", "implicit"), (10, 10)),
+                                             (("explicit", "explicit"), (10, 10)), (("explicit", "implicit"), (10, 5))])
+def test_wave1d_stepper_matrix_matches_dalembert(gpu, steppers, counts):
+    """The 1D bar of Sec. 5.1 on the paper's decomposition and mesh (dz = 1e-3 m) with each time-stepper
+    pairing of its table of steppers (implicit / implicit, explicit / implicit, explicit / explicit at
+    dt = 1e-7 s, and explicit 1e-7 s / implicit 2e-7 s), controller intervals of 1e-6 s: after the
+    pulse has crossed both Schwarz boundaries (t = 3e-4 s) the FOM-FOM solution matches the exact
+    solution Eq. disp_exact to the discretisation error (the explicit / explicit run of the oracle at
+    this resolution: 2.1e-3 relative L2)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "wave1d_symmetric_gaussian.json")))
+    a, b, s = g["initial_condition"]["a"], g["initial_condition"]["b"], g["initial_condition"]["s"]
+    c = (g["E"] / g["rho"]) ** 0.5
+    T = g["T"]
+
+    def exact(z, t):
+        f = lambda x: a * np.exp(-((x - b) ** 2) / (2 * s * s))  # noqa: E731
+        return 0.5 * f(z - c * t) + 0.5 * f(z + c * t) - 0.5 * f(z - c * (T - t)) - 0.5 * f(z + c * (T - t))
+
+    p = W.wave1d(n_elem=1000, dt=1e-7, subdomains=True, n_substeps=10)
+    _setup(p, counts, steppers)
+    prob = osam.Problem(p)
+    t = 0.0
+    for _ in range(300):
+        assert prob.step()["status"] == osam.OK
+        t += p.dt * p.n_substeps
+    num = den = 0.0
+    for i in range(2):
+        u = prob.state(i)[0][:, 2]
+        ex = exact(p.subdomains[i].node_coords()[:, 2], t)
+        num += np.sum((u - ex) ** 2)
+        den += np.sum(ex ** 2)
+    prob.close()
+    assert np.sqrt(num / den) < 5e-3
