@@ -523,6 +523,40 @@ def _timed_steps(prob, torch, flush, steps, warmup):
     return ms, upd, its
 
 
+def _sample_pair(W, osam, spec, rom_ops, local, n_steps=2):
+    """The same variant on a small seeded problem, GPU and oracle side by side (element-updates/s of
+    the FOM subdomains; oracle on one core)."""
+    from oracle import oracle as O
+    g = osam.Problem(spec, rom_ops=rom_ops, device=local)
+    g.step()
+    gms, gupd = 0.0, 0
+    for _ in range(n_steps):
+        r = g.step()
+        gms += r["elapsed_ms"]
+        gupd += r["element_updates"]
+    g.close()
+    ref = O.Problem(spec, rom_ops=rom_ops)
+    t0 = time.process_time()
+    its = [ref.step()["iterations"] for _ in range(n_steps)]
+    cpu = time.process_time() - t0
+    upd = sum(it * sum((sd.n_substeps or spec.n_substeps) * sd.n_elements for sd in spec.subdomains
+                       if sd.kind == "fom") for it in its)
+    return {"sample_gpu_value": gupd / (gms * 1e-3), "sample_oracle_value": upd / cpu, "oracle_cores": 1}
+
+
+def _small_cubic_rom(W, spec_ff, i, r):
+    from oracle import fit as OF
+    from oracle import oracle as O
+    prob = O.Problem(spec_ff)
+    free, sdof = prob.free_dofs(i), prob.schwarz_dofs(i)
+    U, A, S = [], [], []
+    for _ in range(40):
+        prob.step()
+        u, _, a = prob.state(i)
+        U.append(u.reshape(-1)[free]); A.append(a.reshape(-1)[free]); S.append(u.reshape(-1)[sdof])
+    return OF.opinf_fit(np.array(U).T, np.array(A).T, np.array(S).T, r=r, lam=1e-6, r_s=4, cubic=True)
+
+
 def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5, warmup=2):
     """The headline hybrid under the method's other variants (each a parity-tested path):
     additive sweeps (FOM and ROM concurrently on their own streams), mixed time integrators and steps
@@ -570,8 +604,24 @@ def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "flops_per_element": FLOPS_PER_SVK_ELEMENT,
                      "force_ms_per_launch": prof["force_ms"] / max(1, prof["force_launches"])}}
+    # oracle beside each variant, on a small bar of the same kind (3x3x[8,8] FOMs, 20 substeps)
+    small = W.bar_chain("s_add", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 20, max_iters=64)
+    small.schwarz = "additive"
+    out["additive"].update(_sample_pair(W, osam, small, None, local),
+                           sample="3x3x8 + 3x3x8 Neo-Hookean FOM-FOM bar, additive, 2 controller steps")
+    small = W.bar_chain("s_mix", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 20, max_iters=64)
+    small.subdomains[0].integrator = "implicit"
+    small.subdomains[0].n_substeps = 2
+    out["mixed_implicit_explicit"].update(
+        _sample_pair(W, osam, small, None, local),
+        sample="3x3x8 + 3x3x8 Neo-Hookean bar, FOM 0 implicit 2 x 10 us, FOM 1 explicit 20 x 1 us, 2 controller steps")
+    small_ff = W.bar_chain("s_svkff", 3, [8, 8], ["fom", "fom"], "svk", 1e9, 0.3, 1000.0, 1e-3, 1e-6, 4)
+    small = W.bar_chain("s_svk", 3, [8, 8], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 1e-3, 1e-6, 20, max_iters=64)
+    out["svk_copinf"].update(_sample_pair(W, osam, small, {1: _small_cubic_rom(W, small_ff, 1, 6)}, local),
+                             sample="3x3x8 SVK FOM + cubic ROM r=6 (oracle-fitted on 40 snapshots), 2 controller steps")
     for k, v in out.items():
-        log(f"{k}: {v['value']:.3e} element-updates/s, {v['ms_per_step']:.2f} ms/step, {v['mean_iterations']:.1f} its")
+        log(f"{k}: {v['value']:.3e} element-updates/s, {v['ms_per_step']:.2f} ms/step, {v['mean_iterations']:.1f} its; "
+            f"sample GPU {v['sample_gpu_value']:.3e} vs oracle {v['sample_oracle_value']:.3e}")
     out["note"] = (f"intervals_per_s: controller intervals of {T * 1e6:.0f} us advanced per second; "
                    "parity: tests/test_gpu_additive.py, test_gpu_mixed_dt.py, test_gpu_svk.py, test_gpu_cubic.py")
     return out

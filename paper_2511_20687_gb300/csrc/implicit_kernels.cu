@@ -125,20 +125,19 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
     if (!run(mask, inst)) return;
     if (first < 0) first = g.iloop[0] == 0;  // device-side Newton loop: its counter says which step this is
     const int b0 = g.nblk_off[inst], b1 = g.nblk_off[inst + 1];
-    const bool two = mode == 0 || mode == 3;
     double s = 0.0, sz = 0.0;
     for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) {
         s += g.ipart[b];
-        if (two) sz += g.ipart[g.n_nblk + b];
+        sz += g.ipart[g.n_nblk + b];
     }
     s = block_sum1(s);
-    if (two) sz = block_sum1(sz);
+    sz = block_sum1(sz);
     if (threadIdx.x != 0) return;
     if (mode == 0) {
         if (first) g.r0[inst] = s;
         // forcing term of the inexact Newton step (Eisenstat and Walker's second choice, gamma = 1,
-        // alpha = 2): relative CG tolerance eta = min(1e-6, (|R_k| / |R_k-1|)^2), never below the
-        // floor tol of mode 2; stored squared, as r . z is compared squared-norm to squared-norm
+        // alpha = 2): relative CG tolerance eta = min(1e-6, (|R_k| / |R_k-1|)^2), never below the CG
+        // floor of k_cg_step_b; stored squared, as r . z is compared squared-norm to squared-norm
         double eta2 = 1e-12;
         if (!first && g.rn2[inst] > 0.0) {
             const double ratio2 = s / g.rn2[inst];
@@ -153,19 +152,37 @@ __global__ void k_imp_reduce_b(const FomB g, const int* __restrict__ mask, int m
         g.nact[inst] = st;
         g.cgact[inst] = st == 1 ? 1 : 0;
         if (st == 1) g.istat[2 * inst] += 1;
-    } else if (mode == 1) {
-        g.pap[inst] = s;
-    } else if (mode == 3) {
-        // |du|^2 against |u|^2 after the update: an increment at the rounding level of u converges
-        if (isfinite(s) && s <= tol2 * sz) g.nact[inst] = 0;
     } else {
-        g.rrn[inst] = s;
-        g.istat[2 * inst + 1] += 1;
-        if (!(s > fmax(tol2, g.cgtol2[inst]) * g.rr0[inst]) || !isfinite(s)) g.cgact[inst] = 0;
+        // mode 3: |du|^2 against |u|^2 after the update: an increment at the rounding level of u converges
+        if (isfinite(s) && s <= tol2 * sz) g.nact[inst] = 0;
     }
 }
 
-// Ap = M p c0 + K p (free dofs); partial p . Ap
+// The last node block of an instance to finish sums the instance's block partials, in the fixed
+// order of k_imp_reduce_b (same arithmetic, so the fused kernels reproduce the separate reductions
+// bit for bit).  Called by every thread of the block; true in thread 0 of the last block, with the sum.
+__device__ __forceinline__ bool last_block_sum(const FomB& g, int inst, double& total) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int t = atomicAdd(g.iticket + inst, 1u);
+        last = t == (unsigned int)(g.nblk_off[inst + 1] - g.nblk_off[inst] - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const int b0 = g.nblk_off[inst], b1 = g.nblk_off[inst + 1];
+    double s = 0.0;
+    for (int b = b0 + (int)threadIdx.x; b < b1; b += blockDim.x) s += __ldcg(g.ipart + b);
+    s = block_sum1(s);
+    if (threadIdx.x != 0) return false;
+    g.iticket[inst] = 0u;
+    total = s;
+    return true;
+}
+
+// Ap = M p c0 + K p (free dofs); p . Ap summed per instance by its last block, which sets
+// alpha = (r . z) / (p . Ap) for the step kernel
 __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int* __restrict__ mask, double c0) {
     const NodeCtx x = node_ctx(g, mask);
     double s = 0.0;
@@ -190,15 +207,22 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int*
     }
     s = block_sum1(s);
     if (threadIdx.x == 0) g.ipart[blockIdx.x] = s;
+    double pap;
+    if (last_block_sum(g, x.inst, pap) && run(mask, x.inst)) {
+        g.pap[x.inst] = pap;
+        g.alpha[x.inst] = pap > 0.0 ? g.rr[x.inst] / pap : 0.0;
+    }
 }
 
-// x += alpha p, r -= alpha Ap with alpha = (r . z) / (p . Ap); partial r . z of the new residual
-__global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const int* __restrict__ mask, double c0) {
+// x += alpha p, r -= alpha Ap; r . z of the new residual summed per instance by its last block, which
+// counts the iteration, ends the instance's CG solve at the forcing tolerance (floor tol2) and sets
+// beta = (r . z)_new / (r . z) and r . z <- (r . z)_new for the direction kernel
+__global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const int* __restrict__ mask, double c0,
+                                                          double tol2) {
     const NodeCtx x = node_ctx(g, mask);
     double s = 0.0;
     if (x.ok) {
-        const double pap = g.pap[x.inst];
-        const double alpha = pap > 0.0 ? g.rr[x.inst] / pap : 0.0;
+        const double alpha = g.alpha[x.inst];
         const double pz = g.minv[x.gn] / c0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -211,26 +235,29 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const in
     }
     s = block_sum1(s);
     if (threadIdx.x == 0) g.ipart[blockIdx.x] = s;
+    double rrn;
+    if (last_block_sum(g, x.inst, rrn) && run(mask, x.inst)) {
+        const int inst = x.inst;
+        g.rrn[inst] = rrn;
+        g.istat[2 * inst + 1] += 1;
+        if (!(rrn > fmax(tol2, g.cgtol2[inst]) * g.rr0[inst]) || !isfinite(rrn)) g.cgact[inst] = 0;
+        const double rr = g.rr[inst];
+        g.beta[inst] = rr > 0.0 ? rrn / rr : 0.0;
+        g.rr[inst] = rrn;
+    }
 }
 
-// p = z + ((r . z)_new / (r . z)) p; the per-instance r . z is advanced by the kernel after it
+// p = z + beta p
 __global__ void __launch_bounds__(kNodeBlock) k_cg_dir_b(const FomB g, const int* __restrict__ mask, double c0) {
     const NodeCtx x = node_ctx(g, mask);
     if (!x.ok) return;
-    const double rr = g.rr[x.inst];
-    const double beta = rr > 0.0 ? g.rrn[x.inst] / rr : 0.0;
+    const double beta = g.beta[x.inst];
     const double pz = g.minv[x.gn] / c0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long d = (long long)c * g.NN + x.gn;
         g.cg_p[d] = fma(beta, g.cg_p[d], g.cg_r[d] * pz);
     }
-}
-
-__global__ void k_cg_rr_b(const FomB g, const int* __restrict__ mask) {
-    const int inst = blockIdx.x * blockDim.x + threadIdx.x;
-    if (inst >= g.n_inst || !run(mask, inst)) return;
-    g.rr[inst] = g.rrn[inst];
 }
 
 // u += x on free dofs, refreshed u / h for the force kernel; partials |x|^2 and |u|^2 (free dofs)
@@ -338,15 +365,12 @@ cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream
     k_cg_ap_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
     return cudaGetLastError();
 }
-cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
-    k_cg_step_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, double tol2, cudaStream_t s) {
+    k_cg_step_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0, tol2);
     return cudaGetLastError();
 }
 cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
     k_cg_dir_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_cg_rr_b<<<(g.n_inst + 127) / 128, 128, 0, s>>>(g, mask);
     return cudaGetLastError();
 }
 cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s) {

@@ -364,9 +364,7 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
                     else LK(launch_tangent_b(g, g.cgact, ctx->stream));
                     ctx->prof_end(pk, 0);
                     LK(launch_cg_ap_b(g, g.cgact, c0, ctx->stream));
-                    LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, ctx->stream));
-                    LK(launch_cg_step_b(g, g.cgact, c0, ctx->stream));
-                    LK(launch_imp_reduce_b(g, g.cgact, 2, 0, kCgTol2, ctx->stream));
+                    LK(launch_cg_step_b(g, g.cgact, c0, kCgTol2, ctx->stream));
                     LK(launch_cg_dir_b(g, g.cgact, c0, ctx->stream));
                 }
                 bool cg = false;
@@ -454,9 +452,7 @@ int enqueue_implicit_captured(osam_ctx* ctx, int s, const int* active) {
                     if (g.lin) LK(launch_tangent_lin_b(g, g.cgact, b));
                     else LK(launch_tangent_b(g, g.cgact, b));
                     LK(launch_cg_ap_b(g, g.cgact, c0, b));
-                    LK(launch_imp_reduce_b(g, g.cgact, 1, 0, 0.0, b));
-                    LK(launch_cg_step_b(g, g.cgact, c0, b));
-                    LK(launch_imp_reduce_b(g, g.cgact, 2, 0, kCgTol2, b));
+                    LK(launch_cg_step_b(g, g.cgact, c0, kCgTol2, b));
                     LK(launch_cg_dir_b(g, g.cgact, c0, b));
                     LK(launch_imp_loop_cond(g, hc, 1, kCgMax, b));
                     return OSAM_OK;
@@ -927,7 +923,10 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CKA(B.cg_r = ctx->alloc<double>(3 * NN));
         CKA(B.cg_p = ctx->alloc<double>(3 * NN));
         CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
-        for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap, &B.cgtol2}) CKA(*p = ctx->alloc<double>(n));
+        for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap, &B.cgtol2, &B.alpha, &B.beta})
+            CKA(*p = ctx->alloc<double>(n));
+        CKA(B.iticket = ctx->alloc<unsigned int>(n));
+        CK(cudaMemsetAsync(B.iticket, 0, sizeof(unsigned int) * n, ctx->stream));
         CKA(B.istat = ctx->alloc<long long>(2 * n));
         CKA(B.iloop = ctx->alloc<int>(2));
         if (B.material == OSAM_NEO_HOOKEAN) CKA(B.lin = ctx->alloc<double>((long long)kLinPerGp * 8 * NE));

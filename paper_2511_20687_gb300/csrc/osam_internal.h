@@ -110,6 +110,9 @@ struct FomB {
     double* pap;              // per instance: p . A p
     double* cgtol2;           // per instance: squared relative CG tolerance of the current Newton step
     int* iloop;               // device-side loop counters: [0] Newton steps, [1] CG iterations
+    unsigned int* iticket;    // per instance: last-block ticket of the fused CG reductions
+    double* alpha;            // per instance: CG step length of the current iteration
+    double* beta;             // per instance: CG direction update of the current iteration
     int* nact;                // per instance Newton state: 1 iterating, 0 converged, 2 failed
     int* cgact;               // per instance: CG still iterating
     long long* istat;         // per instance: Newton linear solves, CG iterations (since the last reset)
@@ -241,9 +244,9 @@ cudaError_t launch_controller(const CtlB& c, cudaGraphConditionalHandle h, int u
 cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, double dt, cudaStream_t s);
 cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 // reduce the node-block partials per instance; mode 0: Newton residual (sets rn2, r0 on the first
-// iteration (first < 0: the device-side Newton counter decides), rr, rr0, nact, cgact), 1: p . Ap,
-// 2: r . z after a CG update (sets rrn, cgact),
-// 3: |du|^2 <= tol2 |u|^2 after a Newton update (clears nact)
+// iteration (first < 0: the device-side Newton counter decides), rr, rr0, nact, cgact and the CG
+// forcing tolerance), 3: |du|^2 <= tol2 |u|^2 after a Newton update (clears nact).  The CG inner
+// products are reduced inside k_cg_ap_b / k_cg_step_b by each instance's last block.
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s);
 cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
 // Neo-Hookean implicit groups: Newton force that also stores the Gauss-point linearisation, and the
@@ -251,7 +254,7 @@ cudaError_t launch_tangent_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_force_lin_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_tangent_lin_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
-cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
+cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, double tol2, cudaStream_t s);
 cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s);
 cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s);
 cudaError_t launch_imp_finish_b(const FomB& g, const int* active, int slot1, double dt, double c0, cudaStream_t s);
