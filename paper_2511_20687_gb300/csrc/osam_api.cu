@@ -282,9 +282,10 @@ int osam_instance_get_state(osam_ctx* ctx, int inst, int sub, double* u, double*
             CK(launch_rom_full_field(nn, I.r, G.Phi[inst], G.dof_free[inst], G.clamp_d[inst], G.srow_d[inst], hs,
                                      G.d.q + I.q_off + (long long)f * I.r, ctx->scratch, ctx->stream));
         }
+        // stream order lets the next field reuse the staging buffer; one host synchronisation at the end
         CK(cudaMemcpyAsync(outs[f], ctx->scratch, sizeof(double) * 3 * nn, cudaMemcpyDefault, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
     }
+    CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }
 
@@ -298,13 +299,13 @@ int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, c
     if (S.kind == OSAM_FOM) {
         FomB& g = S.fom.d;
         const InstFom& I = S.fom.inst[inst];
+        // the staging buffer is reused in stream order; the caller's buffers are released by the final
+        // synchronisation
         RET(upload(ctx, ctx->scratch, u, sizeof(double) * 3 * I.nn));
         CK(launch_aos_to_soa(ctx->scratch, g.u[0] + I.node_off, I.nn, g.NN, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
         if (v) {
             RET(upload(ctx, ctx->scratch, v, sizeof(double) * 3 * I.nn));
             CK(launch_aos_to_soa(ctx->scratch, g.v + I.node_off, I.nn, g.NN, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
         } else {
             for (int c = 0; c < 3; ++c)
                 CK(cudaMemsetAsync(g.v + c * g.NN + I.node_off, 0, sizeof(double) * I.nn, ctx->stream));
