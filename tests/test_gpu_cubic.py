@@ -156,3 +156,11 @@ def test_cubic_selection_matches_oracle(gpu):
             assert not np.isfinite(eg) or eg >= 1e300
     assert got["best"] == ref_best
     assert "C" in got and got["C"].shape == (4, 20)
+
+
+def test_cubic_rom_with_its_own_time_step(gpu, svk_cubic_ops):
+    """FOM-COpInf with the cubic ROM taking half as many substeps (twice the step) as the SVK FOM:
+    the ROM's boundary data pass through the temporal interpolant, its trace back to the FOM too."""
+    spec = W.bar_chain("svkm", 3, [6, 6], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 2e-3, 1e-6, 4, max_iters=12)
+    spec.subdomains[1].n_substeps = 2
+    _compare(spec, 3, {1: svk_cubic_ops[1]})

@@ -43,7 +43,7 @@ def _synthetic_rom(spec, i, r, rs, seed):
     return W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, r, rs, seed)
 
 
-def _compare(spec, n_ctrl, rom_ops=None, tol=1e-9, **kw):
+def _compare(spec, n_ctrl, rom_ops=None, tol=1e-9, its_slack=1, **kw):
     gpu = osam.Problem(spec, rom_ops=rom_ops, **kw)
     ref = O.Problem(spec, rom_ops=rom_ops)
     n_sd = len(spec.subdomains)
@@ -52,7 +52,7 @@ def _compare(spec, n_ctrl, rom_ops=None, tol=1e-9, **kw):
     for _ in range(n_ctrl):
         rg, rr = gpu.step(), ref.step()
         assert rg["status"] in (osam.OK, osam.MAXITER) and rr["status"] in (O.OK, O.MAXITER)
-        assert abs(rg["iterations"] - rr["iterations"]) <= 1
+        assert its_slack is None or abs(rg["iterations"] - rr["iterations"]) <= its_slack
         for i, sd in enumerate(spec.subdomains):
             if sd.kind == "fom":
                 hg[i].append(np.concatenate([f.reshape(-1) for f in gpu.state(i)]))
@@ -204,3 +204,29 @@ def test_wave1d_stepper_matrix_matches_dalembert(gpu, steppers, counts):
         den += np.sum(ex ** 2)
     prob.close()
     assert np.sqrt(num / den) < 5e-3
+
+
+@pytest.mark.parametrize("precision,tol,slack", [(osam.F32X2_FORCE, 1e-9, 1), (osam.FP32_FORCE, 1e-5, None)])
+def test_mixed_steps_with_reduced_force_precision(gpu, precision, tol, slack):
+    """The double-float and FP32 force paths under different substep counts (their node kernels take
+    the per-subdomain time steps and history levels). FP32 force rounding sits above the Schwarz
+    tolerance, so that run may stop on the iteration cap: its iteration count is not compared."""
+    spec = _setup(W.bar_chain("mxp", 4, [8, 7], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 1e-6, 6,
+                              max_iters=8), (6, 4))
+    _compare(spec, 3, tol=tol, its_slack=slack, precision=precision)
+
+
+def test_additive_with_mixed_steps_graph_equals_host(gpu):
+    spec = _setup(W.bar_chain("mxa", 3, [6, 6, 6], ["fom", "rom", "fom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 6,
+                              max_iters=8), (6, 4, 3))
+    spec.schwarz = "additive"
+    from .test_gpu_additive import _rom_ops
+    ops = {1: _rom_ops(spec, 1, 5, 4, 9)}
+    _compare(spec, 2, rom_ops=ops)
+    a = osam.Problem(spec, rom_ops=ops, scatter=osam.SCATTER_GATHER, graph=True)
+    b = osam.Problem(spec, rom_ops=ops, scatter=osam.SCATTER_GATHER, graph=False)
+    for _ in range(2):
+        assert a.step()["iterations"] == b.step()["iterations"]
+    for i in (0, 2):
+        assert np.array_equal(a.state(i)[0], b.state(i)[0])
+    assert np.array_equal(a.reduced_state(1)[0], b.reduced_state(1)[0])
