@@ -55,14 +55,14 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "527d0af58909dbf621ae4e71b9915f9b2e4dd69db3ed81e4d8366e9d0639aba0", "bytes_per_launch": 3.573e6,
+FORCE_TRAFFIC = {"source_sha256": "b5b3fee699d80ead49f9c330a5c1956a2516f6f06efc65685b9ceb2d9d109b2d", "bytes_per_launch": 3.56992e6,
                  "tiled": True}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
 TANGENT_BYTES_PER_ELEMENT = 22 * 8 * 8 + 24
-TANGENT_TRAFFIC = {"source_sha256": "c880ed687a427bdd598d39c0ac1e3688caa02ed0ebdb8fd6d89e623ed8606ed4",
-                   "bytes_per_launch": 1.96896e8}
+TANGENT_TRAFFIC = {"source_sha256": "e57ddf845a4e93890393885ca4f7b13edf7edc3f7241c56e37fbac8521fc4a41",
+                   "bytes_per_launch": 1.93736e8}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -585,7 +585,8 @@ def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5,
         "value": upd / (ms * 1e-3), "ms_per_step": ms / n, "mean_iterations": float(np.mean(its)),
         "intervals_per_s": n / (ms * 1e-3),
         "workload": "headline hybrid, FOM implicit (Newmark 1/4, 1/2) with 2 substeps of 10 us, ROM explicit with "
-                    "20 substeps of 1 us, temporal interpolant between them (host-driven steps)"}
+                    "20 substeps of 1 us, temporal interpolant between them (each controller step one graph launch, "
+                    "Newton and CG as device-side loops)"}
     svk_ops, svk_fit = train_rom(W, osam, args, local, log, material="svk", rank=20, cubic=True, snapshots=300)
     spec = W.bar_chain("svk_copinf", args.n, [args.nz, args.nz], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 1e-3,
                        1e-6, 20, max_iters=64)

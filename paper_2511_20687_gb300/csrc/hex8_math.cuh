@@ -10,8 +10,10 @@
 // The Neo-Hookean stress of Appendix A.3, P = F S with
 //   S = 1/2 kappa (det C - 1) C^-1 + mu (det C)^-1/3 (I - 1/3 tr C C^-1),
 // is evaluated through F C^-1 = F^-T = cof(F) / J, i.e.
-//   P = [1/2 kappa (J^2 - 1) - 1/3 mu J^-2/3 tr C] / J * cof(F) + mu J^-2/3 F,
-// with J^-1/3 from a reciprocal cube root, J^-2/3 = (J^-1/3)^2 and 1/J = (J^-1/3)^3 (no division).
+//   P = alpha F + beta cof(F),  alpha = mu J^-2/3,
+//   beta = [1/2 kappa (J^2 - 1) - 1/3 mu J^-2/3 tr C] / J = 1/2 kappa (J - 1/J) - (1/3 mu J^-2/3 / J) tr C,
+// with J^-1/3 from a reciprocal cube root, J^-2/3 = (J^-1/3)^2 and 1/J = (J^-1/3)^3 (no division).  At
+// F = I the volumetric term vanishes exactly (J - 1/J = 0), so the stress there is mu - 3 (mu/3) rounded.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -141,12 +143,11 @@ __device__ __forceinline__ void nh_factors(const T H[3][3], T kap2, T mu, T mu3,
     T trC = F[0][0] * F[0][0];
 #pragma unroll
     for (int k = 1; k < 9; ++k) trC = fmaT(F[k / 3][k % 3], F[k / 3][k % 3], trC);
-    const T J2 = J * J;
     const T s1 = rcbrtT(J);                  // J^-1/3
     const T r3 = s1 * s1;                    // J^-2/3
     const T invJ = r3 * s1;                  // 1/J
     alpha = mu * r3;
-    beta = fmaT(-(mu3 * r3), trC, kap2 * (J2 - T(1))) * invJ;
+    beta = fmaT(-(mu3 * r3) * invJ, trC, kap2 * (J - invJ));
 }
 
 template <typename T>
@@ -159,6 +160,103 @@ __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, 
         for (int j = 0; j < 3; ++j) P[i][j] = fmaT(alpha, F[i][j], beta * C[i][j]);
 }
 
+// Neo-Hookean Gauss-point sums Sx[c][q][r] = sum_p P_c0(p, q, r), Sy[c][p][r] = sum_q P_c1,
+// Sz[c][p][q] = sum_r P_c2 with P = alpha F + beta cof(F).  Column k of F depends on two of the three
+// Gauss indices only (column 0 on q and r, column 1 on p and r, column 2 on p and q), so
+//  - tr C = |F_0|^2 + |F_1|^2 + |F_2|^2 is assembled from squared column norms formed once per pair of
+//    Gauss points that share the column, and
+//  - in each sum the alpha F term of a pair is one product (alpha_a + alpha_b) F_k,
+// which takes ~50 FP64 operations per element off the one-Gauss-point-at-a-time evaluation.
+template <typename T>
+__device__ __forceinline__ void nh_gauss_sums(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
+                                              T kap2, T mu, T mu3, T Sx[3][2][2], T Sy[3][2][2], T Sz[3][2][2]) {
+    T F0[3][2][2], F1[3][2][2], F2[3][2][2];   // columns of F = I + H: F0[c][q][r], F1[c][p][r], F2[c][p][q]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F0[c][a][b] = c == 0 ? T(1) + Gx[c][a][b] : Gx[c][a][b];
+                F1[c][a][b] = c == 1 ? T(1) + Gy[c][a][b] : Gy[c][a][b];
+                F2[c][a][b] = c == 2 ? T(1) + Gz[c][a][b] : Gz[c][a][b];
+            }
+    T n0[2][2];                                // |F_0|^2 at (q, r)
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            n0[q][r] = fmaT(F0[2][q][r], F0[2][q][r], fmaT(F0[1][q][r], F0[1][q][r], F0[0][q][r] * F0[0][q][r]));
+    T ax[2][2];                                // alpha at (0, q, r), waiting for its pair (1, q, r)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        T n1[2], n2[2];                        // |F_1|^2 at (p, r), |F_2|^2 at (p, q)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            n1[a] = fmaT(F1[2][p][a], F1[2][p][a], fmaT(F1[1][p][a], F1[1][p][a], F1[0][p][a] * F1[0][p][a]));
+            n2[a] = fmaT(F2[2][p][a], F2[2][p][a], fmaT(F2[1][p][a], F2[1][p][a], F2[0][p][a] * F2[0][p][a]));
+        }
+        T ay[2];                               // alpha at (p, 0, r)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            T az = T(0);                       // alpha at (p, q, 0)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                T Fm[3][3], Cm[3][3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Fm[c][0] = F0[c][q][r];
+                    Fm[c][1] = F1[c][p][r];
+                    Fm[c][2] = F2[c][p][q];
+                }
+                Cm[0][0] = fmaT(Fm[1][1], Fm[2][2], -Fm[1][2] * Fm[2][1]);
+                Cm[0][1] = fmaT(Fm[1][2], Fm[2][0], -Fm[1][0] * Fm[2][2]);
+                Cm[0][2] = fmaT(Fm[1][0], Fm[2][1], -Fm[1][1] * Fm[2][0]);
+                Cm[1][0] = fmaT(Fm[0][2], Fm[2][1], -Fm[0][1] * Fm[2][2]);
+                Cm[1][1] = fmaT(Fm[0][0], Fm[2][2], -Fm[0][2] * Fm[2][0]);
+                Cm[1][2] = fmaT(Fm[0][1], Fm[2][0], -Fm[0][0] * Fm[2][1]);
+                Cm[2][0] = fmaT(Fm[0][1], Fm[1][2], -Fm[0][2] * Fm[1][1]);
+                Cm[2][1] = fmaT(Fm[0][2], Fm[1][0], -Fm[0][0] * Fm[1][2]);
+                Cm[2][2] = fmaT(Fm[0][0], Fm[1][1], -Fm[0][1] * Fm[1][0]);
+                const T J = fmaT(Fm[0][0], Cm[0][0], fmaT(Fm[0][1], Cm[0][1], Fm[0][2] * Cm[0][2]));
+                const T trC = (n0[q][r] + n1[r]) + n2[q];
+                const T s1 = rcbrtT(J);        // J^-1/3
+                const T r3 = s1 * s1;          // J^-2/3
+                const T invJ = r3 * s1;        // 1/J
+                const T alpha = mu * r3;
+                const T beta = fmaT(-(mu3 * r3) * invJ, trC, kap2 * (J - invJ));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Sx[c][q][r] = p == 0 ? beta * Cm[c][0] : fmaT(beta, Cm[c][0], Sx[c][q][r]);
+                    Sy[c][p][r] = q == 0 ? beta * Cm[c][1] : fmaT(beta, Cm[c][1], Sy[c][p][r]);
+                    Sz[c][p][q] = r == 0 ? beta * Cm[c][2] : fmaT(beta, Cm[c][2], Sz[c][p][q]);
+                }
+                if (p == 0) {
+                    ax[q][r] = alpha;
+                } else {
+                    const T a = ax[q][r] + alpha;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Sx[c][q][r] = fmaT(a, Fm[c][0], Sx[c][q][r]);
+                }
+                if (q == 0) {
+                    ay[r] = alpha;
+                } else {
+                    const T a = ay[r] + alpha;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Sy[c][p][r] = fmaT(a, Fm[c][1], Sy[c][p][r]);
+                }
+                if (r == 0) {
+                    az = alpha;
+                } else {
+                    const T a = az + alpha;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) Sz[c][p][q] = fmaT(a, Fm[c][2], Sz[c][p][q]);
+                }
+            }
+        }
+    }
+}
+
 // Element force from the displacement gradients at the Gauss points:
 //   Gx[c][q][r] = d u_c / dx at (y GP q, z GP r), Gy[c][p][r], Gz[c][p][q].
 // Output F[c][corner], corner = ax + 2 ay + 4 az.
@@ -166,34 +264,22 @@ template <int MAT, typename T>
 __device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
                                                    T m1, T m2, T m3, T F[3][8]) {
     T Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+    if constexpr (MAT == OSAM_NEO_HOOKEAN) {
+        nh_gauss_sums<T>(Gx, Gy, Gz, m1, m2, m3, Sx, Sy, Sz);
+    } else {
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+            for (int q = 0; q < 2; ++q)
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                T Hm[3][3], P[3][3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Hm[c][0] = Gx[c][q][r];
-                    Hm[c][1] = Gy[c][p][r];
-                    Hm[c][2] = Gz[c][p][q];
-                }
-                if (MAT == OSAM_NEO_HOOKEAN) {
-                    // P = alpha F + beta cof(F), folded into the Gauss-point sums: the second Gauss
-                    // point of a pair adds with two fused multiply-adds instead of mul + fma + add
-                    T Fm[3][3], Cm[3][3], alpha, beta;
-                    nh_factors<T>(Hm, m1, m2, m3, Fm, Cm, alpha, beta);
+                for (int r = 0; r < 2; ++r) {
+                    T Hm[3][3], P[3][3];
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        Sx[c][q][r] = p == 0 ? fmaT(alpha, Fm[c][0], beta * Cm[c][0])
-                                             : fmaT(alpha, Fm[c][0], fmaT(beta, Cm[c][0], Sx[c][q][r]));
-                        Sy[c][p][r] = q == 0 ? fmaT(alpha, Fm[c][1], beta * Cm[c][1])
-                                             : fmaT(alpha, Fm[c][1], fmaT(beta, Cm[c][1], Sy[c][p][r]));
-                        Sz[c][p][q] = r == 0 ? fmaT(alpha, Fm[c][2], beta * Cm[c][2])
-                                             : fmaT(alpha, Fm[c][2], fmaT(beta, Cm[c][2], Sz[c][p][q]));
+                        Hm[c][0] = Gx[c][q][r];
+                        Hm[c][1] = Gy[c][p][r];
+                        Hm[c][2] = Gz[c][p][q];
                     }
-                } else {
                     if (MAT == OSAM_SAINT_VENANT_KIRCHHOFF) stress_svk<T>(Hm, m1, m2, P);
                     else stress_le<T>(Hm, m1, m2, P);
 #pragma unroll
@@ -203,7 +289,7 @@ __device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T 
                         if (r == 0) Sz[c][p][q] = P[c][2]; else Sz[c][p][q] += P[c][2];
                     }
                 }
-            }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T Tm[2][2];
