@@ -3,6 +3,7 @@
 // products of the offline fit.  The per-step ROM kernels are in step_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "osam_internal.h"
@@ -76,26 +77,35 @@ __global__ void k_build_Rt(int nrow, int r, const int* dnode, const double* dw, 
     Rt[(long long)k * 3 * nrow + col] = acc;
 }
 
-// generic FP64 GEMM C(i,j) = alpha sum_k A(i,k) B(k,j) + beta C(i,j) with element strides
+// generic FP64 GEMM C(i,j) = alpha sum_k A(i,k) B(k,j) + beta C(i,j) with element strides.
+// The tile loaders walk the operand along its contiguous index (k for a row-major A, i for a
+// transposed one; likewise j or k for B), so every warp reads whole 128-byte lines.  With split-K
+// (gridDim.z > 1) block z sums k in [z kchunk, (z + 1) kchunk) and stores its partial tile into
+// ws[z][m][n]; k_gemm_reduce then adds the partials in ascending z (deterministic) and applies
+// alpha and beta.
 constexpr int TM = 64, TN = 64, TK = 16;
-__global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, const double* A, long long ai, long long ak,
-                                              const double* B, long long bk, long long bj, double* C, long long ldc,
-                                              double alpha, double beta) {
+__global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, int kchunk, const double* A, long long ai,
+                                              long long ak, const double* B, long long bk, long long bj, double* C,
+                                              long long ldc, double alpha, double beta, double* ws) {
     __shared__ double As[TK][TM + 1];
     __shared__ double Bs[TK][TN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(kdim, kbeg + kchunk);
+    const bool a_along_i = ai == 1 && ak != 1;   // A stored [k][m]
+    const bool b_along_j = bj == 1;              // B stored [k][n]
     double acc[4][4] = {{0}};
-    for (int k0 = 0; k0 < kdim; k0 += TK) {
+    for (int k0 = kbeg; k0 < kend; k0 += TK) {
         for (int t = threadIdx.x; t < TK * TM; t += 256) {
-            const int kk = t % TK, ii = t / TK;
+            const int kk = a_along_i ? t / TM : t % TK, ii = a_along_i ? t % TM : t / TK;
             const int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < m && gk < kdim) ? A[gi * ai + gk * ak] : 0.0;
+            As[kk][ii] = (gi < m && gk < kend) ? A[gi * ai + gk * ak] : 0.0;
         }
         for (int t = threadIdx.x; t < TK * TN; t += 256) {
-            const int jj = t % TN, kk = t / TN;
+            const int jj = b_along_j ? t % TN : t / TK, kk = b_along_j ? t / TN : t % TK;
             const int gj = j0 + jj, gk = k0 + kk;
-            Bs[kk][jj] = (gj < n && gk < kdim) ? B[gk * bk + gj * bj] : 0.0;
+            Bs[kk][jj] = (gj < n && gk < kend) ? B[gk * bk + gj * bj] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -110,16 +120,69 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, const doub
         }
         __syncthreads();
     }
+    double* W = ws ? ws + (long long)blockIdx.z * m * n : nullptr;
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
             const int gi = i0 + ty * 4 + x, gj = j0 + tx * 4 + y;
             if (gi < m && gj < n) {
-                double* cp = C + gi * ldc + gj;
-                *cp = alpha * acc[x][y] + (beta != 0.0 ? beta * *cp : 0.0);
+                if (W) {
+                    W[(long long)gi * n + gj] = acc[x][y];
+                } else {
+                    double* cp = C + gi * ldc + gj;
+                    *cp = alpha * acc[x][y] + (beta != 0.0 ? beta * *cp : 0.0);
+                }
             }
         }
+}
+
+__global__ void k_gemm_reduce(int m, int n, int nsplit, const double* __restrict__ ws, double* C, long long ldc,
+                              double alpha, double beta) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mn = (long long)m * n;
+    if (idx >= mn) return;
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += ws[z * mn + idx];
+    double* cp = C + (idx / n) * ldc + idx % n;
+    *cp = alpha * s + (beta != 0.0 ? beta * *cp : 0.0);
+}
+
+// Split the reduction when the output tiles alone cannot fill the GPU (two blocks per SM wanted)
+// and the reduction is long: chunks of at least 512 k, a multiple of the k tile.
+cudaError_t launch_gemm(int m, int n, int k, const double* A, long long ai, long long ak, const double* B,
+                        long long bk, long long bj, double* C, long long ldc, double alpha, double beta,
+                        cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const long long tiles = (long long)grid_for(n, TN) * grid_for(m, TM);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = 2LL * sms;
+    int nsplit = 1;
+    if (tiles < want && k >= 2 * 512)
+        nsplit = (int)std::min<long long>((want + tiles - 1) / tiles, k / 512);
+    int kchunk = k;
+    if (nsplit > 1) {
+        kchunk = (k + nsplit - 1) / nsplit;
+        kchunk = (kchunk + TK - 1) / TK * TK;
+        nsplit = (k + kchunk - 1) / kchunk;
+    }
+    dim3 g(grid_for(n, TN), grid_for(m, TM), nsplit);
+    if (nsplit == 1) {
+        k_gemm<<<g, 256, 0, s>>>(m, n, k, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, nullptr);
+        return cudaGetLastError();
+    }
+    double* ws = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), sizeof(double) * (size_t)nsplit * m * n, s);
+    if (e != cudaSuccess) return e;
+    k_gemm<<<g, 256, 0, s>>>(m, n, k, kchunk, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, ws);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        k_gemm_reduce<<<grid_for((long long)m * n, 256), 256, 0, s>>>(m, n, nsplit, ws, C, ldc, alpha, beta);
+        e = cudaGetLastError();
+    }
+    cudaError_t f = cudaFreeAsync(ws, s);
+    return e != cudaSuccess ? e : f;
 }
 
 // compressed Kronecker features: D[s][col0 + idx(i,j)] = Ubar[i][s] * Ubar[j][s] (i <= j)
@@ -276,25 +339,19 @@ cudaError_t launch_build_Rt(int nrow, int r, const int* dnode_local, const doubl
 // row-major helpers: C[m][n] (ldc) = alpha * A^T B, A is [k][m] (lda), B is [k][n] (ldb)
 cudaError_t launch_gemm_tn(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                            double alpha, double beta, cudaStream_t s) {
-    dim3 g(grid_for(n, TN), grid_for(m, TM));
-    k_gemm<<<g, 256, 0, s>>>(m, n, k, A, 1, lda, B, ldb, 1, C, ldc, alpha, beta);
-    return cudaGetLastError();
+    return launch_gemm(m, n, k, A, 1, lda, B, ldb, 1, C, ldc, alpha, beta, s);
 }
 
 // C[m][n] = alpha * A B, A is [m][k] (lda), B is [k][n] (ldb)
 cudaError_t launch_gemm_nn(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                            double alpha, double beta, cudaStream_t s) {
-    dim3 g(grid_for(n, TN), grid_for(m, TM));
-    k_gemm<<<g, 256, 0, s>>>(m, n, k, A, lda, 1, B, ldb, 1, C, ldc, alpha, beta);
-    return cudaGetLastError();
+    return launch_gemm(m, n, k, A, lda, 1, B, ldb, 1, C, ldc, alpha, beta, s);
 }
 
 // C[m][n] = alpha * A B^T, A is [m][k] (lda), B is [n][k] (ldb)
 cudaError_t launch_gemm_nt(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                            double alpha, double beta, cudaStream_t s) {
-    dim3 g(grid_for(n, TN), grid_for(m, TM));
-    k_gemm<<<g, 256, 0, s>>>(m, n, k, A, lda, 1, B, 1, ldb, C, ldc, alpha, beta);
-    return cudaGetLastError();
+    return launch_gemm(m, n, k, A, lda, 1, B, 1, ldb, C, ldc, alpha, beta, s);
 }
 
 cudaError_t launch_kron_features(const double* Ubar, int r, int nsnap, double* D, int ldd, int col0, cudaStream_t s) {
