@@ -370,11 +370,10 @@ def test_non_finite_state_is_reported(torch_cuda, rom):
 # ---------------------------------------------------------------------------------------------
 # offline fit and adjoint
 # ---------------------------------------------------------------------------------------------
-def test_opinf_fit_matches_oracle_fit(torch_cuda):
-    """Same snapshots: bases agree up to column signs, singular values and fitted operators (after
-    aligning signs) agree; full-space predicted accelerations agree."""
-    rng = np.random.default_rng(21)
-    n, ns, nsd, r, rs = 900, 60, 45, 5, 3
+def _fit_case(n, ns, nsd, seed):
+    """Snapshots of a known quadratic model (r = 5, r_s = 3) in random orthonormal bases, with noise."""
+    rng = np.random.default_rng(seed)
+    r, rs = 5, 3
     Q = np.diag([6.0, 4.5, 3.0, 2.0, 1.0]) @ rng.standard_normal((r, ns))
     Phi_t, _ = np.linalg.qr(rng.standard_normal((n, r)))
     PhiS_t, _ = np.linalg.qr(rng.standard_normal((nsd, rs)))
@@ -387,6 +386,10 @@ def test_opinf_fit_matches_oracle_fit(torch_cuda):
     U = (Phi_t @ Q).T + 1e-3 * rng.standard_normal((ns, n))
     A = (Phi_t @ Qdd).T
     S = (PhiS_t @ G).T + 1e-3 * rng.standard_normal((ns, nsd))
+    return U, A, S, r, rs, rng
+
+
+def _check_fit(U, A, S, r, rs, rng):
     ref = OF.opinf_fit(U.T, A.T, S.T, r=r, lam=1e-6, r_s=rs)
     got = osam.opinf_fit(U, A, S, r=r, lam=1e-6, r_s=rs)
     assert got["r_s"] == rs
@@ -405,6 +408,20 @@ def test_opinf_fit_matches_oracle_fit(torch_cuda):
         qg, gg = sg * qs[:, k], ss * gs[:, k]
         have = got["Phi"] @ OF.rom_rhs(got["K"], got["H"], got["B"], got["c"], qg, gg)
         assert np.linalg.norm(have - want) < 1e-7 * np.linalg.norm(want)
+
+
+def test_opinf_fit_matches_oracle_fit(torch_cuda):
+    """Same snapshots: bases agree up to column signs, singular values and fitted operators (after
+    aligning signs) agree; full-space predicted accelerations agree."""
+    _check_fit(*_fit_case(900, 60, 45, 21))
+
+
+def test_opinf_fit_long_reductions_match_oracle_fit(torch_cuda):
+    """40,000 dofs and 3,000 Schwarz dofs against 60 snapshots: the Gram, Phi^T Phi, the projections
+    and the boundary projection reduce over thousands of entries into outputs of one tile or less, so
+    the GEMM splits the reduction (76 chunks of 528 and a ragged last chunk of 400 for the dof sums)
+    and sums the partials in a second kernel; the transposed-operand loaders serve Phi = U^T W."""
+    _check_fit(*_fit_case(40000, 60, 3000, 22))
 
 
 def test_adjoint_matches_oracle_and_fd(torch_cuda):
