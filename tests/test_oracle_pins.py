@@ -523,8 +523,12 @@ def _translating_pair(material, n_sub, integrators):
 
 @pytest.mark.parametrize("n_sub", [(6, 6), (6, 4), (5, 3), (3, 7)])
 @pytest.mark.parametrize("integrators", [("explicit", "explicit"), ("explicit", "implicit")])
-def test_mixed_time_steps_keep_rigid_translation_exact(oracle, n_sub, integrators):
+@pytest.mark.parametrize("schwarz", ["multiplicative", "additive"])
+def test_mixed_time_steps_keep_rigid_translation_exact(oracle, n_sub, integrators, schwarz):
+    """Rigid motion at constant velocity is an exact solution of every integrator and of the
+    temporal interpolant (linear in time), under either sweep order."""
     p, V = _translating_pair("nh", n_sub, integrators)
+    p.schwarz = schwarz
     prob = oracle.Problem(p)
     t = 0.0
     for _ in range(3):
