@@ -145,25 +145,32 @@ def test_rollout_adjoint_matches_central_differences(oracle, small_adjoint_case)
 # ---------------------------------------------------------------------------------------------
 # regularisation selection (Algorithm 3)
 # ---------------------------------------------------------------------------------------------
-def _known_quadratic_trajectory(n=5, n_g=2, steps=400, dt=0.02, seed=3, k=1):
-    """Trajectory of q'' = K q + H kron_c(q) + B g(t) + c by explicit central differences with step dt,
-    recorded every k steps; g(t) smooth.  Returns snapshots (U, A, S, v0) and the step."""
+def _known_quadratic_trajectory(n=5, n_g=2, steps=400, dt=0.02, seed=3, k=1, cubic=0.0):
+    """Trajectory of q'' = K q + H kron_c(q) (+ C kron3_c(q)) + B g(t) + c by explicit central
+    differences with step dt, recorded every k steps; g(t) smooth; C of scale `cubic` (0: none).
+    Returns snapshots (U, A, S, v0) and the step."""
     rng = np.random.default_rng(seed)
     K = -np.diag(rng.uniform(1.0, 4.0, n) ** 2)
     H = 0.05 * rng.standard_normal((n, n * (n + 1) // 2))
     B = rng.standard_normal((n, n_g))
     c = 0.1 * rng.standard_normal(n)
+    Cc = None
+    if cubic:   # restoring (Duffing) terms -cubic q_i^3 plus a small random part of the cube
+        trip = [(i, j, l) for i in range(n) for j in range(i, n) for l in range(j, n)]
+        Cc = 0.02 * cubic * rng.standard_normal((n, len(trip)))
+        for i in range(n):
+            Cc[i, trip.index((i, i, i))] -= cubic
     g = lambda t: np.array([np.sin(1.3 * t), np.cos(0.7 * t)])[:n_g]
     q = 0.1 * rng.standard_normal(n)
     qd = 0.1 * rng.standard_normal(n)
-    qdd = OF.rom_rhs(K, H, B, c, q, g(0.0))
+    qdd = OF.rom_rhs(K, H, B, c, q, g(0.0), Cc)
     U, A, S, V = [q.copy()], [qdd.copy()], [g(0.0)], [qd.copy()]
     t = 0.0
     for j in range(steps):
         for _ in range(k):
             t += dt
             q = q + dt * qd + 0.5 * dt * dt * qdd
-            qn = OF.rom_rhs(K, H, B, c, q, g(t))
+            qn = OF.rom_rhs(K, H, B, c, q, g(t), Cc)
             qd = qd + 0.5 * dt * (qdd + qn)
             qdd = qn
         U.append(q.copy()); A.append(qdd.copy()); S.append(g(t)); V.append(qd.copy())
@@ -180,6 +187,21 @@ def test_selection_recovers_the_generating_model():
     assert errs[0] < 1e-6 and errs[best] < 1e-6
     assert errs[-1] > 1e-3
     assert lams[best] <= 1e-4
+
+
+CUBIC_SCALE = 20.0
+
+
+def test_cubic_selection_recovers_a_cubic_model_that_the_quadratic_one_misses():
+    """Noise-free data of a model with a cubic term: cubic candidates at small lambda reproduce the
+    trajectory; the best quadratic candidate, which has no C block, stays orders of magnitude worse."""
+    U, A, S, v0 = _known_quadratic_trajectory(cubic=CUBIC_SCALE, seed=4)
+    lams = OF.lambda_grid()
+    errs_c, best_c, ops = OF.select_lambda(U, A, S, v0, r=5, lambdas=lams, dt=0.02, k=1, r_s=2, cubic=True)
+    errs_q, best_q, _ = OF.select_lambda(U, A, S, v0, r=5, lambdas=lams, dt=0.02, k=1, r_s=2)
+    assert errs_c[0] < 1e-6 and errs_c[best_c] < 1e-6 and lams[best_c] <= 1e-4
+    assert ops["C"].shape == (5, 35)
+    assert errs_q[best_q] > 1e3 * errs_c[best_c]
 
 
 def test_selection_rollout_interpolates_the_boundary_between_snapshots():
