@@ -286,6 +286,31 @@ def test_set_state_roundtrip(torch_cuda):
     assert np.array_equal(u3[~clamped], u2[~clamped]) and np.all(u3[clamped] == 0)
 
 
+@pytest.mark.parametrize("graph", [True, False])
+def test_single_iteration_cap_matches_oracle(torch_cuda, graph):
+    """max_iters = 1: the criterion needs two iterates, so every controller step commits after one
+    sweep with MAXITER, on both sides (graph-captured and host-driven)."""
+    spec = W.fom_fom_plain()
+    spec.max_iters = 1
+    hist, its, _, _ = _run_pair(spec, 3, graph=graph)
+    assert all(a == 1 and b == 1 for a, b in its)
+    for i in range(2):
+        assert rel_l2(*hist[i]) < 1e-9
+
+
+def test_empty_mesh_is_rejected(torch_cuda):
+    torch = torch_cuda
+    u = torch.zeros((16, 3), dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(u)
+    for dims in ((0, 3, 3), (3, 0, 3), (3, 3, 0)):
+        with pytest.raises(osam.OsamError) as ei:
+            osam.hex8_force(dims, 0.01, "nh", LAM, MU, u, f)
+        assert ei.value.code == osam.EINVAL
+        with pytest.raises(osam.OsamError) as ei:
+            osam.hex8_force_vjp(dims, 0.01, "nh", LAM, MU, u, u, f)
+        assert ei.value.code == osam.EINVAL
+
+
 def test_donor_failure_is_reported(torch_cuda):
     spec = W.fom_fom_plain()
     # move subdomain 1 away so its Schwarz nodes fall outside subdomain 0
@@ -446,6 +471,23 @@ def test_adjoint_matches_oracle_and_fd(torch_cuda):
 
     fd = (J_of(sd.lam_e + hl * dl) - J_of(sd.lam_e - hl * dl)) / (2 * hl)
     assert abs(fd - got["grad_lambda"] @ dl) < 1e-6 * abs(fd)
+
+
+def test_adjoint_with_no_steps_is_the_identity(torch_cuda):
+    """T = 0: J = w . u0 over the free dofs, dJ/du0 = w there and zero at clamped dofs, every other
+    gradient zero -- GPU and oracle alike."""
+    p, w = W.adjoint_bar(n=3, nz=4, n_steps=0)
+    sd = p.subdomains[0]
+    got = osam.adjoint(sd.dims, sd.h, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0, None, p.dt, 0, w)
+    J, gu, gv, gl, gm = O.adjoint(sd.dims, sd.h, sd.origin, "nh", sd.lam_e, sd.mu_e, sd.rho, sd.dirichlet, sd.u0,
+                                  None, p.dt, 0, w)
+    wm = np.array(w, dtype=np.float64).reshape(-1, 3)
+    wm[sd.dirichlet.astype(bool)] = 0.0
+    assert abs(got["J"] - J) <= 1e-14 * abs(J)
+    assert np.abs(got["grad_u0"].reshape(-1) - wm.reshape(-1)).max() <= 1e-15 * np.abs(wm).max()
+    assert np.abs(gu - wm.reshape(-1)).max() == 0.0
+    for a in (got["grad_v0"], got["grad_lambda"], got["grad_mu"], gv, gl, gm):
+        assert np.abs(a).max() == 0.0
 
 
 def test_profile_counters(torch_cuda):
