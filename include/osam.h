@@ -100,7 +100,8 @@ typedef struct {
     const double* u0;         /* initial displacement [nodes][3] (required) */
     const double* v0;         /* initial velocity [nodes][3] or NULL (zero) */
     /* ROM operators (kind == OSAM_ROM), all row-major float64 */
-    int r, r_s;               /* reduced dimension and boundary reduced dimension */
+    int r, r_s;               /* reduced dimension (1..256; 1..128 with a cubic operator C) and boundary
+                               * reduced dimension (>= 0; 0 = no boundary input); else OSAM_EINVAL */
     const double* Phi;        /* [n_free][r] orthonormal POD basis */
     const double* Phi_S;      /* [3*n_schwarz_nodes][r_s] boundary POD basis */
     const double* K;          /* [r][r] */

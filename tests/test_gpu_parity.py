@@ -237,6 +237,35 @@ def test_fitted_rom_hybrid_matches_oracle(torch_cuda, fitted_hybrid):
     assert all(abs(a - b) <= 1 for a, b in its)
 
 
+@pytest.mark.parametrize("r,r_s", [(1, 1), (128, 64), (256, 64)])
+def test_rom_rank_extremes_match_oracle(torch_cuda, r, r_s):
+    """FOM-ROM with the smallest ROM rank, the large chain's r = 128 and the largest rank the ROM
+    kernels take (256; H has 32,896 columns), seeded stand-in operators on a 6x6x8 + 6x6x8 bar."""
+    from .test_gpu_additive import _rom_ops
+    spec = W.bar_chain("rk", 6, [8, 8], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10, max_iters=8)
+    ops = {1: _rom_ops(spec, 1, r, r_s, 11)}
+    gpu = osam.Problem(spec, rom_ops=ops)
+    ref = O.Problem(spec, rom_ops=ops)
+    hu, hq = ([], []), ([], [])
+    for _ in range(2):
+        rg, rr = gpu.step(), ref.step()
+        assert rg["status"] == osam.OK and rr["status"] == O.OK
+        assert abs(rg["iterations"] - rr["iterations"]) <= 1
+        hu[0].append(gpu.state(0)[0].copy()); hu[1].append(ref.state(0)[0].copy())
+        hq[0].append(gpu.reduced_state(1)[0].copy()); hq[1].append(ref.rom_state(1)[0].copy())
+    gpu.close()
+    assert rel_l2(*hu) < 1e-9
+    assert rel_l2(*hq) < 1e-9
+
+
+def test_rom_rank_above_the_kernel_limit_is_rejected(torch_cuda):
+    from .test_gpu_additive import _rom_ops
+    spec = W.bar_chain("rk", 6, [8, 8], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10, max_iters=8)
+    with pytest.raises(osam.OsamError) as ei:
+        osam.Problem(spec, rom_ops={1: _rom_ops(spec, 1, 257, 4, 11)})
+    assert ei.value.code == osam.EINVAL
+
+
 def test_three_subdomain_chain_fom_rom_fom(torch_cuda):
     pf = W.bar_chain("c", 2, [4, 4, 4], ["fom", "fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
     pr = W.bar_chain("c", 2, [4, 4, 4], ["fom", "rom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
