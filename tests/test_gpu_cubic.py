@@ -164,3 +164,21 @@ def test_cubic_rom_with_its_own_time_step(gpu, svk_cubic_ops):
     spec = W.bar_chain("svkm", 3, [6, 6], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 2e-3, 1e-6, 4, max_iters=12)
     spec.subdomains[1].n_substeps = 2
     _compare(spec, 3, {1: svk_cubic_ops[1]})
+
+
+def test_cubic_rom_at_the_maximum_rank(gpu):
+    """COpInf at r = 128, the largest cubic rank the library takes (C has 357,760 columns, 366 MB):
+    seeded stand-in operators with a cubic part that moves the reduced state by ~1e-5 relative,
+    four orders of magnitude above the parity bar, coupled to an SVK FOM; r = 129 is rejected."""
+    from .test_gpu_additive import _rom_ops
+    r, rs = 128, 16
+    spec = W.bar_chain("c128", 6, [8, 8], ["fom", "rom"], "svk", 1e9, 0.3, 1000.0, 1e-3, 1e-6, 10, max_iters=8)
+    ops = _rom_ops(spec, 1, r, rs, 12)
+    nc = r * (r + 1) * (r + 2) // 6
+    ops["C"] = 1e12 * np.random.default_rng(13).standard_normal((r, nc)) / np.sqrt(nc)
+    _compare(spec, 2, {1: ops})
+    big = _rom_ops(spec, 1, r + 1, rs, 12)
+    big["C"] = np.zeros((r + 1, (r + 1) * (r + 2) * (r + 3) // 6))
+    with pytest.raises(osam.OsamError) as ei:
+        osam.Problem(spec, rom_ops={1: big})
+    assert ei.value.code == osam.EINVAL
