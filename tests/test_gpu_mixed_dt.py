@@ -230,3 +230,11 @@ def test_additive_with_mixed_steps_graph_equals_host(gpu):
     for i in (0, 2):
         assert np.array_equal(a.state(i)[0], b.state(i)[0])
     assert np.array_equal(a.reduced_state(1)[0], b.reduced_state(1)[0])
+
+
+def test_single_substep_implicit_subdomain(gpu):
+    """The degenerate count: an implicit subdomain taking the whole controller interval as one step
+    (levels 0 and 1 only) against an explicit one with six substeps."""
+    spec = _setup(W.bar_chain("one", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 1e-6, 6,
+                              max_iters=40), (6, 1), ("explicit", "implicit"))
+    _compare(spec, 3)

@@ -258,6 +258,29 @@ def test_rom_rank_extremes_match_oracle(torch_cuda, r, r_s):
     assert rel_l2(*hq) < 1e-9
 
 
+def test_five_subdomain_chain_with_two_roms(torch_cuda):
+    """FOM-ROM-FOM-FOM-ROM: five subdomains, eight couplings, a ROM at the free end."""
+    from .test_gpu_additive import _rom_ops
+    spec = W.bar_chain("five", 3, [6, 6, 6, 6, 6], ["fom", "rom", "fom", "fom", "rom"], "nh", 1e9, 0.25, 1000.0,
+                       1e-3, 1e-6, 6, max_iters=12)
+    ops = {1: _rom_ops(spec, 1, 6, 4, 21), 4: _rom_ops(spec, 4, 5, 3, 22)}
+    gpu = osam.Problem(spec, rom_ops=ops)
+    ref = O.Problem(spec, rom_ops=ops)
+    hist = {i: ([], []) for i in range(5)}
+    for _ in range(2):
+        rg, rr = gpu.step(), ref.step()
+        assert rg["status"] == osam.OK and rr["status"] == O.OK
+        assert abs(rg["iterations"] - rr["iterations"]) <= 1
+        for i, sd in enumerate(spec.subdomains):
+            if sd.kind == "fom":
+                hist[i][0].append(gpu.state(i)[0].copy()); hist[i][1].append(ref.state(i)[0].copy())
+            else:
+                hist[i][0].append(gpu.reduced_state(i)[0].copy()); hist[i][1].append(ref.rom_state(i)[0].copy())
+    gpu.close()
+    for i in range(5):
+        assert rel_l2(*hist[i]) < 1e-9, i
+
+
 def test_rom_rank_above_the_kernel_limit_is_rejected(torch_cuda):
     from .test_gpu_additive import _rom_ops
     spec = W.bar_chain("rk", 6, [8, 8], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 10, max_iters=8)
