@@ -80,3 +80,27 @@ def test_selection_penalises_non_finite_rollouts(gpu):
     with pytest.raises(osam.OsamError) as ei:
         osam.opinf_select(U.T, A.T, S.T, v0, r=5, lambdas=lams[:2], dt=0.6, substeps=1, r_s=2)
     assert ei.value.code == osam.ENONFINITE
+
+
+def test_single_candidate_selection_is_the_fit_at_that_lambda(gpu):
+    """One candidate: it is selected, its E(lambda) matches the oracle's, and the returned operators
+    are the plain fit at that lambda."""
+    U, A, S, v0 = _known_quadratic_trajectory()
+    ref_err, ref_best, _ = OF.select_lambda(U, A, S, v0, r=5, lambdas=[1e-6], dt=0.02, k=1, r_s=2)
+    got = osam.opinf_select(U.T, A.T, S.T, v0, r=5, lambdas=[1e-6], dt=0.02, substeps=1, r_s=2)
+    assert got["best"] == ref_best == 0 and got["lambda"] == 1e-6
+    _compare(got["errors"], ref_err)
+    fit = osam.opinf_fit(U.T, A.T, S.T, r=5, lam=1e-6, r_s=2)
+    for key in ("K", "H", "B", "c"):
+        assert np.array_equal(got[key], fit[key]), key
+
+
+def test_cubic_selection_on_a_duffing_model_matches_oracle(gpu):
+    """Algorithm 3 with cubic candidates on the oracle-pinned model with Duffing-type cubic terms."""
+    from .test_oracle_fit_adjoint import CUBIC_SCALE
+    U, A, S, v0 = _known_quadratic_trajectory(cubic=CUBIC_SCALE, seed=4)
+    lams = OF.lambda_grid()
+    ref_err, ref_best, _ = OF.select_lambda(U, A, S, v0, r=5, lambdas=lams, dt=0.02, k=1, r_s=2, cubic=True)
+    got = osam.opinf_select(U.T, A.T, S.T, v0, r=5, lambdas=lams, dt=0.02, substeps=1, r_s=2, cubic=True)
+    _compare(got["errors"], ref_err)
+    assert got["best"] == ref_best and got["errors"][got["best"]] < 1e-6
