@@ -718,3 +718,59 @@ def test_tangent_action_is_the_derivative_of_the_force(oracle, material):
     fd = (oracle.internal_force(dims, h, org, material, LAM, MU, u + eps * p)
           - oracle.internal_force(dims, h, org, material, LAM, MU, u - eps * p)) / (2 * eps)
     assert np.abs(y - fd).max() < 1e-6 * np.abs(fd).max()
+
+
+def _free_mask(spec, i):
+    """Free dofs of subdomain i from the spec alone: not clamped, not on a Schwarz node."""
+    sd = spec.subdomains[i]
+    snodes = np.zeros(sd.n_nodes, bool)
+    for c in spec.couplings:
+        if c.dst == i:
+            snodes |= np.asarray(c.nodes, bool)
+    dm = np.zeros(sd.n_nodes, np.uint8) if sd.dirichlet is None else np.asarray(sd.dirichlet)
+    free = np.zeros((sd.n_nodes, 3), bool)
+    for comp in range(3):
+        free[:, comp] = ((dm >> comp) & 1) == 0
+    free[snodes] = False
+    return free.reshape(-1)
+
+
+def test_convergence_criterion_is_eq_conv_criterion(oracle):
+    """The c_num, c_den reported after the second sweep equal Eq. conv_criterion written out from the
+    first and second iterates at t_k: each subdomain with its own step Delta t_i (here 1.5 us and 2 us
+    in a 6 us interval),
+    FOM terms over free dofs (neither clamped nor Schwarz), ROM terms over q and qdot.  The same sums
+    with the common step, or without the velocity term, miss by far more than rounding."""
+    def spec_with(max_iters):
+        s = W.bar_chain("crit", 3, [7, 6], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 1e-6, 6,
+                        max_iters=max_iters)
+        s.subdomains[0].n_substeps, s.subdomains[1].n_substeps = 4, 3
+        return s
+    s1 = spec_with(1)
+    free0, free1 = _free_mask(s1, 0), _free_mask(s1, 1)
+    n_sdof = 3 * int(np.asarray(s1.couplings[[c.dst for c in s1.couplings].index(1)].nodes, bool).sum())
+    ops = {1: W.synthetic_rom_operators(int(free1.sum()), n_sdof, 5, 4, 31)}
+    first = oracle.Problem(s1, rom_ops=ops)
+    assert first.step()["iterations"] == 1
+    second = oracle.Problem(spec_with(2), rom_ops=ops)
+    rep = second.step()
+    assert rep["iterations"] == 2
+    T = s1.dt * s1.n_substeps
+    dts = (T / 4, T / 3)
+    (u1, v1, _), (u2, v2, _) = first.state(0), second.state(0)
+    (q1, qd1, _), (q2, qd2, _) = first.rom_state(1), second.rom_state(1)
+    du = (u2 - u1).reshape(-1)[free0]
+    dv = (v2 - v1).reshape(-1)[free0]
+    uu, vv = u2.reshape(-1)[free0], v2.reshape(-1)[free0]
+
+    def sums(dt0, dt1, vel=1.0):
+        num = np.sum((du + vel * dt0 * dv) ** 2) + np.sum(((q2 - q1) + vel * dt1 * (qd2 - qd1)) ** 2)
+        den = np.sum((uu + vel * dt0 * vv) ** 2) + np.sum((q2 + vel * dt1 * qd2) ** 2)
+        return num, den
+
+    num, den = sums(*dts)
+    assert rep["cnum"] > 0.0
+    assert abs(rep["cnum"] - num) <= 1e-12 * num
+    assert abs(rep["cden"] - den) <= 1e-12 * den
+    for alt in (sums(s1.dt, s1.dt), sums(*dts, vel=0.0)):
+        assert abs(alt[0] - num) > 1e-6 * num
