@@ -238,3 +238,22 @@ def test_single_substep_implicit_subdomain(gpu):
     spec = _setup(W.bar_chain("one", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 1e-6, 6,
                               max_iters=40), (6, 1), ("explicit", "implicit"))
     _compare(spec, 3)
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_criterion_sums_match_oracle(gpu, graph):
+    """The c_num, c_den of Eq. conv_criterion after two sweeps (per-subdomain steps 1.5 us and 2 us, a
+    FOM and a ROM) against the oracle's, whose sums are pinned to the written-out formula."""
+    from .test_oracle_pins import _free_mask
+    spec = W.bar_chain("crit", 3, [7, 6], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 1e-6, 6, max_iters=2)
+    spec.subdomains[0].n_substeps, spec.subdomains[1].n_substeps = 4, 3
+    n_sdof = 3 * int(np.asarray(spec.couplings[[c.dst for c in spec.couplings].index(1)].nodes, bool).sum())
+    ops = {1: W.synthetic_rom_operators(int(_free_mask(spec, 1).sum()), n_sdof, 5, 4, 31)}
+    g = osam.Problem(spec, rom_ops=ops, graph=graph)
+    ref = O.Problem(spec, rom_ops=ops)
+    for _ in range(2):
+        rg, rr = g.step(), ref.step()
+        assert rg["iterations"] == rr["iterations"] == 2
+        assert abs(rg["cden"] - rr["cden"]) <= 1e-12 * rr["cden"]
+        assert abs(rg["cnum"] - rr["cnum"]) <= 1e-6 * rr["cnum"]
+    g.close()
