@@ -833,8 +833,11 @@ def main():
         if e2e:
             e2e["value"] = e2e_pair[1] / (e2e_pair[0] * 1e-3)
             del e2e["seconds"], e2e["updates"]
+        n_launch = launches["kernel_launches"]
+        if world > 1:   # the whole job's launches, like the whole job's element-updates
+            n_launch = combine_ranks([(0.0, n_launch)], f"cuda:{local}")[0][1]
         results[name] = {"total_ms": total_ms, "updates": updates, "iters": iters, "prof": prof, "clk": clk,
-                         "launches": launches["kernel_launches"], "prof_total_ms": p_ms,
+                         "launches": n_launch, "prof_total_ms": p_ms,
                          "host_value": p_upd / (p_ms * 1e-3), "host_ms_per_step": p_ms / args.steps, "e2e": e2e,
                          "tuning": prob.tuning()}
         prob.close()
@@ -927,7 +930,7 @@ def main():
                                      "roofline: a second pass of the same steps driven from the host with CUDA "
                                      "events around every internal-force launch (variants[*].value_host_loop)"},
                 "roofline": roofline(head, head_name), "cpu_baseline": cpu, "e2e": head["e2e"],
-                "gpu_launches": head["launches"] if world == 1 else None,
+                "gpu_launches": head["launches"],
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
                 "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
                 "adjoint": adjoint_meas, "implicit": implicit_meas, "next_rows": next_meas,
