@@ -1,5 +1,5 @@
 """The N > 1 bookkeeping of bench.py (replicas: max of the timed milliseconds, sum of the element-
-updates over ranks) on two CPU ranks with the gloo backend."""
+updates and of the kernel launches over ranks) on two CPU ranks with the gloo backend."""
 import os
 import socket
 import sys
@@ -26,7 +26,8 @@ def _rank_main(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         pairs = [(10.0 + rank, 1000 * (rank + 1)), (5.0 * (2 - rank), 7)]
-        out[rank] = bench.combine_ranks(pairs, "cpu")
+        launches = bench.combine_ranks([(0.0, 1107 + rank)], "cpu")   # the gpu_launches reduction
+        out[rank] = (bench.combine_ranks(pairs, "cpu"), launches)
     finally:
         dist.destroy_process_group()
 
@@ -37,7 +38,7 @@ def test_combine_ranks_gloo_world_size_2():
         out = mgr.dict()
         mp.start_processes(_rank_main, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
         got = dict(out)
-    expect = [(11.0, 3000), (10.0, 14)]
+    expect = ([(11.0, 3000), (10.0, 14)], [(0.0, 2215)])
     assert got[0] == expect and got[1] == expect
 
 
