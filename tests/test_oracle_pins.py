@@ -337,6 +337,32 @@ def test_full_basis_rom_reproduces_fom_fom(oracle):
     assert np.abs(uB - u1).max() < 1e-12 * np.abs(u1).max()
 
 
+@pytest.mark.parametrize("integrator0,counts", [("implicit", (5, 5)), ("explicit", (5, 3)), ("implicit", (2, 5))])
+def test_full_basis_rom_reproduces_fom_fom_across_integrators_and_steps(oracle, integrator0, counts):
+    """The exact full-basis linear ROM is an explicit FOM on its free dofs under any coupling: next to
+    an implicit neighbour, and with its own step through the temporal interpolant, FOM-ROM equals the
+    FOM-FOM run with the same integrators and counts to rounding."""
+    def spec(kinds):
+        p = W.bar_chain("x", 2, [4, 4], kinds, "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+        p.subdomains[0].integrator = integrator0
+        p.subdomains[0].n_substeps, p.subdomains[1].n_substeps = counts
+        return p
+    pf, pr = spec(["fom", "fom"]), spec(["fom", "rom"])
+    ops, free = _exact_linear_rom(oracle, pf, 1)
+    A = oracle.Problem(pf)
+    B = oracle.Problem(pr, rom_ops={1: ops})
+    for _ in range(3):
+        ra, rb = A.step(), B.step()
+        assert ra["status"] == rb["status"] == oracle.OK and ra["iterations"] == rb["iterations"]
+    ua, _, _ = A.state(0)
+    ub, _, _ = B.state(0)
+    assert np.abs(ua - ub).max() < 1e-12 * np.abs(ua).max()
+    u1, v1, _ = A.state(1)
+    q, qd, _ = B.rom_state(1)
+    assert np.abs(q - u1.reshape(-1)[free]).max() < 1e-12 * np.abs(u1).max()
+    assert np.abs(qd - v1.reshape(-1)[free]).max() < 1e-12 * np.abs(v1).max()
+
+
 # ---------------------------------------------------------------------------------------------
 # stability limit of the explicit scheme (set-up check)
 # ---------------------------------------------------------------------------------------------
