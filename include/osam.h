@@ -301,7 +301,7 @@ OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int mater
  *   D has more columns than rows).  Snapshot matrices are [n_snap][n_dof] (one snapshot per row).
  * ------------------------------------------------------------------------------------------------ */
 typedef struct {
-    int n_dof, n_snap, n_sdof;
+    int n_dof, n_snap, n_sdof;  /* each at most 4,194,240 (else OSAM_EINVAL) */
     const double* U;          /* [n_snap][n_dof] displacement snapshots (free dofs) */
     const double* A;          /* [n_snap][n_dof] acceleration snapshots */
     const double* S;          /* [n_snap][n_sdof] Schwarz boundary displacement snapshots */

@@ -438,10 +438,19 @@ int fit_output(const osam_fit_input* in, const FitData& F, const std::vector<dou
     return OSAM_OK;
 }
 
+// The GEMM of rom_kernels.cu maps the output rows of a contraction to grid.y in tiles of 64 rows,
+// and the fit's contractions have n_dof or n_sdof rows (the bases), so both are bounded by
+// 65535 tiles x 64 rows.
+constexpr long long kFitMaxRows = 65535LL * 64;
+
 int fit_check(const osam_fit_input* in) {
     if (!in || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
         (in->n_sdof > 0 && !in->S) || (in->cubic && in->r > 128))
         return OSAM_EINVAL;
+    if (in->n_dof > kFitMaxRows || in->n_sdof > kFitMaxRows || in->n_snap > kFitMaxRows) {
+        g_fit_error = "n_dof, n_sdof and n_snap must not exceed 4,194,240 (65535 GEMM row tiles of 64)";
+        return OSAM_EINVAL;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { g_fit_error = "no CUDA device"; return OSAM_ECUDA; }
     FK(cudaSetDevice(in->device));
