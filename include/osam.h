@@ -175,15 +175,19 @@ OSAM_API int schwarz_init(const osam_problem_desc* desc, osam_ctx** out);
  * schwarz_opinf_discrete), and record its trace at every Schwarz node it feeds. */
 OSAM_API int subdomain_advance(osam_ctx* ctx, int sub);
 
-/* Publish src's recorded trace of the current interval into dst's input boundary history:
+/* Publish src's recorded trace of the current interval into dst's input boundary history -- the
+ * Schwarz Dirichlet data of Eq. schwarz_discrete / Eq. schwarz_opinf_discrete (Sec. 4.1): the
+ * projection Pi at dst's Schwarz nodes, taken onto dst's levels by the temporal interpolant Xi.
  * FOM->FOM copy; FOM->ROM the ROM's boundary snapshot rows; ROM->any Pi Phi q at every substep. */
 OSAM_API int transfer_overlap(osam_ctx* ctx, int src, int dst);
 
-/* Start a controller interval: save every state at t_{k-1} and fill every input boundary history with
- * the zero-order hold of its source's state at t_{k-1} (initial guess of iteration 1). */
+/* Start a controller interval of Algorithm 1: save every state at t_{k-1} and fill every input
+ * boundary history with the zero-order hold of its source's state at t_{k-1} (initial guess of
+ * iteration 1). */
 OSAM_API int osam_begin_interval(osam_ctx* ctx);
 
-/* Return every subdomain to the state saved by osam_begin_interval (start of a new iteration). */
+/* Return every subdomain to the state saved by osam_begin_interval (start of a new Schwarz iteration
+ * of Algorithm 1). */
 OSAM_API int osam_restore_interval(osam_ctx* ctx);
 
 /* Sums of Eq. conv_criterion between the current end states and those of the previous call:
@@ -204,6 +208,7 @@ OSAM_API int schwarz_step(osam_ctx* ctx, osam_step_report* rep);
  * that meets the criterion stops iterating (its state is frozen) while the others continue, so each
  * instance follows exactly its own single-instance iteration sequence.  schwarz_init is a batch of
  * one.  The instance index of the functions below is 0-based; functions without it act on instance 0.
+ * Batching has no counterpart in the paper: each instance runs Algorithm 1 unchanged.
  * ------------------------------------------------------------------------------------------------ */
 OSAM_API int osam_batch_init(int n_instances, const osam_problem_desc* descs, osam_ctx** out);
 /* One controller step of every instance; per_instance[n_instances] (or NULL) receives each instance's
@@ -228,12 +233,13 @@ OSAM_API int osam_set_graph(osam_ctx* ctx, int enable);
  * thread) and tiling (1: the FP64 force by 8x4x4 element tiles).  Any pointer may be NULL. */
 OSAM_API int osam_tuning(osam_ctx* ctx, int* scatter, int* element_block, int* register_cap, int* tiled);
 
-/* Copy a subdomain's nodal state out / in ([nodes][3] each, any pointer may be NULL).  For a ROM the
+/* Copy a subdomain's nodal state (u, v, a of Eq. schwarz_discrete at the end of the last committed
+ * interval) out / in ([nodes][3] each, any pointer may be NULL).  For a ROM the
  * output is the reconstructed field: Phi q on free dofs, boundary data on Schwarz dofs, 0 on clamped
  * dofs; osam_set_state on a ROM projects u, v onto the basis (q = Phi^T u) and recomputes qdd. */
 OSAM_API int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a);
 OSAM_API int osam_set_state(osam_ctx* ctx, int sub, const double* u, const double* v, const double* a);
-/* Reduced state of a ROM subdomain ([r] each). */
+/* Reduced state (q, qd, qdd of Eq. schwarz_opinf_discrete) of a ROM subdomain ([r] each). */
 OSAM_API int osam_get_reduced_state(osam_ctx* ctx, int sub, double* q, double* qd, double* qdd);
 OSAM_API int osam_set_reduced_state(osam_ctx* ctx, int sub, const double* q, const double* qd, const double* qdd);
 /* Sizes of subdomain `sub` (any output may be NULL). */
@@ -256,6 +262,8 @@ OSAM_API int osam_implicit_profile(osam_ctx* ctx, double* tangent_ms, long long*
 OSAM_API int osam_fp64_peak(int device, double* gflops);
 /* The scatter mode in use (OSAM_SCATTER_ATOMIC / GATHER) after any autotuning. */
 OSAM_API int osam_scatter_mode(osam_ctx* ctx);
+/* Free every resource of ctx (library-owned memory, streams, graphs); caller memory is untouched.
+ * NULL is a no-op. */
 OSAM_API void osam_destroy(osam_ctx* ctx);
 /* Message of the last error on ctx, or of the calling thread's last failed schwarz_init if ctx is NULL. */
 OSAM_API const char* osam_last_error(const osam_ctx* ctx);
