@@ -32,3 +32,23 @@ def test_binding_loads():
     build_lib.build()
     L = osam.load()
     assert L.osam_last_error(None) is not None
+
+
+def test_product_path_never_touches_the_oracle():
+    """The library sources and the Python package import, link or name no part of oracle/ (the
+    oracle is test infrastructure; only tests, smoke() and bench.py's CPU legs use it), and the CUDA
+    sources include nothing from it."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2511_20687_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                continue
+            text = open(os.path.join(dirpath, f)).read()
+            assert not re.search(r"^\s*(from\s+oracle|import\s+oracle)", text, re.M), f
+            assert "osam_oracle" not in text and "liboracle" not in text, f
+    header = open(os.path.join(root, "include", "osam.h")).read()
+    assert "oracle" not in header
