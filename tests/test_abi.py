@@ -52,3 +52,17 @@ def test_product_path_never_touches_the_oracle():
             assert "osam_oracle" not in text and "liboracle" not in text, f
     header = open(os.path.join(root, "include", "osam.h")).read()
     assert "oracle" not in header
+
+
+def test_oracle_shares_no_code_with_the_library():
+    """The oracle includes only the C standard library and imports neither the package nor its
+    binding; the seeded workload generators reach it as plain arrays, not imports."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    c_src = open(os.path.join(root, "oracle", "osam_oracle.c")).read()
+    includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', c_src)
+    assert includes and all(i in ("math.h", "stdint.h", "stdlib.h", "string.h", "stdio.h") for i in includes), includes
+    for f in ("fit.py", "oracle.py"):
+        text = open(os.path.join(root, "oracle", f)).read()
+        assert "paper_2511_20687_gb300" not in text, f
+        assert "libosam" not in text, f
