@@ -363,6 +363,143 @@ def test_full_basis_rom_reproduces_fom_fom_across_integrators_and_steps(oracle, 
     assert np.abs(qd - v1.reshape(-1)[free]).max() < 1e-12 * np.abs(v1).max()
 
 
+def _rotated_full_basis_rom(oracle, p, i, seed):
+    """The exact full-basis linear ROM of subdomain i written in rotated bases: Phi = Q, Phi_S = Q_S
+    (seeded random orthogonal, non-symmetric), K' = Q^T K Q, B' = Q^T B Q_S.  Then Phi q = u on the
+    free dofs and B' Phi_S^T s = Q^T B s, so the ROM still reproduces the FOM exactly, but only if
+    ghat = Phi_S^T s, the reconstruction Phi q and the initial projection q0 = Phi^T u0 each read
+    their basis the right way round (Sec. 4.2.1, Eq. schwarz_opinf_discrete)."""
+    ops, free = _exact_linear_rom(oracle, p, i)
+    rng = np.random.default_rng(seed)
+    r, rs = ops["K"].shape[0], ops["B"].shape[1]
+    Q, _ = np.linalg.qr(rng.standard_normal((r, r)))
+    QS, _ = np.linalg.qr(rng.standard_normal((rs, rs)))
+    rot = {"Phi": Q, "Phi_S": QS, "K": Q.T @ ops["K"] @ Q, "H": np.zeros((r, r * (r + 1) // 2)),
+           "B": Q.T @ ops["B"] @ QS, "c": np.zeros(r)}
+    return rot, free
+
+
+def rotated_rom_mismatch(oracle):
+    """Largest relative deviation from FOM-FOM of three couplings of rotated full-basis ROMs (a
+    FOM-ROM pair, a ROM-ROM pair and a FOM-ROM pair with its own substep count through Xi) over three
+    controller steps: displacements of every subdomain (the ROM's reconstructed field) and the
+    reduced state against Phi^T u of the FOM-FOM run.  Exact arithmetic gives 0."""
+    worst = 0.0
+
+    def spec(kinds, counts):
+        sp = W.bar_chain("rot", 2, [4, 4], kinds, "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+        if counts:
+            sp.subdomains[0].n_substeps, sp.subdomains[1].n_substeps = counts
+        return sp
+
+    for kinds, counts in ((["fom", "rom"], None), (["rom", "rom"], None), (["fom", "rom"], (5, 3))):
+        pf = spec(["fom", "fom"], counts)
+        rom_ops, frees = {}, {}
+        for i, k in enumerate(kinds):
+            if k == "rom":
+                rom_ops[i], frees[i] = _rotated_full_basis_rom(oracle, pf, i, 100 + i)
+        A = oracle.Problem(pf)
+        B = oracle.Problem(spec(kinds, counts), rom_ops=rom_ops)
+        for _ in range(3):
+            ra, rb = A.step(), B.step()
+            if rb["status"] != oracle.OK or ra["iterations"] != rb["iterations"]:
+                return float("inf")
+        for i in range(2):
+            u = A.state(i)[0]
+            scale = np.abs(u).max()
+            worst = max(worst, np.abs(B.state(i)[0] - u).max() / scale)
+            if i in rom_ops:
+                q = B.rom_state(i)[0]
+                worst = max(worst, np.abs(rom_ops[i]["Phi"] @ q - u.reshape(-1)[frees[i]]).max() / scale)
+                worst = max(worst, np.abs(q - rom_ops[i]["Phi"].T @ u.reshape(-1)[frees[i]]).max() / scale)
+    return worst
+
+
+def test_rotated_full_basis_rom_reproduces_fom_fom(oracle):
+    """Non-identity orthogonal Phi and Phi_S: FOM-ROM, ROM-ROM and FOM-ROM with mixed substep
+    counts all equal FOM-FOM to 1e-12 (the identity-basis pins cannot see a transposed basis)."""
+    assert rotated_rom_mismatch(oracle) < 1e-12
+
+
+def test_rom_norm_identity(oracle):
+    """The norm identity of an orthonormal basis, ||Phi dq|| = ||dq||, holds for the bases the
+    rotated pin uses, and the ROM's reconstruction at the overlap is Phi q (checked through the
+    reconstructed field above); this fixes the scale of the pin's tolerance."""
+    pf = W.bar_chain("rot", 2, [4, 4], ["fom", "fom"], "le", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5)
+    rot, _ = _rotated_full_basis_rom(oracle, pf, 1, 5)
+    dq = np.random.default_rng(6).standard_normal(rot["Phi"].shape[1])
+    assert abs(np.linalg.norm(rot["Phi"] @ dq) - np.linalg.norm(dq)) < 1e-13 * np.linalg.norm(dq)
+
+
+# Each mutation reads one basis transposed: in the boundary projection ghat = Phi_S^T s, in the
+# reconstruction Phi q, and in the initial projection q0 = Phi^T u0 of the set-up.
+_BASIS_MUTATIONS = {
+    "ghat": ("acc += s->PhiS[i * s->rs + k] * su[i];", "acc += s->PhiS[k * 3 * ns + i] * su[i];"),
+    "reconstruction": ("val += s->Phi[(size_t)row * s->r + k] * qv[k];",
+                       "val += s->Phi[(size_t)k * s->r + row] * qv[k];"),
+    "initial_projection": ("a += s->Phi[(size_t)f * s->r + k] * s->u[s->free_dof[f]];",
+                           "a += s->Phi[(size_t)k * s->r + f] * s->u[s->free_dof[f]];"),
+}
+
+
+@pytest.mark.parametrize("site", sorted(_BASIS_MUTATIONS))
+def test_rotated_pin_fails_on_a_transposed_basis(tmp_path, site):
+    """Plant a transposed basis read in a copy of the oracle (CPU only) and check that the rotated
+    full-basis pin rejects it; the unmodified copy passes the same check."""
+    import shutil
+    import subprocess
+    import sys
+    root = os.path.dirname(HERE)
+    src = open(os.path.join(root, "oracle", "osam_oracle.c")).read()
+    before, after = _BASIS_MUTATIONS[site]
+    assert src.count(before) == 1, f"mutation site {site} not found exactly once"
+    results = {}
+    for tag, text in (("planted", src.replace(before, after)), ("unmodified", src)):
+        d = tmp_path / tag
+        d.mkdir()
+        shutil.copy(os.path.join(root, "oracle", "oracle.py"), d / "oracle.py")
+        (d / "osam_oracle.c").write_text(text)
+        code = ("import importlib.util, sys\n"
+                f"sys.path.insert(0, {root!r})\n"
+                f"spec = importlib.util.spec_from_file_location('oracle_copy', {str(d / 'oracle.py')!r})\n"
+                "O = importlib.util.module_from_spec(spec); spec.loader.exec_module(O)\n"
+                "from tests.test_oracle_pins import rotated_rom_mismatch\n"
+                "print(rotated_rom_mismatch(O))\n")
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+        assert out.returncode == 0, out.stderr
+        results[tag] = float(out.stdout.strip().splitlines()[-1])
+    assert results["unmodified"] < 1e-12
+    assert results["planted"] > 1e-6, results
+
+
+def test_lame_relations_give_uniaxial_stress(oracle):
+    """The (lambda, mu) of workloads.lame(E, nu), used by both sides, through the oracle's linear
+    elastic force: under the affine field u = eps (x, -nu y, -nu z) of a uniaxial stress state the
+    summed nodal force on the +x face is E eps times its area and the +y and +z faces carry no
+    normal force.  A wrong nu term in lambda or mu breaks the second condition, a wrong E scale the
+    first (Appendix A.1 with the standard isotropic relations)."""
+    dims, h = (2, 3, 2), 0.01
+    xyz, (ii, jj, kk) = _coords(dims, h, (0.0, 0.0, 0.0))
+    X, Y, Z = xyz.T
+    eps = 1e-4
+    for E, nu in ((1e9, 0.2), (2e9, 0.3), (7e8, 0.25)):
+        lam, mu = W.lame(E, nu)
+        u = np.stack([eps * X, -nu * eps * Y, -nu * eps * Z], axis=1)
+        f = oracle.internal_force(dims, h, (0.0, 0.0, 0.0), "le", lam, mu, u).reshape(-1, 3)
+        ax, ay, az = dims[1] * dims[2] * h * h, dims[0] * dims[2] * h * h, dims[0] * dims[1] * h * h
+        sxx = f[ii == dims[0], 0].sum() / ax
+        syy = f[jj == dims[1], 1].sum() / ay
+        szz = f[kk == dims[2], 2].sum() / az
+        assert abs(sxx - E * eps) < 1e-10 * E * eps
+        assert abs(syy) < 1e-10 * E * eps and abs(szz) < 1e-10 * E * eps
+    # the check has teeth: Poisson's ratio in the wrong place of lambda leaves a lateral stress
+    E, nu = 1e9, 0.3
+    lam_bad, mu = E * nu / ((1 + nu) * (1 - nu)), E / (2 * (1 + nu))
+    u = np.stack([eps * X, -nu * eps * Y, -nu * eps * Z], axis=1)
+    f = oracle.internal_force(dims, h, (0.0, 0.0, 0.0), "le", lam_bad, mu, u).reshape(-1, 3)
+    assert abs(f[jj == dims[1], 1].sum() / (dims[0] * dims[2] * h * h)) > 1e-3 * E * eps
+
+
 # ---------------------------------------------------------------------------------------------
 # stability limit of the explicit scheme (set-up check)
 # ---------------------------------------------------------------------------------------------
