@@ -258,8 +258,16 @@ OSAM_API int osam_profile_read(osam_ctx* ctx, double* force_ms, long long* force
 OSAM_API int osam_implicit_profile(osam_ctx* ctx, double* tangent_ms, long long* tangent_launches,
                                    long long* tangent_elements, long long* newton_steps, long long* cg_iterations);
 /* FP64 fused multiply-add throughput of device `device` in GFLOP/s (2 flops per FMA), measured by a
- * register-resident FMA loop over 8 blocks per SM; the ALU roofline of the FP64 element kernels. */
+ * register-resident FMA loop over 8 blocks per SM (best of five launches); the ALU roofline of the
+ * FP64 element kernels. */
 OSAM_API int osam_fp64_peak(int device, double* gflops);
+/* FP64 throughput probe: `repeats` launches (1..1000) of about 20 ms each on device `device`, each
+ * reported as TFLOP/s in tflops[r] and, if ms is not NULL, its CUDA-event duration in ms[r].
+ * kind 0: FMA on the FP64 pipe (8 register chains per thread); kind 1: FP64 tensor-core MMA
+ * (mma.sync m8n8k4, 4 accumulator chains per warp); kind 2: both interleaved in the same warps
+ * (total flops), which shows whether the two share one unit.  Synchronous; allocates a small
+ * output buffer.  Bad arguments -> OSAM_EINVAL. */
+OSAM_API int osam_fp64_probe(int device, int kind, int repeats, double* tflops, double* ms);
 /* The scatter mode in use (OSAM_SCATTER_ATOMIC / GATHER) after any autotuning. */
 OSAM_API int osam_scatter_mode(osam_ctx* ctx);
 /* Free every resource of ctx (library-owned memory, streams, graphs); caller memory is untouched.
@@ -274,6 +282,8 @@ OSAM_API const char* osam_last_error(const osam_ctx* ctx);
  * the materials of Appendix A) and its vector-Jacobian product
  *   ubar = (df/du)^T ybar,  lambda_bar[e] = ybar . df/dlambda_e,  mu_bar[e] = ybar . df/dmu_e.
  * lambda_e / mu_e: per-element device arrays or NULL for the uniform lambda / mu.
+ * Meshes whose element count or 3 x node count exceeds INT_MAX -> OSAM_EINVAL; every OSAM_EINVAL
+ * leaves its reason in osam_last_error(NULL).
  * ------------------------------------------------------------------------------------------------ */
 OSAM_API int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambda, double mu,
                     const double* lambda_e, const double* mu_e, const double* u, double* f, void* stream);
@@ -287,13 +297,18 @@ OSAM_API int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material,
  * another allocator's hooks, or a thread that must never block on cudaFree's implicit
  * synchronisation.  Same inputs, layout and result as osam_hex8_force (device pointers, [nodes][3]),
  * computed with the deterministic element-buffer scatter; the buffer is a static device array of
- * 24 * OSAM_NOALLOC_MAX_ELEMENTS doubles (6 MiB) that every GPU loading the library holds until the
- * process exits.  Calls no allocator.  More than OSAM_NOALLOC_MAX_ELEMENTS elements -> OSAM_EINVAL
- * (message in osam_last_error(NULL)).  The first call on a device, with that device current, looks up
- * the array's device address (once per device); make that first call before any stream capture.
+ * 24 * OSAM_NOALLOC_MAX_ELEMENTS doubles (6 MiB).  A dimension or an element count above
+ * OSAM_NOALLOC_MAX_ELEMENTS -> OSAM_EINVAL (message in osam_last_error(NULL)).
+ * Set-up: the first call on a device, with that device current, does a one-time set-up on `stream`
+ * and waits for it: it looks up the array's device address and runs each kernel of this entry point
+ * once on a one-element mesh.  The CUDA runtime loads the array and the kernels' code lazily, so this
+ * first call is the one that makes the device take the 6 MiB (and the code); make it during start-up
+ * (a 1x1x1 mesh is enough), before the memory budget is frozen and before any stream capture.  Later
+ * calls on that device call no allocator and do not synchronise.  The device then holds the array
+ * until the process exits.
  * Every call shares the one buffer and overwrites it entirely (nothing in it needs to start at zero):
  * calls whose kernels overlap on the GPU (different streams, or different host threads on one device)
- * race and must be serialised by the caller.  Asynchronous on `stream`. */
+ * race and must be serialised by the caller.  Asynchronous on `stream` after the set-up. */
 #define OSAM_NOALLOC_MAX_ELEMENTS 32768
 OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int material, double lambda, double mu,
                             const double* lambda_e, const double* mu_e, const double* u, double* f, void* stream);
@@ -309,7 +324,7 @@ OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h, int mater
  *   D has more columns than rows).  Snapshot matrices are [n_snap][n_dof] (one snapshot per row).
  * ------------------------------------------------------------------------------------------------ */
 typedef struct {
-    int n_dof, n_snap, n_sdof;  /* each at most 4,194,240 (else OSAM_EINVAL) */
+    int n_dof, n_snap, n_sdof;  /* each below 2^31 - 64 (else OSAM_EINVAL) */
     const double* U;          /* [n_snap][n_dof] displacement snapshots (free dofs) */
     const double* A;          /* [n_snap][n_dof] acceleration snapshots */
     const double* S;          /* [n_snap][n_sdof] Schwarz boundary displacement snapshots */

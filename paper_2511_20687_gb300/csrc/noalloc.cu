@@ -17,8 +17,9 @@
 
 namespace {
 
-// 24 element contributions per element, OSAM_NOALLOC_MAX_ELEMENTS elements: 6 MiB of FP64 held by
-// every GPU that loads the library, until the process exits.
+// 24 element contributions per element, OSAM_NOALLOC_MAX_ELEMENTS elements: 6 MiB of FP64.  The CUDA
+// runtime loads this file's module (and with it the array) lazily: on a device, the memory is taken
+// by the set-up of the first call (below), then held until the process exits.
 __device__ __align__(256) double g_noalloc_fe[24LL * OSAM_NOALLOC_MAX_ELEMENTS];
 
 constexpr int kMaxDevices = 64;
@@ -53,8 +54,13 @@ __global__ void k_gather_aos(int nx, int ny, int nz, const double* __restrict__ 
     f[t] = s;
 }
 
-// device address of the static element buffer on the current device, looked up once per device
-int fe_address(double** out) {
+// Set-up of a device, once, with that device current: look up the device address of the static
+// element buffer and run every kernel this entry point can launch once (each material's force and the
+// gather) on a one-element mesh carved out of the same buffer.  Under the runtime's lazy loading, the
+// first use of a module or kernel loads its code and may take device memory (the module's __device__
+// array, kernel code, a larger local-memory reservation) and synchronise; doing all of it here keeps
+// later calls free of that.  The warm-up results are never read: every call overwrites the buffer.
+int device_setup(cudaStream_t s, double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         osam::set_thread_error("osam_hex8_force_noalloc: no current CUDA device");
@@ -69,7 +75,26 @@ int fe_address(double** out) {
                                    cudaGetErrorString(e));
             return OSAM_ECUDA;
         }
-        g_fe_addr[dev] = static_cast<double*>(p);
+        double* base = static_cast<double*>(p);
+        // one element: element buffer at [0, 24), its 8 nodes' u at [24, 48), f at [48, 72)
+        osam::ElemArgs a{};
+        a.nx = a.ny = a.nz = a.ne = 1;
+        a.invh = 1.0; a.w8 = 0.125; a.wq = 1.0 / 32.0; a.wq3 = 1.0 / 96.0; a.lam = 1.0; a.mu = 1.0;
+        a.u = base + 24; a.usn = 3; a.usc = 1;
+        a.fe = base;
+        for (int m : {OSAM_LINEAR_ELASTIC, OSAM_NEO_HOOKEAN, OSAM_SAINT_VENANT_KIRCHHOFF})
+            if (e == cudaSuccess) e = osam::launch_hex8_force(m, false, osam::kGather, a, s);
+        if (e == cudaSuccess) {
+            k_gather_aos<<<1, 32, 0, s>>>(1, 1, 1, base, base + 48);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            osam::set_thread_error(std::string("osam_hex8_force_noalloc: device set-up failed: ") +
+                                   cudaGetErrorString(e));
+            return OSAM_ECUDA;
+        }
+        g_fe_addr[dev] = base;
     }
     *out = g_fe_addr[dev];
     return OSAM_OK;
@@ -85,6 +110,12 @@ extern "C" OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h
         osam::set_thread_error("osam_hex8_force_noalloc: invalid argument");
         return OSAM_EINVAL;
     }
+    // each dimension is bounded first, so the element count below cannot overflow
+    if (nx > OSAM_NOALLOC_MAX_ELEMENTS || ny > OSAM_NOALLOC_MAX_ELEMENTS || nz > OSAM_NOALLOC_MAX_ELEMENTS) {
+        osam::set_thread_error("osam_hex8_force_noalloc: a mesh dimension exceeds the static buffer limit of " +
+                               std::to_string(OSAM_NOALLOC_MAX_ELEMENTS) + " elements");
+        return OSAM_EINVAL;
+    }
     const long long ne = (long long)nx * ny * nz;
     if (ne > OSAM_NOALLOC_MAX_ELEMENTS) {
         osam::set_thread_error("osam_hex8_force_noalloc: " + std::to_string(ne) +
@@ -92,13 +123,15 @@ extern "C" OSAM_API int osam_hex8_force_noalloc(int nx, int ny, int nz, double h
                                std::to_string(OSAM_NOALLOC_MAX_ELEMENTS));
         return OSAM_EINVAL;
     }
-    double* fe = nullptr;
-    if (int rc = fe_address(&fe)) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* fe = nullptr;
+    if (int rc = device_setup(s, &fe)) return rc;
     osam::ElemArgs a{};
     a.nx = nx; a.ny = ny; a.nz = nz; a.ne = (int)ne;
     a.invh = 1.0 / h;
     a.w8 = h * h / 8.0;
+    a.wq = h * h / 32.0;
+    a.wq3 = h * h / 96.0;
     a.lam = lambda; a.mu = mu;
     a.lam_e = lambda_e; a.mu_e = mu_e;
     a.u = u; a.usn = 3; a.usc = 1;
