@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -392,6 +393,8 @@ static ElemArgs standalone_args(int nx, int ny, int nz, double h, double lambda,
     a.nx = nx; a.ny = ny; a.nz = nz; a.ne = nx * ny * nz;
     a.invh = 1.0 / h;
     a.w8 = h * h / 8.0;
+    a.wq = h * h / 32.0;
+    a.wq3 = h * h / 96.0;
     a.lam = lambda; a.mu = mu;
     a.lam_e = lam_e; a.mu_e = mu_e;
     a.u = u; a.usn = 3; a.usc = 1;
@@ -399,11 +402,32 @@ static ElemArgs standalone_args(int nx, int ny, int nz, double h, double lambda,
     return a;
 }
 
+// mesh sizes the element-level kernels index with 32-bit element and node numbers
+static bool elem_mesh_ok(const char* who, int nx, int ny, int nz, double h) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0)) {
+        set_thread_error(std::string(who) + ": mesh dimensions and h must be positive");
+        return false;
+    }
+    const long long ne = (long long)nx * ny * nz;   // < 2^93 cannot wrap in the node product below
+    const double nn = (double(nx) + 1.0) * (double(ny) + 1.0) * (double(nz) + 1.0);
+    if (ne > INT_MAX || 3.0 * nn > double(INT_MAX)) {
+        set_thread_error(std::string(who) + ": mesh too large for 32-bit element / node indices");
+        return false;
+    }
+    return true;
+}
+
 int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambda, double mu, const double* lambda_e,
                     const double* mu_e, const double* u, double* f, void* stream) {
-    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !f) return OSAM_EINVAL;
-    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN && material != OSAM_SAINT_VENANT_KIRCHHOFF)
+    if (!elem_mesh_ok("osam_hex8_force", nx, ny, nz, h)) return OSAM_EINVAL;
+    if (!u || !f) {
+        set_thread_error("osam_hex8_force: u and f must be device pointers");
         return OSAM_EINVAL;
+    }
+    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN && material != OSAM_SAINT_VENANT_KIRCHHOFF) {
+        set_thread_error("osam_hex8_force: unknown material");
+        return OSAM_EINVAL;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
     if (cudaMemsetAsync(f, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
@@ -415,8 +439,15 @@ int osam_hex8_force(int nx, int ny, int nz, double h, int material, double lambd
 int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double lambda, double mu,
                         const double* lambda_e, const double* mu_e, const double* u, const double* ybar, double* ubar,
                         double* lambda_bar, double* mu_bar, void* stream) {
-    if (nx < 1 || ny < 1 || nz < 1 || !(h > 0.0) || !u || !ybar || !ubar) return OSAM_EINVAL;
-    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN) return OSAM_EINVAL;
+    if (!elem_mesh_ok("osam_hex8_force_vjp", nx, ny, nz, h)) return OSAM_EINVAL;
+    if (!u || !ybar || !ubar) {
+        set_thread_error("osam_hex8_force_vjp: u, ybar and ubar must be device pointers");
+        return OSAM_EINVAL;
+    }
+    if (material != OSAM_LINEAR_ELASTIC && material != OSAM_NEO_HOOKEAN) {
+        set_thread_error("osam_hex8_force_vjp: material must be linear elastic or Neo-Hookean");
+        return OSAM_EINVAL;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
     if (cudaMemsetAsync(ubar, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
