@@ -27,7 +27,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
             "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
-            "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_hex8_force_noalloc", "osam_batch_init",
+            "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_fp64_probe", "osam_hex8_force_noalloc", "osam_batch_init",
             "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
             "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
             "osam_set_graph", "osam_tuning", "opinf_select"]
@@ -134,6 +134,7 @@ def load():
                                     C.POINTER(C.c_longlong)]
     L.osam_implicit_profile.argtypes = [_vp, _dp] + [C.POINTER(C.c_longlong)] * 4
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
+    L.osam_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
     L.osam_batch_init.argtypes = [C.c_int, C.POINTER(ProblemDesc), C.POINTER(_vp)]
     L.osam_batch_step.argtypes = [_vp, C.POINTER(StepReport), C.POINTER(StepReport)]
     L.osam_num_instances.argtypes = [_vp]
@@ -511,3 +512,12 @@ def fp64_peak_gflops(device=0) -> float:
     g = C.c_double()
     _check(load().osam_fp64_peak(device, C.byref(g)))
     return g.value
+
+
+def fp64_probe(kind=0, repeats=10, device=0):
+    """FP64 throughput probe: (TFLOP/s, ms) of each of `repeats` launches; kind 0 FMA, 1 tensor-core
+    MMA (m8n8k4), 2 both interleaved in the same warps."""
+    t = np.zeros(repeats)
+    ms = np.zeros(repeats)
+    _check(load().osam_fp64_probe(device, kind, repeats, t.ctypes.data_as(_dp), ms.ctypes.data_as(_dp)))
+    return t, ms
