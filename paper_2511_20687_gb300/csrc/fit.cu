@@ -288,22 +288,36 @@ struct FitData {
     std::vector<double> sigma, sigma_s;
 };
 
+// A snapshot matrix already in this device's memory is read in place (the fit never writes its
+// inputs); host memory, or another device's, is copied into a buffer of the fit.
+int snapshot_operand(const double* src, size_t count, int device, cudaStream_t s, Dev& dev, const double** out) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, src) == cudaSuccess && at.device == device &&
+        (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) {
+        *out = src;
+        return OSAM_OK;
+    }
+    cudaGetLastError();   // an unregistered host pointer may leave an error behind on older runtimes
+    double* d = dev.alloc(count);
+    FA(d);
+    FK(cudaMemcpyAsync(d, src, sizeof(double) * count, cudaMemcpyDefault, s));
+    *out = d;
+    return OSAM_OK;
+}
+
 int fit_prepare(const osam_fit_input* in, cudaStream_t s, Dev& dev, FitData& F) {
     const int ns = in->n_snap, n = in->n_dof, nsd = in->n_sdof, r = in->r;
     F.ns = ns; F.n = n; F.nsd = nsd; F.r = r;
-    double* U = dev.alloc((size_t)ns * n);
-    double* A = dev.alloc((size_t)ns * n);
-    FA(U); FA(A);
-    FK(cudaMemcpyAsync(U, in->U, sizeof(double) * ns * n, cudaMemcpyDefault, s));
-    FK(cudaMemcpyAsync(A, in->A, sizeof(double) * ns * n, cudaMemcpyDefault, s));
+    const double* U = nullptr;
+    const double* A = nullptr;
+    if (int rc = snapshot_operand(in->U, (size_t)ns * n, in->device, s, dev, &U)) return rc;
+    if (int rc = snapshot_operand(in->A, (size_t)ns * n, in->device, s, dev, &A)) return rc;
     int r_used = 0;
     if (int rc = pod(s, dev, U, ns, n, r, 0.0, 0, &r_used, &F.Phi, F.sigma)) return rc;
     // boundary basis
-    double* S = nullptr;
+    const double* S = nullptr;
     if (nsd > 0) {
-        S = dev.alloc((size_t)ns * nsd);
-        FA(S);
-        FK(cudaMemcpyAsync(S, in->S, sizeof(double) * ns * nsd, cudaMemcpyDefault, s));
+        if (int rc = snapshot_operand(in->S, (size_t)ns * nsd, in->device, s, dev, &S)) return rc;
         const int rs_cap = std::min(in->r_s_max > 0 ? in->r_s_max : ns, ns);
         if (int rc = pod(s, dev, S, ns, nsd, in->r_s > 0 ? std::min(in->r_s, ns) : 0, in->energy_s, rs_cap, &F.rs,
                          &F.PhiS, F.sigma_s))
@@ -438,17 +452,15 @@ int fit_output(const osam_fit_input* in, const FitData& F, const std::vector<dou
     return OSAM_OK;
 }
 
-// The GEMM of rom_kernels.cu maps the output rows of a contraction to grid.y in tiles of 64 rows,
-// and the fit's contractions have n_dof or n_sdof rows (the bases), so both are bounded by
-// 65535 tiles x 64 rows.
-constexpr long long kFitMaxRows = 65535LL * 64;
+// The kernels of the fit index rows, snapshot columns and feature columns with 32-bit integers.
+constexpr long long kFitMaxRows = 0x7fffffffLL - 64;
 
 int fit_check(const osam_fit_input* in) {
     if (!in || !in->U || !in->A || in->n_dof < 1 || in->n_snap < 1 || in->r < 1 || in->r > 256 ||
         (in->n_sdof > 0 && !in->S) || (in->cubic && in->r > 128))
         return OSAM_EINVAL;
     if (in->n_dof > kFitMaxRows || in->n_sdof > kFitMaxRows || in->n_snap > kFitMaxRows) {
-        g_fit_error = "n_dof, n_sdof and n_snap must not exceed 4,194,240 (65535 GEMM row tiles of 64)";
+        g_fit_error = "n_dof, n_sdof and n_snap must be below 2^31 - 64";
         return OSAM_EINVAL;
     }
     int ndev = 0;

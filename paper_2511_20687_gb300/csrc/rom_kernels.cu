@@ -82,7 +82,8 @@ __global__ void k_build_Rt(int nrow, int r, const int* dnode, const double* dw, 
 // transposed one; likewise j or k for B), so every warp reads whole 128-byte lines.  With split-K
 // (gridDim.z > 1) block z sums k in [z kchunk, (z + 1) kchunk) and stores its partial tile into
 // ws[z][m][n]; k_gemm_reduce then adds the partials in ascending z (deterministic) and applies
-// alpha and beta.
+// alpha and beta.  The output tiles are numbered along grid.x, column tile fastest (blocks that
+// share a row tile of A run together and find it in L2), so m is bounded only by 32-bit indices.
 constexpr int TM = 64, TN = 64, TK = 16;
 __global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, int kchunk, const double* A, long long ai,
                                               long long ak, const double* B, long long bk, long long bj, double* C,
@@ -90,7 +91,8 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, int kchunk
     __shared__ double As[TK][TM + 1];
     __shared__ double Bs[TK][TN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+    const int ntn = (n + TN - 1) / TN;
+    const int i0 = (int)(blockIdx.x / ntn) * TM, j0 = (int)(blockIdx.x % ntn) * TN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(kdim, kbeg + kchunk);
     const bool a_along_i = ai == 1 && ak != 1;   // A stored [k][m]
@@ -167,7 +169,8 @@ cudaError_t launch_gemm(int m, int n, int k, const double* A, long long ai, long
         kchunk = (kchunk + TK - 1) / TK * TK;
         nsplit = (k + kchunk - 1) / kchunk;
     }
-    dim3 g(grid_for(n, TN), grid_for(m, TM), nsplit);
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 g((unsigned)tiles, 1, nsplit);
     if (nsplit == 1) {
         k_gemm<<<g, 256, 0, s>>>(m, n, k, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, nullptr);
         return cudaGetLastError();
