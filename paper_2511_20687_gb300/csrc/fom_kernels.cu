@@ -31,12 +31,7 @@ __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
     const double lam = a.lam_e ? a.lam_e[e] : a.lam;
     const double mu = a.mu_e ? a.mu_e[e] : a.mu;
     T m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = T(0.5 * kappa * a.w8); m2 = T(mu * a.w8); m3 = T(mu * a.w8 / 3.0);
-    } else {
-        m1 = T(lam * a.w8); m2 = T(mu * a.w8); m3 = T(0);
-    }
+    material_factors<MAT, T>(lam, mu, a.wq, a.wq3, m1, m2, m3);
     T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {

@@ -5,8 +5,9 @@
 // grad_X N = grad_s N / h, detJ * w = h^3/8 at each of the 8 Gauss points s = (1 -+ 1/sqrt3)/2, so
 //   H = grad u = sum_a (u_a / h) (x) grad_s N_a,     f_a = (h^2/8) sum_gp P(H) grad_s N_a.
 // Trilinear shape functions factor per axis, so both sums are evaluated by sum factorisation:
-// edge differences along one axis followed by linear interpolation along the other two (and the
-// transpose for the force), 16 FP64 operations per (component, direction) instead of 8 x 8.
+// edge differences along one axis followed by linear interpolation along the other two, 16 FP64
+// operations per (component, direction) instead of 8 x 8; the transposed interpolation and the
+// nodal sums run in the sum / difference (Walsh) basis of the 8 corners (element_force_grad).
 // The Neo-Hookean stress of Appendix A.3, P = F S with
 //   S = 1/2 kappa (det C - 1) C^-1 + mu (det C)^-1/3 (I - 1/3 tr C C^-1),
 // is evaluated through F C^-1 = F^-T = cof(F) / J, i.e.
@@ -41,15 +42,17 @@ __device__ __forceinline__ double rcbrtT(double x) {
 }
 __device__ __forceinline__ float rcbrtT(float x) { return rcbrtf(x); }
 
-// nodal values D[b][e] on a unit square -> values at the 2x2 Gauss points out[q][r]
+// nodal values D[b][e] on a unit square -> values at the 2x2 Gauss points out[q][r]; plus_one adds 1
+// to every output (folded into the first stage: the weights of each stage sum to 1)
 template <typename T>
-__device__ __forceinline__ void lerp2(const T D[2][2], T out[2][2]) {
+__device__ __forceinline__ void lerp2(const T D[2][2], T out[2][2], bool plus_one = false) {
     T E[2][2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         T d = D[1][e] - D[0][e];
-        E[0][e] = fmaT(T(kG0), d, D[0][e]);
-        E[1][e] = fmaT(T(kG1), d, D[0][e]);
+        const T base = plus_one ? D[0][e] + T(1) : D[0][e];
+        E[0][e] = fmaT(T(kG0), d, base);
+        E[1][e] = fmaT(T(kG1), d, base);
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -123,6 +126,19 @@ __device__ __forceinline__ void stress_svk(const T H[3][3], T lam, T mu, T P[3][
         }
 }
 
+// Material factors (m1, m2, m3) of element_force_grad: Neo-Hookean (kappa/2, mu, mu/3) or linear
+// elastic / Saint Venant-Kirchhoff (lambda, mu, 0), each times wq = h^2/32 -- the Gauss weight times
+// detJ / h (h^2/8) and the 1/4 of the Walsh-basis transposed interpolation.  wq3 = wq / 3.
+template <int MAT, typename T>
+__device__ __forceinline__ void material_factors(double lam, double mu, double wq, double wq3, T& m1, T& m2, T& m3) {
+    if (MAT == OSAM_NEO_HOOKEAN) {
+        const double kappa = lam + (2.0 / 3.0) * mu;
+        m1 = T(0.5 * kappa * wq); m2 = T(mu * wq); m3 = T(mu * wq3);
+    } else {
+        m1 = T(lam * wq); m2 = T(mu * wq); m3 = T(0);
+    }
+}
+
 // Appendix A.3 in cofactor form (kap2 = kappa/2, mu, mu3 = mu/3, all pre-scaled by h^2/8):
 // P = alpha F + beta cof(F); returns F, cof(F), alpha, beta
 template <typename T>
@@ -161,7 +177,10 @@ __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, 
 }
 
 // Neo-Hookean Gauss-point sums Sx[c][q][r] = sum_p P_c0(p, q, r), Sy[c][p][r] = sum_q P_c1,
-// Sz[c][p][q] = sum_r P_c2 with P = alpha F + beta cof(F).  Column k of F depends on two of the three
+// Sz[c][p][q] = sum_r P_c2 with P = alpha F + beta cof(F).  The inputs are the columns of F = I + H at
+// the Gauss points: Gx = dx u + e_x, Gy = dy u + e_y, Gz = dz u + e_z (the callers add the 1 of the
+// diagonal before the last interpolation stage, where it costs fewer operations; rigid translations
+// still give F = I exactly).  Column k of F depends on two of the three
 // Gauss indices only (column 0 on q and r, column 1 on p and r, column 2 on p and q), so
 //  - tr C = |F_0|^2 + |F_1|^2 + |F_2|^2 is assembled from squared column norms formed once per pair of
 //    Gauss points that share the column, and
@@ -170,17 +189,9 @@ __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, 
 template <typename T>
 __device__ __forceinline__ void nh_gauss_sums(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
                                               T kap2, T mu, T mu3, T Sx[3][2][2], T Sy[3][2][2], T Sz[3][2][2]) {
-    T F0[3][2][2], F1[3][2][2], F2[3][2][2];   // columns of F = I + H: F0[c][q][r], F1[c][p][r], F2[c][p][q]
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                F0[c][a][b] = c == 0 ? T(1) + Gx[c][a][b] : Gx[c][a][b];
-                F1[c][a][b] = c == 1 ? T(1) + Gy[c][a][b] : Gy[c][a][b];
-                F2[c][a][b] = c == 2 ? T(1) + Gz[c][a][b] : Gz[c][a][b];
-            }
+    const T (*F0)[2][2] = Gx;   // columns of F: F0[c][q][r], F1[c][p][r], F2[c][p][q]
+    const T (*F1)[2][2] = Gy;
+    const T (*F2)[2][2] = Gz;
     T n0[2][2];                                // |F_0|^2 at (q, r)
 #pragma unroll
     for (int q = 0; q < 2; ++q)
@@ -257,9 +268,35 @@ __device__ __forceinline__ void nh_gauss_sums(const T Gx[3][2][2], const T Gy[3]
     }
 }
 
+// Hadamard (sum / difference) coefficients of a 2x2 array S[a][b]: h0 = sum, ha = sum (2a - 1) S,
+// hb = sum (2b - 1) S, hab = sum (2a - 1)(2b - 1) S (two butterfly stages, 8 additions)
+template <typename T>
+__device__ __forceinline__ void hadamard2(const T S[2][2], T& h0, T& ha, T& hb, T& hab) {
+    const T e0 = S[0][0] + S[0][1], e1 = S[1][0] + S[1][1];
+    const T d0 = S[0][1] - S[0][0], d1 = S[1][1] - S[1][0];
+    h0 = e0 + e1; ha = e1 - e0; hb = d0 + d1; hab = d1 - d0;
+}
+
+template <typename T>
+__device__ __forceinline__ void walsh_transpose(const T Sx[3][2][2], const T Sy[3][2][2], const T Sz[3][2][2],
+                                                T F[3][8]);
+
 // Element force from the displacement gradients at the Gauss points:
-//   Gx[c][q][r] = d u_c / dx at (y GP q, z GP r), Gy[c][p][r], Gz[c][p][q].
-// Output F[c][corner], corner = ax + 2 ay + 4 az.
+//   Gx[c][q][r] = d u_c / dx at (y GP q, z GP r), Gy[c][p][r], Gz[c][p][q]
+// (Neo-Hookean: the columns of F, i.e. with the 1 of the diagonal added, see nh_gauss_sums), and the
+// material factors of material_factors().  Output F[c][corner], corner = ax + 2 ay + 4 az.
+//
+// Transposed interpolation in the Walsh basis.  With s_d = 2 a_d - 1 the sign of a corner along axis d
+// and t = 1/sqrt3, the trilinear weights at the Gauss points are l_a(g_q) = (1 + s t_q) / 2 with
+// t_q = (2q - 1) t, so the force of the x-direction sums Sx[q][r] at corner s is
+//   s_x Tx = s_x / 4 [h0(Sx) + t s_y ha(Sx) + t s_z hb(Sx) + t^2 s_y s_z hab(Sx)],
+// and likewise for y and z.  Summed over the directions, the corner force is
+//   F(s) = 1/4 [wx sx + wy sy + wz sz + t (wxy sx sy + wxz sx sz + wyz sy sz) + t^2 wxyz sx sy sz],
+//   wx = h0(Sx), wy = h0(Sy), wz = h0(Sz), wxy = ha(Sx) + ha(Sy), wxz = hb(Sx) + ha(Sz),
+//   wyz = hb(Sy) + hb(Sz), wxyz = hab(Sx) + hab(Sy) + hab(Sz)
+// (no constant term: the element force is self-equilibrated).  With P = sx wx + sy wy + t sx sy wxy
+// and Q = wz + t sx wxz + t sy wyz + t^2 sx sy wxyz, F = (P + sz Q) / 4; the 1/4 is in the material
+// factors.  51 FP64 operations per component instead of 64 for three tensor-product transposes.
 template <int MAT, typename T>
 __device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
                                                    T m1, T m2, T m3, T F[3][8]) {
@@ -290,33 +327,32 @@ __device__ __forceinline__ void element_force_grad(const T Gx[3][2][2], const T 
                     }
                 }
     }
+    walsh_transpose<T>(Sx, Sy, Sz, F);
+}
+
+// The transposed interpolation and nodal sums of element_force_grad on its own (Gauss-point sums S
+// scaled by 1/4 -> corner forces F[c][corner]); also used by the force's vector-Jacobian product.
+template <typename T>
+__device__ __forceinline__ void walsh_transpose(const T Sx[3][2][2], const T Sy[3][2][2], const T Sz[3][2][2],
+                                                T F[3][8]) {
+    const T t = T(kGd);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        T Tm[2][2];
-        lerp2T<T>(Sx[c], Tm);  // Tm[ay][az]
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[c][1 + 2 * ay + 4 * az] = Tm[ay][az];
-                F[c][2 * ay + 4 * az] = -Tm[ay][az];
-            }
-        lerp2T<T>(Sy[c], Tm);  // Tm[ax][az]
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) {
-                F[c][ax + 2 + 4 * az] += Tm[ax][az];
-                F[c][ax + 4 * az] -= Tm[ax][az];
-            }
-        lerp2T<T>(Sz[c], Tm);  // Tm[ax][ay]
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) {
-                F[c][ax + 2 * ay + 4] += Tm[ax][ay];
-                F[c][ax + 2 * ay] -= Tm[ax][ay];
-            }
+        T wx, ax_, bx_, abx, wy, ay_, by_, aby, wz, az_, bz_, abz;
+        hadamard2<T>(Sx[c], wx, ax_, bx_, abx);   // Sx[q][r]: a along y, b along z
+        hadamard2<T>(Sy[c], wy, ay_, by_, aby);   // Sy[p][r]: a along x, b along z
+        hadamard2<T>(Sz[c], wz, az_, bz_, abz);   // Sz[p][q]: a along x, b along y
+        const T wxy = ax_ + ay_, wxz = bx_ + az_, wyz = by_ + bz_, wxyz = (abx + aby) + abz;
+        const T up = fmaT(t, wxy, wx), um = fmaT(-t, wxy, wx);      // wx + t sy wxy, sy = +1 / -1
+        const T ap = fmaT(t, wyz, wz), am = fmaT(-t, wyz, wz);      // wz + t sy wyz
+        const T bp = fmaT(t, wxyz, wxz), bm = fmaT(-t, wxyz, wxz);  // wxz + t sy wxyz
+        // P and Q at (sx, sy) = (+,+), (-,+), (+,-), (-,-); corner index ax + 2 ay + 4 az
+        const T Ppp = up + wy, Pmp = wy - up, Ppm = um - wy, Pmm = -um - wy;
+        const T Qpp = fmaT(t, bp, ap), Qmp = fmaT(-t, bp, ap), Qpm = fmaT(t, bm, am), Qmm = fmaT(-t, bm, am);
+        F[c][3] = Ppp - Qpp; F[c][7] = Ppp + Qpp;
+        F[c][2] = Pmp - Qmp; F[c][6] = Pmp + Qmp;
+        F[c][1] = Ppm - Qpm; F[c][5] = Ppm + Qpm;
+        F[c][0] = Pmm - Qmm; F[c][4] = Pmm + Qmm;
     }
 }
 
@@ -328,9 +364,10 @@ __device__ __forceinline__ void element_force(const T Dx[3][2][2], const T Dy[3]
     T Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        lerp2<T>(Dx[c], Gx[c]);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
-        lerp2<T>(Dy[c], Gy[c]);   // Gy[c][p][r]
-        lerp2<T>(Dz[c], Gz[c]);   // Gz[c][p][q]
+        const bool nh = MAT == OSAM_NEO_HOOKEAN;
+        lerp2<T>(Dx[c], Gx[c], nh && c == 0);   // Gx[c][q][r]  (q: y Gauss point, r: z Gauss point)
+        lerp2<T>(Dy[c], Gy[c], nh && c == 1);   // Gy[c][p][r]
+        lerp2<T>(Dz[c], Gz[c], nh && c == 2);   // Gz[c][p][q]
     }
     element_force_grad<MAT, T>(Gx, Gy, Gz, m1, m2, m3, F);
 }

@@ -40,6 +40,7 @@ struct Grid {
 struct ElemArgs {
     int nx, ny, nz, ne;
     double invh, w8;          // 1/h and h^2/8 (Gauss weight x detJ / h for unit cubes)
+    double wq, wq3;           // h^2/32 and h^2/96 (the element force's material-factor weights)
     double lam, mu;
     const double* lam_e;
     const double* mu_e;
@@ -56,6 +57,8 @@ struct ElemArgs {
 struct InstFom {
     int nx, ny, nz, nn, ne, ns;
     double invh, w8, lam, mu;
+    double wq, wq3;           // h^2/32 and h^2/96: weights of the force kernels' material factors
+    double m1, m2, m3;        // material factors of the uniform material (hex8::material_factors)
     const double* lam_e;      // absolute device pointers or null (uniform lam / mu)
     const double* mu_e;
     long long node_off, elem_off, hist_off;

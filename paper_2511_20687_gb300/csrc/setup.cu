@@ -158,7 +158,15 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         I.nx = g.nx; I.ny = g.ny; I.nz = g.nz; I.nn = g.nn(); I.ne = g.ne(); I.ns = G.ns[i];
         I.invh = 1.0 / g.h;
         I.w8 = g.h * g.h / 8.0;
+        I.wq = g.h * g.h / 32.0;
+        I.wq3 = g.h * g.h / 96.0;
         I.lam = d.lambda; I.mu = d.mu;
+        if (d.material == OSAM_NEO_HOOKEAN) {
+            const double kappa = d.lambda + (2.0 / 3.0) * d.mu;
+            I.m1 = 0.5 * kappa * I.wq; I.m2 = d.mu * I.wq; I.m3 = d.mu * I.wq3;
+        } else {
+            I.m1 = d.lambda * I.wq; I.m2 = d.mu * I.wq; I.m3 = 0.0;
+        }
         I.node_off = NN; I.elem_off = NE; I.hist_off = H;
         NN += I.nn; NE += I.ne; H += (long long)(ctx->slots[s].nsub + 1) * 9 * I.ns;
     }

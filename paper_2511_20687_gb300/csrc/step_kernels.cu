@@ -53,15 +53,10 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
     int node[8];
 #pragma unroll
     for (int c8 = 0; c8 < 8; ++c8) node[c8] = n0 + (c8 & 1) + ((c8 >> 1) & 1) * sy + ((c8 >> 2) & 1) * sz;
-    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
     T m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = T(0.5 * kappa * I.w8); m2 = T(mu * I.w8); m3 = T(mu * I.w8 / 3.0);
-    } else {
-        m1 = T(lam * I.w8); m2 = T(mu * I.w8); m3 = T(0);
-    }
+    if (I.lam_e || I.mu_e)
+        material_factors<MAT, T>(I.lam_e ? I.lam_e[e] : I.lam, I.mu_e ? I.mu_e[e] : I.mu, I.wq, I.wq3, m1, m2, m3);
+    else { m1 = T(I.m1); m2 = T(I.m2); m3 = T(I.m3); }
     T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
     const double* ub = g.us + I.node_off;
 #pragma unroll
@@ -90,10 +85,11 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
 
 // Tiled FP64 force: one block of 128 threads per 8x4x4 tile of elements.  The edge differences and
 // the first interpolation stage of the gradients are shared by neighbouring elements (an x-edge pair
-// interpolated along y serves the elements below and above it), so the block computes them once per
-// tile in shared memory and each thread finishes its element with the second stage.  The arithmetic
-// per value is the one of edge_differences_prescaled + lerp2, so the result equals the untiled
-// kernel's bit for bit; the sharing saves ~34 of the ~850 FP64 operations per element.
+// interpolated along y serves the elements below and above it, and every edge difference serves two
+// such pairs), so the block computes them once per tile in shared memory and each thread finishes its
+// element with the second stage.  The arithmetic per value is the one of edge_differences_prescaled +
+// lerp2, so the result equals the untiled kernel's bit for bit; the sharing saves ~43 of the ~780 FP64
+// operations per element.
 constexpr int kTX = 8, kTY = 4, kTZ = 4;
 
 template <int MAT, int MODE>
@@ -104,6 +100,9 @@ __global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* _
         return;
     }
     __shared__ double su[3][kTZ + 1][kTY + 1][kTX + 1];  // u / h at the tile's nodes
+    __shared__ double sdx[3][kTZ + 1][kTY + 1][kTX];     // x-edge differences [c][k][j][i]
+    __shared__ double sdy[3][kTZ + 1][kTY][kTX + 1];     // y-edge differences
+    __shared__ double sdz[3][kTZ][kTY + 1][kTX + 1];     // z-edge differences
     __shared__ double sax[3][kTZ + 1][kTY][kTX][2];     // x-edges interpolated along y: [c][k][j][i][gy]
     __shared__ double say[3][kTZ + 1][kTY][kTX][2];     // y-edges interpolated along x: [c][k][j][i][gx]
     __shared__ double saz[3][kTZ][kTY + 1][kTX][2];     // z-edges interpolated along x: [c][k][j][i][gx]
@@ -125,35 +124,52 @@ __global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* _
         su[c][kk][jj][ii] = v;
     }
     __syncthreads();
-    // (2) edge differences and the first interpolation stage, 3 directions x 3 components x 160 pairs
-    const double G[2] = {hex8::kG0, hex8::kG1};
-    for (int q = tid; q < 3 * 3 * 160; q += blockDim.x) {
-        const int dir = q / 480, c = (q / 160) % 3, w = q % 160;
-        if (dir == 0) {          // x-edges (i; j, k) and (i; j + 1, k), interpolated along y
-            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
-            const double d0 = su[c][k][j][i + 1] - su[c][k][j][i];
-            const double d1 = su[c][k][j + 1][i + 1] - su[c][k][j + 1][i];
-            const double dd = d1 - d0;
-            sax[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
-            sax[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
-        } else if (dir == 1) {   // y-edges (i, j; k) and (i + 1, j; k), interpolated along x
-            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
-            const double d0 = su[c][k][j + 1][i] - su[c][k][j][i];
-            const double d1 = su[c][k][j + 1][i + 1] - su[c][k][j][i + 1];
-            const double dd = d1 - d0;
-            say[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
-            say[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
-        } else {                 // z-edges (i, j, k) and (i + 1, j, k), interpolated along x
-            const int k = w / 40, j = (w / 8) % 5, i = w % 8;
-            const double d0 = su[c][k + 1][j][i] - su[c][k][j][i];
-            const double d1 = su[c][k + 1][j][i + 1] - su[c][k][j][i + 1];
-            const double dd = d1 - d0;
-            saz[c][k][j][i][0] = hex8::fmaT(G[0], dd, d0);
-            saz[c][k][j][i][1] = hex8::fmaT(G[1], dd, d0);
+    // (2) edge differences, each once per tile (two staged pairs share every one of them)
+    constexpr int nX = (kTZ + 1) * (kTY + 1) * kTX, nY = (kTZ + 1) * kTY * (kTX + 1), nZ = kTZ * (kTY + 1) * (kTX + 1);
+    for (int q = tid; q < 3 * (nX + nY + nZ); q += blockDim.x) {
+        const int c = q / (nX + nY + nZ), w = q % (nX + nY + nZ);
+        if (w < nX) {
+            const int k = w / ((kTY + 1) * kTX), j = (w / kTX) % (kTY + 1), i = w % kTX;
+            sdx[c][k][j][i] = su[c][k][j][i + 1] - su[c][k][j][i];
+        } else if (w < nX + nY) {
+            const int v = w - nX, k = v / (kTY * (kTX + 1)), j = (v / (kTX + 1)) % kTY, i = v % (kTX + 1);
+            sdy[c][k][j][i] = su[c][k][j + 1][i] - su[c][k][j][i];
+        } else {
+            const int v = w - nX - nY, k = v / ((kTY + 1) * (kTX + 1)), j = (v / (kTX + 1)) % (kTY + 1),
+                      i = v % (kTX + 1);
+            sdz[c][k][j][i] = su[c][k + 1][j][i] - su[c][k][j][i];
         }
     }
     __syncthreads();
-    // (3) one element per thread: second stage, constitutive law, transposed interpolation
+    // (3) the first interpolation stage, 3 directions x 3 components x 160 pairs
+    const double G[2] = {hex8::kG0, hex8::kG1};
+    for (int q = tid; q < 3 * 3 * 160; q += blockDim.x) {
+        const int dir = q / 480, c = (q / 160) % 3, w = q % 160;
+        // Neo-Hookean: the derivative of component c along direction c gets the 1 of F's diagonal here
+        // (once per staged pair instead of once per Gauss point), as element_force does in lerp2
+        const bool diag = MAT == OSAM_NEO_HOOKEAN && c == dir;
+        if (dir == 0) {          // x-edges (i; j, k) and (i; j + 1, k), interpolated along y
+            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
+            const double d0 = sdx[c][k][j][i], d1 = sdx[c][k][j + 1][i];
+            const double dd = d1 - d0, base = diag ? d0 + 1.0 : d0;
+            sax[c][k][j][i][0] = hex8::fmaT(G[0], dd, base);
+            sax[c][k][j][i][1] = hex8::fmaT(G[1], dd, base);
+        } else if (dir == 1) {   // y-edges (i, j; k) and (i + 1, j; k), interpolated along x
+            const int k = w / 32, j = (w / 8) % 4, i = w % 8;
+            const double d0 = sdy[c][k][j][i], d1 = sdy[c][k][j][i + 1];
+            const double dd = d1 - d0, base = diag ? d0 + 1.0 : d0;
+            say[c][k][j][i][0] = hex8::fmaT(G[0], dd, base);
+            say[c][k][j][i][1] = hex8::fmaT(G[1], dd, base);
+        } else {                 // z-edges (i, j, k) and (i + 1, j, k), interpolated along x
+            const int k = w / 40, j = (w / 8) % 5, i = w % 8;
+            const double d0 = sdz[c][k][j][i], d1 = sdz[c][k][j][i + 1];
+            const double dd = d1 - d0, base = diag ? d0 + 1.0 : d0;
+            saz[c][k][j][i][0] = hex8::fmaT(G[0], dd, base);
+            saz[c][k][j][i][1] = hex8::fmaT(G[1], dd, base);
+        }
+    }
+    __syncthreads();
+    // (4) one element per thread: second stage, constitutive law, transposed interpolation
     const int ti = tid % kTX, tj = (tid / kTX) % kTY, tk = tid / (kTX * kTY);
     const int ei = i0 + ti, ej = j0 + tj, ek = k0 + tk;
     if (ei >= I.nx || ej >= I.ny || ek >= I.nz) return;
@@ -175,15 +191,11 @@ __global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* _
             Gz[c][a][0] = hex8::fmaT(G[0], d, e0);
             Gz[c][a][1] = hex8::fmaT(G[1], d, e0);
         }
-    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
     double m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = 0.5 * kappa * I.w8; m2 = mu * I.w8; m3 = mu * I.w8 / 3.0;
-    } else {
-        m1 = lam * I.w8; m2 = mu * I.w8; m3 = 0.0;
-    }
+    if (I.lam_e || I.mu_e)
+        material_factors<MAT, double>(I.lam_e ? I.lam_e[e] : I.lam, I.mu_e ? I.mu_e[e] : I.mu, I.wq, I.wq3, m1, m2,
+                                      m3);
+    else { m1 = I.m1; m2 = I.m2; m3 = I.m3; }
     double F[3][8];
     element_force_grad<MAT, double>(Gx, Gy, Gz, m1, m2, m3, F);
     if (MODE == kAtomic) {
