@@ -47,8 +47,9 @@ UNIT = "element-updates/s"
 # the Gauss points 180 + 8 x 90 constitutive + 36 accumulation + 180 transposed interpolation +
 # 48 nodal accumulation + 8.
 FLOPS_PER_NH_ELEMENT = 1232
-# FP64 peak: recipe figure for the GB300 (nominal FP64 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 1.25
+# FP64 nominal figure of the recipe for the GB300 (1.25 TFLOP/s); the rooflines divide by the FP64
+# peak measured on the GPU itself (measure_fp64_peak) and give the fraction of this one beside it
+FP64_NOMINAL_TFLOPS = 1.25
 # double-float force: FP32-pipe thread-instructions per Neo-Hookean element (ncu smsp__inst_executed
 # x 32 / elements of the phased kernel) and the FP32 issue peak (152 SMs x 128 lanes x 2.07 GHz)
 F32X2_INST_PER_NH_ELEMENT = 12012
@@ -75,6 +76,31 @@ TANGENT_FLOPS_PER_NH_ELEMENT = 1832
 # FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
 # around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
 FLOPS_PER_SVK_ELEMENT = 1424
+
+
+# the measured FP64 peak of this run (set by measure_fp64_peak before any roofline is formed)
+FP64_PEAK = [FP64_NOMINAL_TFLOPS]
+
+
+def measure_fp64_peak(osam, local, repeats=10):
+    """The FP64 roofline denominator measured on this GPU: the best of `repeats` launches (~20 ms
+    each) of the library's FMA probe and of its FP64 tensor-core (mma.sync m8n8k4) probe, with the SM
+    clock sampled during them; the interleaved probe shows whether the two share one unit."""
+    clocks = ClockSampler(local)
+    clocks.start()
+    fma, _ = osam.fp64_probe(0, repeats, local)
+    mma, _ = osam.fp64_probe(1, repeats, local)
+    mix, _ = osam.fp64_probe(2, max(2, repeats // 2), local)
+    clk = clocks.stop()
+    best = float(max(fma.max(), mma.max()))
+    FP64_PEAK[0] = best
+    return {"tflops": best, "unit": "TFLOP/s", "repeats": repeats,
+            "fma_best": float(fma.max()), "fma_median": float(np.median(fma)),
+            "mma_best": float(mma.max()), "mma_median": float(np.median(mma)),
+            "fma_plus_mma_interleaved_best": float(mix.max()),
+            "sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "clock_reasons": clk["reasons"],
+            "nominal_tflops": FP64_NOMINAL_TFLOPS,
+            "kind": "measured: best of the FP64 FMA and FP64 tensor-core probes (osam_fp64_probe)"}
 
 
 def measured_hbm_gbs():
@@ -108,6 +134,16 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=5)
     ap.add_argument("--batched-plain-steps", type=int, default=1)
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain parameter sweep")
+    ap.add_argument("--no-large", action="store_true", help="skip the large FOM-OpInf-FOM chain")
+    ap.add_argument("--fp64-peak-repeats", type=int, default=10,
+                    help="launches per FP64 probe for the roofline denominator (0: skip the probes and divide by "
+                         "the nominal 1.25 TFLOP/s, for profiling runs)")
+    ap.add_argument("--large-only", action="store_true", help="run only the large-chain block (profiling runs)")
+    ap.add_argument("--large-n", type=int, default=96)
+    ap.add_argument("--large-nz", type=int, default=192)
+    ap.add_argument("--large-rank", type=int, default=128)
+    ap.add_argument("--large-snapshots", type=int, default=500)
+    ap.add_argument("--large-steps", type=int, default=5)
     ap.add_argument("--no-implicit", action="store_true", help="skip the implicit-FOM measurement")
     ap.add_argument("--implicit-only", action="store_true",
                     help="run only the implicit-FOM block (stand-in ROM operators): profiling runs")
@@ -490,13 +526,13 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
             "ms_per_step_host_loop": p_ms / steps,
             "tangent_time_share": ip["tangent_ms"] / p_ms if p_ms else None,
             "roofline": {"bound": "alu", "kernel": "k_tangent_lin_b (Neo-Hookean)", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak": FP64_PEAK[0], "unit": "TFLOP/s", "frac": achieved / FP64_PEAK[0],
                          "traffic": (TANGENT_TRAFFIC["bytes_per_launch"]
                                      if TANGENT_TRAFFIC["source_sha256"] == source_sha(TANGENT_SOURCES) else None),
                          "algorithmic_bytes_per_launch": ne * TANGENT_BYTES_PER_ELEMENT,
                          "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
                          "ms_per_launch": ip["tangent_ms"] / max(1, ip["tangent_launches"]),
-                         "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)"},
+                         "peak_kind": "of measured: FP64 peak of this GPU (fp64_peak block)"},
             "timing": "value: library CUDA events around each controller step, each one graph launch with the "
                       "Newton and CG loops as device-side WHILE nodes (L2 flushed between steps); roofline and "
                       "counts: a second pass of the same steps driven from the host with CUDA events around "
@@ -602,7 +638,7 @@ def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5,
                     f"(r_s={svk_fit['r_s']}, fitted on {svk_fit['n_snap']} snapshots of an SVK FOM-FOM run)",
         "fit_seconds": svk_fit["gpu_seconds"],
         "roofline": {"bound": "alu", "kernel": "k_force_*<SaintVenantKirchhoff>", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak": FP64_PEAK[0], "unit": "TFLOP/s", "frac": achieved / FP64_PEAK[0],
                      "flops_per_element": FLOPS_PER_SVK_ELEMENT,
                      "force_ms_per_launch": prof["force_ms"] / max(1, prof["force_launches"])}}
     # oracle beside each variant, on a small bar of the same kind (3x3x[8,8] FOMs, 20 substeps)
@@ -625,6 +661,118 @@ def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5,
             f"sample GPU {v['sample_gpu_value']:.3e} vs oracle {v['sample_oracle_value']:.3e}")
     out["note"] = (f"intervals_per_s: controller intervals of {T * 1e6:.0f} us advanced per second; "
                    "parity: tests/test_gpu_additive.py, test_gpu_mixed_dt.py, test_gpu_svk.py, test_gpu_cubic.py")
+    return out
+
+
+# FP32 FMA peak of the FP32-force variant (152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz)
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def train_large_rom(W, osam, torch, args, device, log):
+    """The middle ROM of the large chain: a seeded FOM-FOM-FOM training run of the same geometry
+    (controller steps of 4 substeps, one snapshot of the middle subdomain per step, double-float
+    force, snapshots kept on the device), then the library's opinf_fit of rank args.large_rank."""
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    amp = float(rng.uniform(0.5e-3, 1.0e-3))
+    spec = W.large_chain(args.large_n, args.large_nz, rom_middle=False, amplitude=amp, n_substeps=4)
+    dev = f"cuda:{device}"
+    free, sdof = W.subdomain_dof_masks(spec, 1)
+    fi = torch.from_numpy(np.flatnonzero(free)).to(dev)
+    si = torch.from_numpy(np.flatnonzero(sdof)).to(dev)
+    n_snap = args.large_snapshots
+    U = torch.empty((n_snap, fi.numel()), dtype=torch.float64, device=dev)
+    A = torch.empty_like(U)
+    S = torch.empty((n_snap, si.numel()), dtype=torch.float64, device=dev)
+    nn = spec.subdomains[1].n_nodes
+    bu = torch.empty((nn, 3), dtype=torch.float64, device=dev)
+    ba = torch.empty_like(bu)
+    prob = osam.Problem(spec, precision=osam.F32X2_FORCE, device=device)
+    t0 = time.time()
+    for k in range(n_snap):
+        prob.step()
+        prob.state(1, out=(bu, None, ba))
+        uf, af = bu.reshape(-1), ba.reshape(-1)
+        U[k] = uf[fi]
+        A[k] = af[fi]
+        S[k] = uf[si]
+    torch.cuda.synchronize()
+    prob.close()
+    train_s = time.time() - t0
+    t0 = time.time()
+    ops = osam.opinf_fit(U, A, S, r=args.large_rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=device)
+    fit_s = time.time() - t0
+    info = {"training_seconds": train_s, "fit_seconds": fit_s, "n_snap": n_snap, "n_dof": int(fi.numel()),
+            "n_sdof": int(si.numel()), "r": args.large_rank, "r_s": int(ops["r_s"]), "amplitude": amp}
+    del U, A, S
+    torch.cuda.empty_cache()
+    log(f"large chain: training run {n_snap} x 4 substeps in {train_s:.1f}s, opinf_fit r={args.large_rank} "
+        f"r_s={ops['r_s']} over {info['n_dof']} dofs in {fit_s:.1f}s")
+    return {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}, info
+
+
+def measure_large(W, osam, torch, flush, args, local, log, warmup=3):
+    """The large chain: two n x n x nz Neo-Hookean FOMs with the quadratic OpInf ROM (rank
+    args.large_rank, fitted on the GPU from the chain's own FOM-FOM-FOM training run) in the middle,
+    dt = 5e-7, controller steps of 20 substeps.  FP64 (the library's default graph-captured steps)
+    and the FP32-force variant (FP32 element force, FP64 state), each with its force kernel's
+    roofline from a host-driven pass with CUDA events around every force launch.  The FP32-force
+    rounding noise keeps the relative criterion above 1e-12, so that variant runs with its iteration
+    count fixed to the largest FP64 count (same work per step); beside them the oracle on a bounded
+    sample of the same chain."""
+    ops, info = train_large_rom(W, osam, torch, args, local, log)
+    out = {"workload": f"large_chain {args.large_n}x{args.large_n}x{args.large_nz} Neo-Hookean FOM - quadratic OpInf "
+                       f"ROM r={args.large_rank} (r_s={info['r_s']}, fitted on {info['n_snap']} snapshots of "
+                       f"{info['n_dof']} free dofs) - FOM, dt=5e-7, 20 substeps per controller step",
+           "unit": UNIT, "fit": info}
+    max_its = None
+    for name, prec in (("f64", osam.FP64), ("fp32_force", osam.FP32_FORCE)):
+        spec = W.large_chain(args.large_n, args.large_nz, rom_middle=True)
+        if max_its is not None:
+            spec.max_iters = max_its
+        prob = osam.Problem(spec, rom_ops={1: ops}, device=local, precision=prec)
+        ms, upd, its = _timed_steps(prob, torch, flush, args.large_steps, warmup)
+        p_ms, p_upd, _, prof = timed_pass(prob, torch, flush, 2, profile=True)
+        tuning = prob.tuning()
+        prob.close()
+        if max_its is None:
+            max_its = int(max(its))
+        per_launch = prof["force_ms"] / max(1, prof["force_launches"])
+        achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
+        peak = FP64_PEAK[0] if name == "f64" else FP32_FMA_PEAK_TFLOPS
+        out[name] = {"value": upd / (ms * 1e-3), "ms_per_step": ms / args.large_steps, "steps": args.large_steps,
+                     "warmup": warmup, "mean_iterations": float(np.mean(its)), "max_iterations": int(max(its)),
+                     "effective_rate": upd / (ms * 1e-3) / float(np.mean(its)),
+                     "value_host_loop": p_upd / (p_ms * 1e-3), "tuning": tuning,
+                     "roofline": {"bound": "alu", "kernel": "internal force (Neo-Hookean, %s)" % name,
+                                  "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                  "flops_per_element": FLOPS_PER_NH_ELEMENT, "elements_per_launch":
+                                  spec.subdomains[0].n_elements, "force_ms_per_launch": per_launch,
+                                  "force_time_share": prof["force_ms"] / p_ms,
+                                  "peak_kind": ("of measured: FP64 peak of this GPU (fp64_peak block)" if name == "f64"
+                                                else "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"),
+                                  "frac_of_nominal": (achieved / FP64_NOMINAL_TFLOPS if name == "f64" else None)}}
+        if name == "fp32_force":
+            out[name]["iterations"] = f"fixed at {max_its} (the largest FP64 count)"
+        log(f"large chain [{name}]: {out[name]['value']:.3e} element-updates/s, {ms / args.large_steps:.1f} ms/step, "
+            f"{np.mean(its):.1f} its, force {per_launch:.3f} ms/launch = {achieved:.3f} TFLOP/s")
+    # oracle on a bounded sample: the same chain, one controller step of one substep and one Schwarz
+    # iteration, seeded stand-in ROM operators of the fitted sizes (the set-up is not timed)
+    from oracle import oracle as O
+    spec = W.large_chain(args.large_n, args.large_nz, rom_middle=True, n_substeps=1)
+    spec.max_iters = 1
+    free, sdof = W.subdomain_dof_masks(spec, 1)
+    stand_in = W.synthetic_rom_operators(int(free.sum()), int(sdof.sum()), args.large_rank, info["r_s"],
+                                         W.SEED_BASE + 15)
+    ref = O.Problem(spec, rom_ops={1: stand_in})
+    t0 = time.process_time()
+    ref.step()
+    cpu_s = time.process_time() - t0
+    cpu_upd = 2 * spec.subdomains[0].n_elements
+    out["oracle"] = {"value": cpu_upd / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                     "sample": f"1 controller step of 1 substep x 1 Schwarz iteration of the same chain (stand-in ROM "
+                               f"operators of the fitted sizes), {cpu_s:.1f} s CPU"}
+    out["parity"] = ("1e-9 (FP64), 1e-5 (FP32 force) relative L2 vs the oracle on a truncated horizon of the full "
+                     "chain (tests/test_gpu_fullsize.py)")
     return out
 
 
@@ -781,6 +929,16 @@ def main():
     from paper_2511_20687_gb300 import workloads as W
 
     fit_info = None
+    fp64_peak = (measure_fp64_peak(osam, local, args.fp64_peak_repeats) if args.fp64_peak_repeats > 0 else
+                 {"tflops": FP64_NOMINAL_TFLOPS, "kind": "nominal (probes skipped)", "fma_best": float("nan"),
+                  "mma_best": float("nan"), "fma_plus_mma_interleaved_best": float("nan"), "sm_mhz": None})
+    log(f"FP64 peak: FMA {fp64_peak['fma_best']:.3f}, tensor-core MMA {fp64_peak['mma_best']:.3f}, interleaved "
+        f"{fp64_peak['fma_plus_mma_interleaved_best']:.3f} TFLOP/s at {fp64_peak['sm_mhz']} MHz")
+    if args.large_only:
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+        print(json.dumps({"large_chain": measure_large(W, osam, torch, flush, args, local, log),
+                          "fp64_peak": fp64_peak}), flush=True)
+        return
     if args.implicit_only:
         # profiling entry: the implicit-FOM block alone, with seeded stand-in ROM operators of the
         # fitted model's sizes and at most 3 Schwarz iterations per controller step
@@ -842,7 +1000,6 @@ def main():
                          "tuning": prob.tuning()}
         prob.close()
     head = results["f32x2" if head_prec == osam.F32X2_FORCE else "f64"]
-    fp64_meas = osam.fp64_peak_gflops(local) / 1e3
 
     def roofline(res, prec_name):
         prof = res["prof"]
@@ -852,12 +1009,15 @@ def main():
             same = (FORCE_TRAFFIC["source_sha256"] == source_sha()
                     and FORCE_TRAFFIC["tiled"] == bool(res["tuning"].get("tiled")))
             traffic = FORCE_TRAFFIC["bytes_per_launch"] if same else None
-            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+            return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK[0], "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK[0], "traffic": traffic,
                     "kernel": ("k_force_tile_b<NeoHookean, gather>" if res["tuning"].get("tiled")
                                else "k_force_b<NeoHookean, f64, %s>" % res["tuning"]["scatter"]),
-                    "peak_kind": "recipe nominal FP64 (1.25 TFLOP/s)", "fp64_fma_measured_tflops": fp64_meas,
-                    "frac_of_measured_fp64": achieved / fp64_meas, "force_ms_per_launch": per_launch,
+                    "peak_kind": "of measured: FP64 peak of this GPU (fp64_peak block)",
+                    "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
+                    "flops_per_element": FLOPS_PER_NH_ELEMENT, "elements_per_launch":
+                    prof["force_elements"] // max(1, prof["force_launches"]),
+                    "force_ms_per_launch": per_launch,
                     "force_time_share": prof["force_ms"] / res["prof_total_ms"]}
         # double-float force: FP32-pipe instruction issue is the binding unit
         achieved = F32X2_INST_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
@@ -877,6 +1037,9 @@ def main():
         fit_meas = measure_fit(fit_info, log)
         select_meas = measure_select(osam, fit_info, local, log)
         adjoint_meas = measure_adjoint(W, osam, local, log)
+    large_meas = None
+    if world == 1 and not args.no_large and not args.fom_only:
+        large_meas = measure_large(W, osam, torch, flush, args, local, log)
     next_meas = None
     if world == 1 and not args.no_implicit and rom_ops:
         implicit_meas = measure_implicit(W, osam, torch, flush, rom_ops, args, local, log)
@@ -933,8 +1096,8 @@ def main():
                 "gpu_launches": head["launches"],
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
                 "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
-                "adjoint": adjoint_meas, "implicit": implicit_meas, "next_rows": next_meas,
-                "hbm": hbm,
+                "adjoint": adjoint_meas, "implicit": implicit_meas, "next_rows": next_meas, "large_chain": large_meas,
+                "hbm": hbm, "fp64_peak": fp64_peak,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}
         print(json.dumps(line), flush=True)

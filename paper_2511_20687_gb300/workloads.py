@@ -205,11 +205,28 @@ def batched_samples(n_samples: int = 256, seed: int = SEED_BASE + 3, n_min: int 
     return out
 
 
-def large_chain(n: int = 96, nz: int = 192, rom_middle: bool = True) -> Problem:
-    """FOM / OpInf / FOM chain, FOM meshes n x n x nz Neo-Hookean, dt=5e-7 s, 10000 steps (controller 20)."""
+def large_chain(n: int = 96, nz: int = 192, rom_middle: bool = True, amplitude: float = 1e-3,
+                n_substeps: int = 20) -> Problem:
+    """FOM / OpInf / FOM chain, FOM meshes n x n x nz Neo-Hookean, dt=5e-7 s, 10000 steps (controller 20).
+    rom_middle=False gives the FOM-FOM-FOM run of the same geometry (the ROM's training run)."""
     kinds = ["fom", "rom" if rom_middle else "fom", "fom"]
-    return bar_chain(f"large_chain_{n}x{n}x{nz}", n, [nz, nz, nz], kinds, "nh", 1e9, 0.25, 1000.0, 1e-3, 5e-7, 20,
-                     n_controller_steps=500)
+    return bar_chain(f"large_chain_{n}x{n}x{nz}", n, [nz, nz, nz], kinds, "nh", 1e9, 0.25, 1000.0, amplitude, 5e-7,
+                     n_substeps, n_controller_steps=10000 // n_substeps)
+
+
+def subdomain_dof_masks(spec: Problem, i: int):
+    """(free, schwarz) boolean masks over the dofs (node-major, 3 components) of subdomain i: Schwarz
+    dofs are all components of the nodes a coupling into i feeds, free dofs are the rest minus the
+    clamped components (the ROM's dof sets, in increasing dof order)."""
+    sd = spec.subdomains[i]
+    schwarz = np.zeros(sd.n_nodes, bool)
+    for c in spec.couplings:
+        if c.dst == i:
+            schwarz |= np.asarray(c.nodes).astype(bool)
+    dm = np.zeros(sd.n_nodes, np.uint8) if sd.dirichlet is None else np.asarray(sd.dirichlet, np.uint8)
+    clamped = ((dm[:, None] >> np.arange(3, dtype=np.uint8)) & 1).astype(bool)
+    free = (~clamped & ~schwarz[:, None]).reshape(-1)
+    return free, np.repeat(schwarz, 3)
 
 
 def wave1d(n_elem: int = 1000, dt: Optional[float] = None, subdomains: bool = False, n_substeps: int = 10) -> Problem:
