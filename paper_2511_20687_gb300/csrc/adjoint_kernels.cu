@@ -14,48 +14,13 @@
 
 #include <cstdint>
 
+#include "hex8_math.cuh"
 #include "nh_tangent.cuh"
 #include "osam_internal.h"
 
 namespace osam {
 
 namespace {
-
-constexpr double kG0 = 0.21132486540518711775;
-constexpr double kG1 = 0.78867513459481288225;
-constexpr double kGd = 0.57735026918962576451;
-
-__device__ __forceinline__ void lerp2(const double D[2][2], double out[2][2]) {
-    double E[2][2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        double d = D[1][e] - D[0][e];
-        E[0][e] = fma(kG0, d, D[0][e]);
-        E[1][e] = fma(kG1, d, D[0][e]);
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        double d = E[q][1] - E[q][0];
-        out[q][0] = fma(kG0, d, E[q][0]);
-        out[q][1] = fma(kG1, d, E[q][0]);
-    }
-}
-
-__device__ __forceinline__ void lerp2T(const double S[2][2], double out[2][2]) {
-    double V[2][2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        double s = S[q][0] + S[q][1];
-        V[q][0] = fma(kGd, S[q][0], kG0 * s);
-        V[q][1] = s - V[q][0];
-    }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        double s = V[0][e] + V[1][e];
-        out[0][e] = fma(kGd, V[0][e], kG0 * s);
-        out[1][e] = s - out[0][e];
-    }
-}
 
 // scaled edge differences of a nodal field (see the forward kernel)
 __device__ __forceinline__ void edge_diffs(const double* x, int sn, long long sc, const int node[8], double invh,
@@ -78,7 +43,11 @@ __device__ __forceinline__ void edge_diffs(const double* x, int sn, long long sc
 
 using tangent::nh_tangent;
 
-template <int MAT>
+// One thread per element.  MODE kAtomic adds ubar into a.f ([3] x strided nodes); kGather writes the
+// element's 24 contributions to the element buffer a.fe [24][ne] (corner-major, component), which a
+// fixed-order gather sums per node (deterministic).  The transposed interpolation is the force's
+// Walsh-basis stage (hex8::walsh_transpose), so the material factors carry its 1/4.
+template <int MAT, int MODE>
 __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double* ybar, int ysn, long long ysc,
                                                   double* lam_bar, double* mu_bar, int accumulate) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -101,16 +70,11 @@ __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double
     double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2], Bx[3][2][2], By[3][2][2], Bz[3][2][2];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        lerp2(Dx[c], Gx[c]); lerp2(Dy[c], Gy[c]); lerp2(Dz[c], Gz[c]);
-        lerp2(Ex[c], Bx[c]); lerp2(Ey[c], By[c]); lerp2(Ez[c], Bz[c]);
+        hex8::lerp2(Dx[c], Gx[c]); hex8::lerp2(Dy[c], Gy[c]); hex8::lerp2(Dz[c], Gz[c]);
+        hex8::lerp2(Ex[c], Bx[c]); hex8::lerp2(Ey[c], By[c]); hex8::lerp2(Ez[c], Bz[c]);
     }
     double m1, m2, m3;
-    if (MAT == OSAM_NEO_HOOKEAN) {
-        const double kappa = lam + (2.0 / 3.0) * mu;
-        m1 = 0.5 * kappa * a.w8; m2 = mu * a.w8; m3 = mu * a.w8 / 3.0;
-    } else {
-        m1 = lam * a.w8; m2 = mu * a.w8; m3 = 0.0;
-    }
+    hex8::material_factors<MAT, double>(lam, mu, a.wq, a.wq3, m1, m2, m3);
     double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
     double lb = 0.0, mb = 0.0;
 #pragma unroll
@@ -129,7 +93,7 @@ __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double
                     double pk, pm;
                     nh_tangent(Hm, Gm, m1, m2, m3, dP, pk, pm);
                     lb += pk;
-                    mb += pm + (2.0 / 3.0) * pk;
+                    mb = fma(2.0 / 3.0, pk, mb + pm);
                 } else {
                     const double trG = Gm[0][0] + Gm[1][1] + Gm[2][2];
                     const double trH = Hm[0][0] + Hm[1][1] + Hm[2][2];
@@ -139,9 +103,9 @@ __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double
 #pragma unroll
                         for (int y = 0; y < 3; ++y) {
                             dP[x][y] = m2 * (Gm[x][y] + Gm[y][x]) + (x == y ? m1 * trG : 0.0);
-                            symHG += (Hm[x][y] + Hm[y][x]) * Gm[x][y];
+                            symHG = fma(Hm[x][y] + Hm[y][x], Gm[x][y], symHG);
                         }
-                    lb += trH * trG;
+                    lb = fma(trH, trG, lb);
                     mb += symHG;
                 }
 #pragma unroll
@@ -151,28 +115,20 @@ __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double
                     if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
                 }
             }
-    double* ub = static_cast<double*>(a.f);
+    double Fe[3][8];
+    hex8::walsh_transpose<double>(Sx, Sy, Sz, Fe);
+    if (MODE == kAtomic) {
+        double* ub = static_cast<double*>(a.f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double Fc[8];
-        double Tm[2][2];
-        lerp2T(Sx[c], Tm);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
+            for (int c8 = 0; c8 < 8; ++c8) atomicAdd(ub + (long long)c * a.fsc + (long long)node[c8] * a.fsn, Fe[c][c8]);
+    } else {
+        double* fe = static_cast<double*>(a.fe);
 #pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
-        lerp2T(Sy[c], Tm);
+        for (int c8 = 0; c8 < 8; ++c8)
 #pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
-        lerp2T(Sz[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) atomicAdd(ub + (long long)c * a.fsc + (long long)node[c8] * a.fsn, Fc[c8]);
+            for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * a.ne + e] = Fe[c][c8];
     }
     // w detJ = h^3/8 per Gauss point; Gbar above is the physical gradient
     const double vol8 = a.w8 / a.invh;
@@ -182,12 +138,18 @@ __global__ void __launch_bounds__(128) k_hex8_vjp(const ElemArgs a, const double
 
 }  // namespace
 
-cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
+cudaError_t launch_hex8_vjp(int material, int scatter, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
                             double* lam_bar, double* mu_bar, int acc, cudaStream_t s) {
     if (a.ne <= 0) return cudaSuccess;
     const int g = grid_for(a.ne, 128);
-    if (material == OSAM_NEO_HOOKEAN) k_hex8_vjp<OSAM_NEO_HOOKEAN><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
-    else k_hex8_vjp<OSAM_LINEAR_ELASTIC><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+    const bool at = scatter == kAtomic;
+    if (material == OSAM_NEO_HOOKEAN) {
+        if (at) k_hex8_vjp<OSAM_NEO_HOOKEAN, kAtomic><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+        else k_hex8_vjp<OSAM_NEO_HOOKEAN, kGather><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+    } else {
+        if (at) k_hex8_vjp<OSAM_LINEAR_ELASTIC, kAtomic><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+        else k_hex8_vjp<OSAM_LINEAR_ELASTIC, kGather><<<g, 128, 0, s>>>(a, ybar, ysn, ysc, lam_bar, mu_bar, acc);
+    }
     return cudaGetLastError();
 }
 
@@ -197,28 +159,30 @@ namespace osam {
 namespace {
 
 // reverse of the corrector v' = v + dt/2 (a + a'), a' = -M^-1 f(u'):  abar' += dt/2 vbar;
-// y = -M^-1 abar' (free dofs), cleared VJP accumulator
+// y = -M^-1 abar' (free dofs)
 __global__ void k_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb,
-                              double* ab, double* y, double* tmp) {
+                              double* ab, double* y) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
     const int c = t / nn, n = t % nn;
-    tmp[t] = 0.0;
     if (clamp[n] & (1 << c)) { y[t] = 0.0; ab[t] = 0.0; return; }
     const double a = fma(0.5 * dt, vb[t], ab[t]);
     ab[t] = a;
     y[t] = -a * minv[n];
 }
 
-// ubar' += VJP; then the adjoints at the previous step:
-//   abar = dt/2 vbar' + dt^2/2 ubar',  vbar = vbar' + dt ubar',  ubar = ubar'
-__global__ void k_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
-                               double* ab) {
+// ubar' += VJP (gathered from the element buffer in a fixed order); then the adjoints at the previous
+// step:  abar = dt/2 vbar' + dt^2/2 ubar',  vbar = vbar' + dt ubar',  ubar = ubar'
+__global__ void k_adjoint_post(int nx, int ny, int nz, double dt, const uint8_t* clamp, const double* fe, double* ub,
+                               double* vb, double* ab) {
+    const int nn = (nx + 1) * (ny + 1) * (nz + 1);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 3 * nn) return;
     const int c = t / nn, n = t % nn;
     if (clamp[n] & (1 << c)) { ub[t] = 0.0; vb[t] = 0.0; ab[t] = 0.0; return; }
-    const double u = ub[t] + tmp[t];
+    const int i = n % (nx + 1), q = n / (nx + 1);
+    const double g = hex8::gather_force(fe, nx, ny, nz, nx * ny * nz, i, q % (ny + 1), q / (ny + 1), c);
+    const double u = ub[t] + g;
     const double v = vb[t];
     ub[t] = u;
     ab[t] = fma(0.5 * dt * dt, u, 0.5 * dt * v);
@@ -228,14 +192,15 @@ __global__ void k_adjoint_post(int nn, double dt, const uint8_t* clamp, const do
 }  // namespace
 
 cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb, double* ab,
-                               double* y, double* tmp, cudaStream_t s) {
-    k_adjoint_pre<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, minv, vb, ab, y, tmp);
+                               double* y, cudaStream_t s) {
+    k_adjoint_pre<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, minv, vb, ab, y);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
-                                double* ab, cudaStream_t s) {
-    k_adjoint_post<<<grid_for(3LL * nn, 256), 256, 0, s>>>(nn, dt, clamp, tmp, ub, vb, ab);
+cudaError_t launch_adjoint_post(int nx, int ny, int nz, double dt, const uint8_t* clamp, const double* fe, double* ub,
+                                double* vb, double* ab, cudaStream_t s) {
+    const long long nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+    k_adjoint_post<<<grid_for(3 * nn, 256), 256, 0, s>>>(nx, ny, nz, dt, clamp, fe, ub, vb, ab);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -453,7 +454,8 @@ int osam_hex8_force_vjp(int nx, int ny, int nz, double h, int material, double l
     if (cudaMemsetAsync(ubar, 0, sizeof(double) * 3 * nn, s) != cudaSuccess) return OSAM_ECUDA;
     ElemArgs a = standalone_args(nx, ny, nz, h, lambda, mu, lambda_e, mu_e, u);
     a.f = ubar;
-    return launch_hex8_vjp(material, a, ybar, 3, 1, lambda_bar, mu_bar, 0, s) == cudaSuccess ? OSAM_OK : OSAM_ECUDA;
+    return launch_hex8_vjp(material, kAtomic, a, ybar, 3, 1, lambda_bar, mu_bar, 0, s) == cudaSuccess ? OSAM_OK
+                                                                                              : OSAM_ECUDA;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -480,7 +482,7 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     pd.n_substeps = 1;
     pd.max_iters = 1;
     pd.precision = OSAM_FP64;
-    pd.scatter = OSAM_SCATTER_ATOMIC;
+    pd.scatter = OSAM_SCATTER_GATHER;   // element buffer + fixed-order gather: bitwise repeatable gradients
     pd.stream = d->stream;
     pd.device = d->device;
     osam_ctx* raw = nullptr;
@@ -501,16 +503,15 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     double* vb = ctx->alloc<double>(n3);
     double* ab = ctx->alloc<double>(n3);
     double* y = ctx->alloc<double>(n3);
-    double* tmp = ctx->alloc<double>(n3);
     double* glam = ctx->alloc<double>(ne);
     double* gmu = ctx->alloc<double>(ne);
-    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(tmp); CKA(glam); CKA(gmu);
+    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(glam); CKA(gmu);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    // one explicit step in place on (u[0], v, a)
+    // one explicit step in place on (u[0], v, a), deterministic element-buffer scatter
     auto step = [&](double* u_store) -> int {
-        CK(launch_node_b(F, nullptr, kAtomic, -1, 1, 1, F.u[0], F.u[1], dt, ctx->stream));
-        CK(launch_force_b(F, nullptr, kAtomic, ctx->stream));
-        CK(launch_node_b(F, nullptr, kAtomic, 1, -1, 0, F.u[1], F.u[0], dt, ctx->stream));
+        CK(launch_node_b(F, nullptr, kGather, -1, 1, 1, F.u[0], F.u[1], dt, ctx->stream));
+        CK(launch_force_b(F, nullptr, kGather, ctx->stream));
+        CK(launch_node_b(F, nullptr, kGather, 1, -1, 0, F.u[1], F.u[0], dt, ctx->stream));
         CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         return OSAM_OK;
@@ -529,10 +530,58 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
         CK(cudaMemcpyAsync(F.a, base + 2 * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
         return OSAM_OK;
     };
+    ElemArgs va{};
+    va.nx = I.nx; va.ny = I.ny; va.nz = I.nz; va.ne = ne;
+    va.invh = I.invh; va.w8 = I.w8; va.wq = I.wq; va.wq3 = I.wq3;
+    va.lam_e = I.lam_e; va.mu_e = I.mu_e;
+    va.usn = 1; va.usc = nn;
+    va.fe = F.fe;
+    // reverse of step t + 1 (state u_{t+1} stored at useg[t + 1 - t0])
+    auto reverse = [&](int t, int t0) -> int {
+        CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, ctx->stream));
+        va.u = useg + (size_t)(t + 1 - t0) * n3;
+        CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, ctx->stream));
+        CK(launch_adjoint_post(I.nx, I.ny, I.nz, dt, F.clamp, static_cast<const double*>(F.fe), ub, vb, ab, ctx->stream));
+        return OSAM_OK;
+    };
+    // A full segment of Cp steps is the same sequence of launches every time (the checkpoint is loaded
+    // outside it and the segment buffer is reused), so the forward sweep, the recomputation and the
+    // reverse sweep of a segment are each captured once as a CUDA graph and replayed; a partial last
+    // segment runs from the host.
+    struct Graphs {
+        cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
+        ~Graphs() { for (auto x : g) if (x) cudaGraphExecDestroy(x); }
+    } graphs;
+    auto capture = [&](int which, const std::function<int()>& body) -> int {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = body();
+        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+        if (rc) { if (gr) cudaGraphDestroy(gr); return rc; }
+        CK(e);
+        const cudaError_t ei = cudaGraphInstantiate(&graphs.g[which], gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ei);
+        return OSAM_OK;
+    };
+    const bool full = T >= Cp;
+    if (full) {
+        RET(capture(0, [&]() -> int { for (int t = 0; t < Cp; ++t) RET(step(nullptr)); return OSAM_OK; }));
+        RET(capture(1, [&]() -> int {
+            CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+            for (int t = 1; t <= Cp; ++t) RET(step(useg + (size_t)t * n3));
+            return OSAM_OK;
+        }));
+        RET(capture(2, [&]() -> int { for (int t = Cp - 1; t >= 0; --t) RET(reverse(t, 0)); return OSAM_OK; }));
+    }
     RET(save_ck(0));
-    for (int t = 1; t <= T; ++t) {
-        RET(step(nullptr));
-        if (t % Cp == 0) RET(save_ck(t / Cp));
+    for (int t0 = 0; t0 < T; t0 += Cp) {
+        if (t0 + Cp <= T) {
+            CK(cudaGraphLaunch(graphs.g[0], ctx->stream));
+        } else {
+            for (int t = t0 + 1; t <= T; ++t) RET(step(nullptr));
+        }
+        if ((t0 + Cp) <= T) RET(save_ck((t0 + Cp) / Cp));
     }
     // J = w . u_T
     RET(upload(ctx, ctx->scratch, d->w, sizeof(double) * n3));
@@ -544,30 +593,24 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     CK(cudaStreamSynchronize(ctx->stream));
     double J = 0.0;
     for (long long q = 0; q < n3; ++q) J += wh[q] * uh[q];
-    ElemArgs va{};
-    va.nx = I.nx; va.ny = I.ny; va.nz = I.nz; va.ne = ne;
-    va.invh = I.invh; va.w8 = I.w8;
-    va.lam_e = I.lam_e; va.mu_e = I.mu_e;
-    va.usn = 1; va.usc = nn; va.fsn = 1; va.fsc = nn;
-    va.f = tmp;
     for (int seg = (T - 1) / Cp; seg >= 0 && T > 0; --seg) {
         const int t0 = seg * Cp, t1 = std::min(T, t0 + Cp);
         RET(load_ck(seg));
-        CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        for (int t = t0 + 1; t <= t1; ++t) RET(step(useg + (size_t)(t - t0) * n3));
-        for (int t = t1 - 1; t >= t0; --t) {
-            CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
-            va.u = useg + (size_t)(t + 1 - t0) * n3;
-            CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
-            CK(launch_adjoint_post(nn, dt, F.clamp, tmp, ub, vb, ab, ctx->stream));
+        if (t1 - t0 == Cp) {
+            CK(cudaGraphLaunch(graphs.g[1], ctx->stream));
+            CK(cudaGraphLaunch(graphs.g[2], ctx->stream));
+        } else {
+            CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+            for (int t = t0 + 1; t <= t1; ++t) RET(step(useg + (size_t)(t - t0) * n3));
+            for (int t = t1 - 1; t >= t0; --t) RET(reverse(t, t0));
         }
     }
     // a_0 = -M^-1 f(u_0)
-    CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, tmp, ctx->stream));
+    CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, ctx->stream));
     RET(load_ck(0));
     va.u = F.u[0];
-    CK(launch_hex8_vjp(F.material, va, y, 1, nn, glam, gmu, 1, ctx->stream));
-    CK(launch_adjoint_post(nn, 0.0, F.clamp, tmp, ub, vb, ab, ctx->stream));
+    CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, ctx->stream));
+    CK(launch_adjoint_post(I.nx, I.ny, I.nz, 0.0, F.clamp, static_cast<const double*>(F.fe), ub, vb, ab, ctx->stream));
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
