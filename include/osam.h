@@ -375,6 +375,12 @@ OSAM_API int opinf_select(const osam_fit_input* in, const osam_select_input* sel
                           osam_fit_output* out);
 /* Message of the calling thread's last failed opinf_fit / opinf_select. */
 OSAM_API const char* osam_fit_last_error(void);
+/* Accounting of the fit's device contractions on the calling host thread (a measurement hook; the
+ * paper has no counterpart).  enable = 1 resets the counters and turns it on: every GEMM of a later
+ * opinf_fit / opinf_select on this thread is bracketed by CUDA events and waited for (slower fits).
+ * enable = 0 turns it off.  Either call returns, through the non-NULL pointers, the event time in ms,
+ * the flops (2 m n k per product) and the number of GEMMs since the last reset. */
+OSAM_API int osam_fit_profile(int enable, double* gemm_ms, double* gemm_flops, long long* gemm_launches);
 
 /* ------------------------------------------------------------------------------------------------
  * Adjoint of the explicit single-domain rollout (gradients through the central-difference scheme

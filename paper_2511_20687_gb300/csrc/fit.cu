@@ -560,3 +560,7 @@ extern "C" OSAM_API int opinf_select(const osam_fit_input* in, const osam_select
 }
 
 extern "C" OSAM_API const char* osam_fit_last_error(void) { return g_fit_error.c_str(); }
+
+extern "C" OSAM_API int osam_fit_profile(int enable, double* gemm_ms, double* gemm_flops, long long* gemm_launches) {
+    return osam::gemm_profile(enable, gemm_ms, gemm_flops, gemm_launches);
+}

@@ -276,6 +276,8 @@ cudaError_t launch_build_Rt(int nrow, int r, const int* dnode_local, const doubl
                             const int* srow, const double* Phi, double* Rt, int* err, cudaStream_t s);
 
 // dense helpers (fit)
+// GEMM accounting of the fit (osam_fit_profile)
+int gemm_profile(int enable, double* ms, double* flops, long long* launches);
 cudaError_t launch_gemm_tn(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C,
                            int ldc, double alpha, double beta, cudaStream_t s);
 cudaError_t launch_gemm_nn(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C,
@@ -294,12 +296,12 @@ cudaError_t launch_select_rollout(int nl, int r, int d, int nq, int nc, int rs, 
                                   int k, double dt, double* phi, double* num, double* den, cudaStream_t s);
 
 // adjoint (adjoint_kernels.cu)
-cudaError_t launch_hex8_vjp(int material, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
-                            double* lam_bar, double* mu_bar, int accumulate, cudaStream_t s);
+cudaError_t launch_hex8_vjp(int material, int scatter, const ElemArgs& a, const double* ybar, int ysn, long long ysc,
+                            double* lam_bar, double* mu_bar, int acc, cudaStream_t s);
 cudaError_t launch_adjoint_pre(int nn, double dt, const uint8_t* clamp, const double* minv, const double* vb, double* ab,
-                               double* y, double* tmp, cudaStream_t s);
-cudaError_t launch_adjoint_post(int nn, double dt, const uint8_t* clamp, const double* tmp, double* ub, double* vb,
-                                double* ab, cudaStream_t s);
+                               double* y, cudaStream_t s);
+cudaError_t launch_adjoint_post(int nx, int ny, int nz, double dt, const uint8_t* clamp, const double* fe, double* ub,
+                                double* vb, double* ab, cudaStream_t s);
 
 // message returned by osam_last_error(NULL) on the calling thread
 void set_thread_error(const std::string& msg);

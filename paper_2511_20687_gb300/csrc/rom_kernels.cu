@@ -150,11 +150,45 @@ __global__ void k_gemm_reduce(int m, int n, int nsplit, const double* __restrict
     *cp = alpha * s + (beta != 0.0 ? beta * *cp : 0.0);
 }
 
-// Split the reduction when the output tiles alone cannot fill the GPU (two blocks per SM wanted)
-// and the reduction is long: chunks of at least 512 k, a multiple of the k tile.
+// Optional accounting of the fit's contractions (osam_fit_profile): CUDA events around every GEMM
+// (both kernels of a split reduction), its 2 m n k flops, per host thread.  Off by default; when on,
+// each GEMM waits for its end event, so the fit runs slower than without it.
+struct GemmProfile {
+    bool on = false;
+    double ms = 0.0, flops = 0.0;
+    long long launches = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+thread_local GemmProfile g_gemm_prof;
+
+cudaError_t launch_gemm_impl(int m, int n, int k, const double* A, long long ai, long long ak, const double* B,
+                             long long bk, long long bj, double* C, long long ldc, double alpha, double beta,
+                             cudaStream_t s);
+
 cudaError_t launch_gemm(int m, int n, int k, const double* A, long long ai, long long ak, const double* B,
                         long long bk, long long bj, double* C, long long ldc, double alpha, double beta,
                         cudaStream_t s) {
+    GemmProfile& P = g_gemm_prof;
+    if (!P.on || m <= 0 || n <= 0) return launch_gemm_impl(m, n, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, s);
+    cudaError_t e = cudaEventRecord(P.e0, s);
+    if (e == cudaSuccess) e = launch_gemm_impl(m, n, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, s);
+    if (e == cudaSuccess) e = cudaEventRecord(P.e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(P.e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, P.e0, P.e1);
+    if (e == cudaSuccess) {
+        P.ms += ms;
+        P.flops += 2.0 * m * (double)n * k;
+        P.launches += 1;
+    }
+    return e;
+}
+
+// Split the reduction when the output tiles alone cannot fill the GPU (two blocks per SM wanted)
+// and the reduction is long: chunks of at least 512 k, a multiple of the k tile.
+cudaError_t launch_gemm_impl(int m, int n, int k, const double* A, long long ai, long long ak, const double* B,
+                             long long bk, long long bj, double* C, long long ldc, double alpha, double beta,
+                             cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const long long tiles = (long long)grid_for(n, TN) * grid_for(m, TM);
     int dev = 0, sms = 152;
@@ -337,6 +371,20 @@ cudaError_t launch_build_Rt(int nrow, int r, const int* dnode_local, const doubl
     dim3 g(grid_for(3LL * nrow, 128), r);
     k_build_Rt<<<g, 128, 0, s>>>(nrow, r, dnode_local, dw, dof_free, srow, Phi, Rt, err);
     return cudaGetLastError();
+}
+
+int gemm_profile(int enable, double* ms, double* flops, long long* launches) {
+    GemmProfile& P = g_gemm_prof;
+    if (enable) {
+        if (!P.e0 && (cudaEventCreate(&P.e0) != cudaSuccess || cudaEventCreate(&P.e1) != cudaSuccess))
+            return OSAM_ECUDA;
+        P.ms = 0.0; P.flops = 0.0; P.launches = 0;
+    }
+    P.on = enable != 0;
+    if (ms) *ms = P.ms;
+    if (flops) *flops = P.flops;
+    if (launches) *launches = P.launches;
+    return OSAM_OK;
 }
 
 // row-major helpers: C[m][n] (ldc) = alpha * A^T B, A is [k][m] (lda), B is [k][n] (ldb)

@@ -30,7 +30,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_fp64_probe", "osam_hex8_force_noalloc", "osam_batch_init",
             "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
             "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
-            "osam_set_graph", "osam_tuning", "opinf_select"]
+            "osam_set_graph", "osam_tuning", "opinf_select", "osam_fit_profile"]
 
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
@@ -135,6 +135,7 @@ def load():
     L.osam_implicit_profile.argtypes = [_vp, _dp] + [C.POINTER(C.c_longlong)] * 4
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
     L.osam_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
+    L.osam_fit_profile.argtypes = [C.c_int, _dp, _dp, C.POINTER(C.c_longlong)]
     L.osam_batch_init.argtypes = [C.c_int, C.POINTER(ProblemDesc), C.POINTER(_vp)]
     L.osam_batch_step.argtypes = [_vp, C.POINTER(StepReport), C.POINTER(StepReport)]
     L.osam_num_instances.argtypes = [_vp]
@@ -521,3 +522,10 @@ def fp64_probe(kind=0, repeats=10, device=0):
     ms = np.zeros(repeats)
     _check(load().osam_fp64_probe(device, kind, repeats, t.ctypes.data_as(_dp), ms.ctypes.data_as(_dp)))
     return t, ms
+
+
+def fit_profile(enable: bool) -> dict:
+    """Turn the accounting of the fit's GEMMs on (resetting it) or off; returns the totals so far."""
+    ms, fl, n = C.c_double(), C.c_double(), C.c_longlong()
+    _check(load().osam_fit_profile(int(enable), C.byref(ms), C.byref(fl), C.byref(n)))
+    return {"gemm_ms": ms.value, "gemm_flops": fl.value, "gemm_launches": n.value}
