@@ -56,8 +56,8 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "b5b3fee699d80ead49f9c330a5c1956a2516f6f06efc65685b9ceb2d9d109b2d", "bytes_per_launch": 3.56992e6,
-                 "tiled": True}
+FORCE_TRAFFIC = {"source_sha256": "f9b33758e4465a68a7d1c8b8d8470f1976b96f1393496e0abe00cbbbb4491359",
+                 "bytes_per_launch": 3.567104e6, "tiled": True}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
@@ -80,6 +80,7 @@ FLOPS_PER_SVK_ELEMENT = 1424
 
 # the measured FP64 peak of this run (set by measure_fp64_peak before any roofline is formed)
 FP64_PEAK = [FP64_NOMINAL_TFLOPS]
+FP64_PEAK_KIND = ["of nominal: the recipe's 1.25 TFLOP/s (FP64 probes skipped)"]
 
 
 def measure_fp64_peak(osam, local, repeats=10):
@@ -94,6 +95,7 @@ def measure_fp64_peak(osam, local, repeats=10):
     clk = clocks.stop()
     best = float(max(fma.max(), mma.max()))
     FP64_PEAK[0] = best
+    FP64_PEAK_KIND[0] = "of measured: FP64 peak of this GPU (fp64_peak block)"
     return {"tflops": best, "unit": "TFLOP/s", "repeats": repeats,
             "fma_best": float(fma.max()), "fma_median": float(np.median(fma)),
             "mma_best": float(mma.max()), "mma_median": float(np.median(mma)),
@@ -101,6 +103,27 @@ def measure_fp64_peak(osam, local, repeats=10):
             "sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "clock_reasons": clk["reasons"],
             "nominal_tflops": FP64_NOMINAL_TFLOPS,
             "kind": "measured: best of the FP64 FMA and FP64 tensor-core probes (osam_fp64_probe)"}
+
+
+def host_cpu():
+    """CPU model and logical core count of the host the oracle legs run on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        if model is None:   # Arm hosts: implementer / part numbers only
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
 
 
 def measured_hbm_gbs():
@@ -132,13 +155,17 @@ def parse():
     ap.add_argument("--batched-samples", type=int, default=256)
     ap.add_argument("--batched-snapshots", type=int, default=100)
     ap.add_argument("--batched-steps", type=int, default=5)
-    ap.add_argument("--batched-plain-steps", type=int, default=1)
+    ap.add_argument("--batched-plain-steps", type=int, default=0,
+                    help="timed steps of the one-context-per-sample arm (0: as many as the batched arm)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain parameter sweep")
     ap.add_argument("--no-large", action="store_true", help="skip the large FOM-OpInf-FOM chain")
     ap.add_argument("--fp64-peak-repeats", type=int, default=10,
                     help="launches per FP64 probe for the roofline denominator (0: skip the probes and divide by "
                          "the nominal 1.25 TFLOP/s, for profiling runs)")
     ap.add_argument("--large-only", action="store_true", help="run only the large-chain block (profiling runs)")
+    ap.add_argument("--fit-only", action="store_true",
+                    help="profiling entry: one opinf_fit of seeded synthetic snapshots of the headline size "
+                         "(--snapshots x 403,440 free dofs, 5,043 Schwarz dofs, rank --rank), no training run")
     ap.add_argument("--large-n", type=int, default=96)
     ap.add_argument("--large-nz", type=int, default=192)
     ap.add_argument("--large-rank", type=int, default=128)
@@ -324,68 +351,130 @@ def train_batched_roms(W, osam, torch, specs_ff, snapshots, r, device, log, chun
     return ops, ranks
 
 
-def measure_batched(W, osam, torch, flush, args, device, log):
+def measure_batched(W, osam, torch, flush, args, device, log, rank=0, world=1):
     """Batched vs plain on the parameter-sweep workload: the same samples (FOM / OpInf pairs) advanced
-    by one batched context (graph-captured step) and by one context per sample, run one after another."""
-    specs = W.batched_samples(n_samples=args.batched_samples, rom=True)
-    ops, ranks = train_batched_roms(W, osam, torch, W.batched_samples(n_samples=args.batched_samples, rom=False),
-                                    args.batched_snapshots, 32, device, log)
+    by one batched context (graph-captured step) and by one context per sample, run one after another.
+    Under torchrun the samples are sharded over the ranks by element count (shard_samples): each rank
+    trains and advances its own, with no exchange on the data path; the per-instance reports are
+    gathered at the end, time is the maximum over ranks and the element-updates the sum."""
+    import torch.distributed as dist
+    multi = world > 1
+
+    def barrier():
+        if multi:
+            dist.barrier()
+
+    specs_all = W.batched_samples(n_samples=args.batched_samples, rom=True)
+    ff_all = W.batched_samples(n_samples=args.batched_samples, rom=False)
+    mine = shard_samples([sp.subdomains[0].n_elements for sp in specs_all], world)[rank]
+    specs = [specs_all[i] for i in mine]
+    ops, ranks = train_batched_roms(W, osam, torch, [ff_all[i] for i in mine], args.batched_snapshots, 32, device,
+                                    log)
     batch = osam.Batch(specs, rom_ops=ops, device=device)
     for _ in range(3):
         batch.step()
     torch.cuda.synchronize()
     dev_ms, upd, wall, its = 0.0, 0, 0.0, []
+    per_inst = {i: [] for i in mine}
     for _ in range(args.batched_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         per, tot = batch.step()
+        torch.cuda.synchronize()
+        barrier()
         wall += time.perf_counter() - t0
         dev_ms += tot["elapsed_ms"]
         upd += tot["element_updates"]
         its += [p["iterations"] for p in per]
+        for i, p in zip(mine, per):
+            per_inst[i].append((p["status"], p["iterations"]))
     tuning = batch.tuning()
+    # the batched force kernel's roofline: one more step driven from the host with CUDA events around
+    # every force launch
+    batch.profile(True)
+    batch.set_graph(False)
+    batch.step()
+    bprof = batch.profile_read()
+    batch.profile(False)
     batch.close()
+    bach_force = FLOPS_PER_NH_ELEMENT * bprof["force_elements"] / (bprof["force_ms"] * 1e-3) / 1e12
+    # the same samples with the tiled force kernel forced (the autotuner's choice is timed against it)
+    tb = osam.Batch(specs, rom_ops=ops, device=device, scatter=osam.SCATTER_GATHER_TILED)
+    tb.step()
+    t_ms, t_upd = 0.0, 0
+    for _ in range(2):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        _, tt = tb.step()
+        t_ms += tt["elapsed_ms"]
+        t_upd += tt["element_updates"]
+    tb.close()
     singles = [osam.Problem(sp, rom_ops=o, device=device) for sp, o in zip(specs, ops)]
     for p in singles:
         p.step()
     torch.cuda.synchronize()
     p_ms, p_upd, p_wall = 0.0, 0, 0.0
-    for _ in range(args.batched_plain_steps):
+    plain_steps = args.batched_plain_steps or args.batched_steps
+    for _ in range(plain_steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
+        barrier()
         t0 = time.perf_counter()
         for p in singles:
             r = p.step()
             p_ms += r["elapsed_ms"]
             p_upd += r["element_updates"]
+        torch.cuda.synchronize()
+        barrier()
         p_wall += time.perf_counter() - t0
     for p in singles:
         p.close()
-    n_el = sum(sp.subdomains[0].n_elements for sp in specs)
-    # the oracle on a bounded sample of the same sweep: the first two samples, one controller step of
-    # one Schwarz iteration each, their fitted ROMs
-    from oracle import oracle as O
-    o_upd, o_s = 0, 0.0
-    for sp, o in list(zip(specs, ops))[:2]:
-        sp1 = sp
-        sp1.max_iters = 1
-        ref = O.Problem(sp1, rom_ops=o)
-        t0 = time.process_time()
-        ref.step()
-        o_s += time.process_time() - t0
-        o_upd += sp1.n_substeps * sp1.subdomains[0].n_elements
-    return {"workload": f"{len(specs)} FOM / OpInf(r=32) pairs, n x n x 2n Neo-Hookean FOM, n ~ U{{8..32}}, "
-                        f"{n_el} FOM elements in total, ROMs fitted on {args.batched_snapshots} snapshots each",
-            "rom_ranks": {"32": sum(x == 32 for x in ranks), "below_32": sum(x < 32 for x in ranks)},
-            "steps": args.batched_steps, "value": upd / wall, "value_device": upd / (dev_ms * 1e-3),
-            "plain_steps": args.batched_plain_steps, "plain_value": p_upd / p_wall,
-            "plain_value_device": p_upd / (p_ms * 1e-3), "speedup": (upd / wall) / (p_upd / p_wall),
-            "mean_iterations": float(np.mean(its)), "max_iterations": int(max(its)), "unit": UNIT,
-            "oracle_value": o_upd / o_s, "oracle_cores": 1,
-            "oracle_sample": f"samples 0-1, one controller step of one Schwarz iteration each, {o_s:.1f} s CPU",
-            "tuning": tuning, "timing": "host wall clock around each synchronous step call (value) and the "
-                                        "library's CUDA events (value_device); L2 flushed between steps"}
+    reports = gather_reports(per_inst)
+    (wall_ms, upd_all), (dev_max, _), (p_wall_ms, p_upd_all), (p_dev, _), (t_dev, t_upd_all) = combine_ranks(
+        [(wall * 1e3, upd), (dev_ms, upd), (p_wall * 1e3, p_upd), (p_ms, p_upd), (t_ms, t_upd)], f"cuda:{device}")
+    n_el = sum(sp.subdomains[0].n_elements for sp in specs_all)
+    all_its = [it for v in reports.values() for _, it in v]
+    out = {"workload": f"{len(specs_all)} FOM / OpInf(r=32) pairs, n x n x 2n Neo-Hookean FOM, n ~ U{{8..32}}, "
+                       f"{n_el} FOM elements in total, ROMs fitted on {args.batched_snapshots} snapshots each",
+           "rom_ranks": {"32": sum(x == 32 for x in ranks), "below_32": sum(x < 32 for x in ranks)},
+           "steps": args.batched_steps, "value": upd_all / (wall_ms * 1e-3),
+           "value_device": upd_all / (dev_max * 1e-3),
+           "plain_steps": plain_steps, "plain_value": p_upd_all / (p_wall_ms * 1e-3),
+           "plain_value_device": p_upd_all / (p_dev * 1e-3),
+           "speedup": (upd_all / wall_ms) / (p_upd_all / p_wall_ms),
+           "mean_iterations": float(np.mean(all_its)), "max_iterations": int(max(all_its)), "unit": UNIT,
+           "instances_reported": len(reports), "ranks": world,
+           "scaling": "strong (the 256 samples are split over the ranks)" if multi else None,
+           "tuning": tuning, "timing": "host wall clock around each synchronous step call (value) and the "
+                                       "library's CUDA events (value_device); L2 flushed between steps; "
+                                       "under torchrun a barrier on both sides and the maximum over ranks",
+           "roofline": {"bound": "alu", "kernel": "batched internal force (Neo-Hookean, %s)" %
+                        ("tiled" if tuning.get("tiled") else "%d-thread blocks" % tuning["element_block"]),
+                        "achieved": bach_force, "peak": FP64_PEAK[0], "unit": "TFLOP/s",
+                        "frac": bach_force / FP64_PEAK[0], "flops_per_element": FLOPS_PER_NH_ELEMENT,
+                        "force_ms_per_launch": bprof["force_ms"] / max(1, bprof["force_launches"]),
+                        "elements_per_launch": bprof["force_elements"] // max(1, bprof["force_launches"]),
+                        "peak_kind": FP64_PEAK_KIND[0]},
+           "tiled_forced": {"value_device": t_upd_all / (t_dev * 1e-3), "steps": 2,
+                            "note": "the same samples with the 8x4x4-tile force kernel forced (n x n x 2n "
+                                    "meshes, n in 8..32, leave partial tiles on most instances)"}}
+    if rank == 0:
+        # the oracle on a bounded sample of the same sweep: two samples of this rank, one controller step
+        # of one Schwarz iteration each, their fitted ROMs
+        from oracle import oracle as O
+        o_upd, o_s = 0, 0.0
+        for sp, o in list(zip(specs, ops))[:2]:
+            sp.max_iters = 1
+            ref = O.Problem(sp, rom_ops=o)
+            t0 = time.process_time()
+            ref.step()
+            o_s += time.process_time() - t0
+            o_upd += sp.n_substeps * sp.subdomains[0].n_elements
+        out.update({"oracle_value": o_upd / o_s, "oracle_cores": 1,
+                    "oracle_sample": f"two samples, one controller step of one Schwarz iteration each, {o_s:.1f} s CPU"})
+    return out
 
 
 def measure_fit(fit_info, log):
@@ -397,10 +486,72 @@ def measure_fit(fit_info, log):
     OF.opinf_fit(U.T, A.T, S.T, r=fit_info["r"], lam=1e-6, r_s=fit_info["r_s"])
     cpu = time.perf_counter() - t0
     log(f"oracle fit: {cpu:.1f}s")
+    one = fit_one_thread_sample(fit_info, log)
+    gemm = fit_gemm_roofline(U, A, S, fit_info["r"], fit_info["r_s"], log)
     return {**{k: v for k, v in fit_info.items() if k != "training"}, "unit": "s", "higher_is_better": False,
             "oracle_seconds": cpu,
             "oracle_threads": os.cpu_count(), "oracle_kind": "oracle/fit.py (numpy SVD and solve, threaded BLAS)",
-            "speedup_vs_oracle": cpu / fit_info["gpu_seconds"]}
+            "speedup_vs_oracle": cpu / fit_info["gpu_seconds"], "one_thread_sample": one, "gemm": gemm,
+            "roofline": gemm["roofline"]}
+
+
+def fit_gemm_roofline(U, A, S, r, rs, log, device=0):
+    """The fit from device arrays with the library's GEMM accounting on (CUDA events around every
+    contraction): FP64 flops of its GEMMs / their event time against the measured FP64 peak."""
+    import torch
+    from paper_2511_20687_gb300 import osam
+    dev = f"cuda:{device}"
+    Ud, Ad, Sd = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (U, A, S))
+    osam.opinf_fit(Ud, Ad, Sd, r=r, lam=1e-6, r_s=rs, device=device)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    osam.opinf_fit(Ud, Ad, Sd, r=r, lam=1e-6, r_s=rs, device=device)
+    plain_s = time.perf_counter() - t0
+    osam.fit_profile(True)
+    osam.opinf_fit(Ud, Ad, Sd, r=r, lam=1e-6, r_s=rs, device=device)
+    prof = osam.fit_profile(False)
+    achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12
+    log(f"fit GEMMs: {prof['gemm_launches']} products, {prof['gemm_flops'] / 1e9:.0f} GFLOP in {prof['gemm_ms']:.1f} ms "
+        f"= {achieved:.3f} TFLOP/s; device-input fit {plain_s:.2f} s")
+    del Ud, Ad, Sd
+    torch.cuda.empty_cache()
+    return {"device_input_seconds": plain_s, "gemm_ms": prof["gemm_ms"], "gemm_flops": prof["gemm_flops"],
+            "gemm_launches": prof["gemm_launches"], "gemm_share_of_fit": prof["gemm_ms"] * 1e-3 / plain_s,
+            "roofline": {"bound": "alu", "kernel": "k_gemm (+ k_gemm_reduce), FP64 SIMT", "achieved": achieved,
+                         "peak": FP64_PEAK[0], "unit": "TFLOP/s", "frac": achieved / FP64_PEAK[0],
+                         "peak_kind": FP64_PEAK_KIND[0],
+                         "timing": "library CUDA events around every GEMM of one device-input fit "
+                                   "(osam_fit_profile)"}}
+
+
+def fit_one_thread_sample(fit_info, log, n_snap=100):
+    """The fit on a bounded sample (the first n_snap snapshots, same r and r_s): the GPU from host
+    arrays, the oracle's numpy fit in a child process with one BLAS thread (the other oracle figures
+    are one core too)."""
+    from paper_2511_20687_gb300 import osam
+    U, A, S, _ = fit_info["training"]
+    U, A, S = (np.ascontiguousarray(x[:n_snap]) for x in (U, A, S))
+    r, rs = fit_info["r"], fit_info["r_s"]
+    t0 = time.perf_counter()
+    osam.opinf_fit(U, A, S, r=r, lam=1e-6, r_s=rs)
+    gpu_s = time.perf_counter() - t0
+    with tempfile.TemporaryDirectory() as d:
+        for name, x in (("U", U), ("A", A), ("S", S)):
+            np.save(os.path.join(d, name + ".npy"), x)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        code = ("import os, sys, time, numpy as np\n"
+                f"sys.path.insert(0, {ROOT!r})\n"
+                "from oracle import fit as OF\n"
+                f"U, A, S = (np.load(os.path.join({d!r}, n + '.npy')) for n in 'UAS')\n"
+                "t0 = time.process_time()\n"
+                f"OF.opinf_fit(U.T, A.T, S.T, r={r}, lam=1e-6, r_s={rs})\n"
+                "print(time.process_time() - t0)\n")
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    cpu_s = float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+    log(f"fit sample ({n_snap} snapshots): GPU {gpu_s:.2f}s, oracle on one thread {cpu_s}s")
+    return {"n_snap": n_snap, "gpu_seconds": gpu_s, "oracle_seconds": cpu_s, "oracle_threads": 1,
+            "speedup_vs_oracle": (cpu_s / gpu_s) if cpu_s else None,
+            "note": "GPU from host arrays; oracle in a child process with OMP/OPENBLAS/MKL_NUM_THREADS=1"}
 
 
 def measure_select(osam, fit_info, local, log, sample_snaps=100, sample_r=32):
@@ -532,7 +683,7 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
                          "algorithmic_bytes_per_launch": ne * TANGENT_BYTES_PER_ELEMENT,
                          "flops_per_element": TANGENT_FLOPS_PER_NH_ELEMENT,
                          "ms_per_launch": ip["tangent_ms"] / max(1, ip["tangent_launches"]),
-                         "peak_kind": "of measured: FP64 peak of this GPU (fp64_peak block)"},
+                         "peak_kind": FP64_PEAK_KIND[0]},
             "timing": "value: library CUDA events around each controller step, each one graph launch with the "
                       "Newton and CG loops as device-side WHILE nodes (L2 flushed between steps); roofline and "
                       "counts: a second pass of the same steps driven from the host with CUDA events around "
@@ -748,7 +899,7 @@ def measure_large(W, osam, torch, flush, args, local, log, warmup=3):
                                   "flops_per_element": FLOPS_PER_NH_ELEMENT, "elements_per_launch":
                                   spec.subdomains[0].n_elements, "force_ms_per_launch": per_launch,
                                   "force_time_share": prof["force_ms"] / p_ms,
-                                  "peak_kind": ("of measured: FP64 peak of this GPU (fp64_peak block)" if name == "f64"
+                                  "peak_kind": (FP64_PEAK_KIND[0] if name == "f64"
                                                 else "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz"),
                                   "frac_of_nominal": (achieved / FP64_NOMINAL_TFLOPS if name == "f64" else None)}}
         if name == "fp32_force":
@@ -773,6 +924,81 @@ def measure_large(W, osam, torch, flush, args, local, log, warmup=3):
                                f"operators of the fitted sizes), {cpu_s:.1f} s CPU"}
     out["parity"] = ("1e-9 (FP64), 1e-5 (FP32 force) relative L2 vs the oracle on a truncated horizon of the full "
                      "chain (tests/test_gpu_fullsize.py)")
+    return out
+
+
+def fit_only(W, osam, torch, args, local, log):
+    """One GPU fit of seeded synthetic snapshots shaped like the headline training set: U = low-rank
+    signal (decaying mode weights) + noise over the ROM subdomain's free dofs, A and S likewise."""
+    dev = f"cuda:{local}"
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_BASE + 17)
+    # the 40x40x80 ROM mesh: 41 x 41 x 81 nodes, the Schwarz face z = 0 excluded from the free dofs
+    ns, n_dof, n_sdof = args.snapshots, 3 * 41 * 41 * 80, 3 * 41 * 41
+    k = args.rank + 16
+    w = torch.pow(0.8, torch.arange(k, dtype=torch.float64, device=dev))
+    modes = torch.randn((k, n_dof), generator=gen, dtype=torch.float64, device=dev)
+    U = (torch.randn((ns, k), generator=gen, dtype=torch.float64, device=dev) * w) @ modes
+    U += 1e-6 * torch.randn((ns, n_dof), generator=gen, dtype=torch.float64, device=dev)
+    A = (torch.randn((ns, k), generator=gen, dtype=torch.float64, device=dev) * w) @ modes
+    S = torch.randn((ns, n_sdof), generator=gen, dtype=torch.float64, device=dev)
+    del modes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=local)
+    secs = time.perf_counter() - t0
+    osam.fit_profile(True)
+    osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=local)
+    prof = osam.fit_profile(False)
+    achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12
+    log(f"fit-only: {ns} x {n_dof}, r={args.rank}: {secs:.2f} s, GEMMs {achieved:.3f} TFLOP/s")
+    return {"n_snap": ns, "n_dof": n_dof, "r": args.rank, "seconds": secs, **prof, "gemm_tflops": achieved}
+
+
+def measure_fom_fom_plain(W, osam, local, log, repeats=10):
+    """FOM-FOM plain: two 6x6x12 linear-elastic FOMs (global 6x6x22), 200 steps in 10 controller steps
+    of 20 substeps, relative tolerance 1e-12, at most 64 Schwarz iterations -- the whole run, repeated,
+    as graph-captured controller steps and from the host loop (the latency-bound configuration where
+    the graph matters most); beside it the oracle over the whole run on one core."""
+    from oracle import oracle as O
+    out = {"workload": "fom_fom_plain 2 x 6x6x12 linear elastic, 10 controller steps of 20 substeps (the whole "
+                       "200-step run), tol 1e-12, max 64 iterations", "unit": UNIT, "repeats": repeats}
+    for mode in ("graph", "host_loop"):
+        ms, wall, upd, its = 0.0, 0.0, 0, []
+        for rep in range(repeats + 1):          # the first run is a warm-up
+            spec = W.fom_fom_plain()
+            prob = osam.Problem(spec, device=local)
+            prob.set_graph(mode == "graph")
+            t0 = time.perf_counter()
+            run_ms, run_upd, run_its = 0.0, 0, []
+            for _ in range(spec.n_controller_steps):
+                r = prob.step()
+                run_ms += r["elapsed_ms"]
+                run_upd += r["element_updates"]
+                run_its.append(r["iterations"])
+            run_wall = time.perf_counter() - t0
+            prob.close()
+            if rep:
+                ms += run_ms
+                wall += run_wall
+                upd += run_upd
+                its += run_its
+        out[mode] = {"value": upd / (ms * 1e-3), "value_wall": upd / wall, "ms_per_run": ms / repeats,
+                     "ms_per_step": ms / (repeats * 10), "mean_iterations": float(np.mean(its)),
+                     "max_iterations": int(max(its))}
+    spec = W.fom_fom_plain()
+    ref = O.Problem(spec)
+    t0 = time.process_time()
+    o_its = [ref.step()["iterations"] for _ in range(spec.n_controller_steps)]
+    cpu_s = time.process_time() - t0
+    o_upd = sum(o_its) * spec.n_substeps * sum(sd.n_elements for sd in spec.subdomains)
+    out["oracle"] = {"value": o_upd / cpu_s, "seconds_per_run": cpu_s, "cores": 1, "kind": "oracle",
+                     "mean_iterations": float(np.mean(o_its)), "sample": "the whole 200-step run"}
+    out["timing"] = ("value: the library's CUDA events around every controller step (graph build excluded); "
+                     "value_wall: host wall clock around the run's step calls")
+    out["parity"] = "1e-9 relative L2 vs the oracle over all 200 steps (tests/test_gpu_parity.py)"
+    log(f"fom_fom_plain: graph {out['graph']['value']:.3e}, host loop {out['host_loop']['value']:.3e}, oracle "
+        f"{out['oracle']['value']:.3e} element-updates/s; {out['graph']['mean_iterations']:.1f} its")
     return out
 
 
@@ -833,7 +1059,7 @@ def run_reference(args):
             "config": {"workload": f"fom_opinf_hybrid {args.n}x{args.n}x{args.nz} NH FOM + r={args.rank} OpInf ROM",
                        "sample": f"{n_sub} substeps x 1 Schwarz iteration per step, seeded stand-in ROM operators",
                        "l2": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{args.steps} controller steps of {n_sub} substeps, 1 Schwarz iteration each"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -854,6 +1080,32 @@ def combine_ranks(pairs, device):
     dist.all_reduce(ms, op=dist.ReduceOp.MAX)
     dist.all_reduce(up, op=dist.ReduceOp.SUM)
     return [(float(a), int(b)) for a, b in zip(ms.tolist(), up.tolist())]
+
+
+def shard_samples(sizes, world):
+    """Split samples over `world` ranks by their element counts: largest first, each to the rank with
+    the least work so far (ties to the lowest rank); returns each rank's sample indices, ascending."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += sizes[i]
+    return [sorted(p) for p in parts]
+
+
+def gather_reports(mine):
+    """Every rank's {sample index: report} gathered on every rank and merged (identity on one
+    process); the data-path needs no exchange, this is the sweep's only collective."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return dict(mine)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, dict(mine))
+    out = {}
+    for p in parts:
+        out.update(p)
+    return out
 
 
 def timed_pass(prob, torch, flush, steps, profile):
@@ -930,10 +1182,13 @@ def main():
 
     fit_info = None
     fp64_peak = (measure_fp64_peak(osam, local, args.fp64_peak_repeats) if args.fp64_peak_repeats > 0 else
-                 {"tflops": FP64_NOMINAL_TFLOPS, "kind": "nominal (probes skipped)", "fma_best": float("nan"),
-                  "mma_best": float("nan"), "fma_plus_mma_interleaved_best": float("nan"), "sm_mhz": None})
-    log(f"FP64 peak: FMA {fp64_peak['fma_best']:.3f}, tensor-core MMA {fp64_peak['mma_best']:.3f}, interleaved "
-        f"{fp64_peak['fma_plus_mma_interleaved_best']:.3f} TFLOP/s at {fp64_peak['sm_mhz']} MHz")
+                 {"tflops": FP64_NOMINAL_TFLOPS, "kind": "nominal (probes skipped)", "fma_best": None,
+                  "mma_best": None, "fma_plus_mma_interleaved_best": None, "sm_mhz": None})
+    log(f"FP64 peak: {fp64_peak['tflops']:.3f} TFLOP/s ({fp64_peak['kind']}; FMA {fp64_peak['fma_best']}, tensor-core "
+        f"MMA {fp64_peak['mma_best']}, interleaved {fp64_peak['fma_plus_mma_interleaved_best']}, {fp64_peak['sm_mhz']} MHz)")
+    if args.fit_only:
+        print(json.dumps({"fit_only": fit_only(W, osam, torch, args, local, log)}), flush=True)
+        return
     if args.large_only:
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
         print(json.dumps({"large_chain": measure_large(W, osam, torch, flush, args, local, log),
@@ -1013,7 +1268,7 @@ def main():
                     "frac": achieved / FP64_PEAK[0], "traffic": traffic,
                     "kernel": ("k_force_tile_b<NeoHookean, gather>" if res["tuning"].get("tiled")
                                else "k_force_b<NeoHookean, f64, %s>" % res["tuning"]["scatter"]),
-                    "peak_kind": "of measured: FP64 peak of this GPU (fp64_peak block)",
+                    "peak_kind": FP64_PEAK_KIND[0],
                     "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,
                     "flops_per_element": FLOPS_PER_NH_ELEMENT, "elements_per_launch":
                     prof["force_elements"] // max(1, prof["force_launches"]),
@@ -1028,8 +1283,8 @@ def main():
                 "force_ms_per_launch": per_launch, "force_time_share": prof["force_ms"] / res["prof_total_ms"]}
 
     batched = None
-    if world == 1 and not args.no_batched and not args.fom_only:
-        batched = measure_batched(W, osam, torch, flush, args, local, log)
+    if not args.no_batched and not args.fom_only:
+        batched = measure_batched(W, osam, torch, flush, args, local, log, rank, world)
         log(f"batched: {batched['value']:.3e} vs plain {batched['plain_value']:.3e} ({batched['speedup']:.1f}x)")
 
     fit_meas = select_meas = adjoint_meas = implicit_meas = None
@@ -1037,6 +1292,9 @@ def main():
         fit_meas = measure_fit(fit_info, log)
         select_meas = measure_select(osam, fit_info, local, log)
         adjoint_meas = measure_adjoint(W, osam, local, log)
+    plain_meas = None
+    if world == 1 and not args.fom_only:
+        plain_meas = measure_fom_fom_plain(W, osam, local, log)
     large_meas = None
     if world == 1 and not args.no_large and not args.fom_only:
         large_meas = measure_large(W, osam, torch, flush, args, local, log)
@@ -1048,7 +1306,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.fom_only:
         rate, steps, secs = cpu_oracle_rate(W, args, 20, 10.0, max_steps=4)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{steps} controller step(s) x 1 Schwarz iteration x 20 substeps of the {args.n}x{args.n}x"
                          f"{args.nz} NH FOM + r={args.rank} ROM (seeded stand-in operators), {secs:.1f} s CPU"}
 
@@ -1097,6 +1355,7 @@ def main():
                 "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
                 "variants": variants, "batched_vs_plain": batched, "opinf_fit": fit_meas, "opinf_select": select_meas,
                 "adjoint": adjoint_meas, "implicit": implicit_meas, "next_rows": next_meas, "large_chain": large_meas,
+                "fom_fom_plain": plain_meas,
                 "hbm": hbm, "fp64_peak": fp64_peak,
                 "effective_rate": value / mean_it,
                 "rom_substeps_per_s": mean_it * 20 * args.steps / (head["total_ms"] * 1e-3) if not args.fom_only else None}
