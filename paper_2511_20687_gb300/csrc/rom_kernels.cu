@@ -85,40 +85,61 @@ __global__ void k_build_Rt(int nrow, int r, const int* dnode, const double* dw, 
 // alpha and beta.  The output tiles are numbered along grid.x, column tile fastest (blocks that
 // share a row tile of A run together and find it in L2), so m is bounded only by 32-bit indices.
 constexpr int TM = 64, TN = 64, TK = 16;
-__global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, int kchunk, const double* A, long long ai,
-                                              long long ak, const double* B, long long bk, long long bj, double* C,
-                                              long long ldc, double alpha, double beta, double* ws) {
-    __shared__ double As[TK][TM + 1];
-    __shared__ double Bs[TK][TN + 1];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+
+// The GEMM runs on the FP64 tensor cores: 128 threads per 64x64 output tile, each warp a 32x32 quarter
+// as 4 x 4 accumulators of mma.sync m8n8k4 (FP64 in and out, each MMA 8x8x4 fused multiply-adds).
+// Fragments (groupID g = lane / 4, t = lane % 4): A element (row g, k t), B element (k t, col g),
+// accumulator elements (row g, cols 2t, 2t + 1).  Shared-memory rows padded to 68 doubles so that the
+// 16 lanes of each half-warp read distinct banks.
+constexpr int TPAD = 4;
+__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};\n"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+__global__ void __launch_bounds__(128) k_gemm_mma(int m, int n, int kdim, int kchunk, const double* A, long long ai,
+                                                  long long ak, const double* B, long long bk, long long bj,
+                                                  double* C, long long ldc, double alpha, double beta, double* ws) {
+    __shared__ double As[TK][TM + TPAD];
+    __shared__ double Bs[TK][TN + TPAD];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wr = warp >> 1, wc = warp & 1;
+    const int g = lane >> 2, t4 = lane & 3;
     const int ntn = (n + TN - 1) / TN;
     const int i0 = (int)(blockIdx.x / ntn) * TM, j0 = (int)(blockIdx.x % ntn) * TN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(kdim, kbeg + kchunk);
     const bool a_along_i = ai == 1 && ak != 1;   // A stored [k][m]
     const bool b_along_j = bj == 1;              // B stored [k][n]
-    double acc[4][4] = {{0}};
+    double acc[4][4][2];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y][0] = acc[x][y][1] = 0.0;
     for (int k0 = kbeg; k0 < kend; k0 += TK) {
-        for (int t = threadIdx.x; t < TK * TM; t += 256) {
+        for (int t = threadIdx.x; t < TK * TM; t += 128) {
             const int kk = a_along_i ? t / TM : t % TK, ii = a_along_i ? t % TM : t / TK;
             const int gi = i0 + ii, gk = k0 + kk;
             As[kk][ii] = (gi < m && gk < kend) ? A[gi * ai + gk * ak] : 0.0;
         }
-        for (int t = threadIdx.x; t < TK * TN; t += 256) {
+        for (int t = threadIdx.x; t < TK * TN; t += 128) {
             const int jj = b_along_j ? t % TN : t / TK, kk = b_along_j ? t / TN : t % TK;
             const int gj = j0 + jj, gk = k0 + kk;
             Bs[kk][jj] = (gj < n && gk < kend) ? B[gk * bk + gj * bj] : 0.0;
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < TK; ++kk) {
-            double a4[4], b4[4];
+        for (int ks = 0; ks < TK; ks += 4) {
+            double a[4], b[4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x) { a4[x] = As[kk][ty * 4 + x]; b4[x] = Bs[kk][tx * 4 + x]; }
+            for (int x = 0; x < 4; ++x) a[x] = As[ks + t4][wr * 32 + x * 8 + g];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) b[y] = Bs[ks + t4][wc * 32 + y * 8 + g];
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a4[x], b4[y], acc[x][y]);
+                for (int y = 0; y < 4; ++y) dmma_8x8x4(acc[x][y][0], acc[x][y][1], a[x], b[y]);
         }
         __syncthreads();
     }
@@ -126,17 +147,19 @@ __global__ void __launch_bounds__(256) k_gemm(int m, int n, int kdim, int kchunk
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) {
-            const int gi = i0 + ty * 4 + x, gj = j0 + tx * 4 + y;
-            if (gi < m && gj < n) {
-                if (W) {
-                    W[(long long)gi * n + gj] = acc[x][y];
-                } else {
-                    double* cp = C + gi * ldc + gj;
-                    *cp = alpha * acc[x][y] + (beta != 0.0 ? beta * *cp : 0.0);
+        for (int y = 0; y < 4; ++y)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int gi = i0 + wr * 32 + x * 8 + g, gj = j0 + wc * 32 + y * 8 + 2 * t4 + q;
+                if (gi < m && gj < n) {
+                    if (W) {
+                        W[(long long)gi * n + gj] = acc[x][y][q];
+                    } else {
+                        double* cp = C + gi * ldc + gj;
+                        *cp = alpha * acc[x][y][q] + (beta != 0.0 ? beta * *cp : 0.0);
+                    }
                 }
             }
-        }
 }
 
 __global__ void k_gemm_reduce(int m, int n, int nsplit, const double* __restrict__ ws, double* C, long long ldc,
@@ -184,8 +207,8 @@ cudaError_t launch_gemm(int m, int n, int k, const double* A, long long ai, long
     return e;
 }
 
-// Split the reduction when the output tiles alone cannot fill the GPU (two blocks per SM wanted)
-// and the reduction is long: chunks of at least 512 k, a multiple of the k tile.
+// Split the reduction when the output tiles alone cannot fill the GPU (four 4-warp blocks per SM
+// wanted) and the reduction is long: chunks of at least 512 k, a multiple of the k tile.
 cudaError_t launch_gemm_impl(int m, int n, int k, const double* A, long long ai, long long ak, const double* B,
                              long long bk, long long bj, double* C, long long ldc, double alpha, double beta,
                              cudaStream_t s) {
@@ -193,10 +216,15 @@ cudaError_t launch_gemm_impl(int m, int n, int k, const double* A, long long ai,
     const long long tiles = (long long)grid_for(n, TN) * grid_for(m, TM);
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long want = 2LL * sms;
+    const long long want = 4LL * sms;
     int nsplit = 1;
     if (tiles < want && k >= 2 * 512)
         nsplit = (int)std::min<long long>((want + tiles - 1) / tiles, k / 512);
+    // prefer a block count that is a multiple of the SM count: every SM then runs the same number of
+    // equal blocks (a 64-tile Gram split 10 ways leaves some SMs three blocks and others two)
+    if (nsplit > 1)
+        for (long long ns = nsplit; ns <= std::min<long long>(k / 512, 4LL * nsplit); ++ns)
+            if ((tiles * ns) % sms == 0) { nsplit = (int)ns; break; }
     int kchunk = k;
     if (nsplit > 1) {
         kchunk = (k + nsplit - 1) / nsplit;
@@ -206,13 +234,13 @@ cudaError_t launch_gemm_impl(int m, int n, int k, const double* A, long long ai,
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 g((unsigned)tiles, 1, nsplit);
     if (nsplit == 1) {
-        k_gemm<<<g, 256, 0, s>>>(m, n, k, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, nullptr);
+        k_gemm_mma<<<g, 128, 0, s>>>(m, n, k, k, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, nullptr);
         return cudaGetLastError();
     }
     double* ws = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), sizeof(double) * (size_t)nsplit * m * n, s);
     if (e != cudaSuccess) return e;
-    k_gemm<<<g, 256, 0, s>>>(m, n, k, kchunk, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, ws);
+    k_gemm_mma<<<g, 128, 0, s>>>(m, n, k, kchunk, A, ai, ak, B, bk, bj, C, ldc, alpha, beta, ws);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         k_gemm_reduce<<<grid_for((long long)m * n, 256), 256, 0, s>>>(m, n, nsplit, ws, C, ldc, alpha, beta);
