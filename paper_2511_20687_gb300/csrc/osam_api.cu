@@ -498,36 +498,45 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     const int nck = T / Cp + 1;
     const long long n3 = 3LL * nn;
     double* ck = ctx->alloc<double>((size_t)nck * 3 * n3);  // (u, v, a) at steps 0, C, 2C, ...
-    double* useg = ctx->alloc<double>((size_t)(Cp + 1) * n3);
+    double* useg[2] = {ctx->alloc<double>((size_t)(Cp + 1) * n3), ctx->alloc<double>((size_t)(Cp + 1) * n3)};
     double* ub = ctx->alloc<double>(n3);
     double* vb = ctx->alloc<double>(n3);
     double* ab = ctx->alloc<double>(n3);
     double* y = ctx->alloc<double>(n3);
+    double* vfe = ctx->alloc<double>(24LL * ne);   // the VJP's element buffer (the recomputation uses F.fe)
     double* glam = ctx->alloc<double>(ne);
     double* gmu = ctx->alloc<double>(ne);
-    CKA(ck); CKA(useg); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(glam); CKA(gmu);
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CKA(ck); CKA(useg[0]); CKA(useg[1]); CKA(ub); CKA(vb); CKA(ab); CKA(y); CKA(vfe); CKA(glam); CKA(gmu);
+    const cudaStream_t R = ctx->stream;   // forward sweep and reverse sweeps (the critical path)
+    const cudaStream_t Q = ctx->side;     // recomputation of the next segment, concurrently
+    struct Events {
+        cudaEvent_t e[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        ~Events() { for (auto x : e) if (x) cudaEventDestroy(x); }
+    } ev;
+    for (auto& x : ev.e) CK(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+    cudaEvent_t ev_rec[2] = {ev.e[0], ev.e[1]}, ev_rev[2] = {ev.e[2], ev.e[3]}, ev_start = ev.e[4];
+    CK(cudaEventRecord(ctx->ev0, R));
     // one explicit step in place on (u[0], v, a), deterministic element-buffer scatter
-    auto step = [&](double* u_store) -> int {
-        CK(launch_node_b(F, nullptr, kGather, -1, 1, 1, F.u[0], F.u[1], dt, ctx->stream));
-        CK(launch_force_b(F, nullptr, kGather, ctx->stream));
-        CK(launch_node_b(F, nullptr, kGather, 1, -1, 0, F.u[1], F.u[0], dt, ctx->stream));
-        CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+    auto step = [&](double* u_store, cudaStream_t st) -> int {
+        CK(launch_node_b(F, nullptr, kGather, -1, 1, 1, F.u[0], F.u[1], dt, st));
+        CK(launch_force_b(F, nullptr, kGather, st));
+        CK(launch_node_b(F, nullptr, kGather, 1, -1, 0, F.u[1], F.u[0], dt, st));
+        CK(cudaMemcpyAsync(F.u[0], F.u[1], sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+        if (u_store) CK(cudaMemcpyAsync(u_store, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
         return OSAM_OK;
     };
     auto save_ck = [&](int idx) -> int {
         double* base = ck + (size_t)idx * 3 * n3;
-        CK(cudaMemcpyAsync(base, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(base + n3, F.v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(base + 2 * n3, F.a, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(base, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, R));
+        CK(cudaMemcpyAsync(base + n3, F.v, sizeof(double) * n3, cudaMemcpyDeviceToDevice, R));
+        CK(cudaMemcpyAsync(base + 2 * n3, F.a, sizeof(double) * n3, cudaMemcpyDeviceToDevice, R));
         return OSAM_OK;
     };
-    auto load_ck = [&](int idx) -> int {
+    auto load_ck = [&](int idx, cudaStream_t st) -> int {
         double* base = ck + (size_t)idx * 3 * n3;
-        CK(cudaMemcpyAsync(F.u[0], base, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(F.v, base + n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(F.a, base + 2 * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(F.u[0], base, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(F.v, base + n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(F.a, base + 2 * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st));
         return OSAM_OK;
     };
     ElemArgs va{};
@@ -535,28 +544,28 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
     va.invh = I.invh; va.w8 = I.w8; va.wq = I.wq; va.wq3 = I.wq3;
     va.lam_e = I.lam_e; va.mu_e = I.mu_e;
     va.usn = 1; va.usc = nn;
-    va.fe = F.fe;
-    // reverse of step t + 1 (state u_{t+1} stored at useg[t + 1 - t0])
-    auto reverse = [&](int t, int t0) -> int {
-        CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, ctx->stream));
-        va.u = useg + (size_t)(t + 1 - t0) * n3;
-        CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, ctx->stream));
-        CK(launch_adjoint_post(I.nx, I.ny, I.nz, dt, F.clamp, static_cast<const double*>(F.fe), ub, vb, ab, ctx->stream));
+    va.fe = vfe;
+    // reverse of step t + 1 of a segment starting at t0 (state u_{t+1} stored at buf[t + 1 - t0])
+    auto reverse = [&](int t, int t0, const double* buf, cudaStream_t st) -> int {
+        CK(launch_adjoint_pre(nn, dt, F.clamp, F.minv, vb, ab, y, st));
+        va.u = buf + (size_t)(t + 1 - t0) * n3;
+        CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, st));
+        CK(launch_adjoint_post(I.nx, I.ny, I.nz, dt, F.clamp, vfe, ub, vb, ab, st));
         return OSAM_OK;
     };
     // A full segment of Cp steps is the same sequence of launches every time (the checkpoint is loaded
-    // outside it and the segment buffer is reused), so the forward sweep, the recomputation and the
-    // reverse sweep of a segment are each captured once as a CUDA graph and replayed; a partial last
-    // segment runs from the host.
+    // outside it and the segment buffers are reused), so the forward sweep, the recomputation into
+    // either buffer and the reverse sweep from either buffer are each captured once as a CUDA graph and
+    // replayed; a partial last segment runs from the host.
     struct Graphs {
-        cudaGraphExec_t g[3] = {nullptr, nullptr, nullptr};
+        cudaGraphExec_t g[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
         ~Graphs() { for (auto x : g) if (x) cudaGraphExecDestroy(x); }
     } graphs;
     auto capture = [&](int which, const std::function<int()>& body) -> int {
         cudaGraph_t gr = nullptr;
-        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(R, cudaStreamCaptureModeThreadLocal));
         const int rc = body();
-        const cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+        const cudaError_t e = cudaStreamEndCapture(R, &gr);
         if (rc) { if (gr) cudaGraphDestroy(gr); return rc; }
         CK(e);
         const cudaError_t ei = cudaGraphInstantiate(&graphs.g[which], gr, 0);
@@ -564,53 +573,76 @@ int osam_adjoint(const osam_adjoint_desc* d, osam_adjoint_out* out) {
         CK(ei);
         return OSAM_OK;
     };
-    const bool full = T >= Cp;
-    if (full) {
-        RET(capture(0, [&]() -> int { for (int t = 0; t < Cp; ++t) RET(step(nullptr)); return OSAM_OK; }));
-        RET(capture(1, [&]() -> int {
-            CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-            for (int t = 1; t <= Cp; ++t) RET(step(useg + (size_t)t * n3));
-            return OSAM_OK;
-        }));
-        RET(capture(2, [&]() -> int { for (int t = Cp - 1; t >= 0; --t) RET(reverse(t, 0)); return OSAM_OK; }));
+    if (T >= Cp) {
+        RET(capture(0, [&]() -> int { for (int t = 0; t < Cp; ++t) RET(step(nullptr, R)); return OSAM_OK; }));
+        for (int b = 0; b < 2; ++b) {
+            RET(capture(1 + b, [&]() -> int {
+                CK(cudaMemcpyAsync(useg[b], F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, R));
+                for (int t = 1; t <= Cp; ++t) RET(step(useg[b] + (size_t)t * n3, R));
+                return OSAM_OK;
+            }));
+            RET(capture(3 + b, [&]() -> int {
+                for (int t = Cp - 1; t >= 0; --t) RET(reverse(t, 0, useg[b], R));
+                return OSAM_OK;
+            }));
+        }
     }
     RET(save_ck(0));
     for (int t0 = 0; t0 < T; t0 += Cp) {
         if (t0 + Cp <= T) {
-            CK(cudaGraphLaunch(graphs.g[0], ctx->stream));
+            CK(cudaGraphLaunch(graphs.g[0], R));
+            RET(save_ck((t0 + Cp) / Cp));
         } else {
-            for (int t = t0 + 1; t <= T; ++t) RET(step(nullptr));
+            for (int t = t0 + 1; t <= T; ++t) RET(step(nullptr, R));
         }
-        if ((t0 + Cp) <= T) RET(save_ck((t0 + Cp) / Cp));
     }
     // J = w . u_T
     RET(upload(ctx, ctx->scratch, d->w, sizeof(double) * n3));
-    CK(launch_aos_to_soa(ctx->scratch, ub, nn, nn, ctx->stream));
-    CK(launch_zero_clamped(nn, F.clamp, ub, nullptr, nn, ctx->stream));
+    CK(launch_aos_to_soa(ctx->scratch, ub, nn, nn, R));
+    CK(launch_zero_clamped(nn, F.clamp, ub, nullptr, nn, R));
     std::vector<double> wh(n3), uh(n3);
-    CK(cudaMemcpyAsync(wh.data(), ub, sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(uh.data(), F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(wh.data(), ub, sizeof(double) * n3, cudaMemcpyDeviceToHost, R));
+    CK(cudaMemcpyAsync(uh.data(), F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToHost, R));
+    CK(cudaStreamSynchronize(R));
     double J = 0.0;
     for (long long q = 0; q < n3; ++q) J += wh[q] * uh[q];
-    for (int seg = (T - 1) / Cp; seg >= 0 && T > 0; --seg) {
-        const int t0 = seg * Cp, t1 = std::min(T, t0 + Cp);
-        RET(load_ck(seg));
-        if (t1 - t0 == Cp) {
-            CK(cudaGraphLaunch(graphs.g[1], ctx->stream));
-            CK(cudaGraphLaunch(graphs.g[2], ctx->stream));
-        } else {
-            CK(cudaMemcpyAsync(useg, F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, ctx->stream));
-            for (int t = t0 + 1; t <= t1; ++t) RET(step(useg + (size_t)(t - t0) * n3));
-            for (int t = t1 - 1; t >= t0; --t) RET(reverse(t, t0));
+    // Reverse sweep.  A partial last segment is recomputed and reversed on R first.  Then the full
+    // segments s = S-1 .. 0: the recomputation of segment s - 1 needs only checkpoint s - 1, so it runs
+    // on Q into the other buffer while the reverse sweep of segment s runs on R.  Buffer s % 2 is
+    // rewritten only after the reverse sweep that last read it (segment s + 2) is done.
+    int seg = T > 0 ? (T - 1) / Cp : -1;
+    if (seg >= 0 && T - seg * Cp < Cp) {
+        const int t0 = seg * Cp;
+        RET(load_ck(seg, R));
+        CK(cudaMemcpyAsync(useg[0], F.u[0], sizeof(double) * n3, cudaMemcpyDeviceToDevice, R));
+        for (int t = t0 + 1; t <= T; ++t) RET(step(useg[0] + (size_t)(t - t0) * n3, R));
+        for (int t = T - 1; t >= t0; --t) RET(reverse(t, t0, useg[0], R));
+        --seg;
+    }
+    if (seg >= 0) {
+        CK(cudaEventRecord(ev_start, R));
+        CK(cudaStreamWaitEvent(Q, ev_start, 0));
+        RET(load_ck(seg, Q));
+        CK(cudaGraphLaunch(graphs.g[1 + seg % 2], Q));
+        CK(cudaEventRecord(ev_rec[seg % 2], Q));
+        for (int sg = seg; sg >= 0; --sg) {
+            CK(cudaStreamWaitEvent(R, ev_rec[sg % 2], 0));
+            CK(cudaGraphLaunch(graphs.g[3 + sg % 2], R));
+            CK(cudaEventRecord(ev_rev[sg % 2], R));
+            if (sg > 0) {
+                if (sg + 1 <= seg) CK(cudaStreamWaitEvent(Q, ev_rev[(sg - 1) % 2], 0));   // segment sg + 1's
+                RET(load_ck(sg - 1, Q));
+                CK(cudaGraphLaunch(graphs.g[1 + (sg - 1) % 2], Q));
+                CK(cudaEventRecord(ev_rec[(sg - 1) % 2], Q));
+            }
         }
     }
-    // a_0 = -M^-1 f(u_0)
-    CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, ctx->stream));
-    RET(load_ck(0));
+    // a_0 = -M^-1 f(u_0) (Q has no work left: every recomputation finished before its reverse sweep)
+    CK(launch_adjoint_pre(nn, 0.0, F.clamp, F.minv, vb, ab, y, R));
+    RET(load_ck(0, R));
     va.u = F.u[0];
-    CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, ctx->stream));
-    CK(launch_adjoint_post(I.nx, I.ny, I.nz, 0.0, F.clamp, static_cast<const double*>(F.fe), ub, vb, ab, ctx->stream));
+    CK(launch_hex8_vjp(F.material, kGather, va, y, 1, nn, glam, gmu, 1, R));
+    CK(launch_adjoint_post(I.nx, I.ny, I.nz, 0.0, F.clamp, vfe, ub, vb, ab, R));
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.f;
