@@ -517,7 +517,7 @@ def fit_gemm_roofline(U, A, S, r, rs, log, device=0):
     torch.cuda.empty_cache()
     return {"device_input_seconds": plain_s, "gemm_ms": prof["gemm_ms"], "gemm_flops": prof["gemm_flops"],
             "gemm_launches": prof["gemm_launches"], "gemm_share_of_fit": prof["gemm_ms"] * 1e-3 / plain_s,
-            "roofline": {"bound": "alu", "kernel": "k_gemm (+ k_gemm_reduce), FP64 SIMT", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": "k_gemm_mma (+ k_gemm_reduce), FP64 tensor-core mma.sync m8n8k4", "achieved": achieved,
                          "peak": FP64_PEAK[0], "unit": "TFLOP/s", "frac": achieved / FP64_PEAK[0],
                          "peak_kind": FP64_PEAK_KIND[0],
                          "timing": "library CUDA events around every GEMM of one device-input fit "
@@ -951,8 +951,18 @@ def fit_only(W, osam, torch, args, local, log):
     osam.opinf_fit(U, A, S, r=args.rank, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64, device=local)
     prof = osam.fit_profile(False)
     achieved = prof["gemm_flops"] / (prof["gemm_ms"] * 1e-3) / 1e12
-    log(f"fit-only: {ns} x {n_dof}, r={args.rank}: {secs:.2f} s, GEMMs {achieved:.3f} TFLOP/s")
-    return {"n_snap": ns, "n_dof": n_dof, "r": args.rank, "seconds": secs, **prof, "gemm_tflops": achieved}
+    # Algorithm 3 on the same snapshots (11 candidates, rollouts 4 steps apart): the selection kernels
+    # (random snapshots are no dynamical system: every rollout may blow up, which the selection reports)
+    t0 = time.perf_counter()
+    try:
+        best = int(osam.opinf_select(U, A, S, None, args.rank, np.logspace(-10, 0, 11), 1e-6, 4, r_s=0,
+                                     energy_s=1.0 - 1e-6, r_s_max=64, device=local)["best"])
+    except osam.OsamError as err:
+        best = f"none ({err})"
+    sel_s = time.perf_counter() - t0
+    log(f"fit-only: {ns} x {n_dof}, r={args.rank}: {secs:.2f} s, GEMMs {achieved:.3f} TFLOP/s; selection {sel_s:.2f} s")
+    return {"n_snap": ns, "n_dof": n_dof, "r": args.rank, "seconds": secs, **prof, "gemm_tflops": achieved,
+            "select_seconds": sel_s, "select_best": best}
 
 
 def measure_fom_fom_plain(W, osam, local, log, repeats=10):
