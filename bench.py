@@ -56,8 +56,8 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "f9b33758e4465a68a7d1c8b8d8470f1976b96f1393496e0abe00cbbbb4491359",
-                 "bytes_per_launch": 3.567104e6, "tiled": True}
+FORCE_TRAFFIC = {"source_sha256": "9544cf17b201411e62cdbee44c1ea7d973d12fc8d3153fa7d22c71333481dde7",
+                 "bytes_per_launch": 3.56672e6, "tiled": True, "register_cap": 0}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
@@ -149,7 +149,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"],
                     help="f64: native FP64 force; f32x2: double-float force on the FP32 pipes (FP64 state)")
-    ap.add_argument("--scatter", default="auto", choices=["auto", "gather", "atomic", "tiled", "lowreg"],
+    ap.add_argument("--scatter", default="auto", choices=["auto", "gather", "atomic", "tiled", "lowreg", "tiled_lowreg"],
                     help="force-kernel configuration (auto: the library's autotuner); fixed choices make ncu "
                          "captures reproducible")
     ap.add_argument("--batched-samples", type=int, default=256)
@@ -1226,7 +1226,8 @@ def main():
     for prec in ([head_prec] + [p for p in (osam.FP64, osam.F32X2_FORCE) if p != head_prec]):
         name = "f32x2" if prec == osam.F32X2_FORCE else "f64"
         scatter = {"auto": osam.SCATTER_AUTO, "gather": osam.SCATTER_GATHER, "atomic": osam.SCATTER_ATOMIC,
-                   "tiled": osam.SCATTER_GATHER_TILED, "lowreg": osam.SCATTER_GATHER_LOWREG}[args.scatter]
+                   "tiled": osam.SCATTER_GATHER_TILED, "lowreg": osam.SCATTER_GATHER_LOWREG,
+                   "tiled_lowreg": osam.SCATTER_GATHER_TILED_LOWREG}[args.scatter]
         prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=prec, scatter=scatter)
         log(f"[{name}] tuning: {prob.tuning()}")
         for _ in range(args.warmup):
@@ -1272,11 +1273,13 @@ def main():
         if prec_name == "f64":
             achieved = FLOPS_PER_NH_ELEMENT * prof["force_elements"] / (prof["force_ms"] * 1e-3) / 1e12
             same = (FORCE_TRAFFIC["source_sha256"] == source_sha()
-                    and FORCE_TRAFFIC["tiled"] == bool(res["tuning"].get("tiled")))
+                    and FORCE_TRAFFIC["tiled"] == bool(res["tuning"].get("tiled"))
+                    and FORCE_TRAFFIC.get("register_cap", 0) == res["tuning"].get("register_cap", 0))
             traffic = FORCE_TRAFFIC["bytes_per_launch"] if same else None
             return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK[0], "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK[0], "traffic": traffic,
-                    "kernel": ("k_force_tile_b<NeoHookean, gather>" if res["tuning"].get("tiled")
+                    "kernel": (("k_force_tile_occ_b<NeoHookean> (128-register cap)" if res["tuning"].get("register_cap")
+                                else "k_force_tile_b<NeoHookean, gather>") if res["tuning"].get("tiled")
                                else "k_force_b<NeoHookean, f64, %s>" % res["tuning"]["scatter"]),
                     "peak_kind": FP64_PEAK_KIND[0],
                     "frac_of_nominal": achieved / FP64_NOMINAL_TFLOPS,

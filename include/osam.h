@@ -63,14 +63,16 @@ enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1, OSAM_F32X2_FORCE = 2 };
  * element-buffer / node-gather scheme; GATHER_LOWREG is the gather scheme with the FP64 force kernel
  * compiled for at most 128 registers per thread (more resident warps, a few spilled values);
  * GATHER_TILED the gather scheme with the FP64 force evaluated by 8x4x4 element tiles that share
- * their edge interpolation (same results bit for bit); the FP32 variants ignore both.  AUTO times
+ * their edge interpolation (same results bit for bit), GATHER_TILED_LOWREG the tiled kernel capped at
+ * 128 registers (4 instead of 3 resident tiles per SM); the FP32 variants ignore these.  AUTO times
  * the candidates at initialisation and keeps the fastest */
 enum {
     OSAM_SCATTER_AUTO = 0,
     OSAM_SCATTER_ATOMIC = 1,
     OSAM_SCATTER_GATHER = 2,
     OSAM_SCATTER_GATHER_LOWREG = 3,
-    OSAM_SCATTER_GATHER_TILED = 4
+    OSAM_SCATTER_GATHER_TILED = 4,
+    OSAM_SCATTER_GATHER_TILED_LOWREG = 5   /* the tiled FP64 force capped at 128 registers (4 tiles per SM) */
 };
 
 typedef struct osam_ctx osam_ctx;

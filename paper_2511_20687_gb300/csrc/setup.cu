@@ -26,7 +26,7 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
         return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
     if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE)
         return ctx->fail(OSAM_EINVAL, "bad precision");
-    if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_TILED)
+    if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_TILED_LOWREG)
         return ctx->fail(OSAM_EINVAL, "bad scatter mode");
     if (d0.schwarz != OSAM_MULTIPLICATIVE && d0.schwarz != OSAM_ADDITIVE)
         return ctx->fail(OSAM_EINVAL, "bad Schwarz variant");
@@ -633,20 +633,22 @@ int autotune(osam_ctx* ctx) {
     g.a = a;
     const int slot2 = std::min(2, best_s->nsub);
     float best_ms = 1e30f, gather_ms = 1e30f;
-    int best_block = 128, best_scatter = kGather, best_tiled = 0;
-    // (scatter, element block, tiled).  The 128-register FP64 kernel measured level with the natural
-    // one on the bench meshes, so AUTO does not try it (OSAM_SCATTER_GATHER_LOWREG selects it).
-    const int cands[8][3] = {{kGather, 64, 0}, {kGather, 128, 0}, {kGather, 256, 0}, {kGather, 128, 1},
-                             {kAtomic, 64, 0}, {kAtomic, 128, 0}, {kAtomic, 256, 0}, {kAtomic, 128, 1}};
+    int best_block = 128, best_scatter = kGather, best_tiled = 0, best_occ = 0;
+    // (scatter, element block, tiled, 128-register cap).  Both FP64 kernels capped at 128 registers
+    // measured level with their natural builds on the bench meshes (tiled: 192.8 vs 193.1 us per launch
+    // on 40x40x80, the fourth resident tile per SM paid for by its spills), so AUTO does not try them
+    // (OSAM_SCATTER_GATHER_LOWREG / _TILED_LOWREG select them).
+    const int cands[8][4] = {{kGather, 64, 0, 0}, {kGather, 128, 0, 0}, {kGather, 256, 0, 0}, {kGather, 128, 1, 0},
+                             {kAtomic, 64, 0, 0}, {kAtomic, 128, 0, 0}, {kAtomic, 256, 0, 0}, {kAtomic, 128, 1, 0}};
     for (const auto& cd : cands) {
-        const int mode = cd[0], block = cd[1], tiled = cd[2];
+        const int mode = cd[0], block = cd[1], tiled = cd[2], occ = cd[3];
         if (g.df32 && (mode == kAtomic || block > 128 || tiled)) continue;  // double-float force: gather, <= 128 threads
         if (tiled && g.fp32) continue;                                    // the tiled kernel is FP64
         RET(set_eblocks(ctx, G, block));
         g.eblk = G.d.eblk;
         g.n_eblk = G.d.n_eblk;
         g.eblock = block;
-        g.occ = 0;
+        g.occ = occ;
         g.tiled = tiled;
         for (int rep = 0; rep < 4; ++rep) {
             if (rep == 1) CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -658,9 +660,11 @@ int autotune(osam_ctx* ctx) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
         if (mode == kGather) {
-            if (ms < gather_ms) { gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; best_tiled = tiled; }
+            if (ms < gather_ms) {
+                gather_ms = ms; best_block = block; best_scatter = kGather; best_ms = ms; best_tiled = tiled; best_occ = occ;
+            }
         } else if (ms < 0.95f * gather_ms && ms < best_ms) {
-            best_ms = ms; best_block = block; best_scatter = kAtomic; best_tiled = tiled;
+            best_ms = ms; best_block = block; best_scatter = kAtomic; best_tiled = tiled; best_occ = 0;
         }
     }
     CK(cudaMemsetAsync(G.d.f, 0, sizeof(double) * 3 * NN, ctx->stream));
@@ -671,6 +675,7 @@ int autotune(osam_ctx* ctx) {
         if (S.kind == OSAM_FOM) {
             RET(set_eblocks(ctx, S.fom, best_block));
             S.fom.d.tiled = best_tiled;
+            S.fom.d.occ = best_occ;
         }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
@@ -792,9 +797,13 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     if (d0.scatter == OSAM_SCATTER_GATHER_LOWREG && d0.precision == OSAM_FP64)
         for (Slot& S : ctx->slots)
             if (S.kind == OSAM_FOM) S.fom.d.occ = 1;
-    if (d0.scatter == OSAM_SCATTER_GATHER_TILED && d0.precision == OSAM_FP64)
+    if ((d0.scatter == OSAM_SCATTER_GATHER_TILED || d0.scatter == OSAM_SCATTER_GATHER_TILED_LOWREG) &&
+        d0.precision == OSAM_FP64)
         for (Slot& S : ctx->slots)
-            if (S.kind == OSAM_FOM) S.fom.d.tiled = 1;
+            if (S.kind == OSAM_FOM) {
+                S.fom.d.tiled = 1;
+                S.fom.d.occ = d0.scatter == OSAM_SCATTER_GATHER_TILED_LOWREG;
+            }
     for (Slot& S : ctx->slots)
         if (S.kind == OSAM_FOM) S.fom.d.scatter = ctx->scatter;
     CK(cudaStreamSynchronize(ctx->stream));

@@ -93,8 +93,7 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
 constexpr int kTX = 8, kTY = 4, kTZ = 4;
 
 template <int MAT, int MODE>
-__global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* __restrict__ active,
-                                                      const TraceFuse tr) {
+__device__ __forceinline__ void force_tile_body(const FomB& g, const int* __restrict__ active, const TraceFuse& tr) {
     if ((int)blockIdx.x >= g.n_tblk) {
         trace::fused_trace_block(tr, active, g, (int)blockIdx.x - g.n_tblk);
         return;
@@ -214,6 +213,21 @@ __global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* _
 #pragma unroll
             for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
     }
+}
+
+// the tiled force as compiled for its natural register count (166 for Neo-Hookean: 3 blocks per SM)
+// and capped at 128 registers (4 blocks per SM, a few spilled values): 1000 tiles of the 40x40x80
+// mesh are 2.19 waves of the first and 1.64 of the second; the autotuner times both
+template <int MAT, int MODE>
+__global__ void __launch_bounds__(128) k_force_tile_b(const FomB g, const int* __restrict__ active,
+                                                      const TraceFuse tr) {
+    force_tile_body<MAT, MODE>(g, active, tr);
+}
+
+template <int MAT>
+__global__ void __launch_bounds__(128, 4) k_force_tile_occ_b(const FomB g, const int* __restrict__ active,
+                                                             const TraceFuse tr) {
+    force_tile_body<MAT, kGather>(g, active, tr);
 }
 
 // the force kernel at its natural register count (168 for Neo-Hookean FP64: 12 warps per SM) ...
@@ -786,6 +800,13 @@ cudaError_t launch_force_b(const FomB& g, const int* active, int scatter, cudaSt
         long long titems = 0;
         for (int k = 0; k < tr.n; ++k) titems += 3LL * tr.c[k].R;
         const int tgrid = g.n_tblk + (int)((titems + 127) / 128);
+        if (g.occ && scatter == kGather) {
+            if (g.material == OSAM_NEO_HOOKEAN) k_force_tile_occ_b<OSAM_NEO_HOOKEAN><<<tgrid, 128, 0, s>>>(g, active, tr);
+            else if (g.material == OSAM_SAINT_VENANT_KIRCHHOFF)
+                k_force_tile_occ_b<OSAM_SAINT_VENANT_KIRCHHOFF><<<tgrid, 128, 0, s>>>(g, active, tr);
+            else k_force_tile_occ_b<OSAM_LINEAR_ELASTIC><<<tgrid, 128, 0, s>>>(g, active, tr);
+            return cudaGetLastError();
+        }
         if (g.material == OSAM_NEO_HOOKEAN) {
             if (scatter == kAtomic) k_force_tile_b<OSAM_NEO_HOOKEAN, kAtomic><<<tgrid, 128, 0, s>>>(g, active, tr);
             else k_force_tile_b<OSAM_NEO_HOOKEAN, kGather><<<tgrid, 128, 0, s>>>(g, active, tr);

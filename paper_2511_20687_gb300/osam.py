@@ -22,6 +22,7 @@ EXPLICIT, IMPLICIT = 0, 1
 MULTIPLICATIVE, ADDITIVE = 0, 1
 FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG, SCATTER_GATHER_TILED = 0, 1, 2, 3, 4
+SCATTER_GATHER_TILED_LOWREG = 5
 
 EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin_interval", "osam_restore_interval",
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",

@@ -170,14 +170,18 @@ def _chain_rom(spec, r, rs, seed):
     return W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, r, rs, seed)
 
 
-@pytest.mark.parametrize("material", ["le", "nh"])
-def test_tiled_force_equals_untiled(gpu, material):
+@pytest.mark.parametrize("tiled", ["tiled", "tiled_lowreg"])
+@pytest.mark.parametrize("material", ["le", "nh", "svk"])
+def test_tiled_force_equals_untiled(gpu, material, tiled):
     """The tiled FP64 force shares the edge interpolation between neighbouring elements with the same
-    per-value arithmetic: states equal the untiled gather path bit for bit (ragged tiles included)."""
+    per-value arithmetic: states equal the untiled gather path bit for bit (ragged tiles included),
+    also for its build capped at 128 registers."""
     spec = W.bar_chain("tile", 11, [13, 9], ["fom", "fom"], material, 1e9, 0.3, 1000.0, 2e-3, 1e-6, 5)
-    a = osam.Problem(spec, scatter=osam.SCATTER_GATHER_TILED)
+    mode = osam.SCATTER_GATHER_TILED if tiled == "tiled" else osam.SCATTER_GATHER_TILED_LOWREG
+    a = osam.Problem(spec, scatter=mode)
     b = osam.Problem(spec, scatter=osam.SCATTER_GATHER)
     assert a.tuning()["tiled"] and not b.tuning()["tiled"]
+    assert a.tuning()["register_cap"] == (128 if tiled == "tiled_lowreg" else 0)
     for _ in range(3):
         ra, rb = a.step(), b.step()
         assert ra["iterations"] == rb["iterations"] and ra["cnum"] == rb["cnum"]
