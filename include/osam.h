@@ -174,7 +174,11 @@ OSAM_API int schwarz_init(const osam_problem_desc* desc, osam_ctx** out);
 
 /* Advance subdomain `sub` over the current controller interval (n_substeps steps) from its current
  * state, with Dirichlet data from its input boundary history (Eq. schwarz_discrete / Eq.
- * schwarz_opinf_discrete), and record its trace at every Schwarz node it feeds. */
+ * schwarz_opinf_discrete), and record its trace at every Schwarz node it feeds.  The step count is the
+ * subdomain's own substep count from its description (osam_subdomain_desc.n_substeps, else the
+ * problem's), not an argument: the boundary history, the temporal interpolant and the criterion are
+ * all laid out for that count when the context is built, so a different count per call would have no
+ * matching boundary data. */
 OSAM_API int subdomain_advance(osam_ctx* ctx, int sub);
 
 /* Publish src's recorded trace of the current interval into dst's input boundary history -- the
@@ -355,6 +359,9 @@ typedef struct {
     double* C;                /* [r][r(r+1)(r+2)/6] cubic operator (cubic fits), or NULL */
 } osam_fit_output;
 
+/* The regularisation lambda is a field of osam_fit_input (next to the other fit settings it goes with,
+ * e.g. the same input serves opinf_select, which ignores it and scans its candidates) rather than a
+ * separate argument. */
 OSAM_API int opinf_fit(const osam_fit_input* in, osam_fit_output* out);
 
 /* Schwarz-aware regularisation selection (Sec. 4.2.4, Algorithm 3): for every candidate lambda the
