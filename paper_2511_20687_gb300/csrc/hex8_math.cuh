@@ -418,6 +418,32 @@ __device__ __forceinline__ void edge_differences_prescaled(const double V[8], T 
         }
 }
 
+// edge differences for the FP32 force from the (hi, lo) float split of u/h (hi = fl32(u/h), lo =
+// fl32(u/h - hi)): (hi1 - hi0) + (lo1 - lo0) on the FP32 pipes.  For neighbouring nodes of a smooth
+// field hi1 - hi0 is exact (Sterbenz) or far larger than the lo terms, so the difference keeps FP32
+// relative accuracy without FP64 arithmetic (the FP64 form costs an FP64 subtraction and conversion
+// per difference, which bound the FP32 kernel by the FP64 pipe).
+__device__ __forceinline__ void edge_differences_split(const float2 V[8], float Dx[2][2], float Dy[2][2],
+                                                       float Dz[2][2]) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float2 x1 = V[1 + 2 * p + 4 * q], x0 = V[2 * p + 4 * q];
+            const float2 y1 = V[p + 2 + 4 * q], y0 = V[p + 4 * q];
+            const float2 z1 = V[p + 2 * q + 4], z0 = V[p + 2 * q];
+            Dx[p][q] = (x1.x - x0.x) + (x1.y - x0.y);
+            Dy[p][q] = (y1.x - y0.x) + (y1.y - y0.y);
+            Dz[p][q] = (z1.x - z0.x) + (z1.y - z0.y);
+        }
+}
+
+// (hi, lo) float split of an FP64 value
+__device__ __forceinline__ float2 split_f2(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 // nodal force of node (i,j,k), component c, from the element buffer (fixed order: deterministic)
 template <typename TF>
 __device__ __forceinline__ double gather_force(const TF* fe, int nx, int ny, int nz, int ne, int i, int j, int k,

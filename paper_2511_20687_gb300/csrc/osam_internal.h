@@ -91,7 +91,7 @@ struct FomB {
     double* hist;             // per instance [(nsub+1)][3 fields][3 comps][ns] at hist_off
     double* partial;          // criterion partial sums, 2 per node block
     double* us;               // predicted displacement divided by h [3][NN] (input of the FP64 / FP32 force)
-    float2* u2;               // double-float copy of the predicted displacement / h [3][NN] (f32x2 force)
+    float2* u2;               // (hi, lo) float split of the predicted displacement / h [3][NN] (f32x2 and FP32 force)
     int material, fp32, scatter;
     int occ;                  // 1: FP64 gather force capped at 128 registers
     const int4* tblk;         // 8x4x4 element tiles: (instance, i0, j0, k0)

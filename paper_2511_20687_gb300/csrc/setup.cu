@@ -193,7 +193,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     CKA(B.pv = ctx->alloc<double>(3 * NN));
     CKA(B.hist = ctx->alloc<double>(std::max<long long>(H, 1)));
     CKA(B.us = ctx->alloc<double>(3 * NN));
-    if (B.df32) CKA(B.u2 = ctx->alloc<float2>(3 * NN));
+    if (B.df32 || B.fp32) CKA(B.u2 = ctx->alloc<float2>(3 * NN));   // the FP32 forces' split of u/h
     B.implicit = descs[0].subdomains[s].integrator == OSAM_IMPLICIT;
     if (B.implicit) {
         ctx->any_implicit = true;
@@ -267,7 +267,7 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
     RET(set_eblocks(ctx, G, 128));
     RET(set_tiles(ctx, G));
     RET(check_stability(ctx, G, s, n, descs));
-    if (B.df32) CK(launch_split_u2_b(B, ctx->stream));
+    if (B.df32 || B.fp32) CK(launch_split_u2_b(B, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
 }

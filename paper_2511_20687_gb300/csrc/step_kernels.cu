@@ -58,13 +58,25 @@ __device__ __forceinline__ void force_body(const FomB& g, const int* __restrict_
         material_factors<MAT, T>(I.lam_e ? I.lam_e[e] : I.lam, I.mu_e ? I.mu_e[e] : I.mu, I.wq, I.wq3, m1, m2, m3);
     else { m1 = T(I.m1); m2 = T(I.m2); m3 = T(I.m3); }
     T Dx[3][2][2], Dy[3][2][2], Dz[3][2][2];
-    const double* ub = g.us + I.node_off;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 force: differences of the float split of u/h (the node kernel writes it beside u/h)
+        const float2* ub2 = g.u2 + I.node_off;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double U[8];
+        for (int c = 0; c < 3; ++c) {
+            float2 U2[8];
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) U[c8] = ub[(long long)c * g.NN + node[c8]];
-        edge_differences_prescaled<T>(U, Dx[c], Dy[c], Dz[c]);
+            for (int c8 = 0; c8 < 8; ++c8) U2[c8] = ub2[(long long)c * g.NN + node[c8]];
+            edge_differences_split(U2, Dx[c], Dy[c], Dz[c]);
+        }
+    } else {
+        const double* ub = g.us + I.node_off;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double U[8];
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) U[c8] = ub[(long long)c * g.NN + node[c8]];
+            edge_differences_prescaled<T>(U, Dx[c], Dy[c], Dz[c]);
+        }
     }
     T F[3][8];
     element_force<MAT, T>(Dx, Dy, Dz, m1, m2, m3, F);
@@ -371,6 +383,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
         if (h2) {
             unext[d] = un;
             g.us[d] = un * I.invh;
+            if (sizeof(TF) == 4) g.u2[d] = split_f2(un * I.invh);   // FP32 force input
         }
     }
 }
