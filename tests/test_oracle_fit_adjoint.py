@@ -316,3 +316,44 @@ def test_cubic_rom_subdomain_integrates_a_duffing_oscillator(oracle):
     errs = [abs(run(n) - ref) for n in (400, 800, 1600)]
     assert errs[2] < 1e-3 * a0
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_quadratic_rom_subdomain_integrates_its_ode(oracle):
+    """A two-mode quadratic ROM subdomain q'' = K q + H kron_c(q) + c (Eq. schwarz_opinf_discrete with
+    the constant of reading c10), kron_c(q) = (q0^2, q0 q1, q1^2), every H column and both c entries
+    distinct: the controller's trajectory converges at second order to the ODE's solution (scipy,
+    tight tolerances), and dropping H changes it at leading order -- so the compressed column order,
+    the row order of H and the sign and placement of c are all pinned."""
+    from scipy.integrate import solve_ivp
+    w0, w1, a0, a1, T = 2.0e4, 3.0e4, 1e-3, 5e-4, 4e-4
+    K = np.diag([-w0 * w0, -w1 * w1])
+    H = np.array([[1e11, 3e11, -2e11], [-4e11, 2e11, 5e11]])
+    c = np.array([1e4, -2e4])
+
+    def rhs(t, y, Hm):
+        q = y[:2]
+        kq = np.array([q[0] * q[0], q[0] * q[1], q[1] * q[1]])
+        return np.concatenate([y[2:], K @ q + Hm @ kq + c])
+
+    ode = lambda Hm: solve_ivp(rhs, (0.0, T), [a0, a1, 0.0, 0.0], args=(Hm,), rtol=1e-12, atol=1e-18,
+                               method="DOP853").y[:2, -1]
+    ref = ode(H)
+    assert np.abs(ref - ode(np.zeros_like(H))).max() > 0.05 * a0   # the quadratic term matters
+
+    def run(n_steps):
+        sd = W.Subdomain(kind="rom", dims=(1, 1, 1), h=0.01, origin=(0.0, 0.0, 0.0))
+        sd.dirichlet = np.zeros(sd.n_nodes, np.uint8)
+        sd.u0 = np.zeros((sd.n_nodes, 3))
+        sd.u0[0, 0], sd.u0[0, 1] = a0, a1
+        sd.v0 = np.zeros((sd.n_nodes, 3))
+        p = W.Problem(name="quadratic", subdomains=[sd], couplings=[], dt=T / n_steps, n_substeps=n_steps)
+        Phi = np.zeros((3 * sd.n_nodes, 2))
+        Phi[0, 0] = Phi[1, 1] = 1.0
+        ops = {"Phi": Phi, "Phi_S": np.zeros((0, 0)), "K": K, "H": H, "B": np.zeros((2, 0)), "c": c}
+        prob = oracle.Problem(p, rom_ops={0: ops})
+        prob.step()
+        return prob.rom_state(0)[0]
+
+    errs = [np.abs(run(n) - ref).max() for n in (400, 800, 1600)]
+    assert errs[2] < 1e-3 * a0
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
