@@ -56,14 +56,14 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "9544cf17b201411e62cdbee44c1ea7d973d12fc8d3153fa7d22c71333481dde7",
-                 "bytes_per_launch": 3.56672e6, "tiled": True, "register_cap": 0}
+FORCE_TRAFFIC = {"source_sha256": "585c72f815512979f05683a5fc4b661769beadb86c07d7a242dc6803938ca3b0",
+                 "bytes_per_launch": 3.577344e6, "tiled": True, "register_cap": 0}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
 TANGENT_BYTES_PER_ELEMENT = 22 * 8 * 8 + 24
-TANGENT_TRAFFIC = {"source_sha256": "e57ddf845a4e93890393885ca4f7b13edf7edc3f7241c56e37fbac8521fc4a41",
-                   "bytes_per_launch": 1.93736e8}
+TANGENT_TRAFFIC = {"source_sha256": "62b5af73dcb2441b8e0f127c2e495699e646666c0e90910d1de69a4f67bdb3a4",
+                   "bytes_per_launch": 1.93771e8}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152

@@ -202,3 +202,51 @@ def test_opinf_fit_beyond_four_million_rows(torch_cuda):
     same seeded snapshots of a known quadratic model."""
     from .test_gpu_parity import _check_fit, _fit_case
     _check_fit(*_fit_case(5_391_357, 60, 56_454, 23))
+
+
+def test_hybrid_40x40x80_fitted_rom_properties(torch_cuda):
+    """The benchmark's own configuration: the r = 64 ROM trained on the GPU from a FOM-FOM run of the
+    40x40x80 geometry (500 controller steps of 4 substeps, snapshots kept on the device) and fitted by
+    opinf_fit, coupled to the tiled FP64 FOM.  The oracle never takes operators fitted on the GPU (its
+    inputs do not come from the CUDA path; its full-size comparison above uses seeded stand-in operators
+    of these sizes), so this run is checked by properties that hold at any size: the double-float force
+    mode agrees with FP64 to 1e-9 over 3 controller steps, the graph-captured step equals the
+    host-driven loop bit for bit, and every step converges before the iteration cap."""
+    torch = torch_cuda
+    rng = np.random.default_rng(W.SEED_BASE + 1)
+    amp = float(rng.uniform(0.5e-3, 1.0e-3))
+    train = W.bar_chain("train", 40, [80, 80], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, amp, 1e-6, 4)
+    free, sdof = W.subdomain_dof_masks(train, 1)
+    fi = torch.from_numpy(np.flatnonzero(free)).cuda()
+    si = torch.from_numpy(np.flatnonzero(sdof)).cuda()
+    ns = 500
+    U = torch.empty((ns, fi.numel()), dtype=torch.float64, device="cuda")
+    A = torch.empty_like(U)
+    S = torch.empty((ns, si.numel()), dtype=torch.float64, device="cuda")
+    bu = torch.empty((train.subdomains[1].n_nodes, 3), dtype=torch.float64, device="cuda")
+    ba = torch.empty_like(bu)
+    tp = osam.Problem(train)
+    for k in range(ns):
+        tp.step()
+        tp.state(1, out=(bu, None, ba))
+        U[k], A[k], S[k] = bu.reshape(-1)[fi], ba.reshape(-1)[fi], bu.reshape(-1)[si]
+    tp.close()
+    ops = osam.opinf_fit(U, A, S, r=64, lam=1e-6, r_s=0, energy_s=1.0 - 1e-6, r_s_max=64)
+    del U, A, S
+    rom = {1: {k: ops[k] for k in ("Phi", "Phi_S", "K", "H", "B", "c")}}
+    spec = W.fom_opinf_hybrid(40, 80, rom=True)
+    g = osam.Problem(spec, rom_ops=rom, scatter=osam.SCATTER_GATHER_TILED, graph=True)
+    h = osam.Problem(spec, rom_ops=rom, scatter=osam.SCATTER_GATHER_TILED, graph=False)
+    d = osam.Problem(spec, rom_ops=rom, precision=osam.F32X2_FORCE)
+    hg, hd = [], []
+    for _ in range(3):
+        rg, rh, rd = g.step(), h.step(), d.step()
+        assert rg["status"] == osam.OK and rg["iterations"] < spec.max_iters
+        assert rg["iterations"] == rh["iterations"] and rg["cnum"] == rh["cnum"]
+        hg.append(g.state(0)[0].copy())
+        hd.append(d.state(0)[0].copy())
+        assert np.array_equal(g.state(0)[0], h.state(0)[0])
+        assert np.array_equal(g.reduced_state(1)[0], h.reduced_state(1)[0])
+    assert rel_l2(hd, hg) < 1e-9
+    for p in (g, h, d):
+        p.close()
