@@ -56,8 +56,8 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "585c72f815512979f05683a5fc4b661769beadb86c07d7a242dc6803938ca3b0",
-                 "bytes_per_launch": 3.577344e6, "tiled": True, "register_cap": 0}
+FORCE_TRAFFIC = {"source_sha256": "967e0e4190d286474408e350258f88587fcc7deea972eebffd098024c5708ff7",
+                 "bytes_per_launch": 3.567104e6, "tiled": True, "register_cap": 0}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
@@ -395,7 +395,7 @@ def measure_batched(W, osam, torch, flush, args, device, log, rank=0, world=1):
     # every force launch
     batch.profile(True)
     batch.set_graph(False)
-    batch.step()
+    _, prof_tot = batch.step()
     bprof = batch.profile_read()
     batch.profile(False)
     batch.close()
@@ -456,6 +456,9 @@ def measure_batched(W, osam, torch, flush, args, device, log, rank=0, world=1):
                         "frac": bach_force / FP64_PEAK[0], "flops_per_element": FLOPS_PER_NH_ELEMENT,
                         "force_ms_per_launch": bprof["force_ms"] / max(1, bprof["force_launches"]),
                         "elements_per_launch": bprof["force_elements"] // max(1, bprof["force_launches"]),
+                        "force_launches_per_step": bprof["force_launches"],
+                        "force_time_share": bprof["force_ms"] / prof_tot["elapsed_ms"],
+                        "kernel_launches_per_step": bprof["kernel_launches"],
                         "peak_kind": FP64_PEAK_KIND[0]},
            "tiled_forced": {"value_device": t_upd_all / (t_dev * 1e-3), "steps": 2,
                             "note": "the same samples with the 8x4x4-tile force kernel forced (n x n x 2n "

@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
     // all loads of a free node first (state and the element contributions of the three components,
     // summed per component in the fixed corner order), so that they are in flight together
     double uc[3], vc[3], ac[3], f[3] = {0.0, 0.0, 0.0};
+    TF fs[3] = {TF(0), TF(0), TF(0)};   // the gather sums in the element buffer's precision
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long d = (long long)c * g.NN + gn;
@@ -343,10 +344,13 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
                         const long long e = ie + (long long)I.nx * (je + I.ny * ke);
                         const int corner = ax + 2 * ay + 4 * az;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) f[c] += double(__ldg(fe + (long long)(corner * 3 + c) * g.NE + e));
+                        for (int c = 0; c < 3; ++c) fs[c] += __ldg(fe + (long long)(corner * 3 + c) * g.NE + e);
                     }
                 }
             }
+            // FP64: the same sums; FP32 force: summed in FP32 (its own precision) and converted once
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = double(fs[c]);
         } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) f[c] = double(fa[(long long)c * g.NN + gn]);
