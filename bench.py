@@ -12,7 +12,8 @@ value   = FOM element-updates executed in the timed steps / device time of those
           launch of the library's captured controller-step graph (its default path), CUDA events on the
           library's stream; L2 flushed between steps by a 256 MiB write outside the timing.
 e2e     = the same metric through the public API with host buffers: every step sets the FOM and ROM
-          states from pinned host memory, runs schwarz_step and reads the states back.
+          states from pinned host memory, runs schwarz_step (its default, graph-captured path) and reads
+          the states back; wall-clock time on the host.
 roofline= the Neo-Hookean FP64 internal-force kernel (the dominant kernel): algorithmic FP64 flops of
           its launches / their CUDA-event time, from a second timed pass of the same steps driven from
           the host with events around every force launch, against the FP64 peak.
@@ -1142,7 +1143,10 @@ def timed_pass(prob, torch, flush, steps, profile):
 
 
 def e2e_pass(prob, torch, steps, rank_r):
-    """Same metric through the public API with pinned host buffers: state in, step, state out."""
+    """Same metric through the public API with pinned host buffers: state in, step, state out, on the
+    library's default path (graph-captured controller steps; the profiling pass before this one drives
+    the steps from the host)."""
+    prob.set_graph(True)
     nA = prob.sizes(0)["n_nodes"]
     hu = [torch.empty((nA, 3), dtype=torch.float64).pin_memory() for _ in range(3)]
     hq = [torch.empty(rank_r, dtype=torch.float64).pin_memory() for _ in range(3)]

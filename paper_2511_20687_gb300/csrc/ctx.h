@@ -246,6 +246,34 @@ inline int upload(osam_ctx* ctx, void* dst, const void* src, size_t bytes) {
     return OSAM_OK;
 }
 
+// Address at which the context's kernels can read or write the caller's buffer p in place: device
+// memory of the context's device, or page-locked host memory mapped into the device's address space
+// (cudaHostAlloc, cudaHostRegister; torch's pinned tensors).  nullptr for anything else (pageable
+// host memory, managed memory, another device's memory): those are staged through the scratch buffer
+// with a copy.
+inline void* direct_view(osam_ctx* ctx, const void* p) {
+    cudaPointerAttributes at{};
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // an unregistered host pointer may leave an error behind on older runtimes
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == ctx->device ? at.devicePointer : nullptr;
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+    return nullptr;
+}
+
+// Device-readable form of the caller's n doubles at p: p's own device view when direct_view gives one,
+// else the staging buffer, filled by an asynchronous copy in stream order.
+inline int stage_in(osam_ctx* ctx, const double* p, size_t n, const double** out) {
+    if (const void* d = direct_view(ctx, p)) {
+        *out = static_cast<const double*>(d);
+        return OSAM_OK;
+    }
+    RET(upload(ctx, ctx->scratch, p, sizeof(double) * n));
+    *out = ctx->scratch;
+    return OSAM_OK;
+}
+
 template <typename T>
 inline int to_host(osam_ctx* ctx, std::vector<T>& out, const T* src, size_t n) {
     out.resize(n);

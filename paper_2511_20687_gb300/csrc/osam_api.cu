@@ -270,22 +270,27 @@ int osam_instance_get_state(osam_ctx* ctx, int inst, int sub, double* u, double*
     double* outs[3] = {u, v, a};
     for (int f = 0; f < 3; ++f) {
         if (!outs[f]) continue;
+        // a device-accessible buffer (this device's memory, mapped page-locked host memory) is written
+        // in place by the layout kernel; anything else through the staging buffer and a copy
+        double* direct = static_cast<double*>(direct_view(ctx, outs[f]));
+        double* dst = direct ? direct : ctx->scratch;
         int nn;
         if (S.kind == OSAM_FOM) {
             const InstFom& I = S.fom.inst[inst];
             nn = I.nn;
             const double* src = f == 0 ? S.fom.d.u[0] : (f == 1 ? S.fom.d.v : S.fom.d.a);
-            CK(launch_soa_to_aos(src + I.node_off, ctx->scratch, nn, S.fom.d.NN, ctx->stream));
+            CK(launch_soa_to_aos(src + I.node_off, dst, nn, S.fom.d.NN, ctx->stream));
         } else {
             RomGroupH& G = S.rom;
             const InstRom& I = G.inst[inst];
             nn = G.grid[inst].nn();
             const double* hs = G.d.hist + I.hist_off + ((long long)S.nsub * 3 + f) * I.nsdof;
             CK(launch_rom_full_field(nn, I.r, G.Phi[inst], G.dof_free[inst], G.clamp_d[inst], G.srow_d[inst], hs,
-                                     G.d.q + I.q_off + (long long)f * I.r, ctx->scratch, ctx->stream));
+                                     G.d.q + I.q_off + (long long)f * I.r, dst, ctx->stream));
         }
         // stream order lets the next field reuse the staging buffer; one host synchronisation at the end
-        CK(cudaMemcpyAsync(outs[f], ctx->scratch, sizeof(double) * 3 * nn, cudaMemcpyDefault, ctx->stream));
+        if (!direct)
+            CK(cudaMemcpyAsync(outs[f], ctx->scratch, sizeof(double) * 3 * nn, cudaMemcpyDefault, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return OSAM_OK;
@@ -298,24 +303,25 @@ int osam_get_state(osam_ctx* ctx, int sub, double* u, double* v, double* a) {
 int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, const double* v, const double* a) {
     if (!valid(ctx, inst, sub) || !u) return OSAM_EINVAL;
     Slot& S = ctx->slots[sub];
+    const double* src = nullptr;
     if (S.kind == OSAM_FOM) {
         FomB& g = S.fom.d;
         const InstFom& I = S.fom.inst[inst];
         // the staging buffer is reused in stream order; the caller's buffers are released by the final
         // synchronisation
-        RET(upload(ctx, ctx->scratch, u, sizeof(double) * 3 * I.nn));
-        CK(launch_aos_to_soa(ctx->scratch, g.u[0] + I.node_off, I.nn, g.NN, ctx->stream));
+        RET(stage_in(ctx, u, 3 * (size_t)I.nn, &src));
+        CK(launch_aos_to_soa(src, g.u[0] + I.node_off, I.nn, g.NN, ctx->stream));
         if (v) {
-            RET(upload(ctx, ctx->scratch, v, sizeof(double) * 3 * I.nn));
-            CK(launch_aos_to_soa(ctx->scratch, g.v + I.node_off, I.nn, g.NN, ctx->stream));
+            RET(stage_in(ctx, v, 3 * (size_t)I.nn, &src));
+            CK(launch_aos_to_soa(src, g.v + I.node_off, I.nn, g.NN, ctx->stream));
         } else {
             for (int c = 0; c < 3; ++c)
                 CK(cudaMemsetAsync(g.v + c * g.NN + I.node_off, 0, sizeof(double) * I.nn, ctx->stream));
         }
         CK(launch_zero_clamped(I.nn, g.clamp + I.node_off, g.u[0] + I.node_off, g.v + I.node_off, g.NN, ctx->stream));
         if (a) {
-            RET(upload(ctx, ctx->scratch, a, sizeof(double) * 3 * I.nn));
-            CK(launch_aos_to_soa(ctx->scratch, g.a + I.node_off, I.nn, g.NN, ctx->stream));
+            RET(stage_in(ctx, a, 3 * (size_t)I.nn, &src));
+            CK(launch_aos_to_soa(src, g.a + I.node_off, I.nn, g.NN, ctx->stream));
         } else {
             RET(select_instance(ctx, inst));
             CK(launch_force_init_b(g, ctx->sel, ctx->stream));
@@ -326,13 +332,13 @@ int osam_instance_set_state(osam_ctx* ctx, int inst, int sub, const double* u, c
         const InstRom& I = G.inst[inst];
         const int nn = G.grid[inst].nn();
         std::vector<double> qh(I.r), qdh(I.r, 0.0);
-        RET(upload(ctx, ctx->scratch, u, sizeof(double) * 3 * nn));
-        CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], ctx->scratch, nullptr,
+        RET(stage_in(ctx, u, 3 * (size_t)nn, &src));
+        CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], src, nullptr,
                                     G.d.q + I.q_off, ctx->stream));
         RET(to_host(ctx, qh, G.d.q + I.q_off, I.r));
         if (v) {
-            RET(upload(ctx, ctx->scratch, v, sizeof(double) * 3 * nn));
-            CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], ctx->scratch, nullptr,
+            RET(stage_in(ctx, v, 3 * (size_t)nn, &src));
+            CK(launch_rom_basis_project(G.nfree[inst], I.r, G.Phi[inst], G.free_dof[inst], src, nullptr,
                                         G.d.q + I.q_off, ctx->stream));
             RET(to_host(ctx, qdh, G.d.q + I.q_off, I.r));
         }

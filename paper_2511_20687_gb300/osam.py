@@ -332,9 +332,15 @@ class Batch:
                 "newton_steps": v[2].value, "cg_iterations": v[3].value}
 
     def sizes(self, i, inst=0):
-        v = [C.c_int() for _ in range(4)]
-        self._c(load().osam_instance_sizes(self.h, inst, i, *[C.byref(x) for x in v]))
-        return {"n_nodes": v[0].value, "n_elements": v[1].value, "n_free": v[2].value, "n_schwarz": v[3].value}
+        """Node, element, free-dof and Schwarz-node counts of subdomain i (fixed at initialisation, so
+        asked of the library once per subdomain: its free-dof count is a pass over the masks)."""
+        cache = self.__dict__.setdefault("_sizes", {})
+        if (i, inst) not in cache:
+            v = [C.c_int() for _ in range(4)]
+            self._c(load().osam_instance_sizes(self.h, inst, i, *[C.byref(x) for x in v]))
+            cache[(i, inst)] = {"n_nodes": v[0].value, "n_elements": v[1].value, "n_free": v[2].value,
+                                "n_schwarz": v[3].value}
+        return dict(cache[(i, inst)])
 
     def state(self, i, out=None, fields=(0, 1, 2), inst=0):
         """(u, v, a) of subdomain i of instance inst as [nodes, 3] arrays (numpy unless `out` arrays /

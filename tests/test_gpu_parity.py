@@ -338,6 +338,48 @@ def test_set_state_roundtrip(torch_cuda):
     assert np.array_equal(u3[~clamped], u2[~clamped]) and np.all(u3[clamped] == 0)
 
 
+def test_state_calls_agree_for_pageable_pinned_and_device_buffers(torch_cuda):
+    """Pageable host arrays go through the staging buffer; pinned host and device tensors are read and
+    written in place by the layout kernels.  All three give the same states, for a FOM and for the
+    reconstructed field of a ROM, and a state set from any of them steps identically."""
+    torch = torch_cuda
+    spec = W.bar_chain("views", 3, [6, 6], ["fom", "rom"], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 5, max_iters=6)
+    sd = spec.subdomains[1]
+    n_sdof = 3 * (sd.dims[0] + 1) ** 2
+    ops = {1: W.synthetic_rom_operators(3 * sd.n_nodes - n_sdof, n_sdof, 5, 4, 21)}
+    g = osam.Problem(spec, rom_ops=ops, scatter=osam.SCATTER_GATHER)
+    g.step()
+    for i in range(2):
+        n = g.sizes(i)["n_nodes"]
+        ref = g.state(i)
+        pinned = tuple(torch.full((n, 3), np.nan, dtype=torch.float64).pin_memory() for _ in range(3))
+        device = tuple(torch.full((n, 3), np.nan, dtype=torch.float64, device="cuda") for _ in range(3))
+        g.state(i, out=pinned)
+        g.state(i, out=device)
+        for f in range(3):
+            assert np.array_equal(pinned[f].numpy(), ref[f])
+            assert np.array_equal(device[f].cpu().numpy(), ref[f])
+    u, v, a = g.state(0)
+    rng = np.random.default_rng(5)
+    u2 = u + 1e-6 * rng.standard_normal(u.shape)
+    runs = []
+    for kind in ("pageable", "pinned", "device"):
+        p = osam.Problem(spec, rom_ops=ops, scatter=osam.SCATTER_GATHER)
+        p.step()
+        if kind == "pageable":
+            p.set_state(0, u2, v, a)
+        else:
+            ts = [torch.from_numpy(np.ascontiguousarray(x)) for x in (u2, v, a)]
+            ts = [t.pin_memory() if kind == "pinned" else t.cuda() for t in ts]
+            p.set_state(0, *ts)
+        p.step()
+        runs.append((p.state(0), p.reduced_state(1)))
+    for (s, q) in runs[1:]:
+        for f in range(3):
+            assert np.array_equal(s[f], runs[0][0][f])
+            assert np.array_equal(q[f], runs[0][1][f])
+
+
 @pytest.mark.parametrize("graph", [True, False])
 def test_single_iteration_cap_matches_oracle(torch_cuda, graph):
     """max_iters = 1: the criterion needs two iterates, so every controller step commits after one
