@@ -93,6 +93,8 @@ def measure_fp64_peak(osam, local, repeats=10):
     fma, _ = osam.fp64_probe(0, repeats, local)
     mma, _ = osam.fp64_probe(1, repeats, local)
     mix, _ = osam.fp64_probe(2, max(2, repeats // 2), local)
+    # the per-warp latency floor of the element kernels on small meshes (one block on one SM)
+    issue = {f"{w}_warps_{l}_lanes": osam.fp64_issue_probe(w, l, local) for w, l in ((1, 32), (1, 8), (4, 32), (8, 32))}
     clk = clocks.stop()
     best = float(max(fma.max(), mma.max()))
     FP64_PEAK[0] = best
@@ -101,6 +103,7 @@ def measure_fp64_peak(osam, local, repeats=10):
             "fma_best": float(fma.max()), "fma_median": float(np.median(fma)),
             "mma_best": float(mma.max()), "mma_median": float(np.median(mma)),
             "fma_plus_mma_interleaved_best": float(mix.max()),
+            "issue_ns_per_warp_instruction": issue,
             "sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "clock_reasons": clk["reasons"],
             "nominal_tflops": FP64_NOMINAL_TFLOPS,
             "kind": "measured: best of the FP64 FMA and FP64 tensor-core probes (osam_fp64_probe)"}

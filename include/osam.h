@@ -274,6 +274,12 @@ OSAM_API int osam_fp64_peak(int device, double* gflops);
  * (total flops), which shows whether the two share one unit.  Synchronous; allocates a small
  * output buffer.  Bad arguments -> OSAM_EINVAL. */
 OSAM_API int osam_fp64_probe(int device, int kind, int repeats, double* tflops, double* ms);
+/* FP64 issue probe: one block of `warps` warps (1..32), `lanes` active lanes each (1..32), running
+ * 8 independent FMA chains per thread alone on one SM of device `device`; *ns_per_instruction = the
+ * time per FP64 warp-instruction of one warp (best of three launches of ~160,000 instructions per
+ * warp).  With few warps per SM sub-partition this is the latency floor of an element kernel on a
+ * small mesh.  Synchronous; allocates a small output buffer.  Bad arguments -> OSAM_EINVAL. */
+OSAM_API int osam_fp64_issue_probe(int device, int warps, int lanes, double* ns_per_instruction);
 /* The scatter mode in use (OSAM_SCATTER_ATOMIC / GATHER) after any autotuning. */
 OSAM_API int osam_scatter_mode(osam_ctx* ctx);
 /* Free every resource of ctx (library-owned memory, streams, graphs); caller memory is untouched.

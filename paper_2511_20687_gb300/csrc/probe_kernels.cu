@@ -6,6 +6,9 @@
 //   kind 2: both in one kernel (the same warps interleave the chains of kinds 0 and 1), which shows
 //           whether the two share one unit: if they do, its time is the sum of the other two.
 // Each repeat is one launch of roughly 20 ms at the nominal rate, timed with CUDA events.
+// The issue probe runs the FMA chains of kind 0 in one block (one SM) of `warps` warps with `lanes`
+// active lanes each: the time per FP64 warp-instruction of one warp, the latency floor of element
+// kernels on meshes too small to give every SM sub-partition several warps.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -50,6 +53,23 @@ __global__ void __launch_bounds__(256) k_fp64_probe(int iters, double seed, doub
 #pragma unroll
     for (int k = 0; k < kMmaChains; ++k) s += c0[k] + c1[k];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// FP64 FMA chains of kind 0 on the first `lanes` lanes of every warp of one block
+__global__ void __launch_bounds__(1024) k_fp64_issue(int lanes, int iters, double* out) {
+    double a[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    const double m = 0.999999, c = 1e-7;
+    if ((int)(threadIdx.x & 31) < lanes)
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], m, c);
+        }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += a[k];
+    out[threadIdx.x] = s;
 }
 
 // flops of one loop iteration of one 256-thread block
@@ -111,4 +131,40 @@ extern "C" OSAM_API int osam_fp64_peak(int device, double* gflops) {
     for (double x : t) best = x > best ? x : best;
     *gflops = best * 1e3;
     return OSAM_OK;
+}
+
+// time per FP64 warp-instruction of one warp when one block of `warps` warps (1..32) with `lanes`
+// active lanes each (1..32) runs the FMA chains alone on one SM: best of three launches of ~20000
+// iterations of 8 independent FMAs
+extern "C" OSAM_API int osam_fp64_issue_probe(int device, int warps, int lanes, double* ns_per_instruction) {
+    if (!ns_per_instruction || warps < 1 || warps > 32 || lanes < 1 || lanes > 32) return OSAM_EINVAL;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return OSAM_ECUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return OSAM_ECUDA;
+    const int threads = 32 * warps, iters = 20000;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * threads) != cudaSuccess) return OSAM_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    osam::k_fp64_issue<<<1, threads>>>(lanes, 64, out);   // warm-up
+    cudaError_t err = cudaGetLastError();
+    double best = 0.0;
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) {
+        cudaEventRecord(e0);
+        osam::k_fp64_issue<<<1, threads>>>(lanes, iters, out);
+        cudaEventRecord(e1);
+        err = cudaGetLastError();
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (err == cudaSuccess && t <= 0.f) err = cudaErrorUnknown;
+        const double ns = t * 1e6 / ((double)iters * osam::kFmaChains);
+        if (r == 0 || ns < best) best = ns;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    *ns_per_instruction = best;
+    return err == cudaSuccess ? OSAM_OK : OSAM_ECUDA;
 }

@@ -621,11 +621,12 @@ int autotune(osam_ctx* ctx) {
     FomGroupH& G = *best_g;
     FomB g = G.d;
     const long long NN = g.NN;
-    double *u = nullptr, *v = nullptr, *a = nullptr, *un = nullptr;
-    CK(cudaMalloc(&u, sizeof(double) * 3 * NN));
-    CK(cudaMalloc(&v, sizeof(double) * 3 * NN));
-    CK(cudaMalloc(&a, sizeof(double) * 3 * NN));
-    CK(cudaMalloc(&un, sizeof(double) * 3 * NN));
+    struct Scratch {   // the candidates' state copies, freed on every return path
+        double* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Scratch() { for (double* q : p) cudaFree(q); }
+    } sc;
+    for (double*& q : sc.p) CK(cudaMalloc(&q, sizeof(double) * 3 * NN));
+    double *u = sc.p[0], *v = sc.p[1], *a = sc.p[2], *un = sc.p[3];
     CK(cudaMemcpyAsync(u, G.d.u[0], sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(v, G.d.v, sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(a, G.d.a, sizeof(double) * 3 * NN, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -669,7 +670,6 @@ int autotune(osam_ctx* ctx) {
     }
     CK(cudaMemsetAsync(G.d.f, 0, sizeof(double) * 3 * NN, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    cudaFree(u); cudaFree(v); cudaFree(a); cudaFree(un);
     ctx->scatter = best_scatter;
     for (Slot& S : ctx->slots)
         if (S.kind == OSAM_FOM) {

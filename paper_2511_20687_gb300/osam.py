@@ -28,7 +28,7 @@ EXPORTED = ["schwarz_init", "subdomain_advance", "transfer_overlap", "osam_begin
             "osam_criterion", "schwarz_step", "osam_get_state", "osam_set_state", "osam_get_reduced_state",
             "osam_set_reduced_state", "osam_sizes", "osam_scatter_mode", "osam_destroy", "osam_last_error",
             "osam_hex8_force", "osam_hex8_force_vjp", "opinf_fit", "osam_fit_last_error", "osam_adjoint",
-            "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_fp64_probe", "osam_hex8_force_noalloc", "osam_batch_init",
+            "osam_profile", "osam_profile_read", "osam_implicit_profile", "osam_fp64_peak", "osam_fp64_probe", "osam_fp64_issue_probe", "osam_hex8_force_noalloc", "osam_batch_init",
             "osam_batch_step", "osam_num_instances", "osam_instance_get_state", "osam_instance_set_state",
             "osam_instance_get_reduced_state", "osam_instance_set_reduced_state", "osam_instance_sizes",
             "osam_set_graph", "osam_tuning", "opinf_select", "osam_fit_profile"]
@@ -136,6 +136,7 @@ def load():
     L.osam_implicit_profile.argtypes = [_vp, _dp] + [C.POINTER(C.c_longlong)] * 4
     L.osam_fp64_peak.argtypes = [C.c_int, _dp]
     L.osam_fp64_probe.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
+    L.osam_fp64_issue_probe.argtypes = [C.c_int, C.c_int, C.c_int, _dp]
     L.osam_fit_profile.argtypes = [C.c_int, _dp, _dp, C.POINTER(C.c_longlong)]
     L.osam_batch_init.argtypes = [C.c_int, C.POINTER(ProblemDesc), C.POINTER(_vp)]
     L.osam_batch_step.argtypes = [_vp, C.POINTER(StepReport), C.POINTER(StepReport)]
@@ -529,6 +530,14 @@ def fp64_probe(kind=0, repeats=10, device=0):
     ms = np.zeros(repeats)
     _check(load().osam_fp64_probe(device, kind, repeats, t.ctypes.data_as(_dp), ms.ctypes.data_as(_dp)))
     return t, ms
+
+
+def fp64_issue_probe(warps=1, lanes=32, device=0):
+    """ns per FP64 warp-instruction of one warp, one block of `warps` warps with `lanes` active lanes
+    each alone on one SM."""
+    ns = C.c_double()
+    _check(load().osam_fp64_issue_probe(device, warps, lanes, C.byref(ns)))
+    return ns.value
 
 
 def fit_profile(enable: bool) -> dict:

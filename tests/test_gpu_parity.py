@@ -596,6 +596,21 @@ def test_profile_counters(torch_cuda):
     assert osam.fp64_peak_gflops(0) > 0.0
 
 
+def test_fp64_probes_are_consistent(torch_cuda):
+    """The throughput probe gives rates within a factor of the nominal 1.25 TFLOP/s; the issue probe's
+    per-warp interval is no shorter with eight warps on the SM than with one (the SM's FP64 share is
+    fixed), and it rejects block shapes outside 1..32 warps of 1..32 lanes."""
+    t, ms = osam.fp64_probe(0, 2, 0)
+    assert np.all(t > 0.1) and np.all(t < 5.0) and np.all(ms > 0.0)
+    one = osam.fp64_issue_probe(1, 32, 0)
+    eight = osam.fp64_issue_probe(8, 32, 0)
+    assert one > 0.0 and eight >= 0.9 * one
+    with pytest.raises(osam.OsamError):
+        osam.fp64_issue_probe(0, 32, 0)
+    with pytest.raises(osam.OsamError):
+        osam.fp64_issue_probe(1, 33, 0)
+
+
 # ---------------------------------------------------------------------------------------------
 # double-float force (f32x2): held to the FP64 tolerance
 # ---------------------------------------------------------------------------------------------
