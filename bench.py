@@ -74,6 +74,9 @@ STATE_BYTES_PER_NODE_UPDATE = 152
 # 36, derivative of the cofactor 63, scalar chain 4, dP 63) + 36 accumulation + 180 transposed
 # interpolation + 48 nodal accumulation.
 TANGENT_FLOPS_PER_NH_ELEMENT = 1832
+# bytes the FP32 tangent kernel must move per element: the FP32 linearisation (22 floats x 8 Gauss
+# points) from HBM, p at 8 nodes / 8 elements per node (24 B), the FP32 element buffer out (24 floats)
+TANGENT32_BYTES_PER_ELEMENT = 22 * 8 * 4 + 24 + 24 * 4
 # FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
 # around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
 FLOPS_PER_SVK_ELEMENT = 1424
@@ -632,35 +635,67 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
     spec.subdomains[0].integrator = "implicit"
     if max_iters:
         spec.max_iters = max_iters
-    prob = osam.Problem(spec, rom_ops=rom_ops, device=local)
-    for _ in range(warmup):
-        prob.step()
-    # headline of the block: the library's default path (the controller step as one graph, Newton and
-    # CG as device-side WHILE loops); then the host-driven loop with CUDA events around every tangent
-    prob.profile(False)
-    total_ms, upd, its = 0.0, 0, []
-    for _ in range(steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        r = prob.step()
-        total_ms += r["elapsed_ms"]
-        upd += r["element_updates"]
-        its.append(r["iterations"])
-    prob.profile(True)
-    p_ms, p_its = 0.0, []
-    for _ in range(steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        r = prob.step()
-        p_ms += r["elapsed_ms"]
-        p_its.append(r["iterations"])
-    ip = prob.implicit_profile()
-    prof = prob.profile_read()
-    prob.profile(False)
-    prob.close()
+
+    def run(precision):
+        tag = "implicit_tangent32" if precision == osam.FP64_TANGENT32 else "implicit_f64"
+        prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=precision)
+        for _ in range(warmup):
+            prob.step()
+        # the library's default path (the controller step as one graph, Newton and CG as device-side
+        # WHILE loops); then the host-driven loop with CUDA events around every tangent launch
+        prob.profile(False)
+        total_ms, upd, its = 0.0, 0, []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            r = prob.step()
+            total_ms += r["elapsed_ms"]
+            upd += r["element_updates"]
+            its.append(r["iterations"])
+        prob.profile(True)
+        p_ms, p_its = 0.0, []
+        torch.cuda.nvtx.range_push(tag + "_host")
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            r = prob.step()
+            p_ms += r["elapsed_ms"]
+            p_its.append(r["iterations"])
+        torch.cuda.nvtx.range_pop()
+        ip = prob.implicit_profile()
+        prof = prob.profile_read()
+        prob.profile(False)
+        prob.close()
+        return total_ms, upd, its, p_ms, p_its, ip, prof
+
+    total_ms, upd, its, p_ms, p_its, ip, prof = run(osam.FP64)
     ne = spec.subdomains[0].n_elements
     substeps = 20 * sum(p_its)
     achieved = TANGENT_FLOPS_PER_NH_ELEMENT * ip["tangent_elements"] / (ip["tangent_ms"] * 1e-3) / 1e12
+    # the same with the Neo-Hookean Newton tangent in FP32 (OSAM_FP64_TANGENT32): residual, Newton test
+    # and CG vectors in FP64; its tangent kernel moves the FP32 linearisation (704 B per element), reads
+    # p and writes the FP32 element buffer (96 B per element, L2-resident) -- an HBM-bound kernel
+    t_ms, t_upd, t_its, tp_ms, tp_its, tip, _ = run(osam.FP64_TANGENT32)
+    t_sub = 20 * sum(tp_its)
+    t_launch_ms = tip["tangent_ms"] / max(1, tip["tangent_launches"])
+    t_bytes = ne * TANGENT32_BYTES_PER_ELEMENT
+    hbm_peak, hbm_kind = measured_hbm_gbs()
+    t_gbs = t_bytes / (t_launch_ms * 1e-3) / 1e9 if t_launch_ms > 0 else None
+    fp32_tangent = {
+        "value": t_upd / (t_ms * 1e-3), "ms_per_step": t_ms / steps, "mean_iterations": float(np.mean(t_its)),
+        "newton_per_substep": tip["newton_steps"] / max(1, t_sub),
+        "cg_per_newton": tip["cg_iterations"] / max(1, tip["newton_steps"]),
+        "ms_per_step_host_loop": tp_ms / steps,
+        "tangent_time_share": tip["tangent_ms"] / tp_ms if tp_ms else None,
+        "roofline": {"bound": "hbm", "kernel": "k_tangent_lin32_b (Neo-Hookean, FP32)",
+                     "achieved": t_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": t_gbs / hbm_peak if (t_gbs and hbm_peak) else None, "peak_kind": hbm_kind,
+                     "algorithmic_bytes_per_launch": t_bytes, "ms_per_launch": t_launch_ms,
+                     "traffic": None},
+        "speedup_vs_fp64_tangent": (t_upd / t_ms) / (upd / total_ms),
+        "parity": "1e-9 relative L2 vs the oracle, 1e-10 vs the FP64 tangent (tests/test_gpu_implicit.py)"}
+    log(f"implicit, FP32 tangent: {t_ms / steps:.1f} ms/step, {fp32_tangent['newton_per_substep']:.2f} "
+        f"Newton/substep, {fp32_tangent['cg_per_newton']:.1f} CG/Newton, tangent {t_launch_ms * 1e3:.1f} us/launch")
     # bounded sample: a small implicit Neo-Hookean bar, 1 controller step of 4 substeps, both sides
     sample = W.single_bar("imp_sample", oracle_dims[0], oracle_dims[2], "nh", 1e9, 0.25, 1000.0, 1e-3, 1e-6, 4)
     sample.subdomains[0].integrator = "implicit"
@@ -700,7 +735,8 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
                       f"step of 4 substeps",
             "sample_gpu_value": ns * rg["iterations"] / (rg["elapsed_ms"] * 1e-3),
             "sample_oracle_value": ns / cpu_s, "oracle_cores": 1,
-            "parity": "1e-9 relative L2 vs the oracle (tests/test_gpu_implicit.py)"}
+            "parity": "1e-9 relative L2 vs the oracle (tests/test_gpu_implicit.py)",
+            "fp32_tangent": fp32_tangent}
 
 
 def _timed_steps(prob, torch, flush, steps, warmup):
@@ -774,10 +810,15 @@ def measure_next_rows(W, osam, torch, flush, rom_ops, args, local, log, steps=5,
     prob = osam.Problem(spec, rom_ops=rom_ops, device=local)
     ms, upd, its = _timed_steps(prob, torch, flush, max(2, steps // 2), 1)
     prob.close()
+    prob = osam.Problem(spec, rom_ops=rom_ops, device=local, precision=osam.FP64_TANGENT32)
+    t_ms, t_upd, t_its = _timed_steps(prob, torch, flush, max(2, steps // 2), 1)
+    prob.close()
     n = max(2, steps // 2)
     out["mixed_implicit_explicit"] = {
         "value": upd / (ms * 1e-3), "ms_per_step": ms / n, "mean_iterations": float(np.mean(its)),
         "intervals_per_s": n / (ms * 1e-3),
+        "fp32_tangent": {"value": t_upd / (t_ms * 1e-3), "ms_per_step": t_ms / n,
+                         "mean_iterations": float(np.mean(t_its)), "intervals_per_s": n / (t_ms * 1e-3)},
         "workload": "headline hybrid, FOM implicit (Newmark 1/4, 1/2) with 2 substeps of 10 us, ROM explicit with "
                     "20 substeps of 1 us, temporal interpolant between them (each controller step one graph launch, "
                     "Newton and CG as device-side loops)"}

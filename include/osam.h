@@ -57,8 +57,13 @@ enum { OSAM_MULTIPLICATIVE = 0, OSAM_ADDITIVE = 1 };
 /* OSAM_FP64: native FP64 everywhere.  OSAM_FP32_FORCE: internal force in FP32 (checked to 1e-5).
  * OSAM_F32X2_FORCE: internal force in double-float arithmetic (pairs of FP32 values, ~48-bit
  * significands) on the FP32 pipes, state and time integration in FP64 (checked to 1e-9 like FP64);
- * uses the deterministic gather scatter. */
-enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1, OSAM_F32X2_FORCE = 2 };
+ * uses the deterministic gather scatter.  OSAM_FP64_TANGENT32: OSAM_FP64, except that the Newton
+ * tangent of implicit Neo-Hookean subdomains (its stored Gauss-point linearisation, its action on
+ * the conjugate-gradient direction and the element contributions of that action) is in FP32; the
+ * Newton residual and its test, the CG vectors and reductions stay FP64, so a converged step meets the
+ * same FP64 residual test as OSAM_FP64 (inexact Newton with a lower-precision inner solve; each CG
+ * solve stops at a relative tolerance of at least 1e-6).  Explicit subdomains run as OSAM_FP64. */
+enum { OSAM_FP64 = 0, OSAM_FP32_FORCE = 1, OSAM_F32X2_FORCE = 2, OSAM_FP64_TANGENT32 = 3 };
 /* element-to-node scatter of the internal force: FP64 atomics, or a deterministic two-pass
  * element-buffer / node-gather scheme; GATHER_LOWREG is the gather scheme with the FP64 force kernel
  * compiled for at most 128 registers per thread (more resident warps, a few spilled values);

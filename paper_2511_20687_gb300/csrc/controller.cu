@@ -74,6 +74,11 @@ constexpr double kNewtonInc2 = 1e-28;  // or an increment |du|^2 <= kNewtonInc2 
 constexpr int kCgMax = 1000;           // CG iterations per Newton step
 constexpr int kCgCheck = 8;            // CG iterations between host checks of the activity mask
 constexpr double kCgTol2 = 1e-26;      // floor of the CG test r.z <= eta^2 (r.z)_0 (eta: the Newton forcing term)
+constexpr double kCgTol2F32 = 1e-12;   // the floor with the FP32 tangent (eta >= 1e-6, above its rounding)
+
+// the stored-linearisation path (Neo-Hookean groups), and the CG floor that goes with its precision
+bool stored_lin(const FomB& g) { return g.lin || g.linf; }
+double cg_floor(const FomB& g) { return g.linf ? kCgTol2F32 : kCgTol2; }
 
 // Implicit Newmark interval of FOM slot s (beta = 1/4, gamma = 1/2): per substep the predictor, a
 // Newton solve of M (u - u~) c0 + f_int(u) = 0 (c0 = 1 / (beta dt^2)) with mass-preconditioned
@@ -92,7 +97,7 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
         LK(launch_mask_copy(n, active, g.nact, ctx->stream));
         LK(launch_mask_copy(n, active, g.cgact, ctx->stream));
         for (int it = 0; it < kNewtonMax; ++it) {
-            if (g.lin) LK(launch_force_lin_b(g, g.nact, ctx->stream));
+            if (stored_lin(g)) LK(launch_force_lin_b(g, g.nact, ctx->stream));
             else LK(launch_force_b(g, g.nact, kGather, ctx->stream, nullptr));
             LK(launch_imp_residual_b(g, g.nact, c0, ctx->stream));
             LK(launch_imp_reduce_b(g, g.nact, 0, it == 0, kNewtonTol2, ctx->stream));
@@ -102,11 +107,11 @@ int advance_implicit(osam_ctx* ctx, int s, const int* active) {
             for (int k = 0; k < kCgMax;) {
                 for (int q = 0; q < kCgCheck; ++q, ++k) {
                     const int pk = ctx->prof_begin(1);
-                    if (g.lin) LK(launch_tangent_lin_b(g, g.cgact, ctx->stream));
+                    if (stored_lin(g)) LK(launch_tangent_lin_b(g, g.cgact, ctx->stream));
                     else LK(launch_tangent_b(g, g.cgact, ctx->stream));
                     ctx->prof_end(pk, 0);
                     LK(launch_cg_ap_b(g, g.cgact, c0, ctx->stream));
-                    LK(launch_cg_step_b(g, g.cgact, c0, kCgTol2, ctx->stream));
+                    LK(launch_cg_step_b(g, g.cgact, c0, cg_floor(g), ctx->stream));
                     LK(launch_cg_dir_b(g, g.cgact, c0, ctx->stream));
                 }
                 bool cg = false;
@@ -178,7 +183,7 @@ int enqueue_implicit_captured(osam_ctx* ctx, int s, const int* active) {
         {
             cudaStream_t a = ctx->cap[0];
             auto body = [&]() -> int {
-                if (g.lin) LK(launch_force_lin_b(g, g.nact, a));
+                if (stored_lin(g)) LK(launch_force_lin_b(g, g.nact, a));
                 else LK(launch_force_b(g, g.nact, kGather, a, nullptr));
                 LK(launch_imp_residual_b(g, g.nact, c0, a));
                 LK(launch_imp_reduce_b(g, g.nact, 0, -1, kNewtonTol2, a));
@@ -191,10 +196,10 @@ int enqueue_implicit_captured(osam_ctx* ctx, int s, const int* active) {
                 cudaStream_t b = ctx->cap[1];
                 int rc2 = OSAM_OK;
                 auto cg = [&]() -> int {
-                    if (g.lin) LK(launch_tangent_lin_b(g, g.cgact, b));
+                    if (stored_lin(g)) LK(launch_tangent_lin_b(g, g.cgact, b));
                     else LK(launch_tangent_b(g, g.cgact, b));
                     LK(launch_cg_ap_b(g, g.cgact, c0, b));
-                    LK(launch_cg_step_b(g, g.cgact, c0, kCgTol2, b));
+                    LK(launch_cg_step_b(g, g.cgact, c0, cg_floor(g), b));
                     LK(launch_cg_dir_b(g, g.cgact, c0, b));
                     LK(launch_imp_loop_cond(g, hc, 1, kCgMax, b));
                     return OSAM_OK;

@@ -181,8 +181,32 @@ __device__ __forceinline__ bool last_block_sum(const FomB& g, int inst, double& 
     return true;
 }
 
-// Ap = M p c0 + K p (free dofs); p . Ap summed per instance by its last block, which sets
-// alpha = (r . z) / (p . Ap) for the step kernel
+// K p at node (i, j, k), component c, from the FP32 element buffer of the FP32 tangent: the 8 corner
+// contributions summed in FP32 in the fixed order of gather_force, converted once
+__device__ __forceinline__ double gather_tangent32(const float* fe, int nx, int ny, int nz, int ne, int i, int j,
+                                                   int k, int c) {
+    float s = 0.f;
+#pragma unroll
+    for (int az = 0; az < 2; ++az) {
+        const int ke = k - az;
+        if (ke < 0 || ke >= nz) continue;
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay) {
+            const int je = j - ay;
+            if (je < 0 || je >= ny) continue;
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax) {
+                const int ie = i - ax;
+                if (ie < 0 || ie >= nx) continue;
+                s += __ldg(fe + (long long)((ax + 2 * ay + 4 * az) * 3 + c) * ne + (ie + nx * (je + ny * ke)));
+            }
+        }
+    }
+    return double(s);
+}
+
+// Ap = M p c0 + K p (free dofs; K p from the FP64 element buffer, or the FP32 one of the FP32 tangent);
+// p . Ap summed per instance by its last block, which sets alpha = (r . z) / (p . Ap) for the step kernel
 __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int* __restrict__ mask, double c0) {
     const NodeCtx x = node_ctx(g, mask);
     double s = 0.0;
@@ -192,13 +216,15 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int*
         const int j = t % (x.I.ny + 1);
         const int k = t / (x.I.ny + 1);
         const double* fe = static_cast<const double*>(g.fe) + x.I.elem_off;
+        const float* fe32 = g.fe32 ? g.fe32 + x.I.elem_off : nullptr;
         const double m = 1.0 / g.minv[x.gn];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long d = (long long)c * g.NN + x.gn;
             double ap = 0.0;
             if (is_free(g, x.gn, c)) {
-                const double kp = gather_force<double>(fe, x.I.nx, x.I.ny, x.I.nz, (int)g.NE, i, j, k, c);
+                const double kp = fe32 ? gather_tangent32(fe32, x.I.nx, x.I.ny, x.I.nz, (int)g.NE, i, j, k, c)
+                                       : gather_force<double>(fe, x.I.nx, x.I.ny, x.I.nz, (int)g.NE, i, j, k, c);
                 ap = c0 * m * g.cg_p[d] + kp;
             }
             g.cg_ap[d] = ap;

@@ -120,6 +120,8 @@ struct FomB {
     int* cgact;               // per instance: CG still iterating
     long long* istat;         // per instance: Newton linear solves, CG iterations (since the last reset)
     double* lin;              // Neo-Hookean implicit groups: stored Newton linearisation [kLinPerGp][8][NE]
+    float* linf;              // the same in FP32 (OSAM_FP64_TANGENT32; lin is then null)
+    float* fe32;              // FP32 element buffer [24][NE] of the FP32 tangent action
     int df32;                 // 1: internal force in double-float arithmetic (element buffer of float2)
 };
 

@@ -24,7 +24,8 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     if (d0.n_couplings < 0 || (d0.n_couplings > 0 && !d0.couplings)) return ctx->fail(OSAM_EINVAL, "bad couplings");
     if (!(d0.dt > 0.0) || d0.n_substeps < 1 || d0.max_iters < 1)
         return ctx->fail(OSAM_EINVAL, "dt, n_substeps and max_iters must be positive");
-    if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE)
+    if (d0.precision != OSAM_FP64 && d0.precision != OSAM_FP32_FORCE && d0.precision != OSAM_F32X2_FORCE &&
+        d0.precision != OSAM_FP64_TANGENT32)
         return ctx->fail(OSAM_EINVAL, "bad precision");
     if (d0.scatter < OSAM_SCATTER_AUTO || d0.scatter > OSAM_SCATTER_GATHER_TILED_LOWREG)
         return ctx->fail(OSAM_EINVAL, "bad scatter mode");
@@ -64,8 +65,10 @@ int validate_topology(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: bad or differing n_substeps", i, s);
             if (a.kind == OSAM_FOM && a.integrator != b.integrator)
                 return ctx->fail(OSAM_EINVAL, "instance %d subdomain %d: integrator differs from instance 0", i, s);
-            if (a.kind == OSAM_FOM && a.integrator == OSAM_IMPLICIT && d0.precision != OSAM_FP64)
-                return ctx->fail(OSAM_EINVAL, "subdomain %d: implicit integration needs OSAM_FP64", s);
+            if (a.kind == OSAM_FOM && a.integrator == OSAM_IMPLICIT && d0.precision != OSAM_FP64 &&
+                d0.precision != OSAM_FP64_TANGENT32)
+                return ctx->fail(OSAM_EINVAL,
+                                 "subdomain %d: implicit integration needs OSAM_FP64 or OSAM_FP64_TANGENT32", s);
         }
         for (int k = 0; k < d0.n_couplings; ++k) {
             if (!d.couplings || d.couplings[k].dst != d0.couplings[k].dst || d.couplings[k].src != d0.couplings[k].src ||
@@ -208,7 +211,12 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CK(cudaMemsetAsync(B.iticket, 0, sizeof(unsigned int) * n, ctx->stream));
         CKA(B.istat = ctx->alloc<long long>(2 * n));
         CKA(B.iloop = ctx->alloc<int>(2));
-        if (B.material == OSAM_NEO_HOOKEAN) CKA(B.lin = ctx->alloc<double>((long long)kLinPerGp * 8 * NE));
+        if (B.material == OSAM_NEO_HOOKEAN && ctx->precision == OSAM_FP64_TANGENT32) {
+            CKA(B.linf = ctx->alloc<float>((long long)kLinPerGp * 8 * NE));
+            CKA(B.fe32 = ctx->alloc<float>(24 * NE));
+        } else if (B.material == OSAM_NEO_HOOKEAN) {
+            CKA(B.lin = ctx->alloc<double>((long long)kLinPerGp * 8 * NE));
+        }
         CK(cudaMemsetAsync(B.istat, 0, sizeof(long long) * 2 * n, ctx->stream));
         CKA(B.nact = ctx->alloc<int>(n));
         CKA(B.cgact = ctx->alloc<int>(n));
@@ -794,11 +802,11 @@ int init_impl(osam_ctx* ctx, int n, const osam_problem_desc* descs) {
     for (CplH& c : ctx->cpls) RET(zoh_cpl(ctx, c, nullptr));
     RET(initial_accel(ctx, nullptr));
     if (d0.scatter == OSAM_SCATTER_AUTO) RET(autotune(ctx));
-    if (d0.scatter == OSAM_SCATTER_GATHER_LOWREG && d0.precision == OSAM_FP64)
+    const bool fp64_force = d0.precision == OSAM_FP64 || d0.precision == OSAM_FP64_TANGENT32;
+    if (d0.scatter == OSAM_SCATTER_GATHER_LOWREG && fp64_force)
         for (Slot& S : ctx->slots)
             if (S.kind == OSAM_FOM) S.fom.d.occ = 1;
-    if ((d0.scatter == OSAM_SCATTER_GATHER_TILED || d0.scatter == OSAM_SCATTER_GATHER_TILED_LOWREG) &&
-        d0.precision == OSAM_FP64)
+    if ((d0.scatter == OSAM_SCATTER_GATHER_TILED || d0.scatter == OSAM_SCATTER_GATHER_TILED_LOWREG) && fp64_force)
         for (Slot& S : ctx->slots)
             if (S.kind == OSAM_FOM) {
                 S.fom.d.tiled = 1;

@@ -232,8 +232,11 @@ __device__ __forceinline__ ElemIdx elem_idx(const FomB& g, const int* mask) {
     return x;
 }
 
-// Newton residual force of a Neo-Hookean group at u (from u / h) plus the stored linearisation
-__global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, const int* __restrict__ mask) {
+// Newton residual force of a Neo-Hookean group at u (from u / h) plus the stored linearisation (TL:
+// its storage type; computed in FP64 either way)
+template <typename TL>
+__global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, TL* __restrict__ lin_base,
+                                                     const int* __restrict__ mask) {
     const ElemIdx x = elem_idx(g, mask);
     if (!x.ok) return;
     const InstFom& I = x.I;
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, const int* __
     const double mu = I.mu_e ? I.mu_e[e] : I.mu;
     const double kappa = lam + (2.0 / 3.0) * mu;
     const double m1 = 0.5 * kappa * I.w8, m2 = mu * I.w8, m3 = mu * I.w8 / 3.0;
-    double* lin = g.lin + I.elem_off + e;
+    TL* lin = lin_base + I.elem_off + e;
     const long long st = 8LL * g.NE;  // stride between quantities
     double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
 #pragma unroll
@@ -265,13 +268,13 @@ __global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, const int* __
                 const double invJ = 1.0 / J;
                 const double a1 = -(2.0 / 3.0) * alpha * invJ;
                 const double b1 = 2.0 * m1 - invJ * fma(a1, trC * (1.0 / 3.0), beta);
-                double* lg = lin + (long long)gp * g.NE;
+                TL* lg = lin + (long long)gp * g.NE;
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
-                    lg[a * st] = Fm[a / 3][a % 3];
-                    lg[(9 + a) * st] = Cm[a / 3][a % 3];
+                    lg[a * st] = TL(Fm[a / 3][a % 3]);
+                    lg[(9 + a) * st] = TL(Cm[a / 3][a % 3]);
                 }
-                lg[18 * st] = alpha; lg[19 * st] = beta; lg[20 * st] = a1; lg[21 * st] = b1;
+                lg[18 * st] = TL(alpha); lg[19 * st] = TL(beta); lg[20 * st] = TL(a1); lg[21 * st] = TL(b1);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const double P0 = fma(alpha, Fm[c][0], beta * Cm[c][0]);
@@ -348,19 +351,125 @@ __global__ void __launch_bounds__(256) k_tangent_lin_b(const FomB g, const int* 
     write_element(g, I, e, Sx, Sy, Sz);
 }
 
+// The tangent action of k_tangent_lin_b in FP32 (OSAM_FP64_TANGENT32): the linearisation read as
+// stored in FP32 (half the bytes), the direction p converted once per nodal value, every Gauss-point
+// operation on the FP32 pipes, and the element contributions written in FP32 to the FP32 element
+// buffer (the CG's Ap kernel sums them in FP32 and adds them to its FP64 mass term).  The only FP64-pipe
+// work left is the 24 conversions of p per element.
+__global__ void __launch_bounds__(256) k_tangent_lin32_b(const FomB g, const int* __restrict__ mask) {
+    const ElemIdx x = elem_idx(g, mask);
+    if (!x.ok) return;
+    const InstFom& I = x.I;
+    const int e = x.e;
+    const float sc = float(I.invh);
+    float Bx[3][2][2], By[3][2][2], Bz[3][2][2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float V[8], Dx[2][2], Dy[2][2], Dz[2][2];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8)
+            V[c8] = __double2float_rn(g.cg_p[(long long)c * g.NN + I.node_off + x.node[c8]]) * sc;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                Dx[a][b] = V[1 + 2 * a + 4 * b] - V[2 * a + 4 * b];
+                Dy[a][b] = V[a + 2 + 4 * b] - V[a + 4 * b];
+                Dz[a][b] = V[a + 2 * b + 4] - V[a + 2 * b];
+            }
+        lerp2<float>(Dx, Bx[c]); lerp2<float>(Dy, By[c]); lerp2<float>(Dz, Bz[c]);
+    }
+    const float* lin = g.linf + I.elem_off + e;
+    const long long st = 8LL * g.NE;
+    float Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int gp = 4 * p + 2 * q + r;
+                const float* lg = lin + (long long)gp * g.NE;
+                float F[3][3], cf[3][3], G[3][3], dc[3][3];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    F[a / 3][a % 3] = __ldg(lg + a * st);
+                    cf[a / 3][a % 3] = __ldg(lg + (9 + a) * st);
+                }
+                const float alpha = __ldg(lg + 18 * st), beta = __ldg(lg + 19 * st);
+                const float a1 = __ldg(lg + 20 * st), b1 = __ldg(lg + 21 * st);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) { G[c][0] = Bx[c][q][r]; G[c][1] = By[c][p][r]; G[c][2] = Bz[c][p][q]; }
+                float dJ = 0.f, FG = 0.f;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    dJ = fmaf(cf[a / 3][a % 3], G[a / 3][a % 3], dJ);
+                    FG = fmaf(F[a / 3][a % 3], G[a / 3][a % 3], FG);
+                }
+                dc[0][0] = G[1][1] * F[2][2] + F[1][1] * G[2][2] - G[1][2] * F[2][1] - F[1][2] * G[2][1];
+                dc[0][1] = G[1][2] * F[2][0] + F[1][2] * G[2][0] - G[1][0] * F[2][2] - F[1][0] * G[2][2];
+                dc[0][2] = G[1][0] * F[2][1] + F[1][0] * G[2][1] - G[1][1] * F[2][0] - F[1][1] * G[2][0];
+                dc[1][0] = G[0][2] * F[2][1] + F[0][2] * G[2][1] - G[0][1] * F[2][2] - F[0][1] * G[2][2];
+                dc[1][1] = G[0][0] * F[2][2] + F[0][0] * G[2][2] - G[0][2] * F[2][0] - F[0][2] * G[2][0];
+                dc[1][2] = G[0][1] * F[2][0] + F[0][1] * G[2][0] - G[0][0] * F[2][1] - F[0][0] * G[2][1];
+                dc[2][0] = G[0][1] * F[1][2] + F[0][1] * G[1][2] - G[0][2] * F[1][1] - F[0][2] * G[1][1];
+                dc[2][1] = G[0][2] * F[1][0] + F[0][2] * G[1][0] - G[0][0] * F[1][2] - F[0][0] * G[1][2];
+                dc[2][2] = G[0][0] * F[1][1] + F[0][0] * G[1][1] - G[0][1] * F[1][0] - F[0][1] * G[1][0];
+                const float dalpha = a1 * dJ;
+                const float dbeta = fmaf(b1, dJ, a1 * FG);
+                float dP[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b2 = 0; b2 < 3; ++b2)
+                        dP[a][b2] = fmaf(dbeta, cf[a][b2], fmaf(beta, dc[a][b2], fmaf(dalpha, F[a][b2], alpha * G[a][b2])));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (p == 0) Sx[c][q][r] = dP[c][0]; else Sx[c][q][r] += dP[c][0];
+                    if (q == 0) Sy[c][p][r] = dP[c][1]; else Sy[c][p][r] += dP[c][1];
+                    if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
+                }
+            }
+    float* fe = g.fe32 + I.elem_off;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float Fc[8], Tm[2][2];
+        lerp2T<float>(Sx[c], Tm);
+#pragma unroll
+        for (int ay = 0; ay < 2; ++ay)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
+        lerp2T<float>(Sy[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
+        lerp2T<float>(Sz[c], Tm);
+#pragma unroll
+        for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_force_lin_b(const FomB& g, const int* mask, cudaStream_t s) {
     if (g.n_eblk == 0) return cudaSuccess;
-    if (g.eblock > 256 || !g.lin || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
-    k_force_lin_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    if (g.eblock > 256 || (!g.lin && !g.linf) || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
+    if (g.linf) k_force_lin_b<float><<<g.n_eblk, g.eblock, 0, s>>>(g, g.linf, mask);
+    else k_force_lin_b<double><<<g.n_eblk, g.eblock, 0, s>>>(g, g.lin, mask);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tangent_lin_b(const FomB& g, const int* mask, cudaStream_t s) {
     if (g.n_eblk == 0) return cudaSuccess;
-    if (g.eblock > 256 || !g.lin || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
-    k_tangent_lin_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    if (g.eblock > 256 || g.material != OSAM_NEO_HOOKEAN) return cudaErrorInvalidValue;
+    if (g.linf && g.fe32) k_tangent_lin32_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    else if (g.lin) k_tangent_lin_b<<<g.n_eblk, g.eblock, 0, s>>>(g, mask);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

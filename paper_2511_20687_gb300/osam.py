@@ -20,7 +20,7 @@ FOM, ROM = 0, 1
 LINEAR_ELASTIC, NEO_HOOKEAN, SAINT_VENANT_KIRCHHOFF = 0, 1, 2
 EXPLICIT, IMPLICIT = 0, 1
 MULTIPLICATIVE, ADDITIVE = 0, 1
-FP64, FP32_FORCE, F32X2_FORCE = 0, 1, 2
+FP64, FP32_FORCE, F32X2_FORCE, FP64_TANGENT32 = 0, 1, 2, 3
 SCATTER_AUTO, SCATTER_ATOMIC, SCATTER_GATHER, SCATTER_GATHER_LOWREG, SCATTER_GATHER_TILED = 0, 1, 2, 3, 4
 SCATTER_GATHER_TILED_LOWREG = 5
 

@@ -60,42 +60,51 @@ def _compare(spec, n_ctrl, rom_ops=None, tol=1e-9, **kw):
         assert err < tol, (i, err)
 
 
+# OSAM_FP64_TANGENT32 (the Neo-Hookean Newton tangent in FP32, residual and CG vectors in FP64) meets
+# the same FP64 Newton test, so it is held to the same bar; linear elastic runs it as FP64
+PRECISIONS = [osam.FP64, osam.FP64_TANGENT32]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("material", ["le", "nh"])
-def test_single_implicit_fom(gpu, material):
+def test_single_implicit_fom(gpu, material, precision):
     """5x5x13 bar (325 elements, 504 nodes: several blocks and a ragged tail), displacement, velocity
     and acceleration over 3 controller steps of 6 substeps."""
     spec = _implicit(W.single_bar("imp1", 5, 13, material, 1e9, 0.25, 1000.0, 2e-3, 2e-6, 6))
-    _compare(spec, 3)
+    _compare(spec, 3, precision=precision)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("material", ["le", "nh"])
-def test_implicit_above_explicit_limit(gpu, material):
+def test_implicit_above_explicit_limit(gpu, material, precision):
     """dt = 5x the explicit stability limit: accepted for an implicit subdomain (the explicit one is
     refused with OSAM_ECFL) and still equal to the oracle.  (At twice this pulse amplitude the
     Neo-Hookean Newton solve from the predictor fails on both sides at this step.)"""
     spec = _implicit(W.single_bar("imp5", 4, 9, material, 1e9, 0.25, 1000.0, 1e-3, 1e-6, 4))
     sd = spec.subdomains[0]
     spec.dt = 5.0 * O.stable_dt(sd.dims, sd.h, sd.origin, sd.lam, sd.mu, sd.rho)
-    _compare(spec, 3)
+    _compare(spec, 3, precision=precision)
     sd.integrator = "explicit"
     with pytest.raises(osam.OsamError) as e:
         osam.Problem(spec)
     assert e.value.code == osam.ECFL
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("material", ["le", "nh"])
-def test_implicit_implicit_schwarz(gpu, material):
+def test_implicit_implicit_schwarz(gpu, material, precision):
     spec = _implicit(W.bar_chain("imp2", 3, [8, 8], ["fom", "fom"], material, 1e9, 0.25, 1000.0, 2e-3, 2e-6, 5,
                                  max_iters=40))
-    _compare(spec, 3)
+    _compare(spec, 3, precision=precision)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("which", [{0}, {1}])
-def test_explicit_implicit_schwarz(gpu, which):
+def test_explicit_implicit_schwarz(gpu, which, precision):
     """Neo-Hookean chain with one implicit and one explicit FOM at a common time step."""
     spec = _implicit(W.bar_chain("mix", 4, [9, 7], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 2e-6, 5,
                                  max_iters=40), which)
-    _compare(spec, 3)
+    _compare(spec, 3, precision=precision)
 
 
 def test_three_subdomain_chain_mixed(gpu):
@@ -113,15 +122,16 @@ def test_implicit_fom_with_rom(gpu):
     _compare(spec, 3, rom_ops={1: ops})
 
 
-def test_implicit_batch_equals_single_runs(gpu):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_implicit_batch_equals_single_runs(gpu, precision):
     """Instances with different meshes and materials in one batch follow their own runs bit for bit
     (per-instance Newton / CG masks, fixed-order reductions)."""
     specs = W.batched_samples(n_samples=3, n_min=3, n_max=6, rom=False)
     for s in specs:
         s.max_iters = 20
         _implicit(s, {1})
-    batch = osam.Batch(specs, scatter=osam.SCATTER_GATHER)
-    singles = [osam.Problem(s, scatter=osam.SCATTER_GATHER) for s in specs]
+    batch = osam.Batch(specs, scatter=osam.SCATTER_GATHER, precision=precision)
+    singles = [osam.Problem(s, scatter=osam.SCATTER_GATHER, precision=precision) for s in specs]
     for _ in range(2):
         per, _ = batch.step()
         reps = [p.step() for p in singles]
@@ -138,6 +148,31 @@ def test_implicit_needs_fp64(gpu):
         with pytest.raises(osam.OsamError) as e:
             osam.Problem(spec, precision=prec)
         assert e.value.code == osam.EINVAL
+    osam.Problem(spec, precision=osam.FP64_TANGENT32).close()
+
+
+def test_fp32_tangent_converges_to_the_fp64_tangent_state(gpu):
+    """The FP32 tangent changes only how each Newton system is solved, not the FP64 residual test that
+    ends a substep: two implicit Neo-Hookean FOMs at three times the explicit limit agree between the
+    two precisions to well inside the effect of the Newton tolerance on the state, within one Schwarz
+    iteration per controller step, and the FP32 run does solve Newton systems by CG."""
+    spec = _implicit(W.bar_chain("t32", 5, [12, 10], ["fom", "fom"], "nh", 1e9, 0.3, 1000.0, 2e-3, 1e-6, 4,
+                                 max_iters=40))
+    sd = spec.subdomains[0]
+    spec.dt = 3.0 * O.stable_dt(sd.dims, sd.h, sd.origin, sd.lam, sd.mu, sd.rho)
+    runs = {}
+    for prec in PRECISIONS:
+        p = osam.Problem(spec, precision=prec, scatter=osam.SCATTER_GATHER)
+        p.profile(False)
+        its = [p.step()["iterations"] for _ in range(3)]
+        runs[prec] = (its, [p.state(i) for i in range(2)], p.implicit_profile())
+        p.close()
+    (i64, s64, _), (i32, s32, p32) = runs[osam.FP64], runs[osam.FP64_TANGENT32]
+    assert all(abs(a - b) <= 1 for a, b in zip(i64, i32))
+    for i in range(2):
+        for f in range(3):
+            assert rel_l2([s32[i][f]], [s64[i][f]]) < 1e-10
+    assert p32["newton_steps"] > 0 and p32["cg_iterations"] >= p32["newton_steps"]
 
 
 def test_implicit_nonfinite_state_reported(gpu):
@@ -157,7 +192,8 @@ def test_implicit_nonfinite_state_reported(gpu):
     assert e.value.code == O.ENONFINITE
 
 
-def test_device_loops_equal_host_loop(gpu):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_device_loops_equal_host_loop(gpu, precision):
     """The implicit interval as a graph (Newton and CG as device-side WHILE nodes, inside the captured
     controller step or as a per-interval graph) follows the host-driven Newton / CG loop bit for bit:
     same kernels, same per-instance masks, only the trailing masked CG passes and the host round trips
@@ -165,9 +201,9 @@ def test_device_loops_equal_host_loop(gpu):
     autotuner, each problem may pick atomics on a mesh this small, whose order of additions varies."""
     spec = _implicit(W.bar_chain("dl", 3, [8, 8], ["fom", "fom"], "nh", 1e9, 0.25, 1000.0, 2e-3, 2e-6, 5,
                                  max_iters=40), {1})
-    a = osam.Problem(spec, graph=True, scatter=osam.SCATTER_GATHER)
-    b = osam.Problem(spec, graph=False, scatter=osam.SCATTER_GATHER)
-    c = osam.Problem(spec, graph=False, scatter=osam.SCATTER_GATHER)
+    a = osam.Problem(spec, graph=True, scatter=osam.SCATTER_GATHER, precision=precision)
+    b = osam.Problem(spec, graph=False, scatter=osam.SCATTER_GATHER, precision=precision)
+    c = osam.Problem(spec, graph=False, scatter=osam.SCATTER_GATHER, precision=precision)
     c.profile(True)   # kernel-level profiling drives the Newton / CG loops from the host
     for _ in range(3):
         ra, rb, rc = a.step(), b.step(), c.step()
