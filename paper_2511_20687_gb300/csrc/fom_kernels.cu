@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_hex8_force(const ElemArgs a) {
 }
 
 // inverse row-sum lumped mass of a uniform cubic mesh: m_n = rho h^3 / 8 x (adjacent elements)
-__global__ void k_lumped_minv(int nx, int ny, int nz, double m_e8, double* minv) {
+__global__ void k_lumped_minv(int nx, int ny, int nz, double m_e8, double* minv, double* mass) {
     const int nn = (nx + 1) * (ny + 1) * (nz + 1);
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
@@ -68,7 +68,9 @@ __global__ void k_lumped_minv(int nx, int ny, int nz, double m_e8, double* minv)
     const int j = t % (ny + 1);
     const int k = t / (ny + 1);
     const int cx = (i > 0) + (i < nx), cy = (j > 0) + (j < ny), cz = (k > 0) + (k < nz);
-    minv[n] = 1.0 / (m_e8 * double(cx * cy * cz));
+    const double m = m_e8 * double(cx * cy * cz);
+    minv[n] = 1.0 / m;
+    if (mass) mass[n] = m;
 }
 
 // donor element and trilinear weights of each destination Schwarz node in a structured source box:
@@ -180,9 +182,9 @@ cudaError_t launch_hex8_force(int material, bool fp32, int scatter, const ElemAr
     return cudaGetLastError();
 }
 
-cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s) {
+cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s, double* mass) {
     const double m_e8 = rho * g.h * g.h * g.h / 8.0;
-    k_lumped_minv<<<grid_for(g.nn(), 256), 256, 0, s>>>(g.nx, g.ny, g.nz, m_e8, minv);
+    k_lumped_minv<<<grid_for(g.nn(), 256), 256, 0, s>>>(g.nx, g.ny, g.nz, m_e8, minv, mass);
     return cudaGetLastError();
 }
 

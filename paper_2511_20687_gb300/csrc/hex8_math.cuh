@@ -186,9 +186,19 @@ __device__ __forceinline__ void stress_nh(const T H[3][3], T kap2, T mu, T mu3, 
 //    Gauss points that share the column, and
 //  - in each sum the alpha F term of a pair is one product (alpha_a + alpha_b) F_k,
 // which takes ~50 FP64 operations per element off the one-Gauss-point-at-a-time evaluation.
-template <typename T>
+// `at_gp(p, q, r, F, cofF, J, trC, invJ, alpha, beta)` is called at every Gauss point with its
+// quantities (the implicit Newton force stores them as the tangent's linearisation); the default
+// does nothing and compiles away.
+struct NoGaussHook {
+    template <typename T>
+    __device__ __forceinline__ void operator()(int, int, int, const T (&)[3][3], const T (&)[3][3], T, T, T, T,
+                                               T) const {}
+};
+
+template <typename T, typename Hook = NoGaussHook>
 __device__ __forceinline__ void nh_gauss_sums(const T Gx[3][2][2], const T Gy[3][2][2], const T Gz[3][2][2],
-                                              T kap2, T mu, T mu3, T Sx[3][2][2], T Sy[3][2][2], T Sz[3][2][2]) {
+                                              T kap2, T mu, T mu3, T Sx[3][2][2], T Sy[3][2][2], T Sz[3][2][2],
+                                              const Hook& at_gp = Hook()) {
     const T (*F0)[2][2] = Gx;   // columns of F: F0[c][q][r], F1[c][p][r], F2[c][p][q]
     const T (*F1)[2][2] = Gy;
     const T (*F2)[2][2] = Gz;
@@ -236,6 +246,7 @@ __device__ __forceinline__ void nh_gauss_sums(const T Gx[3][2][2], const T Gy[3]
                 const T invJ = r3 * s1;        // 1/J
                 const T alpha = mu * r3;
                 const T beta = fmaT(-(mu3 * r3) * invJ, trC, kap2 * (J - invJ));
+                at_gp(p, q, r, Fm, Cm, J, trC, invJ, alpha, beta);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     Sx[c][q][r] = p == 0 ? beta * Cm[c][0] : fmaT(beta, Cm[c][0], Sx[c][q][r]);

@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kNodeBlock) k_imp_predict_b(const FomB g, cons
 // R = M (u - ut) c0 + f (free dofs; the element forces of u are in the element buffer).  CG start
 // x = 0, r = -R, z = p = M^-1 r / c0 (the mass part of the tangent as preconditioner); partials
 // |R|^2 and r . z
-__global__ void __launch_bounds__(kNodeBlock) k_imp_residual_b(const FomB g, const int* __restrict__ mask, double c0) {
+__global__ void __launch_bounds__(kNodeBlock) k_imp_residual_b(const FomB g, const int* __restrict__ mask, double c0,
+                                                               double ic0) {
     const NodeCtx x = node_ctx(g, mask);
     double s = 0.0, sz = 0.0;
     if (x.ok) {
@@ -93,9 +94,8 @@ __global__ void __launch_bounds__(kNodeBlock) k_imp_residual_b(const FomB g, con
         const int j = t % (x.I.ny + 1);
         const int k = t / (x.I.ny + 1);
         const double* fe = static_cast<const double*>(g.fe) + x.I.elem_off;
-        const double mi = g.minv[x.gn];
-        const double m = 1.0 / mi;
-        const double pz = mi / c0;
+        const double m = g.mass[x.gn];
+        const double pz = g.minv[x.gn] * ic0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long d = (long long)c * g.NN + x.gn;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int*
         const int k = t / (x.I.ny + 1);
         const double* fe = static_cast<const double*>(g.fe) + x.I.elem_off;
         const float* fe32 = g.fe32 ? g.fe32 + x.I.elem_off : nullptr;
-        const double m = 1.0 / g.minv[x.gn];
+        const double m = g.mass[x.gn];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long d = (long long)c * g.NN + x.gn;
@@ -243,13 +243,13 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_ap_b(const FomB g, const int*
 // x += alpha p, r -= alpha Ap; r . z of the new residual summed per instance by its last block, which
 // counts the iteration, ends the instance's CG solve at the forcing tolerance (floor tol2) and sets
 // beta = (r . z)_new / (r . z) and r . z <- (r . z)_new for the direction kernel
-__global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const int* __restrict__ mask, double c0,
+__global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const int* __restrict__ mask, double ic0,
                                                           double tol2) {
     const NodeCtx x = node_ctx(g, mask);
     double s = 0.0;
     if (x.ok) {
         const double alpha = g.alpha[x.inst];
-        const double pz = g.minv[x.gn] / c0;
+        const double pz = g.minv[x.gn] * ic0;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const long long d = (long long)c * g.NN + x.gn;
@@ -274,11 +274,11 @@ __global__ void __launch_bounds__(kNodeBlock) k_cg_step_b(const FomB g, const in
 }
 
 // p = z + beta p
-__global__ void __launch_bounds__(kNodeBlock) k_cg_dir_b(const FomB g, const int* __restrict__ mask, double c0) {
+__global__ void __launch_bounds__(kNodeBlock) k_cg_dir_b(const FomB g, const int* __restrict__ mask, double ic0) {
     const NodeCtx x = node_ctx(g, mask);
     if (!x.ok) return;
     const double beta = g.beta[x.inst];
-    const double pz = g.minv[x.gn] / c0;
+    const double pz = g.minv[x.gn] * ic0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const long long d = (long long)c * g.NN + x.gn;
@@ -380,7 +380,7 @@ cudaError_t launch_imp_predict_b(const FomB& g, const int* active, int slot1, do
     return cudaGetLastError();
 }
 cudaError_t launch_imp_residual_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
-    k_imp_residual_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    k_imp_residual_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0, 1.0 / c0);   // 1 / c0 once, on the host
     return cudaGetLastError();
 }
 cudaError_t launch_imp_reduce_b(const FomB& g, const int* mask, int mode, int first, double tol2, cudaStream_t s) {
@@ -392,11 +392,11 @@ cudaError_t launch_cg_ap_b(const FomB& g, const int* mask, double c0, cudaStream
     return cudaGetLastError();
 }
 cudaError_t launch_cg_step_b(const FomB& g, const int* mask, double c0, double tol2, cudaStream_t s) {
-    k_cg_step_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0, tol2);
+    k_cg_step_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, 1.0 / c0, tol2);
     return cudaGetLastError();
 }
 cudaError_t launch_cg_dir_b(const FomB& g, const int* mask, double c0, cudaStream_t s) {
-    k_cg_dir_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, c0);
+    k_cg_dir_b<<<g.n_nblk, kNodeBlock, 0, s>>>(g, mask, 1.0 / c0);
     return cudaGetLastError();
 }
 cudaError_t launch_imp_update_b(const FomB& g, const int* mask, cudaStream_t s) {

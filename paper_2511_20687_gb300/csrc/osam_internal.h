@@ -76,6 +76,7 @@ struct FomB {
     int n_nblk;
     const int* nblk_off;      // [n_inst + 1] first node block of each instance
     const double* minv;
+    const double* mass;       // lumped mass itself (implicit groups: the Newton system's M, no division)
     const uint8_t* clamp;
     const int* srow;
     double* u[2];
@@ -201,7 +202,7 @@ struct CtlB {
 // ------------------------------------------------------------------------------------------------
 int grid_for(long long n, int block);
 cudaError_t launch_hex8_force(int material, bool fp32, int scatter, const ElemArgs& a, cudaStream_t s);
-cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s);
+cudaError_t launch_lumped_minv(const Grid& g, double rho, double* minv, cudaStream_t s, double* mass = nullptr);
 cudaError_t launch_donor(const Grid& src, const Grid& dst, const int* dst_nodes, int nrow, int* dnode, double* dw,
                          int* err, cudaStream_t s);
 cudaError_t launch_aos_to_soa(const double* aos, double* soa, int nn, long long stride, cudaStream_t s);

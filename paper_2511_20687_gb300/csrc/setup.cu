@@ -205,6 +205,9 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
         CKA(B.cg_r = ctx->alloc<double>(3 * NN));
         CKA(B.cg_p = ctx->alloc<double>(3 * NN));
         CKA(B.cg_ap = ctx->alloc<double>(3 * NN));
+        double* mass = ctx->alloc<double>(NN);
+        CKA(mass);
+        B.mass = mass;
         for (double** p : {&B.rn2, &B.r0, &B.rr, &B.rrn, &B.rr0, &B.pap, &B.cgtol2, &B.alpha, &B.beta})
             CKA(*p = ctx->alloc<double>(n));
         CKA(B.iticket = ctx->alloc<unsigned int>(n));
@@ -243,7 +246,8 @@ int setup_fom_group(osam_ctx* ctx, FomGroupH& G, int s, int n, const osam_proble
             RET(upload(ctx, mu_e + I.elem_off, d.mu_e, sizeof(double) * I.ne));
             I.mu_e = mu_e + I.elem_off;
         }
-        CK(launch_lumped_minv(G.grid[i], d.rho, minv + I.node_off, ctx->stream));
+        CK(launch_lumped_minv(G.grid[i], d.rho, minv + I.node_off, ctx->stream,
+                              B.mass ? const_cast<double*>(B.mass) + I.node_off : nullptr));
         RET(upload(ctx, clamp + I.node_off, G.clamp[i].data(), I.nn));
         RET(upload(ctx, srow + I.node_off, G.srow[i].data(), sizeof(int) * I.nn));
         RET(upload(ctx, ctx->scratch, d.u0, sizeof(double) * 3 * I.nn));

@@ -179,31 +179,17 @@ __device__ __forceinline__ void nodal_grads(const FomB& g, const InstFom& I, con
     }
 }
 
-// transposed interpolation of the Gauss-point sums and the element-buffer write
-__device__ __forceinline__ void write_element(const FomB& g, const InstFom& I, int e, const double Sx[3][2][2],
-                                              const double Sy[3][2][2], const double Sz[3][2][2]) {
-    double* fe = static_cast<double*>(g.fe) + I.elem_off;
+// transposed interpolation of the Gauss-point sums (scaled like the force's: Walsh basis, factor 4 in
+// the material factors) and the element-buffer write
+template <typename T>
+__device__ __forceinline__ void write_element(T* fe, long long ne, int e, const T Sx[3][2][2], const T Sy[3][2][2],
+                                              const T Sz[3][2][2]) {
+    T F[3][8];
+    walsh_transpose<T>(Sx, Sy, Sz, F);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double Fc[8], Tm[2][2];
-        lerp2T<double>(Sx[c], Tm);
+    for (int c8 = 0; c8 < 8; ++c8)
 #pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
-        lerp2T<double>(Sy[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
-        lerp2T<double>(Sz[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
-    }
+        for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * ne + e] = F[c][c8];
 }
 
 struct ElemIdx {
@@ -232,8 +218,34 @@ __device__ __forceinline__ ElemIdx elem_idx(const FomB& g, const int* mask) {
     return x;
 }
 
-// Newton residual force of a Neo-Hookean group at u (from u / h) plus the stored linearisation (TL:
-// its storage type; computed in FP64 either way)
+// The per-Gauss-point quantities of the Newton linearisation, stored by the Neo-Hookean Gauss sums'
+// hook (TL: the storage type); a1 and b1 from the force's own 1/J (the cube of its reciprocal cube
+// root, no division).  Material factors scaled by h^2/32 like the force's (the Walsh-basis transposed
+// interpolation carries the remaining factor 4), so the tangent's dP is scaled alike.
+template <typename TL>
+struct LinStore {
+    TL* lin;             // this element's first entry
+    long long st;        // stride between quantities (8 NE)
+    long long ne;        // stride between Gauss points (NE)
+    double kap2;         // m1 of the material factors
+    __device__ __forceinline__ void operator()(int p, int q, int r, const double (&Fm)[3][3], const double (&Cm)[3][3],
+                                               double J, double trC, double invJ, double alpha, double beta) const {
+        (void)J;
+        const double a1 = -(2.0 / 3.0) * alpha * invJ;
+        const double b1 = 2.0 * kap2 - invJ * fma(a1, trC * (1.0 / 3.0), beta);
+        TL* lg = lin + (long long)(4 * p + 2 * q + r) * ne;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            lg[a * st] = TL(Fm[a / 3][a % 3]);
+            lg[(9 + a) * st] = TL(Cm[a / 3][a % 3]);
+        }
+        lg[18 * st] = TL(alpha); lg[19 * st] = TL(beta); lg[20 * st] = TL(a1); lg[21 * st] = TL(b1);
+    }
+};
+
+// Newton residual force of a Neo-Hookean group at u (from u / h) plus the stored linearisation: the
+// explicit force's arithmetic (1 of F's diagonal in the first interpolation stage, paired Gauss-point
+// sums, Walsh-basis transposed interpolation) with the linearisation written at each Gauss point
 template <typename TL>
 __global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, TL* __restrict__ lin_base,
                                                      const int* __restrict__ mask) {
@@ -242,50 +254,30 @@ __global__ void __launch_bounds__(256) k_force_lin_b(const FomB g, TL* __restric
     const InstFom& I = x.I;
     const int e = x.e;
     double Gx[3][2][2], Gy[3][2][2], Gz[3][2][2];
-    nodal_grads(g, I, g.us, 1.0, x.node, Gx, Gy, Gz);
-    const double lam = I.lam_e ? I.lam_e[e] : I.lam;
-    const double mu = I.mu_e ? I.mu_e[e] : I.mu;
-    const double kappa = lam + (2.0 / 3.0) * mu;
-    const double m1 = 0.5 * kappa * I.w8, m2 = mu * I.w8, m3 = mu * I.w8 / 3.0;
-    TL* lin = lin_base + I.elem_off + e;
-    const long long st = 8LL * g.NE;  // stride between quantities
-    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int c = 0; c < 3; ++c) {
+        double V[8], Dx[2][2], Dy[2][2], Dz[2][2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int c8 = 0; c8 < 8; ++c8) V[c8] = g.us[(long long)c * g.NN + I.node_off + x.node[c8]];
+        edge_differences_prescaled<double>(V, Dx, Dy, Dz);
+        lerp2<double>(Dx, Gx[c], c == 0);
+        lerp2<double>(Dy, Gy[c], c == 1);
+        lerp2<double>(Dz, Gz[c], c == 2);
+    }
+    double m1, m2, m3;
+    if (I.lam_e || I.mu_e)
+        material_factors<OSAM_NEO_HOOKEAN, double>(I.lam_e ? I.lam_e[e] : I.lam, I.mu_e ? I.mu_e[e] : I.mu, I.wq,
+                                                   I.wq3, m1, m2, m3);
+    else { m1 = I.m1; m2 = I.m2; m3 = I.m3; }
+    const LinStore<TL> store{lin_base + I.elem_off + e, 8LL * g.NE, g.NE, m1};
+    double Sx[3][2][2], Sy[3][2][2], Sz[3][2][2], F[3][8];
+    nh_gauss_sums<double>(Gx, Gy, Gz, m1, m2, m3, Sx, Sy, Sz, store);
+    walsh_transpose<double>(Sx, Sy, Sz, F);
+    double* fe = static_cast<double*>(g.fe) + I.elem_off;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int gp = 4 * p + 2 * q + r;
-                double Hm[3][3], Fm[3][3], Cm[3][3], alpha, beta;
+    for (int c8 = 0; c8 < 8; ++c8)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) { Hm[c][0] = Gx[c][q][r]; Hm[c][1] = Gy[c][p][r]; Hm[c][2] = Gz[c][p][q]; }
-                nh_factors<double>(Hm, m1, m2, m3, Fm, Cm, alpha, beta);
-                const double J = fma(Fm[0][0], Cm[0][0], fma(Fm[0][1], Cm[0][1], Fm[0][2] * Cm[0][2]));
-                double trC = 0.0;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) trC = fma(Fm[a / 3][a % 3], Fm[a / 3][a % 3], trC);
-                const double invJ = 1.0 / J;
-                const double a1 = -(2.0 / 3.0) * alpha * invJ;
-                const double b1 = 2.0 * m1 - invJ * fma(a1, trC * (1.0 / 3.0), beta);
-                TL* lg = lin + (long long)gp * g.NE;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) {
-                    lg[a * st] = TL(Fm[a / 3][a % 3]);
-                    lg[(9 + a) * st] = TL(Cm[a / 3][a % 3]);
-                }
-                lg[18 * st] = TL(alpha); lg[19 * st] = TL(beta); lg[20 * st] = TL(a1); lg[21 * st] = TL(b1);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double P0 = fma(alpha, Fm[c][0], beta * Cm[c][0]);
-                    const double P1 = fma(alpha, Fm[c][1], beta * Cm[c][1]);
-                    const double P2 = fma(alpha, Fm[c][2], beta * Cm[c][2]);
-                    if (p == 0) Sx[c][q][r] = P0; else Sx[c][q][r] += P0;
-                    if (q == 0) Sy[c][p][r] = P1; else Sy[c][p][r] += P1;
-                    if (r == 0) Sz[c][p][q] = P2; else Sz[c][p][q] += P2;
-                }
-            }
-    write_element(g, I, e, Sx, Sy, Sz);
+        for (int c = 0; c < 3; ++c) fe[(long long)(c8 * 3 + c) * g.NE + e] = F[c][c8];
 }
 
 // tangent action from the stored linearisation: per Gauss point 166 FP64 flops instead of 243, and
@@ -348,7 +340,7 @@ __global__ void __launch_bounds__(256) k_tangent_lin_b(const FomB g, const int* 
                     if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
                 }
             }
-    write_element(g, I, e, Sx, Sy, Sz);
+    write_element<double>(static_cast<double*>(g.fe) + I.elem_off, g.NE, e, Sx, Sy, Sz);
 }
 
 // The tangent action of k_tangent_lin_b in FP32 (OSAM_FP64_TANGENT32): the linearisation read as
@@ -430,28 +422,7 @@ __global__ void __launch_bounds__(256) k_tangent_lin32_b(const FomB g, const int
                     if (r == 0) Sz[c][p][q] = dP[c][2]; else Sz[c][p][q] += dP[c][2];
                 }
             }
-    float* fe = g.fe32 + I.elem_off;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float Fc[8], Tm[2][2];
-        lerp2T<float>(Sx[c], Tm);
-#pragma unroll
-        for (int ay = 0; ay < 2; ++ay)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[1 + 2 * ay + 4 * az] = Tm[ay][az]; Fc[2 * ay + 4 * az] = -Tm[ay][az]; }
-        lerp2T<float>(Sy[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int az = 0; az < 2; ++az) { Fc[ax + 2 + 4 * az] += Tm[ax][az]; Fc[ax + 4 * az] -= Tm[ax][az]; }
-        lerp2T<float>(Sz[c], Tm);
-#pragma unroll
-        for (int ax = 0; ax < 2; ++ax)
-#pragma unroll
-            for (int ay = 0; ay < 2; ++ay) { Fc[ax + 2 * ay + 4] += Tm[ax][ay]; Fc[ax + 2 * ay] -= Tm[ax][ay]; }
-#pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) fe[(long long)(c8 * 3 + c) * g.NE + e] = Fc[c8];
-    }
+    write_element<float>(g.fe32 + I.elem_off, g.NE, e, Sx, Sy, Sz);
 }
 
 }  // namespace
