@@ -57,14 +57,14 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "967e0e4190d286474408e350258f88587fcc7deea972eebffd098024c5708ff7",
-                 "bytes_per_launch": 3.567104e6, "tiled": True, "register_cap": 0}
+FORCE_TRAFFIC = {"source_sha256": "87c3938cbd8d72f31ddde5c6a4f4dee2acf03812d007c5bd7954f585fb7c2858",
+                 "bytes_per_launch": 3.566592e6, "tiled": True, "register_cap": 0}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
 TANGENT_BYTES_PER_ELEMENT = 22 * 8 * 8 + 24
-TANGENT_TRAFFIC = {"source_sha256": "62b5af73dcb2441b8e0f127c2e495699e646666c0e90910d1de69a4f67bdb3a4",
-                   "bytes_per_launch": 1.93771e8}
+TANGENT_TRAFFIC = {"source_sha256": "30bd3010b69880f16ca0360afe63e3e3b9e01b95a553c852833b8e45de927967",
+                   "bytes_per_launch": 1.947720e8}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -77,6 +77,9 @@ TANGENT_FLOPS_PER_NH_ELEMENT = 1832
 # bytes the FP32 tangent kernel must move per element: the FP32 linearisation (22 floats x 8 Gauss
 # points) from HBM, p at 8 nodes / 8 elements per node (24 B), the FP32 element buffer out (24 floats)
 TANGENT32_BYTES_PER_ELEMENT = 22 * 8 * 4 + 24 + 24 * 4
+# DRAM traffic of one FP32-tangent launch (ncu, same sources as TANGENT_TRAFFIC)
+TANGENT32_TRAFFIC = {"source_sha256": "30bd3010b69880f16ca0360afe63e3e3b9e01b95a553c852833b8e45de927967",
+                     "bytes_per_launch": 9.370906e7}
 # FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
 # around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
 FLOPS_PER_SVK_ELEMENT = 1424
@@ -691,7 +694,8 @@ def measure_implicit(W, osam, torch, flush, rom_ops, args, local, log, steps=2, 
                      "achieved": t_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": t_gbs / hbm_peak if (t_gbs and hbm_peak) else None, "peak_kind": hbm_kind,
                      "algorithmic_bytes_per_launch": t_bytes, "ms_per_launch": t_launch_ms,
-                     "traffic": None},
+                     "traffic": (TANGENT32_TRAFFIC["bytes_per_launch"]
+                                 if TANGENT32_TRAFFIC["source_sha256"] == source_sha(TANGENT_SOURCES) else None)},
         "speedup_vs_fp64_tangent": (t_upd / t_ms) / (upd / total_ms),
         "parity": "1e-9 relative L2 vs the oracle, 1e-10 vs the FP64 tangent (tests/test_gpu_implicit.py)"}
     log(f"implicit, FP32 tangent: {t_ms / steps:.1f} ms/step, {fp32_tangent['newton_per_substep']:.2f} "

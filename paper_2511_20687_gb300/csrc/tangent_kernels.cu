@@ -218,6 +218,23 @@ __device__ __forceinline__ ElemIdx elem_idx(const FomB& g, const int* mask) {
     return x;
 }
 
+// FP64 -> FP32 for the stored FP32 linearisation, rounded toward zero, with integer operations only
+// (a conversion instruction would take a slot of GB300's FP64 pipe, the bound of the Newton force,
+// 176 times per element): from the IEEE-754 layouts, the sign is kept, the exponent re-biased from
+// 1023 to 127 and the top 23 of the 52 fraction bits kept.  Magnitudes below 2^-126 become zero and
+// above the FP32 range infinity -- the linearisation's entries (F, cof F and the material-scaled
+// factors) lie far inside it.  Relative error below 2^-23, the CG operator's own FP32 level.
+__device__ __forceinline__ float f32_rz(double x) {
+    const unsigned int hi = (unsigned int)(__double_as_longlong(x) >> 32);
+    const unsigned int lo = (unsigned int)__double_as_longlong(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned int frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int mag = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : ((unsigned int)e << 23) | frac);
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+__device__ __forceinline__ double lin_value(double x, double*) { return x; }
+__device__ __forceinline__ float lin_value(double x, float*) { return f32_rz(x); }
+
 // The per-Gauss-point quantities of the Newton linearisation, stored by the Neo-Hookean Gauss sums'
 // hook (TL: the storage type); a1 and b1 from the force's own 1/J (the cube of its reciprocal cube
 // root, no division).  Material factors scaled by h^2/32 like the force's (the Walsh-basis transposed
@@ -236,10 +253,11 @@ struct LinStore {
         TL* lg = lin + (long long)(4 * p + 2 * q + r) * ne;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
-            lg[a * st] = TL(Fm[a / 3][a % 3]);
-            lg[(9 + a) * st] = TL(Cm[a / 3][a % 3]);
+            lg[a * st] = lin_value(Fm[a / 3][a % 3], lg);
+            lg[(9 + a) * st] = lin_value(Cm[a / 3][a % 3], lg);
         }
-        lg[18 * st] = TL(alpha); lg[19 * st] = TL(beta); lg[20 * st] = TL(a1); lg[21 * st] = TL(b1);
+        lg[18 * st] = lin_value(alpha, lg); lg[19 * st] = lin_value(beta, lg);
+        lg[20 * st] = lin_value(a1, lg); lg[21 * st] = lin_value(b1, lg);
     }
 };
 
@@ -346,8 +364,8 @@ __global__ void __launch_bounds__(256) k_tangent_lin_b(const FomB g, const int* 
 // The tangent action of k_tangent_lin_b in FP32 (OSAM_FP64_TANGENT32): the linearisation read as
 // stored in FP32 (half the bytes), the direction p converted once per nodal value, every Gauss-point
 // operation on the FP32 pipes, and the element contributions written in FP32 to the FP32 element
-// buffer (the CG's Ap kernel sums them in FP32 and adds them to its FP64 mass term).  The only FP64-pipe
-// work left is the 24 conversions of p per element.
+// buffer (the CG's Ap kernel sums them in FP32 and adds them to its FP64 mass term).  p is converted
+// with the integer-only f32_rz, so no FP64-pipe instruction is left.
 __global__ void __launch_bounds__(256) k_tangent_lin32_b(const FomB g, const int* __restrict__ mask) {
     const ElemIdx x = elem_idx(g, mask);
     if (!x.ok) return;
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(256) k_tangent_lin32_b(const FomB g, const int
         float V[8], Dx[2][2], Dy[2][2], Dz[2][2];
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8)
-            V[c8] = __double2float_rn(g.cg_p[(long long)c * g.NN + I.node_off + x.node[c8]]) * sc;
+            V[c8] = f32_rz(g.cg_p[(long long)c * g.NN + I.node_off + x.node[c8]]) * sc;
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
