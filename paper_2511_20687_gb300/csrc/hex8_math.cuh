@@ -30,13 +30,38 @@ constexpr double kGd = 0.57735026918962576451;   // kG1 - kG0 = 1/sqrt(3)
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+
+// FP64 <-> FP32 with integer operations only.  GB300 executes the conversion instructions on its FP64
+// pipe, the bound of every FP64 kernel here, so the hot paths rebuild the values from the IEEE-754
+// layouts instead (sign kept, exponent re-biased between 1023 and 127, fraction cut to or widened
+// from 23 bits).  f32_rz rounds toward zero (relative error below 2^-23); magnitudes below 2^-126
+// become zero and beyond the FP32 range infinity (NaN too).  f64_of is exact for normal FP32 values
+// and infinities; FP32 subnormals become zero.
+__device__ __forceinline__ float f32_rz(double x) {
+    const unsigned int hi = (unsigned int)__double2hiint(x);
+    const unsigned int lo = (unsigned int)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned int frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned int mag = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : ((unsigned int)e << 23) | frac);
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+__device__ __forceinline__ double f64_of(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned int e = (b >> 23) & 0xffu;
+    const unsigned int sign = b & 0x80000000u;
+    if (e == 0) return __hiloint2double((int)sign, 0);
+    const unsigned int ed = e == 255 ? 2047u : e + (1023u - 127u);
+    return __hiloint2double((int)(sign | (ed << 20) | ((b & 0x7fffffu) >> 3)), (int)((b & 0x7u) << 29));
+}
+
 // x^(-1/3) in FP64 (x != 0): a single-precision seed y, then one third-order correction from the
 // binomial series of the exact factor (1 - e)^(-1/3) = 1 + e/3 + 2e^2/9 + ..., e = 1 - x y^3 the seed's
 // residual (Householder's third-order iteration for y^-3 = x).  The remaining error is ~14 e^3 / 81:
-// with the seed's |e| < 1e-6 that is below the FP64 rounding.  Six FP64 operations and two
-// conversions; zero, Inf or NaN propagate to a non-finite result (caught by the step's criterion).
+// with the seed's |e| < 1e-6 that is below the FP64 rounding.  Six FP64 operations; the seed's
+// conversions are integer operations (f32_rz, f64_of).  Zero, Inf or NaN propagate to a non-finite
+// result (caught by the step's criterion).
 __device__ __forceinline__ double rcbrtT(double x) {
-    const double y = (double)rcbrtf(__double2float_rn(x));
+    const double y = f64_of(rcbrtf(f32_rz(x)));
     const double e = fma(-x, y * y * y, 1.0);
     return fma(y, e * fma(e, 2.0 / 9.0, 1.0 / 3.0), y);
 }
@@ -449,10 +474,11 @@ __device__ __forceinline__ void edge_differences_split(const float2 V[8], float 
         }
 }
 
-// (hi, lo) float split of an FP64 value
+// (hi, lo) float split of an FP64 value for the FP32 force: hi = v cut to 24 bits, lo = the exact
+// remainder v - hi cut to 24 bits (|v - (hi + lo)| < 2^-47 |v|), by integer conversions
 __device__ __forceinline__ float2 split_f2(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(v - (double)hi));
+    const float hi = f32_rz(v);
+    return make_float2(hi, f32_rz(v - f64_of(hi)));
 }
 
 // nodal force of node (i,j,k), component c, from the element buffer (fixed order: deterministic)

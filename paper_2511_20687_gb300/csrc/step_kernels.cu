@@ -348,12 +348,19 @@ __global__ void __launch_bounds__(kNodeBlock) k_node_b(const FomB g, const int* 
                     }
                 }
             }
-            // FP64: the same sums; FP32 force: summed in FP32 (its own precision) and converted once
+            // FP64: the same sums; FP32 force: summed in FP32 (its own precision) and widened once, by
+            // integer operations (f64_of: exact)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = double(fs[c]);
+            for (int c = 0; c < 3; ++c) {
+                if constexpr (sizeof(TF) == 4) f[c] = f64_of(fs[c]);
+                else f[c] = fs[c];
+            }
         } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) f[c] = double(fa[(long long)c * g.NN + gn]);
+            for (int c = 0; c < 3; ++c) {
+                if constexpr (sizeof(TF) == 4) f[c] = f64_of(fa[(long long)c * g.NN + gn]);
+                else f[c] = fa[(long long)c * g.NN + gn];
+            }
         }
     }
 #pragma unroll

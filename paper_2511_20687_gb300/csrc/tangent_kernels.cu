@@ -218,20 +218,10 @@ __device__ __forceinline__ ElemIdx elem_idx(const FomB& g, const int* mask) {
     return x;
 }
 
-// FP64 -> FP32 for the stored FP32 linearisation, rounded toward zero, with integer operations only
-// (a conversion instruction would take a slot of GB300's FP64 pipe, the bound of the Newton force,
-// 176 times per element): from the IEEE-754 layouts, the sign is kept, the exponent re-biased from
-// 1023 to 127 and the top 23 of the 52 fraction bits kept.  Magnitudes below 2^-126 become zero and
-// above the FP32 range infinity -- the linearisation's entries (F, cof F and the material-scaled
-// factors) lie far inside it.  Relative error below 2^-23, the CG operator's own FP32 level.
-__device__ __forceinline__ float f32_rz(double x) {
-    const unsigned int hi = (unsigned int)(__double_as_longlong(x) >> 32);
-    const unsigned int lo = (unsigned int)__double_as_longlong(x);
-    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-    const unsigned int frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
-    const unsigned int mag = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : ((unsigned int)e << 23) | frac);
-    return __uint_as_float((hi & 0x80000000u) | mag);
-}
+// FP64 -> FP32 for the stored FP32 linearisation by integer operations (f32_rz: a conversion
+// instruction would take a slot of the FP64 pipe, the bound of the Newton force, 176 times per
+// element; the entries -- F, cof F and the material-scaled factors -- lie far inside the FP32 range,
+// and the rounding toward zero is at the CG operator's own FP32 level).
 __device__ __forceinline__ double lin_value(double x, double*) { return x; }
 __device__ __forceinline__ float lin_value(double x, float*) { return f32_rz(x); }
 
