@@ -249,7 +249,7 @@ class ClockSampler:
         return out
 
 
-def source_sha(files=("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh")):
+def source_sha(files=("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh", "fp_bits.cuh")):
     import hashlib
     h = hashlib.sha256()
     for f in files:
@@ -257,7 +257,7 @@ def source_sha(files=("step_kernels.cu", "hex8_math.cuh", "trace_item.cuh")):
     return h.hexdigest()
 
 
-TANGENT_SOURCES = ("tangent_kernels.cu", "hex8_math.cuh", "nh_tangent.cuh")
+TANGENT_SOURCES = ("tangent_kernels.cu", "hex8_math.cuh", "nh_tangent.cuh", "fp_bits.cuh")
 
 
 # ---------------------------------------------------------------------------------------------

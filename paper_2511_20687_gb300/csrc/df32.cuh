@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fp_bits.cuh"
+
 namespace osam {
 namespace df {
 
@@ -75,12 +77,16 @@ __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) {
     return fast_two_sum(s.h, s.l);
 }
 
+// FP64 -> double-float and back with the integer conversions of fp_bits.cuh (the conversion
+// instructions run on GB300's FP64 pipe): h = x cut to 24 bits, l = the exact remainder x - h cut to
+// 24 bits (|x - (h + l)| < 2^-46 |x|), renormalised by FastTwoSum so that |l| <= ulp(h)/2 as the
+// arithmetic above assumes; the way back is exact up to the final FP64 addition
 __device__ __forceinline__ f2 from_double(double x) {
-    const float h = __double2float_rn(x);
-    return f2{h, __double2float_rn(x - (double)h)};
+    const float h = hex8::f32_rz(x);
+    return fast_two_sum(h, hex8::f32_rz(x - hex8::f64_of(h)));
 }
 
-__device__ __forceinline__ double to_double(f2 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double to_double(f2 a) { return hex8::f64_of(a.h) + hex8::f64_of(a.l); }
 
 // x^(-1/3) for x > 0: float seed, one Newton step y <- y + y (1 - x y^3) / 3 in double-float
 // (the seed's relative error e becomes about 2 e^2, below the double-float rounding)
