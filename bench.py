@@ -57,14 +57,14 @@ F32X2_INST_PER_NH_ELEMENT = 12012
 FP32_ISSUE_PEAK_TINST = 152 * 128 * 2.07e9 / 1e12
 # DRAM traffic of one force launch of the bench workload (ncu dram__bytes_read.sum + write.sum),
 # valid only for the kernel source and variant (tiled or not) it was captured on.
-FORCE_TRAFFIC = {"source_sha256": "1a728aca66e20ede056f125191e1851a43bb863b9aa0824c3f2c398a7f87ba38",
+FORCE_TRAFFIC = {"source_sha256": "5329782da603ec0d213b49ef60d6836089a9f41f0ba6bc0fa18cff46cede7c3d",
                  "bytes_per_launch": 3.567616e6, "tiled": True, "register_cap": 0}
 # the same for the Neo-Hookean tangent-action kernel of the implicit block (sources TANGENT_SOURCES)
 # bytes one tangent launch must move per element: the stored linearisation (22 doubles x 8 Gauss
 # points) + p at 8 nodes / 8 elements per node (24 B); the element buffer stays in L2
 TANGENT_BYTES_PER_ELEMENT = 22 * 8 * 8 + 24
-TANGENT_TRAFFIC = {"source_sha256": "49d5d38f10cb3e56c166d195e22992fc9009e1926626e57efb67767a36049df8",
-                   "bytes_per_launch": 1.946766e8}
+TANGENT_TRAFFIC = {"source_sha256": "cd475f28af922fbeaa85abd62d838d03451fea6f47a72d3046ce0d821fae63fc",
+                   "bytes_per_launch": 1.947856e8}
 
 
 STATE_BYTES_PER_NODE_UPDATE = 152
@@ -78,8 +78,8 @@ TANGENT_FLOPS_PER_NH_ELEMENT = 1832
 # points) from HBM, p at 8 nodes / 8 elements per node (24 B), the FP32 element buffer out (24 floats)
 TANGENT32_BYTES_PER_ELEMENT = 22 * 8 * 4 + 24 + 24 * 4
 # DRAM traffic of one FP32-tangent launch (ncu, same sources as TANGENT_TRAFFIC)
-TANGENT32_TRAFFIC = {"source_sha256": "49d5d38f10cb3e56c166d195e22992fc9009e1926626e57efb67767a36049df8",
-                     "bytes_per_launch": 9.363482e7}
+TANGENT32_TRAFFIC = {"source_sha256": "cd475f28af922fbeaa85abd62d838d03451fea6f47a72d3046ce0d821fae63fc",
+                     "bytes_per_launch": 9.375027e7}
 # FP64 flops of one Saint Venant-Kirchhoff element force: the 504 flops of the sum factorisation
 # around the constitutive law (as for Neo-Hookean) + 8 x 115 (Green-Lagrange strain 48, S 13, P = F S 54)
 FLOPS_PER_SVK_ELEMENT = 1424
